@@ -1,0 +1,28 @@
+"""Named synthetic workloads for LIDER batched search.
+
+Each entry fixes the corpus/query generator recipe (see ``synth``) and the
+index/search parameters in the paper's vocabulary (Table 1, Sec. 6):
+``n_clusters`` = c (total k-means clusters), ``c`` = c_0 (clusters probed per
+query), ``L`` = H (hashkey arrays per core model), ``m`` = M (hashes per
+hashkey), ``r0`` with R = r0 * k (expansion range per array, Sec. 6.1),
+``leaves`` = RMI width (number of second-stage linear models, Sec. 5.2),
+``W`` = p-stable bucket width.
+"""
+
+CONFIGS = {
+    # Plain method, tiny: every query fits the oracle in seconds.
+    "tiny": dict(n=10_000, d=128, n_comp=64, sigma=0.3, zipf_s=None, nq=1_000,
+                 n_clusters=16, c=4, L=4, m=8, W=1.0, leaves=16, k=10, r0=2,
+                 B=1, kmeans_iters=10, kmeans_sample=10_000, seed=0),
+    # Plain method, mid: 1M x 768, 256 clusters, c=8, L=8, m=16, k=100.
+    "mid": dict(n=1_000_000, d=768, n_comp=1_024, sigma=0.3, zipf_s=None, nq=10_000,
+                n_clusters=256, c=8, L=8, m=16, W=1.0, leaves=1_024, k=100, r0=2,
+                B=1, kmeans_iters=10, kmeans_sample=65_536, seed=0),
+}
+
+
+def get(name: str) -> dict:
+    cfg = dict(CONFIGS[name])
+    cfg["name"] = name
+    cfg["R"] = cfg["r0"] * cfg["k"]
+    return cfg
