@@ -1,0 +1,188 @@
+/*
+ * lider.h -- C ABI of LIDER batched query search on one B300 (sm_103a).
+ *
+ * LIDER (arXiv 2205.00970) indexes dense embeddings with a clustering-based
+ * two-layer architecture (Sec. 3.2): k-means clusters, and inside each cluster
+ * a core model made of ESK-LSH hashkey arrays (Sec. 4), key re-scaling
+ * (Sec. 5.1) and one simplified two-stage RMI per array (Sec. 5.2).  A query
+ * is routed to its nearest clusters, hashed, located in every sorted array,
+ * expanded bi-directionally, and its candidates are scored by exact inner
+ * product; the per-cluster top-k lists are merged (Sec. 3.3.2, Sec. 6.2).
+ *
+ * Conventions for every entry point:
+ *   - return LIDER_OK (0) on success, a negative LIDER_E* code otherwise; the
+ *     message of the last failure on the calling thread is lider_last_error();
+ *   - no C++ exception crosses this boundary;
+ *   - pointers documented "device" must be CUDA device (or managed) memory on
+ *     the current device; "host" pointers are ordinary host memory;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream); device work is enqueued on it and, unless stated otherwise, the
+ *     call returns before that work completes;
+ *   - matrices are row-major FP32 with rows of d contiguous floats;
+ *   - there is no CPU fallback: without a usable CUDA device every call that
+ *     needs one fails with LIDER_ECUDA.
+ */
+#ifndef LIDER_H_
+#define LIDER_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LIDER_OK        0
+#define LIDER_EINVAL   -1   /* an argument is out of range or inconsistent   */
+#define LIDER_ENOMEM   -2   /* a device allocation failed                     */
+#define LIDER_ECUDA    -3   /* a CUDA runtime call or kernel launch failed    */
+#define LIDER_ELIMIT   -4   /* a size exceeds a documented implementation cap */
+
+#define LIDER_HASH_PSTABLE 0   /* h = floor((a.x + b) / W), Sec. 4.1 (p-stable) */
+
+/* Implementation caps (checked; LIDER_ELIMIT beyond them). */
+#define LIDER_MAX_L        32      /* hashkey arrays per core model (H)     */
+#define LIDER_MAX_C        32      /* clusters probed per query (c_0)       */
+#define LIDER_MAX_K        1024    /* results per query                     */
+#define LIDER_MAX_LR       4096    /* L * R candidates per (query, cluster) */
+#define LIDER_MAX_D        4096    /* embedding dimension                   */
+
+typedef struct lider_index lider_index;   /* opaque; owns its device memory */
+
+/* Index parameters, in the paper's notation (Table 1):
+ *   L  = H, number of hashkey arrays (LSH repetitions) per core model;
+ *   m  = M, hashes per hashkey; each packs into floor(64/m) bits with offset
+ *        2^(floor(64/m)-1) and clamping (a 64-bit sortable key);
+ *   rmi_leaves = width of the RMI second stage (linear models per array);
+ *   r0 = expansion factor, R = r0 * k positions per array (Sec. 6.1);
+ *   B  = elements read by KD_e in the extended hashkey distance dist_e
+ *        (Sec. 4.2); floor(64/m) * B must be <= 56;
+ *   hash_kind = LIDER_HASH_PSTABLE;
+ *   W  = p-stable bucket width (> 0). */
+typedef struct {
+    int32_t L;
+    int32_t m;
+    int32_t rmi_leaves;
+    int32_t r0;
+    int32_t B;
+    int32_t hash_kind;
+    double  W;
+} lider_params;
+
+/* Counters of one search (host struct, filled when the call returns). */
+typedef struct {
+    int64_t n_queries;
+    int64_t pairs;             /* (query, probed cluster) pairs searched          */
+    int64_t candidates;        /* unique candidates scored, summed over pairs      */
+    int64_t qkey_boundary;     /* query hash values within 1e-6*W of a bucket edge */
+    int64_t qkey_clamped;      /* query hash values clamped into the element range */
+    int64_t locate_fallback;   /* lower bounds found outside the RMI error window  */
+    int64_t empty_pairs;       /* probed clusters that hold no point               */
+    int64_t reserved;
+} lider_search_stats;
+
+/* Optional per-step outputs of a search, for parity checking.  Every member
+ * may be NULL; non-NULL members are device arrays the caller allocates:
+ *   route  [nq*c]    probed clusters of each query, best first;
+ *   qkeys  [nq*L]    packed query hashkeys;
+ *   pstar  [nq*c*L]  lower bound of the query key in each probed cluster's array
+ *                    (cluster-local position);
+ *   wstart [nq*c*L]  start of the expansion window (cluster-local);
+ *   wlen   [nq*c*L]  its length, min(R, n_c);
+ *   ucount [nq*c]    unique candidates scored in each probed cluster. */
+typedef struct {
+    int32_t*  route;
+    uint64_t* qkeys;
+    int32_t*  pstar;
+    int32_t*  wstart;
+    int32_t*  wlen;
+    int32_t*  ucount;
+} lider_trace;
+
+/* Build an index (Sec. 3.3.2 "LIDER is built as follows"; Sec. 3.3.1 for one
+ * core model; Table 5 stages 2-3).
+ *   corpus     device, n x d FP32, the embeddings (n >= 1, d % 4 == 0);
+ *   centroids  device, n_clusters x d FP32, the k-means centroids; every point
+ *              joins the centroid maximising x.mu - |mu|^2/2 (ties: lower index);
+ *   A, b       device, (L*m) x d and (L*m) FP32: row l*m+j of A and entry
+ *              l*m+j of b define hash j of array l (the LSH draws, Sec. 4.1);
+ *   params     host, see lider_params;
+ *   stream     the build runs on it and is synchronised before returning;
+ *   out        host, receives the new index.
+ * The corpus, centroids and projections are copied; the caller keeps
+ * ownership of its buffers.  Errors: LIDER_EINVAL for null pointers, n < 1,
+ * d % 4 != 0, n_clusters < 1, L/m/r0/B/rmi_leaves < 1, W <= 0, an unknown
+ * hash_kind, or floor(64/m)*B > 56; LIDER_ELIMIT past the caps above;
+ * LIDER_ENOMEM / LIDER_ECUDA from the device.  On error *out is NULL. */
+int lider_build(const float* corpus, int64_t n, int32_t d,
+                const float* centroids, int32_t n_clusters,
+                const float* A, const float* b,
+                const lider_params* params, void* stream, lider_index** out);
+
+/* Batched k-NN search (Sec. 3.3.2 "When using LIDER for ANN queries"; Sec. 6).
+ *   queries     device, nq x d FP32;
+ *   k           results per query (1..LIDER_MAX_K); R = r0*k, L*R <= LIDER_MAX_LR;
+ *   c           clusters probed per query, c_0 (1..min(n_clusters, LIDER_MAX_C));
+ *   out_ids     device, nq x k int64: corpus row ids, best first (score
+ *               descending, ties by lower id), -1 past the candidates found;
+ *   out_scores  device, nq x k FP32: exact inner products, -inf where id = -1;
+ *   stats       host or NULL; when non-NULL the call synchronises `stream`
+ *               and fills the counters;
+ *   stream      all work is enqueued on it.
+ * Scratch memory comes from a stream-ordered pool owned by the index, so
+ * concurrent calls on different streams are safe; the index is read-only.
+ * nq == 0 is a no-op.  Errors: LIDER_EINVAL (null index/pointers, nq < 0,
+ * k < 1, c < 1 or c > n_clusters), LIDER_ELIMIT (caps), LIDER_ENOMEM,
+ * LIDER_ECUDA. */
+int lider_search(const lider_index* index, const float* queries, int64_t nq,
+                 int32_t k, int32_t c, int64_t* out_ids, float* out_scores,
+                 lider_search_stats* stats, void* stream);
+
+/* lider_search plus the optional per-step outputs of `trace` (may be NULL). */
+int lider_search_trace(const lider_index* index, const float* queries, int64_t nq,
+                       int32_t k, int32_t c, int64_t* out_ids, float* out_scores,
+                       const lider_trace* trace, lider_search_stats* stats,
+                       void* stream);
+
+/* End-to-end form of lider_search on HOST buffers: copies queries (host,
+ * nq x d FP32; pinned memory gives asynchronous copies) to the device,
+ * searches, copies ids/scores back into host arrays of nq x k, and
+ * synchronises `stream` before returning.  Same arguments and errors. */
+int lider_search_host(const lider_index* index, const float* queries_host, int64_t nq,
+                      int32_t k, int32_t c, int64_t* ids_host, float* scores_host,
+                      lider_search_stats* stats, void* stream);
+
+/* Index shape, host outputs (any may be NULL). */
+int lider_index_info(const lider_index* index, int64_t* n, int32_t* d,
+                     int32_t* n_clusters, lider_params* params);
+
+/* Cluster sizes as offsets, host array of n_clusters + 1 entries: points of
+ * cluster j are rows offsets[j]..offsets[j+1]-1 of the index's reordered copy. */
+int lider_cluster_offsets(const lider_index* index, int64_t* offsets_host);
+
+/* Copy one sorted hashkey array of one core model to host memory (parity
+ * checks).  keys_host: n_c uint64 keys in SK-LSH order; ids_host: n_c corpus
+ * row ids (int64), equal keys ordered by id.  Synchronous. */
+int lider_export_array(const lider_index* index, int32_t cluster, int32_t array,
+                       uint64_t* keys_host, int64_t* ids_host);
+
+/* Copy the RMI of one (cluster, array) to host memory.  Synchronous.
+ *   minmax_host [2]   x_min, x_max of the re-scaling (Sec. 5.1);
+ *   root_host   [2]   intercept, slope of the first stage;
+ *   leaf_host   [2*F] intercept, slope of each leaf;
+ *   err_host    [2*F] error window [lo, hi] of each leaf: for every key of the
+ *                     leaf, lo <= first position of that key - prediction <= hi. */
+int lider_export_rmi(const lider_index* index, int32_t cluster, int32_t array,
+                     uint64_t* minmax_host, double* root_host, double* leaf_host,
+                     int32_t* err_host);
+
+/* Release the index and its device memory.  NULL is accepted. */
+void lider_free(lider_index* index);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* lider_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIDER_H_ */

@@ -1,0 +1,153 @@
+// extern "C" entry points of liblider.so (declared in include/lider.h) and the
+// thread-local error message.  No C++ exception crosses this boundary.
+#include <exception>
+#include <string>
+
+#include "lider_internal.cuh"
+
+namespace lider {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+const char* g_last_error_ptr() { return g_last_error.c_str(); }
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int fail(int code, const std::string& msg) {
+    set_error(msg);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    cudaGetLastError();   // clear a non-sticky error so the next call starts clean
+    set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+    return e == cudaErrorMemoryAllocation ? LIDER_ENOMEM : LIDER_ECUDA;
+}
+
+int build_entry(const float*, int64_t, int32_t, const float*, int32_t, const float*, const float*,
+                const lider_params*, void*, lider_index**);
+void destroy_index(lider_index*);
+int search_entry(const lider_index*, const float*, int64_t, int, int, int64_t*, float*, const lider_trace*,
+                 lider_search_stats*, void*);
+int search_host_entry(const lider_index*, const float*, int64_t, int, int, int64_t*, float*,
+                      lider_search_stats*, void*);
+
+template <class F>
+int guarded(F&& f) {
+    try {
+        return f();
+    } catch (const std::bad_alloc&) {
+        return fail(LIDER_ENOMEM, "host allocation failed");
+    } catch (const std::exception& e) {
+        return fail(LIDER_ECUDA, std::string("internal error: ") + e.what());
+    } catch (...) {
+        return fail(LIDER_ECUDA, "internal error");
+    }
+}
+
+}  // namespace lider
+
+using namespace lider;
+
+extern "C" {
+
+int lider_build(const float* corpus, int64_t n, int32_t d, const float* centroids, int32_t n_clusters,
+                const float* A, const float* b, const lider_params* params, void* stream, lider_index** out) {
+    return guarded([&] { return build_entry(corpus, n, d, centroids, n_clusters, A, b, params, stream, out); });
+}
+
+int lider_search(const lider_index* index, const float* queries, int64_t nq, int32_t k, int32_t c,
+                 int64_t* out_ids, float* out_scores, lider_search_stats* stats, void* stream) {
+    return guarded([&] {
+        return search_entry(index, queries, nq, k, c, out_ids, out_scores, nullptr, stats, stream);
+    });
+}
+
+int lider_search_trace(const lider_index* index, const float* queries, int64_t nq, int32_t k, int32_t c,
+                       int64_t* out_ids, float* out_scores, const lider_trace* trace, lider_search_stats* stats,
+                       void* stream) {
+    return guarded([&] {
+        return search_entry(index, queries, nq, k, c, out_ids, out_scores, trace, stats, stream);
+    });
+}
+
+int lider_search_host(const lider_index* index, const float* queries_host, int64_t nq, int32_t k, int32_t c,
+                      int64_t* ids_host, float* scores_host, lider_search_stats* stats, void* stream) {
+    return guarded([&] {
+        return search_host_entry(index, queries_host, nq, k, c, ids_host, scores_host, stats, stream);
+    });
+}
+
+int lider_index_info(const lider_index* index, int64_t* n, int32_t* d, int32_t* n_clusters, lider_params* params) {
+    if (!index) return fail(LIDER_EINVAL, "lider_index_info: index is NULL");
+    if (n) *n = index->g.n;
+    if (d) *d = index->g.d;
+    if (n_clusters) *n_clusters = index->g.ncl;
+    if (params) *params = index->params;
+    return LIDER_OK;
+}
+
+int lider_cluster_offsets(const lider_index* index, int64_t* offsets_host) {
+    if (!index || !offsets_host) return fail(LIDER_EINVAL, "lider_cluster_offsets: NULL argument");
+    for (size_t i = 0; i < index->h_cl_off.size(); ++i) offsets_host[i] = index->h_cl_off[i];
+    return LIDER_OK;
+}
+
+int lider_export_array(const lider_index* index, int32_t cluster, int32_t array, uint64_t* keys_host,
+                       int64_t* ids_host) {
+    return guarded([&]() -> int {
+        if (!index || !keys_host || !ids_host) return fail(LIDER_EINVAL, "lider_export_array: NULL argument");
+        const Geometry& g = index->g;
+        if (cluster < 0 || cluster >= g.ncl || array < 0 || array >= g.L)
+            return fail(LIDER_EINVAL, "lider_export_array: cluster or array out of range");
+        const int64_t base = index->h_cl_off[cluster], n_c = index->h_cl_off[cluster + 1] - base;
+        if (n_c == 0) return LIDER_OK;
+        LIDER_CUDA_TRY(cudaMemcpy(keys_host, g.keys + (int64_t)array * g.n + base, n_c * 8, cudaMemcpyDeviceToHost));
+        std::vector<int32_t> pos(n_c);
+        std::vector<int64_t> orig(n_c);
+        LIDER_CUDA_TRY(cudaMemcpy(pos.data(), g.pos + (int64_t)array * g.n + base, n_c * 4, cudaMemcpyDeviceToHost));
+        LIDER_CUDA_TRY(cudaMemcpy(orig.data(), g.orig_id + base, n_c * 8, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < n_c; ++i) {
+            if (pos[i] < 0 || pos[i] >= n_c) return fail(LIDER_ECUDA, "lider_export_array: corrupt position");
+            ids_host[i] = orig[pos[i]];
+        }
+        return LIDER_OK;
+    });
+}
+
+int lider_export_rmi(const lider_index* index, int32_t cluster, int32_t array, uint64_t* minmax_host,
+                     double* root_host, double* leaf_host, int32_t* err_host) {
+    return guarded([&]() -> int {
+        if (!index) return fail(LIDER_EINVAL, "lider_export_rmi: index is NULL");
+        const Geometry& g = index->g;
+        if (cluster < 0 || cluster >= g.ncl || array < 0 || array >= g.L)
+            return fail(LIDER_EINVAL, "lider_export_rmi: cluster or array out of range");
+        RmiRoot rt;
+        LIDER_CUDA_TRY(cudaMemcpy(&rt, g.root + (int64_t)cluster * g.L + array, sizeof(rt), cudaMemcpyDeviceToHost));
+        if (minmax_host) { minmax_host[0] = rt.x_min; minmax_host[1] = rt.x_max; }
+        if (root_host) { root_host[0] = rt.a0; root_host[1] = rt.b0; }
+        if (leaf_host || err_host) {
+            std::vector<RmiLeaf> lv(g.F);
+            LIDER_CUDA_TRY(cudaMemcpy(lv.data(), g.leaf + ((int64_t)cluster * g.L + array) * g.F,
+                                      sizeof(RmiLeaf) * g.F, cudaMemcpyDeviceToHost));
+            for (int f = 0; f < g.F; ++f) {
+                if (leaf_host) { leaf_host[2 * f] = lv[f].a; leaf_host[2 * f + 1] = lv[f].b; }
+                if (err_host) { err_host[2 * f] = lv[f].lo; err_host[2 * f + 1] = lv[f].hi; }
+            }
+        }
+        return LIDER_OK;
+    });
+}
+
+void lider_free(lider_index* index) {
+    try {
+        destroy_index(index);
+    } catch (...) {
+    }
+}
+
+const char* lider_last_error(void) { return g_last_error_ptr(); }
+
+}  // extern "C"

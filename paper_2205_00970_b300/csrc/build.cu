@@ -1,0 +1,414 @@
+// Index construction (Sec. 3.3.2 "LIDER is built as follows", Sec. 3.3.1 for
+// one core model): partition the corpus by nearest centroid, hash every point
+// into L packed hashkeys, sort each (cluster, array) segment by key (ties by
+// id), then fit one two-stage linear RMI per segment on re-scaled keys
+// (Sec. 5.1, Sec. 5.2) and record each leaf's error window.
+//
+// Build is not on the search hot path; its sorts use CUB.
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_segmented_radix_sort.cuh>
+
+#include <algorithm>
+#include <cmath>
+
+#include "lider_internal.cuh"
+
+namespace lider {
+
+int score_kernel_occupancy(int d, int max_lr, int* blocks_per_sm);   // search.cu
+
+namespace {
+
+constexpr int64_t kRowChunk = 131072;   // rows per hashing / assignment pass
+
+__global__ void half_norm_kernel(const float* __restrict__ C, int ncl, int d, double* __restrict__ hn) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ncl) return;
+    double s = 0.0;
+    for (int i = 0; i < d; ++i) {
+        const double v = (double)C[(int64_t)j * d + i];
+        s = __dadd_rn(s, __dmul_rn(v, v));      // each product is exact in FP64
+    }
+    hn[j] = 0.5 * s;
+}
+
+// Nearest centroid per row: argmax of x.mu - |mu|^2/2, ties -> lower index.
+__global__ void argmax_rows_kernel(const double* __restrict__ S, int64_t n, int ncl,
+                                   int64_t row_offset, int32_t* __restrict__ asg) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    double best = -INFINITY;
+    int bj = 0x7fffffff;
+    for (int j = lane; j < ncl; j += 32) {
+        const double v = S[row * ncl + j];
+        if (v > best || (v == best && j < bj)) { best = v; bj = j; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+        if (ov > best || (ov == best && oj < bj)) { best = ov; bj = oj; }
+    }
+    if (lane == 0) asg[row_offset + row] = bj;
+}
+
+__global__ void iota_kernel(int64_t* __restrict__ v, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = i;
+}
+
+// cl_off[j] = first position of cluster j in the sorted assignment.
+__global__ void cluster_offsets_kernel(const int32_t* __restrict__ sorted_asg, int64_t n, int ncl,
+                                       int64_t* __restrict__ cl_off) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > ncl) return;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (sorted_asg[mid] < j) lo = mid + 1; else hi = mid;
+    }
+    cl_off[j] = lo;
+}
+
+// X_re[row] = corpus[orig_id[row]]: one warp per row, float4 copies.
+__global__ void gather_rows_kernel(const float* __restrict__ src, const int64_t* __restrict__ ids,
+                                   int64_t n, int d, float* __restrict__ dst) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const float4* s = reinterpret_cast<const float4*>(src + ids[row] * (int64_t)d);
+    float4* o = reinterpret_cast<float4*>(dst + row * (int64_t)d);
+    for (int i = lane; i < d / 4; i += 32) o[i] = s[i];
+}
+
+// pos[l][row] = row - cl_off[cluster(row)], the cluster-local row index.
+__global__ void local_pos_kernel(const int32_t* __restrict__ sorted_asg, const int64_t* __restrict__ cl_off,
+                                 int64_t n, int L, int32_t* __restrict__ pos) {
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n) return;
+    const int32_t p = (int32_t)(row - cl_off[sorted_asg[row]]);
+    for (int l = 0; l < L; ++l) pos[(int64_t)l * n + row] = p;
+}
+
+// ---------------------------------------------------------------- RMI fit ----
+__device__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+        red[32] = t;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+__device__ __forceinline__ int64_t seg_lower_bound(const uint64_t* K, int64_t n, uint64_t x) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (K[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// One block per (cluster j, array l).  Root: least squares of position i on
+// r_i.  Leaves: the root's prediction selects leaf floor(pred * F / n_c);
+// since r_i is non-decreasing along the sorted array and the root slope is
+// non-negative, every leaf owns one contiguous run of positions, found here by
+// binary search.  Each leaf fits its own least squares (zero variance: slope
+// 0, intercept = mean position; empty: copy of the root) and records
+// [min, max] of (first position of key_i) - prediction_i.
+__global__ void __launch_bounds__(256) rmi_fit_kernel(
+        const uint64_t* __restrict__ keys, const int64_t* __restrict__ cl_off, int64_t n,
+        int L, int F, RmiRoot* __restrict__ roots, RmiLeaf* __restrict__ leaves,
+        int* __restrict__ err_flag) {
+    __shared__ double red[33];
+    const int j = blockIdx.x, l = blockIdx.y;
+    const int64_t base = cl_off[j];
+    const int64_t n_c = cl_off[j + 1] - base;
+    RmiRoot* root = roots + (int64_t)j * L + l;
+    RmiLeaf* lf = leaves + ((int64_t)j * L + l) * F;
+    if (n_c == 0) {
+        if (threadIdx.x == 0) *root = RmiRoot{0.0, 0.0, 0ull, 0ull};
+        for (int f = threadIdx.x; f < F; f += blockDim.x) lf[f] = RmiLeaf{0.0, 0.0, 0, 0};
+        return;
+    }
+    const uint64_t* K = keys + (int64_t)l * n + base;
+    const uint64_t x_min = K[0], x_max = K[n_c - 1];
+
+    // root least squares, two passes
+    double sr = 0.0, sy = 0.0;
+    for (int64_t i = threadIdx.x; i < n_c; i += blockDim.x) {
+        sr += rescale_key(K[i], x_min, x_max, n_c);
+        sy += (double)i;
+    }
+    sr = block_sum(sr, red);
+    sy = block_sum(sy, red);
+    const double rbar = sr / (double)n_c, ybar = sy / (double)n_c;
+    const double r_first = rescale_key(K[0], x_min, x_max, n_c);
+    const double r_last = rescale_key(K[n_c - 1], x_min, x_max, n_c);
+    double a0, b0;
+    if (r_first == r_last) {
+        a0 = ybar; b0 = 0.0;
+    } else {
+        double sxx = 0.0, sxy = 0.0;
+        for (int64_t i = threadIdx.x; i < n_c; i += blockDim.x) {
+            const double dr = rescale_key(K[i], x_min, x_max, n_c) - rbar;
+            sxx += dr * dr;
+            sxy += dr * ((double)i - ybar);
+        }
+        sxx = block_sum(sxx, red);
+        sxy = block_sum(sxy, red);
+        b0 = sxy / sxx;
+        a0 = ybar - b0 * rbar;
+    }
+    if (threadIdx.x == 0) {
+        *root = RmiRoot{a0, b0, x_min, x_max};
+        if (b0 < 0.0) atomicExch(err_flag, 1);   // contiguity of leaves needs b0 >= 0
+    }
+    if (b0 < 0.0) return;
+
+    for (int f = threadIdx.x; f < F; f += blockDim.x) {
+        // first position whose leaf is >= f, and >= f + 1
+        int64_t bounds[2];
+        for (int e = 0; e < 2; ++e) {
+            int64_t lo = 0, hi = n_c;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                const double r = rescale_key(K[mid], x_min, x_max, n_c);
+                if (rmi_leaf(a0, b0, r, F, n_c) < f + e) lo = mid + 1; else hi = mid;
+            }
+            bounds[e] = lo;
+        }
+        const int64_t s = bounds[0], t = bounds[1];
+        if (s >= t) {
+            lf[f] = RmiLeaf{a0, b0, 0, 0};
+            continue;
+        }
+        const int64_t cnt = t - s;
+        double lr = 0.0, ly = 0.0;
+        for (int64_t i = s; i < t; ++i) {
+            lr += rescale_key(K[i], x_min, x_max, n_c);
+            ly += (double)i;
+        }
+        const double lrbar = lr / (double)cnt, lybar = ly / (double)cnt;
+        double a, b;
+        if (rescale_key(K[s], x_min, x_max, n_c) == rescale_key(K[t - 1], x_min, x_max, n_c)) {
+            a = lybar; b = 0.0;
+        } else {
+            double sxx = 0.0, sxy = 0.0;
+            for (int64_t i = s; i < t; ++i) {
+                const double dr = rescale_key(K[i], x_min, x_max, n_c) - lrbar;
+                sxx += dr * dr;
+                sxy += dr * ((double)i - lybar);
+            }
+            b = sxy / sxx;
+            a = lybar - b * lrbar;
+        }
+        int64_t elo = INT64_MAX, ehi = INT64_MIN;
+        for (int64_t i = s; i < t; ++i) {
+            const double r = rescale_key(K[i], x_min, x_max, n_c);
+            const int64_t lb = (i > s && K[i - 1] != K[i]) ? i : seg_lower_bound(K, i, K[i]);
+            const int64_t e = lb - rmi_predict(a, b, r, n_c);
+            elo = min(elo, e);
+            ehi = max(ehi, e);
+        }
+        lf[f] = RmiLeaf{a, b, (int32_t)elo, (int32_t)ehi};
+    }
+}
+
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+    template <class T> T* as() { return static_cast<T*>(p); }
+};
+
+int dev_alloc(void** p, size_t bytes, const char* what) {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LIDER_ENOMEM, std::string("cudaMalloc failed for ") + what + " (" +
+                                      std::to_string(bytes) + " bytes): " + cudaGetErrorString(e));
+    }
+    return LIDER_OK;
+}
+
+void release(lider_index* ix) {
+    if (!ix) return;
+    void* bufs[] = {ix->X, ix->orig_id, ix->cl_off, ix->C, ix->half_norm, ix->A, ix->bproj,
+                    ix->keys, ix->pos, ix->root, ix->leaf};
+    for (void* p : bufs)
+        if (p) cudaFree(p);
+    if (ix->pool) cudaMemPoolDestroy(ix->pool);
+    delete ix;
+}
+
+int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids, int32_t ncl,
+               const float* A, const float* b, const lider_params* P, cudaStream_t st,
+               lider_index** out) {
+    if (!out) return fail(LIDER_EINVAL, "lider_build: out is NULL");
+    *out = nullptr;
+    if (!corpus || !centroids || !A || !b || !P) return fail(LIDER_EINVAL, "lider_build: NULL argument");
+    if (n < 1 || n > (int64_t)INT32_MAX) return fail(LIDER_EINVAL, "lider_build: n must be in [1, 2^31-1]");
+    if (d < 4 || d % 4 != 0) return fail(LIDER_EINVAL, "lider_build: d must be a positive multiple of 4");
+    if (d > LIDER_MAX_D) return fail(LIDER_ELIMIT, "lider_build: d exceeds LIDER_MAX_D");
+    if (ncl < 1) return fail(LIDER_EINVAL, "lider_build: n_clusters must be >= 1");
+    if (P->L < 1 || P->m < 1 || P->rmi_leaves < 1 || P->r0 < 1 || P->B < 1)
+        return fail(LIDER_EINVAL, "lider_build: L, m, rmi_leaves, r0 and B must be >= 1");
+    if (!(P->W > 0.0) || !std::isfinite(P->W)) return fail(LIDER_EINVAL, "lider_build: W must be > 0");
+    if (P->hash_kind != LIDER_HASH_PSTABLE) return fail(LIDER_EINVAL, "lider_build: unknown hash_kind");
+    if (P->m > 64) return fail(LIDER_EINVAL, "lider_build: m must be <= 64");
+    const int beta = 64 / P->m;
+    if ((int64_t)beta * P->B > 56) return fail(LIDER_EINVAL, "lider_build: floor(64/m) * B must be <= 56");
+    if (P->L > LIDER_MAX_L) return fail(LIDER_ELIMIT, "lider_build: L exceeds LIDER_MAX_L");
+    if (P->rmi_leaves > (1 << 24)) return fail(LIDER_ELIMIT, "lider_build: rmi_leaves too large");
+
+    int dev = 0;
+    LIDER_CUDA_TRY(cudaGetDevice(&dev));
+    lider_index* ix = new lider_index();
+    struct Guard {
+        lider_index* ix;
+        ~Guard() { if (ix) release(ix); }
+    } guard{ix};
+    ix->device = dev;
+    ix->params = *P;
+    LIDER_CUDA_TRY(cudaDeviceGetAttribute(&ix->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    const int L = P->L, m = P->m, H = L * m, F = P->rmi_leaves;
+
+    int rc;
+#define ALLOC(ptr, bytes, what) \
+    if ((rc = dev_alloc((void**)&(ptr), (bytes), what)) != LIDER_OK) return rc
+    ALLOC(ix->X, (size_t)n * d * sizeof(float), "corpus");
+    ALLOC(ix->orig_id, (size_t)n * sizeof(int64_t), "ids");
+    ALLOC(ix->cl_off, (size_t)(ncl + 1) * sizeof(int64_t), "cluster offsets");
+    ALLOC(ix->C, (size_t)ncl * d * sizeof(float), "centroids");
+    ALLOC(ix->half_norm, (size_t)ncl * sizeof(double), "centroid norms");
+    ALLOC(ix->A, (size_t)H * d * sizeof(float), "projections");
+    ALLOC(ix->bproj, (size_t)H * sizeof(float), "offsets");
+    ALLOC(ix->keys, (size_t)L * n * sizeof(uint64_t), "keys");
+    ALLOC(ix->pos, (size_t)L * n * sizeof(int32_t), "positions");
+    ALLOC(ix->root, (size_t)ncl * L * sizeof(RmiRoot), "rmi roots");
+    ALLOC(ix->leaf, (size_t)ncl * L * F * sizeof(RmiLeaf), "rmi leaves");
+
+    LIDER_CUDA_TRY(cudaMemcpyAsync(ix->C, centroids, (size_t)ncl * d * sizeof(float), cudaMemcpyDefault, st));
+    LIDER_CUDA_TRY(cudaMemcpyAsync(ix->A, A, (size_t)H * d * sizeof(float), cudaMemcpyDefault, st));
+    LIDER_CUDA_TRY(cudaMemcpyAsync(ix->bproj, b, (size_t)H * sizeof(float), cudaMemcpyDefault, st));
+    half_norm_kernel<<<(unsigned)cdiv(ncl, 128), 128, 0, st>>>(ix->C, ncl, d, ix->half_norm);
+    LIDER_LAUNCH_CHECK("half_norm_kernel");
+
+    // 1. partition: nearest centroid of every point
+    const int64_t chunk = std::min<int64_t>(n, kRowChunk);
+    DevBuf asg, asg_sorted, ids_in, tbuf, sbuf, errf;
+    ALLOC(asg.p, (size_t)n * sizeof(int32_t), "assignment");
+    ALLOC(asg_sorted.p, (size_t)n * sizeof(int32_t), "sorted assignment");
+    ALLOC(ids_in.p, (size_t)n * sizeof(int64_t), "ids");
+    ALLOC(sbuf.p, (size_t)chunk * std::max(ncl, H) * sizeof(double), "score chunk");
+    ALLOC(errf.p, 64, "flags");
+    LIDER_CUDA_TRY(cudaMemsetAsync(errf.p, 0, 64, st));
+    for (int64_t r0 = 0; r0 < n; r0 += chunk) {
+        const int64_t rows = std::min(chunk, n - r0);
+        if ((rc = launch_scores(corpus + r0 * d, rows, d, ix->C, ix->half_norm, ncl, sbuf.as<double>(), st)))
+            return rc;
+        argmax_rows_kernel<<<(unsigned)cdiv(rows * 32, 256), 256, 0, st>>>(sbuf.as<double>(), rows, ncl, r0,
+                                                                          asg.as<int32_t>());
+        LIDER_LAUNCH_CHECK("argmax_rows_kernel");
+    }
+
+    // 2. stable reorder by cluster (ids ascending inside each cluster)
+    iota_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(ids_in.as<int64_t>(), n);
+    LIDER_LAUNCH_CHECK("iota_kernel");
+    int end_bit = 1;
+    while ((1ll << end_bit) <= ncl) ++end_bit;
+    {
+        size_t tmp_bytes = 0;
+        LIDER_CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, asg.as<int32_t>(), asg_sorted.as<int32_t>(),
+                                                       ids_in.as<int64_t>(), ix->orig_id, n, 0, end_bit, st));
+        DevBuf tmp;
+        ALLOC(tmp.p, tmp_bytes, "sort scratch");
+        LIDER_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp.p, tmp_bytes, asg.as<int32_t>(), asg_sorted.as<int32_t>(),
+                                                       ids_in.as<int64_t>(), ix->orig_id, n, 0, end_bit, st));
+    }
+    cluster_offsets_kernel<<<(unsigned)cdiv(ncl + 1, 128), 128, 0, st>>>(asg_sorted.as<int32_t>(), n, ncl, ix->cl_off);
+    LIDER_LAUNCH_CHECK("cluster_offsets_kernel");
+    gather_rows_kernel<<<(unsigned)cdiv(n * 32, 256), 256, 0, st>>>(corpus, ix->orig_id, n, d, ix->X);
+    LIDER_LAUNCH_CHECK("gather_rows_kernel");
+
+    // 3. hash every point (shared projections), keys laid out [array][row]
+    DevBuf keys_tmp, pos_tmp;
+    ALLOC(keys_tmp.p, (size_t)L * n * sizeof(uint64_t), "key scratch");
+    ALLOC(pos_tmp.p, (size_t)L * n * sizeof(int32_t), "position scratch");
+    for (int64_t r0 = 0; r0 < n; r0 += chunk) {
+        const int64_t rows = std::min(chunk, n - r0);
+        if ((rc = launch_hash_t(ix->X + r0 * d, rows, d, ix->A, ix->bproj, H, P->W, sbuf.as<double>(), st))) return rc;
+        if ((rc = launch_pack(sbuf.as<double>(), rows, L, m, beta, r0, 1, n, keys_tmp.as<uint64_t>(), nullptr,
+                              nullptr, st)))
+            return rc;
+    }
+    local_pos_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(asg_sorted.as<int32_t>(), ix->cl_off, n, L,
+                                                           pos_tmp.as<int32_t>());
+    LIDER_LAUNCH_CHECK("local_pos_kernel");
+
+    // 4. sort every (cluster, array) segment by key; radix sort is stable, so
+    //    equal keys stay in ascending position (= ascending id) order
+    {
+        size_t tmp_bytes = 0;
+        LIDER_CUDA_TRY(cub::DeviceSegmentedRadixSort::SortPairs(
+            nullptr, tmp_bytes, keys_tmp.as<uint64_t>(), ix->keys, pos_tmp.as<int32_t>(), ix->pos, n, ncl,
+            ix->cl_off, ix->cl_off + 1, 0, 64, st));
+        DevBuf tmp;
+        ALLOC(tmp.p, tmp_bytes, "segmented sort scratch");
+        for (int l = 0; l < L; ++l) {
+            LIDER_CUDA_TRY(cub::DeviceSegmentedRadixSort::SortPairs(
+                tmp.p, tmp_bytes, keys_tmp.as<uint64_t>() + (int64_t)l * n, ix->keys + (int64_t)l * n,
+                pos_tmp.as<int32_t>() + (int64_t)l * n, ix->pos + (int64_t)l * n, n, ncl, ix->cl_off,
+                ix->cl_off + 1, 0, 64, st));
+        }
+    }
+
+    // 5. RMI per (cluster, array)
+    rmi_fit_kernel<<<dim3(ncl, L), 256, 0, st>>>(ix->keys, ix->cl_off, n, L, F, ix->root, ix->leaf,
+                                                errf.as<int>());
+    LIDER_LAUNCH_CHECK("rmi_fit_kernel");
+
+    ix->h_cl_off.resize(ncl + 1);
+    LIDER_CUDA_TRY(cudaMemcpyAsync(ix->h_cl_off.data(), ix->cl_off, (ncl + 1) * sizeof(int64_t),
+                                   cudaMemcpyDeviceToHost, st));
+    int h_err = 0;
+    LIDER_CUDA_TRY(cudaMemcpyAsync(&h_err, errf.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LIDER_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h_err) return fail(LIDER_ECUDA, "lider_build: negative RMI root slope (unsorted segment)");
+
+    // stream-ordered pool for search scratch; memory is kept between calls
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    LIDER_CUDA_TRY(cudaMemPoolCreate(&ix->pool, &props));
+    uint64_t thr = UINT64_MAX;
+    LIDER_CUDA_TRY(cudaMemPoolSetAttribute(ix->pool, cudaMemPoolAttrReleaseThreshold, &thr));
+
+    Geometry& g = ix->g;
+    g.n = n; g.d = d; g.ncl = ncl; g.L = L; g.m = m; g.F = F; g.beta = beta; g.B = P->B; g.H = H;
+    g.W = P->W;
+    g.X = ix->X; g.orig_id = ix->orig_id; g.cl_off = ix->cl_off; g.C = ix->C; g.half_norm = ix->half_norm;
+    g.A = ix->A; g.bproj = ix->bproj; g.keys = ix->keys; g.pos = ix->pos; g.root = ix->root; g.leaf = ix->leaf;
+#undef ALLOC
+    guard.ix = nullptr;
+    *out = ix;
+    return LIDER_OK;
+}
+
+}  // namespace
+
+void destroy_index(lider_index* ix) { release(ix); }
+
+int build_entry(const float* corpus, int64_t n, int32_t d, const float* centroids, int32_t ncl,
+                const float* A, const float* b, const lider_params* P, void* stream, lider_index** out) {
+    return build_impl(corpus, n, d, centroids, ncl, A, b, P, (cudaStream_t)stream, out);
+}
+
+}  // namespace lider

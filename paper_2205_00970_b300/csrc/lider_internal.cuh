@@ -1,0 +1,194 @@
+// Internal definitions shared by the LIDER CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lider.h"
+
+namespace lider {
+
+// ---------------------------------------------------------------- errors ----
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define LIDER_CUDA_TRY(expr)                                   \
+    do {                                                       \
+        cudaError_t _e = (expr);                               \
+        if (_e != cudaSuccess) return ::lider::cuda_fail(_e, #expr); \
+    } while (0)
+
+#define LIDER_LAUNCH_CHECK(name)                               \
+    do {                                                       \
+        cudaError_t _e = cudaGetLastError();                   \
+        if (_e != cudaSuccess) return ::lider::cuda_fail(_e, name); \
+    } while (0)
+
+// ----------------------------------------------------------------- index ----
+struct RmiLeaf {          // one second-stage linear model and its error window
+    double a;             // intercept
+    double b;             // slope
+    int32_t lo;           // min(first position of key - prediction)
+    int32_t hi;           // max(...)
+};
+static_assert(sizeof(RmiLeaf) == 24, "RmiLeaf layout");
+
+struct RmiRoot {          // first stage and re-scaling range of one (cluster, array)
+    double a0, b0;
+    uint64_t x_min, x_max;
+};
+
+struct Geometry {         // everything a search kernel needs, passed by value
+    int64_t n;
+    int32_t d, ncl, L, m, F, beta, B, H;
+    double W;
+    const float* X;         // n x d, rows grouped by cluster
+    const int64_t* orig_id; // n
+    const int64_t* cl_off;  // ncl + 1
+    const float* C;         // ncl x d
+    const double* half_norm;// ncl
+    const float* A;         // H x d
+    const float* bproj;     // H
+    const uint64_t* keys;   // L x n
+    const int32_t* pos;     // L x n, cluster-local row of each sorted entry
+    const RmiRoot* root;    // ncl x L
+    const RmiLeaf* leaf;    // ncl x L x F
+};
+
+}  // namespace lider
+
+struct lider_index {
+    lider::Geometry g;
+    lider_params params;
+    int device = 0;
+    std::vector<int64_t> h_cl_off;
+    // owned device buffers
+    float* X = nullptr;
+    int64_t* orig_id = nullptr;
+    int64_t* cl_off = nullptr;
+    float* C = nullptr;
+    double* half_norm = nullptr;
+    float* A = nullptr;
+    float* bproj = nullptr;
+    uint64_t* keys = nullptr;
+    int32_t* pos = nullptr;
+    lider::RmiRoot* root = nullptr;
+    lider::RmiLeaf* leaf = nullptr;
+    cudaMemPool_t pool = nullptr;
+    int score_blocks_per_sm = 1;
+    int num_sms = 148;
+};
+
+namespace lider {
+
+// ------------------------------------------------------ Dot2 arithmetic ----
+// Compensated dot product (Ogita, Rump and Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 2005, Algorithm Dot2): TwoProduct via FMA and
+// TwoSum, accumulated in FP32; s + c carries about twice the working
+// precision.  All operations use explicit round-to-nearest intrinsics so that
+// the compiler cannot contract or reassociate them.
+struct Dot2 {
+    float s, c;
+};
+
+__device__ __forceinline__ void dot2_step(Dot2& acc, float a, float b) {
+    float p = __fmul_rn(a, b);
+    float e = __fmaf_rn(a, b, -p);              // exact: a*b = p + e
+    float t = __fadd_rn(acc.s, p);
+    float z = __fadd_rn(t, -acc.s);
+    float err = __fadd_rn(__fadd_rn(acc.s, -__fadd_rn(t, -z)), __fadd_rn(p, -z));  // exact: s+p = t+err
+    acc.s = t;
+    acc.c = __fadd_rn(acc.c, __fadd_rn(err, e));
+}
+
+__device__ __forceinline__ double dot2_value(const Dot2& acc) {
+    return __dadd_rn((double)acc.s, (double)acc.c);
+}
+
+// ----------------------------------------------- hashkey distance dist_e ----
+// Packed key: element j (j = 0 most significant, i.e. h_1) in bits
+// [beta*(m-1-j), beta*(m-j)).  Returns (KL << 57) | KD_e so that one unsigned
+// comparison orders pairs exactly like dist_e = KL + KD_e / 2^(beta*B)
+// (Sec. 4.2).  Requires beta*B <= 56.
+__device__ __forceinline__ uint64_t dist_code(uint64_t a, uint64_t q, int m, int beta, int B) {
+    uint64_t x = a ^ q;
+    if (x == 0) return 0;
+    int nb = m * beta;
+    int lz = __clzll(x) - (64 - nb);
+    int lcp = lz / beta;
+    int rem = m - lcp;                           // elements after the prefix (>= 1)
+    int wb = beta * B;
+    uint64_t mask = (wb >= 64) ? ~0ull : ((1ull << wb) - 1);
+    uint64_t da, dq;
+    if (B <= rem) {
+        int sh = beta * (rem - B);
+        da = (a >> sh) & mask;
+        dq = (q >> sh) & mask;
+    } else {
+        int rb = beta * rem;
+        uint64_t rmask = (rb >= 64) ? ~0ull : ((1ull << rb) - 1);
+        int sh = beta * (B - rem);
+        da = (a & rmask) << sh;
+        dq = (q & rmask) << sh;
+    }
+    uint64_t kd = da > dq ? da - dq : dq - da;
+    return ((uint64_t)(m - lcp) << 57) | kd;
+}
+
+// Order-preserving map of an FP32 score to uint32 (ascending).
+__device__ __forceinline__ uint32_t float_order(float f) {
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float float_from_order(uint32_t u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// ------------------------------------------------------------ re-scaling ----
+// r = (x - x_min) / (x_max - x_min) * (n_c - 1), Sec. 5.1; the difference is an
+// exact integer, converted to FP64 with round-to-nearest; a key below x_min
+// gives r < 0 (query keys only).
+__device__ __forceinline__ double rescale_key(uint64_t x, uint64_t x_min, uint64_t x_max, int64_t n_c) {
+    if (x_max == x_min) return 0.0;
+    double num = (x >= x_min) ? __ull2double_rn(x - x_min) : -__ull2double_rn(x_min - x);
+    double den = __ull2double_rn(x_max - x_min);
+    return __dmul_rn(__ddiv_rn(num, den), (double)(n_c - 1));
+}
+
+// Leaf of the second RMI stage: clamp(floor((a0 + b0 r) * F / n_c), 0, F-1).
+__device__ __forceinline__ int rmi_leaf(double a0, double b0, double r, int F, int64_t n_c) {
+    double g = __ddiv_rn(__dmul_rn(__dadd_rn(a0, __dmul_rn(b0, r)), (double)F), (double)n_c);
+    g = floor(g);
+    if (!(g > 0.0)) return 0;                   // also catches NaN
+    if (g >= (double)(F - 1)) return F - 1;
+    return (int)g;
+}
+
+// Clamped floor prediction of a linear model: clamp(floor(a + b r), 0, n_c - 1).
+__device__ __forceinline__ int64_t rmi_predict(double a, double b, double r, int64_t n_c) {
+    double p = floor(__dadd_rn(a, __dmul_rn(b, r)));
+    if (!(p > 0.0)) return 0;
+    if (p >= (double)(n_c - 1)) return n_c - 1;
+    return (int64_t)p;
+}
+
+// ------------------------------------------------------- small utilities ----
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+__device__ __forceinline__ size_t align_up_dev(size_t x, size_t a) { return (x + a - 1) / a * a; }
+__device__ __forceinline__ int next_pow2_dev(int x) { return x <= 1 ? 1 : 1 << (32 - __clz(x - 1)); }
+
+// Device kernels shared between translation units (defined in kernels.cu).
+int launch_hash_t(const float* X, int64_t n, int d, const float* A, const float* b, int H,
+                  double W, double* t_out, cudaStream_t s);
+int launch_scores(const float* X, int64_t n, int d, const float* C, const double* half_norm,
+                  int ncl, double* out, cudaStream_t s);
+int launch_pack(const double* t, int64_t n, int L, int m, int beta, int64_t row_offset,
+                int64_t key_stride_row, int64_t key_stride_arr, uint64_t* keys,
+                unsigned long long* n_boundary, unsigned long long* n_clamped, cudaStream_t s);
+
+}  // namespace lider

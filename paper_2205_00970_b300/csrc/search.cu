@@ -1,0 +1,612 @@
+// LIDER batched search (Sec. 3.3.2, Sec. 6.2) on one GPU.
+//
+// Steps and kernels, in order, for nq queries probing c clusters each:
+//   1. hash     dot2_tile_kernel<hash> + pack_kernel: packed query hashkeys
+//               for the L arrays (projections shared by all clusters)
+//   2. route    dot2_tile_kernel<score> + topc_kernel: the c best centroids,
+//               score x.mu - |mu|^2/2, ties -> lower cluster index
+//   3. group    group_*_kernel: (query, probe) pairs bucketed by cluster, cut
+//               into work items of up to kGroup pairs of one cluster
+//   4. locate   locate_kernel, one thread per (pair, array): re-scale the key
+//               (Sec. 5.1), two-stage RMI prediction (Sec. 5.2), clamp
+//               (Sec. 7.3), lower bound searched inside the leaf's recorded
+//               error window (with a counted fallback outside it), then the
+//               bi-directional expansion window of Sec. 4 by co-rank search
+//   5. score    score_kernel, persistent, one work item at a time: union of
+//               the L windows (deduplicated in a shared-memory hash set),
+//               exact FP32 inner products of the gathered rows, per-pair
+//               top-k by bitonic sort in shared memory
+//   6. merge    merge_kernel, one warp per query: k-way merge of its c lists
+//               (Sec. 6.2, heap of list heads)
+#include <algorithm>
+#include <mutex>
+
+#include "lider_internal.cuh"
+
+namespace lider {
+
+namespace {
+
+constexpr int kScoreThreads = 256;
+constexpr int kGroup = 8;            // pairs of one cluster per work item
+constexpr uint32_t kEmpty = 0xffffffffu;
+
+// counters[] slots
+enum {
+    CNT_QBOUNDARY = 0,
+    CNT_QCLAMPED,
+    CNT_FALLBACK,
+    CNT_CANDIDATES,
+    CNT_EMPTY,
+    CNT_ITEM,       // persistent-kernel work counter
+    CNT_SLOTS = 8
+};
+
+inline int next_pow2(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// ------------------------------------------------------------------ route --
+// Warp per query: the c best (score desc, index asc) of ncl FP64 scores.
+__global__ void topc_kernel(const double* __restrict__ S, int64_t nq, int ncl, int c,
+                            int32_t* __restrict__ route, int32_t* __restrict__ trace_route) {
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (q >= nq) return;
+    const double* s = S + q * ncl;
+    double ps = INFINITY;
+    int pj = -1;
+    for (int r = 0; r < c; ++r) {
+        double best = -INFINITY;
+        int bj = 0x7fffffff;
+        for (int j = lane; j < ncl; j += 32) {
+            double v = s[j];
+            if (v != v) v = -INFINITY;                            // NaN ranks last
+            const bool after = (v < ps) || (v == ps && j > pj);   // strictly after the last pick
+            if (after && (v > best || (v == best && j < bj))) { best = v; bj = j; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+            if (ov > best || (ov == best && oj < bj)) { best = ov; bj = oj; }
+        }
+        if (bj >= ncl) bj = 0;                                    // unreachable: c <= ncl
+        ps = best;
+        pj = bj;
+        if (lane == 0) {
+            route[q * c + r] = bj;
+            if (trace_route) trace_route[q * c + r] = bj;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ group --
+__global__ void group_count_kernel(const int32_t* __restrict__ route, int64_t npairs, int32_t* __restrict__ cnt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < npairs) atomicAdd(&cnt[route[i]], 1);
+}
+
+// Single block: off = exclusive scan of cnt, item_off = exclusive scan of
+// ceil(cnt / kGroup), cursor = off.
+__global__ void group_scan_kernel(const int32_t* __restrict__ cnt, int ncl, int32_t* __restrict__ off,
+                                  int32_t* __restrict__ cursor, int32_t* __restrict__ item_off) {
+    __shared__ int32_t s_a[1024], s_b[1024];
+    __shared__ int32_t carry_a, carry_b;
+    if (threadIdx.x == 0) { carry_a = 0; carry_b = 0; }
+    __syncthreads();
+    for (int base = 0; base < ncl; base += 1024) {
+        const int j = base + threadIdx.x;
+        const int32_t v = (j < ncl) ? cnt[j] : 0;
+        s_a[threadIdx.x] = v;
+        s_b[threadIdx.x] = (v + kGroup - 1) / kGroup;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {          // inclusive Hillis-Steele scan
+            const int32_t ta = threadIdx.x >= o ? s_a[threadIdx.x - o] : 0;
+            const int32_t tb = threadIdx.x >= o ? s_b[threadIdx.x - o] : 0;
+            __syncthreads();
+            s_a[threadIdx.x] += ta;
+            s_b[threadIdx.x] += tb;
+            __syncthreads();
+        }
+        if (j < ncl) {
+            const int32_t ea = carry_a + s_a[threadIdx.x] - v;
+            off[j] = ea;
+            cursor[j] = ea;
+            item_off[j] = carry_b + s_b[threadIdx.x] - (v + kGroup - 1) / kGroup;
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) { carry_a += s_a[1023]; carry_b += s_b[1023]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { off[ncl] = carry_a; item_off[ncl] = carry_b; }
+}
+
+__global__ void group_fill_kernel(const int32_t* __restrict__ route, int64_t npairs, int32_t* __restrict__ cursor,
+                                  int32_t* __restrict__ pairs) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < npairs) pairs[atomicAdd(&cursor[route[i]], 1)] = (int32_t)i;
+}
+
+// ----------------------------------------------------------------- locate --
+// One thread per (pair, array l).  pair = q * c + probe.
+__global__ void locate_kernel(Geometry g, int64_t npairs, int c, int R,
+                              const int32_t* __restrict__ route, const uint64_t* __restrict__ qkeys,
+                              int32_t* __restrict__ wstart, int32_t* __restrict__ wlen,
+                              int32_t* __restrict__ trace_pstar, int32_t* __restrict__ trace_wstart,
+                              int32_t* __restrict__ trace_wlen, unsigned long long* __restrict__ counters) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned fb = 0, empty = 0;
+    if (gid < npairs * g.L) {
+        const int64_t pair = gid / g.L;
+        const int l = (int)(gid % g.L);
+        const int64_t q = pair / c;
+        const int j = route[pair];
+        const int64_t base = g.cl_off[j];
+        const int64_t n_c = g.cl_off[j + 1] - base;
+        const uint64_t x = qkeys[q * g.L + l];
+        int64_t p = 0, s = 0, T = 0;
+        if (n_c == 0) {
+            empty = (l == 0);
+        } else {
+            const uint64_t* K = g.keys + (int64_t)l * g.n + base;
+            const RmiRoot rt = g.root[(int64_t)j * g.L + l];
+            const double r = rescale_key(x, rt.x_min, rt.x_max, n_c);
+            const int f = rmi_leaf(rt.a0, rt.b0, r, g.F, n_c);
+            const RmiLeaf lf = g.leaf[((int64_t)j * g.L + l) * g.F + f];
+            const int64_t ph = rmi_predict(lf.a, lf.b, r, n_c);
+            int64_t lo = max((int64_t)0, ph + lf.lo);
+            int64_t hi = min(n_c, ph + (int64_t)lf.hi + 1);
+            if (lo > hi) lo = hi = min(max(ph, (int64_t)0), n_c);
+            // the lower bound lies in [lo, hi] iff K[lo-1] < x and K[hi] >= x
+            if (lo > 0 && K[lo - 1] >= x) {
+                ++fb;
+                hi = lo - 1;
+                lo = 0;
+            } else if (hi < n_c && K[hi] < x) {
+                ++fb;
+                lo = hi + 1;
+                hi = n_c;
+            }
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (K[mid] < x) lo = mid + 1; else hi = mid;
+            }
+            p = lo;
+            // Bi-directional expansion: the first T = min(R, n_c) picks of the
+            // greedy merge of the left run (p-1, p-2, ...) and the right run
+            // (p, p+1, ...) by dist_e, ties to the left.  Both runs are
+            // non-decreasing in dist_e (Lemmas 2 and 3), so the picks form one
+            // window [p - t, p - t + T) with t found by co-rank search: t is
+            // the largest count such that left item t-1 precedes right item T-t.
+            T = min((int64_t)R, n_c);
+            const int64_t nr = n_c - p;
+            int64_t tlo = max((int64_t)0, T - nr), thi = min(T, p);
+            while (tlo < thi) {
+                const int64_t mid = (tlo + thi + 1) >> 1;
+                const uint64_t dl = dist_code(K[p - mid], x, g.m, g.beta, g.B);
+                const uint64_t dr = dist_code(K[p + (T - mid)], x, g.m, g.beta, g.B);
+                if (dl <= dr) tlo = mid; else thi = mid - 1;
+            }
+            s = p - tlo;
+        }
+        wstart[gid] = (int32_t)s;
+        wlen[gid] = (int32_t)T;
+        if (trace_pstar) trace_pstar[gid] = (int32_t)p;
+        if (trace_wstart) trace_wstart[gid] = (int32_t)s;
+        if (trace_wlen) trace_wlen[gid] = (int32_t)T;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        fb += __shfl_xor_sync(0xffffffffu, fb, o);
+        empty += __shfl_xor_sync(0xffffffffu, empty, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (fb) atomicAdd(&counters[CNT_FALLBACK], (unsigned long long)fb);
+        if (empty) atomicAdd(&counters[CNT_EMPTY], (unsigned long long)empty);
+    }
+}
+
+// ------------------------------------------------------------------ score --
+struct ScoreArgs {
+    Geometry g;
+    const float* Q;
+    int c, k, max_lr, ht_size, sort_cap;
+    const int32_t* off;
+    const int32_t* cnt;
+    const int32_t* item_off;
+    const int32_t* pairs;
+    const int32_t* wstart;
+    const int32_t* wlen;
+    float* pscore;          // npairs x k
+    int64_t* pid;           // npairs x k (corpus ids)
+    int32_t* trace_ucount;
+    unsigned long long* counters;
+};
+
+__device__ __forceinline__ float warp_sum(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Dynamic shared memory: q (d floats) | hash set (ht_size u32) |
+// candidate list (max_lr u32) | sort keys (sort_cap u64).
+__global__ void __launch_bounds__(kScoreThreads) score_kernel(ScoreArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Geometry& g = a.g;
+    float* qv = reinterpret_cast<float*>(smem);
+    uint32_t* htab = reinterpret_cast<uint32_t*>(smem + (size_t)g.d * 4);
+    uint32_t* cand = htab + a.ht_size;
+    uint64_t* skey = reinterpret_cast<uint64_t*>(
+        smem + align_up_dev((size_t)g.d * 4 + (size_t)(a.ht_size + a.max_lr) * 4, 16));
+    __shared__ int s_item, s_U;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarps = kScoreThreads / 32;
+    const int total_items = a.item_off[g.ncl];
+    const uint32_t hmask = (uint32_t)a.ht_size - 1;
+
+    for (;;) {
+        if (tid == 0) s_item = (int)atomicAdd(&a.counters[CNT_ITEM], 1ull);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total_items) break;
+        // cluster of this item: last j with item_off[j] <= item
+        int lo = 0, hi = g.ncl - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.item_off[mid] <= item) lo = mid; else hi = mid - 1;
+        }
+        const int j = lo;
+        const int first = a.off[j] + (item - a.item_off[j]) * kGroup;
+        const int count = min(kGroup, a.off[j] + a.cnt[j] - first);
+        const int64_t base = g.cl_off[j];
+
+        for (int gi = 0; gi < count; ++gi) {
+            const int64_t pair = a.pairs[first + gi];
+            const int64_t q = pair / a.c;
+            for (int i = tid; i < a.ht_size; i += kScoreThreads) htab[i] = kEmpty;
+            const float4* q4 = reinterpret_cast<const float4*>(a.Q + q * g.d);
+            for (int i = tid; i < g.d / 4; i += kScoreThreads) reinterpret_cast<float4*>(qv)[i] = q4[i];
+            if (tid == 0) s_U = 0;
+            __syncthreads();
+
+            // union of the L windows (Sec. 3.3.1: merge the arrays' results)
+            for (int l = 0; l < g.L; ++l) {
+                const int32_t ws = a.wstart[pair * g.L + l];
+                const int32_t wl = a.wlen[pair * g.L + l];
+                const int32_t* P = g.pos + (int64_t)l * g.n + base + ws;
+                for (int t = tid; t < wl; t += kScoreThreads) {
+                    const uint32_t p = (uint32_t)P[t];
+                    uint32_t h = (p * 2654435761u) & hmask;
+                    for (;;) {
+                        const uint32_t old = atomicCAS(&htab[h], kEmpty, p);
+                        if (old == kEmpty) {
+                            cand[atomicAdd(&s_U, 1)] = p;
+                            break;
+                        }
+                        if (old == p) break;
+                        h = (h + 1) & hmask;
+                    }
+                }
+            }
+            __syncthreads();
+            const int U = s_U;
+
+            // exact inner products: one warp per candidate row
+            const float4* qv4 = reinterpret_cast<const float4*>(qv);
+            const int d4 = g.d / 4;
+            for (int u = warp; u < U; u += nwarps) {
+                const uint32_t p = cand[u];
+                const float4* row = reinterpret_cast<const float4*>(g.X + (base + p) * (int64_t)g.d);
+                float acc = 0.f;
+                for (int i = lane; i < d4; i += 32) {
+                    const float4 x = __ldg(row + i);
+                    const float4 y = qv4[i];
+                    acc = fmaf(x.x, y.x, acc);
+                    acc = fmaf(x.y, y.y, acc);
+                    acc = fmaf(x.z, y.z, acc);
+                    acc = fmaf(x.w, y.w, acc);
+                }
+                acc = warp_sum(acc);
+                if (lane == 0)
+                    skey[u] = ((uint64_t)(~float_order(acc)) << 32) | (uint64_t)p;
+            }
+            const int SP = U > 1 ? next_pow2_dev(U) : 1;
+            for (int u = U + tid; u < SP; u += kScoreThreads) skey[u] = ~0ull;
+            __syncthreads();
+
+            // ascending sort of (~score order, position): best first, ties by
+            // position, which follows corpus id inside a cluster
+            for (int size = 2; size <= SP; size <<= 1) {
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    for (int i = tid; i < SP / 2; i += kScoreThreads) {
+                        const int lo_i = 2 * stride * (i / stride) + (i % stride);
+                        const int hi_i = lo_i + stride;
+                        const bool up = (lo_i & size) == 0;
+                        const uint64_t x0 = skey[lo_i], x1 = skey[hi_i];
+                        if ((x0 > x1) == up) { skey[lo_i] = x1; skey[hi_i] = x0; }
+                    }
+                    __syncthreads();
+                }
+            }
+
+            float* ps = a.pscore + pair * a.k;
+            int64_t* pi = a.pid + pair * a.k;
+            for (int r = tid; r < a.k; r += kScoreThreads) {
+                if (r < U) {
+                    const uint64_t kv = skey[r];
+                    ps[r] = float_from_order(~(uint32_t)(kv >> 32));
+                    pi[r] = g.orig_id[base + (int64_t)(uint32_t)kv];
+                } else {
+                    ps[r] = -INFINITY;
+                    pi[r] = -1;
+                }
+            }
+            if (tid == 0) {
+                atomicAdd(&a.counters[CNT_CANDIDATES], (unsigned long long)U);
+                if (a.trace_ucount) a.trace_ucount[pair] = U;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ------------------------------------------------------------------ merge --
+// Warp per query; lane p < c walks list p (sorted best first).
+__global__ void merge_kernel(const float* __restrict__ pscore, const int64_t* __restrict__ pid, int64_t nq,
+                             int c, int k, int64_t* __restrict__ out_ids, float* __restrict__ out_scores) {
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (q >= nq) return;
+    const int64_t lbase = (q * c + lane) * (int64_t)k;
+    int head = 0;
+    float hs = -INFINITY;
+    int64_t hid = -1;
+    if (lane < c) { hs = pscore[lbase]; hid = pid[lbase]; }
+    for (int r = 0; r < k; ++r) {
+        // best head: score desc, id asc; exhausted lists (id -1) lose
+        float bs = hs;
+        int64_t bid = hid;
+        int bl = lane;
+        for (int o = 16; o > 0; o >>= 1) {
+            const float os = __shfl_xor_sync(0xffffffffu, bs, o);
+            const int64_t oid = __shfl_xor_sync(0xffffffffu, bid, o);
+            const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+            bool take;
+            if (oid < 0) take = false;
+            else if (bid < 0) take = true;
+            else take = (os > bs) || (os == bs && oid < bid);
+            if (take) { bs = os; bid = oid; bl = ol; }
+        }
+        if (lane == 0) {
+            out_ids[q * k + r] = bid;
+            out_scores[q * k + r] = bid < 0 ? -INFINITY : bs;
+        }
+        if (bid < 0) continue;
+        if (lane == bl) {
+            ++head;
+            if (head < k) { hs = pscore[lbase + head]; hid = pid[lbase + head]; }
+            else { hs = -INFINITY; hid = -1; }
+        }
+    }
+}
+
+}  // namespace
+}  // namespace lider
+
+namespace lider {
+
+namespace {
+
+struct Workspace {
+    unsigned long long* counters;
+    int32_t* cnt;
+    int32_t* off;
+    int32_t* cursor;
+    int32_t* item_off;
+    double* tq;
+    uint64_t* qkeys;
+    double* rscore;
+    int32_t* route;
+    int32_t* pairs;
+    int32_t* wstart;
+    int32_t* wlen;
+    float* pscore;
+    int64_t* pid;
+    size_t zero_bytes;   // counters + cnt, cleared at the start of a search
+    size_t total;
+};
+
+// Carve one allocation into the search buffers (base == nullptr: sizes only).
+Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, int k) {
+    Workspace w{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        unsigned char* p = base ? base + o : nullptr;
+        o = align_up(o + bytes, 256);
+        return p;
+    };
+    const int64_t np = nq * c;
+    w.counters = (unsigned long long*)take(CNT_SLOTS * sizeof(unsigned long long));
+    w.cnt = (int32_t*)take((size_t)g.ncl * 4);
+    w.zero_bytes = o;
+    w.off = (int32_t*)take((size_t)(g.ncl + 1) * 4);
+    w.cursor = (int32_t*)take((size_t)g.ncl * 4);
+    w.item_off = (int32_t*)take((size_t)(g.ncl + 1) * 4);
+    w.tq = (double*)take((size_t)nq * g.H * 8);
+    w.qkeys = (uint64_t*)take((size_t)nq * g.L * 8);
+    w.rscore = (double*)take((size_t)nq * g.ncl * 8);
+    w.route = (int32_t*)take((size_t)np * 4);
+    w.pairs = (int32_t*)take((size_t)np * 4);
+    w.wstart = (int32_t*)take((size_t)np * g.L * 4);
+    w.wlen = (int32_t*)take((size_t)np * g.L * 4);
+    w.pscore = (float*)take((size_t)np * k * 4);
+    w.pid = (int64_t*)take((size_t)np * k * 8);
+    w.total = o;
+    return w;
+}
+
+int check_search_args(const lider_index* ix, const float* Q, int64_t nq, int k, int c, const void* ids,
+                      const void* scores) {
+    if (!ix) return fail(LIDER_EINVAL, "lider_search: index is NULL");
+    if (nq < 0) return fail(LIDER_EINVAL, "lider_search: nq < 0");
+    if (k < 1) return fail(LIDER_EINVAL, "lider_search: k must be >= 1");
+    if (c < 1 || c > ix->g.ncl) return fail(LIDER_EINVAL, "lider_search: c must be in [1, n_clusters]");
+    if (k > LIDER_MAX_K) return fail(LIDER_ELIMIT, "lider_search: k exceeds LIDER_MAX_K");
+    if (c > LIDER_MAX_C) return fail(LIDER_ELIMIT, "lider_search: c exceeds LIDER_MAX_C");
+    const int64_t R = (int64_t)ix->params.r0 * k;
+    if (R * ix->g.L > LIDER_MAX_LR) return fail(LIDER_ELIMIT, "lider_search: L * r0 * k exceeds LIDER_MAX_LR");
+    if (nq * c > (int64_t)INT32_MAX) return fail(LIDER_ELIMIT, "lider_search: nq * c exceeds 2^31-1");
+    if (nq > 0 && (!Q || !ids || !scores)) return fail(LIDER_EINVAL, "lider_search: NULL buffer");
+    int dev = -1;
+    LIDER_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != ix->device) return fail(LIDER_EINVAL, "lider_search: index lives on another device");
+    return LIDER_OK;
+}
+
+// Enqueue steps 1-6 on `st` using workspace `w`.
+int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int c, int64_t* out_ids,
+                   float* out_scores, const lider_trace* tr, const Workspace& w, cudaStream_t st) {
+    const Geometry& g = ix->g;
+    const int R = ix->params.r0 * k;
+    const int64_t np = nq * c;
+    int rc;
+    LIDER_CUDA_TRY(cudaMemsetAsync(w.counters, 0, w.zero_bytes, st));
+
+    // 1. hash
+    if ((rc = launch_hash_t(Q, nq, g.d, g.A, g.bproj, g.H, g.W, w.tq, st))) return rc;
+    if ((rc = launch_pack(w.tq, nq, g.L, g.m, g.beta, 0, g.L, 1, w.qkeys, &w.counters[CNT_QBOUNDARY],
+                          &w.counters[CNT_QCLAMPED], st)))
+        return rc;
+    if (tr && tr->qkeys)
+        LIDER_CUDA_TRY(cudaMemcpyAsync(tr->qkeys, w.qkeys, (size_t)nq * g.L * 8, cudaMemcpyDeviceToDevice, st));
+    // 2. route
+    if ((rc = launch_scores(Q, nq, g.d, g.C, g.half_norm, g.ncl, w.rscore, st))) return rc;
+    topc_kernel<<<(unsigned)cdiv(nq * 32, 256), 256, 0, st>>>(w.rscore, nq, g.ncl, c, w.route,
+                                                              tr ? tr->route : nullptr);
+    LIDER_LAUNCH_CHECK("topc_kernel");
+    // 3. group
+    group_count_kernel<<<(unsigned)cdiv(np, 256), 256, 0, st>>>(w.route, np, w.cnt);
+    LIDER_LAUNCH_CHECK("group_count_kernel");
+    group_scan_kernel<<<1, 1024, 0, st>>>(w.cnt, g.ncl, w.off, w.cursor, w.item_off);
+    LIDER_LAUNCH_CHECK("group_scan_kernel");
+    group_fill_kernel<<<(unsigned)cdiv(np, 256), 256, 0, st>>>(w.route, np, w.cursor, w.pairs);
+    LIDER_LAUNCH_CHECK("group_fill_kernel");
+    // 4. locate + expand
+    locate_kernel<<<(unsigned)cdiv(np * g.L, 256), 256, 0, st>>>(
+        g, np, c, R, w.route, w.qkeys, w.wstart, w.wlen, tr ? tr->pstar : nullptr, tr ? tr->wstart : nullptr,
+        tr ? tr->wlen : nullptr, w.counters);
+    LIDER_LAUNCH_CHECK("locate_kernel");
+    // 5. gather + score + per-pair top-k
+    ScoreArgs sa;
+    sa.g = g;
+    sa.Q = Q;
+    sa.c = c;
+    sa.k = k;
+    sa.max_lr = g.L * R;
+    sa.sort_cap = next_pow2(sa.max_lr);
+    sa.ht_size = 2 * sa.sort_cap;
+    sa.off = w.off;
+    sa.cnt = w.cnt;
+    sa.item_off = w.item_off;
+    sa.pairs = w.pairs;
+    sa.wstart = w.wstart;
+    sa.wlen = w.wlen;
+    sa.pscore = w.pscore;
+    sa.pid = w.pid;
+    sa.trace_ucount = tr ? tr->ucount : nullptr;
+    sa.counters = w.counters;
+    const size_t smem = align_up((size_t)g.d * 4 + (size_t)(sa.ht_size + sa.max_lr) * 4, 16) +
+                        (size_t)sa.sort_cap * 8;
+    LIDER_CUDA_TRY(cudaFuncSetAttribute(score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    LIDER_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, score_kernel, kScoreThreads, smem));
+    if (per_sm < 1) return fail(LIDER_ELIMIT, "lider_search: score kernel does not fit on an SM");
+    const int64_t max_items = cdiv(np, kGroup) + g.ncl;
+    const int grid = (int)std::min<int64_t>(max_items, (int64_t)per_sm * ix->num_sms);
+    score_kernel<<<grid, kScoreThreads, smem, st>>>(sa);
+    LIDER_LAUNCH_CHECK("score_kernel");
+    // 6. merge
+    merge_kernel<<<(unsigned)cdiv(nq * 32, 256), 256, 0, st>>>(w.pscore, w.pid, nq, c, k, out_ids, out_scores);
+    LIDER_LAUNCH_CHECK("merge_kernel");
+    return LIDER_OK;
+}
+
+int read_stats(const Workspace& w, int64_t nq, int c, lider_search_stats* stats, cudaStream_t st) {
+    unsigned long long h[CNT_SLOTS] = {};
+    LIDER_CUDA_TRY(cudaMemcpyAsync(h, w.counters, sizeof(h), cudaMemcpyDeviceToHost, st));
+    LIDER_CUDA_TRY(cudaStreamSynchronize(st));
+    stats->n_queries = nq;
+    stats->pairs = nq * c;
+    stats->candidates = (int64_t)h[CNT_CANDIDATES];
+    stats->qkey_boundary = (int64_t)h[CNT_QBOUNDARY];
+    stats->qkey_clamped = (int64_t)h[CNT_QCLAMPED];
+    stats->locate_fallback = (int64_t)h[CNT_FALLBACK];
+    stats->empty_pairs = (int64_t)h[CNT_EMPTY];
+    stats->reserved = 0;
+    return LIDER_OK;
+}
+
+int pool_alloc(const lider_index* ix, void** p, size_t bytes, cudaStream_t st) {
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes ? bytes : 256, ix->pool, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LIDER_ENOMEM, std::string("lider_search: scratch allocation of ") + std::to_string(bytes) +
+                                      " bytes failed: " + cudaGetErrorString(e));
+    }
+    return LIDER_OK;
+}
+
+}  // namespace
+
+int search_entry(const lider_index* ix, const float* Q, int64_t nq, int k, int c, int64_t* out_ids,
+                 float* out_scores, const lider_trace* tr, lider_search_stats* stats, void* stream) {
+    int rc = check_search_args(ix, Q, nq, k, c, out_ids, out_scores);
+    if (rc) return rc;
+    if (stats) *stats = lider_search_stats{};
+    if (nq == 0) return LIDER_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace sz = carve(nullptr, ix->g, nq, c, k);
+    void* mem = nullptr;
+    if ((rc = pool_alloc(ix, &mem, sz.total, st))) return rc;
+    Workspace w = carve((unsigned char*)mem, ix->g, nq, c, k);
+    rc = enqueue_search(ix, Q, nq, k, c, out_ids, out_scores, tr, w, st);
+    if (rc == LIDER_OK && stats) rc = read_stats(w, nq, c, stats, st);
+    cudaError_t e = cudaFreeAsync(mem, st);
+    if (rc == LIDER_OK && e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync");
+    return rc;
+}
+
+int search_host_entry(const lider_index* ix, const float* Qh, int64_t nq, int k, int c, int64_t* ids_h,
+                      float* scores_h, lider_search_stats* stats, void* stream) {
+    int rc = check_search_args(ix, Qh, nq, k, c, ids_h, scores_h);
+    if (rc) return rc;
+    if (stats) *stats = lider_search_stats{};
+    if (nq == 0) return LIDER_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t qb = (size_t)nq * ix->g.d * 4, ib = (size_t)nq * k * 8, sb = (size_t)nq * k * 4;
+    const size_t o_ids = align_up(qb, 256), o_sc = align_up(o_ids + ib, 256);
+    Workspace sz = carve(nullptr, ix->g, nq, c, k);
+    const size_t o_ws = align_up(o_sc + sb, 256);
+    void* mem = nullptr;
+    if ((rc = pool_alloc(ix, &mem, o_ws + sz.total, st))) return rc;
+    unsigned char* m = (unsigned char*)mem;
+    float* Qd = (float*)m;
+    int64_t* idd = (int64_t*)(m + o_ids);
+    float* scd = (float*)(m + o_sc);
+    Workspace w = carve(m + o_ws, ix->g, nq, c, k);
+    cudaError_t e = cudaMemcpyAsync(Qd, Qh, qb, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync(queries)");
+    if (!rc) rc = enqueue_search(ix, Qd, nq, k, c, idd, scd, nullptr, w, st);
+    if (!rc && (e = cudaMemcpyAsync(ids_h, idd, ib, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        rc = cuda_fail(e, "cudaMemcpyAsync(ids)");
+    if (!rc && (e = cudaMemcpyAsync(scores_h, scd, sb, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        rc = cuda_fail(e, "cudaMemcpyAsync(scores)");
+    if (!rc && stats) rc = read_stats(w, nq, c, stats, st);
+    e = cudaFreeAsync(mem, st);
+    if (!rc && e != cudaSuccess) rc = cuda_fail(e, "cudaFreeAsync");
+    if (!rc && (e = cudaStreamSynchronize(st)) != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
+    return rc;
+}
+
+}  // namespace lider

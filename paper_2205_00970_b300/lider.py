@@ -1,0 +1,221 @@
+"""Python binding of liblider.so (the C ABI in include/lider.h).
+
+Argument marshalling only: every step of build and search runs in the CUDA
+library.  Device buffers are torch CUDA tensors; the stream is torch's current
+stream unless one is given.  There is no CPU fallback: if the library cannot
+be loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblider.so")
+
+LIDER_OK = 0
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ELIMIT"}
+MAX_L, MAX_C, MAX_K, MAX_LR, MAX_D = 32, 32, 1024, 4096, 4096
+
+
+class LiderError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("m", ctypes.c_int32), ("rmi_leaves", ctypes.c_int32),
+                ("r0", ctypes.c_int32), ("B", ctypes.c_int32), ("hash_kind", ctypes.c_int32),
+                ("W", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in
+                ("n_queries", "pairs", "candidates", "qkey_boundary", "qkey_clamped",
+                 "locate_fallback", "empty_pairs", "reserved")]
+
+    def as_dict(self) -> dict:
+        return {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "reserved"}
+
+
+class Trace(ctypes.Structure):
+    _fields_ = [("route", ctypes.c_void_p), ("qkeys", ctypes.c_void_p), ("pstar", ctypes.c_void_p),
+                ("wstart", ctypes.c_void_p), ("wlen", ctypes.c_void_p), ("ucount", ctypes.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -m paper_2205_00970_b300.build_lib`")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    sig = {
+        "lider_build": ([P, I64, I32, P, I32, P, P, ctypes.POINTER(Params), P, ctypes.POINTER(P)], ctypes.c_int),
+        "lider_search": ([P, P, I64, I32, I32, P, P, ctypes.POINTER(Stats), P], ctypes.c_int),
+        "lider_search_trace": ([P, P, I64, I32, I32, P, P, ctypes.POINTER(Trace), ctypes.POINTER(Stats), P],
+                               ctypes.c_int),
+        "lider_search_host": ([P, P, I64, I32, I32, P, P, ctypes.POINTER(Stats), P], ctypes.c_int),
+        "lider_index_info": ([P, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I32),
+                              ctypes.POINTER(Params)], ctypes.c_int),
+        "lider_cluster_offsets": ([P, P], ctypes.c_int),
+        "lider_export_array": ([P, I32, I32, P, P], ctypes.c_int),
+        "lider_export_rmi": ([P, I32, I32, P, P, P, P], ctypes.c_int),
+        "lider_free": ([P], None),
+        "lider_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def exported_symbols() -> list[str]:
+    return [n for n in ("lider_build", "lider_search", "lider_search_trace", "lider_search_host",
+                        "lider_index_info", "lider_cluster_offsets", "lider_export_array",
+                        "lider_export_rmi", "lider_free", "lider_last_error") if hasattr(_lib, n)]
+
+
+def _check(rc: int):
+    if rc != LIDER_OK:
+        raise LiderError(rc, (_lib.lider_last_error() or b"").decode())
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dev(t: torch.Tensor, dtype, name: str) -> torch.Tensor:
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    return t.contiguous()
+
+
+class Index:
+    """A LIDER index resident on the current CUDA device (owns its memory)."""
+
+    def __init__(self, corpus: torch.Tensor, centroids: torch.Tensor, A: torch.Tensor, b: torch.Tensor,
+                 L: int, m: int, W: float, rmi_leaves: int, r0: int = 2, B: int = 1, stream=None):
+        corpus = _dev(corpus, torch.float32, "corpus")
+        centroids = _dev(centroids, torch.float32, "centroids")
+        A = _dev(A, torch.float32, "A")
+        b = _dev(b, torch.float32, "b")
+        n, d = corpus.shape
+        p = Params(L, m, rmi_leaves, r0, B, 0, float(W))
+        h = ctypes.c_void_p()
+        _check(_lib.lider_build(corpus.data_ptr(), n, d, centroids.data_ptr(), centroids.shape[0],
+                                A.data_ptr(), b.data_ptr(), ctypes.byref(p), _stream_ptr(stream),
+                                ctypes.byref(h)))
+        self._h = h
+        self.n, self.d, self.n_clusters = int(n), int(d), int(centroids.shape[0])
+        self.L, self.m, self.W, self.rmi_leaves, self.r0, self.B = L, m, W, rmi_leaves, r0, B
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def free(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.lider_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def search(self, Q: torch.Tensor, k: int, c: int, stats: bool = False, trace: bool = False,
+               stream=None, out: tuple | None = None):
+        """ids (nq, k) int64 and scores (nq, k) float32 on the device.
+
+        With stats=True also returns the counters (the call synchronises);
+        with trace=True also returns the per-step outputs as tensors."""
+        Q = _dev(Q, torch.float32, "queries")
+        nq = Q.shape[0]
+        if out is None:
+            ids = torch.empty((nq, k), dtype=torch.int64, device=Q.device)
+            sc = torch.empty((nq, k), dtype=torch.float32, device=Q.device)
+        else:
+            ids, sc = out
+        st = Stats()
+        sp = ctypes.byref(st) if stats else None
+        if trace:
+            tr_t = {
+                "route": torch.empty((nq, c), dtype=torch.int32, device=Q.device),
+                "qkeys": torch.empty((nq, self.L), dtype=torch.int64, device=Q.device),
+                "pstar": torch.empty((nq, c, self.L), dtype=torch.int32, device=Q.device),
+                "wstart": torch.empty((nq, c, self.L), dtype=torch.int32, device=Q.device),
+                "wlen": torch.empty((nq, c, self.L), dtype=torch.int32, device=Q.device),
+                "ucount": torch.empty((nq, c), dtype=torch.int32, device=Q.device),
+            }
+            tr = Trace(*(tr_t[n].data_ptr() for n in ("route", "qkeys", "pstar", "wstart", "wlen", "ucount")))
+            _check(_lib.lider_search_trace(self._h, Q.data_ptr(), nq, k, c, ids.data_ptr(), sc.data_ptr(),
+                                           ctypes.byref(tr), sp, _stream_ptr(stream)))
+        else:
+            _check(_lib.lider_search(self._h, Q.data_ptr(), nq, k, c, ids.data_ptr(), sc.data_ptr(), sp,
+                                     _stream_ptr(stream)))
+        res = [ids, sc]
+        if stats:
+            res.append(st.as_dict())
+        if trace:
+            res.append(tr_t)
+        return tuple(res)
+
+    def search_host(self, Q: torch.Tensor, k: int, c: int, ids: torch.Tensor | None = None,
+                    scores: torch.Tensor | None = None, stats: bool = False, stream=None):
+        """End-to-end search on host tensors (pinned for asynchronous copies)."""
+        if Q.is_cuda or Q.dtype != torch.float32 or not Q.is_contiguous():
+            raise TypeError("queries must be a contiguous float32 CPU tensor")
+        nq = Q.shape[0]
+        ids = torch.empty((nq, k), dtype=torch.int64) if ids is None else ids
+        scores = torch.empty((nq, k), dtype=torch.float32) if scores is None else scores
+        st = Stats()
+        _check(_lib.lider_search_host(self._h, Q.data_ptr(), nq, k, c, ids.data_ptr(), scores.data_ptr(),
+                                      ctypes.byref(st) if stats else None, _stream_ptr(stream)))
+        return (ids, scores, st.as_dict()) if stats else (ids, scores)
+
+    def cluster_offsets(self) -> np.ndarray:
+        off = np.zeros(self.n_clusters + 1, dtype=np.int64)
+        _check(_lib.lider_cluster_offsets(self._h, off.ctypes.data))
+        return off
+
+    def export_array(self, cluster: int, array: int):
+        off = self.cluster_offsets()
+        n_c = int(off[cluster + 1] - off[cluster])
+        keys = np.zeros(n_c, dtype=np.uint64)
+        ids = np.zeros(n_c, dtype=np.int64)
+        _check(_lib.lider_export_array(self._h, cluster, array, keys.ctypes.data, ids.ctypes.data))
+        return keys, ids
+
+    def export_rmi(self, cluster: int, array: int) -> dict:
+        mm = np.zeros(2, dtype=np.uint64)
+        root = np.zeros(2, dtype=np.float64)
+        leaf = np.zeros(2 * self.rmi_leaves, dtype=np.float64)
+        err = np.zeros(2 * self.rmi_leaves, dtype=np.int32)
+        _check(_lib.lider_export_rmi(self._h, cluster, array, mm.ctypes.data, root.ctypes.data,
+                                     leaf.ctypes.data, err.ctypes.data))
+        return {"x_min": int(mm[0]), "x_max": int(mm[1]), "a0": float(root[0]), "b0": float(root[1]),
+                "a": leaf[0::2].copy(), "b": leaf[1::2].copy(), "e_lo": err[0::2].astype(np.int64),
+                "e_hi": err[1::2].astype(np.int64)}
+
+
+def raw_call(name: str, *args):
+    """Call a C ABI function by name and return its code (tests of argument
+    validation use this to pass deliberately invalid arguments)."""
+    return getattr(_lib, name)(*args)
+
+
+def last_error() -> str:
+    return (_lib.lider_last_error() or b"").decode()

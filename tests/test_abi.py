@@ -1,0 +1,61 @@
+"""The C-ABI library loads and exports every declared entry point; argument
+validation answers without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lider.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lider_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_core_abi():
+    syms = declared_symbols()
+    for s in ("lider_build", "lider_search", "lider_free", "lider_last_error"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2205_00970_b300 import build_lib
+    lib = ctypes.CDLL(build_lib.build())
+    for s in declared_symbols():
+        assert hasattr(lib, s), s
+
+
+def test_binding_loads_and_validates_without_gpu():
+    from paper_2205_00970_b300 import lider
+    assert set(declared_symbols()) <= set(lider.exported_symbols())
+    # NULL out pointer / NULL index are rejected before any CUDA call
+    rc = lider.raw_call("lider_build", None, 10, 8, None, 2, None, None, None, None, None)
+    assert rc == -1 and "out is NULL" in lider.last_error()
+    rc = lider.raw_call("lider_search", None, None, 0, 10, 1, None, None, None, None)
+    assert rc == -1 and "index is NULL" in lider.last_error()
+    rc = lider.raw_call("lider_index_info", None, None, None, None, None)
+    assert rc == -1
+    lider.raw_call("lider_free", None)   # NULL is accepted
+    # invalid build arguments are rejected before the device is touched
+    out = ctypes.c_void_p()
+    p = lider.Params(4, 8, 16, 2, 1, 0, 1.0)
+    dummy = ctypes.c_void_p(16)
+    for n, d, ncl, pp, msg in [
+        (0, 8, 2, p, "n must be"),
+        (10, 6, 2, p, "multiple of 4"),
+        (10, 8, 0, p, "n_clusters"),
+        (10, 8, 2, lider.Params(4, 8, 16, 2, 1, 0, -1.0), "W must be"),
+        (10, 8, 2, lider.Params(4, 8, 16, 2, 8, 0, 1.0), "<= 56"),
+        (10, 8, 2, lider.Params(4, 8, 16, 2, 1, 7, 1.0), "hash_kind"),
+        (10, 8, 2, lider.Params(0, 8, 16, 2, 1, 0, 1.0), ">= 1"),
+    ]:
+        rc = lider.raw_call("lider_build", dummy, n, d, dummy, ncl, dummy, dummy, ctypes.byref(pp), None,
+                            ctypes.byref(out))
+        assert rc == -1 and msg in lider.last_error(), (msg, lider.last_error())
+    rc = lider.raw_call("lider_build", dummy, 10, 8, dummy, 2, dummy, dummy,
+                        ctypes.byref(lider.Params(33, 8, 16, 2, 1, 0, 1.0)), None, ctypes.byref(out))
+    assert rc == -4

@@ -1,0 +1,172 @@
+"""GPU search vs the FP64 oracle on the tiny workload (10k x 128, 16 clusters,
+c=4, L=4, m=8, RMI 16 leaves, k=10): every query, every step."""
+import numpy as np
+import pytest
+
+from oracle import lider_oracle as O
+from tests import lider_fixtures as F
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    import torch
+    cfg, X, Q, C, A, b = F.workload("tiny")
+    ref_idx = F.oracle_index(cfg, X, C, A, b)
+    gidx = F.gpu_index(cfg, X, C, A, b)
+    ref = O.search(ref_idx, Q, cfg["k"], cfg["c"], cfg["R"])
+    Qd = torch.from_numpy(Q).cuda()
+    return dict(cfg=cfg, X=X, Q=Q, C=C, A=A, b=b, ref_idx=ref_idx, gidx=gidx, ref=ref, Qd=Qd)
+
+
+def test_partition_matches_oracle(tiny):
+    off = tiny["gidx"].cluster_offsets()
+    sizes = np.bincount(tiny["ref_idx"].asg, minlength=tiny["cfg"]["n_clusters"])
+    assert tiny["ref_idx"].asg_near_ties == 0
+    np.testing.assert_array_equal(np.diff(off), sizes)
+
+
+def test_sorted_arrays_bit_exact(tiny):
+    cfg, ref_idx, gidx = tiny["cfg"], tiny["ref_idx"], tiny["gidx"]
+    for j in range(cfg["n_clusters"]):
+        cm = ref_idx.core(j)
+        for l in range(cfg["L"]):
+            keys, ids = gidx.export_array(j, l)
+            diff = (keys != cm.keys[l]) | (ids != cm.sorted_ids[l])
+            assert not np.any(diff & ~cm.flags[l]), (j, l)
+
+
+def test_rmi_window_invariant_and_root(tiny):
+    """Every corpus key's first position lies in its leaf's window, evaluated
+    with the GPU-built RMI parameters; the root model matches the oracle's."""
+    cfg, ref_idx, gidx = tiny["cfg"], tiny["ref_idx"], tiny["gidx"]
+    for j in range(cfg["n_clusters"]):
+        cm = ref_idx.core(j)
+        for l in range(cfg["L"]):
+            g = gidx.export_rmi(j, l)
+            ks = cm.keys[l]
+            n_c = len(ks)
+            assert g["x_min"] == int(ks[0]) and g["x_max"] == int(ks[-1])
+            rmi = O.RMI(n_c, cfg["leaves"], g["a0"], g["b0"], g["a"], g["b"], g["e_lo"], g["e_hi"])
+            o = cm.rmi[l]
+            assert abs(g["b0"] - o.b0) <= 1e-9 * abs(o.b0) + 1e-12
+            assert abs(g["a0"] - o.a0) <= 1e-9 * max(abs(o.a0), n_c) + 1e-12
+            lb = np.searchsorted(ks, ks, side="left")
+            for i in range(n_c):
+                r = O.rescale(int(ks[i]), g["x_min"], g["x_max"], n_c)
+                lf, p = rmi.predict(r)
+                assert p + g["e_lo"][lf] <= lb[i] <= p + g["e_hi"][lf], (j, l, i)
+
+
+def test_search_steps_match_oracle(tiny):
+    cfg = tiny["cfg"]
+    ids, sc, stats, tr = tiny["gidx"].search(tiny["Qd"], cfg["k"], cfg["c"], stats=True, trace=True)
+    bad, exempt = F.check_trace(tr, tiny["ref"])
+    assert not bad, bad[:10]
+    assert len(exempt) <= 2
+    assert stats["candidates"] == int(tr["ucount"].sum())
+    assert stats["pairs"] == cfg["nq"] * cfg["c"]
+    assert stats["empty_pairs"] == 0
+
+
+def test_topk_matches_oracle(tiny):
+    cfg, ref = tiny["cfg"], tiny["ref"]
+    ids, sc = tiny["gidx"].search(tiny["Qd"], cfg["k"], cfg["c"])
+    ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+    bad = F.check_topk(ids, sc, ref.ids, ref.scores, tiny["X"], tiny["Q"])
+    assert not bad, bad[:10]
+
+
+def test_host_path_equals_device_path(tiny):
+    import torch
+    cfg = tiny["cfg"]
+    ids, sc = tiny["gidx"].search(tiny["Qd"], cfg["k"], cfg["c"])
+    Qh = torch.from_numpy(tiny["Q"]).pin_memory()
+    hid, hsc = tiny["gidx"].search_host(Qh, cfg["k"], cfg["c"])
+    assert torch.equal(hid, ids.cpu()) and torch.equal(hsc, sc.cpu())
+
+
+@pytest.mark.parametrize("nq", [0, 1, 7, 33, 257])
+def test_ragged_batches_are_batch_invariant(tiny, nq):
+    """A query's result does not depend on its batch-mates or batch size."""
+    import torch
+    cfg = tiny["cfg"]
+    full_ids, full_sc = tiny["gidx"].search(tiny["Qd"], cfg["k"], cfg["c"])
+    sub = tiny["Qd"][100:100 + nq].contiguous()
+    ids, sc = tiny["gidx"].search(sub, cfg["k"], cfg["c"])
+    assert ids.shape == (nq, cfg["k"])
+    assert torch.equal(ids, full_ids[100:100 + nq]) and torch.equal(sc, full_sc[100:100 + nq])
+
+
+def test_exhaustive_search_is_exact_knn(tiny):
+    """All clusters probed with R >= every cluster size: exact brute force."""
+    import torch
+    cfg = dict(tiny["cfg"])
+    X, Q, C, A, b = tiny["X"][:2000], tiny["Q"][:50], tiny["C"], tiny["A"], tiny["b"]
+    asg, _ = O.assign(X, C)
+    k = 1
+    cfg["r0"] = int(np.bincount(asg).max())       # R >= every cluster size
+    assert cfg["r0"] * k * cfg["L"] <= 4096
+    g = F.gpu_index(cfg, X, C, A, b)
+    ids, sc = g.search(torch.from_numpy(Q).cuda(), k, cfg["n_clusters"])
+    tid, tsc = O.exact_knn(X, Q, k)
+    bad = F.check_topk(ids.cpu().numpy(), sc.cpu().numpy(), tid, tsc, X, Q)
+    assert not bad, bad[:5]
+
+
+def test_k_beyond_candidates_pads(tiny):
+    import torch
+    cfg = dict(tiny["cfg"])
+    cfg["r0"] = 1
+    X, C, A, b = tiny["X"], tiny["C"], tiny["A"], tiny["b"]
+    Q = tiny["Q"][:20]
+    g = F.gpu_index(cfg, X, C, A, b)
+    k = 600                               # R = 600 per array but clusters are smaller
+    ids, sc = g.search(torch.from_numpy(Q).cuda(), k, 1)
+    ref = O.search(O.build_index(X, C, A, b, cfg["L"], cfg["m"], cfg["W"], cfg["leaves"]), Q, k, 1, k)
+    bad = F.check_topk(ids.cpu().numpy(), sc.cpu().numpy(), ref.ids, ref.scores, X, Q)
+    assert not bad, bad[:5]
+    assert np.any(ids.cpu().numpy() == -1)
+
+
+def test_duplicates_empty_and_singleton_clusters():
+    """Duplicate corpus rows (equal keys), a centroid no point chooses (empty
+    cluster) and a one-point cluster."""
+    import torch
+    rng = np.random.default_rng(5)
+    d, n = 16, 600
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    X /= np.linalg.norm(X, axis=1, keepdims=True)
+    X[100:140] = X[3]                                   # 41 identical rows
+    X[599] *= 10.0                                      # an outlier with its own centroid
+    far = np.full((1, d), 50.0, np.float32)             # nobody's nearest centroid
+    lone = X[599:600].copy()
+    C = np.concatenate([X[rng.choice(599, 4, replace=False)], far, lone]).astype(np.float32)
+    cfg = dict(L=3, m=8, W=0.7, leaves=8, r0=3, B=2, k=5)
+    A = rng.standard_normal((cfg["L"] * cfg["m"], d)).astype(np.float32)
+    b = (rng.random(cfg["L"] * cfg["m"]) * cfg["W"]).astype(np.float32)
+    Q = np.concatenate([X[:40], rng.standard_normal((20, d)).astype(np.float32)])
+    g = F.gpu_index(cfg, X, C, A, b)
+    ref_idx = O.build_index(X, C, A, b, cfg["L"], cfg["m"], cfg["W"], cfg["leaves"], B=cfg["B"])
+    sizes = np.diff(g.cluster_offsets())
+    assert sizes[4] == 0 and sizes[5] == 1
+    for c in (1, 3, 6):
+        ids, sc, st, tr = g.search(torch.from_numpy(Q).cuda(), cfg["k"], c, stats=True, trace=True)
+        ref = O.search(ref_idx, Q, cfg["k"], c, cfg["r0"] * cfg["k"])
+        bad, _ = F.check_trace(tr, ref)
+        assert not bad, bad[:5]
+        bad = F.check_topk(ids.cpu().numpy(), sc.cpu().numpy(), ref.ids, ref.scores, X, Q)
+        assert not bad, bad[:5]
+        if c == 6:
+            assert st["empty_pairs"] == len(Q)
+
+
+def test_invalid_search_arguments(tiny):
+    import torch
+    from paper_2205_00970_b300 import lider
+    g, Qd = tiny["gidx"], tiny["Qd"][:4]
+    for k, c, code in [(0, 1, -1), (10, 0, -1), (10, 17, -1), (2000, 1, -4), (1000, 1, -4)]:
+        with pytest.raises(lider.LiderError) as e:
+            g.search(Qd, k, c)
+        assert e.value.code == code
