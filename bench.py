@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""LIDER batched query search throughput on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lider|reference]
+
+One step = one lider_search of the whole query batch of the workload (all
+steps of the method: hash, route, group, locate/expand, gather/score/top-k,
+merge) with the index and queries resident in HBM.  Prints one JSON line.
+
+  value     queries/s over all ranks (device-resident inputs, CUDA events)
+  e2e       the same through lider_search_host: queries copied from pinned
+            host memory and results copied back inside the timed region
+  roofline  the gather/score kernel: algorithmic bytes (unique candidates x
+            (d*4 + 4)) per launch / its event-timed duration vs measured HBM
+  cpu_baseline  the FP64 oracle on a bounded query sample on host cores
+
+--impl reference times the FP64 oracle itself (there is no released
+implementation of the paper) on the same workload and prints its line.
+Under torchrun (N > 1) every rank searches its own replica (replicas only:
+the method has no cross-GPU exchange at one-GPU scale); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2205_00970_b300 import configs, synth  # noqa: E402
+
+METRIC = "queries/s at fixed recall@10 vs FP64 oracle (plain vs served BF16); p50/p99 ms"
+LAUNCHES_PER_SEARCH = 10   # our kernels per lider_search (see the phase list in search.cu)
+
+
+def workload_desc(cfg) -> dict:
+    return {
+        "workload": (f"{cfg['name']}: corpus {cfg['n']:,} x {cfg['d']} FP32 ({cfg['n_comp']:,}-component "
+                     f"Gaussian mixture, sigma {cfg['sigma']}, L2-normalised), {cfg['nq']:,} queries; "
+                     f"{cfg['n_clusters']} k-means clusters, c={cfg['c']}; L={cfg['L']}, m={cfg['m']}, "
+                     f"W={cfg['W']}; RMI {cfg['leaves']} leaves; k={cfg['k']}, R=r0*k={cfg['R']}; seed {cfg['seed']}"),
+        "nq_per_step": cfg["nq"],
+        "l2": f"inputs larger than L2 (corpus {cfg['n'] * cfg['d'] * 4 / 1e9:.2f} GB resident)",
+    }
+
+
+def load_inputs(cfg):
+    X = synth.corpus(cfg["seed"], cfg["n"], cfg["d"], cfg["n_comp"], cfg["sigma"], cfg["zipf_s"])
+    Q = synth.queries(cfg["seed"], cfg["nq"], cfg["d"], cfg["n_comp"], cfg["sigma"], cfg["zipf_s"])
+    C = np.load(os.path.join(ROOT, "tests", "golden", f"centroids_{cfg['name']}.npy"))
+    A, b = synth.projections(cfg["seed"], cfg["L"], cfg["m"], cfg["d"], cfg["W"])
+    return X, Q, C, A, b
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{self.gpu}.csv")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names[1:], f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- oracle ---
+
+def cpu_baseline(cfg, X, Q, C, A, b, gpu_ids, budget_s: float = 20.0) -> dict:
+    """The FP64 oracle as it stands, on host cores, on a bounded query sample;
+    also recall@10 of the GPU results on that sample against exact FP64 kNN."""
+    from threadpoolctl import threadpool_limits
+
+    from oracle import lider_oracle as O
+    t = time.perf_counter()
+    idx = O.build_index(X, C, A, b, cfg["L"], cfg["m"], cfg["W"], cfg["leaves"], B=cfg["B"])
+    build_s = time.perf_counter() - t
+    done = 0
+    ref_ids = []
+    with threadpool_limits(limits=1):
+        t = time.perf_counter()
+        while done < len(Q) and (time.perf_counter() - t < budget_s or done < 4):
+            r = O.search(idx, Q[done:done + 1], cfg["k"], cfg["c"], cfg["R"])
+            ref_ids.append(r.ids[0])
+            done += 1
+        search_s = time.perf_counter() - t
+    ref_ids = np.array(ref_ids)
+    truth, _ = O.exact_knn(X, Q[:done], 10)
+    out = {
+        "value": done / search_s, "unit": "queries/s", "cores": 1, "kind": "oracle",
+        "sample": (f"first {done} of {len(Q)} queries of the same workload, FP64 oracle search "
+                   f"(Python/numpy, BLAS limited to 1 thread), {search_s:.1f} s; oracle build {build_s:.1f} s "
+                   f"on {os.cpu_count()} cores not timed"),
+        "recall_at_10_gpu": O.recall_at(gpu_ids[:done], truth, 10),
+        "recall_at_10_oracle": O.recall_at(ref_ids, truth, 10),
+        "gpu_eq_oracle_top10": float(np.mean([np.array_equal(gpu_ids[i, :10], ref_ids[i, :10])
+                                              for i in range(done)])),
+    }
+    return out
+
+
+def run_reference(args, cfg):
+    """--impl reference: the FP64 oracle timed on host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from threadpoolctl import threadpool_limits
+
+    from oracle import lider_oracle as O
+    X, Q, C, A, b = load_inputs(cfg)
+    idx = O.build_index(X, C, A, b, cfg["L"], cfg["m"], cfg["W"], cfg["leaves"], B=cfg["B"])
+    per_step = args.ref_queries_per_step
+    times = []
+    with threadpool_limits(limits=1):
+        for s in range(args.warmup + args.steps):
+            q0 = (s * per_step) % len(Q)
+            t = time.perf_counter()
+            O.search(idx, Q[q0:q0 + per_step], cfg["k"], cfg["c"], cfg["R"])
+            if s >= args.warmup:
+                times.append(time.perf_counter() - t)
+    total = sum(times)
+    value = per_step * len(times) / total
+    sample = (f"{per_step} queries per step of the {cfg['nq']:,}-query batch, FP64 oracle "
+              f"(Python/numpy, BLAS limited to 1 thread)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_desc(cfg),
+        "cpu_baseline": {"value": value, "unit": "queries/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ lider ---
+
+def run_lider(args, cfg):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2205_00970_b300 import lider
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    X, Q, C, A, b = load_inputs(cfg)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    Xd = t(X)
+    idx = lider.Index(Xd, t(C), t(A), t(b), L=cfg["L"], m=cfg["m"], W=cfg["W"], rmi_leaves=cfg["leaves"],
+                      r0=cfg["r0"], B=cfg["B"])
+    del Xd
+    Qd = t(Q)
+    k, c, nq = cfg["k"], cfg["c"], cfg["nq"]
+    ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
+    sc = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    _, _, stats = idx.search(Qd, k, c, stats=True, out=(ids, sc))
+    gpu_ids = ids.cpu().numpy()
+
+    for _ in range(args.warmup):
+        idx.search(Qd, k, c, out=(ids, sc))
+    nph = lider.NUM_PHASES + 1
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nph)] for _ in range(args.steps)]
+    for row in evs:
+        for e in row:
+            e.record()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    t0.record()
+    for s in range(args.steps):
+        idx.search_phased(Qd, k, c, evs[s], out=(ids, sc))
+    t1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    total_ms = t0.elapsed_time(t1)
+    step_ms = [evs[s][0].elapsed_time(evs[s][nph - 1]) for s in range(args.steps)]
+    phase_ms = {name: float(np.mean([evs[s][i].elapsed_time(evs[s][i + 1]) for s in range(args.steps)]))
+                for i, name in enumerate(lider.PHASES)}
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = world * nq * args.steps / (total_ms / 1e3)
+
+    # end to end: pinned host queries in, host results out, every step
+    Qh = torch.from_numpy(Q).pin_memory()
+    ids_h = torch.empty((nq, k), dtype=torch.int64).pin_memory()
+    sc_h = torch.empty((nq, k), dtype=torch.float32).pin_memory()
+    for _ in range(max(1, args.warmup // 2)):
+        idx.search_host(Qh, k, c, ids_h, sc_h)
+    if world > 1:
+        dist.barrier()
+    te = time.perf_counter()
+    for _ in range(args.steps):
+        idx.search_host(Qh, k, c, ids_h, sc_h)
+    e2e_s = time.perf_counter() - te
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_value = world * nq * args.steps / e2e_s
+
+    cand = stats["candidates"]
+    alg_bytes = cand * (cfg["d"] * 4 + 4)
+    score_s = phase_ms["score"] / 1e3
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / score_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "score_kernel",
+                "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback",
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "note": "gathered rows are reused across the queries of one cluster through L2; "
+                        "DRAM traffic per launch is below the algorithmic bytes"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(workload_desc(cfg), parallelism=f"replicas x{world}"),
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                       "of": f"one batch of {nq:,} queries"},
+        "phase_ms": phase_ms,
+        "search_stats": stats,
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": int(Q.nbytes),
+                "d2h_bytes_per_step": int(nq * k * (8 + 4))},
+        "gpu_launches": LAUNCHES_PER_SEARCH * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, X, Q, C, A, b, gpu_ids, args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    idx.free()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["lider", "reference"], default="lider")
+    ap.add_argument("--workload", default="mid")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--ref-queries-per-step", type=int, default=8)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    cfg = configs.get(args.workload)
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+    return run_lider(args, cfg)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

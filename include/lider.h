@@ -80,15 +80,29 @@ typedef struct {
     int64_t reserved;
 } lider_search_stats;
 
-/* Optional per-step outputs of a search, for parity checking.  Every member
- * may be NULL; non-NULL members are device arrays the caller allocates:
+/* Phases of one search, in order; events[i] is recorded when phase i starts
+ * and events[LIDER_NUM_PHASES] when the last one ends. */
+#define LIDER_PHASE_HASH    0   /* query hashkeys (Sec. 4.1)                   */
+#define LIDER_PHASE_ROUTE   1   /* top-c centroids (Sec. 3.3.2)                */
+#define LIDER_PHASE_GROUP   2   /* (query, cluster) pairs bucketed by cluster  */
+#define LIDER_PHASE_LOCATE  3   /* re-scale, RMI, bounded search, expansion    */
+#define LIDER_PHASE_SCORE   4   /* candidate union, exact scores, per-pair top-k */
+#define LIDER_PHASE_MERGE   5   /* per-query merge of the c lists (Sec. 6.2)   */
+#define LIDER_NUM_PHASES    6
+
+/* Optional per-step outputs of a search, for parity checking and profiling.
+ * Every member may be NULL; non-NULL array members are device arrays the
+ * caller allocates:
  *   route  [nq*c]    probed clusters of each query, best first;
  *   qkeys  [nq*L]    packed query hashkeys;
  *   pstar  [nq*c*L]  lower bound of the query key in each probed cluster's array
  *                    (cluster-local position);
  *   wstart [nq*c*L]  start of the expansion window (cluster-local);
  *   wlen   [nq*c*L]  its length, min(R, n_c);
- *   ucount [nq*c]    unique candidates scored in each probed cluster. */
+ *   ucount [nq*c]    unique candidates scored in each probed cluster;
+ *   events           host array of LIDER_NUM_PHASES + 1 cudaEvent_t handles
+ *                    (entries may be NULL), recorded on the search stream at
+ *                    the phase boundaries; the caller creates and owns them. */
 typedef struct {
     int32_t*  route;
     uint64_t* qkeys;
@@ -96,6 +110,7 @@ typedef struct {
     int32_t*  wstart;
     int32_t*  wlen;
     int32_t*  ucount;
+    void* const* events;
 } lider_trace;
 
 /* Build an index (Sec. 3.3.2 "LIDER is built as follows"; Sec. 3.3.1 for one

@@ -376,7 +376,8 @@ class Index:
         return np.nonzero(self.asg == j)[0]
 
     def core(self, j: int, fit: bool = True) -> CoreModel:
-        if j not in self.cores:
+        cached = self.cores.get(j)
+        if cached is None or (fit and any(r is None for r in cached.rmi) and len(cached.ids)):
             self.cores[j] = build_core(self, j, fit)
         return self.cores[j]
 

@@ -16,7 +16,7 @@ CONFIGS = {
                  B=1, kmeans_iters=10, kmeans_sample=10_000, seed=0),
     # Plain method, mid: 1M x 768, 256 clusters, c=8, L=8, m=16, k=100.
     "mid": dict(n=1_000_000, d=768, n_comp=1_024, sigma=0.3, zipf_s=None, nq=10_000,
-                n_clusters=256, c=8, L=8, m=16, W=1.0, leaves=1_024, k=100, r0=2,
+                n_clusters=256, c=8, L=8, m=16, W=1.0, leaves=1_024, k=100, r0=3,
                 B=1, kmeans_iters=10, kmeans_sample=65_536, seed=0),
 }
 

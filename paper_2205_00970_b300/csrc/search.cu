@@ -471,9 +471,15 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
     const int R = ix->params.r0 * k;
     const int64_t np = nq * c;
     int rc;
+    void* const* ev = tr ? tr->events : nullptr;
+    auto mark = [&](int phase) -> int {
+        if (ev && ev[phase]) LIDER_CUDA_TRY(cudaEventRecord((cudaEvent_t)ev[phase], st));
+        return LIDER_OK;
+    };
     LIDER_CUDA_TRY(cudaMemsetAsync(w.counters, 0, w.zero_bytes, st));
 
     // 1. hash
+    if ((rc = mark(LIDER_PHASE_HASH))) return rc;
     if ((rc = launch_hash_t(Q, nq, g.d, g.A, g.bproj, g.H, g.W, w.tq, st))) return rc;
     if ((rc = launch_pack(w.tq, nq, g.L, g.m, g.beta, 0, g.L, 1, w.qkeys, &w.counters[CNT_QBOUNDARY],
                           &w.counters[CNT_QCLAMPED], st)))
@@ -481,11 +487,13 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
     if (tr && tr->qkeys)
         LIDER_CUDA_TRY(cudaMemcpyAsync(tr->qkeys, w.qkeys, (size_t)nq * g.L * 8, cudaMemcpyDeviceToDevice, st));
     // 2. route
+    if ((rc = mark(LIDER_PHASE_ROUTE))) return rc;
     if ((rc = launch_scores(Q, nq, g.d, g.C, g.half_norm, g.ncl, w.rscore, st))) return rc;
     topc_kernel<<<(unsigned)cdiv(nq * 32, 256), 256, 0, st>>>(w.rscore, nq, g.ncl, c, w.route,
                                                               tr ? tr->route : nullptr);
     LIDER_LAUNCH_CHECK("topc_kernel");
     // 3. group
+    if ((rc = mark(LIDER_PHASE_GROUP))) return rc;
     group_count_kernel<<<(unsigned)cdiv(np, 256), 256, 0, st>>>(w.route, np, w.cnt);
     LIDER_LAUNCH_CHECK("group_count_kernel");
     group_scan_kernel<<<1, 1024, 0, st>>>(w.cnt, g.ncl, w.off, w.cursor, w.item_off);
@@ -493,11 +501,13 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
     group_fill_kernel<<<(unsigned)cdiv(np, 256), 256, 0, st>>>(w.route, np, w.cursor, w.pairs);
     LIDER_LAUNCH_CHECK("group_fill_kernel");
     // 4. locate + expand
+    if ((rc = mark(LIDER_PHASE_LOCATE))) return rc;
     locate_kernel<<<(unsigned)cdiv(np * g.L, 256), 256, 0, st>>>(
         g, np, c, R, w.route, w.qkeys, w.wstart, w.wlen, tr ? tr->pstar : nullptr, tr ? tr->wstart : nullptr,
         tr ? tr->wlen : nullptr, w.counters);
     LIDER_LAUNCH_CHECK("locate_kernel");
     // 5. gather + score + per-pair top-k
+    if ((rc = mark(LIDER_PHASE_SCORE))) return rc;
     ScoreArgs sa;
     sa.g = g;
     sa.Q = Q;
@@ -527,9 +537,10 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
     score_kernel<<<grid, kScoreThreads, smem, st>>>(sa);
     LIDER_LAUNCH_CHECK("score_kernel");
     // 6. merge
+    if ((rc = mark(LIDER_PHASE_MERGE))) return rc;
     merge_kernel<<<(unsigned)cdiv(nq * 32, 256), 256, 0, st>>>(w.pscore, w.pid, nq, c, k, out_ids, out_scores);
     LIDER_LAUNCH_CHECK("merge_kernel");
-    return LIDER_OK;
+    return mark(LIDER_NUM_PHASES);
 }
 
 int read_stats(const Workspace& w, int64_t nq, int c, lider_search_stats* stats, cudaStream_t st) {

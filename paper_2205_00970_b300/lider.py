@@ -44,7 +44,11 @@ class Stats(ctypes.Structure):
 
 class Trace(ctypes.Structure):
     _fields_ = [("route", ctypes.c_void_p), ("qkeys", ctypes.c_void_p), ("pstar", ctypes.c_void_p),
-                ("wstart", ctypes.c_void_p), ("wlen", ctypes.c_void_p), ("ucount", ctypes.c_void_p)]
+                ("wstart", ctypes.c_void_p), ("wlen", ctypes.c_void_p), ("ucount", ctypes.c_void_p),
+                ("events", ctypes.POINTER(ctypes.c_void_p))]
+
+NUM_PHASES = 6
+PHASES = ("hash", "route", "group", "locate", "score", "merge")
 
 
 def _load():
@@ -160,7 +164,7 @@ class Index:
                 "wlen": torch.empty((nq, c, self.L), dtype=torch.int32, device=Q.device),
                 "ucount": torch.empty((nq, c), dtype=torch.int32, device=Q.device),
             }
-            tr = Trace(*(tr_t[n].data_ptr() for n in ("route", "qkeys", "pstar", "wstart", "wlen", "ucount")))
+            tr = Trace(*(tr_t[n].data_ptr() for n in ("route", "qkeys", "pstar", "wstart", "wlen", "ucount")), None)
             _check(_lib.lider_search_trace(self._h, Q.data_ptr(), nq, k, c, ids.data_ptr(), sc.data_ptr(),
                                            ctypes.byref(tr), sp, _stream_ptr(stream)))
         else:
@@ -172,6 +176,20 @@ class Index:
         if trace:
             res.append(tr_t)
         return tuple(res)
+
+    def search_phased(self, Q: torch.Tensor, k: int, c: int, events, stream=None, out=None):
+        """lider_search that records NUM_PHASES + 1 torch.cuda.Events (already
+        created, e.g. recorded once) at the phase boundaries on the stream."""
+        Q = _dev(Q, torch.float32, "queries")
+        nq = Q.shape[0]
+        ids, sc = out if out is not None else (
+            torch.empty((nq, k), dtype=torch.int64, device=Q.device),
+            torch.empty((nq, k), dtype=torch.float32, device=Q.device))
+        arr = (ctypes.c_void_p * (NUM_PHASES + 1))(*[e.cuda_event for e in events])
+        tr = Trace(None, None, None, None, None, None, ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)))
+        _check(_lib.lider_search_trace(self._h, Q.data_ptr(), nq, k, c, ids.data_ptr(), sc.data_ptr(),
+                                       ctypes.byref(tr), None, _stream_ptr(stream)))
+        return ids, sc
 
     def search_host(self, Q: torch.Tensor, k: int, c: int, ids: torch.Tensor | None = None,
                     scores: torch.Tensor | None = None, stats: bool = False, stream=None):
