@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 from paper_2205_00970_b300 import configs, synth  # noqa: E402
 
 METRIC = "queries/s at fixed recall@10 vs FP64 oracle (plain vs served BF16); p50/p99 ms"
-LAUNCHES_PER_SEARCH = 10   # our kernels per lider_search (see the phase list in search.cu)
+LAUNCHES_PER_SEARCH = 11   # our kernels per lider_search (see the phase list in search.cu)
 
 
 def workload_desc(cfg) -> dict:
@@ -347,10 +347,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-queries-per-step", type=int, default=8)
+    ap.add_argument("--n", type=int, default=None, help="profiling size: first n corpus rows")
+    ap.add_argument("--nq", type=int, default=None, help="profiling size: first nq queries")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     cfg = configs.get(args.workload)
+    if args.n:
+        cfg["n"] = min(cfg["n"], args.n)
+    if args.nq:
+        cfg["nq"] = min(cfg["nq"], args.nq)
     if args.impl == "reference":
         return run_reference(args, cfg)
     return run_lider(args, cfg)

@@ -6,16 +6,18 @@
 //   2. route    dot2_tile_kernel<score> + topc_kernel: the c best centroids,
 //               score x.mu - |mu|^2/2, ties -> lower cluster index
 //   3. group    group_*_kernel: (query, probe) pairs bucketed by cluster, cut
-//               into work items of up to kGroup pairs of one cluster
+//               into work items of up to G pairs of one cluster
 //   4. locate   locate_kernel, one thread per (pair, array): re-scale the key
 //               (Sec. 5.1), two-stage RMI prediction (Sec. 5.2), clamp
 //               (Sec. 7.3), lower bound searched inside the leaf's recorded
 //               error window (with a counted fallback outside it), then the
 //               bi-directional expansion window of Sec. 4 by co-rank search
-//   5. score    score_kernel, persistent, one work item at a time: union of
-//               the L windows (deduplicated in a shared-memory hash set),
-//               exact FP32 inner products of the gathered rows, per-pair
-//               top-k by bitonic sort in shared memory
+//   5. score    score_group_kernel, persistent, one work item (G pairs of
+//               one cluster) at a time: union of each pair's L windows as
+//               bits of a shared-memory position mask, the marked rows
+//               streamed once and scored by exact FP32 inner products with
+//               every query that marked them; topk_kernel: per-pair top-k
+//               by bitonic sort in shared memory
 //   6. merge    merge_kernel, one warp per query: k-way merge of its c lists
 //               (Sec. 6.2, heap of list heads)
 #include <algorithm>
@@ -28,8 +30,6 @@ namespace lider {
 namespace {
 
 constexpr int kScoreThreads = 256;
-constexpr int kGroup = 8;            // pairs of one cluster per work item
-constexpr uint32_t kEmpty = 0xffffffffu;
 
 // counters[] slots
 enum {
@@ -89,8 +89,8 @@ __global__ void group_count_kernel(const int32_t* __restrict__ route, int64_t np
 }
 
 // Single block: off = exclusive scan of cnt, item_off = exclusive scan of
-// ceil(cnt / kGroup), cursor = off.
-__global__ void group_scan_kernel(const int32_t* __restrict__ cnt, int ncl, int32_t* __restrict__ off,
+// ceil(cnt / G), cursor = off.
+__global__ void group_scan_kernel(const int32_t* __restrict__ cnt, int ncl, int G, int32_t* __restrict__ off,
                                   int32_t* __restrict__ cursor, int32_t* __restrict__ item_off) {
     __shared__ int32_t s_a[1024], s_b[1024];
     __shared__ int32_t carry_a, carry_b;
@@ -100,7 +100,7 @@ __global__ void group_scan_kernel(const int32_t* __restrict__ cnt, int ncl, int3
         const int j = base + threadIdx.x;
         const int32_t v = (j < ncl) ? cnt[j] : 0;
         s_a[threadIdx.x] = v;
-        s_b[threadIdx.x] = (v + kGroup - 1) / kGroup;
+        s_b[threadIdx.x] = (v + G - 1) / G;
         __syncthreads();
         for (int o = 1; o < 1024; o <<= 1) {          // inclusive Hillis-Steele scan
             const int32_t ta = threadIdx.x >= o ? s_a[threadIdx.x - o] : 0;
@@ -114,7 +114,7 @@ __global__ void group_scan_kernel(const int32_t* __restrict__ cnt, int ncl, int3
             const int32_t ea = carry_a + s_a[threadIdx.x] - v;
             off[j] = ea;
             cursor[j] = ea;
-            item_off[j] = carry_b + s_b[threadIdx.x] - (v + kGroup - 1) / kGroup;
+            item_off[j] = carry_b + s_b[threadIdx.x] - (v + G - 1) / G;
         }
         __syncthreads();
         if (threadIdx.x == 1023) { carry_a += s_a[1023]; carry_b += s_b[1023]; }
@@ -208,147 +208,204 @@ __global__ void locate_kernel(Geometry g, int64_t npairs, int c, int R,
 }
 
 // ------------------------------------------------------------------ score --
+// Work item = up to G (query, probe) pairs of one cluster j.  Each pair's
+// candidate set is the union of its L expansion windows (Sec. 3.3.1: each
+// array is searched, then the results are merged); here it is a bit per
+// (cluster-local position, pair) in a shared-memory mask, so duplicates
+// across arrays collapse for free.  The cluster's rows are then streamed
+// once per item: every marked row is loaded by one warp and dotted with each
+// query whose bit is set.  A row shared by several queries of the item is
+// read once instead of once per query.
+//
+// Score of (q, row): lane l accumulates x[i]*q[i] for float4 chunks
+// i = l, l+32, ... in ascending order with FMA, then a butterfly sum over the
+// warp.  The order depends only on d, so a query's scores do not depend on
+// its batch-mates.
 struct ScoreArgs {
     Geometry g;
     const float* Q;
-    int c, k, max_lr, ht_size, sort_cap;
+    int c, G, T_cap;            // T_cap = L * R, capacity of one pair's score list
     const int32_t* off;
     const int32_t* cnt;
     const int32_t* item_off;
     const int32_t* pairs;
+    const int32_t* route;
     const int32_t* wstart;
     const int32_t* wlen;
-    float* pscore;          // npairs x k
-    int64_t* pid;           // npairs x k (corpus ids)
-    int32_t* trace_ucount;
+    uint64_t* pbuf;             // npairs x T_cap keys: (~order(score) << 32) | position
+    int32_t* ucount;            // npairs
     unsigned long long* counters;
 };
+
+constexpr int kMaxGroup = 16;    // bits of a position's mask
+constexpr int kTile = 8192;      // positions per mask tile
+constexpr int kNV = 8;           // float4 per lane per row chunk (1024 columns)
 
 __device__ __forceinline__ float warp_sum(float v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-// Dynamic shared memory: q (d floats) | hash set (ht_size u32) |
-// candidate list (max_lr u32) | sort keys (sort_cap u64).
-__global__ void __launch_bounds__(kScoreThreads) score_kernel(ScoreArgs a) {
+// Dynamic shared memory: queries G x d floats | mask kTile/2 u32 (16 bits per position).
+__global__ void __launch_bounds__(kScoreThreads) score_group_kernel(ScoreArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const Geometry& g = a.g;
-    float* qv = reinterpret_cast<float*>(smem);
-    uint32_t* htab = reinterpret_cast<uint32_t*>(smem + (size_t)g.d * 4);
-    uint32_t* cand = htab + a.ht_size;
-    uint64_t* skey = reinterpret_cast<uint64_t*>(
-        smem + align_up_dev((size_t)g.d * 4 + (size_t)(a.ht_size + a.max_lr) * 4, 16));
-    __shared__ int s_item, s_U;
+    float* Qs = reinterpret_cast<float*>(smem);
+    uint32_t* mask = reinterpret_cast<uint32_t*>(smem + (size_t)a.G * g.d * 4);
+    __shared__ int s_item;
+    __shared__ int s_cnt[kMaxGroup];
+    __shared__ int64_t s_pair[kMaxGroup];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nwarps = kScoreThreads / 32;
+    constexpr int nwarps = kScoreThreads / 32;
     const int total_items = a.item_off[g.ncl];
-    const uint32_t hmask = (uint32_t)a.ht_size - 1;
+    const int d4 = g.d / 4;
+    const float4* Qs4 = reinterpret_cast<const float4*>(Qs);
 
     for (;;) {
         if (tid == 0) s_item = (int)atomicAdd(&a.counters[CNT_ITEM], 1ull);
         __syncthreads();
         const int item = s_item;
         if (item >= total_items) break;
-        // cluster of this item: last j with item_off[j] <= item
-        int lo = 0, hi = g.ncl - 1;
+        int lo = 0, hi = g.ncl - 1;                       // last j with item_off[j] <= item
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (a.item_off[mid] <= item) lo = mid; else hi = mid - 1;
         }
         const int j = lo;
-        const int first = a.off[j] + (item - a.item_off[j]) * kGroup;
-        const int count = min(kGroup, a.off[j] + a.cnt[j] - first);
+        const int first = a.off[j] + (item - a.item_off[j]) * a.G;
+        const int count = min(a.G, a.off[j] + a.cnt[j] - first);
         const int64_t base = g.cl_off[j];
+        const int64_t n_c = g.cl_off[j + 1] - base;
 
-        for (int gi = 0; gi < count; ++gi) {
-            const int64_t pair = a.pairs[first + gi];
-            const int64_t q = pair / a.c;
-            for (int i = tid; i < a.ht_size; i += kScoreThreads) htab[i] = kEmpty;
-            const float4* q4 = reinterpret_cast<const float4*>(a.Q + q * g.d);
-            for (int i = tid; i < g.d / 4; i += kScoreThreads) reinterpret_cast<float4*>(qv)[i] = q4[i];
-            if (tid == 0) s_U = 0;
+        if (tid < count) {
+            s_pair[tid] = a.pairs[first + tid];
+            s_cnt[tid] = 0;
+        }
+        __syncthreads();
+        for (int i = tid; i < count * d4; i += kScoreThreads) {
+            const int gq = i / d4, c4 = i - gq * d4;
+            const int64_t q = s_pair[gq] / a.c;
+            reinterpret_cast<float4*>(Qs)[i] = reinterpret_cast<const float4*>(a.Q + q * g.d)[c4];
+        }
+        const int T = (int)min((int64_t)a.T_cap / g.L, n_c);   // window length min(R, n_c)
+
+        for (int64_t t0 = 0; t0 < n_c; t0 += kTile) {
+            const int tl = (int)min((int64_t)kTile, n_c - t0);
+            for (int i = tid; i < (tl + 1) / 2; i += kScoreThreads) mask[i] = 0u;
             __syncthreads();
-
-            // union of the L windows (Sec. 3.3.1: merge the arrays' results)
-            for (int l = 0; l < g.L; ++l) {
-                const int32_t ws = a.wstart[pair * g.L + l];
-                const int32_t wl = a.wlen[pair * g.L + l];
-                const int32_t* P = g.pos + (int64_t)l * g.n + base + ws;
-                for (int t = tid; t < wl; t += kScoreThreads) {
-                    const uint32_t p = (uint32_t)P[t];
-                    uint32_t h = (p * 2654435761u) & hmask;
-                    for (;;) {
-                        const uint32_t old = atomicCAS(&htab[h], kEmpty, p);
-                        if (old == kEmpty) {
-                            cand[atomicAdd(&s_U, 1)] = p;
-                            break;
+            // mark the union of the windows of every pair of the item
+            const int per_pair = g.L * T;
+            for (int i = tid; i < count * per_pair; i += kScoreThreads) {
+                const int gq = i / per_pair;
+                const int r = i - gq * per_pair;
+                const int l = r / T, t = r - l * T;
+                const int32_t ws = a.wstart[s_pair[gq] * g.L + l];
+                const int32_t p = g.pos[(int64_t)l * g.n + base + ws + t];
+                const int64_t pl = (int64_t)p - t0;
+                if (pl >= 0 && pl < tl)
+                    atomicOr(&mask[pl >> 1], (1u << gq) << (16 * (int)(pl & 1)));
+            }
+            __syncthreads();
+            // stream the marked rows of the tile
+            for (int pl = warp; pl < tl; pl += nwarps) {
+                const uint32_t m = (mask[pl >> 1] >> (16 * (pl & 1))) & 0xffffu;
+                if (m == 0u) continue;
+                const int64_t row = base + t0 + pl;
+                const float4* X4 = reinterpret_cast<const float4*>(g.X + row * (int64_t)g.d);
+                float part[kMaxGroup];
+#pragma unroll
+                for (int q = 0; q < kMaxGroup; ++q) part[q] = 0.f;
+                for (int c0 = 0; c0 < d4; c0 += 32 * kNV) {
+                    float4 x[kNV];
+#pragma unroll
+                    for (int v = 0; v < kNV; ++v) {
+                        const int i4 = c0 + lane + 32 * v;
+                        x[v] = (i4 < d4) ? __ldg(X4 + i4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int q = 0; q < kMaxGroup; ++q) {
+                        if (!((m >> q) & 1u)) continue;
+                        float acc = part[q];
+#pragma unroll
+                        for (int v = 0; v < kNV; ++v) {
+                            const int i4 = c0 + lane + 32 * v;
+                            if (i4 < d4) {
+                                const float4 y = Qs4[q * d4 + i4];
+                                acc = fmaf(x[v].x, y.x, acc);
+                                acc = fmaf(x[v].y, y.y, acc);
+                                acc = fmaf(x[v].z, y.z, acc);
+                                acc = fmaf(x[v].w, y.w, acc);
+                            }
                         }
-                        if (old == p) break;
-                        h = (h + 1) & hmask;
+                        part[q] = acc;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kMaxGroup; ++q) {
+                    if (!((m >> q) & 1u)) continue;
+                    const float sc = warp_sum(part[q]);
+                    if (lane == 0) {
+                        const int slot = atomicAdd(&s_cnt[q], 1);
+                        a.pbuf[s_pair[q] * a.T_cap + slot] =
+                            ((uint64_t)(~float_order(sc)) << 32) | (uint64_t)(uint32_t)(t0 + pl);
                     }
                 }
             }
             __syncthreads();
-            const int U = s_U;
+        }
+        if (tid < count) {
+            a.ucount[s_pair[tid]] = s_cnt[tid];
+            atomicAdd(&a.counters[CNT_CANDIDATES], (unsigned long long)s_cnt[tid]);
+        }
+        __syncthreads();
+    }
+}
 
-            // exact inner products: one warp per candidate row
-            const float4* qv4 = reinterpret_cast<const float4*>(qv);
-            const int d4 = g.d / 4;
-            for (int u = warp; u < U; u += nwarps) {
-                const uint32_t p = cand[u];
-                const float4* row = reinterpret_cast<const float4*>(g.X + (base + p) * (int64_t)g.d);
-                float acc = 0.f;
-                for (int i = lane; i < d4; i += 32) {
-                    const float4 x = __ldg(row + i);
-                    const float4 y = qv4[i];
-                    acc = fmaf(x.x, y.x, acc);
-                    acc = fmaf(x.y, y.y, acc);
-                    acc = fmaf(x.z, y.z, acc);
-                    acc = fmaf(x.w, y.w, acc);
-                }
-                acc = warp_sum(acc);
-                if (lane == 0)
-                    skey[u] = ((uint64_t)(~float_order(acc)) << 32) | (uint64_t)p;
-            }
-            const int SP = U > 1 ? next_pow2_dev(U) : 1;
-            for (int u = U + tid; u < SP; u += kScoreThreads) skey[u] = ~0ull;
-            __syncthreads();
-
-            // ascending sort of (~score order, position): best first, ties by
-            // position, which follows corpus id inside a cluster
-            for (int size = 2; size <= SP; size <<= 1) {
-                for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                    for (int i = tid; i < SP / 2; i += kScoreThreads) {
-                        const int lo_i = 2 * stride * (i / stride) + (i % stride);
-                        const int hi_i = lo_i + stride;
-                        const bool up = (lo_i & size) == 0;
-                        const uint64_t x0 = skey[lo_i], x1 = skey[hi_i];
-                        if ((x0 > x1) == up) { skey[lo_i] = x1; skey[hi_i] = x0; }
-                    }
-                    __syncthreads();
-                }
-            }
-
-            float* ps = a.pscore + pair * a.k;
-            int64_t* pi = a.pid + pair * a.k;
-            for (int r = tid; r < a.k; r += kScoreThreads) {
-                if (r < U) {
-                    const uint64_t kv = skey[r];
-                    ps[r] = float_from_order(~(uint32_t)(kv >> 32));
-                    pi[r] = g.orig_id[base + (int64_t)(uint32_t)kv];
-                } else {
-                    ps[r] = -INFINITY;
-                    pi[r] = -1;
-                }
-            }
-            if (tid == 0) {
-                atomicAdd(&a.counters[CNT_CANDIDATES], (unsigned long long)U);
-                if (a.trace_ucount) a.trace_ucount[pair] = U;
+// Per pair: the k best keys of its list (score descending, position
+// ascending, which follows corpus id inside a cluster) by bitonic sort in
+// shared memory.  One block per pair.
+__global__ void __launch_bounds__(256) topk_kernel(const uint64_t* __restrict__ pbuf, int T_cap,
+                                                   const int32_t* __restrict__ ucount,
+                                                   const int32_t* __restrict__ route,
+                                                   const int64_t* __restrict__ cl_off,
+                                                   const int64_t* __restrict__ orig_id, int k,
+                                                   float* __restrict__ pscore, int64_t* __restrict__ pid,
+                                                   int32_t* __restrict__ trace_ucount) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t* key = reinterpret_cast<uint64_t*>(smem);
+    const int64_t pair = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int U = ucount[pair];
+    const int SP = U > 1 ? next_pow2_dev(U) : 1;
+    const uint64_t* src = pbuf + pair * T_cap;
+    for (int u = tid; u < SP; u += blockDim.x) key[u] = (u < U) ? src[u] : ~0ull;
+    __syncthreads();
+    for (int size = 2; size <= SP; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = tid; i < SP / 2; i += blockDim.x) {
+                const int lo_i = 2 * stride * (i / stride) + (i % stride);
+                const int hi_i = lo_i + stride;
+                const bool up = (lo_i & size) == 0;
+                const uint64_t x0 = key[lo_i], x1 = key[hi_i];
+                if ((x0 > x1) == up) { key[lo_i] = x1; key[hi_i] = x0; }
             }
             __syncthreads();
         }
     }
+    const int64_t base = cl_off[route[pair]];
+    float* ps = pscore + pair * k;
+    int64_t* pi = pid + pair * k;
+    for (int r = tid; r < k; r += blockDim.x) {
+        if (r < U) {
+            const uint64_t kv = key[r];
+            ps[r] = float_from_order(~(uint32_t)(kv >> 32));
+            pi[r] = orig_id[base + (int64_t)(uint32_t)kv];
+        } else {
+            ps[r] = -INFINITY;
+            pi[r] = -1;
+        }
+    }
+    if (tid == 0 && trace_ucount) trace_ucount[pair] = U;
 }
 
 // ------------------------------------------------------------------ merge --
@@ -413,12 +470,14 @@ struct Workspace {
     int32_t* wlen;
     float* pscore;
     int64_t* pid;
+    uint64_t* pbuf;
+    int32_t* ucount;
     size_t zero_bytes;   // counters + cnt, cleared at the start of a search
     size_t total;
 };
 
 // Carve one allocation into the search buffers (base == nullptr: sizes only).
-Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, int k) {
+Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, int k, int R) {
     Workspace w{};
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -442,6 +501,8 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, int k
     w.wlen = (int32_t*)take((size_t)np * g.L * 4);
     w.pscore = (float*)take((size_t)np * k * 4);
     w.pid = (int64_t*)take((size_t)np * k * 8);
+    w.pbuf = (uint64_t*)take((size_t)np * g.L * R * 8);
+    w.ucount = (int32_t*)take((size_t)np * 4);
     w.total = o;
     return w;
 }
@@ -494,9 +555,10 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
     LIDER_LAUNCH_CHECK("topc_kernel");
     // 3. group
     if ((rc = mark(LIDER_PHASE_GROUP))) return rc;
+    const int G = std::max(1, std::min(kMaxGroup, (96 * 1024) / (g.d * 4)));
     group_count_kernel<<<(unsigned)cdiv(np, 256), 256, 0, st>>>(w.route, np, w.cnt);
     LIDER_LAUNCH_CHECK("group_count_kernel");
-    group_scan_kernel<<<1, 1024, 0, st>>>(w.cnt, g.ncl, w.off, w.cursor, w.item_off);
+    group_scan_kernel<<<1, 1024, 0, st>>>(w.cnt, g.ncl, G, w.off, w.cursor, w.item_off);
     LIDER_LAUNCH_CHECK("group_scan_kernel");
     group_fill_kernel<<<(unsigned)cdiv(np, 256), 256, 0, st>>>(w.route, np, w.cursor, w.pairs);
     LIDER_LAUNCH_CHECK("group_fill_kernel");
@@ -506,36 +568,37 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         g, np, c, R, w.route, w.qkeys, w.wstart, w.wlen, tr ? tr->pstar : nullptr, tr ? tr->wstart : nullptr,
         tr ? tr->wlen : nullptr, w.counters);
     LIDER_LAUNCH_CHECK("locate_kernel");
-    // 5. gather + score + per-pair top-k
+    // 5. candidate union + exact scores, then per-pair top-k
     if ((rc = mark(LIDER_PHASE_SCORE))) return rc;
     ScoreArgs sa;
     sa.g = g;
     sa.Q = Q;
     sa.c = c;
-    sa.k = k;
-    sa.max_lr = g.L * R;
-    sa.sort_cap = next_pow2(sa.max_lr);
-    sa.ht_size = 2 * sa.sort_cap;
+    sa.G = G;
+    sa.T_cap = g.L * R;
     sa.off = w.off;
     sa.cnt = w.cnt;
     sa.item_off = w.item_off;
     sa.pairs = w.pairs;
+    sa.route = w.route;
     sa.wstart = w.wstart;
     sa.wlen = w.wlen;
-    sa.pscore = w.pscore;
-    sa.pid = w.pid;
-    sa.trace_ucount = tr ? tr->ucount : nullptr;
+    sa.pbuf = w.pbuf;
+    sa.ucount = w.ucount;
     sa.counters = w.counters;
-    const size_t smem = align_up((size_t)g.d * 4 + (size_t)(sa.ht_size + sa.max_lr) * 4, 16) +
-                        (size_t)sa.sort_cap * 8;
-    LIDER_CUDA_TRY(cudaFuncSetAttribute(score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem = (size_t)G * g.d * 4 + (size_t)(kTile / 2) * 4;
+    LIDER_CUDA_TRY(cudaFuncSetAttribute(score_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    LIDER_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, score_kernel, kScoreThreads, smem));
+    LIDER_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, score_group_kernel, kScoreThreads, smem));
     if (per_sm < 1) return fail(LIDER_ELIMIT, "lider_search: score kernel does not fit on an SM");
-    const int64_t max_items = cdiv(np, kGroup) + g.ncl;
+    const int64_t max_items = cdiv(np, G) + g.ncl;
     const int grid = (int)std::min<int64_t>(max_items, (int64_t)per_sm * ix->num_sms);
-    score_kernel<<<grid, kScoreThreads, smem, st>>>(sa);
-    LIDER_LAUNCH_CHECK("score_kernel");
+    score_group_kernel<<<grid, kScoreThreads, smem, st>>>(sa);
+    LIDER_LAUNCH_CHECK("score_group_kernel");
+    const size_t tk_smem = (size_t)next_pow2(sa.T_cap) * 8;
+    topk_kernel<<<(unsigned)np, 256, tk_smem, st>>>(w.pbuf, sa.T_cap, w.ucount, w.route, g.cl_off, g.orig_id, k,
+                                                    w.pscore, w.pid, tr ? tr->ucount : nullptr);
+    LIDER_LAUNCH_CHECK("topk_kernel");
     // 6. merge
     if ((rc = mark(LIDER_PHASE_MERGE))) return rc;
     merge_kernel<<<(unsigned)cdiv(nq * 32, 256), 256, 0, st>>>(w.pscore, w.pid, nq, c, k, out_ids, out_scores);
@@ -577,10 +640,10 @@ int search_entry(const lider_index* ix, const float* Q, int64_t nq, int k, int c
     if (stats) *stats = lider_search_stats{};
     if (nq == 0) return LIDER_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    Workspace sz = carve(nullptr, ix->g, nq, c, k);
+    Workspace sz = carve(nullptr, ix->g, nq, c, k, ix->params.r0 * k);
     void* mem = nullptr;
     if ((rc = pool_alloc(ix, &mem, sz.total, st))) return rc;
-    Workspace w = carve((unsigned char*)mem, ix->g, nq, c, k);
+    Workspace w = carve((unsigned char*)mem, ix->g, nq, c, k, ix->params.r0 * k);
     rc = enqueue_search(ix, Q, nq, k, c, out_ids, out_scores, tr, w, st);
     if (rc == LIDER_OK && stats) rc = read_stats(w, nq, c, stats, st);
     cudaError_t e = cudaFreeAsync(mem, st);
@@ -597,7 +660,7 @@ int search_host_entry(const lider_index* ix, const float* Qh, int64_t nq, int k,
     cudaStream_t st = (cudaStream_t)stream;
     const size_t qb = (size_t)nq * ix->g.d * 4, ib = (size_t)nq * k * 8, sb = (size_t)nq * k * 4;
     const size_t o_ids = align_up(qb, 256), o_sc = align_up(o_ids + ib, 256);
-    Workspace sz = carve(nullptr, ix->g, nq, c, k);
+    Workspace sz = carve(nullptr, ix->g, nq, c, k, ix->params.r0 * k);
     const size_t o_ws = align_up(o_sc + sb, 256);
     void* mem = nullptr;
     if ((rc = pool_alloc(ix, &mem, o_ws + sz.total, st))) return rc;
@@ -605,7 +668,7 @@ int search_host_entry(const lider_index* ix, const float* Qh, int64_t nq, int k,
     float* Qd = (float*)m;
     int64_t* idd = (int64_t*)(m + o_ids);
     float* scd = (float*)(m + o_sc);
-    Workspace w = carve(m + o_ws, ix->g, nq, c, k);
+    Workspace w = carve(m + o_ws, ix->g, nq, c, k, ix->params.r0 * k);
     cudaError_t e = cudaMemcpyAsync(Qd, Qh, qb, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync(queries)");
     if (!rc) rc = enqueue_search(ix, Qd, nq, k, c, idd, scd, nullptr, w, st);
