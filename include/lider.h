@@ -166,6 +166,27 @@ int lider_search_host(const lider_index* index, const float* queries_host, int64
                       int32_t k, int32_t c, int64_t* ids_host, float* scores_host,
                       lider_search_stats* stats, void* stream);
 
+/* Bytes of the fixed device scratch used by lider_search_noalloc. */
+#define LIDER_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/* lider_search without any device allocation (the paper has no counterpart:
+ * this serves callers that cannot allocate device memory while they search,
+ * e.g. a service that reserved its whole GPU budget up front, or code running
+ * while another framework owns the CUDA allocator).
+ * Same arguments, results and errors as lider_search, except:
+ *   - scratch is one fixed device array of LIDER_NOALLOC_SCRATCH_BYTES that
+ *     every GPU loading this library holds until the process exits; a batch
+ *     whose scratch would not fit is rejected with LIDER_ELIMIT (search fewer
+ *     queries per call; the need grows with nq * c * L * r0 * k);
+ *   - the first call on a device looks up the array's device address; make it
+ *     before any stream capture;
+ *   - all calls share the array: calls that overlap on the GPU race and must
+ *     be serialised by the caller.
+ * No cudaMalloc, cudaFree or allocating library routine is called. */
+int lider_search_noalloc(const lider_index* index, const float* queries, int64_t nq,
+                         int32_t k, int32_t c, int64_t* out_ids, float* out_scores,
+                         lider_search_stats* stats, void* stream);
+
 /* Index shape, host outputs (any may be NULL). */
 int lider_index_info(const lider_index* index, int64_t* n, int32_t* d,
                      int32_t* n_clusters, lider_params* params);

@@ -684,3 +684,82 @@ int search_host_entry(const lider_index* ix, const float* Qh, int64_t nq, int k,
 }
 
 }  // namespace lider
+
+// ---------------------------------------------------------------------------
+// Search without any device allocation.
+//
+// Some callers cannot allocate device memory when they search: a service that
+// reserves all of its GPU memory up front and must not grow its footprint
+// afterwards, code that runs while another framework owns the CUDA allocator,
+// or a latency-critical thread where cudaMalloc (or a pool that may need to
+// grow) could block or fail under memory pressure.  lider_search_noalloc runs
+// the same kernels as lider_search, but its scratch lives in the fixed device
+// array below instead of coming from the index's pool.
+//
+// The array is LIDER_NOALLOC_SCRATCH_BYTES long.  Every GPU on which this
+// library's device code is loaded holds it until the process exits.  In host
+// code `lider_noalloc_scratch` only names a host-side stand-in, so its device
+// address is looked up once per device (cudaGetSymbolAddress, with that device
+// current) on the first call there; make that first call before any stream
+// capture.  All calls share the array: calls whose work overlaps on the GPU
+// (other streams, or other host threads) race on it and must be serialised by
+// the caller.  The array keeps the last call's contents; every search clears
+// its counters before use and writes every other scratch word before reading.
+static __device__ __align__(256) unsigned char lider_noalloc_scratch[LIDER_NOALLOC_SCRATCH_BYTES];
+
+namespace lider {
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned char* g_noalloc_base[kMaxDevices] = {};
+
+// Device address of the static scratch on the current device `dev`.
+int noalloc_scratch(int dev, unsigned char** out) {
+    if (dev < 0 || dev >= kMaxDevices) return fail(LIDER_ELIMIT, "lider_search_noalloc: device ordinal too large");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_base[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, lider_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(lider_noalloc_scratch)");
+        if (!p) return fail(LIDER_ECUDA, "lider_search_noalloc: scratch symbol has no device address");
+        g_noalloc_base[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_noalloc_base[dev];
+    return LIDER_OK;
+}
+
+int search_noalloc_impl(const lider_index* ix, const float* Q, int64_t nq, int k, int c, int64_t* out_ids,
+                        float* out_scores, lider_search_stats* stats, void* stream) {
+    int rc = check_search_args(ix, Q, nq, k, c, out_ids, out_scores);
+    if (rc) return rc;
+    if (stats) *stats = lider_search_stats{};
+    if (nq == 0) return LIDER_OK;
+    const int R = ix->params.r0 * k;
+    const Workspace need = carve(nullptr, ix->g, nq, c, k, R);
+    if (need.total > (size_t)LIDER_NOALLOC_SCRATCH_BYTES)
+        return fail(LIDER_ELIMIT, "lider_search_noalloc: this batch needs " + std::to_string(need.total) +
+                                      " bytes of scratch, more than the fixed LIDER_NOALLOC_SCRATCH_BYTES (" +
+                                      std::to_string((size_t)LIDER_NOALLOC_SCRATCH_BYTES) +
+                                      "); search fewer queries per call");
+    unsigned char* base = nullptr;
+    if ((rc = noalloc_scratch(ix->device, &base))) return rc;
+    const Workspace w = carve(base, ix->g, nq, c, k, R);
+    cudaStream_t st = (cudaStream_t)stream;
+    rc = enqueue_search(ix, Q, nq, k, c, out_ids, out_scores, nullptr, w, st);
+    if (rc == LIDER_OK && stats) rc = read_stats(w, nq, c, stats, st);
+    return rc;
+}
+
+}  // namespace
+}  // namespace lider
+
+extern "C" int lider_search_noalloc(const lider_index* index, const float* queries, int64_t nq, int32_t k,
+                                    int32_t c, int64_t* out_ids, float* out_scores, lider_search_stats* stats,
+                                    void* stream) {
+    try {
+        return lider::search_noalloc_impl(index, queries, nq, k, c, out_ids, out_scores, stats, stream);
+    } catch (...) {
+        return lider::fail(LIDER_ECUDA, "lider_search_noalloc: internal error");
+    }
+}

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "liblider.so")
 LIDER_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ELIMIT"}
 MAX_L, MAX_C, MAX_K, MAX_LR, MAX_D = 32, 32, 1024, 4096, 4096
+NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
 class LiderError(RuntimeError):
@@ -63,6 +64,7 @@ def _load():
         "lider_search_trace": ([P, P, I64, I32, I32, P, P, ctypes.POINTER(Trace), ctypes.POINTER(Stats), P],
                                ctypes.c_int),
         "lider_search_host": ([P, P, I64, I32, I32, P, P, ctypes.POINTER(Stats), P], ctypes.c_int),
+        "lider_search_noalloc": ([P, P, I64, I32, I32, P, P, ctypes.POINTER(Stats), P], ctypes.c_int),
         "lider_index_info": ([P, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I32),
                               ctypes.POINTER(Params)], ctypes.c_int),
         "lider_cluster_offsets": ([P, P], ctypes.c_int),
@@ -83,6 +85,7 @@ _lib = _load()
 
 def exported_symbols() -> list[str]:
     return [n for n in ("lider_build", "lider_search", "lider_search_trace", "lider_search_host",
+                        "lider_search_noalloc",
                         "lider_index_info", "lider_cluster_offsets", "lider_export_array",
                         "lider_export_rmi", "lider_free", "lider_last_error") if hasattr(_lib, n)]
 
