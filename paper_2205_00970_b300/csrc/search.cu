@@ -16,8 +16,8 @@
 //               one cluster) at a time: union of each pair's L windows as
 //               bits of a shared-memory position mask, the marked rows
 //               streamed once and scored by exact FP32 inner products with
-//               every query that marked them; topk_kernel: per-pair top-k
-//               by bitonic sort in shared memory
+//               every query that marked them, then each pair's top-k by
+//               bucket selection and bitonic sort in shared memory
 //   6. merge    merge_kernel, one warp per query: k-way merge of its c lists
 //               (Sec. 6.2, heap of list heads)
 #include <algorithm>
@@ -214,8 +214,11 @@ __global__ void locate_kernel(Geometry g, int64_t npairs, int c, int R,
 // (cluster-local position, pair) in a shared-memory mask, so duplicates
 // across arrays collapse for free.  The cluster's rows are then streamed
 // once per item: every marked row is loaded by one warp and dotted with each
-// query whose bit is set.  A row shared by several queries of the item is
-// read once instead of once per query.
+// query whose bit is set, so a row shared by several queries of the item is
+// read once.  Each pair's (score, position) keys go to its list in global
+// scratch; after the item, the block selects each pair's top k (Sec. 6.1:
+// the k best of the verified candidates) by bucket selection and a small
+// bitonic sort in shared memory.
 //
 // Score of (q, row): lane l accumulates x[i]*q[i] for float4 chunks
 // i = l, l+32, ... in ascending order with FMA, then a butterfly sum over the
@@ -224,39 +227,254 @@ __global__ void locate_kernel(Geometry g, int64_t npairs, int c, int R,
 struct ScoreArgs {
     Geometry g;
     const float* Q;
-    int c, G, T_cap;            // T_cap = L * R, capacity of one pair's score list
+    int c, G, k, T_cap;         // T_cap = L * R, capacity of one pair's score list
+    int region_bytes;           // dynamic shared memory before the mask
     const int32_t* off;
     const int32_t* cnt;
     const int32_t* item_off;
     const int32_t* pairs;
-    const int32_t* route;
     const int32_t* wstart;
-    const int32_t* wlen;
     uint64_t* pbuf;             // npairs x T_cap keys: (~order(score) << 32) | position
-    int32_t* ucount;            // npairs
+    float* pscore;              // npairs x k, best first
+    int64_t* pid;               // npairs x k corpus ids
+    int32_t* trace_ucount;
     unsigned long long* counters;
 };
 
 constexpr int kMaxGroup = 16;    // bits of a position's mask
 constexpr int kTile = 8192;      // positions per mask tile
-constexpr int kNV = 8;           // float4 per lane per row chunk (1024 columns)
+constexpr int kChunkNV = 8;      // general path: float4 per lane per row chunk
+constexpr int kBins = 256;       // buckets of the top-k selection
+constexpr int kCandCap = 1024;   // keys sorted after bucket selection
 
-__device__ __forceinline__ float warp_sum(float v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+__device__ __forceinline__ uint32_t mask_bits(const uint32_t* mask, int pl) {
+    return (mask[pl >> 1] >> (16 * (pl & 1))) & 0xffffu;
 }
 
-// Dynamic shared memory: queries G x d floats | mask kTile/2 u32 (16 bits per position).
+__device__ __forceinline__ uint64_t score_key(float sc, uint32_t pos) {
+    return ((uint64_t)(~float_order(sc)) << 32) | (uint64_t)pos;
+}
+
+// Block-wide ascending bitonic sort of n (a power of two) keys in shared memory.
+__device__ void block_bitonic(uint64_t* key, int n) {
+    for (int size = 2; size <= n; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < n / 2; i += blockDim.x) {
+                const int lo_i = 2 * stride * (i / stride) + (i % stride);
+                const int hi_i = lo_i + stride;
+                const bool up = (lo_i & size) == 0;
+                const uint64_t x0 = key[lo_i], x1 = key[hi_i];
+                if ((x0 > x1) == up) { key[lo_i] = x1; key[hi_i] = x0; }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// The k smallest of U distinct keys at src (global), written best first to
+// (ps, pi) with padding.  K: shared buffer of next_pow2(T_cap) keys; cand:
+// kCandCap keys.  Bucket selection on the 32-bit score order finds the bucket
+// holding the k-th key; only the keys up to that bucket are sorted.
+__device__ void block_topk(const uint64_t* __restrict__ src, int U, int k, uint64_t* K, uint64_t* cand,
+                           uint32_t* bins, uint32_t* scal, int64_t base, const int64_t* __restrict__ orig_id,
+                           float* __restrict__ ps, int64_t* __restrict__ pi) {
+    const int tid = threadIdx.x;
+    const int kk = min(k, U);
+    uint64_t* out = cand;
+    if (U <= kCandCap) {
+        const int SP = U > 1 ? next_pow2_dev(U) : 1;
+        for (int u = tid; u < SP; u += blockDim.x) cand[u] = (u < U) ? src[u] : ~0ull;
+        __syncthreads();
+        block_bitonic(cand, SP);
+    } else {
+        if (tid == 0) { scal[0] = 0xffffffffu; scal[1] = 0u; scal[2] = 0u; }
+        for (int b = tid; b < kBins; b += blockDim.x) bins[b] = 0u;
+        __syncthreads();
+        uint32_t lo = 0xffffffffu, hi = 0u;
+        for (int u = tid; u < U; u += blockDim.x) {
+            const uint64_t v = src[u];
+            K[u] = v;
+            const uint32_t h = (uint32_t)(v >> 32);
+            lo = min(lo, h);
+            hi = max(hi, h);
+        }
+        atomicMin(&scal[0], lo);
+        atomicMax(&scal[1], hi);
+        __syncthreads();
+        lo = scal[0];
+        const uint64_t span = (uint64_t)(scal[1] - lo) + 1;
+        for (int u = tid; u < U; u += blockDim.x) {
+            const uint32_t h = (uint32_t)(K[u] >> 32);
+            atomicAdd(&bins[(uint32_t)(((uint64_t)(h - lo) * kBins) / span)], 1u);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t cum = 0;
+            int bsel = kBins - 1;
+            for (int b = 0; b < kBins; ++b) {
+                cum += bins[b];
+                if (cum >= (uint32_t)kk) { bsel = b; break; }
+            }
+            scal[2] = (uint32_t)bsel;
+            scal[3] = cum;
+            scal[4] = 0u;
+        }
+        __syncthreads();
+        const uint32_t bsel = scal[2], sel = scal[3];
+        if (sel <= (uint32_t)kCandCap) {
+            for (int u = tid; u < U; u += blockDim.x) {
+                const uint64_t v = K[u];
+                const uint32_t bb = (uint32_t)(((uint64_t)((uint32_t)(v >> 32) - lo) * kBins) / span);
+                if (bb <= bsel) cand[atomicAdd(&scal[4], 1u)] = v;
+            }
+            __syncthreads();
+            const int SP = sel > 1 ? next_pow2_dev((int)sel) : 1;
+            for (int u = (int)sel + tid; u < SP; u += blockDim.x) cand[u] = ~0ull;
+            __syncthreads();
+            block_bitonic(cand, SP);
+        } else {                                    // many equal scores: sort everything
+            const int SP = next_pow2_dev(U);
+            for (int u = U + tid; u < SP; u += blockDim.x) K[u] = ~0ull;
+            __syncthreads();
+            block_bitonic(K, SP);
+            out = K;
+        }
+    }
+    for (int r = tid; r < k; r += blockDim.x) {
+        if (r < kk) {
+            const uint64_t kv = out[r];
+            ps[r] = float_from_order(~(uint32_t)(kv >> 32));
+            pi[r] = orig_id[base + (int64_t)(uint32_t)kv];
+        } else {
+            ps[r] = -INFINITY;
+            pi[r] = -1;
+        }
+    }
+    __syncthreads();
+}
+
+// Score the marked rows of one tile.  NV > 0: d == 128 * NV, a row is NV
+// float4 per lane held in registers and the set bits are visited two at a
+// time with one shared butterfly; NV == 0: any d, chunks of kChunkNV float4
+// with bounds checks.
+template <int NV>
+__device__ __forceinline__ void score_tile(const ScoreArgs& a, const float4* Qs4, const uint32_t* mask, int tl,
+                                           int64_t base, int64_t t0, int* s_cnt, const int64_t* s_pair) {
+    const Geometry& g = a.g;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int nwarps = kScoreThreads / 32;
+    const int d4 = g.d / 4;
+    for (int pl = warp; pl < tl; pl += nwarps) {
+        uint32_t m = mask_bits(mask, pl);
+        if (m == 0u) continue;
+        const uint32_t pos = (uint32_t)(t0 + pl);
+        const float4* X4 = reinterpret_cast<const float4*>(g.X + (base + pos) * (int64_t)g.d);
+        if constexpr (NV > 0) {
+            float4 x[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) x[v] = __ldg(X4 + lane + 32 * v);
+            while (m) {
+                const int qa = __ffs(m) - 1;
+                m &= m - 1;
+                int qb = -1;
+                if (m) {
+                    qb = __ffs(m) - 1;
+                    m &= m - 1;
+                }
+                float aa = 0.f, ab = 0.f;
+                const float4* ya = Qs4 + qa * d4 + lane;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const float4 y = ya[32 * v];
+                    aa = fmaf(x[v].x, y.x, aa);
+                    aa = fmaf(x[v].y, y.y, aa);
+                    aa = fmaf(x[v].z, y.z, aa);
+                    aa = fmaf(x[v].w, y.w, aa);
+                }
+                if (qb >= 0) {
+                    const float4* yb = Qs4 + qb * d4 + lane;
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        const float4 y = yb[32 * v];
+                        ab = fmaf(x[v].x, y.x, ab);
+                        ab = fmaf(x[v].y, y.y, ab);
+                        ab = fmaf(x[v].z, y.z, ab);
+                        ab = fmaf(x[v].w, y.w, ab);
+                    }
+                }
+                // butterfly for two dots at once: lanes 0-15 finish qa, 16-31 qb
+                const bool upper = (lane & 16) != 0;
+                float keep = upper ? ab : aa;
+                const float send = upper ? aa : ab;
+                keep += __shfl_xor_sync(0xffffffffu, send, 16);
+                for (int o = 8; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+                if (lane == 0) {
+                    const int slot = atomicAdd(&s_cnt[qa], 1);
+                    a.pbuf[s_pair[qa] * a.T_cap + slot] = score_key(keep, pos);
+                } else if (lane == 16 && qb >= 0) {
+                    const int slot = atomicAdd(&s_cnt[qb], 1);
+                    a.pbuf[s_pair[qb] * a.T_cap + slot] = score_key(keep, pos);
+                }
+            }
+        } else {
+            float part[kMaxGroup];
+#pragma unroll
+            for (int q = 0; q < kMaxGroup; ++q) part[q] = 0.f;
+            for (int c0 = 0; c0 < d4; c0 += 32 * kChunkNV) {
+                float4 x[kChunkNV];
+#pragma unroll
+                for (int v = 0; v < kChunkNV; ++v) {
+                    const int i4 = c0 + lane + 32 * v;
+                    x[v] = (i4 < d4) ? __ldg(X4 + i4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int q = 0; q < kMaxGroup; ++q) {
+                    if (!((m >> q) & 1u)) continue;
+                    float acc = part[q];
+#pragma unroll
+                    for (int v = 0; v < kChunkNV; ++v) {
+                        const int i4 = c0 + lane + 32 * v;
+                        if (i4 < d4) {
+                            const float4 y = Qs4[q * d4 + i4];
+                            acc = fmaf(x[v].x, y.x, acc);
+                            acc = fmaf(x[v].y, y.y, acc);
+                            acc = fmaf(x[v].z, y.z, acc);
+                            acc = fmaf(x[v].w, y.w, acc);
+                        }
+                    }
+                    part[q] = acc;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kMaxGroup; ++q) {
+                if (!((m >> q) & 1u)) continue;
+                float sc = part[q];
+                for (int o = 16; o > 0; o >>= 1) sc += __shfl_xor_sync(0xffffffffu, sc, o);
+                if (lane == 0) {
+                    const int slot = atomicAdd(&s_cnt[q], 1);
+                    a.pbuf[s_pair[q] * a.T_cap + slot] = score_key(sc, pos);
+                }
+            }
+        }
+    }
+}
+
+// Dynamic shared memory: region of region_bytes (queries G x d floats while
+// scoring, then the top-k buffers) | mask kTile/2 u32 (16 bits per position).
+template <int NV>
 __global__ void __launch_bounds__(kScoreThreads) score_group_kernel(ScoreArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const Geometry& g = a.g;
     float* Qs = reinterpret_cast<float*>(smem);
-    uint32_t* mask = reinterpret_cast<uint32_t*>(smem + (size_t)a.G * g.d * 4);
+    uint32_t* mask = reinterpret_cast<uint32_t*>(smem + a.region_bytes);
+    uint64_t* K = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* cand = K + next_pow2_dev(a.T_cap);
     __shared__ int s_item;
     __shared__ int s_cnt[kMaxGroup];
     __shared__ int64_t s_pair[kMaxGroup];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int nwarps = kScoreThreads / 32;
+    __shared__ uint32_t s_bins[kBins];
+    __shared__ uint32_t s_scal[8];
+    const int tid = threadIdx.x;
     const int total_items = a.item_off[g.ncl];
     const int d4 = g.d / 4;
     const float4* Qs4 = reinterpret_cast<const float4*>(Qs);
@@ -306,106 +524,22 @@ __global__ void __launch_bounds__(kScoreThreads) score_group_kernel(ScoreArgs a)
                     atomicOr(&mask[pl >> 1], (1u << gq) << (16 * (int)(pl & 1)));
             }
             __syncthreads();
-            // stream the marked rows of the tile
-            for (int pl = warp; pl < tl; pl += nwarps) {
-                const uint32_t m = (mask[pl >> 1] >> (16 * (pl & 1))) & 0xffffu;
-                if (m == 0u) continue;
-                const int64_t row = base + t0 + pl;
-                const float4* X4 = reinterpret_cast<const float4*>(g.X + row * (int64_t)g.d);
-                float part[kMaxGroup];
-#pragma unroll
-                for (int q = 0; q < kMaxGroup; ++q) part[q] = 0.f;
-                for (int c0 = 0; c0 < d4; c0 += 32 * kNV) {
-                    float4 x[kNV];
-#pragma unroll
-                    for (int v = 0; v < kNV; ++v) {
-                        const int i4 = c0 + lane + 32 * v;
-                        x[v] = (i4 < d4) ? __ldg(X4 + i4) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
-#pragma unroll
-                    for (int q = 0; q < kMaxGroup; ++q) {
-                        if (!((m >> q) & 1u)) continue;
-                        float acc = part[q];
-#pragma unroll
-                        for (int v = 0; v < kNV; ++v) {
-                            const int i4 = c0 + lane + 32 * v;
-                            if (i4 < d4) {
-                                const float4 y = Qs4[q * d4 + i4];
-                                acc = fmaf(x[v].x, y.x, acc);
-                                acc = fmaf(x[v].y, y.y, acc);
-                                acc = fmaf(x[v].z, y.z, acc);
-                                acc = fmaf(x[v].w, y.w, acc);
-                            }
-                        }
-                        part[q] = acc;
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < kMaxGroup; ++q) {
-                    if (!((m >> q) & 1u)) continue;
-                    const float sc = warp_sum(part[q]);
-                    if (lane == 0) {
-                        const int slot = atomicAdd(&s_cnt[q], 1);
-                        a.pbuf[s_pair[q] * a.T_cap + slot] =
-                            ((uint64_t)(~float_order(sc)) << 32) | (uint64_t)(uint32_t)(t0 + pl);
-                    }
-                }
-            }
+            score_tile<NV>(a, Qs4, mask, tl, base, t0, s_cnt, s_pair);
             __syncthreads();
         }
+        // per-pair top-k (the query rows in shared memory are no longer needed)
+        for (int gq = 0; gq < count; ++gq) {
+            const int64_t pair = s_pair[gq];
+            const int U = s_cnt[gq];
+            block_topk(a.pbuf + pair * a.T_cap, U, a.k, K, cand, s_bins, s_scal, base, g.orig_id,
+                       a.pscore + pair * a.k, a.pid + pair * a.k);
+        }
         if (tid < count) {
-            a.ucount[s_pair[tid]] = s_cnt[tid];
             atomicAdd(&a.counters[CNT_CANDIDATES], (unsigned long long)s_cnt[tid]);
+            if (a.trace_ucount) a.trace_ucount[s_pair[tid]] = s_cnt[tid];
         }
         __syncthreads();
     }
-}
-
-// Per pair: the k best keys of its list (score descending, position
-// ascending, which follows corpus id inside a cluster) by bitonic sort in
-// shared memory.  One block per pair.
-__global__ void __launch_bounds__(256) topk_kernel(const uint64_t* __restrict__ pbuf, int T_cap,
-                                                   const int32_t* __restrict__ ucount,
-                                                   const int32_t* __restrict__ route,
-                                                   const int64_t* __restrict__ cl_off,
-                                                   const int64_t* __restrict__ orig_id, int k,
-                                                   float* __restrict__ pscore, int64_t* __restrict__ pid,
-                                                   int32_t* __restrict__ trace_ucount) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t* key = reinterpret_cast<uint64_t*>(smem);
-    const int64_t pair = blockIdx.x;
-    const int tid = threadIdx.x;
-    const int U = ucount[pair];
-    const int SP = U > 1 ? next_pow2_dev(U) : 1;
-    const uint64_t* src = pbuf + pair * T_cap;
-    for (int u = tid; u < SP; u += blockDim.x) key[u] = (u < U) ? src[u] : ~0ull;
-    __syncthreads();
-    for (int size = 2; size <= SP; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = tid; i < SP / 2; i += blockDim.x) {
-                const int lo_i = 2 * stride * (i / stride) + (i % stride);
-                const int hi_i = lo_i + stride;
-                const bool up = (lo_i & size) == 0;
-                const uint64_t x0 = key[lo_i], x1 = key[hi_i];
-                if ((x0 > x1) == up) { key[lo_i] = x1; key[hi_i] = x0; }
-            }
-            __syncthreads();
-        }
-    }
-    const int64_t base = cl_off[route[pair]];
-    float* ps = pscore + pair * k;
-    int64_t* pi = pid + pair * k;
-    for (int r = tid; r < k; r += blockDim.x) {
-        if (r < U) {
-            const uint64_t kv = key[r];
-            ps[r] = float_from_order(~(uint32_t)(kv >> 32));
-            pi[r] = orig_id[base + (int64_t)(uint32_t)kv];
-        } else {
-            ps[r] = -INFINITY;
-            pi[r] = -1;
-        }
-    }
-    if (tid == 0 && trace_ucount) trace_ucount[pair] = U;
 }
 
 // ------------------------------------------------------------------ merge --
@@ -471,7 +605,6 @@ struct Workspace {
     float* pscore;
     int64_t* pid;
     uint64_t* pbuf;
-    int32_t* ucount;
     size_t zero_bytes;   // counters + cnt, cleared at the start of a search
     size_t total;
 };
@@ -502,7 +635,6 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, int k
     w.pscore = (float*)take((size_t)np * k * 4);
     w.pid = (int64_t*)take((size_t)np * k * 8);
     w.pbuf = (uint64_t*)take((size_t)np * g.L * R * 8);
-    w.ucount = (int32_t*)take((size_t)np * 4);
     w.total = o;
     return w;
 }
@@ -568,37 +700,48 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         g, np, c, R, w.route, w.qkeys, w.wstart, w.wlen, tr ? tr->pstar : nullptr, tr ? tr->wstart : nullptr,
         tr ? tr->wlen : nullptr, w.counters);
     LIDER_LAUNCH_CHECK("locate_kernel");
-    // 5. candidate union + exact scores, then per-pair top-k
+    // 5. candidate union, exact scores and per-pair top-k
     if ((rc = mark(LIDER_PHASE_SCORE))) return rc;
     ScoreArgs sa;
     sa.g = g;
     sa.Q = Q;
     sa.c = c;
     sa.G = G;
+    sa.k = k;
     sa.T_cap = g.L * R;
+    sa.region_bytes = (int)align_up(std::max((size_t)G * g.d * 4,
+                                             ((size_t)next_pow2(sa.T_cap) + kCandCap) * 8), 16);
     sa.off = w.off;
     sa.cnt = w.cnt;
     sa.item_off = w.item_off;
     sa.pairs = w.pairs;
-    sa.route = w.route;
     sa.wstart = w.wstart;
-    sa.wlen = w.wlen;
     sa.pbuf = w.pbuf;
-    sa.ucount = w.ucount;
+    sa.pscore = w.pscore;
+    sa.pid = w.pid;
+    sa.trace_ucount = tr ? tr->ucount : nullptr;
     sa.counters = w.counters;
-    const size_t smem = (size_t)G * g.d * 4 + (size_t)(kTile / 2) * 4;
-    LIDER_CUDA_TRY(cudaFuncSetAttribute(score_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem = (size_t)sa.region_bytes + (size_t)(kTile / 2) * 4;
+    const void* kern = nullptr;
+    switch ((g.d % 128 == 0 && g.d <= 1024) ? g.d / 128 : 0) {
+        case 1: kern = (const void*)score_group_kernel<1>; break;
+        case 2: kern = (const void*)score_group_kernel<2>; break;
+        case 3: kern = (const void*)score_group_kernel<3>; break;
+        case 4: kern = (const void*)score_group_kernel<4>; break;
+        case 5: kern = (const void*)score_group_kernel<5>; break;
+        case 6: kern = (const void*)score_group_kernel<6>; break;
+        case 7: kern = (const void*)score_group_kernel<7>; break;
+        case 8: kern = (const void*)score_group_kernel<8>; break;
+        default: kern = (const void*)score_group_kernel<0>; break;
+    }
+    LIDER_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    LIDER_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, score_group_kernel, kScoreThreads, smem));
+    LIDER_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kScoreThreads, smem));
     if (per_sm < 1) return fail(LIDER_ELIMIT, "lider_search: score kernel does not fit on an SM");
     const int64_t max_items = cdiv(np, G) + g.ncl;
     const int grid = (int)std::min<int64_t>(max_items, (int64_t)per_sm * ix->num_sms);
-    score_group_kernel<<<grid, kScoreThreads, smem, st>>>(sa);
-    LIDER_LAUNCH_CHECK("score_group_kernel");
-    const size_t tk_smem = (size_t)next_pow2(sa.T_cap) * 8;
-    topk_kernel<<<(unsigned)np, 256, tk_smem, st>>>(w.pbuf, sa.T_cap, w.ucount, w.route, g.cl_off, g.orig_id, k,
-                                                    w.pscore, w.pid, tr ? tr->ucount : nullptr);
-    LIDER_LAUNCH_CHECK("topk_kernel");
+    void* kargs[] = {&sa};
+    LIDER_CUDA_TRY(cudaLaunchKernel(kern, dim3(grid), dim3(kScoreThreads), kargs, smem, st));
     // 6. merge
     if ((rc = mark(LIDER_PHASE_MERGE))) return rc;
     merge_kernel<<<(unsigned)cdiv(nq * 32, 256), 256, 0, st>>>(w.pscore, w.pid, nq, c, k, out_ids, out_scores);
