@@ -301,12 +301,18 @@ __device__ void block_topk(const uint64_t* __restrict__ src, int U, int k, uint6
         atomicMin(&scal[0], lo);
         atomicMax(&scal[1], hi);
         __syncthreads();
-        lo = scal[0];
-        const uint64_t span = (uint64_t)(scal[1] - lo) + 1;
-        for (int u = tid; u < U; u += blockDim.x) {
-            const uint32_t h = (uint32_t)(K[u] >> 32);
-            atomicAdd(&bins[(uint32_t)(((uint64_t)(h - lo) * kBins) / span)], 1u);
-        }
+        // buckets linear in the score between the best and the worst key; the
+        // map is monotone (round-to-nearest subtraction and scaling preserve
+        // order), so every key of a better bucket beats every key of a worse one
+        const float s_best = float_from_order(~scal[0]);
+        const float s_worst = float_from_order(~scal[1]);
+        const float span = s_best - s_worst;
+        const float scale = span > 0.f ? (float)kBins / span : 0.f;
+        auto bucket = [&](uint64_t v) -> uint32_t {
+            const float sc = float_from_order(~(uint32_t)(v >> 32));
+            return (uint32_t)fminf(__fmul_rn(__fadd_rn(s_best, -sc), scale), (float)(kBins - 1));
+        };
+        for (int u = tid; u < U; u += blockDim.x) atomicAdd(&bins[bucket(K[u])], 1u);
         __syncthreads();
         if (tid == 0) {
             uint32_t cum = 0;
@@ -324,8 +330,7 @@ __device__ void block_topk(const uint64_t* __restrict__ src, int U, int k, uint6
         if (sel <= (uint32_t)kCandCap) {
             for (int u = tid; u < U; u += blockDim.x) {
                 const uint64_t v = K[u];
-                const uint32_t bb = (uint32_t)(((uint64_t)((uint32_t)(v >> 32) - lo) * kBins) / span);
-                if (bb <= bsel) cand[atomicAdd(&scal[4], 1u)] = v;
+                if (bucket(v) <= bsel) cand[atomicAdd(&scal[4], 1u)] = v;
             }
             __syncthreads();
             const int SP = sel > 1 ? next_pow2_dev((int)sel) : 1;
@@ -374,46 +379,50 @@ __device__ __forceinline__ void score_tile(const ScoreArgs& a, const float4* Qs4
 #pragma unroll
             for (int v = 0; v < NV; ++v) x[v] = __ldg(X4 + lane + 32 * v);
             while (m) {
-                const int qa = __ffs(m) - 1;
-                m &= m - 1;
-                int qb = -1;
-                if (m) {
-                    qb = __ffs(m) - 1;
-                    m &= m - 1;
-                }
-                float aa = 0.f, ab = 0.f;
-                const float4* ya = Qs4 + qa * d4 + lane;
+                // up to four set bits at a time: four independent FMA chains
+                int q[4];
 #pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    const float4 y = ya[32 * v];
-                    aa = fmaf(x[v].x, y.x, aa);
-                    aa = fmaf(x[v].y, y.y, aa);
-                    aa = fmaf(x[v].z, y.z, aa);
-                    aa = fmaf(x[v].w, y.w, aa);
-                }
-                if (qb >= 0) {
-                    const float4* yb = Qs4 + qb * d4 + lane;
-#pragma unroll
-                    for (int v = 0; v < NV; ++v) {
-                        const float4 y = yb[32 * v];
-                        ab = fmaf(x[v].x, y.x, ab);
-                        ab = fmaf(x[v].y, y.y, ab);
-                        ab = fmaf(x[v].z, y.z, ab);
-                        ab = fmaf(x[v].w, y.w, ab);
+                for (int s2 = 0; s2 < 4; ++s2) {
+                    if (m) {
+                        q[s2] = __ffs(m) - 1;
+                        m &= m - 1;
+                    } else {
+                        q[s2] = -1;
                     }
                 }
-                // butterfly for two dots at once: lanes 0-15 finish qa, 16-31 qb
-                const bool upper = (lane & 16) != 0;
-                float keep = upper ? ab : aa;
-                const float send = upper ? aa : ab;
-                keep += __shfl_xor_sync(0xffffffffu, send, 16);
-                for (int o = 8; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
-                if (lane == 0) {
-                    const int slot = atomicAdd(&s_cnt[qa], 1);
-                    a.pbuf[s_pair[qa] * a.T_cap + slot] = score_key(keep, pos);
-                } else if (lane == 16 && qb >= 0) {
-                    const int slot = atomicAdd(&s_cnt[qb], 1);
-                    a.pbuf[s_pair[qb] * a.T_cap + slot] = score_key(keep, pos);
+                float acc[4];
+#pragma unroll
+                for (int s2 = 0; s2 < 4; ++s2) {
+                    acc[s2] = 0.f;
+                    const float4* y4 = Qs4 + (q[s2] >= 0 ? q[s2] : q[0]) * d4 + lane;
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        const float4 y = y4[32 * v];
+                        acc[s2] = fmaf(x[v].x, y.x, acc[s2]);
+                        acc[s2] = fmaf(x[v].y, y.y, acc[s2]);
+                        acc[s2] = fmaf(x[v].z, y.z, acc[s2]);
+                        acc[s2] = fmaf(x[v].w, y.w, acc[s2]);
+                    }
+                }
+                // one butterfly for four dots: after the xor-16 and xor-8 halving
+                // steps lanes 0-7 hold dot 0, 8-15 dot 1, 16-23 dot 2, 24-31 dot 3;
+                // every dot gets the same pairing tree as a plain warp sum
+                const bool b16 = (lane & 16) != 0, b8 = (lane & 8) != 0;
+                float k0 = b16 ? acc[2] : acc[0], k1 = b16 ? acc[3] : acc[1];
+                const float s0 = b16 ? acc[0] : acc[2], s1 = b16 ? acc[1] : acc[3];
+                k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+                k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+                float keep = b8 ? k1 : k0;
+                const float send = b8 ? k0 : k1;
+                keep += __shfl_xor_sync(0xffffffffu, send, 8);
+                for (int o = 4; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+                if ((lane & 7) == 0) {
+                    const int grp = lane >> 3;
+                    const int qs = grp == 0 ? q[0] : grp == 1 ? q[1] : grp == 2 ? q[2] : q[3];
+                    if (qs >= 0) {
+                        const int slot = atomicAdd(&s_cnt[qs], 1);
+                        a.pbuf[s_pair[qs] * a.T_cap + slot] = score_key(keep, pos);
+                    }
                 }
             }
         } else {
@@ -512,16 +521,18 @@ __global__ void __launch_bounds__(kScoreThreads) score_group_kernel(ScoreArgs a)
             for (int i = tid; i < (tl + 1) / 2; i += kScoreThreads) mask[i] = 0u;
             __syncthreads();
             // mark the union of the windows of every pair of the item
-            const int per_pair = g.L * T;
-            for (int i = tid; i < count * per_pair; i += kScoreThreads) {
-                const int gq = i / per_pair;
-                const int r = i - gq * per_pair;
-                const int l = r / T, t = r - l * T;
-                const int32_t ws = a.wstart[s_pair[gq] * g.L + l];
-                const int32_t p = g.pos[(int64_t)l * g.n + base + ws + t];
-                const int64_t pl = (int64_t)p - t0;
-                if (pl >= 0 && pl < tl)
-                    atomicOr(&mask[pl >> 1], (1u << gq) << (16 * (int)(pl & 1)));
+            {   // one warp per window, lanes along the window
+                const int warp = tid >> 5, lane = tid & 31;
+                for (int wi = warp; wi < count * g.L; wi += kScoreThreads / 32) {
+                    const int gq = wi / g.L, l = wi - gq * g.L;
+                    const int32_t ws = a.wstart[s_pair[gq] * g.L + l];
+                    const int32_t* P = g.pos + (int64_t)l * g.n + base + ws;
+                    const uint32_t bit = 1u << gq;
+                    for (int t = lane; t < T; t += 32) {
+                        const int64_t pl = (int64_t)P[t] - t0;
+                        if (pl >= 0 && pl < tl) atomicOr(&mask[pl >> 1], bit << (16 * (int)(pl & 1)));
+                    }
+                }
             }
             __syncthreads();
             score_tile<NV>(a, Qs4, mask, tl, base, t0, s_cnt, s_pair);
