@@ -39,6 +39,10 @@ extern "C" {
 
 #define LIDER_HASH_PSTABLE 0   /* h = floor((a.x + b) / W), Sec. 4.1 (p-stable) */
 
+/* How candidates are scored (the results are the same within FP32 rounding). */
+#define LIDER_SCORE_TENSOR 0   /* tcgen05 tensor cores, 3 TF32 products per FP32 product */
+#define LIDER_SCORE_SIMT   1   /* FP32 FMA on the CUDA cores                             */
+
 /* Implementation caps (checked; LIDER_ELIMIT beyond them). */
 #define LIDER_MAX_L        32      /* hashkey arrays per core model (H)     */
 #define LIDER_MAX_C        32      /* clusters probed per query (c_0)       */
@@ -57,7 +61,8 @@ typedef struct lider_index lider_index;   /* opaque; owns its device memory */
  *   B  = elements read by KD_e in the extended hashkey distance dist_e
  *        (Sec. 4.2); floor(64/m) * B must be <= 56;
  *   hash_kind = LIDER_HASH_PSTABLE;
- *   W  = p-stable bucket width (> 0). */
+ *   W  = p-stable bucket width (> 0);
+ *   score_mode = LIDER_SCORE_TENSOR (needs L <= 16) or LIDER_SCORE_SIMT. */
 typedef struct {
     int32_t L;
     int32_t m;
@@ -66,6 +71,8 @@ typedef struct {
     int32_t B;
     int32_t hash_kind;
     double  W;
+    int32_t score_mode;
+    int32_t reserved;
 } lider_params;
 
 /* Counters of one search (host struct, filled when the call returns). */
@@ -210,6 +217,14 @@ int lider_export_array(const lider_index* index, int32_t cluster, int32_t array,
 int lider_export_rmi(const lider_index* index, int32_t cluster, int32_t array,
                      uint64_t* minmax_host, double* root_host, double* leaf_host,
                      int32_t* err_host);
+
+/* Self-test of the tensor-core scoring engine (tcgen05 + TMA + TMEM, three
+ * TF32 products per FP32 product): out[m x n] = A[m x d] . B[n x d]^T for
+ * device row-major FP32 A, B, out with 1 <= m <= 128, 1 <= n <= 256,
+ * d % 4 == 0.  Synchronous; allocates its own scratch.  LIDER_ECUDA if an
+ * internal wait times out (the kernel then exits cleanly). */
+int lider_debug_tc_tile(const float* A, int32_t m, const float* B, int32_t n, int32_t d,
+                        float* out, void* stream);
 
 /* Release the index and its device memory.  NULL is accepted. */
 void lider_free(lider_index* index);

@@ -15,8 +15,6 @@
 
 namespace lider {
 
-int score_kernel_occupancy(int d, int max_lr, int* blocks_per_sm);   // search.cu
-
 namespace {
 
 constexpr int64_t kRowChunk = 131072;   // rows per hashing / assignment pass
@@ -79,6 +77,19 @@ __global__ void gather_rows_kernel(const float* __restrict__ src, const int64_t*
     const float4* s = reinterpret_cast<const float4*>(src + ids[row] * (int64_t)d);
     float4* o = reinterpret_cast<float4*>(dst + row * (int64_t)d);
     for (int i = lane; i < d / 4; i += 32) o[i] = s[i];
+}
+
+// rank[l][base + pos] = i for every sorted entry i of array l: the inverse of
+// the sorted order, per cluster.
+__global__ void rank_kernel(const int32_t* __restrict__ pos, const int32_t* __restrict__ sorted_asg,
+                            const int64_t* __restrict__ cl_off, int64_t n, int L, int32_t* __restrict__ rank) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t base = cl_off[sorted_asg[i]];
+    for (int l = 0; l < L; ++l) {
+        const int32_t p = pos[(int64_t)l * n + i];
+        rank[(int64_t)l * n + base + p] = (int32_t)(i - base);
+    }
 }
 
 // pos[l][row] = row - cl_off[cluster(row)], the cluster-local row index.
@@ -240,7 +251,7 @@ int dev_alloc(void** p, size_t bytes, const char* what) {
 void release(lider_index* ix) {
     if (!ix) return;
     void* bufs[] = {ix->X, ix->orig_id, ix->cl_off, ix->C, ix->half_norm, ix->A, ix->bproj,
-                    ix->keys, ix->pos, ix->root, ix->leaf};
+                    ix->keys, ix->pos, ix->root, ix->leaf, ix->X_hi, ix->X_lo, ix->rank};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (ix->pool) cudaMemPoolDestroy(ix->pool);
@@ -266,6 +277,10 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
     if ((int64_t)beta * P->B > 56) return fail(LIDER_EINVAL, "lider_build: floor(64/m) * B must be <= 56");
     if (P->L > LIDER_MAX_L) return fail(LIDER_ELIMIT, "lider_build: L exceeds LIDER_MAX_L");
     if (P->rmi_leaves > (1 << 24)) return fail(LIDER_ELIMIT, "lider_build: rmi_leaves too large");
+    if (P->score_mode != LIDER_SCORE_TENSOR && P->score_mode != LIDER_SCORE_SIMT)
+        return fail(LIDER_EINVAL, "lider_build: unknown score_mode");
+    if (P->score_mode == LIDER_SCORE_TENSOR && P->L > 16)
+        return fail(LIDER_ELIMIT, "lider_build: tensor-core scoring supports L <= 16 (use LIDER_SCORE_SIMT)");
 
     int dev = 0;
     LIDER_CUDA_TRY(cudaGetDevice(&dev));
@@ -369,6 +384,19 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
         }
     }
 
+    // tensor-core scoring: TF32 split of the corpus, rank tables, TMA maps
+    if (P->score_mode == LIDER_SCORE_TENSOR) {
+        ALLOC(ix->X_hi, (size_t)n * d * sizeof(float), "corpus TF32 head");
+        ALLOC(ix->X_lo, (size_t)n * d * sizeof(float), "corpus TF32 tail");
+        ALLOC(ix->rank, (size_t)L * n * sizeof(int32_t), "rank tables");
+        if ((rc = launch_split_tf32(ix->X, n * d, ix->X_hi, ix->X_lo, st))) return rc;
+        rank_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(ix->pos, asg_sorted.as<int32_t>(), ix->cl_off, n, L,
+                                                           ix->rank);
+        LIDER_LAUNCH_CHECK("rank_kernel");
+        if ((rc = make_tensor_map(&ix->map_xhi, ix->X_hi, n, d, 256))) return rc;
+        if ((rc = make_tensor_map(&ix->map_xlo, ix->X_lo, n, d, 256))) return rc;
+    }
+
     // 5. RMI per (cluster, array)
     rmi_fit_kernel<<<dim3(ncl, L), 256, 0, st>>>(ix->keys, ix->cl_off, n, L, F, ix->root, ix->leaf,
                                                 errf.as<int>());
@@ -396,6 +424,7 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
     g.W = P->W;
     g.X = ix->X; g.orig_id = ix->orig_id; g.cl_off = ix->cl_off; g.C = ix->C; g.half_norm = ix->half_norm;
     g.A = ix->A; g.bproj = ix->bproj; g.keys = ix->keys; g.pos = ix->pos; g.root = ix->root; g.leaf = ix->leaf;
+    g.X_hi = ix->X_hi; g.X_lo = ix->X_lo; g.rank = ix->rank;
 #undef ALLOC
     guard.ix = nullptr;
     *out = ix;

@@ -1,6 +1,7 @@
 // Internal definitions shared by the LIDER CUDA translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -57,6 +58,9 @@ struct Geometry {         // everything a search kernel needs, passed by value
     const int32_t* pos;     // L x n, cluster-local row of each sorted entry
     const RmiRoot* root;    // ncl x L
     const RmiLeaf* leaf;    // ncl x L x F
+    const float* X_hi;      // n x d, TF32 head of X (tensor-core scoring)
+    const float* X_lo;      // n x d, X - X_hi
+    const int32_t* rank;    // L x n, rank[l][base + p] = sorted position of row p in array l
 };
 
 }  // namespace lider
@@ -78,6 +82,11 @@ struct lider_index {
     int32_t* pos = nullptr;
     lider::RmiRoot* root = nullptr;
     lider::RmiLeaf* leaf = nullptr;
+    float* X_hi = nullptr;
+    float* X_lo = nullptr;
+    int32_t* rank = nullptr;
+    CUtensorMap map_xhi;        // TMA maps over X_hi / X_lo, boxes of 32 x 256
+    CUtensorMap map_xlo;
     cudaMemPool_t pool = nullptr;
     int score_blocks_per_sm = 1;
     int num_sms = 148;
@@ -187,6 +196,8 @@ int launch_hash_t(const float* X, int64_t n, int d, const float* A, const float*
                   double W, double* t_out, cudaStream_t s);
 int launch_scores(const float* X, int64_t n, int d, const float* C, const double* half_norm,
                   int ncl, double* out, cudaStream_t s);
+int launch_split_tf32(const float* x, int64_t n, float* hi, float* lo, cudaStream_t s);
+int make_tensor_map(CUtensorMap* map, const float* base, int64_t rows, int d, int box_rows);
 int launch_pack(const double* t, int64_t n, int L, int m, int beta, int64_t row_offset,
                 int64_t key_stride_row, int64_t key_stride_arr, uint64_t* keys,
                 unsigned long long* n_boundary, unsigned long long* n_clamped, cudaStream_t s);

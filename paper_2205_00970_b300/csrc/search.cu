@@ -24,6 +24,7 @@
 #include <mutex>
 
 #include "lider_internal.cuh"
+#include "tc.cuh"
 
 namespace lider {
 
@@ -90,37 +91,49 @@ __global__ void group_count_kernel(const int32_t* __restrict__ route, int64_t np
 
 // Single block: off = exclusive scan of cnt, item_off = exclusive scan of
 // ceil(cnt / G), cursor = off.
-__global__ void group_scan_kernel(const int32_t* __restrict__ cnt, int ncl, int G, int32_t* __restrict__ off,
-                                  int32_t* __restrict__ cursor, int32_t* __restrict__ item_off) {
-    __shared__ int32_t s_a[1024], s_b[1024];
-    __shared__ int32_t carry_a, carry_b;
-    if (threadIdx.x == 0) { carry_a = 0; carry_b = 0; }
+// Tensor-core units of cluster j: ceil(cnt/128) query tiles x ceil(n_c/256) row tiles.
+__device__ __forceinline__ int32_t tc_units(int32_t cnt, int64_t n_c) {
+    return n_c > 0 ? ((cnt + tc::kBM - 1) / tc::kBM) * (int32_t)((n_c + tc::kBN - 1) / tc::kBN) : 0;
+}
+
+__global__ void group_scan_kernel(const int32_t* __restrict__ cnt, int ncl, int G, const int64_t* __restrict__ cl_off,
+                                  int32_t* __restrict__ off, int32_t* __restrict__ cursor,
+                                  int32_t* __restrict__ item_off, int32_t* __restrict__ unit_off) {
+    __shared__ int32_t s_a[1024], s_b[1024], s_c[1024];
+    __shared__ int32_t carry_a, carry_b, carry_c;
+    if (threadIdx.x == 0) { carry_a = 0; carry_b = 0; carry_c = 0; }
     __syncthreads();
     for (int base = 0; base < ncl; base += 1024) {
         const int j = base + threadIdx.x;
         const int32_t v = (j < ncl) ? cnt[j] : 0;
+        const int32_t vb = (v + G - 1) / G;
+        const int32_t vc = (j < ncl) ? tc_units(v, cl_off[j + 1] - cl_off[j]) : 0;
         s_a[threadIdx.x] = v;
-        s_b[threadIdx.x] = (v + G - 1) / G;
+        s_b[threadIdx.x] = vb;
+        s_c[threadIdx.x] = vc;
         __syncthreads();
-        for (int o = 1; o < 1024; o <<= 1) {          // inclusive Hillis-Steele scan
+        for (int o = 1; o < 1024; o <<= 1) {          // inclusive Hillis-Steele scans
             const int32_t ta = threadIdx.x >= o ? s_a[threadIdx.x - o] : 0;
             const int32_t tb = threadIdx.x >= o ? s_b[threadIdx.x - o] : 0;
+            const int32_t tcv = threadIdx.x >= o ? s_c[threadIdx.x - o] : 0;
             __syncthreads();
             s_a[threadIdx.x] += ta;
             s_b[threadIdx.x] += tb;
+            s_c[threadIdx.x] += tcv;
             __syncthreads();
         }
         if (j < ncl) {
             const int32_t ea = carry_a + s_a[threadIdx.x] - v;
             off[j] = ea;
             cursor[j] = ea;
-            item_off[j] = carry_b + s_b[threadIdx.x] - (v + G - 1) / G;
+            item_off[j] = carry_b + s_b[threadIdx.x] - vb;
+            unit_off[j] = carry_c + s_c[threadIdx.x] - vc;
         }
         __syncthreads();
-        if (threadIdx.x == 1023) { carry_a += s_a[1023]; carry_b += s_b[1023]; }
+        if (threadIdx.x == 1023) { carry_a += s_a[1023]; carry_b += s_b[1023]; carry_c += s_c[1023]; }
         __syncthreads();
     }
-    if (threadIdx.x == 0) { off[ncl] = carry_a; item_off[ncl] = carry_b; }
+    if (threadIdx.x == 0) { off[ncl] = carry_a; item_off[ncl] = carry_b; unit_off[ncl] = carry_c; }
 }
 
 __global__ void group_fill_kernel(const int32_t* __restrict__ route, int64_t npairs, int32_t* __restrict__ cursor,
@@ -553,6 +566,177 @@ __global__ void __launch_bounds__(kScoreThreads) score_group_kernel(ScoreArgs a)
     }
 }
 
+// ----------------------------------------------------- tensor-core score --
+// Scoring on the tcgen05 tensor cores (LIDER_SCORE_TENSOR).  The pairs of one
+// cluster are cut into query tiles of 128 (their queries gathered, in pair
+// order, into Qp, split into TF32 head and tail) and the cluster's rows into
+// row tiles of 256; each (query tile, row tile) unit is one dense 128 x 256
+// tile computed with three TF32 products per FP32 product (tc.cuh).  The
+// epilogue keeps only candidates: row p is a candidate of pair (q, cluster)
+// when its sorted position in some array l falls in q's expansion window
+// there, rank_l(p) - wstart_l in [0, T).  Each candidate's key goes to the
+// pair's list; topk_pairs_kernel then selects each pair's top k.
+__global__ void qgather_kernel(const float* __restrict__ Q, const int32_t* __restrict__ pairs, int64_t np, int c,
+                               int d, float* __restrict__ qp_hi, float* __restrict__ qp_lo) {
+    const int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (slot >= np) return;
+    const int64_t q = pairs[slot] / c;
+    const float4* src = reinterpret_cast<const float4*>(Q + q * d);
+    float4* hi = reinterpret_cast<float4*>(qp_hi + slot * d);
+    float4* lo = reinterpret_cast<float4*>(qp_lo + slot * d);
+    for (int i = lane; i < d / 4; i += 32) {
+        const float4 v = src[i];
+        float4 h, l;
+        h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u); l.x = __fsub_rn(v.x, h.x);
+        h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u); l.y = __fsub_rn(v.y, h.y);
+        h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u); l.z = __fsub_rn(v.z, h.z);
+        h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u); l.w = __fsub_rn(v.w, h.w);
+        hi[i] = h;
+        lo[i] = l;
+    }
+}
+
+constexpr int kTcMaxL = 16;
+
+struct TcArgs {
+    const int32_t* unit_off;
+    const int32_t* off;
+    const int32_t* cnt;
+    const int64_t* cl_off;
+    const int32_t* pairs;
+    const int32_t* wstart;
+    const int32_t* rank;
+    int64_t n;
+    int ncl, L, R, T_cap;
+    uint64_t* pbuf;
+    int32_t* pcount;
+};
+
+__device__ __forceinline__ void tc_decode(const TcArgs& a, int u, int& j, int& it, int& rt) {
+    int lo = 0, hi = a.ncl - 1;                  // last j with unit_off[j] <= u
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.unit_off[mid] <= u) lo = mid; else hi = mid - 1;
+    }
+    j = lo;
+    const int64_t n_c = a.cl_off[j + 1] - a.cl_off[j];
+    const int nrt = (int)((n_c + tc::kBN - 1) / tc::kBN);
+    const int local = u - a.unit_off[j];
+    it = local / nrt;
+    rt = local - it * nrt;
+}
+
+struct TcSched {
+    const TcArgs* a;
+    __device__ int count() const { return a->unit_off[a->ncl]; }
+    __device__ void coords(int u, int& arow, int& brow) const {
+        int j, it, rt;
+        tc_decode(*a, u, j, it, rt);
+        arow = a->off[j] + it * tc::kBM;
+        brow = (int)(a->cl_off[j] + (int64_t)rt * tc::kBN);
+    }
+};
+
+struct TcEpi {
+    const TcArgs* a;
+    int32_t* rank_s;            // shared, L x 256 sorted positions of the tile's rows
+    bool valid;
+    int64_t pair;
+    int p0, cursor;
+    uint32_t bits[tc::kBN / 32];
+
+    __device__ void begin(int u, int row) {
+        int j, it, rt;
+        tc_decode(*a, u, j, it, rt);
+        const int64_t base = a->cl_off[j];
+        const int64_t n_c = a->cl_off[j + 1] - base;
+        p0 = rt * tc::kBN;
+        const int et = threadIdx.x - 64;          // 0..127 across the epilogue warps
+        for (int idx = et; idx < a->L * tc::kBN; idx += 128) {
+            const int l = idx / tc::kBN, col = idx - l * tc::kBN;
+            const int64_t p = (int64_t)p0 + col;
+            rank_s[idx] = p < n_c ? a->rank[(int64_t)l * a->n + base + p] : -1;
+        }
+        tc::epi_sync();
+        const int in_tile = min(tc::kBM, a->cnt[j] - it * tc::kBM);
+        valid = row < in_tile;
+        if (!valid) return;
+        pair = a->pairs[a->off[j] + it * tc::kBM + row];
+        const uint32_t T = (uint32_t)min((int64_t)a->R, n_c);
+        uint32_t ws[kTcMaxL];
+#pragma unroll
+        for (int l = 0; l < kTcMaxL; ++l) ws[l] = l < a->L ? (uint32_t)a->wstart[pair * a->L + l] : 0u;
+        int total = 0;
+#pragma unroll
+        for (int w = 0; w < tc::kBN / 32; ++w) {
+            uint32_t word = 0;
+            for (int b = 0; b < 32; ++b) {
+                const int col = w * 32 + b;
+                bool m = false;
+#pragma unroll
+                for (int l = 0; l < kTcMaxL; ++l)
+                    if (l < a->L) m |= (uint32_t)rank_s[l * tc::kBN + col] - ws[l] < T;
+                word |= (uint32_t)m << b;
+            }
+            bits[w] = word;
+            total += __popc(word);
+        }
+        cursor = total ? atomicAdd(&a->pcount[pair], total) : 0;
+    }
+
+    __device__ void operator()(int, int, int col0, const uint32_t (&v)[32]) {
+        if (!valid) return;
+        uint32_t w = bits[col0 >> 5];
+        uint64_t* dst = a->pbuf + pair * a->T_cap;
+        while (w) {
+            const int i = __ffs(w) - 1;
+            w &= w - 1;
+            dst[cursor++] = score_key(__uint_as_float(v[i]), (uint32_t)(p0 + col0 + i));
+        }
+    }
+
+    __device__ void done(int, int) { tc::epi_sync(); }   // the rank tile may now be reloaded
+};
+
+__global__ void __launch_bounds__(tc::kThreads, 1)
+    tc_score_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+                    const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, int kchunks,
+                    TcArgs args, int* err) {
+    extern __shared__ unsigned char smem[];
+    __shared__ tc::Ctl ctl;
+    int32_t* rank_s = reinterpret_cast<int32_t*>(smem + tc::kSmemBytes);
+    TcSched sched{&args};
+    TcEpi epi;
+    epi.a = &args;
+    epi.rank_s = rank_s;
+    tc::gemm_tiles(&mAhi, &mAlo, &mBhi, &mBlo, kchunks, sched, epi, err, smem, ctl);
+}
+
+// Per pair: top k of its candidate list (bucket selection, see block_topk).
+__global__ void __launch_bounds__(256) topk_pairs_kernel(const uint64_t* __restrict__ pbuf, int T_cap,
+                                                         const int32_t* __restrict__ pcount,
+                                                         const int32_t* __restrict__ route,
+                                                         const int64_t* __restrict__ cl_off,
+                                                         const int64_t* __restrict__ orig_id, int k,
+                                                         float* __restrict__ pscore, int64_t* __restrict__ pid,
+                                                         int32_t* __restrict__ trace_ucount,
+                                                         unsigned long long* counters) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint32_t s_bins[kBins];
+    __shared__ uint32_t s_scal[8];
+    uint64_t* K = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* cand = K + next_pow2_dev(T_cap);
+    const int64_t pair = blockIdx.x;
+    const int U = pcount[pair];
+    block_topk(pbuf + pair * T_cap, U, k, K, cand, s_bins, s_scal, cl_off[route[pair]], orig_id,
+               pscore + pair * k, pid + pair * k);
+    if (threadIdx.x == 0) {
+        atomicAdd(&counters[CNT_CANDIDATES], (unsigned long long)U);
+        if (trace_ucount) trace_ucount[pair] = U;
+    }
+}
+
 // ------------------------------------------------------------------ merge --
 // Warp per query; lane p < c walks list p (sorted best first).
 __global__ void merge_kernel(const float* __restrict__ pscore, const int64_t* __restrict__ pid, int64_t nq,
@@ -616,12 +800,17 @@ struct Workspace {
     float* pscore;
     int64_t* pid;
     uint64_t* pbuf;
+    int32_t* pcount;            // tensor path: candidates per pair (cleared)
+    int32_t* unit_off;
+    float* qp_hi;               // tensor path: queries in pair order, TF32 head / tail
+    float* qp_lo;
+    int* tc_err;
     size_t zero_bytes;   // counters + cnt, cleared at the start of a search
     size_t total;
 };
 
 // Carve one allocation into the search buffers (base == nullptr: sizes only).
-Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, int k, int R) {
+Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, int k, int R, bool tensor) {
     Workspace w{};
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -632,7 +821,12 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, int k
     const int64_t np = nq * c;
     w.counters = (unsigned long long*)take(CNT_SLOTS * sizeof(unsigned long long));
     w.cnt = (int32_t*)take((size_t)g.ncl * 4);
+    w.tc_err = (int*)take(16);
+    w.pcount = tensor ? (int32_t*)take((size_t)np * 4) : nullptr;
     w.zero_bytes = o;
+    w.unit_off = (int32_t*)take((size_t)(g.ncl + 1) * 4);
+    w.qp_hi = tensor ? (float*)take((size_t)np * g.d * 4) : nullptr;
+    w.qp_lo = tensor ? (float*)take((size_t)np * g.d * 4) : nullptr;
     w.off = (int32_t*)take((size_t)(g.ncl + 1) * 4);
     w.cursor = (int32_t*)take((size_t)g.ncl * 4);
     w.item_off = (int32_t*)take((size_t)(g.ncl + 1) * 4);
@@ -701,7 +895,7 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
     const int G = std::max(1, std::min(kMaxGroup, (96 * 1024) / (g.d * 4)));
     group_count_kernel<<<(unsigned)cdiv(np, 256), 256, 0, st>>>(w.route, np, w.cnt);
     LIDER_LAUNCH_CHECK("group_count_kernel");
-    group_scan_kernel<<<1, 1024, 0, st>>>(w.cnt, g.ncl, G, w.off, w.cursor, w.item_off);
+    group_scan_kernel<<<1, 1024, 0, st>>>(w.cnt, g.ncl, G, g.cl_off, w.off, w.cursor, w.item_off, w.unit_off);
     LIDER_LAUNCH_CHECK("group_scan_kernel");
     group_fill_kernel<<<(unsigned)cdiv(np, 256), 256, 0, st>>>(w.route, np, w.cursor, w.pairs);
     LIDER_LAUNCH_CHECK("group_fill_kernel");
@@ -713,46 +907,81 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
     LIDER_LAUNCH_CHECK("locate_kernel");
     // 5. candidate union, exact scores and per-pair top-k
     if ((rc = mark(LIDER_PHASE_SCORE))) return rc;
-    ScoreArgs sa;
-    sa.g = g;
-    sa.Q = Q;
-    sa.c = c;
-    sa.G = G;
-    sa.k = k;
-    sa.T_cap = g.L * R;
-    sa.region_bytes = (int)align_up(std::max((size_t)G * g.d * 4,
-                                             ((size_t)next_pow2(sa.T_cap) + kCandCap) * 8), 16);
-    sa.off = w.off;
-    sa.cnt = w.cnt;
-    sa.item_off = w.item_off;
-    sa.pairs = w.pairs;
-    sa.wstart = w.wstart;
-    sa.pbuf = w.pbuf;
-    sa.pscore = w.pscore;
-    sa.pid = w.pid;
-    sa.trace_ucount = tr ? tr->ucount : nullptr;
-    sa.counters = w.counters;
-    const size_t smem = (size_t)sa.region_bytes + (size_t)(kTile / 2) * 4;
-    const void* kern = nullptr;
-    switch ((g.d % 128 == 0 && g.d <= 1024) ? g.d / 128 : 0) {
-        case 1: kern = (const void*)score_group_kernel<1>; break;
-        case 2: kern = (const void*)score_group_kernel<2>; break;
-        case 3: kern = (const void*)score_group_kernel<3>; break;
-        case 4: kern = (const void*)score_group_kernel<4>; break;
-        case 5: kern = (const void*)score_group_kernel<5>; break;
-        case 6: kern = (const void*)score_group_kernel<6>; break;
-        case 7: kern = (const void*)score_group_kernel<7>; break;
-        case 8: kern = (const void*)score_group_kernel<8>; break;
-        default: kern = (const void*)score_group_kernel<0>; break;
+    if (ix->params.score_mode == LIDER_SCORE_TENSOR) {
+        qgather_kernel<<<(unsigned)cdiv(np * 32, 256), 256, 0, st>>>(Q, w.pairs, np, c, g.d, w.qp_hi, w.qp_lo);
+        LIDER_LAUNCH_CHECK("qgather_kernel");
+        CUtensorMap mqh, mql;
+        if ((rc = make_tensor_map(&mqh, w.qp_hi, np, g.d, tc::kBM))) return rc;
+        if ((rc = make_tensor_map(&mql, w.qp_lo, np, g.d, tc::kBM))) return rc;
+        TcArgs ta;
+        ta.unit_off = w.unit_off;
+        ta.off = w.off;
+        ta.cnt = w.cnt;
+        ta.cl_off = g.cl_off;
+        ta.pairs = w.pairs;
+        ta.wstart = w.wstart;
+        ta.rank = g.rank;
+        ta.n = g.n;
+        ta.ncl = g.ncl;
+        ta.L = g.L;
+        ta.R = R;
+        ta.T_cap = g.L * R;
+        ta.pbuf = w.pbuf;
+        ta.pcount = w.pcount;
+        const int tc_smem = tc::kSmemBytes + kTcMaxL * tc::kBN * 4;
+        LIDER_CUDA_TRY(cudaFuncSetAttribute(tc_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem));
+        tc_score_kernel<<<ix->num_sms, tc::kThreads, tc_smem, st>>>(ix->map_xhi, ix->map_xlo, mqh, mql,
+                                                                    (g.d + tc::kBK - 1) / tc::kBK, ta, w.tc_err);
+        LIDER_LAUNCH_CHECK("tc_score_kernel");
+        const int T_cap = g.L * R;
+        const size_t tk_smem = ((size_t)next_pow2(T_cap) + kCandCap) * 8;
+        LIDER_CUDA_TRY(cudaFuncSetAttribute(topk_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)tk_smem));
+        topk_pairs_kernel<<<(unsigned)np, 256, tk_smem, st>>>(w.pbuf, T_cap, w.pcount, w.route, g.cl_off, g.orig_id, k,
+                                                              w.pscore, w.pid, tr ? tr->ucount : nullptr, w.counters);
+        LIDER_LAUNCH_CHECK("topk_pairs_kernel");
+    } else {
+        ScoreArgs sa;
+        sa.g = g;
+        sa.Q = Q;
+        sa.c = c;
+        sa.G = G;
+        sa.k = k;
+        sa.T_cap = g.L * R;
+        sa.region_bytes = (int)align_up(std::max((size_t)G * g.d * 4,
+                                                 ((size_t)next_pow2(sa.T_cap) + kCandCap) * 8), 16);
+        sa.off = w.off;
+        sa.cnt = w.cnt;
+        sa.item_off = w.item_off;
+        sa.pairs = w.pairs;
+        sa.wstart = w.wstart;
+        sa.pbuf = w.pbuf;
+        sa.pscore = w.pscore;
+        sa.pid = w.pid;
+        sa.trace_ucount = tr ? tr->ucount : nullptr;
+        sa.counters = w.counters;
+        const size_t smem = (size_t)sa.region_bytes + (size_t)(kTile / 2) * 4;
+        const void* kern = nullptr;
+        switch ((g.d % 128 == 0 && g.d <= 1024) ? g.d / 128 : 0) {
+            case 1: kern = (const void*)score_group_kernel<1>; break;
+            case 2: kern = (const void*)score_group_kernel<2>; break;
+            case 3: kern = (const void*)score_group_kernel<3>; break;
+            case 4: kern = (const void*)score_group_kernel<4>; break;
+            case 5: kern = (const void*)score_group_kernel<5>; break;
+            case 6: kern = (const void*)score_group_kernel<6>; break;
+            case 7: kern = (const void*)score_group_kernel<7>; break;
+            case 8: kern = (const void*)score_group_kernel<8>; break;
+            default: kern = (const void*)score_group_kernel<0>; break;
+        }
+        LIDER_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        LIDER_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kScoreThreads, smem));
+        if (per_sm < 1) return fail(LIDER_ELIMIT, "lider_search: score kernel does not fit on an SM");
+        const int64_t max_items = cdiv(np, G) + g.ncl;
+        const int grid = (int)std::min<int64_t>(max_items, (int64_t)per_sm * ix->num_sms);
+        void* kargs[] = {&sa};
+        LIDER_CUDA_TRY(cudaLaunchKernel(kern, dim3(grid), dim3(kScoreThreads), kargs, smem, st));
     }
-    LIDER_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    LIDER_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kScoreThreads, smem));
-    if (per_sm < 1) return fail(LIDER_ELIMIT, "lider_search: score kernel does not fit on an SM");
-    const int64_t max_items = cdiv(np, G) + g.ncl;
-    const int grid = (int)std::min<int64_t>(max_items, (int64_t)per_sm * ix->num_sms);
-    void* kargs[] = {&sa};
-    LIDER_CUDA_TRY(cudaLaunchKernel(kern, dim3(grid), dim3(kScoreThreads), kargs, smem, st));
     // 6. merge
     if ((rc = mark(LIDER_PHASE_MERGE))) return rc;
     merge_kernel<<<(unsigned)cdiv(nq * 32, 256), 256, 0, st>>>(w.pscore, w.pid, nq, c, k, out_ids, out_scores);
@@ -762,8 +991,13 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
 
 int read_stats(const Workspace& w, int64_t nq, int c, lider_search_stats* stats, cudaStream_t st) {
     unsigned long long h[CNT_SLOTS] = {};
+    int tc_err = 0;
     LIDER_CUDA_TRY(cudaMemcpyAsync(h, w.counters, sizeof(h), cudaMemcpyDeviceToHost, st));
+    LIDER_CUDA_TRY(cudaMemcpyAsync(&tc_err, w.tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     LIDER_CUDA_TRY(cudaStreamSynchronize(st));
+    if (tc_err)
+        return fail(LIDER_ECUDA, "lider_search: tensor-core scoring stopped after a wait timed out (code " +
+                                     std::to_string(tc_err) + ")");
     stats->n_queries = nq;
     stats->pairs = nq * c;
     stats->candidates = (int64_t)h[CNT_CANDIDATES];
@@ -794,10 +1028,10 @@ int search_entry(const lider_index* ix, const float* Q, int64_t nq, int k, int c
     if (stats) *stats = lider_search_stats{};
     if (nq == 0) return LIDER_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    Workspace sz = carve(nullptr, ix->g, nq, c, k, ix->params.r0 * k);
+    Workspace sz = carve(nullptr, ix->g, nq, c, k, ix->params.r0 * k, ix->params.score_mode == LIDER_SCORE_TENSOR);
     void* mem = nullptr;
     if ((rc = pool_alloc(ix, &mem, sz.total, st))) return rc;
-    Workspace w = carve((unsigned char*)mem, ix->g, nq, c, k, ix->params.r0 * k);
+    Workspace w = carve((unsigned char*)mem, ix->g, nq, c, k, ix->params.r0 * k, ix->params.score_mode == LIDER_SCORE_TENSOR);
     rc = enqueue_search(ix, Q, nq, k, c, out_ids, out_scores, tr, w, st);
     if (rc == LIDER_OK && stats) rc = read_stats(w, nq, c, stats, st);
     cudaError_t e = cudaFreeAsync(mem, st);
@@ -814,7 +1048,7 @@ int search_host_entry(const lider_index* ix, const float* Qh, int64_t nq, int k,
     cudaStream_t st = (cudaStream_t)stream;
     const size_t qb = (size_t)nq * ix->g.d * 4, ib = (size_t)nq * k * 8, sb = (size_t)nq * k * 4;
     const size_t o_ids = align_up(qb, 256), o_sc = align_up(o_ids + ib, 256);
-    Workspace sz = carve(nullptr, ix->g, nq, c, k, ix->params.r0 * k);
+    Workspace sz = carve(nullptr, ix->g, nq, c, k, ix->params.r0 * k, ix->params.score_mode == LIDER_SCORE_TENSOR);
     const size_t o_ws = align_up(o_sc + sb, 256);
     void* mem = nullptr;
     if ((rc = pool_alloc(ix, &mem, o_ws + sz.total, st))) return rc;
@@ -822,7 +1056,7 @@ int search_host_entry(const lider_index* ix, const float* Qh, int64_t nq, int k,
     float* Qd = (float*)m;
     int64_t* idd = (int64_t*)(m + o_ids);
     float* scd = (float*)(m + o_sc);
-    Workspace w = carve(m + o_ws, ix->g, nq, c, k, ix->params.r0 * k);
+    Workspace w = carve(m + o_ws, ix->g, nq, c, k, ix->params.r0 * k, ix->params.score_mode == LIDER_SCORE_TENSOR);
     cudaError_t e = cudaMemcpyAsync(Qd, Qh, qb, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync(queries)");
     if (!rc) rc = enqueue_search(ix, Qd, nq, k, c, idd, scd, nullptr, w, st);
@@ -890,7 +1124,7 @@ int search_noalloc_impl(const lider_index* ix, const float* Q, int64_t nq, int k
     if (stats) *stats = lider_search_stats{};
     if (nq == 0) return LIDER_OK;
     const int R = ix->params.r0 * k;
-    const Workspace need = carve(nullptr, ix->g, nq, c, k, R);
+    const Workspace need = carve(nullptr, ix->g, nq, c, k, R, ix->params.score_mode == LIDER_SCORE_TENSOR);
     if (need.total > (size_t)LIDER_NOALLOC_SCRATCH_BYTES)
         return fail(LIDER_ELIMIT, "lider_search_noalloc: this batch needs " + std::to_string(need.total) +
                                       " bytes of scratch, more than the fixed LIDER_NOALLOC_SCRATCH_BYTES (" +
@@ -898,7 +1132,7 @@ int search_noalloc_impl(const lider_index* ix, const float* Q, int64_t nq, int k
                                       "); search fewer queries per call");
     unsigned char* base = nullptr;
     if ((rc = noalloc_scratch(ix->device, &base))) return rc;
-    const Workspace w = carve(base, ix->g, nq, c, k, R);
+    const Workspace w = carve(base, ix->g, nq, c, k, R, ix->params.score_mode == LIDER_SCORE_TENSOR);
     cudaStream_t st = (cudaStream_t)stream;
     rc = enqueue_search(ix, Q, nq, k, c, out_ids, out_scores, nullptr, w, st);
     if (rc == LIDER_OK && stats) rc = read_stats(w, nq, c, stats, st);

@@ -1,0 +1,327 @@
+// 5th-generation tensor-core (tcgen05) tile engine for sm_103a: TMA loads into
+// 128-byte-swizzled shared memory, tcgen05.mma with the accumulator in TMEM,
+// tcgen05.ld for the epilogue.  Used for the dense part of candidate scoring:
+// D[128 x 256] = A[128 x d] . B[256 x d]^T with FP32 accuracy from three TF32
+// products (A_hi B_hi + A_hi B_lo + A_lo B_hi; x = x_hi + x_lo with x_hi the
+// TF32-representable head of x, so the dropped A_lo B_lo term and the TF32
+// rounding of x_lo stay below 2^-21 relative).
+//
+// Warp roles of a 192-thread block: warp 0 issues TMA loads (and owns the TMEM
+// allocation), warp 1 issues MMAs (one elected thread), warps 2-5 run the
+// epilogue (warp w reads TMEM lanes 32*(w%4)..+31).  Two shared-memory stages
+// and two TMEM accumulators let loads, MMAs and the epilogue overlap.
+//
+// Every wait is bounded: after kTimeoutNs the waiter records an error code,
+// raises the block's abort flag and every role leaves its loop; the block then
+// waits (bounded) for its outstanding copies and frees TMEM before exiting.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lider {
+namespace tc {
+
+constexpr int kBM = 128;                       // MMA M = TMEM lanes
+constexpr int kBN = 256;                       // MMA N = accumulator columns
+constexpr int kBK = 32;                        // FP32 elements per 128-byte swizzle row
+constexpr int kStages = 2;
+constexpr int kTileA = kBM * kBK * 4;          // 16 KB
+constexpr int kTileB = kBN * kBK * 4;          // 32 KB
+constexpr int kStageBytes = 2 * kTileA + 2 * kTileB;   // A_hi, A_lo, B_hi, B_lo
+constexpr int kSmemBytes = kStages * kStageBytes + 1024;  // + alignment slack
+constexpr int kThreads = 192;
+constexpr int kTmemCols = 2 * kBN;
+constexpr uint64_t kTimeoutNs = 2000000000ull;
+
+// instruction descriptor, kind::tf32: D F32 (bits 4-5 = 1), A and B TF32
+// (bits 7-9 and 10-12 = 2), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kBN >> 3) << 17) |
+                                ((uint32_t)(kBM >> 4) << 24);
+
+enum {
+    TC_OK = 0,
+    TC_TIMEOUT_EMPTY = 1,
+    TC_TIMEOUT_FULL = 2,
+    TC_TIMEOUT_TFULL = 3,
+    TC_TIMEOUT_TEMPTY = 4,
+    TC_TIMEOUT_DRAIN = 5,
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of `parity` to complete; false on timeout or abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (globaltimer() - t0 > kTimeoutNs) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
+            "r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+                 "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrive on `bar` once every MMA issued so far by this thread has completed.
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 32 consecutive columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major operand stored as rows of 128
+// bytes with the 128-byte swizzle (the layout TMA writes with
+// CU_TENSOR_MAP_SWIZZLE_128B): start address >> 4 in bits 0-13, leading byte
+// offset (unused for this layout, 16 B) >> 4 at bit 16, stride byte offset
+// between 8-row groups (1024 B) >> 4 at bit 32, descriptor version 1 at bit 46,
+// layout type 2 (128-byte swizzle) at bit 61.  The tile base must be
+// 1024-byte aligned; a K offset inside the 128-byte row is added to the start.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(16u >> 4) << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Named barrier of the four epilogue warps (barrier 0 is __syncthreads).
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Shared state of one block.
+struct Ctl {
+    uint64_t full[kStages];
+    uint64_t empty[kStages];
+    uint64_t tfull[2];
+    uint64_t tempty[2];
+    uint32_t tmem_base;
+    int abort;
+    int epi_bad;        // an epilogue warp's wait failed (read only after epi_sync)
+};
+
+// One unit = one 128 x 256 tile: A rows [a_row, a_row+128), B rows
+// [b_row, b_row+256), all of K.  Sched provides: int count() and
+// void coords(int u, int& a_row, int& b_row).  Epi provides, called by every
+// epilogue thread (row = its accumulator row): void begin(int u, int row)
+// before the first column group (it may use epi_sync), void operator()(int u,
+// int row, int col0, const uint32_t (&v)[32]) for columns col0..col0+31, and
+// void done(int u, int row) after the last group.  The epilogue warps leave
+// their loop only together, so their named barriers cannot be left waiting.
+template <class Sched, class Epi>
+__device__ void gemm_tiles(const CUtensorMap* mAhi, const CUtensorMap* mAlo, const CUtensorMap* mBhi,
+                           const CUtensorMap* mBlo, int kchunks, Sched& sched, Epi& epi, int* err,
+                           unsigned char* smem_raw, Ctl& ctl) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                           ~(uintptr_t)1023);
+    auto stage_ptr = [&](int s) { return smem + (size_t)s * kStageBytes; };
+    volatile int* abort_flag = &ctl.abort;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&ctl.full[s], 1);
+            mbar_init(&ctl.empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&ctl.tfull[b], 1);
+            mbar_init(&ctl.tempty[b], 4);
+        }
+        ctl.abort = 0;
+        ctl.epi_bad = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(&ctl.tmem_base, kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = ctl.tmem_base;
+    const int nunits = sched.count();
+    auto fail = [&](int code) {
+        atomicCAS(err, 0, code);
+        *abort_flag = 1;
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {                                         // TMA producer
+            int it = 0;
+            for (int u = blockIdx.x; u < nunits && !*abort_flag; u += gridDim.x) {
+                int arow, brow;
+                sched.coords(u, arow, brow);
+                for (int kc = 0; kc < kchunks; ++kc, ++it) {
+                    const int s = it % kStages;
+                    const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+                    if (!mbar_wait(&ctl.empty[s], ph ^ 1u, abort_flag)) { fail(TC_TIMEOUT_EMPTY); break; }
+                    unsigned char* st = stage_ptr(s);
+                    mbar_expect_tx(&ctl.full[s], (uint32_t)kStageBytes);
+                    const int k0 = kc * kBK;
+                    tma_load_2d(st, mAhi, &ctl.full[s], k0, arow);
+                    tma_load_2d(st + kTileA, mAlo, &ctl.full[s], k0, arow);
+                    tma_load_2d(st + 2 * kTileA, mBhi, &ctl.full[s], k0, brow);
+                    tma_load_2d(st + 2 * kTileA + kTileB, mBlo, &ctl.full[s], k0, brow);
+                }
+            }
+            // drain: wait until every issued stage has landed (bounded)
+            const int issued = it;
+            for (int j = (issued > kStages ? issued - kStages : 0); j < issued; ++j) {
+                const int s = j % kStages;
+                const uint32_t ph = (uint32_t)(j / kStages) & 1u;
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try(&ctl.full[s], ph)) {
+                    if (globaltimer() - t0 > kTimeoutNs) { atomicCAS(err, 0, TC_TIMEOUT_DRAIN); break; }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {                                         // MMA issuer
+            int it = 0, ui = 0;
+            for (int u = blockIdx.x; u < nunits && !*abort_flag; u += gridDim.x, ++ui) {
+                const int ab = ui & 1;
+                const uint32_t aph = (uint32_t)(ui >> 1) & 1u;
+                if (!mbar_wait(&ctl.tempty[ab], aph ^ 1u, abort_flag)) { fail(TC_TIMEOUT_TEMPTY); break; }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(ab * kBN);
+                bool ok = true;
+                for (int kc = 0; kc < kchunks; ++kc, ++it) {
+                    const int s = it % kStages;
+                    const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+                    if (!mbar_wait(&ctl.full[s], ph, abort_flag)) { fail(TC_TIMEOUT_FULL); ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(stage_ptr(s));
+                    const uint32_t a_hi = sa, a_lo = sa + kTileA;
+                    const uint32_t b_hi = sa + 2 * kTileA, b_lo = sa + 2 * kTileA + kTileB;
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 8; ++kk) {           // K = 8 TF32 (32 bytes) per MMA
+                        const uint32_t off = (uint32_t)kk * 32u;
+                        const uint64_t dah = sdesc_sw128(a_hi + off), dal = sdesc_sw128(a_lo + off);
+                        const uint64_t dbh = sdesc_sw128(b_hi + off), dbl = sdesc_sw128(b_lo + off);
+                        mma_tf32(d, dah, dbh, kIdescTf32, (kc | kk) != 0 ? 1u : 0u);
+                        mma_tf32(d, dah, dbl, kIdescTf32, 1u);
+                        mma_tf32(d, dal, dbh, kIdescTf32, 1u);
+                    }
+                    mma_commit(&ctl.empty[s]);                 // stage reusable once these finish
+                }
+                if (!ok) break;
+                mma_commit(&ctl.tfull[ab]);                    // accumulator ready
+            }
+        }
+    } else {                                                     // epilogue warps 2..5
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        int ui = 0;
+        for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++ui) {
+            const int ab = ui & 1;
+            const uint32_t aph = (uint32_t)(ui >> 1) & 1u;
+            const bool ok = mbar_wait(&ctl.tfull[ab], aph, abort_flag);
+            if (!ok && lane == 0) {
+                fail(TC_TIMEOUT_TFULL);
+                atomicOr(&ctl.epi_bad, 1);
+            }
+            epi_sync();                                  // every epilogue warp arrives
+            if (*(volatile int*)&ctl.epi_bad) break;     // same decision in all four
+            tc_fence_after();
+            epi.begin(u, row);
+            const uint32_t base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * kBN);
+#pragma unroll
+            for (int cb = 0; cb < kBN / 32; ++cb) {
+                uint32_t v[32];
+                tmem_ld32(base + (uint32_t)(cb * 32), v);
+                epi(u, row, cb * 32, v);
+            }
+            epi.done(u, row);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl.tempty[ab]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+}  // namespace tc
+}  // namespace lider

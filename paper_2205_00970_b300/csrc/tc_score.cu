@@ -1,0 +1,145 @@
+// Tensor-core candidate scoring support: the TF32 hi/lo split, TMA tensor
+// maps, and a one-tile self-test of the tcgen05 engine (tc.cuh).
+#include <mutex>
+
+#include "lider_internal.cuh"
+#include "tc.cuh"
+
+namespace lider {
+
+namespace {
+
+// x = hi + lo exactly: hi keeps sign, exponent and the top 10 mantissa bits
+// (a TF32 value), lo = x - hi is exact in FP32.
+__global__ void split_tf32_kernel(const float* __restrict__ x, int64_t n, float* __restrict__ hi,
+                                  float* __restrict__ lo) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float v = x[i];
+    const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+    hi[i] = h;
+    lo[i] = __fsub_rn(v, h);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+std::once_flag g_encode_once;
+EncodeTiledFn g_encode = nullptr;
+
+int encode_fn(EncodeTiledFn* fn) {
+    std::call_once(g_encode_once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = (EncodeTiledFn)p;
+        cudaGetLastError();
+    });
+    if (!g_encode) return fail(LIDER_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    *fn = g_encode;
+    return LIDER_OK;
+}
+
+struct OneTile {
+    __device__ int count() const { return 1; }
+    __device__ void coords(int, int& a, int& b) const { a = 0; b = 0; }
+};
+
+struct WriteTile {
+    float* out;
+    int m, n;
+    __device__ void operator()(int, int row, int col0, const uint32_t (&v)[32]) const {
+        if (row >= m) return;
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            if (col0 + i < n) out[(int64_t)row * n + col0 + i] = __uint_as_float(v[i]);
+    }
+    __device__ void begin(int, int) const {}
+    __device__ void done(int, int) const {}
+};
+
+__global__ void __launch_bounds__(tc::kThreads, 1)
+    tc_tile_test_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+                        const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
+                        int kchunks, float* out, int m, int n, int* err) {
+    extern __shared__ unsigned char smem[];
+    __shared__ tc::Ctl ctl;
+    OneTile sched;
+    WriteTile epi{out, m, n};
+    tc::gemm_tiles(&mAhi, &mAlo, &mBhi, &mBlo, kchunks, sched, epi, err, smem, ctl);
+}
+
+}  // namespace
+
+int launch_split_tf32(const float* x, int64_t n, float* hi, float* lo, cudaStream_t st) {
+    if (n <= 0) return LIDER_OK;
+    split_tf32_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(x, n, hi, lo);
+    LIDER_LAUNCH_CHECK("split_tf32_kernel");
+    return LIDER_OK;
+}
+
+// 2-D FP32 tensor map over rows x d (row-major), box 32 x box_rows, 128-byte swizzle.
+int make_tensor_map(CUtensorMap* map, const float* base, int64_t rows, int d, int box_rows) {
+    EncodeTiledFn fn;
+    int rc = encode_fn(&fn);
+    if (rc) return rc;
+    const cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)d * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)tc::kBK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(LIDER_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return LIDER_OK;
+}
+
+}  // namespace lider
+
+// Self-test of the tensor-core engine: out[m x n] = A[m x d] . B[n x d]^T with
+// m <= 128, n <= 256, through the same TMA / tcgen05 / TMEM path as search.
+extern "C" int lider_debug_tc_tile(const float* A, int32_t m, const float* B, int32_t n, int32_t d, float* out,
+                                   void* stream) {
+    using namespace lider;
+    try {
+        if (!A || !B || !out) return fail(LIDER_EINVAL, "lider_debug_tc_tile: NULL pointer");
+        if (m < 1 || m > tc::kBM || n < 1 || n > tc::kBN || d < 4 || d % 4 != 0)
+            return fail(LIDER_EINVAL, "lider_debug_tc_tile: need 1<=m<=128, 1<=n<=256, d % 4 == 0");
+        cudaStream_t st = (cudaStream_t)stream;
+        float* buf = nullptr;
+        const size_t na = (size_t)m * d, nb = (size_t)n * d;
+        LIDER_CUDA_TRY(cudaMalloc(&buf, (2 * na + 2 * nb) * sizeof(float) + 64 * sizeof(int)));
+        float *ahi = buf, *alo = buf + na, *bhi = buf + 2 * na, *blo = buf + 2 * na + nb;
+        int* err = reinterpret_cast<int*>(buf + 2 * na + 2 * nb);
+        int rc = LIDER_OK;
+        CUtensorMap mah, mal, mbh, mbl;
+        do {
+            if ((rc = launch_split_tf32(A, (int64_t)na, ahi, alo, st))) break;
+            if ((rc = launch_split_tf32(B, (int64_t)nb, bhi, blo, st))) break;
+            if ((rc = make_tensor_map(&mah, ahi, m, d, tc::kBM))) break;
+            if ((rc = make_tensor_map(&mal, alo, m, d, tc::kBM))) break;
+            if ((rc = make_tensor_map(&mbh, bhi, n, d, tc::kBN))) break;
+            if ((rc = make_tensor_map(&mbl, blo, n, d, tc::kBN))) break;
+            cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemsetAsync"); break; }
+            e = cudaFuncSetAttribute(tc_tile_test_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "cudaFuncSetAttribute"); break; }
+            tc_tile_test_kernel<<<1, tc::kThreads, tc::kSmemBytes, st>>>(mah, mal, mbh, mbl, (d + tc::kBK - 1) / tc::kBK,
+                                                                        out, m, n, err);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) { rc = cuda_fail(e, "tc_tile_test_kernel"); break; }
+            int h_err = 0;
+            e = cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "tc_tile_test_kernel sync"); break; }
+            if (h_err) rc = fail(LIDER_ECUDA, "tc engine wait timed out (code " + std::to_string(h_err) + ")");
+        } while (0);
+        cudaFree(buf);
+        return rc;
+    } catch (...) {
+        return fail(LIDER_ECUDA, "lider_debug_tc_tile: internal error");
+    }
+}

@@ -42,20 +42,24 @@ def test_binding_loads_and_validates_without_gpu():
     lider.raw_call("lider_free", None)   # NULL is accepted
     # invalid build arguments are rejected before the device is touched
     out = ctypes.c_void_p()
-    p = lider.Params(4, 8, 16, 2, 1, 0, 1.0)
+    p = lider.Params(4, 8, 16, 2, 1, 0, 1.0, 0, 0)
     dummy = ctypes.c_void_p(16)
     for n, d, ncl, pp, msg in [
         (0, 8, 2, p, "n must be"),
         (10, 6, 2, p, "multiple of 4"),
         (10, 8, 0, p, "n_clusters"),
-        (10, 8, 2, lider.Params(4, 8, 16, 2, 1, 0, -1.0), "W must be"),
-        (10, 8, 2, lider.Params(4, 8, 16, 2, 8, 0, 1.0), "<= 56"),
-        (10, 8, 2, lider.Params(4, 8, 16, 2, 1, 7, 1.0), "hash_kind"),
-        (10, 8, 2, lider.Params(0, 8, 16, 2, 1, 0, 1.0), ">= 1"),
+        (10, 8, 2, lider.Params(4, 8, 16, 2, 1, 0, -1.0, 0, 0), "W must be"),
+        (10, 8, 2, lider.Params(4, 8, 16, 2, 8, 0, 1.0, 0, 0), "<= 56"),
+        (10, 8, 2, lider.Params(4, 8, 16, 2, 1, 7, 1.0, 0, 0), "hash_kind"),
+        (10, 8, 2, lider.Params(0, 8, 16, 2, 1, 0, 1.0, 0, 0), ">= 1"),
+        (10, 8, 2, lider.Params(4, 8, 16, 2, 1, 0, 1.0, 5, 0), "score_mode"),
     ]:
         rc = lider.raw_call("lider_build", dummy, n, d, dummy, ncl, dummy, dummy, ctypes.byref(pp), None,
                             ctypes.byref(out))
         assert rc == -1 and msg in lider.last_error(), (msg, lider.last_error())
     rc = lider.raw_call("lider_build", dummy, 10, 8, dummy, 2, dummy, dummy,
-                        ctypes.byref(lider.Params(33, 8, 16, 2, 1, 0, 1.0)), None, ctypes.byref(out))
+                        ctypes.byref(lider.Params(33, 8, 16, 2, 1, 0, 1.0, 1, 0)), None, ctypes.byref(out))
     assert rc == -4
+    rc = lider.raw_call("lider_build", dummy, 10, 8, dummy, 2, dummy, dummy,
+                        ctypes.byref(lider.Params(17, 8, 16, 2, 1, 0, 1.0, 0, 0)), None, ctypes.byref(out))
+    assert rc == -4 and "L <= 16" in lider.last_error()

@@ -9,10 +9,15 @@ from tests import lider_fixtures as F
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def tiny():
+MODES = [0, 1]          # tensor-core scoring, SIMT scoring
+MODE_IDS = ["tensor", "simt"]
+
+
+@pytest.fixture(scope="module", params=MODES, ids=MODE_IDS)
+def tiny(request):
     import torch
     cfg, X, Q, C, A, b = F.workload("tiny")
+    cfg["score_mode"] = request.param
     ref_idx = F.oracle_index(cfg, X, C, A, b)
     gidx = F.gpu_index(cfg, X, C, A, b)
     ref = O.search(ref_idx, Q, cfg["k"], cfg["c"], cfg["R"])
@@ -130,7 +135,8 @@ def test_k_beyond_candidates_pads(tiny):
     assert np.any(ids.cpu().numpy() == -1)
 
 
-def test_duplicates_empty_and_singleton_clusters():
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_duplicates_empty_and_singleton_clusters(mode):
     """Duplicate corpus rows (equal keys), a centroid no point chooses (empty
     cluster) and a one-point cluster."""
     import torch
@@ -143,7 +149,7 @@ def test_duplicates_empty_and_singleton_clusters():
     far = np.full((1, d), 50.0, np.float32)             # nobody's nearest centroid
     lone = X[599:600].copy()
     C = np.concatenate([X[rng.choice(599, 4, replace=False)], far, lone]).astype(np.float32)
-    cfg = dict(L=3, m=8, W=0.7, leaves=8, r0=3, B=2, k=5)
+    cfg = dict(L=3, m=8, W=0.7, leaves=8, r0=3, B=2, k=5, score_mode=mode)
     A = rng.standard_normal((cfg["L"] * cfg["m"], d)).astype(np.float32)
     b = (rng.random(cfg["L"] * cfg["m"]) * cfg["W"]).astype(np.float32)
     Q = np.concatenate([X[:40], rng.standard_normal((20, d)).astype(np.float32)])
