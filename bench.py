@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 from paper_2205_00970_b300 import configs, synth  # noqa: E402
 
 METRIC = "queries/s at fixed recall@10 vs FP64 oracle (plain vs served BF16); p50/p99 ms"
-LAUNCHES_PER_SEARCH = 10   # our kernels per lider_search (see the phase list in search.cu)
+LAUNCHES_PER_SEARCH = 13   # our kernels per lider_search (see the phase list in search.cu)
 
 
 def workload_desc(cfg) -> dict:

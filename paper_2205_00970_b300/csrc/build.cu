@@ -92,6 +92,11 @@ __global__ void rank_kernel(const int32_t* __restrict__ pos, const int32_t* __re
     }
 }
 
+__global__ void inverse_ids_kernel(const int64_t* __restrict__ orig_id, int64_t n, int32_t* __restrict__ row_of) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) row_of[orig_id[r]] = (int32_t)r;
+}
+
 // pos[l][row] = row - cl_off[cluster(row)], the cluster-local row index.
 __global__ void local_pos_kernel(const int32_t* __restrict__ sorted_asg, const int64_t* __restrict__ cl_off,
                                  int64_t n, int L, int32_t* __restrict__ pos) {
@@ -251,7 +256,7 @@ int dev_alloc(void** p, size_t bytes, const char* what) {
 void release(lider_index* ix) {
     if (!ix) return;
     void* bufs[] = {ix->X, ix->orig_id, ix->cl_off, ix->C, ix->half_norm, ix->A, ix->bproj,
-                    ix->keys, ix->pos, ix->root, ix->leaf, ix->X_hi, ix->X_lo, ix->rank};
+                    ix->keys, ix->pos, ix->root, ix->leaf, ix->X_hi, ix->X_lo, ix->rank, ix->row_of};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (ix->pool) cudaMemPoolDestroy(ix->pool);
@@ -389,6 +394,9 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
         ALLOC(ix->X_hi, (size_t)n * d * sizeof(float), "corpus TF32 head");
         ALLOC(ix->X_lo, (size_t)n * d * sizeof(float), "corpus TF32 tail");
         ALLOC(ix->rank, (size_t)L * n * sizeof(int32_t), "rank tables");
+        ALLOC(ix->row_of, (size_t)n * sizeof(int32_t), "row of id");
+        inverse_ids_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(ix->orig_id, n, ix->row_of);
+        LIDER_LAUNCH_CHECK("inverse_ids_kernel");
         if ((rc = launch_split_tf32(ix->X, n * d, ix->X_hi, ix->X_lo, st))) return rc;
         rank_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(ix->pos, asg_sorted.as<int32_t>(), ix->cl_off, n, L,
                                                            ix->rank);
@@ -424,7 +432,7 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
     g.W = P->W;
     g.X = ix->X; g.orig_id = ix->orig_id; g.cl_off = ix->cl_off; g.C = ix->C; g.half_norm = ix->half_norm;
     g.A = ix->A; g.bproj = ix->bproj; g.keys = ix->keys; g.pos = ix->pos; g.root = ix->root; g.leaf = ix->leaf;
-    g.X_hi = ix->X_hi; g.X_lo = ix->X_lo; g.rank = ix->rank;
+    g.X_hi = ix->X_hi; g.X_lo = ix->X_lo; g.rank = ix->rank; g.row_of = ix->row_of;
 #undef ALLOC
     guard.ix = nullptr;
     *out = ix;

@@ -61,6 +61,7 @@ struct Geometry {         // everything a search kernel needs, passed by value
     const float* X_hi;      // n x d, TF32 head of X (tensor-core scoring)
     const float* X_lo;      // n x d, X - X_hi
     const int32_t* rank;    // L x n, rank[l][base + p] = sorted position of row p in array l
+    const int32_t* row_of;  // n, row of X holding corpus id i (inverse of orig_id)
 };
 
 }  // namespace lider
@@ -85,6 +86,7 @@ struct lider_index {
     float* X_hi = nullptr;
     float* X_lo = nullptr;
     int32_t* rank = nullptr;
+    int32_t* row_of = nullptr;
     CUtensorMap map_xhi;        // TMA maps over X_hi / X_lo, boxes of 32 x 256
     CUtensorMap map_xlo;
     cudaMemPool_t pool = nullptr;

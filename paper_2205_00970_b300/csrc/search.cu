@@ -737,6 +737,58 @@ __global__ void __launch_bounds__(256) topk_pairs_kernel(const uint64_t* __restr
     }
 }
 
+// Exact re-score of the final lists (tensor-core path).  The tensor cores'
+// FP32 accumulation is biased toward zero by about 1e-5 relative, uniformly,
+// so their scores select the same candidates up to near-ties; the k finally
+// chosen per query are scored again here on the CUDA cores with exactly the
+// SIMT path's arithmetic and re-sorted (score descending, id ascending).
+// One block per query.
+__global__ void __launch_bounds__(256) rescore_kernel(const float* __restrict__ Q, const float* __restrict__ X,
+                                                      const int32_t* __restrict__ row_of, int d, int k,
+                                                      int64_t* __restrict__ ids, float* __restrict__ scores) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    float* qv = reinterpret_cast<float*>(smem);
+    uint64_t* key = reinterpret_cast<uint64_t*>(smem + align_up_dev((size_t)d * 4, 16));
+    const int64_t q = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int d4 = d / 4;
+    for (int i = tid; i < d4; i += blockDim.x)
+        reinterpret_cast<float4*>(qv)[i] = reinterpret_cast<const float4*>(Q + q * d)[i];
+    const int SP = next_pow2_dev(k);
+    __syncthreads();
+    for (int r = warp; r < SP; r += blockDim.x / 32) {
+        const int64_t id = r < k ? ids[q * k + r] : -1;
+        uint64_t kv = ~0ull;
+        if (id >= 0) {
+            const float4* x4 = reinterpret_cast<const float4*>(X + (int64_t)row_of[id] * d);
+            const float4* y4 = reinterpret_cast<const float4*>(qv);
+            float acc = 0.f;
+            for (int i = lane; i < d4; i += 32) {
+                const float4 x = __ldg(x4 + i), y = y4[i];
+                acc = fmaf(x.x, y.x, acc);
+                acc = fmaf(x.y, y.y, acc);
+                acc = fmaf(x.z, y.z, acc);
+                acc = fmaf(x.w, y.w, acc);
+            }
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            kv = ((uint64_t)(~float_order(acc)) << 32) | (uint64_t)(uint32_t)id;
+        }
+        if (lane == 0) key[r] = kv;
+    }
+    __syncthreads();
+    block_bitonic(key, SP);
+    for (int r = tid; r < k; r += blockDim.x) {
+        const uint64_t kv = key[r];
+        if (kv == ~0ull) {
+            ids[q * k + r] = -1;
+            scores[q * k + r] = -INFINITY;
+        } else {
+            ids[q * k + r] = (int64_t)(uint32_t)kv;
+            scores[q * k + r] = float_from_order(~(uint32_t)(kv >> 32));
+        }
+    }
+}
+
 // ------------------------------------------------------------------ merge --
 // Warp per query; lane p < c walks list p (sorted best first).
 __global__ void merge_kernel(const float* __restrict__ pscore, const int64_t* __restrict__ pid, int64_t nq,
@@ -930,7 +982,8 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         ta.pcount = w.pcount;
         const int tc_smem = tc::kSmemBytes + kTcMaxL * tc::kBN * 4;
         LIDER_CUDA_TRY(cudaFuncSetAttribute(tc_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem));
-        tc_score_kernel<<<ix->num_sms, tc::kThreads, tc_smem, st>>>(ix->map_xhi, ix->map_xlo, mqh, mql,
+        // A = queries of the tile (128 rows, box 128), B = cluster rows (256, box 256)
+        tc_score_kernel<<<ix->num_sms, tc::kThreads, tc_smem, st>>>(mqh, mql, ix->map_xhi, ix->map_xlo,
                                                                     (g.d + tc::kBK - 1) / tc::kBK, ta, w.tc_err);
         LIDER_LAUNCH_CHECK("tc_score_kernel");
         const int T_cap = g.L * R;
@@ -986,6 +1039,12 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
     if ((rc = mark(LIDER_PHASE_MERGE))) return rc;
     merge_kernel<<<(unsigned)cdiv(nq * 32, 256), 256, 0, st>>>(w.pscore, w.pid, nq, c, k, out_ids, out_scores);
     LIDER_LAUNCH_CHECK("merge_kernel");
+    if (ix->params.score_mode == LIDER_SCORE_TENSOR) {
+        const size_t rs_smem = align_up((size_t)g.d * 4, 16) + (size_t)next_pow2(k) * 8;
+        LIDER_CUDA_TRY(cudaFuncSetAttribute(rescore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem));
+        rescore_kernel<<<(unsigned)nq, 256, rs_smem, st>>>(Q, g.X, g.row_of, g.d, k, out_ids, out_scores);
+        LIDER_LAUNCH_CHECK("rescore_kernel");
+    }
     return mark(LIDER_NUM_PHASES);
 }
 
