@@ -37,7 +37,8 @@ sys.path.insert(0, ROOT)
 from paper_2205_00970_b300 import configs, synth  # noqa: E402
 
 METRIC = "queries/s at fixed recall@10 vs FP64 oracle (plain vs served BF16); p50/p99 ms"
-LAUNCHES_PER_SEARCH = 13   # our kernels per lider_search (see the phase list in search.cu)
+# our kernels per lider_search (phase list in search.cu; confirmed by the ncu launch list)
+LAUNCHES_PER_SEARCH = {"tensor": 13, "simt": 10}
 
 
 def workload_desc(cfg) -> dict:
@@ -59,12 +60,21 @@ def load_inputs(cfg):
     return X, Q, C, A, b
 
 
+TF32_PER_BF16 = 1.1 / 2.25     # nominal dense TF32 / BF16 tensor rate (B300)
+
+
 def measured_peaks():
+    """(HBM GB/s, BF16 TFLOP/s burst, BF16 TFLOP/s sustained, source)."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return float(d["hbm_gbs"]), "measured"
-    return 6400.0, "fallback"
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), float(d["bf16_tflops_sustained"]), "measured"
+    return 6400.0, 1800.0, 1400.0, "fallback"
+
+
+def fp32_simt_peak_tflops(sm_mhz: float, sms: int = 148) -> float:
+    """FP32 FMA issue peak of the CUDA cores: 128 lanes x 2 flop per SM per clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 class ClockSampler:
@@ -240,8 +250,9 @@ def run_lider(args, cfg):
     X, Q, C, A, b = load_inputs(cfg)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     Xd = t(X)
+    mode = lider.SCORE_TENSOR if args.score == "tensor" else lider.SCORE_SIMT
     idx = lider.Index(Xd, t(C), t(A), t(b), L=cfg["L"], m=cfg["m"], W=cfg["W"], rmi_leaves=cfg["leaves"],
-                      r0=cfg["r0"], B=cfg["B"])
+                      r0=cfg["r0"], B=cfg["B"], score_mode=mode)
     del Xd
     Qd = t(Q)
     k, c, nq = cfg["k"], cfg["c"], cfg["nq"]
@@ -301,16 +312,36 @@ def run_lider(args, cfg):
     e2e_value = world * nq * args.steps / e2e_s
 
     cand = stats["candidates"]
-    alg_bytes = cand * (cfg["d"] * 4 + 4)
+    d = cfg["d"]
+    gather_bytes = cand * (d * 4 + 4)                 # candidate rows + ids, per launch
+    useful_flop = 2.0 * cand * d                      # exact inner products of the candidates
     score_s = phase_ms["score"] / 1e3
-    peak, peak_kind = measured_peaks()
-    achieved = alg_bytes / score_s / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "score_kernel",
-                "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback",
-                "algorithmic_bytes_per_launch": alg_bytes,
-                "note": "gathered rows are reused across the queries of one cluster through L2; "
-                        "DRAM traffic per launch is below the algorithmic bytes"}
+    hbm, bf16, bf16_sus, peak_kind = measured_peaks()
+    src = "MEASURED_PEAKS.json" if peak_kind == "measured" else "fallback figures"
+    if args.score == "tensor":
+        kpad = -(-d // 32) * 32
+        tc_flop = stats["tc_tiles"] * 128 * 256 * kpad * 2.0 * 3     # three TF32 products per FP32 product
+        peak = bf16 * TF32_PER_BF16
+        achieved = tc_flop / score_s / 1e12
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "kernel": "tc_score_kernel",
+                    "peak_source": f"{src}: bf16 burst {bf16} x {TF32_PER_BF16:.3f} (nominal TF32/BF16)",
+                    "tensor_flop_per_launch": tc_flop,
+                    "useful_flop_per_launch": useful_flop,
+                    "useful_tflops": useful_flop / score_s / 1e12,
+                    "gather_bytes_per_launch": gather_bytes,
+                    "gather_gbs_vs_hbm": {"achieved": gather_bytes / score_s / 1e9, "peak": hbm,
+                                          "frac": gather_bytes / score_s / 1e9 / hbm}}
+    else:
+        peak = fp32_simt_peak_tflops(clk.get("sm_max_mhz") or 2032.0)
+        achieved = useful_flop / score_s / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "kernel": "score_group_kernel",
+                    "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x max SM clock",
+                    "useful_flop_per_launch": useful_flop,
+                    "gather_bytes_per_launch": gather_bytes,
+                    "gather_gbs_vs_hbm": {"achieved": gather_bytes / score_s / 1e9, "peak": hbm,
+                                          "frac": gather_bytes / score_s / 1e9 / hbm}}
 
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
@@ -324,7 +355,8 @@ def run_lider(args, cfg):
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": int(Q.nbytes),
                 "d2h_bytes_per_step": int(nq * k * (8 + 4))},
-        "gpu_launches": LAUNCHES_PER_SEARCH * args.steps,
+        "gpu_launches": LAUNCHES_PER_SEARCH[args.score] * args.steps,
+        "score_mode": args.score,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -344,6 +376,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["lider", "reference"], default="lider")
     ap.add_argument("--workload", default="mid")
+    ap.add_argument("--score", choices=["tensor", "simt"], default="tensor")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-queries-per-step", type=int, default=8)

@@ -84,18 +84,21 @@ typedef struct {
     int64_t qkey_clamped;      /* query hash values clamped into the element range */
     int64_t locate_fallback;   /* lower bounds found outside the RMI error window  */
     int64_t empty_pairs;       /* probed clusters that hold no point               */
-    int64_t reserved;
+    int64_t tc_tiles;          /* 128 x 256 tensor-core tiles computed (tensor path) */
 } lider_search_stats;
 
 /* Phases of one search, in order; events[i] is recorded when phase i starts
  * and events[LIDER_NUM_PHASES] when the last one ends. */
-#define LIDER_PHASE_HASH    0   /* query hashkeys (Sec. 4.1)                   */
-#define LIDER_PHASE_ROUTE   1   /* top-c centroids (Sec. 3.3.2)                */
-#define LIDER_PHASE_GROUP   2   /* (query, cluster) pairs bucketed by cluster  */
-#define LIDER_PHASE_LOCATE  3   /* re-scale, RMI, bounded search, expansion    */
-#define LIDER_PHASE_SCORE   4   /* candidate union, exact scores, per-pair top-k */
-#define LIDER_PHASE_MERGE   5   /* per-query merge of the c lists (Sec. 6.2)   */
-#define LIDER_NUM_PHASES    6
+#define LIDER_PHASE_HASH    0   /* query hashkeys (Sec. 4.1)                        */
+#define LIDER_PHASE_ROUTE   1   /* top-c centroids (Sec. 3.3.2)                     */
+#define LIDER_PHASE_GROUP   2   /* (query, cluster) pairs bucketed by cluster       */
+#define LIDER_PHASE_LOCATE  3   /* re-scale, RMI, bounded search, expansion         */
+#define LIDER_PHASE_GATHER  4   /* queries gathered per cluster (tensor path only)  */
+#define LIDER_PHASE_SCORE   5   /* candidate scores (SIMT path: also per-pair top-k)*/
+#define LIDER_PHASE_SELECT  6   /* per-pair top-k (tensor path only)                */
+#define LIDER_PHASE_MERGE   7   /* per-query merge of the c lists (Sec. 6.2); the
+                                   tensor path re-scores the final lists in FP32   */
+#define LIDER_NUM_PHASES    8
 
 /* Optional per-step outputs of a search, for parity checking and profiling.
  * Every member may be NULL; non-NULL array members are device arrays the

@@ -857,6 +857,7 @@ struct Workspace {
     float* qp_hi;               // tensor path: queries in pair order, TF32 head / tail
     float* qp_lo;
     int* tc_err;
+    int ncl;
     size_t zero_bytes;   // counters + cnt, cleared at the start of a search
     size_t total;
 };
@@ -877,6 +878,7 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, int k
     w.pcount = tensor ? (int32_t*)take((size_t)np * 4) : nullptr;
     w.zero_bytes = o;
     w.unit_off = (int32_t*)take((size_t)(g.ncl + 1) * 4);
+    w.ncl = g.ncl;
     w.qp_hi = tensor ? (float*)take((size_t)np * g.d * 4) : nullptr;
     w.qp_lo = tensor ? (float*)take((size_t)np * g.d * 4) : nullptr;
     w.off = (int32_t*)take((size_t)(g.ncl + 1) * 4);
@@ -958,10 +960,11 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         tr ? tr->wlen : nullptr, w.counters);
     LIDER_LAUNCH_CHECK("locate_kernel");
     // 5. candidate union, exact scores and per-pair top-k
-    if ((rc = mark(LIDER_PHASE_SCORE))) return rc;
+    if ((rc = mark(LIDER_PHASE_GATHER))) return rc;
     if (ix->params.score_mode == LIDER_SCORE_TENSOR) {
         qgather_kernel<<<(unsigned)cdiv(np * 32, 256), 256, 0, st>>>(Q, w.pairs, np, c, g.d, w.qp_hi, w.qp_lo);
         LIDER_LAUNCH_CHECK("qgather_kernel");
+        if ((rc = mark(LIDER_PHASE_SCORE))) return rc;
         CUtensorMap mqh, mql;
         if ((rc = make_tensor_map(&mqh, w.qp_hi, np, g.d, tc::kBM))) return rc;
         if ((rc = make_tensor_map(&mql, w.qp_lo, np, g.d, tc::kBM))) return rc;
@@ -986,6 +989,7 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         tc_score_kernel<<<ix->num_sms, tc::kThreads, tc_smem, st>>>(mqh, mql, ix->map_xhi, ix->map_xlo,
                                                                     (g.d + tc::kBK - 1) / tc::kBK, ta, w.tc_err);
         LIDER_LAUNCH_CHECK("tc_score_kernel");
+        if ((rc = mark(LIDER_PHASE_SELECT))) return rc;
         const int T_cap = g.L * R;
         const size_t tk_smem = ((size_t)next_pow2(T_cap) + kCandCap) * 8;
         LIDER_CUDA_TRY(cudaFuncSetAttribute(topk_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -994,6 +998,7 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
                                                               w.pscore, w.pid, tr ? tr->ucount : nullptr, w.counters);
         LIDER_LAUNCH_CHECK("topk_pairs_kernel");
     } else {
+        if ((rc = mark(LIDER_PHASE_SCORE))) return rc;
         ScoreArgs sa;
         sa.g = g;
         sa.Q = Q;
@@ -1034,6 +1039,7 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         const int grid = (int)std::min<int64_t>(max_items, (int64_t)per_sm * ix->num_sms);
         void* kargs[] = {&sa};
         LIDER_CUDA_TRY(cudaLaunchKernel(kern, dim3(grid), dim3(kScoreThreads), kargs, smem, st));
+        if ((rc = mark(LIDER_PHASE_SELECT))) return rc;
     }
     // 6. merge
     if ((rc = mark(LIDER_PHASE_MERGE))) return rc;
@@ -1051,8 +1057,11 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
 int read_stats(const Workspace& w, int64_t nq, int c, lider_search_stats* stats, cudaStream_t st) {
     unsigned long long h[CNT_SLOTS] = {};
     int tc_err = 0;
+    int32_t tiles = 0;
     LIDER_CUDA_TRY(cudaMemcpyAsync(h, w.counters, sizeof(h), cudaMemcpyDeviceToHost, st));
     LIDER_CUDA_TRY(cudaMemcpyAsync(&tc_err, w.tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (w.qp_hi)
+        LIDER_CUDA_TRY(cudaMemcpyAsync(&tiles, w.unit_off + w.ncl, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     LIDER_CUDA_TRY(cudaStreamSynchronize(st));
     if (tc_err)
         return fail(LIDER_ECUDA, "lider_search: tensor-core scoring stopped after a wait timed out (code " +
@@ -1064,7 +1073,7 @@ int read_stats(const Workspace& w, int64_t nq, int c, lider_search_stats* stats,
     stats->qkey_clamped = (int64_t)h[CNT_QCLAMPED];
     stats->locate_fallback = (int64_t)h[CNT_FALLBACK];
     stats->empty_pairs = (int64_t)h[CNT_EMPTY];
-    stats->reserved = 0;
+    stats->tc_tiles = tiles;
     return LIDER_OK;
 }
 

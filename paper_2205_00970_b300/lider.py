@@ -40,10 +40,10 @@ class Params(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in
                 ("n_queries", "pairs", "candidates", "qkey_boundary", "qkey_clamped",
-                 "locate_fallback", "empty_pairs", "reserved")]
+                 "locate_fallback", "empty_pairs", "tc_tiles")]
 
     def as_dict(self) -> dict:
-        return {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "reserved"}
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
 
 
 class Trace(ctypes.Structure):
@@ -51,8 +51,8 @@ class Trace(ctypes.Structure):
                 ("wstart", ctypes.c_void_p), ("wlen", ctypes.c_void_p), ("ucount", ctypes.c_void_p),
                 ("events", ctypes.POINTER(ctypes.c_void_p))]
 
-NUM_PHASES = 6
-PHASES = ("hash", "route", "group", "locate", "score", "merge")
+NUM_PHASES = 8
+PHASES = ("hash", "route", "group", "locate", "gather", "score", "select", "merge")
 
 
 def _load():
