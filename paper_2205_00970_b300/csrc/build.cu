@@ -433,6 +433,9 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
     g.X = ix->X; g.orig_id = ix->orig_id; g.cl_off = ix->cl_off; g.C = ix->C; g.half_norm = ix->half_norm;
     g.A = ix->A; g.bproj = ix->bproj; g.keys = ix->keys; g.pos = ix->pos; g.root = ix->root; g.leaf = ix->leaf;
     g.X_hi = ix->X_hi; g.X_lo = ix->X_lo; g.rank = ix->rank; g.row_of = ix->row_of;
+    int64_t max_nc = 0;
+    for (int j = 0; j < ncl; ++j) max_nc = std::max(max_nc, ix->h_cl_off[j + 1] - ix->h_cl_off[j]);
+    g.max_row_tiles = (int32_t)cdiv(max_nc, 256);
 #undef ALLOC
     guard.ix = nullptr;
     *out = ix;

@@ -46,6 +46,7 @@ struct RmiRoot {          // first stage and re-scaling range of one (cluster, a
 struct Geometry {         // everything a search kernel needs, passed by value
     int64_t n;
     int32_t d, ncl, L, m, F, beta, B, H;
+    int32_t max_row_tiles;  // ceil(largest cluster / 256)
     double W;
     const float* X;         // n x d, rows grouped by cluster
     const int64_t* orig_id; // n

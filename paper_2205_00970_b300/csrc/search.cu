@@ -599,7 +599,25 @@ __global__ void qgather_kernel(const float* __restrict__ Q, const int32_t* __res
 
 constexpr int kTcMaxL = 16;
 
+// One tensor-core tile: A row (first query slot), B row (first corpus row),
+// cluster, and (query tile << 16 | row tile).  Written once per search so the
+// producer, MMA and epilogue warps each read a tile's coordinates with one load.
+__global__ void tc_units_kernel(const int32_t* __restrict__ unit_off, const int32_t* __restrict__ off,
+                                const int64_t* __restrict__ cl_off, int ncl, int4* __restrict__ units) {
+    const int j = blockIdx.x;
+    const int64_t n_c = cl_off[j + 1] - cl_off[j];
+    const int u0 = unit_off[j], u1 = unit_off[j + 1];
+    if (u1 <= u0) return;
+    const int nrt = (int)((n_c + tc::kBN - 1) / tc::kBN);
+    for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+        const int local = u - u0;
+        const int it = local / nrt, rt = local - it * nrt;
+        units[u] = make_int4(off[j] + it * tc::kBM, (int)(cl_off[j] + (int64_t)rt * tc::kBN), j, (it << 16) | rt);
+    }
+}
+
 struct TcArgs {
+    const int4* units;
     const int32_t* unit_off;
     const int32_t* off;
     const int32_t* cnt;
@@ -613,28 +631,13 @@ struct TcArgs {
     int32_t* pcount;
 };
 
-__device__ __forceinline__ void tc_decode(const TcArgs& a, int u, int& j, int& it, int& rt) {
-    int lo = 0, hi = a.ncl - 1;                  // last j with unit_off[j] <= u
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (a.unit_off[mid] <= u) lo = mid; else hi = mid - 1;
-    }
-    j = lo;
-    const int64_t n_c = a.cl_off[j + 1] - a.cl_off[j];
-    const int nrt = (int)((n_c + tc::kBN - 1) / tc::kBN);
-    const int local = u - a.unit_off[j];
-    it = local / nrt;
-    rt = local - it * nrt;
-}
-
 struct TcSched {
     const TcArgs* a;
     __device__ int count() const { return a->unit_off[a->ncl]; }
     __device__ void coords(int u, int& arow, int& brow) const {
-        int j, it, rt;
-        tc_decode(*a, u, j, it, rt);
-        arow = a->off[j] + it * tc::kBM;
-        brow = (int)(a->cl_off[j] + (int64_t)rt * tc::kBN);
+        const int4 t = a->units[u];
+        arow = t.x;
+        brow = t.y;
     }
 };
 
@@ -647,16 +650,29 @@ struct TcEpi {
     uint32_t bits[tc::kBN / 32];
 
     __device__ void begin(int u, int row) {
-        int j, it, rt;
-        tc_decode(*a, u, j, it, rt);
+        const int4 t = a->units[u];
+        const int j = t.z, it = t.w >> 16, rt = t.w & 0xffff;
         const int64_t base = a->cl_off[j];
         const int64_t n_c = a->cl_off[j + 1] - base;
         p0 = rt * tc::kBN;
+        // the tile's sorted positions: two columns per thread and array, all
+        // loads issued before any is used
         const int et = threadIdx.x - 64;          // 0..127 across the epilogue warps
-        for (int idx = et; idx < a->L * tc::kBN; idx += 128) {
-            const int l = idx / tc::kBN, col = idx - l * tc::kBN;
-            const int64_t p = (int64_t)p0 + col;
-            rank_s[idx] = p < n_c ? a->rank[(int64_t)l * a->n + base + p] : -1;
+        int32_t rv[2 * kTcMaxL];
+#pragma unroll
+        for (int l = 0; l < kTcMaxL; ++l) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t p = (int64_t)p0 + et + 128 * h;
+                rv[2 * l + h] = (l < a->L && p < n_c) ? __ldg(a->rank + (int64_t)l * a->n + base + p) : -1;
+            }
+        }
+#pragma unroll
+        for (int l = 0; l < kTcMaxL; ++l) {
+            if (l < a->L) {
+                rank_s[l * tc::kBN + et] = rv[2 * l];
+                rank_s[l * tc::kBN + et + 128] = rv[2 * l + 1];
+            }
         }
         tc::epi_sync();
         const int in_tile = min(tc::kBM, a->cnt[j] - it * tc::kBM);
@@ -854,6 +870,7 @@ struct Workspace {
     uint64_t* pbuf;
     int32_t* pcount;            // tensor path: candidates per pair (cleared)
     int32_t* unit_off;
+    int4* units;                // tensor path: tile descriptors
     float* qp_hi;               // tensor path: queries in pair order, TF32 head / tail
     float* qp_lo;
     int* tc_err;
@@ -879,6 +896,9 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, int k
     w.zero_bytes = o;
     w.unit_off = (int32_t*)take((size_t)(g.ncl + 1) * 4);
     w.ncl = g.ncl;
+    // tiles <= sum_j ceil(cnt_j/128) * ceil(n_c/256) <= (np/128 + ncl) * max_row_tiles
+    w.units = tensor ? (int4*)take((size_t)((np + tc::kBM - 1) / tc::kBM + g.ncl) * (size_t)g.max_row_tiles * 16)
+                     : nullptr;
     w.qp_hi = tensor ? (float*)take((size_t)np * g.d * 4) : nullptr;
     w.qp_lo = tensor ? (float*)take((size_t)np * g.d * 4) : nullptr;
     w.off = (int32_t*)take((size_t)(g.ncl + 1) * 4);
@@ -968,7 +988,10 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         CUtensorMap mqh, mql;
         if ((rc = make_tensor_map(&mqh, w.qp_hi, np, g.d, tc::kBM))) return rc;
         if ((rc = make_tensor_map(&mql, w.qp_lo, np, g.d, tc::kBM))) return rc;
+        tc_units_kernel<<<g.ncl, 128, 0, st>>>(w.unit_off, w.off, g.cl_off, g.ncl, w.units);
+        LIDER_LAUNCH_CHECK("tc_units_kernel");
         TcArgs ta;
+        ta.units = w.units;
         ta.unit_off = w.unit_off;
         ta.off = w.off;
         ta.cnt = w.cnt;
