@@ -38,7 +38,7 @@ from paper_2205_00970_b300 import configs, synth  # noqa: E402
 
 METRIC = "queries/s at fixed recall@10 vs FP64 oracle (plain vs served BF16); p50/p99 ms"
 # our kernels per lider_search (phase list in search.cu; confirmed by the ncu launch list)
-LAUNCHES_PER_SEARCH = {"tensor": 13, "simt": 10}
+LAUNCHES_PER_SEARCH = {"tensor": 14, "simt": 10, "bf16": 14}
 
 
 def workload_desc(cfg) -> dict:
@@ -250,9 +250,9 @@ def run_lider(args, cfg):
     X, Q, C, A, b = load_inputs(cfg)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     Xd = t(X)
-    mode = lider.SCORE_TENSOR if args.score == "tensor" else lider.SCORE_SIMT
+    mode = {"tensor": lider.SCORE_TENSOR, "simt": lider.SCORE_SIMT, "bf16": lider.SCORE_BF16}[args.score]
     idx = lider.Index(Xd, t(C), t(A), t(b), L=cfg["L"], m=cfg["m"], W=cfg["W"], rmi_leaves=cfg["leaves"],
-                      r0=cfg["r0"], B=cfg["B"], score_mode=mode)
+                      r0=cfg["r0"], B=cfg["B"], score_mode=mode, rerank=args.rerank)
     del Xd
     Qd = t(Q)
     k, c, nq = cfg["k"], cfg["c"], cfg["nq"]
@@ -318,14 +318,21 @@ def run_lider(args, cfg):
     score_s = phase_ms["score"] / 1e3
     hbm, bf16, bf16_sus, peak_kind = measured_peaks()
     src = "MEASURED_PEAKS.json" if peak_kind == "measured" else "fallback figures"
-    if args.score == "tensor":
-        kpad = -(-d // 32) * 32
-        tc_flop = stats["tc_tiles"] * 128 * 256 * kpad * 2.0 * 3     # three TF32 products per FP32 product
-        peak = bf16 * TF32_PER_BF16
+    if args.score in ("tensor", "bf16"):
+        if args.score == "tensor":
+            kpad = -(-d // 32) * 32
+            tc_flop = stats["tc_tiles"] * 128 * 256 * kpad * 2.0 * 3   # three TF32 products per FP32 product
+            peak = bf16 * TF32_PER_BF16
+            psrc = f"{src}: bf16 burst {bf16} x {TF32_PER_BF16:.3f} (nominal TF32/BF16)"
+        else:
+            kpad = -(-d // 64) * 64
+            tc_flop = stats["tc_tiles"] * 128 * 256 * kpad * 2.0       # one BF16 product
+            peak = bf16
+            psrc = f"{src}: bf16 burst"
         achieved = tc_flop / score_s / 1e12
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None, "kernel": "tc_score_kernel",
-                    "peak_source": f"{src}: bf16 burst {bf16} x {TF32_PER_BF16:.3f} (nominal TF32/BF16)",
+                    "peak_source": psrc,
                     "tensor_flop_per_launch": tc_flop,
                     "useful_flop_per_launch": useful_flop,
                     "useful_tflops": useful_flop / score_s / 1e12,
@@ -376,7 +383,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["lider", "reference"], default="lider")
     ap.add_argument("--workload", default="mid")
-    ap.add_argument("--score", choices=["tensor", "simt"], default="tensor")
+    ap.add_argument("--score", choices=["tensor", "simt", "bf16"], default="tensor")
+    ap.add_argument("--rerank", type=int, default=4, help="served BF16 form: shortlist = rerank * k")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-queries-per-step", type=int, default=8)

@@ -42,6 +42,9 @@ extern "C" {
 /* How candidates are scored (the results are the same within FP32 rounding). */
 #define LIDER_SCORE_TENSOR 0   /* tcgen05 tensor cores, 3 TF32 products per FP32 product */
 #define LIDER_SCORE_SIMT   1   /* FP32 FMA on the CUDA cores                             */
+#define LIDER_SCORE_BF16   2   /* served form: BF16 corpus copy scored on the tensor
+                                  cores (FP32 accumulation), then an FP32 re-rank of a
+                                  shortlist of rerank * k candidates per query       */
 
 /* Implementation caps (checked; LIDER_ELIMIT beyond them). */
 #define LIDER_MAX_L        32      /* hashkey arrays per core model (H)     */
@@ -62,7 +65,10 @@ typedef struct lider_index lider_index;   /* opaque; owns its device memory */
  *        (Sec. 4.2); floor(64/m) * B must be <= 56;
  *   hash_kind = LIDER_HASH_PSTABLE;
  *   W  = p-stable bucket width (> 0);
- *   score_mode = LIDER_SCORE_TENSOR (needs L <= 16) or LIDER_SCORE_SIMT. */
+ *   score_mode = LIDER_SCORE_TENSOR, LIDER_SCORE_SIMT or LIDER_SCORE_BF16
+ *        (tensor modes need L <= 16; BF16 needs d % 8 == 0);
+ *   rerank = shortlist factor of LIDER_SCORE_BF16: rerank * k candidates per
+ *        query are re-scored in FP32 (0 means 4). */
 typedef struct {
     int32_t L;
     int32_t m;
@@ -72,7 +78,7 @@ typedef struct {
     int32_t hash_kind;
     double  W;
     int32_t score_mode;
-    int32_t reserved;
+    int32_t rerank;
 } lider_params;
 
 /* Counters of one search (host struct, filled when the call returns). */
@@ -221,13 +227,14 @@ int lider_export_rmi(const lider_index* index, int32_t cluster, int32_t array,
                      uint64_t* minmax_host, double* root_host, double* leaf_host,
                      int32_t* err_host);
 
-/* Self-test of the tensor-core scoring engine (tcgen05 + TMA + TMEM, three
- * TF32 products per FP32 product): out[m x n] = A[m x d] . B[n x d]^T for
- * device row-major FP32 A, B, out with 1 <= m <= 128, 1 <= n <= 256,
- * d % 4 == 0.  Synchronous; allocates its own scratch.  LIDER_ECUDA if an
- * internal wait times out (the kernel then exits cleanly). */
+/* Self-test of the tensor-core scoring engine (tcgen05 + TMA + TMEM):
+ * out[m x n] = A[m x d] . B[n x d]^T for device row-major FP32 A, B, out with
+ * 1 <= m <= 128, 1 <= n <= 256.  kind 0: three TF32 products per FP32 product
+ * (d % 4 == 0); kind 1: A and B rounded to BF16, one product, FP32
+ * accumulation (d % 8 == 0).  Synchronous; allocates its own scratch.
+ * LIDER_ECUDA if an internal wait times out (the kernel then exits cleanly). */
 int lider_debug_tc_tile(const float* A, int32_t m, const float* B, int32_t n, int32_t d,
-                        float* out, void* stream);
+                        int32_t kind, float* out, void* stream);
 
 /* Release the index and its device memory.  NULL is accepted. */
 void lider_free(lider_index* index);

@@ -256,7 +256,7 @@ int dev_alloc(void** p, size_t bytes, const char* what) {
 void release(lider_index* ix) {
     if (!ix) return;
     void* bufs[] = {ix->X, ix->orig_id, ix->cl_off, ix->C, ix->half_norm, ix->A, ix->bproj,
-                    ix->keys, ix->pos, ix->root, ix->leaf, ix->X_hi, ix->X_lo, ix->rank, ix->row_of};
+                    ix->keys, ix->pos, ix->root, ix->leaf, ix->X_hi, ix->X_lo, ix->rank, ix->row_of, ix->X_bf16};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (ix->pool) cudaMemPoolDestroy(ix->pool);
@@ -282,10 +282,13 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
     if ((int64_t)beta * P->B > 56) return fail(LIDER_EINVAL, "lider_build: floor(64/m) * B must be <= 56");
     if (P->L > LIDER_MAX_L) return fail(LIDER_ELIMIT, "lider_build: L exceeds LIDER_MAX_L");
     if (P->rmi_leaves > (1 << 24)) return fail(LIDER_ELIMIT, "lider_build: rmi_leaves too large");
-    if (P->score_mode != LIDER_SCORE_TENSOR && P->score_mode != LIDER_SCORE_SIMT)
+    if (P->score_mode != LIDER_SCORE_TENSOR && P->score_mode != LIDER_SCORE_SIMT && P->score_mode != LIDER_SCORE_BF16)
         return fail(LIDER_EINVAL, "lider_build: unknown score_mode");
-    if (P->score_mode == LIDER_SCORE_TENSOR && P->L > 16)
+    if (P->score_mode != LIDER_SCORE_SIMT && P->L > 16)
         return fail(LIDER_ELIMIT, "lider_build: tensor-core scoring supports L <= 16 (use LIDER_SCORE_SIMT)");
+    if (P->score_mode == LIDER_SCORE_BF16 && d % 8 != 0)
+        return fail(LIDER_EINVAL, "lider_build: LIDER_SCORE_BF16 needs d % 8 == 0");
+    if (P->rerank < 0 || P->rerank > 64) return fail(LIDER_EINVAL, "lider_build: rerank must be in [0, 64]");
 
     int dev = 0;
     LIDER_CUDA_TRY(cudaGetDevice(&dev));
@@ -296,6 +299,7 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
     } guard{ix};
     ix->device = dev;
     ix->params = *P;
+    if (ix->params.rerank == 0) ix->params.rerank = 4;
     LIDER_CUDA_TRY(cudaDeviceGetAttribute(&ix->num_sms, cudaDevAttrMultiProcessorCount, dev));
     const int L = P->L, m = P->m, H = L * m, F = P->rmi_leaves;
 
@@ -389,20 +393,27 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
         }
     }
 
-    // tensor-core scoring: TF32 split of the corpus, rank tables, TMA maps
-    if (P->score_mode == LIDER_SCORE_TENSOR) {
-        ALLOC(ix->X_hi, (size_t)n * d * sizeof(float), "corpus TF32 head");
-        ALLOC(ix->X_lo, (size_t)n * d * sizeof(float), "corpus TF32 tail");
+    // tensor-core scoring: TF32 split (or BF16 copy) of the corpus, rank
+    // tables, inverse ids, TMA maps
+    if (P->score_mode != LIDER_SCORE_SIMT) {
+        if (P->score_mode == LIDER_SCORE_TENSOR) {
+            ALLOC(ix->X_hi, (size_t)n * d * sizeof(float), "corpus TF32 head");
+            ALLOC(ix->X_lo, (size_t)n * d * sizeof(float), "corpus TF32 tail");
+            if ((rc = launch_split_tf32(ix->X, n * d, ix->X_hi, ix->X_lo, st))) return rc;
+            if ((rc = make_tensor_map(&ix->map_xhi, ix->X_hi, n, d, 256))) return rc;
+            if ((rc = make_tensor_map(&ix->map_xlo, ix->X_lo, n, d, 256))) return rc;
+        } else {
+            ALLOC(ix->X_bf16, (size_t)n * d * sizeof(uint16_t), "corpus BF16 copy");
+            if ((rc = launch_to_bf16(ix->X, n * d, ix->X_bf16, st))) return rc;
+            if ((rc = make_tensor_map(&ix->map_xbf16, ix->X_bf16, n, d, 256, true))) return rc;
+        }
         ALLOC(ix->rank, (size_t)L * n * sizeof(int32_t), "rank tables");
         ALLOC(ix->row_of, (size_t)n * sizeof(int32_t), "row of id");
         inverse_ids_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(ix->orig_id, n, ix->row_of);
         LIDER_LAUNCH_CHECK("inverse_ids_kernel");
-        if ((rc = launch_split_tf32(ix->X, n * d, ix->X_hi, ix->X_lo, st))) return rc;
         rank_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(ix->pos, asg_sorted.as<int32_t>(), ix->cl_off, n, L,
                                                            ix->rank);
         LIDER_LAUNCH_CHECK("rank_kernel");
-        if ((rc = make_tensor_map(&ix->map_xhi, ix->X_hi, n, d, 256))) return rc;
-        if ((rc = make_tensor_map(&ix->map_xlo, ix->X_lo, n, d, 256))) return rc;
     }
 
     // 5. RMI per (cluster, array)
@@ -432,7 +443,7 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
     g.W = P->W;
     g.X = ix->X; g.orig_id = ix->orig_id; g.cl_off = ix->cl_off; g.C = ix->C; g.half_norm = ix->half_norm;
     g.A = ix->A; g.bproj = ix->bproj; g.keys = ix->keys; g.pos = ix->pos; g.root = ix->root; g.leaf = ix->leaf;
-    g.X_hi = ix->X_hi; g.X_lo = ix->X_lo; g.rank = ix->rank; g.row_of = ix->row_of;
+    g.X_hi = ix->X_hi; g.X_lo = ix->X_lo; g.rank = ix->rank; g.row_of = ix->row_of; g.X_bf16 = ix->X_bf16;
     int64_t max_nc = 0;
     for (int j = 0; j < ncl; ++j) max_nc = std::max(max_nc, ix->h_cl_off[j + 1] - ix->h_cl_off[j]);
     g.max_row_tiles = (int32_t)cdiv(max_nc, 256);

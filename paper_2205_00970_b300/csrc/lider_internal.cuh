@@ -63,6 +63,7 @@ struct Geometry {         // everything a search kernel needs, passed by value
     const float* X_lo;      // n x d, X - X_hi
     const int32_t* rank;    // L x n, rank[l][base + p] = sorted position of row p in array l
     const int32_t* row_of;  // n, row of X holding corpus id i (inverse of orig_id)
+    const uint16_t* X_bf16; // n x d, BF16 copy of X (served mode)
 };
 
 }  // namespace lider
@@ -88,6 +89,8 @@ struct lider_index {
     float* X_lo = nullptr;
     int32_t* rank = nullptr;
     int32_t* row_of = nullptr;
+    uint16_t* X_bf16 = nullptr;
+    CUtensorMap map_xbf16;      // TMA map over X_bf16, boxes of 64 x 256
     CUtensorMap map_xhi;        // TMA maps over X_hi / X_lo, boxes of 32 x 256
     CUtensorMap map_xlo;
     cudaMemPool_t pool = nullptr;
@@ -200,7 +203,8 @@ int launch_hash_t(const float* X, int64_t n, int d, const float* A, const float*
 int launch_scores(const float* X, int64_t n, int d, const float* C, const double* half_norm,
                   int ncl, double* out, cudaStream_t s);
 int launch_split_tf32(const float* x, int64_t n, float* hi, float* lo, cudaStream_t s);
-int make_tensor_map(CUtensorMap* map, const float* base, int64_t rows, int d, int box_rows);
+int make_tensor_map(CUtensorMap* map, const void* base, int64_t rows, int d, int box_rows, bool bf16 = false);
+int launch_to_bf16(const float* x, int64_t n, uint16_t* out, cudaStream_t s);
 int launch_pack(const double* t, int64_t n, int L, int m, int beta, int64_t row_offset,
                 int64_t key_stride_row, int64_t key_stride_arr, uint64_t* keys,
                 unsigned long long* n_boundary, unsigned long long* n_clamped, cudaStream_t s);

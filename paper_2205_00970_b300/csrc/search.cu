@@ -23,6 +23,8 @@
 #include <algorithm>
 #include <mutex>
 
+#include <cuda_bf16.h>
+
 #include "lider_internal.cuh"
 #include "tc.cuh"
 
@@ -597,6 +599,18 @@ __global__ void qgather_kernel(const float* __restrict__ Q, const int32_t* __res
     }
 }
 
+// Served form: the queries in pair order, rounded to BF16.
+__global__ void qgather_bf16_kernel(const float* __restrict__ Q, const int32_t* __restrict__ pairs, int64_t np, int c,
+                                    int d, uint16_t* __restrict__ qp) {
+    const int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (slot >= np) return;
+    const int64_t q = pairs[slot] / c;
+    const float* src = Q + q * d;
+    uint16_t* dst = qp + slot * d;
+    for (int i = lane; i < d; i += 32) dst[i] = __bfloat16_as_ushort(__float2bfloat16_rn(src[i]));
+}
+
 constexpr int kTcMaxL = 16;
 
 // One tensor-core tile: A row (first query slot), B row (first corpus row),
@@ -628,6 +642,8 @@ struct TcArgs {
     int64_t n;
     int ncl, L, R, T_cap;
     uint64_t* pbuf;
+    int64_t* sl_ids;            // served form: per-query shortlist (nq x ks)
+    float* sl_scores;
     int32_t* pcount;
 };
 
@@ -715,6 +731,7 @@ struct TcEpi {
     __device__ void done(int, int) { tc::epi_sync(); }   // the rank tile may now be reloaded
 };
 
+template <class Kind>
 __global__ void __launch_bounds__(tc::kThreads, 1)
     tc_score_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                     const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, int kchunks,
@@ -726,7 +743,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     TcEpi epi;
     epi.a = &args;
     epi.rank_s = rank_s;
-    tc::gemm_tiles(&mAhi, &mAlo, &mBhi, &mBlo, kchunks, sched, epi, err, smem, ctl);
+    tc::gemm_tiles<Kind>(&mAhi, &mAlo, &mBhi, &mBlo, kchunks, sched, epi, err, smem, ctl);
 }
 
 // Per pair: top k of its candidate list (bucket selection, see block_topk).
@@ -753,15 +770,17 @@ __global__ void __launch_bounds__(256) topk_pairs_kernel(const uint64_t* __restr
     }
 }
 
-// Exact re-score of the final lists (tensor-core path).  The tensor cores'
+// Exact re-score of the final lists (tensor-core paths).  The tensor cores'
 // FP32 accumulation is biased toward zero by about 1e-5 relative, uniformly,
-// so their scores select the same candidates up to near-ties; the k finally
-// chosen per query are scored again here on the CUDA cores with exactly the
-// SIMT path's arithmetic and re-sorted (score descending, id ascending).
-// One block per query.
+// so 3xTF32 scores select the same candidates up to near-ties, and the served
+// BF16 form selects a shortlist of S = rerank * k; the S chosen per query are
+// scored again here on the CUDA cores with exactly the SIMT path's arithmetic,
+// re-sorted (score descending, id ascending) and the best k kept.  One block
+// per query; in_ids may alias out_ids when S == k.
 __global__ void __launch_bounds__(256) rescore_kernel(const float* __restrict__ Q, const float* __restrict__ X,
-                                                      const int32_t* __restrict__ row_of, int d, int k,
-                                                      int64_t* __restrict__ ids, float* __restrict__ scores) {
+                                                      const int32_t* __restrict__ row_of, int d, int S,
+                                                      const int64_t* in_ids, int k, int64_t* out_ids,
+                                                      float* out_scores) {
     extern __shared__ __align__(16) unsigned char smem[];
     float* qv = reinterpret_cast<float*>(smem);
     uint64_t* key = reinterpret_cast<uint64_t*>(smem + align_up_dev((size_t)d * 4, 16));
@@ -770,10 +789,10 @@ __global__ void __launch_bounds__(256) rescore_kernel(const float* __restrict__ 
     const int d4 = d / 4;
     for (int i = tid; i < d4; i += blockDim.x)
         reinterpret_cast<float4*>(qv)[i] = reinterpret_cast<const float4*>(Q + q * d)[i];
-    const int SP = next_pow2_dev(k);
+    const int SP = next_pow2_dev(S);
     __syncthreads();
     for (int r = warp; r < SP; r += blockDim.x / 32) {
-        const int64_t id = r < k ? ids[q * k + r] : -1;
+        const int64_t id = r < S ? in_ids[q * S + r] : -1;
         uint64_t kv = ~0ull;
         if (id >= 0) {
             const float4* x4 = reinterpret_cast<const float4*>(X + (int64_t)row_of[id] * d);
@@ -796,28 +815,29 @@ __global__ void __launch_bounds__(256) rescore_kernel(const float* __restrict__ 
     for (int r = tid; r < k; r += blockDim.x) {
         const uint64_t kv = key[r];
         if (kv == ~0ull) {
-            ids[q * k + r] = -1;
-            scores[q * k + r] = -INFINITY;
+            out_ids[q * k + r] = -1;
+            out_scores[q * k + r] = -INFINITY;
         } else {
-            ids[q * k + r] = (int64_t)(uint32_t)kv;
-            scores[q * k + r] = float_from_order(~(uint32_t)(kv >> 32));
+            out_ids[q * k + r] = (int64_t)(uint32_t)kv;
+            out_scores[q * k + r] = float_from_order(~(uint32_t)(kv >> 32));
         }
     }
 }
 
 // ------------------------------------------------------------------ merge --
-// Warp per query; lane p < c walks list p (sorted best first).
+// Warp per query; lane p < c walks list p (kp entries, sorted best first);
+// the ks best heads are written out (score descending, id ascending).
 __global__ void merge_kernel(const float* __restrict__ pscore, const int64_t* __restrict__ pid, int64_t nq,
-                             int c, int k, int64_t* __restrict__ out_ids, float* __restrict__ out_scores) {
+                             int c, int kp, int ks, int64_t* __restrict__ out_ids, float* __restrict__ out_scores) {
     const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (q >= nq) return;
-    const int64_t lbase = (q * c + lane) * (int64_t)k;
+    const int64_t lbase = (q * c + lane) * (int64_t)kp;
     int head = 0;
     float hs = -INFINITY;
     int64_t hid = -1;
     if (lane < c) { hs = pscore[lbase]; hid = pid[lbase]; }
-    for (int r = 0; r < k; ++r) {
+    for (int r = 0; r < ks; ++r) {
         // best head: score desc, id asc; exhausted lists (id -1) lose
         float bs = hs;
         int64_t bid = hid;
@@ -833,13 +853,13 @@ __global__ void merge_kernel(const float* __restrict__ pscore, const int64_t* __
             if (take) { bs = os; bid = oid; bl = ol; }
         }
         if (lane == 0) {
-            out_ids[q * k + r] = bid;
-            out_scores[q * k + r] = bid < 0 ? -INFINITY : bs;
+            out_ids[q * ks + r] = bid;
+            out_scores[q * ks + r] = bid < 0 ? -INFINITY : bs;
         }
         if (bid < 0) continue;
         if (lane == bl) {
             ++head;
-            if (head < k) { hs = pscore[lbase + head]; hid = pid[lbase + head]; }
+            if (head < kp) { hs = pscore[lbase + head]; hid = pid[lbase + head]; }
             else { hs = -INFINITY; hid = -1; }
         }
     }
@@ -868,6 +888,8 @@ struct Workspace {
     float* pscore;
     int64_t* pid;
     uint64_t* pbuf;
+    int64_t* sl_ids;            // served form: per-query shortlist (nq x ks)
+    float* sl_scores;
     int32_t* pcount;            // tensor path: candidates per pair (cleared)
     int32_t* unit_off;
     int4* units;                // tensor path: tile descriptors
@@ -880,7 +902,29 @@ struct Workspace {
 };
 
 // Carve one allocation into the search buffers (base == nullptr: sizes only).
-Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, int k, int R, bool tensor) {
+// List lengths of one search: per pair (kp) and per query before the final
+// re-score (ks).  The served BF16 form keeps a shortlist of rerank * k.
+struct Shape {
+    int mode, R, kp, ks;
+};
+
+Shape search_shape(const lider_index* ix, int k) {
+    Shape sh;
+    sh.mode = ix->params.score_mode;
+    sh.R = ix->params.r0 * k;
+    const int T_cap = ix->g.L * sh.R;
+    if (sh.mode == LIDER_SCORE_BF16) {
+        sh.ks = ix->params.rerank * k;
+        sh.kp = std::min(sh.ks, T_cap);
+    } else {
+        sh.ks = k;
+        sh.kp = k;
+    }
+    return sh;
+}
+
+// Carve one allocation into the search buffers (base == nullptr: sizes only).
+Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, const Shape& sh) {
     Workspace w{};
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -888,6 +932,7 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, int k
         o = align_up(o + bytes, 256);
         return p;
     };
+    const bool tensor = sh.mode != LIDER_SCORE_SIMT;
     const int64_t np = nq * c;
     w.counters = (unsigned long long*)take(CNT_SLOTS * sizeof(unsigned long long));
     w.cnt = (int32_t*)take((size_t)g.ncl * 4);
@@ -899,8 +944,9 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, int k
     // tiles <= sum_j ceil(cnt_j/128) * ceil(n_c/256) <= (np/128 + ncl) * max_row_tiles
     w.units = tensor ? (int4*)take((size_t)((np + tc::kBM - 1) / tc::kBM + g.ncl) * (size_t)g.max_row_tiles * 16)
                      : nullptr;
-    w.qp_hi = tensor ? (float*)take((size_t)np * g.d * 4) : nullptr;
-    w.qp_lo = tensor ? (float*)take((size_t)np * g.d * 4) : nullptr;
+    const size_t qelem = sh.mode == LIDER_SCORE_BF16 ? 2 : 4;
+    w.qp_hi = tensor ? (float*)take((size_t)np * g.d * qelem) : nullptr;
+    w.qp_lo = sh.mode == LIDER_SCORE_TENSOR ? (float*)take((size_t)np * g.d * 4) : nullptr;
     w.off = (int32_t*)take((size_t)(g.ncl + 1) * 4);
     w.cursor = (int32_t*)take((size_t)g.ncl * 4);
     w.item_off = (int32_t*)take((size_t)(g.ncl + 1) * 4);
@@ -911,9 +957,11 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, int k
     w.pairs = (int32_t*)take((size_t)np * 4);
     w.wstart = (int32_t*)take((size_t)np * g.L * 4);
     w.wlen = (int32_t*)take((size_t)np * g.L * 4);
-    w.pscore = (float*)take((size_t)np * k * 4);
-    w.pid = (int64_t*)take((size_t)np * k * 8);
-    w.pbuf = (uint64_t*)take((size_t)np * g.L * R * 8);
+    w.pscore = (float*)take((size_t)np * sh.kp * 4);
+    w.pid = (int64_t*)take((size_t)np * sh.kp * 8);
+    w.pbuf = (uint64_t*)take((size_t)np * g.L * sh.R * 8);
+    w.sl_ids = sh.mode == LIDER_SCORE_BF16 ? (int64_t*)take((size_t)nq * sh.ks * 8) : nullptr;
+    w.sl_scores = sh.mode == LIDER_SCORE_BF16 ? (float*)take((size_t)nq * sh.ks * 4) : nullptr;
     w.total = o;
     return w;
 }
@@ -929,6 +977,8 @@ int check_search_args(const lider_index* ix, const float* Q, int64_t nq, int k, 
     const int64_t R = (int64_t)ix->params.r0 * k;
     if (R * ix->g.L > LIDER_MAX_LR) return fail(LIDER_ELIMIT, "lider_search: L * r0 * k exceeds LIDER_MAX_LR");
     if (nq * c > (int64_t)INT32_MAX) return fail(LIDER_ELIMIT, "lider_search: nq * c exceeds 2^31-1");
+    if (ix->params.score_mode == LIDER_SCORE_BF16 && (int64_t)ix->params.rerank * k > 8192)
+        return fail(LIDER_ELIMIT, "lider_search: rerank * k exceeds 8192");
     if (nq > 0 && (!Q || !ids || !scores)) return fail(LIDER_EINVAL, "lider_search: NULL buffer");
     int dev = -1;
     LIDER_CUDA_TRY(cudaGetDevice(&dev));
@@ -980,14 +1030,24 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         tr ? tr->wlen : nullptr, w.counters);
     LIDER_LAUNCH_CHECK("locate_kernel");
     // 5. candidate union, exact scores and per-pair top-k
+    const Shape sh = search_shape(ix, k);
     if ((rc = mark(LIDER_PHASE_GATHER))) return rc;
-    if (ix->params.score_mode == LIDER_SCORE_TENSOR) {
-        qgather_kernel<<<(unsigned)cdiv(np * 32, 256), 256, 0, st>>>(Q, w.pairs, np, c, g.d, w.qp_hi, w.qp_lo);
-        LIDER_LAUNCH_CHECK("qgather_kernel");
-        if ((rc = mark(LIDER_PHASE_SCORE))) return rc;
+    if (sh.mode != LIDER_SCORE_SIMT) {
+        const bool bf16 = sh.mode == LIDER_SCORE_BF16;
         CUtensorMap mqh, mql;
-        if ((rc = make_tensor_map(&mqh, w.qp_hi, np, g.d, tc::kBM))) return rc;
-        if ((rc = make_tensor_map(&mql, w.qp_lo, np, g.d, tc::kBM))) return rc;
+        if (bf16) {
+            uint16_t* qp = reinterpret_cast<uint16_t*>(w.qp_hi);
+            qgather_bf16_kernel<<<(unsigned)cdiv(np * 32, 256), 256, 0, st>>>(Q, w.pairs, np, c, g.d, qp);
+            LIDER_LAUNCH_CHECK("qgather_bf16_kernel");
+            if ((rc = make_tensor_map(&mqh, qp, np, g.d, tc::kBM, true))) return rc;
+            mql = mqh;
+        } else {
+            qgather_kernel<<<(unsigned)cdiv(np * 32, 256), 256, 0, st>>>(Q, w.pairs, np, c, g.d, w.qp_hi, w.qp_lo);
+            LIDER_LAUNCH_CHECK("qgather_kernel");
+            if ((rc = make_tensor_map(&mqh, w.qp_hi, np, g.d, tc::kBM))) return rc;
+            if ((rc = make_tensor_map(&mql, w.qp_lo, np, g.d, tc::kBM))) return rc;
+        }
+        if ((rc = mark(LIDER_PHASE_SCORE))) return rc;
         tc_units_kernel<<<g.ncl, 128, 0, st>>>(w.unit_off, w.off, g.cl_off, g.ncl, w.units);
         LIDER_LAUNCH_CHECK("tc_units_kernel");
         TcArgs ta;
@@ -1007,18 +1067,29 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         ta.pbuf = w.pbuf;
         ta.pcount = w.pcount;
         const int tc_smem = tc::kSmemBytes + kTcMaxL * tc::kBN * 4;
-        LIDER_CUDA_TRY(cudaFuncSetAttribute(tc_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem));
         // A = queries of the tile (128 rows, box 128), B = cluster rows (256, box 256)
-        tc_score_kernel<<<ix->num_sms, tc::kThreads, tc_smem, st>>>(mqh, mql, ix->map_xhi, ix->map_xlo,
-                                                                    (g.d + tc::kBK - 1) / tc::kBK, ta, w.tc_err);
+        if (bf16) {
+            LIDER_CUDA_TRY(cudaFuncSetAttribute(tc_score_kernel<tc::KindBf16>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem));
+            tc_score_kernel<tc::KindBf16><<<ix->num_sms, tc::kThreads, tc_smem, st>>>(
+                mqh, mql, ix->map_xbf16, ix->map_xbf16, (g.d + tc::KindBf16::kBK - 1) / tc::KindBf16::kBK, ta,
+                w.tc_err);
+        } else {
+            LIDER_CUDA_TRY(cudaFuncSetAttribute(tc_score_kernel<tc::KindTf32x3>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem));
+            tc_score_kernel<tc::KindTf32x3><<<ix->num_sms, tc::kThreads, tc_smem, st>>>(
+                mqh, mql, ix->map_xhi, ix->map_xlo, (g.d + tc::KindTf32x3::kBK - 1) / tc::KindTf32x3::kBK, ta,
+                w.tc_err);
+        }
         LIDER_LAUNCH_CHECK("tc_score_kernel");
         if ((rc = mark(LIDER_PHASE_SELECT))) return rc;
         const int T_cap = g.L * R;
         const size_t tk_smem = ((size_t)next_pow2(T_cap) + kCandCap) * 8;
         LIDER_CUDA_TRY(cudaFuncSetAttribute(topk_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)tk_smem));
-        topk_pairs_kernel<<<(unsigned)np, 256, tk_smem, st>>>(w.pbuf, T_cap, w.pcount, w.route, g.cl_off, g.orig_id, k,
-                                                              w.pscore, w.pid, tr ? tr->ucount : nullptr, w.counters);
+        topk_pairs_kernel<<<(unsigned)np, 256, tk_smem, st>>>(w.pbuf, T_cap, w.pcount, w.route, g.cl_off, g.orig_id,
+                                                              sh.kp, w.pscore, w.pid, tr ? tr->ucount : nullptr,
+                                                              w.counters);
         LIDER_LAUNCH_CHECK("topk_pairs_kernel");
     } else {
         if ((rc = mark(LIDER_PHASE_SCORE))) return rc;
@@ -1064,14 +1135,18 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         LIDER_CUDA_TRY(cudaLaunchKernel(kern, dim3(grid), dim3(kScoreThreads), kargs, smem, st));
         if ((rc = mark(LIDER_PHASE_SELECT))) return rc;
     }
-    // 6. merge
+    // 6. merge, then (tensor paths) the exact FP32 re-score of the final lists
     if ((rc = mark(LIDER_PHASE_MERGE))) return rc;
-    merge_kernel<<<(unsigned)cdiv(nq * 32, 256), 256, 0, st>>>(w.pscore, w.pid, nq, c, k, out_ids, out_scores);
+    const bool shortlist = sh.mode == LIDER_SCORE_BF16;
+    int64_t* m_ids = shortlist ? w.sl_ids : out_ids;
+    float* m_sc = shortlist ? w.sl_scores : out_scores;
+    merge_kernel<<<(unsigned)cdiv(nq * 32, 256), 256, 0, st>>>(w.pscore, w.pid, nq, c, sh.kp, sh.ks, m_ids, m_sc);
     LIDER_LAUNCH_CHECK("merge_kernel");
-    if (ix->params.score_mode == LIDER_SCORE_TENSOR) {
-        const size_t rs_smem = align_up((size_t)g.d * 4, 16) + (size_t)next_pow2(k) * 8;
+    if (sh.mode != LIDER_SCORE_SIMT) {
+        const size_t rs_smem = align_up((size_t)g.d * 4, 16) + (size_t)next_pow2(sh.ks) * 8;
         LIDER_CUDA_TRY(cudaFuncSetAttribute(rescore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem));
-        rescore_kernel<<<(unsigned)nq, 256, rs_smem, st>>>(Q, g.X, g.row_of, g.d, k, out_ids, out_scores);
+        rescore_kernel<<<(unsigned)nq, 256, rs_smem, st>>>(Q, g.X, g.row_of, g.d, sh.ks, m_ids, k, out_ids,
+                                                           out_scores);
         LIDER_LAUNCH_CHECK("rescore_kernel");
     }
     return mark(LIDER_NUM_PHASES);
@@ -1119,10 +1194,10 @@ int search_entry(const lider_index* ix, const float* Q, int64_t nq, int k, int c
     if (stats) *stats = lider_search_stats{};
     if (nq == 0) return LIDER_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    Workspace sz = carve(nullptr, ix->g, nq, c, k, ix->params.r0 * k, ix->params.score_mode == LIDER_SCORE_TENSOR);
+    Workspace sz = carve(nullptr, ix->g, nq, c, search_shape(ix, k));
     void* mem = nullptr;
     if ((rc = pool_alloc(ix, &mem, sz.total, st))) return rc;
-    Workspace w = carve((unsigned char*)mem, ix->g, nq, c, k, ix->params.r0 * k, ix->params.score_mode == LIDER_SCORE_TENSOR);
+    Workspace w = carve((unsigned char*)mem, ix->g, nq, c, search_shape(ix, k));
     rc = enqueue_search(ix, Q, nq, k, c, out_ids, out_scores, tr, w, st);
     if (rc == LIDER_OK && stats) rc = read_stats(w, nq, c, stats, st);
     cudaError_t e = cudaFreeAsync(mem, st);
@@ -1139,7 +1214,7 @@ int search_host_entry(const lider_index* ix, const float* Qh, int64_t nq, int k,
     cudaStream_t st = (cudaStream_t)stream;
     const size_t qb = (size_t)nq * ix->g.d * 4, ib = (size_t)nq * k * 8, sb = (size_t)nq * k * 4;
     const size_t o_ids = align_up(qb, 256), o_sc = align_up(o_ids + ib, 256);
-    Workspace sz = carve(nullptr, ix->g, nq, c, k, ix->params.r0 * k, ix->params.score_mode == LIDER_SCORE_TENSOR);
+    Workspace sz = carve(nullptr, ix->g, nq, c, search_shape(ix, k));
     const size_t o_ws = align_up(o_sc + sb, 256);
     void* mem = nullptr;
     if ((rc = pool_alloc(ix, &mem, o_ws + sz.total, st))) return rc;
@@ -1147,7 +1222,7 @@ int search_host_entry(const lider_index* ix, const float* Qh, int64_t nq, int k,
     float* Qd = (float*)m;
     int64_t* idd = (int64_t*)(m + o_ids);
     float* scd = (float*)(m + o_sc);
-    Workspace w = carve(m + o_ws, ix->g, nq, c, k, ix->params.r0 * k, ix->params.score_mode == LIDER_SCORE_TENSOR);
+    Workspace w = carve(m + o_ws, ix->g, nq, c, search_shape(ix, k));
     cudaError_t e = cudaMemcpyAsync(Qd, Qh, qb, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync(queries)");
     if (!rc) rc = enqueue_search(ix, Qd, nq, k, c, idd, scd, nullptr, w, st);
@@ -1214,8 +1289,7 @@ int search_noalloc_impl(const lider_index* ix, const float* Q, int64_t nq, int k
     if (rc) return rc;
     if (stats) *stats = lider_search_stats{};
     if (nq == 0) return LIDER_OK;
-    const int R = ix->params.r0 * k;
-    const Workspace need = carve(nullptr, ix->g, nq, c, k, R, ix->params.score_mode == LIDER_SCORE_TENSOR);
+    const Workspace need = carve(nullptr, ix->g, nq, c, search_shape(ix, k));
     if (need.total > (size_t)LIDER_NOALLOC_SCRATCH_BYTES)
         return fail(LIDER_ELIMIT, "lider_search_noalloc: this batch needs " + std::to_string(need.total) +
                                       " bytes of scratch, more than the fixed LIDER_NOALLOC_SCRATCH_BYTES (" +
@@ -1223,7 +1297,7 @@ int search_noalloc_impl(const lider_index* ix, const float* Q, int64_t nq, int k
                                       "); search fewer queries per call");
     unsigned char* base = nullptr;
     if ((rc = noalloc_scratch(ix->device, &base))) return rc;
-    const Workspace w = carve(base, ix->g, nq, c, k, R, ix->params.score_mode == LIDER_SCORE_TENSOR);
+    const Workspace w = carve(base, ix->g, nq, c, search_shape(ix, k));
     cudaStream_t st = (cudaStream_t)stream;
     rc = enqueue_search(ix, Q, nq, k, c, out_ids, out_scores, nullptr, w, st);
     if (rc == LIDER_OK && stats) rc = read_stats(w, nq, c, stats, st);

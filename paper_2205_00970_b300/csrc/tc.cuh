@@ -1,19 +1,16 @@
 // 5th-generation tensor-core (tcgen05) tile engine for sm_103a: TMA loads into
 // 128-byte-swizzled shared memory, tcgen05.mma with the accumulator in TMEM,
 // tcgen05.ld for the epilogue.  Used for the dense part of candidate scoring:
-// D[128 x 256] = A[128 x d] . B[256 x d]^T with FP32 accuracy from three TF32
-// products (A_hi B_hi + A_hi B_lo + A_lo B_hi; x = x_hi + x_lo with x_hi the
-// TF32-representable head of x, so the dropped A_lo B_lo term and the TF32
-// rounding of x_lo stay below 2^-21 relative).
+// D[128 x 256] = A[128 x d] . B[256 x d]^T in one of two kinds:
+//   KindTf32x3: FP32 accuracy from three TF32 products (A_hi B_hi + A_hi B_lo +
+//     A_lo B_hi; x = x_hi + x_lo with x_hi the TF32-representable head of x,
+//     so the dropped A_lo B_lo term and the TF32 rounding of x_lo stay below
+//     2^-21 relative); two stages of A_hi, A_lo, B_hi, B_lo;
+//   KindBf16: one BF16 product per element pair (kind::f16, FP32
+//     accumulation); four stages of A, B.
+// Every shared-memory row is 128 bytes (32 FP32 or 64 BF16 elements of K) and
+// every MMA consumes 32 bytes of K, four MMA steps per stage.
 //
-// Warp roles of a 192-thread block: warp 0 issues TMA loads (and owns the TMEM
-// allocation), warp 1 issues MMAs (one elected thread), warps 2-5 run the
-// epilogue (warp w reads TMEM lanes 32*(w%4)..+31).  Two shared-memory stages
-// and two TMEM accumulators let loads, MMAs and the epilogue overlap.
-//
-// Every wait is bounded: after kTimeoutNs the waiter records an error code,
-// raises the block's abort flag and every role leaves its loop; the block then
-// waits (bounded) for its outstanding copies and frees TMEM before exiting.
 #pragma once
 
 #include <cuda.h>
@@ -25,20 +22,38 @@ namespace tc {
 
 constexpr int kBM = 128;                       // MMA M = TMEM lanes
 constexpr int kBN = 256;                       // MMA N = accumulator columns
-constexpr int kBK = 32;                        // FP32 elements per 128-byte swizzle row
-constexpr int kStages = 2;
-constexpr int kTileA = kBM * kBK * 4;          // 16 KB
-constexpr int kTileB = kBN * kBK * 4;          // 32 KB
-constexpr int kStageBytes = 2 * kTileA + 2 * kTileB;   // A_hi, A_lo, B_hi, B_lo
-constexpr int kSmemBytes = kStages * kStageBytes + 1024;  // + alignment slack
+constexpr int kRowBytes = 128;                 // K bytes per shared-memory row (one swizzle span)
+constexpr int kTileA = kBM * kRowBytes;        // 16 KB
+constexpr int kTileB = kBN * kRowBytes;        // 32 KB
+constexpr int kMaxStages = 4;
+constexpr int kSmemBytes = 2 * (2 * kTileA + 2 * kTileB) + 1024;  // both kinds: 192 KB + alignment slack
 constexpr int kThreads = 192;
 constexpr int kTmemCols = 2 * kBN;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 
-// instruction descriptor, kind::tf32: D F32 (bits 4-5 = 1), A and B TF32
-// (bits 7-9 and 10-12 = 2), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
-constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kBN >> 3) << 17) |
-                                ((uint32_t)(kBM >> 4) << 24);
+// instruction descriptors: D F32 (bits 4-5 = 1), A and B formats at bits 7-9
+// and 10-12 (kind::tf32: 2 = TF32; kind::f16: 1 = BF16), both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t idesc(uint32_t ab_format) {
+    return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((uint32_t)(kBN >> 3) << 17) |
+           ((uint32_t)(kBM >> 4) << 24);
+}
+
+struct KindTf32x3 {
+    static constexpr int kStages = 2;
+    static constexpr int kOps = 2;                       // hi and lo buffers per operand
+    static constexpr int kElemBytes = 4;
+    static constexpr int kBK = kRowBytes / kElemBytes;   // 32 elements of K per stage
+    static constexpr uint32_t kIdesc = idesc(2);
+};
+
+struct KindBf16 {
+    static constexpr int kStages = 4;
+    static constexpr int kOps = 1;
+    static constexpr int kElemBytes = 2;
+    static constexpr int kBK = kRowBytes / kElemBytes;   // 64 elements of K per stage
+    static constexpr uint32_t kIdesc = idesc(1);
+};
 
 enum {
     TC_OK = 0,
@@ -129,6 +144,15 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64
         : "memory");
 }
 
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // Arrive on `bar` once every MMA issued so far by this thread has completed.
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -171,8 +195,8 @@ __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" :::
 
 // Shared state of one block.
 struct Ctl {
-    uint64_t full[kStages];
-    uint64_t empty[kStages];
+    uint64_t full[kMaxStages];
+    uint64_t empty[kMaxStages];
     uint64_t tfull[2];
     uint64_t tempty[2];
     uint32_t tmem_base;
@@ -188,10 +212,16 @@ struct Ctl {
 // int row, int col0, const uint32_t (&v)[32]) for columns col0..col0+31, and
 // void done(int u, int row) after the last group.  The epilogue warps leave
 // their loop only together, so their named barriers cannot be left waiting.
-template <class Sched, class Epi>
+// mA0/mB0: the operands (KindTf32x3: their TF32 heads); mA1/mB1: the tails
+// (KindTf32x3 only; ignored otherwise).  kchunks = ceil(d / Kind::kBK).
+template <class Kind, class Sched, class Epi>
 __device__ void gemm_tiles(const CUtensorMap* mAhi, const CUtensorMap* mAlo, const CUtensorMap* mBhi,
                            const CUtensorMap* mBlo, int kchunks, Sched& sched, Epi& epi, int* err,
                            unsigned char* smem_raw, Ctl& ctl) {
+    constexpr int kStages = Kind::kStages;
+    constexpr int kStageBytes = Kind::kOps * (kTileA + kTileB);
+    constexpr int kBK = Kind::kBK;
+    static_assert(kStages * kStageBytes + 1024 <= kSmemBytes, "stages exceed the shared memory plan");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~(uintptr_t)1023);
@@ -239,9 +269,11 @@ __device__ void gemm_tiles(const CUtensorMap* mAhi, const CUtensorMap* mAlo, con
                     mbar_expect_tx(&ctl.full[s], (uint32_t)kStageBytes);
                     const int k0 = kc * kBK;
                     tma_load_2d(st, mAhi, &ctl.full[s], k0, arow);
-                    tma_load_2d(st + kTileA, mAlo, &ctl.full[s], k0, arow);
-                    tma_load_2d(st + 2 * kTileA, mBhi, &ctl.full[s], k0, brow);
-                    tma_load_2d(st + 2 * kTileA + kTileB, mBlo, &ctl.full[s], k0, brow);
+                    tma_load_2d(st + Kind::kOps * kTileA, mBhi, &ctl.full[s], k0, brow);
+                    if constexpr (Kind::kOps == 2) {
+                        tma_load_2d(st + kTileA, mAlo, &ctl.full[s], k0, arow);
+                        tma_load_2d(st + 2 * kTileA + kTileB, mBlo, &ctl.full[s], k0, brow);
+                    }
                 }
             }
             // drain: wait until every issued stage has landed (bounded)
@@ -271,16 +303,22 @@ __device__ void gemm_tiles(const CUtensorMap* mAhi, const CUtensorMap* mAlo, con
                     if (!mbar_wait(&ctl.full[s], ph, abort_flag)) { fail(TC_TIMEOUT_FULL); ok = false; break; }
                     tc_fence_after();
                     const uint32_t sa = smem_u32(stage_ptr(s));
-                    const uint32_t a_hi = sa, a_lo = sa + kTileA;
-                    const uint32_t b_hi = sa + 2 * kTileA, b_lo = sa + 2 * kTileA + kTileB;
 #pragma unroll
-                    for (int kk = 0; kk < kBK / 8; ++kk) {           // K = 8 TF32 (32 bytes) per MMA
+                    for (int kk = 0; kk < kRowBytes / 32; ++kk) {     // 32 bytes of K per MMA
                         const uint32_t off = (uint32_t)kk * 32u;
-                        const uint64_t dah = sdesc_sw128(a_hi + off), dal = sdesc_sw128(a_lo + off);
-                        const uint64_t dbh = sdesc_sw128(b_hi + off), dbl = sdesc_sw128(b_lo + off);
-                        mma_tf32(d, dah, dbh, kIdescTf32, (kc | kk) != 0 ? 1u : 0u);
-                        mma_tf32(d, dah, dbl, kIdescTf32, 1u);
-                        mma_tf32(d, dal, dbh, kIdescTf32, 1u);
+                        const uint32_t acc = (kc | kk) != 0 ? 1u : 0u;
+                        if constexpr (Kind::kOps == 2) {
+                            const uint32_t a_hi = sa, a_lo = sa + kTileA;
+                            const uint32_t b_hi = sa + 2 * kTileA, b_lo = sa + 2 * kTileA + kTileB;
+                            const uint64_t dah = sdesc_sw128(a_hi + off), dal = sdesc_sw128(a_lo + off);
+                            const uint64_t dbh = sdesc_sw128(b_hi + off), dbl = sdesc_sw128(b_lo + off);
+                            mma_tf32(d, dah, dbh, Kind::kIdesc, acc);
+                            mma_tf32(d, dah, dbl, Kind::kIdesc, 1u);
+                            mma_tf32(d, dal, dbh, Kind::kIdesc, 1u);
+                        } else {
+                            const uint64_t da = sdesc_sw128(sa + off), db = sdesc_sw128(sa + kTileA + off);
+                            mma_f16(d, da, db, Kind::kIdesc, acc);
+                        }
                     }
                     mma_commit(&ctl.empty[s]);                 // stage reusable once these finish
                 }

@@ -1,5 +1,7 @@
 // Tensor-core candidate scoring support: the TF32 hi/lo split, TMA tensor
 // maps, and a one-tile self-test of the tcgen05 engine (tc.cuh).
+#include <cuda_bf16.h>
+
 #include <mutex>
 
 #include "lider_internal.cuh"
@@ -19,6 +21,13 @@ __global__ void split_tf32_kernel(const float* __restrict__ x, int64_t n, float*
     const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
     hi[i] = h;
     lo[i] = __fsub_rn(v, h);
+}
+
+// Round to BF16 (nearest, ties to even).
+__global__ void to_bf16_kernel(const float* __restrict__ x, int64_t n, uint16_t* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = __bfloat16_as_ushort(__float2bfloat16_rn(x[i]));
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -61,6 +70,7 @@ struct WriteTile {
     __device__ void done(int, int) const {}
 };
 
+template <class Kind>
 __global__ void __launch_bounds__(tc::kThreads, 1)
     tc_tile_test_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                         const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
@@ -69,10 +79,17 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     __shared__ tc::Ctl ctl;
     OneTile sched;
     WriteTile epi{out, m, n};
-    tc::gemm_tiles(&mAhi, &mAlo, &mBhi, &mBlo, kchunks, sched, epi, err, smem, ctl);
+    tc::gemm_tiles<Kind>(&mAhi, &mAlo, &mBhi, &mBlo, kchunks, sched, epi, err, smem, ctl);
 }
 
 }  // namespace
+
+int launch_to_bf16(const float* x, int64_t n, uint16_t* out, cudaStream_t st) {
+    if (n <= 0) return LIDER_OK;
+    to_bf16_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(x, n, out);
+    LIDER_LAUNCH_CHECK("to_bf16_kernel");
+    return LIDER_OK;
+}
 
 int launch_split_tf32(const float* x, int64_t n, float* hi, float* lo, cudaStream_t st) {
     if (n <= 0) return LIDER_OK;
@@ -81,16 +98,19 @@ int launch_split_tf32(const float* x, int64_t n, float* hi, float* lo, cudaStrea
     return LIDER_OK;
 }
 
-// 2-D FP32 tensor map over rows x d (row-major), box 32 x box_rows, 128-byte swizzle.
-int make_tensor_map(CUtensorMap* map, const float* base, int64_t rows, int d, int box_rows) {
+// 2-D tensor map over rows x d (row-major FP32, or BF16 when bf16), box of
+// one 128-byte row of K (32 FP32 / 64 BF16) x box_rows, 128-byte swizzle.
+int make_tensor_map(CUtensorMap* map, const void* base, int64_t rows, int d, int box_rows, bool bf16) {
     EncodeTiledFn fn;
     int rc = encode_fn(&fn);
     if (rc) return rc;
+    const int esz = bf16 ? 2 : 4;
     const cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)d * 4};
-    const cuuint32_t box[2] = {(cuuint32_t)tc::kBK, (cuuint32_t)box_rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)d * esz};
+    const cuuint32_t box[2] = {(cuuint32_t)(tc::kRowBytes / esz), (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, estr,
+    const CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                          (void*)base, dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(LIDER_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
@@ -101,13 +121,14 @@ int make_tensor_map(CUtensorMap* map, const float* base, int64_t rows, int d, in
 
 // Self-test of the tensor-core engine: out[m x n] = A[m x d] . B[n x d]^T with
 // m <= 128, n <= 256, through the same TMA / tcgen05 / TMEM path as search.
-extern "C" int lider_debug_tc_tile(const float* A, int32_t m, const float* B, int32_t n, int32_t d, float* out,
-                                   void* stream) {
+extern "C" int lider_debug_tc_tile(const float* A, int32_t m, const float* B, int32_t n, int32_t d, int32_t kind,
+                                   float* out, void* stream) {
     using namespace lider;
     try {
         if (!A || !B || !out) return fail(LIDER_EINVAL, "lider_debug_tc_tile: NULL pointer");
-        if (m < 1 || m > tc::kBM || n < 1 || n > tc::kBN || d < 4 || d % 4 != 0)
-            return fail(LIDER_EINVAL, "lider_debug_tc_tile: need 1<=m<=128, 1<=n<=256, d % 4 == 0");
+        if (kind != 0 && kind != 1) return fail(LIDER_EINVAL, "lider_debug_tc_tile: kind must be 0 or 1");
+        if (m < 1 || m > tc::kBM || n < 1 || n > tc::kBN || d < 8 || d % (kind ? 8 : 4) != 0)
+            return fail(LIDER_EINVAL, "lider_debug_tc_tile: need 1<=m<=128, 1<=n<=256, d % 4 (BF16: 8) == 0");
         cudaStream_t st = (cudaStream_t)stream;
         float* buf = nullptr;
         const size_t na = (size_t)m * d, nb = (size_t)n * d;
@@ -117,18 +138,34 @@ extern "C" int lider_debug_tc_tile(const float* A, int32_t m, const float* B, in
         int rc = LIDER_OK;
         CUtensorMap mah, mal, mbh, mbl;
         do {
-            if ((rc = launch_split_tf32(A, (int64_t)na, ahi, alo, st))) break;
-            if ((rc = launch_split_tf32(B, (int64_t)nb, bhi, blo, st))) break;
-            if ((rc = make_tensor_map(&mah, ahi, m, d, tc::kBM))) break;
-            if ((rc = make_tensor_map(&mal, alo, m, d, tc::kBM))) break;
-            if ((rc = make_tensor_map(&mbh, bhi, n, d, tc::kBN))) break;
-            if ((rc = make_tensor_map(&mbl, blo, n, d, tc::kBN))) break;
+            if (kind == 0) {
+                if ((rc = launch_split_tf32(A, (int64_t)na, ahi, alo, st))) break;
+                if ((rc = launch_split_tf32(B, (int64_t)nb, bhi, blo, st))) break;
+                if ((rc = make_tensor_map(&mah, ahi, m, d, tc::kBM))) break;
+                if ((rc = make_tensor_map(&mal, alo, m, d, tc::kBM))) break;
+                if ((rc = make_tensor_map(&mbh, bhi, n, d, tc::kBN))) break;
+                if ((rc = make_tensor_map(&mbl, blo, n, d, tc::kBN))) break;
+            } else {
+                uint16_t* a16 = reinterpret_cast<uint16_t*>(ahi);
+                uint16_t* b16 = reinterpret_cast<uint16_t*>(bhi);
+                if ((rc = launch_to_bf16(A, (int64_t)na, a16, st))) break;
+                if ((rc = launch_to_bf16(B, (int64_t)nb, b16, st))) break;
+                if ((rc = make_tensor_map(&mah, a16, m, d, tc::kBM, true))) break;
+                if ((rc = make_tensor_map(&mbh, b16, n, d, tc::kBN, true))) break;
+                mal = mah;
+                mbl = mbh;
+            }
             cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
             if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemsetAsync"); break; }
-            e = cudaFuncSetAttribute(tc_tile_test_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes);
+            const void* kern = kind == 0 ? (const void*)tc_tile_test_kernel<tc::KindTf32x3>
+                                         : (const void*)tc_tile_test_kernel<tc::KindBf16>;
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes);
             if (e != cudaSuccess) { rc = cuda_fail(e, "cudaFuncSetAttribute"); break; }
-            tc_tile_test_kernel<<<1, tc::kThreads, tc::kSmemBytes, st>>>(mah, mal, mbh, mbl, (d + tc::kBK - 1) / tc::kBK,
-                                                                        out, m, n, err);
+            const int kbk = kind == 0 ? tc::KindTf32x3::kBK : tc::KindBf16::kBK;
+            int kchunks = (d + kbk - 1) / kbk;
+            void* args[] = {&mah, &mal, &mbh, &mbl, &kchunks, &out, &m, &n, &err};
+            e = cudaLaunchKernel(kern, dim3(1), dim3(tc::kThreads), args, tc::kSmemBytes, st);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "tc_tile_test_kernel launch"); break; }
             e = cudaGetLastError();
             if (e != cudaSuccess) { rc = cuda_fail(e, "tc_tile_test_kernel"); break; }
             int h_err = 0;

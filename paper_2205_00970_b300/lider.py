@@ -28,13 +28,13 @@ class LiderError(RuntimeError):
         self.code = code
 
 
-SCORE_TENSOR, SCORE_SIMT = 0, 1
+SCORE_TENSOR, SCORE_SIMT, SCORE_BF16 = 0, 1, 2
 
 
 class Params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("m", ctypes.c_int32), ("rmi_leaves", ctypes.c_int32),
                 ("r0", ctypes.c_int32), ("B", ctypes.c_int32), ("hash_kind", ctypes.c_int32),
-                ("W", ctypes.c_double), ("score_mode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("W", ctypes.c_double), ("score_mode", ctypes.c_int32), ("rerank", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -73,7 +73,7 @@ def _load():
         "lider_cluster_offsets": ([P, P], ctypes.c_int),
         "lider_export_array": ([P, I32, I32, P, P], ctypes.c_int),
         "lider_export_rmi": ([P, I32, I32, P, P, P, P], ctypes.c_int),
-        "lider_debug_tc_tile": ([P, I32, P, I32, I32, P, P], ctypes.c_int),
+        "lider_debug_tc_tile": ([P, I32, P, I32, I32, I32, P, P], ctypes.c_int),
         "lider_free": ([P], None),
         "lider_last_error": ([], ctypes.c_char_p),
     }
@@ -118,13 +118,13 @@ class Index:
 
     def __init__(self, corpus: torch.Tensor, centroids: torch.Tensor, A: torch.Tensor, b: torch.Tensor,
                  L: int, m: int, W: float, rmi_leaves: int, r0: int = 2, B: int = 1,
-                 score_mode: int = SCORE_TENSOR, stream=None):
+                 score_mode: int = SCORE_TENSOR, rerank: int = 0, stream=None):
         corpus = _dev(corpus, torch.float32, "corpus")
         centroids = _dev(centroids, torch.float32, "centroids")
         A = _dev(A, torch.float32, "A")
         b = _dev(b, torch.float32, "b")
         n, d = corpus.shape
-        p = Params(L, m, rmi_leaves, r0, B, 0, float(W), score_mode, 0)
+        p = Params(L, m, rmi_leaves, r0, B, 0, float(W), score_mode, rerank)
         h = ctypes.c_void_p()
         _check(_lib.lider_build(corpus.data_ptr(), n, d, centroids.data_ptr(), centroids.shape[0],
                                 A.data_ptr(), b.data_ptr(), ctypes.byref(p), _stream_ptr(stream),
@@ -133,6 +133,7 @@ class Index:
         self.n, self.d, self.n_clusters = int(n), int(d), int(centroids.shape[0])
         self.L, self.m, self.W, self.rmi_leaves, self.r0, self.B = L, m, W, rmi_leaves, r0, B
         self.score_mode = score_mode
+        self.rerank = rerank
 
     @property
     def handle(self) -> int:
@@ -238,12 +239,13 @@ class Index:
                 "e_hi": err[1::2].astype(np.int64)}
 
 
-def tc_tile(A: torch.Tensor, B: torch.Tensor, stream=None) -> torch.Tensor:
-    """A . B^T through the tensor-core engine (self-test entry)."""
+def tc_tile(A: torch.Tensor, B: torch.Tensor, kind: int = 0, stream=None) -> torch.Tensor:
+    """A . B^T through the tensor-core engine (self-test entry); kind 0:
+    three TF32 products, kind 1: BF16 operands."""
     A = _dev(A, torch.float32, "A")
     B = _dev(B, torch.float32, "B")
     out = torch.empty((A.shape[0], B.shape[0]), dtype=torch.float32, device=A.device)
-    _check(_lib.lider_debug_tc_tile(A.data_ptr(), A.shape[0], B.data_ptr(), B.shape[0], A.shape[1],
+    _check(_lib.lider_debug_tc_tile(A.data_ptr(), A.shape[0], B.data_ptr(), B.shape[0], A.shape[1], kind,
                                     out.data_ptr(), _stream_ptr(stream)))
     return out
 

@@ -38,7 +38,7 @@ def gpu_index(cfg, X, C, A, b, device="cuda"):
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
     return lider.Index(t(X), t(C), t(A), t(b), L=cfg["L"], m=cfg["m"], W=cfg["W"],
                        rmi_leaves=cfg["leaves"], r0=cfg["r0"], B=cfg["B"],
-                       score_mode=cfg.get("score_mode", lider.SCORE_TENSOR))
+                       score_mode=cfg.get("score_mode", lider.SCORE_TENSOR), rerank=cfg.get("rerank", 0))
 
 
 def check_topk(gpu_ids, gpu_sc, ref_ids, ref_sc, X, Q, rows=None):

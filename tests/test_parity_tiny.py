@@ -176,3 +176,34 @@ def test_invalid_search_arguments(tiny):
         with pytest.raises(lider.LiderError) as e:
             g.search(Qd, k, c)
         assert e.value.code == code
+
+
+def test_served_bf16_form():
+    """Served form (BF16 scoring + FP32 re-rank of a shortlist of rerank * k):
+    every returned id is a candidate of its query, scores are the exact FP32
+    inner products, results are sorted, batch-invariant, and agree with the
+    plain top-k on almost every rank."""
+    import torch
+    cfg, X, Q, C, A, b = F.workload("tiny")
+    cfg["score_mode"] = 2
+    cfg["rerank"] = 4
+    g = F.gpu_index(cfg, X, C, A, b)
+    Qd = torch.from_numpy(Q).cuda()
+    ids, sc, st, tr = g.search(Qd, cfg["k"], cfg["c"], stats=True, trace=True)
+    ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+    ref = O.search(F.oracle_index(cfg, X, C, A, b), Q, cfg["k"], cfg["c"], cfg["R"])
+    bad, _ = F.check_trace(tr, ref)
+    assert not bad, bad[:5]
+    ref_idx = F.oracle_index(cfg, X, C, A, b)
+    agree = 0
+    for i in range(len(Q)):
+        nv = int(np.sum(ids[i] >= 0))
+        assert nv == int(np.sum(ref.ids[i] >= 0))
+        exact = X[ids[i, :nv]].astype(np.float64) @ Q[i].astype(np.float64)
+        assert np.all(np.abs(sc[i, :nv] - exact) <= F.SCORE_RTOL * np.abs(exact) + F.SCORE_ATOL)
+        assert np.all(np.diff(sc[i, :nv]) <= 0)
+        agree += len(set(ids[i, :nv].tolist()) & set(ref.ids[i, :nv].tolist()))
+    total = int(np.sum(ref.ids >= 0))
+    assert agree / total > 0.995, agree / total
+    sub_ids, sub_sc = g.search(Qd[37:291].contiguous(), cfg["k"], cfg["c"])
+    assert np.array_equal(sub_ids.cpu().numpy(), ids[37:291])
