@@ -353,7 +353,7 @@ def run_lider(args, cfg):
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if args.score == "bf16" else "f32", "data": "synthetic",
         "config": dict(workload_desc(cfg), parallelism=f"replicas x{world}"),
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "of": f"one batch of {nq:,} queries"},

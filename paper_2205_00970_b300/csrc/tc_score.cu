@@ -127,7 +127,7 @@ extern "C" int lider_debug_tc_tile(const float* A, int32_t m, const float* B, in
     try {
         if (!A || !B || !out) return fail(LIDER_EINVAL, "lider_debug_tc_tile: NULL pointer");
         if (kind != 0 && kind != 1) return fail(LIDER_EINVAL, "lider_debug_tc_tile: kind must be 0 or 1");
-        if (m < 1 || m > tc::kBM || n < 1 || n > tc::kBN || d < 8 || d % (kind ? 8 : 4) != 0)
+        if (m < 1 || m > tc::kBM || n < 1 || n > tc::kBN || d < (kind ? 8 : 4) || d % (kind ? 8 : 4) != 0)
             return fail(LIDER_EINVAL, "lider_debug_tc_tile: need 1<=m<=128, 1<=n<=256, d % 4 (BF16: 8) == 0");
         cudaStream_t st = (cudaStream_t)stream;
         float* buf = nullptr;
