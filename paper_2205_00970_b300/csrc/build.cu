@@ -9,6 +9,7 @@
 #include <cub/device/device_segmented_radix_sort.cuh>
 
 #include <algorithm>
+#include <functional>
 #include <cmath>
 
 #include "lider_internal.cuh"
@@ -77,19 +78,6 @@ __global__ void gather_rows_kernel(const float* __restrict__ src, const int64_t*
     const float4* s = reinterpret_cast<const float4*>(src + ids[row] * (int64_t)d);
     float4* o = reinterpret_cast<float4*>(dst + row * (int64_t)d);
     for (int i = lane; i < d / 4; i += 32) o[i] = s[i];
-}
-
-// rank[l][base + pos] = i for every sorted entry i of array l: the inverse of
-// the sorted order, per cluster.
-__global__ void rank_kernel(const int32_t* __restrict__ pos, const int32_t* __restrict__ sorted_asg,
-                            const int64_t* __restrict__ cl_off, int64_t n, int L, int32_t* __restrict__ rank) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t base = cl_off[sorted_asg[i]];
-    for (int l = 0; l < L; ++l) {
-        const int32_t p = pos[(int64_t)l * n + i];
-        rank[(int64_t)l * n + base + p] = (int32_t)(i - base);
-    }
 }
 
 __global__ void inverse_ids_kernel(const int64_t* __restrict__ orig_id, int64_t n, int32_t* __restrict__ row_of) {
@@ -256,7 +244,7 @@ int dev_alloc(void** p, size_t bytes, const char* what) {
 void release(lider_index* ix) {
     if (!ix) return;
     void* bufs[] = {ix->X, ix->orig_id, ix->cl_off, ix->C, ix->half_norm, ix->A, ix->bproj,
-                    ix->keys, ix->pos, ix->root, ix->leaf, ix->X_hi, ix->X_lo, ix->rank, ix->row_of, ix->X_bf16};
+                    ix->keys, ix->pos, ix->root, ix->leaf, ix->X_hi, ix->X_lo, ix->row_of, ix->X_bf16};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (ix->pool) cudaMemPoolDestroy(ix->pool);
@@ -407,13 +395,10 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
             if ((rc = launch_to_bf16(ix->X, n * d, ix->X_bf16, st))) return rc;
             if ((rc = make_tensor_map(&ix->map_xbf16, ix->X_bf16, n, d, 256, true))) return rc;
         }
-        ALLOC(ix->rank, (size_t)L * n * sizeof(int32_t), "rank tables");
         ALLOC(ix->row_of, (size_t)n * sizeof(int32_t), "row of id");
         inverse_ids_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(ix->orig_id, n, ix->row_of);
         LIDER_LAUNCH_CHECK("inverse_ids_kernel");
-        rank_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(ix->pos, asg_sorted.as<int32_t>(), ix->cl_off, n, L,
-                                                           ix->rank);
-        LIDER_LAUNCH_CHECK("rank_kernel");
+
     }
 
     // 5. RMI per (cluster, array)
@@ -443,10 +428,17 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
     g.W = P->W;
     g.X = ix->X; g.orig_id = ix->orig_id; g.cl_off = ix->cl_off; g.C = ix->C; g.half_norm = ix->half_norm;
     g.A = ix->A; g.bproj = ix->bproj; g.keys = ix->keys; g.pos = ix->pos; g.root = ix->root; g.leaf = ix->leaf;
-    g.X_hi = ix->X_hi; g.X_lo = ix->X_lo; g.rank = ix->rank; g.row_of = ix->row_of; g.X_bf16 = ix->X_bf16;
+    g.X_hi = ix->X_hi; g.X_lo = ix->X_lo; g.row_of = ix->row_of; g.X_bf16 = ix->X_bf16;
     int64_t max_nc = 0;
     for (int j = 0; j < ncl; ++j) max_nc = std::max(max_nc, ix->h_cl_off[j + 1] - ix->h_cl_off[j]);
     g.max_row_tiles = (int32_t)cdiv(max_nc, 256);
+    {
+        std::vector<int64_t> wv(ncl);
+        for (int j = 0; j < ncl; ++j) wv[j] = cdiv(ix->h_cl_off[j + 1] - ix->h_cl_off[j], 32);
+        std::sort(wv.begin(), wv.end(), std::greater<int64_t>());
+        ix->top_words.assign(ncl + 1, 0);
+        for (int j = 0; j < ncl; ++j) ix->top_words[j + 1] = ix->top_words[j] + wv[j];
+    }
 #undef ALLOC
     guard.ix = nullptr;
     *out = ix;

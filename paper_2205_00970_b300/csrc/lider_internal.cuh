@@ -61,7 +61,6 @@ struct Geometry {         // everything a search kernel needs, passed by value
     const RmiLeaf* leaf;    // ncl x L x F
     const float* X_hi;      // n x d, TF32 head of X (tensor-core scoring)
     const float* X_lo;      // n x d, X - X_hi
-    const int32_t* rank;    // L x n, rank[l][base + p] = sorted position of row p in array l
     const int32_t* row_of;  // n, row of X holding corpus id i (inverse of orig_id)
     const uint16_t* X_bf16; // n x d, BF16 copy of X (served mode)
 };
@@ -73,6 +72,7 @@ struct lider_index {
     lider_params params;
     int device = 0;
     std::vector<int64_t> h_cl_off;
+    std::vector<int64_t> top_words;  // [c] = bitmap words of the c largest clusters
     // owned device buffers
     float* X = nullptr;
     int64_t* orig_id = nullptr;
@@ -87,7 +87,6 @@ struct lider_index {
     lider::RmiLeaf* leaf = nullptr;
     float* X_hi = nullptr;
     float* X_lo = nullptr;
-    int32_t* rank = nullptr;
     int32_t* row_of = nullptr;
     uint16_t* X_bf16 = nullptr;
     CUtensorMap map_xbf16;      // TMA map over X_bf16, boxes of 64 x 256

@@ -98,30 +98,41 @@ __device__ __forceinline__ int32_t tc_units(int32_t cnt, int64_t n_c) {
     return n_c > 0 ? ((cnt + tc::kBM - 1) / tc::kBM) * (int32_t)((n_c + tc::kBN - 1) / tc::kBN) : 0;
 }
 
+// Words of one pair's candidate bitmap over its cluster's positions.
+__device__ __forceinline__ int64_t bitmap_words(int64_t n_c) { return (n_c + 31) >> 5; }
+
 __global__ void group_scan_kernel(const int32_t* __restrict__ cnt, int ncl, int G, const int64_t* __restrict__ cl_off,
                                   int32_t* __restrict__ off, int32_t* __restrict__ cursor,
-                                  int32_t* __restrict__ item_off, int32_t* __restrict__ unit_off) {
+                                  int32_t* __restrict__ item_off, int32_t* __restrict__ unit_off,
+                                  int64_t* __restrict__ bm_off) {
     __shared__ int32_t s_a[1024], s_b[1024], s_c[1024];
+    __shared__ int64_t s_d[1024];
     __shared__ int32_t carry_a, carry_b, carry_c;
-    if (threadIdx.x == 0) { carry_a = 0; carry_b = 0; carry_c = 0; }
+    __shared__ int64_t carry_d;
+    if (threadIdx.x == 0) { carry_a = 0; carry_b = 0; carry_c = 0; carry_d = 0; }
     __syncthreads();
     for (int base = 0; base < ncl; base += 1024) {
         const int j = base + threadIdx.x;
         const int32_t v = (j < ncl) ? cnt[j] : 0;
         const int32_t vb = (v + G - 1) / G;
-        const int32_t vc = (j < ncl) ? tc_units(v, cl_off[j + 1] - cl_off[j]) : 0;
+        const int64_t n_c = (j < ncl) ? cl_off[j + 1] - cl_off[j] : 0;
+        const int32_t vc = (j < ncl) ? tc_units(v, n_c) : 0;
+        const int64_t vd = (int64_t)v * bitmap_words(n_c);
         s_a[threadIdx.x] = v;
         s_b[threadIdx.x] = vb;
         s_c[threadIdx.x] = vc;
+        s_d[threadIdx.x] = vd;
         __syncthreads();
         for (int o = 1; o < 1024; o <<= 1) {          // inclusive Hillis-Steele scans
             const int32_t ta = threadIdx.x >= o ? s_a[threadIdx.x - o] : 0;
             const int32_t tb = threadIdx.x >= o ? s_b[threadIdx.x - o] : 0;
             const int32_t tcv = threadIdx.x >= o ? s_c[threadIdx.x - o] : 0;
+            const int64_t td = threadIdx.x >= o ? s_d[threadIdx.x - o] : 0;
             __syncthreads();
             s_a[threadIdx.x] += ta;
             s_b[threadIdx.x] += tb;
             s_c[threadIdx.x] += tcv;
+            s_d[threadIdx.x] += td;
             __syncthreads();
         }
         if (j < ncl) {
@@ -130,12 +141,17 @@ __global__ void group_scan_kernel(const int32_t* __restrict__ cnt, int ncl, int 
             cursor[j] = ea;
             item_off[j] = carry_b + s_b[threadIdx.x] - vb;
             unit_off[j] = carry_c + s_c[threadIdx.x] - vc;
+            bm_off[j] = carry_d + s_d[threadIdx.x] - vd;
         }
         __syncthreads();
-        if (threadIdx.x == 1023) { carry_a += s_a[1023]; carry_b += s_b[1023]; carry_c += s_c[1023]; }
+        if (threadIdx.x == 1023) {
+            carry_a += s_a[1023]; carry_b += s_b[1023]; carry_c += s_c[1023]; carry_d += s_d[1023];
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0) { off[ncl] = carry_a; item_off[ncl] = carry_b; unit_off[ncl] = carry_c; }
+    if (threadIdx.x == 0) {
+        off[ncl] = carry_a; item_off[ncl] = carry_b; unit_off[ncl] = carry_c; bm_off[ncl] = carry_d;
+    }
 }
 
 __global__ void group_fill_kernel(const int32_t* __restrict__ route, int64_t npairs, int32_t* __restrict__ cursor,
@@ -574,10 +590,10 @@ __global__ void __launch_bounds__(kScoreThreads) score_group_kernel(ScoreArgs a)
 // order, into Qp, split into TF32 head and tail) and the cluster's rows into
 // row tiles of 256; each (query tile, row tile) unit is one dense 128 x 256
 // tile computed with three TF32 products per FP32 product (tc.cuh).  The
-// epilogue keeps only candidates: row p is a candidate of pair (q, cluster)
-// when its sorted position in some array l falls in q's expansion window
-// there, rank_l(p) - wstart_l in [0, T).  Each candidate's key goes to the
-// pair's list; topk_pairs_kernel then selects each pair's top k.
+// epilogue keeps only candidates: mark_kernel first writes, per pair, a
+// bitmap over its cluster's positions of the union of its L expansion windows
+// (Sec. 3.3.1), and a tile reads 8 words of it per query.  Each candidate's
+// key goes to the pair's list; topk_pairs_kernel then selects each pair's top k.
 __global__ void qgather_kernel(const float* __restrict__ Q, const int32_t* __restrict__ pairs, int64_t np, int c,
                                int d, float* __restrict__ qp_hi, float* __restrict__ qp_lo) {
     const int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -611,7 +627,44 @@ __global__ void qgather_bf16_kernel(const float* __restrict__ Q, const int32_t* 
     for (int i = lane; i < d; i += 32) dst[i] = __bfloat16_as_ushort(__float2bfloat16_rn(src[i]));
 }
 
-constexpr int kTcMaxL = 16;
+constexpr int kMarkSmemWords = 8192;   // clusters up to 262,144 points mark in shared memory
+
+// One block per pair slot (pairs in cluster order): the union of the pair's L
+// expansion windows as a bitmap over the cluster's positions, at
+// bitmap + bm_off[j] + (slot - off[j]) * words_j.
+__global__ void __launch_bounds__(256) mark_kernel(const int32_t* __restrict__ pairs,
+                                                   const int32_t* __restrict__ route, const int32_t* __restrict__ off,
+                                                   const int64_t* __restrict__ cl_off,
+                                                   const int64_t* __restrict__ bm_off,
+                                                   const int32_t* __restrict__ wstart, const int32_t* __restrict__ pos,
+                                                   int64_t n, int L, int R, uint32_t* __restrict__ bitmap) {
+    __shared__ uint32_t sbits[kMarkSmemWords];
+    const int64_t slot = blockIdx.x;
+    const int64_t pair = pairs[slot];
+    const int j = route[pair];
+    const int64_t base = cl_off[j];
+    const int64_t n_c = cl_off[j + 1] - base;
+    if (n_c == 0) return;
+    const int64_t words = bitmap_words(n_c);
+    uint32_t* dst = bitmap + bm_off[j] + (slot - off[j]) * words;
+    const int T = (int)min((int64_t)R, n_c);
+    const bool in_smem = words <= kMarkSmemWords;
+    uint32_t* bits = in_smem ? sbits : dst;
+    for (int64_t i = threadIdx.x; i < words; i += blockDim.x) bits[i] = 0u;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int l = warp; l < L; l += blockDim.x / 32) {
+        const int32_t* P = pos + (int64_t)l * n + base + wstart[pair * L + l];
+        for (int t = lane; t < T; t += 32) {
+            const uint32_t p = (uint32_t)P[t];
+            atomicOr(&bits[p >> 5], 1u << (p & 31));
+        }
+    }
+    if (in_smem) {
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = sbits[i];
+    }
+}
 
 // One tensor-core tile: A row (first query slot), B row (first corpus row),
 // cluster, and (query tile << 16 | row tile).  Written once per search so the
@@ -637,13 +690,10 @@ struct TcArgs {
     const int32_t* cnt;
     const int64_t* cl_off;
     const int32_t* pairs;
-    const int32_t* wstart;
-    const int32_t* rank;
-    int64_t n;
-    int ncl, L, R, T_cap;
+    const int64_t* bm_off;
+    const uint32_t* bitmap;
+    int ncl, T_cap;
     uint64_t* pbuf;
-    int64_t* sl_ids;            // served form: per-query shortlist (nq x ks)
-    float* sl_scores;
     int32_t* pcount;
 };
 
@@ -659,7 +709,6 @@ struct TcSched {
 
 struct TcEpi {
     const TcArgs* a;
-    int32_t* rank_s;            // shared, L x 256 sorted positions of the tile's rows
     bool valid;
     int64_t pair;
     int p0, cursor;
@@ -668,67 +717,36 @@ struct TcEpi {
     __device__ void begin(int u, int row) {
         const int4 t = a->units[u];
         const int j = t.z, it = t.w >> 16, rt = t.w & 0xffff;
-        const int64_t base = a->cl_off[j];
-        const int64_t n_c = a->cl_off[j + 1] - base;
-        p0 = rt * tc::kBN;
-        // the tile's sorted positions: two columns per thread and array, all
-        // loads issued before any is used
-        const int et = threadIdx.x - 64;          // 0..127 across the epilogue warps
-        int32_t rv[2 * kTcMaxL];
-#pragma unroll
-        for (int l = 0; l < kTcMaxL; ++l) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int64_t p = (int64_t)p0 + et + 128 * h;
-                rv[2 * l + h] = (l < a->L && p < n_c) ? __ldg(a->rank + (int64_t)l * a->n + base + p) : -1;
-            }
-        }
-#pragma unroll
-        for (int l = 0; l < kTcMaxL; ++l) {
-            if (l < a->L) {
-                rank_s[l * tc::kBN + et] = rv[2 * l];
-                rank_s[l * tc::kBN + et + 128] = rv[2 * l + 1];
-            }
-        }
-        tc::epi_sync();
         const int in_tile = min(tc::kBM, a->cnt[j] - it * tc::kBM);
         valid = row < in_tile;
         if (!valid) return;
-        pair = a->pairs[a->off[j] + it * tc::kBM + row];
-        const uint32_t T = (uint32_t)min((int64_t)a->R, n_c);
-        uint32_t ws[kTcMaxL];
-#pragma unroll
-        for (int l = 0; l < kTcMaxL; ++l) ws[l] = l < a->L ? (uint32_t)a->wstart[pair * a->L + l] : 0u;
+        const int64_t n_c = a->cl_off[j + 1] - a->cl_off[j];
+        const int64_t words = bitmap_words(n_c);
+        const int64_t local = (int64_t)it * tc::kBM + row;
+        pair = a->pairs[a->off[j] + local];
+        p0 = rt * tc::kBN;
+        const uint32_t* src = a->bitmap + a->bm_off[j] + local * words + (p0 >> 5);
+        const int64_t nw = words - (p0 >> 5);
         int total = 0;
 #pragma unroll
         for (int w = 0; w < tc::kBN / 32; ++w) {
-            uint32_t word = 0;
-            for (int b = 0; b < 32; ++b) {
-                const int col = w * 32 + b;
-                bool m = false;
-#pragma unroll
-                for (int l = 0; l < kTcMaxL; ++l)
-                    if (l < a->L) m |= (uint32_t)rank_s[l * tc::kBN + col] - ws[l] < T;
-                word |= (uint32_t)m << b;
-            }
-            bits[w] = word;
-            total += __popc(word);
+            bits[w] = w < nw ? __ldg(src + w) : 0u;
+            total += __popc(bits[w]);
         }
         cursor = total ? atomicAdd(&a->pcount[pair], total) : 0;
     }
 
     __device__ void operator()(int, int, int col0, const uint32_t (&v)[32]) {
         if (!valid) return;
-        uint32_t w = bits[col0 >> 5];
+        const uint32_t w = bits[col0 >> 5];
+        if (!w) return;
         uint64_t* dst = a->pbuf + pair * a->T_cap;
-        while (w) {
-            const int i = __ffs(w) - 1;
-            w &= w - 1;
-            dst[cursor++] = score_key(__uint_as_float(v[i]), (uint32_t)(p0 + col0 + i));
-        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            if ((w >> i) & 1u) dst[cursor++] = score_key(__uint_as_float(v[i]), (uint32_t)(p0 + col0 + i));
     }
 
-    __device__ void done(int, int) { tc::epi_sync(); }   // the rank tile may now be reloaded
+    __device__ void done(int, int) {}
 };
 
 template <class Kind>
@@ -738,11 +756,9 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                     TcArgs args, int* err) {
     extern __shared__ unsigned char smem[];
     __shared__ tc::Ctl ctl;
-    int32_t* rank_s = reinterpret_cast<int32_t*>(smem + tc::kSmemBytes);
     TcSched sched{&args};
     TcEpi epi;
     epi.a = &args;
-    epi.rank_s = rank_s;
     tc::gemm_tiles<Kind>(&mAhi, &mAlo, &mBhi, &mBlo, kchunks, sched, epi, err, smem, ctl);
 }
 
@@ -892,6 +908,8 @@ struct Workspace {
     float* sl_scores;
     int32_t* pcount;            // tensor path: candidates per pair (cleared)
     int32_t* unit_off;
+    int64_t* bm_off;            // tensor paths: per-cluster bitmap offsets (words)
+    uint32_t* bitmap;           // tensor paths: per-pair candidate bitmaps
     int4* units;                // tensor path: tile descriptors
     float* qp_hi;               // tensor path: queries in pair order, TF32 head / tail
     float* qp_lo;
@@ -906,12 +924,16 @@ struct Workspace {
 // re-score (ks).  The served BF16 form keeps a shortlist of rerank * k.
 struct Shape {
     int mode, R, kp, ks;
+    int64_t bitmap_words;      // bound on the candidate bitmaps of one search
 };
 
-Shape search_shape(const lider_index* ix, int k) {
+Shape search_shape(const lider_index* ix, int k, int64_t nq = 0, int c = 0) {
     Shape sh;
     sh.mode = ix->params.score_mode;
     sh.R = ix->params.r0 * k;
+    // a query probes c distinct clusters, so its bitmaps take at most the
+    // words of the c largest clusters
+    sh.bitmap_words = (c > 0 && c <= ix->g.ncl) ? nq * ix->top_words[c] : 0;
     const int T_cap = ix->g.L * sh.R;
     if (sh.mode == LIDER_SCORE_BF16) {
         sh.ks = ix->params.rerank * k;
@@ -940,6 +962,8 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, const
     w.pcount = tensor ? (int32_t*)take((size_t)np * 4) : nullptr;
     w.zero_bytes = o;
     w.unit_off = (int32_t*)take((size_t)(g.ncl + 1) * 4);
+    w.bm_off = (int64_t*)take((size_t)(g.ncl + 1) * 8);
+    w.bitmap = tensor ? (uint32_t*)take((size_t)sh.bitmap_words * 4) : nullptr;
     w.ncl = g.ncl;
     // tiles <= sum_j ceil(cnt_j/128) * ceil(n_c/256) <= (np/128 + ncl) * max_row_tiles
     w.units = tensor ? (int4*)take((size_t)((np + tc::kBM - 1) / tc::kBM + g.ncl) * (size_t)g.max_row_tiles * 16)
@@ -979,6 +1003,10 @@ int check_search_args(const lider_index* ix, const float* Q, int64_t nq, int k, 
     if (nq * c > (int64_t)INT32_MAX) return fail(LIDER_ELIMIT, "lider_search: nq * c exceeds 2^31-1");
     if (ix->params.score_mode == LIDER_SCORE_BF16 && (int64_t)ix->params.rerank * k > 8192)
         return fail(LIDER_ELIMIT, "lider_search: rerank * k exceeds 8192");
+    if (ix->params.score_mode != LIDER_SCORE_SIMT && c <= ix->g.ncl &&
+        nq * ix->top_words[c] > ((int64_t)1 << 32))
+        return fail(LIDER_ELIMIT, "lider_search: candidate bitmaps of this batch exceed 16 GiB; search fewer "
+                                  "queries per call");
     if (nq > 0 && (!Q || !ids || !scores)) return fail(LIDER_EINVAL, "lider_search: NULL buffer");
     int dev = -1;
     LIDER_CUDA_TRY(cudaGetDevice(&dev));
@@ -1019,7 +1047,8 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
     const int G = std::max(1, std::min(kMaxGroup, (96 * 1024) / (g.d * 4)));
     group_count_kernel<<<(unsigned)cdiv(np, 256), 256, 0, st>>>(w.route, np, w.cnt);
     LIDER_LAUNCH_CHECK("group_count_kernel");
-    group_scan_kernel<<<1, 1024, 0, st>>>(w.cnt, g.ncl, G, g.cl_off, w.off, w.cursor, w.item_off, w.unit_off);
+    group_scan_kernel<<<1, 1024, 0, st>>>(w.cnt, g.ncl, G, g.cl_off, w.off, w.cursor, w.item_off, w.unit_off,
+                                          w.bm_off);
     LIDER_LAUNCH_CHECK("group_scan_kernel");
     group_fill_kernel<<<(unsigned)cdiv(np, 256), 256, 0, st>>>(w.route, np, w.cursor, w.pairs);
     LIDER_LAUNCH_CHECK("group_fill_kernel");
@@ -1047,6 +1076,9 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
             if ((rc = make_tensor_map(&mqh, w.qp_hi, np, g.d, tc::kBM))) return rc;
             if ((rc = make_tensor_map(&mql, w.qp_lo, np, g.d, tc::kBM))) return rc;
         }
+        mark_kernel<<<(unsigned)np, 256, 0, st>>>(w.pairs, w.route, w.off, g.cl_off, w.bm_off, w.wstart, g.pos, g.n,
+                                                  g.L, R, w.bitmap);
+        LIDER_LAUNCH_CHECK("mark_kernel");
         if ((rc = mark(LIDER_PHASE_SCORE))) return rc;
         tc_units_kernel<<<g.ncl, 128, 0, st>>>(w.unit_off, w.off, g.cl_off, g.ncl, w.units);
         LIDER_LAUNCH_CHECK("tc_units_kernel");
@@ -1057,16 +1089,13 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         ta.cnt = w.cnt;
         ta.cl_off = g.cl_off;
         ta.pairs = w.pairs;
-        ta.wstart = w.wstart;
-        ta.rank = g.rank;
-        ta.n = g.n;
+        ta.bm_off = w.bm_off;
+        ta.bitmap = w.bitmap;
         ta.ncl = g.ncl;
-        ta.L = g.L;
-        ta.R = R;
         ta.T_cap = g.L * R;
         ta.pbuf = w.pbuf;
         ta.pcount = w.pcount;
-        const int tc_smem = tc::kSmemBytes + kTcMaxL * tc::kBN * 4;
+        const int tc_smem = tc::kSmemBytes;
         // A = queries of the tile (128 rows, box 128), B = cluster rows (256, box 256)
         if (bf16) {
             LIDER_CUDA_TRY(cudaFuncSetAttribute(tc_score_kernel<tc::KindBf16>,
@@ -1194,10 +1223,10 @@ int search_entry(const lider_index* ix, const float* Q, int64_t nq, int k, int c
     if (stats) *stats = lider_search_stats{};
     if (nq == 0) return LIDER_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    Workspace sz = carve(nullptr, ix->g, nq, c, search_shape(ix, k));
+    Workspace sz = carve(nullptr, ix->g, nq, c, search_shape(ix, k, nq, c));
     void* mem = nullptr;
     if ((rc = pool_alloc(ix, &mem, sz.total, st))) return rc;
-    Workspace w = carve((unsigned char*)mem, ix->g, nq, c, search_shape(ix, k));
+    Workspace w = carve((unsigned char*)mem, ix->g, nq, c, search_shape(ix, k, nq, c));
     rc = enqueue_search(ix, Q, nq, k, c, out_ids, out_scores, tr, w, st);
     if (rc == LIDER_OK && stats) rc = read_stats(w, nq, c, stats, st);
     cudaError_t e = cudaFreeAsync(mem, st);
@@ -1214,7 +1243,7 @@ int search_host_entry(const lider_index* ix, const float* Qh, int64_t nq, int k,
     cudaStream_t st = (cudaStream_t)stream;
     const size_t qb = (size_t)nq * ix->g.d * 4, ib = (size_t)nq * k * 8, sb = (size_t)nq * k * 4;
     const size_t o_ids = align_up(qb, 256), o_sc = align_up(o_ids + ib, 256);
-    Workspace sz = carve(nullptr, ix->g, nq, c, search_shape(ix, k));
+    Workspace sz = carve(nullptr, ix->g, nq, c, search_shape(ix, k, nq, c));
     const size_t o_ws = align_up(o_sc + sb, 256);
     void* mem = nullptr;
     if ((rc = pool_alloc(ix, &mem, o_ws + sz.total, st))) return rc;
@@ -1222,7 +1251,7 @@ int search_host_entry(const lider_index* ix, const float* Qh, int64_t nq, int k,
     float* Qd = (float*)m;
     int64_t* idd = (int64_t*)(m + o_ids);
     float* scd = (float*)(m + o_sc);
-    Workspace w = carve(m + o_ws, ix->g, nq, c, search_shape(ix, k));
+    Workspace w = carve(m + o_ws, ix->g, nq, c, search_shape(ix, k, nq, c));
     cudaError_t e = cudaMemcpyAsync(Qd, Qh, qb, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync(queries)");
     if (!rc) rc = enqueue_search(ix, Qd, nq, k, c, idd, scd, nullptr, w, st);
@@ -1289,7 +1318,7 @@ int search_noalloc_impl(const lider_index* ix, const float* Q, int64_t nq, int k
     if (rc) return rc;
     if (stats) *stats = lider_search_stats{};
     if (nq == 0) return LIDER_OK;
-    const Workspace need = carve(nullptr, ix->g, nq, c, search_shape(ix, k));
+    const Workspace need = carve(nullptr, ix->g, nq, c, search_shape(ix, k, nq, c));
     if (need.total > (size_t)LIDER_NOALLOC_SCRATCH_BYTES)
         return fail(LIDER_ELIMIT, "lider_search_noalloc: this batch needs " + std::to_string(need.total) +
                                       " bytes of scratch, more than the fixed LIDER_NOALLOC_SCRATCH_BYTES (" +
@@ -1297,7 +1326,7 @@ int search_noalloc_impl(const lider_index* ix, const float* Q, int64_t nq, int k
                                       "); search fewer queries per call");
     unsigned char* base = nullptr;
     if ((rc = noalloc_scratch(ix->device, &base))) return rc;
-    const Workspace w = carve(base, ix->g, nq, c, search_shape(ix, k));
+    const Workspace w = carve(base, ix->g, nq, c, search_shape(ix, k, nq, c));
     cudaStream_t st = (cudaStream_t)stream;
     rc = enqueue_search(ix, Q, nq, k, c, out_ids, out_scores, nullptr, w, st);
     if (rc == LIDER_OK && stats) rc = read_stats(w, nq, c, stats, st);
