@@ -244,7 +244,7 @@ int dev_alloc(void** p, size_t bytes, const char* what) {
 void release(lider_index* ix) {
     if (!ix) return;
     void* bufs[] = {ix->X, ix->orig_id, ix->cl_off, ix->C, ix->half_norm, ix->A, ix->bproj,
-                    ix->keys, ix->pos, ix->root, ix->leaf, ix->X_hi, ix->X_lo, ix->row_of, ix->X_bf16};
+                    ix->keys, ix->pos, ix->root, ix->leaf, ix->X_hi, ix->X_lo, ix->row_of, ix->X_bf16, ix->C_hi, ix->C_lo};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (ix->pool) cudaMemPoolDestroy(ix->pool);
@@ -311,6 +311,19 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
     LIDER_CUDA_TRY(cudaMemcpyAsync(ix->bproj, b, (size_t)H * sizeof(float), cudaMemcpyDefault, st));
     half_norm_kernel<<<(unsigned)cdiv(ncl, 128), 128, 0, st>>>(ix->C, ncl, d, ix->half_norm);
     LIDER_LAUNCH_CHECK("half_norm_kernel");
+    if (P->score_mode != LIDER_SCORE_SIMT) {      // tensor-core routing
+        ALLOC(ix->C_hi, (size_t)ncl * d * sizeof(float), "centroid TF32 head");
+        ALLOC(ix->C_lo, (size_t)ncl * d * sizeof(float), "centroid TF32 tail");
+        if ((rc = launch_split_tf32(ix->C, (int64_t)ncl * d, ix->C_hi, ix->C_lo, st))) return rc;
+        if ((rc = make_tensor_map(&ix->map_chi, ix->C_hi, ncl, d, 256))) return rc;
+        if ((rc = make_tensor_map(&ix->map_clo, ix->C_lo, ncl, d, 256))) return rc;
+        std::vector<double> hn(ncl);
+        LIDER_CUDA_TRY(cudaMemcpyAsync(hn.data(), ix->half_norm, ncl * sizeof(double), cudaMemcpyDeviceToHost, st));
+        LIDER_CUDA_TRY(cudaStreamSynchronize(st));
+        double mx = 0.0;
+        for (double v : hn) mx = std::max(mx, std::sqrt(2.0 * v));
+        ix->max_cnorm = (float)mx;
+    }
 
     // 1. partition: nearest centroid of every point
     const int64_t chunk = std::min<int64_t>(n, kRowChunk);

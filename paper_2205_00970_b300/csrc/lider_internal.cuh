@@ -89,6 +89,11 @@ struct lider_index {
     float* X_lo = nullptr;
     int32_t* row_of = nullptr;
     uint16_t* X_bf16 = nullptr;
+    float* C_hi = nullptr;      // centroids, TF32 head / tail (tensor-core routing)
+    float* C_lo = nullptr;
+    float max_cnorm = 0.f;      // largest centroid norm (routing error guard)
+    CUtensorMap map_chi;        // TMA maps over C_hi / C_lo, boxes of 32 x 256
+    CUtensorMap map_clo;
     CUtensorMap map_xbf16;      // TMA map over X_bf16, boxes of 64 x 256
     CUtensorMap map_xhi;        // TMA maps over X_hi / X_lo, boxes of 32 x 256
     CUtensorMap map_xlo;

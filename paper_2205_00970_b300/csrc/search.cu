@@ -42,6 +42,7 @@ enum {
     CNT_CANDIDATES,
     CNT_EMPTY,
     CNT_ITEM,       // persistent-kernel work counter
+    CNT_ROUTE_FALLBACK,
     CNT_SLOTS = 8
 };
 
@@ -81,6 +82,166 @@ __global__ void topc_kernel(const double* __restrict__ S, int64_t nq, int ncl, i
         if (lane == 0) {
             route[q * c + r] = bj;
             if (trace_route) trace_route[q * c + r] = bj;
+        }
+    }
+}
+
+// Tensor-core routing (tensor score modes).  Approximate scores
+// q.mu - |mu|^2/2 of every (query, centroid) come from 128 x 256 tiles of the
+// tcgen05 engine (three TF32 products per FP32 product); a warp per query then
+// takes the c + kRouteExtra best, scores them again exactly (Dot2, finished in
+// FP64) and keeps the c best by exact score (ties -> lower index).  If the
+// best approximate score left out of the shortlist is within the tensor-core
+// error guard of the c-th exact score, every centroid of that query is scored
+// exactly instead.
+constexpr int kRouteExtra = 8;
+
+struct RouteSched {
+    int nq, ncl;
+    __device__ int count() const { return ((nq + 127) / 128) * ((ncl + 255) / 256); }
+    __device__ void coords(int u, int& arow, int& brow) const {
+        const int nct = (ncl + 255) / 256;
+        arow = (u / nct) * 128;
+        brow = (u % nct) * 256;
+    }
+};
+
+struct RouteEpi {
+    float* S;                   // nq x ncl approximate scores
+    const double* half_norm;
+    int nq, ncl;
+    int q, c0;
+    __device__ void begin(int u, int row) {
+        const int nct = (ncl + 255) / 256;
+        q = (u / nct) * 128 + row;
+        c0 = (u % nct) * 256;
+    }
+    __device__ void operator()(int, int, int col0, const uint32_t (&v)[32]) {
+        if (q >= nq) return;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const int j = c0 + col0 + i;
+            if (j < ncl) S[(int64_t)q * ncl + j] = __uint_as_float(v[i]) - (float)half_norm[j];
+        }
+    }
+    __device__ void done(int, int) {}
+};
+
+__global__ void __launch_bounds__(tc::kThreads, 1)
+    route_tc_kernel(const __grid_constant__ CUtensorMap mQhi, const __grid_constant__ CUtensorMap mQlo,
+                    const __grid_constant__ CUtensorMap mChi, const __grid_constant__ CUtensorMap mClo, int kchunks,
+                    RouteSched sched, RouteEpi epi, int* err) {
+    extern __shared__ unsigned char smem[];
+    __shared__ tc::Ctl ctl;
+    tc::gemm_tiles<tc::KindTf32x3>(&mQhi, &mQlo, &mChi, &mClo, kchunks, sched, epi, err, smem, ctl);
+}
+
+// Exact q.mu - |mu|^2/2 by one warp: per-lane Dot2, lanes summed in FP64.
+__device__ __forceinline__ double warp_exact_score(const float* __restrict__ q, const float* __restrict__ mu, int d,
+                                                   double half_norm) {
+    const int lane = threadIdx.x & 31;
+    Dot2 acc{0.f, 0.f};
+    for (int i = lane; i < d; i += 32) dot2_step(acc, q[i], mu[i]);
+    double v = dot2_value(acc);
+    for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return __dadd_rn(v, -half_norm);
+}
+
+__global__ void topc_exact_kernel(const float* __restrict__ S, const float* __restrict__ Q,
+                                  const float* __restrict__ C, const double* __restrict__ half_norm, int64_t nq,
+                                  int ncl, int d, int c, float guard_scale, int32_t* __restrict__ route,
+                                  int32_t* __restrict__ trace_route, unsigned long long* fallbacks) {
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (q >= nq) return;
+    const float* srow = S + q * ncl;
+    const float* qv = Q + q * d;
+    const int nsl = min(c + kRouteExtra, ncl);
+    // shortlist: the nsl best approximate scores (ties -> lower index)
+    int sl[LIDER_MAX_C + kRouteExtra];
+    float ps = INFINITY;
+    int pj = -1;
+    for (int r = 0; r < nsl; ++r) {
+        float best = -INFINITY;
+        int bj = 0x7fffffff;
+        for (int j = lane; j < ncl; j += 32) {
+            float v = srow[j];
+            if (v != v) v = -INFINITY;
+            const bool after = (v < ps) || (v == ps && j > pj);
+            if (after && (v > best || (v == best && j < bj))) { best = v; bj = j; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+            if (ov > best || (ov == best && oj < bj)) { best = ov; bj = oj; }
+        }
+        if (bj >= ncl) bj = 0;
+        ps = best;
+        pj = bj;
+        sl[r] = bj;
+    }
+    // the best approximate score outside the shortlist
+    float a_out = -INFINITY;
+    if (nsl < ncl) {
+        float best = -INFINITY;
+        for (int j = lane; j < ncl; j += 32) {
+            float v = srow[j];
+            if (v != v) v = -INFINITY;
+            const bool after = (v < ps) || (v == ps && j > pj);
+            if (after && v > best) best = v;
+        }
+        for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+        a_out = best;
+    }
+    // exact scores of the shortlist, then the c best
+    double ex[LIDER_MAX_C + kRouteExtra];
+    float qn2 = 0.f;
+    for (int i = lane; i < d; i += 32) qn2 = fmaf(qv[i], qv[i], qn2);
+    for (int o = 16; o > 0; o >>= 1) qn2 += __shfl_xor_sync(0xffffffffu, qn2, o);
+    for (int r = 0; r < nsl; ++r) ex[r] = warp_exact_score(qv, C + (int64_t)sl[r] * d, d, half_norm[sl[r]]);
+    int out[LIDER_MAX_C];
+    double e_c = -INFINITY;
+    {
+        double pe = INFINITY;
+        int pjj = -1;
+        for (int r = 0; r < c; ++r) {
+            double best = -INFINITY;
+            int bj = 0x7fffffff;
+            for (int t = 0; t < nsl; ++t) {
+                const double v = ex[t];
+                const int j = sl[t];
+                const bool after = (v < pe) || (v == pe && j > pjj);
+                if (after && (v > best || (v == best && j < bj))) { best = v; bj = j; }
+            }
+            out[r] = bj;
+            pe = best;
+            pjj = bj;
+            e_c = best;
+        }
+    }
+    const float guard = guard_scale * sqrtf(qn2);
+    if (nsl < ncl && (double)a_out + (double)guard >= e_c) {
+        // a centroid outside the shortlist may beat the c-th: score them all exactly
+        if (lane == 0) atomicAdd(fallbacks, 1ull);
+        double pe = INFINITY;
+        int pjj = -1;
+        for (int r = 0; r < c; ++r) {
+            double best = -INFINITY;
+            int bj = 0x7fffffff;
+            for (int j = 0; j < ncl; ++j) {
+                const double v = warp_exact_score(qv, C + (int64_t)j * d, d, half_norm[j]);
+                const bool after = (v < pe) || (v == pe && j > pjj);
+                if (after && (v > best || (v == best && j < bj))) { best = v; bj = j; }
+            }
+            out[r] = bj < ncl ? bj : 0;
+            pe = best;
+            pjj = bj;
+        }
+    }
+    if (lane == 0) {
+        for (int r = 0; r < c; ++r) {
+            route[q * c + r] = out[r];
+            if (trace_route) trace_route[q * c + r] = out[r];
         }
     }
 }
@@ -911,6 +1072,8 @@ struct Workspace {
     int64_t* bm_off;            // tensor paths: per-cluster bitmap offsets (words)
     uint32_t* bitmap;           // tensor paths: per-pair candidate bitmaps
     int4* units;                // tensor path: tile descriptors
+    float* qs_hi;               // tensor routing: queries, TF32 head / tail
+    float* qs_lo;
     float* qp_hi;               // tensor path: queries in pair order, TF32 head / tail
     float* qp_lo;
     int* tc_err;
@@ -971,6 +1134,8 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, const
     const size_t qelem = sh.mode == LIDER_SCORE_BF16 ? 2 : 4;
     w.qp_hi = tensor ? (float*)take((size_t)np * g.d * qelem) : nullptr;
     w.qp_lo = sh.mode == LIDER_SCORE_TENSOR ? (float*)take((size_t)np * g.d * 4) : nullptr;
+    w.qs_hi = tensor ? (float*)take((size_t)nq * g.d * 4) : nullptr;
+    w.qs_lo = tensor ? (float*)take((size_t)nq * g.d * 4) : nullptr;
     w.off = (int32_t*)take((size_t)(g.ncl + 1) * 4);
     w.cursor = (int32_t*)take((size_t)g.ncl * 4);
     w.item_off = (int32_t*)take((size_t)(g.ncl + 1) * 4);
@@ -1038,10 +1203,36 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         LIDER_CUDA_TRY(cudaMemcpyAsync(tr->qkeys, w.qkeys, (size_t)nq * g.L * 8, cudaMemcpyDeviceToDevice, st));
     // 2. route
     if ((rc = mark(LIDER_PHASE_ROUTE))) return rc;
+    if (ix->params.score_mode != LIDER_SCORE_SIMT) {
+        float* S = reinterpret_cast<float*>(w.rscore);
+        if ((rc = launch_split_tf32(Q, nq * g.d, w.qs_hi, w.qs_lo, st))) return rc;
+        CUtensorMap mqh, mql;
+        if ((rc = make_tensor_map(&mqh, w.qs_hi, nq, g.d, tc::kBM))) return rc;
+        if ((rc = make_tensor_map(&mql, w.qs_lo, nq, g.d, tc::kBM))) return rc;
+        RouteSched rs{(int)nq, g.ncl};
+        RouteEpi re;
+        re.S = S;
+        re.half_norm = g.half_norm;
+        re.nq = (int)nq;
+        re.ncl = g.ncl;
+        const int64_t tiles = cdiv(nq, tc::kBM) * cdiv(g.ncl, tc::kBN);
+        LIDER_CUDA_TRY(cudaFuncSetAttribute(route_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            tc::kSmemBytes));
+        route_tc_kernel<<<(unsigned)std::min<int64_t>(tiles, ix->num_sms), tc::kThreads, tc::kSmemBytes, st>>>(
+            mqh, mql, ix->map_chi, ix->map_clo, (g.d + tc::KindTf32x3::kBK - 1) / tc::KindTf32x3::kBK, rs, re,
+            w.tc_err);
+        LIDER_LAUNCH_CHECK("route_tc_kernel");
+        // guard: the tensor-core error stays below ~1.5e-5 of |q| |mu|; take 3e-5
+        topc_exact_kernel<<<(unsigned)cdiv(nq * 32, 256), 256, 0, st>>>(
+            S, Q, g.C, g.half_norm, nq, g.ncl, g.d, c, 3e-5f * ix->max_cnorm, w.route, tr ? tr->route : nullptr,
+            &w.counters[CNT_ROUTE_FALLBACK]);
+        LIDER_LAUNCH_CHECK("topc_exact_kernel");
+    } else {
     if ((rc = launch_scores(Q, nq, g.d, g.C, g.half_norm, g.ncl, w.rscore, st))) return rc;
     topc_kernel<<<(unsigned)cdiv(nq * 32, 256), 256, 0, st>>>(w.rscore, nq, g.ncl, c, w.route,
                                                               tr ? tr->route : nullptr);
     LIDER_LAUNCH_CHECK("topc_kernel");
+    }
     // 3. group
     if ((rc = mark(LIDER_PHASE_GROUP))) return rc;
     const int G = std::max(1, std::min(kMaxGroup, (96 * 1024) / (g.d * 4)));
