@@ -99,11 +99,12 @@ typedef struct {
 #define LIDER_PHASE_ROUTE   1   /* top-c centroids (Sec. 3.3.2)                     */
 #define LIDER_PHASE_GROUP   2   /* (query, cluster) pairs bucketed by cluster       */
 #define LIDER_PHASE_LOCATE  3   /* re-scale, RMI, bounded search, expansion         */
-#define LIDER_PHASE_GATHER  4   /* queries gathered per cluster (tensor path only)  */
-#define LIDER_PHASE_SCORE   5   /* candidate scores (SIMT path: also per-pair top-k)*/
-#define LIDER_PHASE_SELECT  6   /* per-pair top-k (tensor path only)                */
-#define LIDER_PHASE_MERGE   7   /* per-query merge of the c lists (Sec. 6.2); the
-                                   tensor path re-scores the final lists in FP32   */
+#define LIDER_PHASE_GATHER  4   /* queries gathered per cluster and candidate
+                                   bitmaps marked (tensor modes only)              */
+#define LIDER_PHASE_SCORE   5   /* candidate scores (SIMT mode: also per-pair top-k)*/
+#define LIDER_PHASE_SELECT  6   /* per-query selection (tensor modes only)          */
+#define LIDER_PHASE_MERGE   7   /* SIMT: per-query merge of the c lists (Sec. 6.2);
+                                   tensor modes: FP32 re-score of the selection    */
 #define LIDER_NUM_PHASES    8
 
 /* Optional per-step outputs of a search, for parity checking and profiling.

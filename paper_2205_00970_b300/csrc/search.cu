@@ -12,14 +12,18 @@
 //               (Sec. 7.3), lower bound searched inside the leaf's recorded
 //               error window (with a counted fallback outside it), then the
 //               bi-directional expansion window of Sec. 4 by co-rank search
-//   5. score    score_group_kernel, persistent, one work item (G pairs of
-//               one cluster) at a time: union of each pair's L windows as
-//               bits of a shared-memory position mask, the marked rows
-//               streamed once and scored by exact FP32 inner products with
-//               every query that marked them, then each pair's top-k by
-//               bucket selection and bitonic sort in shared memory
-//   6. merge    merge_kernel, one warp per query: k-way merge of its c lists
-//               (Sec. 6.2, heap of list heads)
+//   5. score    tensor score modes: mark_kernel (each pair's candidate
+//               union as a bitmap), tc_score_kernel (dense 128 x 256 tiles on
+//               tcgen05, candidates kept by the bitmap), select_query_kernel
+//               (each query's best by bucket selection);
+//               SIMT mode: score_group_kernel, persistent, one work item (G
+//               pairs of one cluster) at a time: union of each pair's L
+//               windows as bits of a shared-memory position mask, the marked
+//               rows streamed once and scored by exact FP32 inner products
+//               with every query that marked them, then each pair's top-k
+//   6. merge    SIMT mode: merge_kernel, one warp per query, k-way merge of
+//               its c lists (Sec. 6.2, heap of list heads); tensor modes:
+//               rescore_kernel, exact FP32 scores of the selected lists
 #include <algorithm>
 #include <mutex>
 
@@ -43,6 +47,7 @@ enum {
     CNT_EMPTY,
     CNT_ITEM,       // persistent-kernel work counter
     CNT_ROUTE_FALLBACK,
+    CNT_BOUNDS,     // accesses skipped by a failed bounds check (must stay 0)
     CNT_SLOTS = 8
 };
 
@@ -754,7 +759,7 @@ __global__ void __launch_bounds__(kScoreThreads) score_group_kernel(ScoreArgs a)
 // epilogue keeps only candidates: mark_kernel first writes, per pair, a
 // bitmap over its cluster's positions of the union of its L expansion windows
 // (Sec. 3.3.1), and a tile reads 8 words of it per query.  Each candidate's
-// key goes to the pair's list; topk_pairs_kernel then selects each pair's top k.
+// key goes to the pair's list; select_query_kernel then picks each query's best.
 __global__ void qgather_kernel(const float* __restrict__ Q, const int32_t* __restrict__ pairs, int64_t np, int c,
                                int d, float* __restrict__ qp_hi, float* __restrict__ qp_lo) {
     const int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -856,6 +861,7 @@ struct TcArgs {
     int ncl, T_cap;
     uint64_t* pbuf;
     int32_t* pcount;
+    unsigned long long* bounds;
 };
 
 struct TcSched {
@@ -903,8 +909,13 @@ struct TcEpi {
         if (!w) return;
         uint64_t* dst = a->pbuf + pair * a->T_cap;
 #pragma unroll
-        for (int i = 0; i < 32; ++i)
-            if ((w >> i) & 1u) dst[cursor++] = score_key(__uint_as_float(v[i]), (uint32_t)(p0 + col0 + i));
+        for (int i = 0; i < 32; ++i) {
+            if ((w >> i) & 1u) {
+                if (cursor < a->T_cap) dst[cursor] = score_key(__uint_as_float(v[i]), (uint32_t)(p0 + col0 + i));
+                else atomicAdd(a->bounds, 1ull);
+                ++cursor;
+            }
+        }
     }
 
     __device__ void done(int, int) {}
@@ -923,29 +934,6 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     tc::gemm_tiles<Kind>(&mAhi, &mAlo, &mBhi, &mBlo, kchunks, sched, epi, err, smem, ctl);
 }
 
-// Per pair: top k of its candidate list (bucket selection, see block_topk).
-__global__ void __launch_bounds__(256) topk_pairs_kernel(const uint64_t* __restrict__ pbuf, int T_cap,
-                                                         const int32_t* __restrict__ pcount,
-                                                         const int32_t* __restrict__ route,
-                                                         const int64_t* __restrict__ cl_off,
-                                                         const int64_t* __restrict__ orig_id, int k,
-                                                         float* __restrict__ pscore, int64_t* __restrict__ pid,
-                                                         int32_t* __restrict__ trace_ucount,
-                                                         unsigned long long* counters) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ uint32_t s_bins[kBins];
-    __shared__ uint32_t s_scal[8];
-    uint64_t* K = reinterpret_cast<uint64_t*>(smem);
-    uint64_t* cand = K + next_pow2_dev(T_cap);
-    const int64_t pair = blockIdx.x;
-    const int U = pcount[pair];
-    block_topk(pbuf + pair * T_cap, U, k, K, cand, s_bins, s_scal, cl_off[route[pair]], orig_id,
-               pscore + pair * k, pid + pair * k);
-    if (threadIdx.x == 0) {
-        atomicAdd(&counters[CNT_CANDIDATES], (unsigned long long)U);
-        if (trace_ucount) trace_ucount[pair] = U;
-    }
-}
 
 // Exact re-score of the final lists (tensor-core paths).  The tensor cores'
 // FP32 accumulation is biased toward zero by about 1e-5 relative, uniformly,
@@ -957,7 +945,8 @@ __global__ void __launch_bounds__(256) topk_pairs_kernel(const uint64_t* __restr
 __global__ void __launch_bounds__(256) rescore_kernel(const float* __restrict__ Q, const float* __restrict__ X,
                                                       const int32_t* __restrict__ row_of, int d, int S,
                                                       const int64_t* in_ids, int k, int64_t* out_ids,
-                                                      float* out_scores) {
+                                                      float* out_scores, int64_t n,
+                                                      unsigned long long* bounds) {
     extern __shared__ __align__(16) unsigned char smem[];
     float* qv = reinterpret_cast<float*>(smem);
     uint64_t* key = reinterpret_cast<uint64_t*>(smem + align_up_dev((size_t)d * 4, 16));
@@ -969,7 +958,11 @@ __global__ void __launch_bounds__(256) rescore_kernel(const float* __restrict__ 
     const int SP = next_pow2_dev(S);
     __syncthreads();
     for (int r = warp; r < SP; r += blockDim.x / 32) {
-        const int64_t id = r < S ? in_ids[q * S + r] : -1;
+        int64_t id = r < S ? in_ids[q * S + r] : -1;
+        if (id >= n) {
+            if (lane == 0) atomicAdd(bounds, 1ull);
+            id = -1;
+        }
         uint64_t kv = ~0ull;
         if (id >= 0) {
             const float4* x4 = reinterpret_cast<const float4*>(X + (int64_t)row_of[id] * d);
@@ -997,6 +990,184 @@ __global__ void __launch_bounds__(256) rescore_kernel(const float* __restrict__ 
         } else {
             out_ids[q * k + r] = (int64_t)(uint32_t)kv;
             out_scores[q * k + r] = float_from_order(~(uint32_t)(kv >> 32));
+        }
+    }
+}
+
+// Per-query selection (tensor paths): the ks best keys over the candidate
+// lists of the query's c pairs, without per-pair lists.  Bucket selection on
+// the score between the best and the worst candidate finds the bucket holding
+// the ks-th key; a crowded bucket is refined (up to three levels, each a new
+// histogram of that bucket's keys).  The selected keys, mapped to corpus ids,
+// are sorted (score descending, id ascending).  One block per query.
+constexpr int kSelCap = 4096;
+constexpr int kSelLevels = 3;
+
+__global__ void __launch_bounds__(256) select_query_kernel(const uint64_t* __restrict__ pbuf, int T_cap,
+                                                           const int32_t* __restrict__ pcount,
+                                                           const int32_t* __restrict__ route,
+                                                           const int64_t* __restrict__ cl_off,
+                                                           const int64_t* __restrict__ orig_id, int c, int ks,
+                                                           int64_t* __restrict__ out_ids, float* __restrict__ out_scores,
+                                                           int32_t* __restrict__ trace_ucount,
+                                                           unsigned long long* counters) {
+    __shared__ uint64_t keys[kSelCap];
+    __shared__ uint32_t bins[kBins];
+    __shared__ float lv_lo[kSelLevels], lv_hi[kSelLevels], lv_scale[kSelLevels];
+    __shared__ int lv_sel[kSelLevels];
+    __shared__ int s_levels, s_total, s_n;
+    __shared__ uint32_t s_lo_ord, s_hi_ord;
+    const int64_t q = blockIdx.x;
+    const int tid = threadIdx.x;
+    if (tid == 0) { s_lo_ord = 0xffffffffu; s_hi_ord = 0u; s_total = 0; s_n = 0; }
+    __syncthreads();
+    // pass 0: candidate count and score range (as ordered keys)
+    uint32_t kmin = 0xffffffffu, kmax = 0u;
+    int tot = 0;
+    for (int p = 0; p < c; ++p) {
+        const int64_t pair = q * c + p;
+        int U = pcount[pair];
+        if (U < 0 || U > T_cap) {
+            if (threadIdx.x == 0) atomicAdd(&counters[CNT_BOUNDS], 1ull);
+            U = 0;
+        }
+        tot += U;
+        const uint64_t* seg = pbuf + pair * T_cap;
+        for (int u = tid; u < U; u += blockDim.x) {
+            const uint32_t h = (uint32_t)(seg[u] >> 32);
+            kmin = min(kmin, h);
+            kmax = max(kmax, h);
+        }
+        if (tid == 0 && trace_ucount) trace_ucount[pair] = U;
+    }
+    atomicMin(&s_lo_ord, kmin);
+    atomicMax(&s_hi_ord, kmax);
+    if (tid == 0) {
+        s_total = tot;
+        atomicAdd(&counters[CNT_CANDIDATES], (unsigned long long)tot);
+    }
+    __syncthreads();
+    const int total = s_total;
+    const int need = min(ks, total);
+    // level l: keys whose score lies in [lv_lo, lv_hi]; bucket = (hi - s) * scale
+    auto bucket = [&](int l, float sc) -> uint32_t {
+        const float x = __fmul_rn(__fadd_rn(lv_hi[l], -sc), lv_scale[l]);
+        return (uint32_t)fminf(fmaxf(x, 0.f), (float)(kBins - 1));
+    };
+    // status of a key after the first `levels` levels: 1 selected, 0 rejected, 2 undecided
+    auto status = [&](float sc, int levels) -> int {
+        for (int l = 0; l < levels; ++l) {
+            if (sc > lv_hi[l]) return 1;
+            const uint32_t b = bucket(l, sc);
+            if (b < (uint32_t)lv_sel[l]) return 1;
+            if (b > (uint32_t)lv_sel[l]) return 0;
+        }
+        return 2;
+    };
+    if (tid == 0) {
+        lv_hi[0] = float_from_order(~s_lo_ord);       // best score
+        lv_lo[0] = float_from_order(~s_hi_ord);       // worst score
+        s_levels = 0;
+    }
+    __syncthreads();
+    int above = 0;
+    for (int l = 0; l < kSelLevels && need > 0; ++l) {
+        if (tid == 0) {
+            const float span = lv_hi[l] - lv_lo[l];
+            lv_scale[l] = span > 0.f ? (float)kBins / span : 0.f;
+        }
+        for (int b = tid; b < kBins; b += blockDim.x) bins[b] = 0u;
+        __syncthreads();
+        for (int p = 0; p < c; ++p) {
+            const int64_t pair = q * c + p;
+            const int U = min(max(pcount[pair], 0), T_cap);
+            const uint64_t* seg = pbuf + pair * T_cap;
+            for (int u = tid; u < U; u += blockDim.x) {
+                const float sc = float_from_order(~(uint32_t)(seg[u] >> 32));
+                if (status(sc, l) == 2) atomicAdd(&bins[bucket(l, sc)], 1u);
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t cum = 0;
+            int bsel = kBins - 1;
+            for (int b = 0; b < kBins; ++b) {
+                if (above + (int)(cum + bins[b]) >= need) { bsel = b; break; }
+                cum += bins[b];
+            }
+            lv_sel[l] = bsel;
+            s_levels = l + 1;
+            // refine when the chosen bucket would not fit next to everything above it
+            if (l + 1 < kSelLevels && above + (int)cum + (int)bins[bsel] > kSelCap && lv_scale[l] > 0.f) {
+                lv_hi[l + 1] = __fadd_rn(lv_hi[l], -(float)bsel / lv_scale[l]);
+                lv_lo[l + 1] = __fadd_rn(lv_hi[l], -(float)(bsel + 1) / lv_scale[l]);
+                s_n = above + (int)cum;          // keys above the refined bucket
+            } else {
+                s_n = -1;                        // done
+            }
+        }
+        __syncthreads();
+        if (s_n < 0) break;
+        above = s_n;
+        __syncthreads();
+    }
+    __syncthreads();                 // every thread has read the loop's last flag
+    const int levels = s_levels;
+    if (tid == 0) s_n = 0;
+    __syncthreads();
+    // collect the selected keys as (score, corpus id) keys: first those better
+    // than the last chosen bucket (fewer than ks), then that bucket's keys
+    // while room remains (overflow only drops keys of equal bucket, the last
+    // refinement's resolution)
+    for (int pass = 0; pass < 2 && need > 0; ++pass) {
+        for (int p = 0; p < c; ++p) {
+            const int64_t pair = q * c + p;
+            const int U = min(max(pcount[pair], 0), T_cap);
+            if (U == 0) continue;
+            const uint64_t* seg = pbuf + pair * T_cap;
+            const int rj = route[pair];
+            const int64_t base = cl_off[rj];
+            const int64_t n_c = cl_off[rj + 1] - base;
+            for (int u = tid; u < U; u += blockDim.x) {
+                const uint64_t kv = seg[u];
+                const float sc = float_from_order(~(uint32_t)(kv >> 32));
+                const int st = status(sc, levels);
+                bool take;
+                if (st == 2) {
+                    const uint32_t b = bucket(levels - 1, sc), bs = (uint32_t)lv_sel[levels - 1];
+                    take = pass == 0 ? b < bs : b == bs;
+                } else {
+                    take = pass == 0 && st == 1;
+                }
+                if (take && (int64_t)(uint32_t)kv >= n_c) {
+                    atomicAdd(&counters[CNT_BOUNDS], 1ull);
+                    take = false;
+                }
+                if (take) {
+                    const int slot = atomicAdd(&s_n, 1);
+                    if (slot < kSelCap) {
+                        const int64_t id = orig_id[base + (int64_t)(uint32_t)kv];
+                        keys[slot] = (kv & 0xffffffff00000000ull) | (uint64_t)(uint32_t)id;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    const int n = max(0, min(s_n, kSelCap));
+    const int SP = n > 1 ? next_pow2_dev(n) : 1;
+    for (int u = n + tid; u < SP; u += blockDim.x) keys[u] = ~0ull;
+    __syncthreads();
+    block_bitonic(keys, SP);
+    for (int r = tid; r < ks; r += blockDim.x) {
+        if (r < min(need, n)) {
+            const uint64_t kv = keys[r];
+            out_ids[q * ks + r] = (int64_t)(uint32_t)kv;
+            out_scores[q * ks + r] = float_from_order(~(uint32_t)(kv >> 32));
+        } else {
+            out_ids[q * ks + r] = -1;
+            out_scores[q * ks + r] = -INFINITY;
         }
     }
 }
@@ -1146,8 +1317,8 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, const
     w.pairs = (int32_t*)take((size_t)np * 4);
     w.wstart = (int32_t*)take((size_t)np * g.L * 4);
     w.wlen = (int32_t*)take((size_t)np * g.L * 4);
-    w.pscore = (float*)take((size_t)np * sh.kp * 4);
-    w.pid = (int64_t*)take((size_t)np * sh.kp * 8);
+    w.pscore = tensor ? nullptr : (float*)take((size_t)np * sh.kp * 4);
+    w.pid = tensor ? nullptr : (int64_t*)take((size_t)np * sh.kp * 8);
     w.pbuf = (uint64_t*)take((size_t)np * g.L * sh.R * 8);
     w.sl_ids = sh.mode == LIDER_SCORE_BF16 ? (int64_t*)take((size_t)nq * sh.ks * 8) : nullptr;
     w.sl_scores = sh.mode == LIDER_SCORE_BF16 ? (float*)take((size_t)nq * sh.ks * 4) : nullptr;
@@ -1166,8 +1337,8 @@ int check_search_args(const lider_index* ix, const float* Q, int64_t nq, int k, 
     const int64_t R = (int64_t)ix->params.r0 * k;
     if (R * ix->g.L > LIDER_MAX_LR) return fail(LIDER_ELIMIT, "lider_search: L * r0 * k exceeds LIDER_MAX_LR");
     if (nq * c > (int64_t)INT32_MAX) return fail(LIDER_ELIMIT, "lider_search: nq * c exceeds 2^31-1");
-    if (ix->params.score_mode == LIDER_SCORE_BF16 && (int64_t)ix->params.rerank * k > 8192)
-        return fail(LIDER_ELIMIT, "lider_search: rerank * k exceeds 8192");
+    if (ix->params.score_mode == LIDER_SCORE_BF16 && (int64_t)ix->params.rerank * k > 4096)
+        return fail(LIDER_ELIMIT, "lider_search: rerank * k exceeds 4096");
     if (ix->params.score_mode != LIDER_SCORE_SIMT && c <= ix->g.ncl &&
         nq * ix->top_words[c] > ((int64_t)1 << 32))
         return fail(LIDER_ELIMIT, "lider_search: candidate bitmaps of this batch exceed 16 GiB; search fewer "
@@ -1286,6 +1457,7 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         ta.T_cap = g.L * R;
         ta.pbuf = w.pbuf;
         ta.pcount = w.pcount;
+        ta.bounds = &w.counters[CNT_BOUNDS];
         const int tc_smem = tc::kSmemBytes;
         // A = queries of the tile (128 rows, box 128), B = cluster rows (256, box 256)
         if (bf16) {
@@ -1303,14 +1475,12 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         }
         LIDER_LAUNCH_CHECK("tc_score_kernel");
         if ((rc = mark(LIDER_PHASE_SELECT))) return rc;
-        const int T_cap = g.L * R;
-        const size_t tk_smem = ((size_t)next_pow2(T_cap) + kCandCap) * 8;
-        LIDER_CUDA_TRY(cudaFuncSetAttribute(topk_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)tk_smem));
-        topk_pairs_kernel<<<(unsigned)np, 256, tk_smem, st>>>(w.pbuf, T_cap, w.pcount, w.route, g.cl_off, g.orig_id,
-                                                              sh.kp, w.pscore, w.pid, tr ? tr->ucount : nullptr,
-                                                              w.counters);
-        LIDER_LAUNCH_CHECK("topk_pairs_kernel");
+        int64_t* sel_ids = sh.mode == LIDER_SCORE_BF16 ? w.sl_ids : out_ids;
+        float* sel_sc = sh.mode == LIDER_SCORE_BF16 ? w.sl_scores : out_scores;
+        select_query_kernel<<<(unsigned)nq, 256, 0, st>>>(w.pbuf, g.L * R, w.pcount, w.route, g.cl_off, g.orig_id, c,
+                                                          sh.ks, sel_ids, sel_sc, tr ? tr->ucount : nullptr,
+                                                          w.counters);
+        LIDER_LAUNCH_CHECK("select_query_kernel");
     } else {
         if ((rc = mark(LIDER_PHASE_SCORE))) return rc;
         ScoreArgs sa;
@@ -1355,18 +1525,18 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         LIDER_CUDA_TRY(cudaLaunchKernel(kern, dim3(grid), dim3(kScoreThreads), kargs, smem, st));
         if ((rc = mark(LIDER_PHASE_SELECT))) return rc;
     }
-    // 6. merge, then (tensor paths) the exact FP32 re-score of the final lists
+    // 6. merge (SIMT path), or the exact FP32 re-score of the selected lists (tensor paths)
     if ((rc = mark(LIDER_PHASE_MERGE))) return rc;
-    const bool shortlist = sh.mode == LIDER_SCORE_BF16;
-    int64_t* m_ids = shortlist ? w.sl_ids : out_ids;
-    float* m_sc = shortlist ? w.sl_scores : out_scores;
-    merge_kernel<<<(unsigned)cdiv(nq * 32, 256), 256, 0, st>>>(w.pscore, w.pid, nq, c, sh.kp, sh.ks, m_ids, m_sc);
-    LIDER_LAUNCH_CHECK("merge_kernel");
-    if (sh.mode != LIDER_SCORE_SIMT) {
+    int64_t* m_ids = sh.mode == LIDER_SCORE_BF16 ? w.sl_ids : out_ids;
+    if (sh.mode == LIDER_SCORE_SIMT) {
+        merge_kernel<<<(unsigned)cdiv(nq * 32, 256), 256, 0, st>>>(w.pscore, w.pid, nq, c, sh.kp, sh.ks, out_ids,
+                                                                   out_scores);
+        LIDER_LAUNCH_CHECK("merge_kernel");
+    } else {
         const size_t rs_smem = align_up((size_t)g.d * 4, 16) + (size_t)next_pow2(sh.ks) * 8;
         LIDER_CUDA_TRY(cudaFuncSetAttribute(rescore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem));
         rescore_kernel<<<(unsigned)nq, 256, rs_smem, st>>>(Q, g.X, g.row_of, g.d, sh.ks, m_ids, k, out_ids,
-                                                           out_scores);
+                                                           out_scores, g.n, &w.counters[CNT_BOUNDS]);
         LIDER_LAUNCH_CHECK("rescore_kernel");
     }
     return mark(LIDER_NUM_PHASES);
@@ -1384,6 +1554,9 @@ int read_stats(const Workspace& w, int64_t nq, int c, lider_search_stats* stats,
     if (tc_err)
         return fail(LIDER_ECUDA, "lider_search: tensor-core scoring stopped after a wait timed out (code " +
                                      std::to_string(tc_err) + ")");
+    if (h[CNT_BOUNDS])
+        return fail(LIDER_ECUDA, "lider_search: " + std::to_string(h[CNT_BOUNDS]) +
+                                     " accesses failed a bounds check and were skipped");
     stats->n_queries = nq;
     stats->pairs = nq * c;
     stats->candidates = (int64_t)h[CNT_CANDIDATES];
