@@ -376,6 +376,73 @@ def run_lider(args, cfg):
     return 0
 
 
+def run_serve(args, cfg):
+    """Serving mode: Poisson arrivals of requests (log-uniform sizes of 1 to
+    --serve-max-req queries, k of 10 or the workload's k) at an offered rate,
+    served by the native continuous-batching server; reports the rate served
+    and per-request latency percentiles (submission to results in the
+    caller's host buffers)."""
+    import torch
+
+    from paper_2205_00970_b300 import lider
+    from paper_2205_00970_b300.serving import Server, poisson_schedule, run_load
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    X, Q, C, A, b = load_inputs(cfg)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    Xd = t(X)
+    mode = {"tensor": lider.SCORE_TENSOR, "simt": lider.SCORE_SIMT, "bf16": lider.SCORE_BF16}[args.score]
+    idx = lider.Index(Xd, t(C), t(A), t(b), L=cfg["L"], m=cfg["m"], W=cfg["W"], rmi_leaves=cfg["leaves"],
+                      r0=cfg["r0"], B=cfg["B"], score_mode=mode, rerank=args.rerank)
+    del Xd
+    ks = (10, cfg["k"])
+    srv = Server(idx, cfg["c"], slots=args.serve_slots, max_batch=args.serve_max_batch, max_k=max(ks),
+                 mem_budget=args.serve_mem_gb << 30, max_wait_us=args.serve_wait_us)
+    nq = Q.shape[0]
+    warm = poisson_schedule(args.serve, 0.5, ks=ks, max_req=args.serve_max_req, n_queries=nq, seed=1)
+    for *_, tk in run_load(srv, Q, warm):
+        tk.result()
+    srv.latencies_ms(clear=True)
+    s0 = srv.stats()
+    sch = poisson_schedule(args.serve, args.serve_seconds, ks=ks, max_req=args.serve_max_req, n_queries=nq, seed=2)
+    clocks = ClockSampler(0)
+    clocks.start()
+    t0 = time.perf_counter()
+    sent = run_load(srv, Q, sch)
+    t_sub = time.perf_counter() - t0
+    for *_, tk in sent:
+        tk.result()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    s1 = srv.stats()
+    lat = srv.latencies_ms()
+    srv.close()
+    served = s1["queries"] - s0["queries"]
+    batches = s1["batches"] - s0["batches"]
+    pct = lambda p: float(np.percentile(lat, p)) if lat.size else None
+    line = {
+        "metric": "served queries/s under Poisson load", "value": served / wall, "unit": "queries/s",
+        "offered_qps": args.serve, "offered_qps_actual": float(sch[1].sum() / args.serve_seconds),
+        "n_gpus": 1, "requests": len(sent), "higher_is_better": True,
+        "latency_ms": {"p50": pct(50), "p90": pct(90), "p99": pct(99), "max": pct(100),
+                       "of": "one request, submission to results in host memory"},
+        "batches": batches, "mean_batch_queries": served / max(1, batches),
+        "max_inflight_batches": s1["max_inflight_batches"],
+        "max_inflight_scratch_bytes": s1["max_inflight_bytes"],
+        "host_s": {"submit_loop": t_sub, "launch": s1["launch_s"] - s0["launch_s"],
+                   "finish": s1["finish_s"] - s0["finish_s"], "wall": wall},
+        "dtype": "bf16" if args.score == "bf16" else "f32", "data": "synthetic", "score_mode": args.score,
+        "config": dict(workload_desc(cfg), request_queries=f"log-uniform 1..{args.serve_max_req}",
+                       k=list(ks), slots=args.serve_slots, max_batch=args.serve_max_batch,
+                       max_wait_us=args.serve_wait_us),
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    idx.free()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -384,7 +451,15 @@ def main():
     ap.add_argument("--impl", choices=["lider", "reference"], default="lider")
     ap.add_argument("--workload", default="mid")
     ap.add_argument("--score", choices=["tensor", "simt", "bf16"], default="tensor")
-    ap.add_argument("--rerank", type=int, default=4, help="served BF16 form: shortlist = rerank * k")
+    ap.add_argument("--rerank", type=int, default=2, help="served BF16 form: shortlist = rerank * k")
+    ap.add_argument("--serve", type=float, default=None,
+                    help="serving mode: offered load in queries/s (Poisson arrivals)")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-max-req", type=int, default=256)
+    ap.add_argument("--serve-max-batch", type=int, default=8192)
+    ap.add_argument("--serve-slots", type=int, default=3)
+    ap.add_argument("--serve-mem-gb", type=int, default=16)
+    ap.add_argument("--serve-wait-us", type=float, default=200.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-queries-per-step", type=int, default=8)
@@ -400,6 +475,8 @@ def main():
         cfg["nq"] = min(cfg["nq"], args.nq)
     if args.impl == "reference":
         return run_reference(args, cfg)
+    if args.serve:
+        return run_serve(args, cfg)
     return run_lider(args, cfg)
 
 

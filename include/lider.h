@@ -36,6 +36,7 @@ extern "C" {
 #define LIDER_ENOMEM   -2   /* a device allocation failed                     */
 #define LIDER_ECUDA    -3   /* a CUDA runtime call or kernel launch failed    */
 #define LIDER_ELIMIT   -4   /* a size exceeds a documented implementation cap */
+#define LIDER_ETIMEDOUT -5  /* lider_server_wait: the request is still running */
 
 #define LIDER_HASH_PSTABLE 0   /* h = floor((a.x + b) / W), Sec. 4.1 (p-stable) */
 
@@ -183,6 +184,14 @@ int lider_search_host(const lider_index* index, const float* queries_host, int64
                       int32_t k, int32_t c, int64_t* ids_host, float* scores_host,
                       lider_search_stats* stats, void* stream);
 
+/* Device scratch, in bytes, that lider_search takes from the index's pool for
+ * one call of this shape (host computation only; no device is touched).  A
+ * server uses it to admit batches against a memory budget.  Writes 0 for
+ * nq == 0.  Errors: those of lider_search's argument checks, and
+ * LIDER_EINVAL for a NULL `bytes`. */
+int lider_search_scratch_bytes(const lider_index* index, int64_t nq, int32_t k,
+                               int32_t c, size_t* bytes);
+
 /* Bytes of the fixed device scratch used by lider_search_noalloc. */
 #define LIDER_NOALLOC_SCRATCH_BYTES (64u << 20)
 
@@ -203,6 +212,81 @@ int lider_search_host(const lider_index* index, const float* queries_host, int64
 int lider_search_noalloc(const lider_index* index, const float* queries, int64_t nq,
                          int32_t k, int32_t c, int64_t* out_ids, float* out_scores,
                          lider_search_stats* stats, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Continuous-batching server (the paper has no counterpart: this serves a
+ * stream of independent requests through the batched search above).
+ *
+ * A request is a block of queries on the host, a k, and host buffers for its
+ * results.  A scheduler thread packs pending requests of equal k, oldest first,
+ * into batches of at most max_batch queries and launches a batch when one of
+ * `slots` execution slots (each a CUDA stream with its own pinned and device
+ * staging) is free and the search scratch of the batches in flight, plus this
+ * one, stays within mem_budget bytes; while batches are in flight it waits up
+ * to max_wait_us for more requests before launching a partly filled batch.  A
+ * completion thread finishes batches in launch order, copies each request's
+ * rows into its buffers and records its latency (submission to results).
+ * A request gets exactly the ids and scores lider_search gives for its queries
+ * alone.  All functions are thread-safe. */
+typedef struct lider_server lider_server;
+
+typedef struct {
+    int32_t c;            /* clusters probed per query (as in lider_search)          */
+    int32_t slots;        /* batches in flight, 1..16                                */
+    int32_t max_batch;    /* queries per batch; a request may not exceed it          */
+    int32_t max_k;        /* largest k a request may ask for (<= LIDER_MAX_K)         */
+    int64_t mem_budget;   /* bytes of search scratch the batches in flight may hold  */
+    double max_wait_us;   /* batching window while the device is busy, >= 0           */
+} lider_server_params;
+
+typedef struct {
+    int64_t requests;              /* completed requests                             */
+    int64_t queries;               /* completed queries                              */
+    int64_t batches;               /* completed batches                              */
+    int64_t refused;               /* requests rejected by lider_server_submit       */
+    int64_t failed;                /* requests whose batch failed                    */
+    int32_t max_inflight_batches;
+    int32_t reserved;
+    int64_t max_inflight_bytes;    /* largest scratch held by batches in flight      */
+    double launch_s;               /* host time gathering and enqueueing batches     */
+    double finish_s;               /* host time waiting for and scattering batches   */
+} lider_server_counters;
+
+/* Start a server over `index` (which must outlive it).  Allocates the slots'
+ * staging (pinned host and device) and starts two host threads.  Errors:
+ * LIDER_EINVAL (NULL arguments, c, slots, max_batch, max_k, mem_budget or
+ * max_wait_us out of range), LIDER_ELIMIT (a batch of max_batch queries with
+ * max_k would exceed lider_search's caps), LIDER_ENOMEM, LIDER_ECUDA. */
+int lider_server_create(const lider_index* index, const lider_server_params* params,
+                        lider_server** out);
+
+/* Enqueue a request: queries_host nq x d FP32, results into ids_host and
+ * scores_host (nq x k each, as lider_search writes them).  The three buffers
+ * belong to the server until lider_server_wait reports the request done.
+ * *ticket identifies the request.  nq == 0 completes at once.  Errors:
+ * LIDER_EINVAL (NULL pointers, nq < 0, k < 1, server stopping), LIDER_ELIMIT
+ * (nq > max_batch, k > max_k, or scratch above mem_budget). */
+int lider_server_submit(lider_server* server, const float* queries_host, int64_t nq,
+                        int32_t k, int64_t* ids_host, float* scores_host, int64_t* ticket);
+
+/* Wait up to timeout_s seconds (< 0: no limit) for a request.  LIDER_OK once
+ * its results are in its buffers (each ticket can be waited for once);
+ * LIDER_ETIMEDOUT if it is still running; LIDER_EINVAL for an unknown or
+ * already waited ticket; the batch's error code if its batch failed. */
+int lider_server_wait(lider_server* server, int64_t ticket, double timeout_s);
+
+/* Counters since the server started (host output). */
+int lider_server_stats(lider_server* server, lider_server_counters* stats);
+
+/* Copy up to cap per-request latencies in milliseconds (completion order) to
+ * out_ms; *total receives how many are recorded.  clear != 0 drops them all
+ * afterwards (e.g. after a warm-up). */
+int lider_server_latencies(lider_server* server, double* out_ms, int64_t cap,
+                           int32_t clear, int64_t* total);
+
+/* Finish every submitted request, stop the threads, free the staging.  NULL
+ * is accepted. */
+void lider_server_destroy(lider_server* server);
 
 /* Index shape, host outputs (any may be NULL). */
 int lider_index_info(const lider_index* index, int64_t* n, int32_t* d,

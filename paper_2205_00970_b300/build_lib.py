@@ -11,8 +11,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblider.so")
-SOURCES = ["abi.cu", "kernels.cu", "build.cu", "search.cu", "tc_score.cu"]
-HEADERS = [os.path.join(CSRC, "lider_internal.cuh"), os.path.join(CSRC, "tc.cuh"), os.path.join(ROOT, "include", "lider.h")]
+SOURCES = ["abi.cu", "kernels.cu", "build.cu", "search.cu", "tc_score.cu", "server.cu"]
+HEADERS = [os.path.join(CSRC, "lider_internal.cuh"), os.path.join(CSRC, "tc.cuh"), os.path.join(CSRC, "server_core.h"), os.path.join(ROOT, "include", "lider.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

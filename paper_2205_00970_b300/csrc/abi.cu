@@ -31,6 +31,13 @@ int build_entry(const float*, int64_t, int32_t, const float*, int32_t, const flo
 void destroy_index(lider_index*);
 int search_entry(const lider_index*, const float*, int64_t, int, int, int64_t*, float*, const lider_trace*,
                  lider_search_stats*, void*);
+int search_scratch_entry(const lider_index*, int64_t, int, int, size_t*);
+int server_create_entry(const lider_index*, const lider_server_params*, lider_server**);
+int server_submit_entry(lider_server*, const float*, int64_t, int32_t, int64_t*, float*, int64_t*);
+int server_wait_entry(lider_server*, int64_t, double);
+int server_stats_entry(lider_server*, lider_server_counters*);
+int server_latencies_entry(lider_server*, double*, int64_t, int32_t, int64_t*);
+void server_destroy_entry(lider_server*);
 int search_host_entry(const lider_index*, const float*, int64_t, int, int, int64_t*, float*,
                       lider_search_stats*, void*);
 
@@ -78,6 +85,38 @@ int lider_search_host(const lider_index* index, const float* queries_host, int64
     return guarded([&] {
         return search_host_entry(index, queries_host, nq, k, c, ids_host, scores_host, stats, stream);
     });
+}
+
+int lider_search_scratch_bytes(const lider_index* index, int64_t nq, int32_t k, int32_t c, size_t* bytes) {
+    return guarded([&] { return search_scratch_entry(index, nq, k, c, bytes); });
+}
+
+int lider_server_create(const lider_index* index, const lider_server_params* params, lider_server** out) {
+    return guarded([&] { return server_create_entry(index, params, out); });
+}
+
+int lider_server_submit(lider_server* server, const float* queries_host, int64_t nq, int32_t k,
+                        int64_t* ids_host, float* scores_host, int64_t* ticket) {
+    return guarded([&] { return server_submit_entry(server, queries_host, nq, k, ids_host, scores_host, ticket); });
+}
+
+int lider_server_wait(lider_server* server, int64_t ticket, double timeout_s) {
+    return guarded([&] { return server_wait_entry(server, ticket, timeout_s); });
+}
+
+int lider_server_stats(lider_server* server, lider_server_counters* stats) {
+    return guarded([&] { return server_stats_entry(server, stats); });
+}
+
+int lider_server_latencies(lider_server* server, double* out_ms, int64_t cap, int32_t clear, int64_t* total) {
+    return guarded([&] { return server_latencies_entry(server, out_ms, cap, clear, total); });
+}
+
+void lider_server_destroy(lider_server* server) {
+    try {
+        server_destroy_entry(server);
+    } catch (...) {
+    }
 }
 
 int lider_index_info(const lider_index* index, int64_t* n, int32_t* d, int32_t* n_clusters, lider_params* params) {

@@ -1326,8 +1326,9 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, const
     return w;
 }
 
+// Shape and cap checks; with `buffers`, also the pointers and the device.
 int check_search_args(const lider_index* ix, const float* Q, int64_t nq, int k, int c, const void* ids,
-                      const void* scores) {
+                      const void* scores, bool buffers = true) {
     if (!ix) return fail(LIDER_EINVAL, "lider_search: index is NULL");
     if (nq < 0) return fail(LIDER_EINVAL, "lider_search: nq < 0");
     if (k < 1) return fail(LIDER_EINVAL, "lider_search: k must be >= 1");
@@ -1343,6 +1344,7 @@ int check_search_args(const lider_index* ix, const float* Q, int64_t nq, int k, 
         nq * ix->top_words[c] > ((int64_t)1 << 32))
         return fail(LIDER_ELIMIT, "lider_search: candidate bitmaps of this batch exceed 16 GiB; search fewer "
                                   "queries per call");
+    if (!buffers) return LIDER_OK;
     if (nq > 0 && (!Q || !ids || !scores)) return fail(LIDER_EINVAL, "lider_search: NULL buffer");
     int dev = -1;
     LIDER_CUDA_TRY(cudaGetDevice(&dev));
@@ -1596,6 +1598,15 @@ int search_entry(const lider_index* ix, const float* Q, int64_t nq, int k, int c
     cudaError_t e = cudaFreeAsync(mem, st);
     if (rc == LIDER_OK && e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync");
     return rc;
+}
+
+int search_scratch_entry(const lider_index* ix, int64_t nq, int k, int c, size_t* bytes) {
+    if (!bytes) return fail(LIDER_EINVAL, "lider_search_scratch_bytes: bytes is NULL");
+    *bytes = 0;
+    int rc = check_search_args(ix, nullptr, nq, k, c, nullptr, nullptr, false);
+    if (rc) return rc;
+    if (nq > 0) *bytes = carve(nullptr, ix->g, nq, c, search_shape(ix, k, nq, c)).total;
+    return LIDER_OK;
 }
 
 int search_host_entry(const lider_index* ix, const float* Qh, int64_t nq, int k, int c, int64_t* ids_h,

@@ -17,7 +17,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblider.so")
 
 LIDER_OK = 0
-ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ELIMIT"}
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ELIMIT", -5: "ETIMEDOUT"}
+ETIMEDOUT = -5
 MAX_L, MAX_C, MAX_K, MAX_LR, MAX_D = 32, 32, 1024, 4096, 4096
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -51,6 +52,21 @@ class Trace(ctypes.Structure):
                 ("wstart", ctypes.c_void_p), ("wlen", ctypes.c_void_p), ("ucount", ctypes.c_void_p),
                 ("events", ctypes.POINTER(ctypes.c_void_p))]
 
+class ServerParams(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_int32), ("slots", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("max_k", ctypes.c_int32), ("mem_budget", ctypes.c_int64), ("max_wait_us", ctypes.c_double)]
+
+
+class ServerCounters(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_int64), ("queries", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("refused", ctypes.c_int64), ("failed", ctypes.c_int64), ("max_inflight_batches", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("max_inflight_bytes", ctypes.c_int64), ("launch_s", ctypes.c_double),
+                ("finish_s", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}
+
+
 NUM_PHASES = 8
 PHASES = ("hash", "route", "group", "locate", "gather", "score", "select", "merge")
 
@@ -68,12 +84,19 @@ def _load():
                                ctypes.c_int),
         "lider_search_host": ([P, P, I64, I32, I32, P, P, ctypes.POINTER(Stats), P], ctypes.c_int),
         "lider_search_noalloc": ([P, P, I64, I32, I32, P, P, ctypes.POINTER(Stats), P], ctypes.c_int),
+        "lider_search_scratch_bytes": ([P, I64, I32, I32, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
         "lider_index_info": ([P, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I32),
                               ctypes.POINTER(Params)], ctypes.c_int),
         "lider_cluster_offsets": ([P, P], ctypes.c_int),
         "lider_export_array": ([P, I32, I32, P, P], ctypes.c_int),
         "lider_export_rmi": ([P, I32, I32, P, P, P, P], ctypes.c_int),
         "lider_debug_tc_tile": ([P, I32, P, I32, I32, I32, P, P], ctypes.c_int),
+        "lider_server_create": ([P, ctypes.POINTER(ServerParams), ctypes.POINTER(P)], ctypes.c_int),
+        "lider_server_submit": ([P, P, I64, I32, P, P, ctypes.POINTER(I64)], ctypes.c_int),
+        "lider_server_wait": ([P, I64, ctypes.c_double], ctypes.c_int),
+        "lider_server_stats": ([P, ctypes.POINTER(ServerCounters)], ctypes.c_int),
+        "lider_server_latencies": ([P, P, I64, I32, ctypes.POINTER(I64)], ctypes.c_int),
+        "lider_server_destroy": ([P], None),
         "lider_free": ([P], None),
         "lider_last_error": ([], ctypes.c_char_p),
     }
@@ -89,9 +112,11 @@ _lib = _load()
 
 def exported_symbols() -> list[str]:
     return [n for n in ("lider_build", "lider_search", "lider_search_trace", "lider_search_host",
-                        "lider_search_noalloc", "lider_debug_tc_tile",
+                        "lider_search_noalloc", "lider_search_scratch_bytes", "lider_debug_tc_tile",
                         "lider_index_info", "lider_cluster_offsets", "lider_export_array",
-                        "lider_export_rmi", "lider_free", "lider_last_error") if hasattr(_lib, n)]
+                        "lider_export_rmi", "lider_server_create", "lider_server_submit", "lider_server_wait",
+                        "lider_server_stats", "lider_server_latencies", "lider_server_destroy",
+                        "lider_free", "lider_last_error") if hasattr(_lib, n)]
 
 
 def _check(rc: int):
@@ -213,6 +238,12 @@ class Index:
         _check(_lib.lider_search_host(self._h, Q.data_ptr(), nq, k, c, ids.data_ptr(), scores.data_ptr(),
                                       ctypes.byref(st) if stats else None, _stream_ptr(stream)))
         return (ids, scores, st.as_dict()) if stats else (ids, scores)
+
+    def search_bytes(self, nq: int, k: int, c: int) -> int:
+        """Device scratch one search of nq queries takes from the index's pool."""
+        b = ctypes.c_size_t()
+        _check(_lib.lider_search_scratch_bytes(self._h, nq, k, c, ctypes.byref(b)))
+        return int(b.value)
 
     def cluster_offsets(self) -> np.ndarray:
         off = np.zeros(self.n_clusters + 1, dtype=np.int64)
