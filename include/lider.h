@@ -92,6 +92,13 @@ typedef struct {
     int64_t locate_fallback;   /* lower bounds found outside the RMI error window  */
     int64_t empty_pairs;       /* probed clusters that hold no point               */
     int64_t tc_tiles;          /* 128 x 256 tensor-core tiles computed (tensor path) */
+    int64_t route_fallback;    /* tensor paths: queries whose routing shortlist was
+                                  too close to call and were routed by an exact
+                                  scan of all centroids                          */
+    int64_t select_overflow;   /* plain tensor path: queries whose guard band of
+                                  near-tied candidates did not fit the re-score
+                                  list (their top k may then differ from the exact
+                                  one by near-ties; 0 in normal operation)       */
 } lider_search_stats;
 
 /* Phases of one search, in order; events[i] is recorded when phase i starts

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <functional>
 #include <cmath>
+#include <cstring>
 
 #include "lider_internal.cuh"
 
@@ -78,6 +79,19 @@ __global__ void gather_rows_kernel(const float* __restrict__ src, const int64_t*
     const float4* s = reinterpret_cast<const float4*>(src + ids[row] * (int64_t)d);
     float4* o = reinterpret_cast<float4*>(dst + row * (int64_t)d);
     for (int i = lane; i < d / 4; i += 32) o[i] = s[i];
+}
+
+// Largest row norm, as the bits of a non-negative float (atomicMax on the
+// bits orders non-negative floats); warp per row, FP64 sum of squares.
+__global__ void max_row_norm_kernel(const float* __restrict__ X, int64_t n, int d, unsigned int* __restrict__ out) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const float* x = X + row * d;
+    double s = 0.0;
+    for (int i = lane; i < d; i += 32) s = fma((double)x[i], (double)x[i], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) atomicMax(out, __float_as_uint(__double2float_ru(sqrt(s))));
 }
 
 __global__ void inverse_ids_kernel(const int64_t* __restrict__ orig_id, int64_t n, int32_t* __restrict__ row_of) {
@@ -411,6 +425,17 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
         ALLOC(ix->row_of, (size_t)n * sizeof(int32_t), "row of id");
         inverse_ids_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(ix->orig_id, n, ix->row_of);
         LIDER_LAUNCH_CHECK("inverse_ids_kernel");
+        DevBuf mx;
+        ALLOC(mx.p, sizeof(unsigned int), "row norm");
+        LIDER_CUDA_TRY(cudaMemsetAsync(mx.p, 0, sizeof(unsigned int), st));
+        max_row_norm_kernel<<<(unsigned)cdiv(n * 32, 256), 256, 0, st>>>(ix->X, n, d, mx.as<unsigned int>());
+        LIDER_LAUNCH_CHECK("max_row_norm_kernel");
+        unsigned int bits = 0;
+        LIDER_CUDA_TRY(cudaMemcpyAsync(&bits, mx.p, sizeof(bits), cudaMemcpyDeviceToHost, st));
+        LIDER_CUDA_TRY(cudaStreamSynchronize(st));
+        float xn;
+        std::memcpy(&xn, &bits, sizeof(xn));
+        ix->max_xnorm = xn;
 
     }
 

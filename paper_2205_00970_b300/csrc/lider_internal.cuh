@@ -92,6 +92,7 @@ struct lider_index {
     float* C_hi = nullptr;      // centroids, TF32 head / tail (tensor-core routing)
     float* C_lo = nullptr;
     float max_cnorm = 0.f;      // largest centroid norm (routing error guard)
+    float max_xnorm = 0.f;      // largest corpus row norm (candidate error guard)
     CUtensorMap map_chi;        // TMA maps over C_hi / C_lo, boxes of 32 x 256
     CUtensorMap map_clo;
     CUtensorMap map_xbf16;      // TMA map over X_bf16, boxes of 64 x 256

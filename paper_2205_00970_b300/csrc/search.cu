@@ -48,7 +48,8 @@ enum {
     CNT_ITEM,       // persistent-kernel work counter
     CNT_ROUTE_FALLBACK,
     CNT_BOUNDS,     // accesses skipped by a failed bounds check (must stay 0)
-    CNT_SLOTS = 8
+    CNT_SEL_OVERFLOW,  // queries whose guarded candidate band did not fit (result may be inexact)
+    CNT_SLOTS = 9
 };
 
 inline int next_pow2(int x) {
@@ -100,6 +101,13 @@ __global__ void topc_kernel(const double* __restrict__ S, int64_t nq, int ncl, i
 // error guard of the c-th exact score, every centroid of that query is scored
 // exactly instead.
 constexpr int kRouteExtra = 8;
+// Bound on the error of one 3xTF32 tensor-core score, relative to |q| |x|
+// (the product of the two norms).  The dropped lo*lo term and the TF32
+// rounding of the tails contribute about 3 * 2^-22 of sum |q_i x_i| <= |q| |x|;
+// with the tensor cores' FP32 accumulation the engine tests measure less than
+// 2e-6 of sum |q_i x_i| up to d = 784, so 3e-5 leaves a wide margin.  The
+// route and candidate guards use it.
+constexpr float kTcGuard = 3e-5f;
 
 struct RouteSched {
     int nq, ncl;
@@ -155,7 +163,8 @@ __device__ __forceinline__ double warp_exact_score(const float* __restrict__ q, 
 __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __restrict__ Q,
                                   const float* __restrict__ C, const double* __restrict__ half_norm, int64_t nq,
                                   int ncl, int d, int c, float guard_scale, int32_t* __restrict__ route,
-                                  int32_t* __restrict__ trace_route, unsigned long long* fallbacks) {
+                                  int32_t* __restrict__ trace_route, float* __restrict__ qnorm,
+                                  unsigned long long* fallbacks) {
     const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (q >= nq) return;
@@ -225,6 +234,7 @@ __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __re
         }
     }
     const float guard = guard_scale * sqrtf(qn2);
+    if (lane == 0) qnorm[q] = sqrtf(qn2);
     if (nsl < ncl && (double)a_out + (double)guard >= e_c) {
         // a centroid outside the shortlist may beat the c-th: score them all exactly
         if (lane == 0) atomicAdd(fallbacks, 1ull);
@@ -1008,6 +1018,7 @@ __global__ void __launch_bounds__(256) select_query_kernel(const uint64_t* __res
                                                            const int32_t* __restrict__ route,
                                                            const int64_t* __restrict__ cl_off,
                                                            const int64_t* __restrict__ orig_id, int c, int ks,
+                                                           const float* __restrict__ qnorm, float guard_scale, int so,
                                                            int64_t* __restrict__ out_ids, float* __restrict__ out_scores,
                                                            int32_t* __restrict__ trace_ucount,
                                                            unsigned long long* counters) {
@@ -1016,6 +1027,8 @@ __global__ void __launch_bounds__(256) select_query_kernel(const uint64_t* __res
     __shared__ float lv_lo[kSelLevels], lv_hi[kSelLevels], lv_scale[kSelLevels];
     __shared__ int lv_sel[kSelLevels];
     __shared__ int s_levels, s_total, s_n;
+    __shared__ float s_thr;
+    __shared__ int s_band;
     __shared__ uint32_t s_lo_ord, s_hi_ord;
     const int64_t q = blockIdx.x;
     const int tid = threadIdx.x;
@@ -1113,8 +1126,21 @@ __global__ void __launch_bounds__(256) select_query_kernel(const uint64_t* __res
     }
     __syncthreads();                 // every thread has read the loop's last flag
     const int levels = s_levels;
-    if (tid == 0) s_n = 0;
+    if (tid == 0) {
+        s_n = 0;
+        // guard band: every key whose approximate score is within twice the
+        // error bound of the chosen bucket's lower edge (and so of the ks-th
+        // key) joins the list, so the exact re-score sees the exact top ks
+        s_thr = INFINITY;
+        if (guard_scale > 0.f && levels > 0) {
+            const int l = levels - 1;
+            const float edge = lv_scale[l] > 0.f ? __fadd_rn(lv_hi[l], -(float)(lv_sel[l] + 1) / lv_scale[l])
+                                                 : lv_lo[l];
+            s_thr = edge - 2.f * guard_scale * qnorm[q];
+        }
+    }
     __syncthreads();
+    const float thr = s_thr;
     // collect the selected keys as (score, corpus id) keys: first those better
     // than the last chosen bucket (fewer than ks), then that bucket's keys
     // while room remains (overflow only drops keys of equal bucket, the last
@@ -1135,9 +1161,9 @@ __global__ void __launch_bounds__(256) select_query_kernel(const uint64_t* __res
                 bool take;
                 if (st == 2) {
                     const uint32_t b = bucket(levels - 1, sc), bs = (uint32_t)lv_sel[levels - 1];
-                    take = pass == 0 ? b < bs : b == bs;
+                    take = pass == 0 ? b < bs : (b == bs || (b > bs && sc >= thr));
                 } else {
-                    take = pass == 0 && st == 1;
+                    take = pass == 0 ? st == 1 : (st == 0 && sc >= thr);
                 }
                 if (take && (int64_t)(uint32_t)kv >= n_c) {
                     atomicAdd(&counters[CNT_BOUNDS], 1ull);
@@ -1156,18 +1182,34 @@ __global__ void __launch_bounds__(256) select_query_kernel(const uint64_t* __res
     }
     __syncthreads();
     const int n = max(0, min(s_n, kSelCap));
+    const bool spilled = s_n > kSelCap;
     const int SP = n > 1 ? next_pow2_dev(n) : 1;
     for (int u = n + tid; u < SP; u += blockDim.x) keys[u] = ~0ull;
     __syncthreads();
     block_bitonic(keys, SP);
-    for (int r = tid; r < ks; r += blockDim.x) {
-        if (r < min(need, n)) {
+    // guard mode: keep every key within twice the error bound of the ks-th
+    // best approximate score (the exact top ks is among them); else the ks best
+    int keep = min(need, n);
+    if (guard_scale > 0.f && keep > 0) {
+        const float vk = float_from_order(~(uint32_t)(keys[keep - 1] >> 32));
+        const float t = vk - 2.f * guard_scale * qnorm[q];
+        if (tid == 0) s_band = keep;
+        __syncthreads();
+        for (int r = keep + tid; r < n; r += blockDim.x)
+            if (float_from_order(~(uint32_t)(keys[r] >> 32)) >= t) atomicMax(&s_band, r + 1);
+        __syncthreads();
+        const int band = s_band;
+        if (tid == 0 && (spilled || band > so)) atomicAdd(&counters[CNT_SEL_OVERFLOW], 1ull);
+        keep = min(band, so);
+    }
+    for (int r = tid; r < so; r += blockDim.x) {
+        if (r < keep) {
             const uint64_t kv = keys[r];
-            out_ids[q * ks + r] = (int64_t)(uint32_t)kv;
-            out_scores[q * ks + r] = float_from_order(~(uint32_t)(kv >> 32));
+            out_ids[q * so + r] = (int64_t)(uint32_t)kv;
+            out_scores[q * so + r] = float_from_order(~(uint32_t)(kv >> 32));
         } else {
-            out_ids[q * ks + r] = -1;
-            out_scores[q * ks + r] = -INFINITY;
+            out_ids[q * so + r] = -1;
+            out_scores[q * so + r] = -INFINITY;
         }
     }
 }
@@ -1236,8 +1278,9 @@ struct Workspace {
     float* pscore;
     int64_t* pid;
     uint64_t* pbuf;
-    int64_t* sl_ids;            // served form: per-query shortlist (nq x ks)
+    int64_t* sl_ids;            // tensor paths: per-query list before the re-score (nq x so)
     float* sl_scores;
+    float* qnorm;               // tensor paths: |q| (FP32), for the error guards
     int32_t* pcount;            // tensor path: candidates per pair (cleared)
     int32_t* unit_off;
     int64_t* bm_off;            // tensor paths: per-cluster bitmap offsets (words)
@@ -1258,6 +1301,7 @@ struct Workspace {
 // re-score (ks).  The served BF16 form keeps a shortlist of rerank * k.
 struct Shape {
     int mode, R, kp, ks;
+    int so;                    // tensor paths: stride of the selected lists (ks + guard band)
     int64_t bitmap_words;      // bound on the candidate bitmaps of one search
 };
 
@@ -1272,9 +1316,11 @@ Shape search_shape(const lider_index* ix, int k, int64_t nq = 0, int c = 0) {
     if (sh.mode == LIDER_SCORE_BF16) {
         sh.ks = ix->params.rerank * k;
         sh.kp = std::min(sh.ks, T_cap);
+        sh.so = sh.ks;
     } else {
         sh.ks = k;
         sh.kp = k;
+        sh.so = std::min(kSelCap, 2 * k + 32);
     }
     return sh;
 }
@@ -1320,8 +1366,9 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, const
     w.pscore = tensor ? nullptr : (float*)take((size_t)np * sh.kp * 4);
     w.pid = tensor ? nullptr : (int64_t*)take((size_t)np * sh.kp * 8);
     w.pbuf = (uint64_t*)take((size_t)np * g.L * sh.R * 8);
-    w.sl_ids = sh.mode == LIDER_SCORE_BF16 ? (int64_t*)take((size_t)nq * sh.ks * 8) : nullptr;
-    w.sl_scores = sh.mode == LIDER_SCORE_BF16 ? (float*)take((size_t)nq * sh.ks * 4) : nullptr;
+    w.sl_ids = tensor ? (int64_t*)take((size_t)nq * sh.so * 8) : nullptr;
+    w.sl_scores = tensor ? (float*)take((size_t)nq * sh.so * 4) : nullptr;
+    w.qnorm = tensor ? (float*)take((size_t)nq * 4) : nullptr;
     w.total = o;
     return w;
 }
@@ -1395,10 +1442,10 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
             mqh, mql, ix->map_chi, ix->map_clo, (g.d + tc::KindTf32x3::kBK - 1) / tc::KindTf32x3::kBK, rs, re,
             w.tc_err);
         LIDER_LAUNCH_CHECK("route_tc_kernel");
-        // guard: the tensor-core error stays below ~1.5e-5 of |q| |mu|; take 3e-5
+        // guard: the tensor-core error of one score stays below kTcGuard |q| |mu|
         topc_exact_kernel<<<(unsigned)cdiv(nq * 32, 256), 256, 0, st>>>(
-            S, Q, g.C, g.half_norm, nq, g.ncl, g.d, c, 3e-5f * ix->max_cnorm, w.route, tr ? tr->route : nullptr,
-            &w.counters[CNT_ROUTE_FALLBACK]);
+            S, Q, g.C, g.half_norm, nq, g.ncl, g.d, c, kTcGuard * ix->max_cnorm, w.route,
+            tr ? tr->route : nullptr, w.qnorm, &w.counters[CNT_ROUTE_FALLBACK]);
         LIDER_LAUNCH_CHECK("topc_exact_kernel");
     } else {
     if ((rc = launch_scores(Q, nq, g.d, g.C, g.half_norm, g.ncl, w.rscore, st))) return rc;
@@ -1477,11 +1524,12 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         }
         LIDER_LAUNCH_CHECK("tc_score_kernel");
         if ((rc = mark(LIDER_PHASE_SELECT))) return rc;
-        int64_t* sel_ids = sh.mode == LIDER_SCORE_BF16 ? w.sl_ids : out_ids;
-        float* sel_sc = sh.mode == LIDER_SCORE_BF16 ? w.sl_scores : out_scores;
+        // plain tensor path: a guard band makes the re-scored top k exact; the
+        // served BF16 form keeps its approximate shortlist
+        const float cand_guard = sh.mode == LIDER_SCORE_TENSOR ? kTcGuard * ix->max_xnorm : 0.f;
         select_query_kernel<<<(unsigned)nq, 256, 0, st>>>(w.pbuf, g.L * R, w.pcount, w.route, g.cl_off, g.orig_id, c,
-                                                          sh.ks, sel_ids, sel_sc, tr ? tr->ucount : nullptr,
-                                                          w.counters);
+                                                          sh.ks, w.qnorm, cand_guard, sh.so, w.sl_ids, w.sl_scores,
+                                                          tr ? tr->ucount : nullptr, w.counters);
         LIDER_LAUNCH_CHECK("select_query_kernel");
     } else {
         if ((rc = mark(LIDER_PHASE_SCORE))) return rc;
@@ -1529,15 +1577,14 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
     }
     // 6. merge (SIMT path), or the exact FP32 re-score of the selected lists (tensor paths)
     if ((rc = mark(LIDER_PHASE_MERGE))) return rc;
-    int64_t* m_ids = sh.mode == LIDER_SCORE_BF16 ? w.sl_ids : out_ids;
     if (sh.mode == LIDER_SCORE_SIMT) {
         merge_kernel<<<(unsigned)cdiv(nq * 32, 256), 256, 0, st>>>(w.pscore, w.pid, nq, c, sh.kp, sh.ks, out_ids,
                                                                    out_scores);
         LIDER_LAUNCH_CHECK("merge_kernel");
     } else {
-        const size_t rs_smem = align_up((size_t)g.d * 4, 16) + (size_t)next_pow2(sh.ks) * 8;
+        const size_t rs_smem = align_up((size_t)g.d * 4, 16) + (size_t)next_pow2(sh.so) * 8;
         LIDER_CUDA_TRY(cudaFuncSetAttribute(rescore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem));
-        rescore_kernel<<<(unsigned)nq, 256, rs_smem, st>>>(Q, g.X, g.row_of, g.d, sh.ks, m_ids, k, out_ids,
+        rescore_kernel<<<(unsigned)nq, 256, rs_smem, st>>>(Q, g.X, g.row_of, g.d, sh.so, w.sl_ids, k, out_ids,
                                                            out_scores, g.n, &w.counters[CNT_BOUNDS]);
         LIDER_LAUNCH_CHECK("rescore_kernel");
     }
@@ -1567,6 +1614,8 @@ int read_stats(const Workspace& w, int64_t nq, int c, lider_search_stats* stats,
     stats->locate_fallback = (int64_t)h[CNT_FALLBACK];
     stats->empty_pairs = (int64_t)h[CNT_EMPTY];
     stats->tc_tiles = tiles;
+    stats->route_fallback = (int64_t)h[CNT_ROUTE_FALLBACK];
+    stats->select_overflow = (int64_t)h[CNT_SEL_OVERFLOW];
     return LIDER_OK;
 }
 

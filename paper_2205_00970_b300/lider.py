@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in
                 ("n_queries", "pairs", "candidates", "qkey_boundary", "qkey_clamped",
-                 "locate_fallback", "empty_pairs", "tc_tiles")]
+                 "locate_fallback", "empty_pairs", "tc_tiles", "route_fallback", "select_overflow")]
 
     def as_dict(self) -> dict:
         return {n: int(getattr(self, n)) for n, _ in self._fields_}

@@ -22,7 +22,7 @@ def mid():
     ids, sc, stats, tr = gidx.search(torch.from_numpy(Q).cuda(), cfg["k"], cfg["c"], stats=True, trace=True)
     ref_idx = F.oracle_index(cfg, X, C, A, b)
     ref = O.search(ref_idx, Q[SAMPLE], cfg["k"], cfg["c"], cfg["R"])
-    return dict(cfg=cfg, X=X, Q=Q, gidx=gidx, ids=ids.cpu().numpy(), sc=sc.cpu().numpy(), stats=stats,
+    return dict(cfg=cfg, X=X, Q=Q, C=C, A=A, b=b, gidx=gidx, ids=ids.cpu().numpy(), sc=sc.cpu().numpy(), stats=stats,
                 tr={k: v[SAMPLE] for k, v in tr.items()}, ref_idx=ref_idx, ref=ref)
 
 
@@ -73,3 +73,18 @@ def test_mid_counters(mid):
     assert st["pairs"] == 10_000 * 8 and st["empty_pairs"] == 0
     assert st["candidates"] > 0
     assert st["qkey_clamped"] == 0
+    assert st["select_overflow"] == 0
+
+
+def test_mid_tensor_equals_simt_exactly(mid):
+    """At full size, all 10,000 queries: the tensor-core path's results equal
+    the SIMT path's (the exact FP32 top-k of each candidate union) bit for bit."""
+    import torch
+    cfg, X, Q, C, A, b = (mid[n] for n in ("cfg", "X", "Q", "C", "A", "b"))
+    g = F.gpu_index(dict(cfg, score_mode=1), X, C, A, b)
+    ids, sc = g.search(torch.from_numpy(Q).cuda(), cfg["k"], cfg["c"])
+    g.free()
+    ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+    diff = np.nonzero(np.any(ids != mid["ids"], axis=1))[0]
+    assert diff.size == 0, (diff[:10], diff.size)
+    assert np.array_equal(sc.view(np.uint32), mid["sc"].view(np.uint32))

@@ -207,3 +207,23 @@ def test_served_bf16_form():
     assert agree / total > 0.995, agree / total
     sub_ids, sub_sc = g.search(Qd[37:291].contiguous(), cfg["k"], cfg["c"])
     assert np.array_equal(sub_ids.cpu().numpy(), ids[37:291])
+
+
+@pytest.mark.parametrize("k", [1, 10, 37])
+def test_tensor_path_equals_simt_path_exactly(k):
+    """The tensor-core path (3xTF32 scores, a guard band around the k-th
+    approximate score, exact FP32 re-score) returns exactly the SIMT path's
+    results: the exact FP32 top-k of every query's candidate union, same ids,
+    same scores bit for bit, ties by lower id."""
+    import torch
+    cfg, X, Q, C, A, b = F.workload("tiny")
+    Qd = torch.from_numpy(Q).cuda()
+    out = {}
+    for mode in (0, 1):
+        g = F.gpu_index(dict(cfg, score_mode=mode), X, C, A, b)
+        ids, sc, st = g.search(Qd, k, cfg["c"], stats=True)
+        out[mode] = (ids.cpu().numpy(), sc.cpu().numpy(), st)
+        g.free()
+    assert out[0][2]["select_overflow"] == 0
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1].view(np.uint32), out[1][1].view(np.uint32))
