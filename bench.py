@@ -38,7 +38,9 @@ from paper_2205_00970_b300 import configs, synth  # noqa: E402
 
 METRIC = "queries/s at fixed recall@10 vs FP64 oracle (plain vs served BF16); p50/p99 ms"
 # our kernels per lider_search (phase list in search.cu; confirmed by the ncu launch list)
-LAUNCHES_PER_SEARCH = {"tensor": 15, "simt": 10, "bf16": 15}
+LAUNCHES_PER_SEARCH = {"tensor": 15, "simt": 10, "bf16": 15, "f16": 15}
+MODES = {"tensor": 0, "simt": 1, "bf16": 2, "f16": 3}
+DTYPES = {"tensor": "f32", "simt": "f32", "bf16": "bf16", "f16": "f16"}
 
 
 def workload_desc(cfg) -> dict:
@@ -250,7 +252,7 @@ def run_lider(args, cfg):
     X, Q, C, A, b = load_inputs(cfg)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     Xd = t(X)
-    mode = {"tensor": lider.SCORE_TENSOR, "simt": lider.SCORE_SIMT, "bf16": lider.SCORE_BF16}[args.score]
+    mode = MODES[args.score]
     idx = lider.Index(Xd, t(C), t(A), t(b), L=cfg["L"], m=cfg["m"], W=cfg["W"], rmi_leaves=cfg["leaves"],
                       r0=cfg["r0"], B=cfg["B"], score_mode=mode, rerank=args.rerank)
     del Xd
@@ -318,7 +320,7 @@ def run_lider(args, cfg):
     score_s = phase_ms["score"] / 1e3
     hbm, bf16, bf16_sus, peak_kind = measured_peaks()
     src = "MEASURED_PEAKS.json" if peak_kind == "measured" else "fallback figures"
-    if args.score in ("tensor", "bf16"):
+    if args.score in ("tensor", "bf16", "f16"):
         if args.score == "tensor":
             kpad = -(-d // 32) * 32
             tc_flop = stats["tc_tiles"] * 128 * 256 * kpad * 2.0 * 3   # three TF32 products per FP32 product
@@ -328,7 +330,7 @@ def run_lider(args, cfg):
             kpad = -(-d // 64) * 64
             tc_flop = stats["tc_tiles"] * 128 * 256 * kpad * 2.0       # one BF16 product
             peak = bf16
-            psrc = f"{src}: bf16 burst"
+            psrc = f"{src}: bf16 burst" + (" (FP16 has the same dense rate)" if args.score == "f16" else "")
         achieved = tc_flop / score_s / 1e12
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None, "kernel": "tc_score_kernel",
@@ -353,7 +355,7 @@ def run_lider(args, cfg):
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if args.score == "bf16" else "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.score], "data": "synthetic",
         "config": dict(workload_desc(cfg), parallelism=f"replicas x{world}"),
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "of": f"one batch of {nq:,} queries"},
@@ -392,7 +394,7 @@ def run_serve(args, cfg):
     X, Q, C, A, b = load_inputs(cfg)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     Xd = t(X)
-    mode = {"tensor": lider.SCORE_TENSOR, "simt": lider.SCORE_SIMT, "bf16": lider.SCORE_BF16}[args.score]
+    mode = MODES[args.score]
     idx = lider.Index(Xd, t(C), t(A), t(b), L=cfg["L"], m=cfg["m"], W=cfg["W"], rmi_leaves=cfg["leaves"],
                       r0=cfg["r0"], B=cfg["B"], score_mode=mode, rerank=args.rerank)
     del Xd
@@ -432,7 +434,7 @@ def run_serve(args, cfg):
         "max_inflight_scratch_bytes": s1["max_inflight_bytes"],
         "host_s": {"submit_loop": t_sub, "launch": s1["launch_s"] - s0["launch_s"],
                    "finish": s1["finish_s"] - s0["finish_s"], "wall": wall},
-        "dtype": "bf16" if args.score == "bf16" else "f32", "data": "synthetic", "score_mode": args.score,
+        "dtype": DTYPES[args.score], "data": "synthetic", "score_mode": args.score,
         "config": dict(workload_desc(cfg), request_queries=f"log-uniform 1..{args.serve_max_req}",
                        k=list(ks), slots=args.serve_slots, max_batch=args.serve_max_batch,
                        max_wait_us=args.serve_wait_us),
@@ -450,7 +452,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["lider", "reference"], default="lider")
     ap.add_argument("--workload", default="mid")
-    ap.add_argument("--score", choices=["tensor", "simt", "bf16"], default="tensor")
+    ap.add_argument("--score", choices=list(MODES), default="tensor")
     ap.add_argument("--rerank", type=int, default=2, help="served BF16 form: shortlist = rerank * k")
     ap.add_argument("--serve", type=float, default=None,
                     help="serving mode: offered load in queries/s (Poisson arrivals)")

@@ -40,12 +40,19 @@ extern "C" {
 
 #define LIDER_HASH_PSTABLE 0   /* h = floor((a.x + b) / W), Sec. 4.1 (p-stable) */
 
-/* How candidates are scored (the results are the same within FP32 rounding). */
+/* How candidates are scored.  SIMT, TENSOR and F16 return the same results
+ * bit for bit: the exact FP32 top-k of each query's candidate union (the two
+ * tensor modes select by an approximate score plus a guard band of twice its
+ * proven error bound, then re-score that list exactly on the CUDA cores). */
 #define LIDER_SCORE_TENSOR 0   /* tcgen05 tensor cores, 3 TF32 products per FP32 product */
 #define LIDER_SCORE_SIMT   1   /* FP32 FMA on the CUDA cores                             */
 #define LIDER_SCORE_BF16   2   /* served form: BF16 corpus copy scored on the tensor
                                   cores (FP32 accumulation), then an FP32 re-rank of a
-                                  shortlist of rerank * k candidates per query       */
+                                  shortlist of rerank * k candidates per query (not
+                                  exact: a candidate may miss the shortlist)          */
+#define LIDER_SCORE_F16    3   /* tcgen05 tensor cores on FP16 copies of the corpus and
+                                  queries (each scaled by a power of two), FP32
+                                  accumulation, guard band, exact FP32 re-score      */
 
 /* Implementation caps (checked; LIDER_ELIMIT beyond them). */
 #define LIDER_MAX_L        32      /* hashkey arrays per core model (H)     */
@@ -66,8 +73,9 @@ typedef struct lider_index lider_index;   /* opaque; owns its device memory */
  *        (Sec. 4.2); floor(64/m) * B must be <= 56;
  *   hash_kind = LIDER_HASH_PSTABLE;
  *   W  = p-stable bucket width (> 0);
- *   score_mode = LIDER_SCORE_TENSOR, LIDER_SCORE_SIMT or LIDER_SCORE_BF16
- *        (tensor modes need L <= 16; BF16 needs d % 8 == 0);
+ *   score_mode = LIDER_SCORE_TENSOR, LIDER_SCORE_SIMT, LIDER_SCORE_BF16 or
+ *        LIDER_SCORE_F16 (tensor modes need L <= 16; BF16 and F16 need
+ *        d % 8 == 0);
  *   rerank = shortlist factor of LIDER_SCORE_BF16: rerank * k candidates per
  *        query are re-scored in FP32 (0 means 4). */
 typedef struct {
@@ -323,7 +331,9 @@ int lider_export_rmi(const lider_index* index, int32_t cluster, int32_t array,
  * out[m x n] = A[m x d] . B[n x d]^T for device row-major FP32 A, B, out with
  * 1 <= m <= 128, 1 <= n <= 256.  kind 0: three TF32 products per FP32 product
  * (d % 4 == 0); kind 1: A and B rounded to BF16, one product, FP32
- * accumulation (d % 8 == 0).  Synchronous; allocates its own scratch.
+ * accumulation (d % 8 == 0); kind 2: the same with FP16 (values outside
+ * FP16's range saturate or flush; no scaling).  Synchronous; allocates its
+ * own scratch.
  * LIDER_ECUDA if an internal wait times out (the kernel then exits cleanly). */
 int lider_debug_tc_tile(const float* A, int32_t m, const float* B, int32_t n, int32_t d,
                         int32_t kind, float* out, void* stream);

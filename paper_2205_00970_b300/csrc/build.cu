@@ -81,17 +81,28 @@ __global__ void gather_rows_kernel(const float* __restrict__ src, const int64_t*
     for (int i = lane; i < d / 4; i += 32) o[i] = s[i];
 }
 
-// Largest row norm, as the bits of a non-negative float (atomicMax on the
-// bits orders non-negative floats); warp per row, FP64 sum of squares.
-__global__ void max_row_norm_kernel(const float* __restrict__ X, int64_t n, int d, unsigned int* __restrict__ out) {
+// Largest row norm (out[0], rounded up) and largest |x_ij| (out[1]), as the
+// bits of non-negative floats (atomicMax on the bits orders them); warp per
+// row, FP64 sum of squares.
+__global__ void max_norms_kernel(const float* __restrict__ X, int64_t n, int d, unsigned int* __restrict__ out) {
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (row >= n) return;
     const float* x = X + row * d;
     double s = 0.0;
-    for (int i = lane; i < d; i += 32) s = fma((double)x[i], (double)x[i], s);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) atomicMax(out, __float_as_uint(__double2float_ru(sqrt(s))));
+    float amax = 0.f;
+    for (int i = lane; i < d; i += 32) {
+        s = fma((double)x[i], (double)x[i], s);
+        amax = fmaxf(amax, fabsf(x[i]));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    }
+    if (lane == 0) {
+        atomicMax(out, __float_as_uint(__double2float_ru(sqrt(s))));
+        atomicMax(out + 1, __float_as_uint(amax));
+    }
 }
 
 __global__ void inverse_ids_kernel(const int64_t* __restrict__ orig_id, int64_t n, int32_t* __restrict__ row_of) {
@@ -258,7 +269,7 @@ int dev_alloc(void** p, size_t bytes, const char* what) {
 void release(lider_index* ix) {
     if (!ix) return;
     void* bufs[] = {ix->X, ix->orig_id, ix->cl_off, ix->C, ix->half_norm, ix->A, ix->bproj,
-                    ix->keys, ix->pos, ix->root, ix->leaf, ix->X_hi, ix->X_lo, ix->row_of, ix->X_bf16, ix->C_hi, ix->C_lo};
+                    ix->keys, ix->pos, ix->root, ix->leaf, ix->X_hi, ix->X_lo, ix->row_of, ix->X_h16, ix->C_hi, ix->C_lo};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (ix->pool) cudaMemPoolDestroy(ix->pool);
@@ -284,12 +295,13 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
     if ((int64_t)beta * P->B > 56) return fail(LIDER_EINVAL, "lider_build: floor(64/m) * B must be <= 56");
     if (P->L > LIDER_MAX_L) return fail(LIDER_ELIMIT, "lider_build: L exceeds LIDER_MAX_L");
     if (P->rmi_leaves > (1 << 24)) return fail(LIDER_ELIMIT, "lider_build: rmi_leaves too large");
-    if (P->score_mode != LIDER_SCORE_TENSOR && P->score_mode != LIDER_SCORE_SIMT && P->score_mode != LIDER_SCORE_BF16)
+    if (P->score_mode != LIDER_SCORE_TENSOR && P->score_mode != LIDER_SCORE_SIMT && P->score_mode != LIDER_SCORE_BF16 &&
+        P->score_mode != LIDER_SCORE_F16)
         return fail(LIDER_EINVAL, "lider_build: unknown score_mode");
     if (P->score_mode != LIDER_SCORE_SIMT && P->L > 16)
         return fail(LIDER_ELIMIT, "lider_build: tensor-core scoring supports L <= 16 (use LIDER_SCORE_SIMT)");
-    if (P->score_mode == LIDER_SCORE_BF16 && d % 8 != 0)
-        return fail(LIDER_EINVAL, "lider_build: LIDER_SCORE_BF16 needs d % 8 == 0");
+    if ((P->score_mode == LIDER_SCORE_BF16 || P->score_mode == LIDER_SCORE_F16) && d % 8 != 0)
+        return fail(LIDER_EINVAL, "lider_build: 16-bit tensor-core scoring needs d % 8 == 0");
     if (P->rerank < 0 || P->rerank > 64) return fail(LIDER_EINVAL, "lider_build: rerank must be in [0, 64]");
 
     int dev = 0;
@@ -408,35 +420,41 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
         }
     }
 
-    // tensor-core scoring: TF32 split (or BF16 copy) of the corpus, rank
-    // tables, inverse ids, TMA maps
+    // tensor-core scoring: norms for the error guards, TF32 split (or 16-bit
+    // copy) of the corpus, inverse ids, TMA maps
     if (P->score_mode != LIDER_SCORE_SIMT) {
+        DevBuf mx;
+        ALLOC(mx.p, 2 * sizeof(unsigned int), "norms");
+        LIDER_CUDA_TRY(cudaMemsetAsync(mx.p, 0, 2 * sizeof(unsigned int), st));
+        max_norms_kernel<<<(unsigned)cdiv(n * 32, 256), 256, 0, st>>>(ix->X, n, d, mx.as<unsigned int>());
+        LIDER_LAUNCH_CHECK("max_norms_kernel");
+        unsigned int bits[2] = {0u, 0u};
+        LIDER_CUDA_TRY(cudaMemcpyAsync(bits, mx.p, sizeof(bits), cudaMemcpyDeviceToHost, st));
+        LIDER_CUDA_TRY(cudaStreamSynchronize(st));
+        float norms[2];
+        std::memcpy(norms, bits, sizeof(norms));
+        ix->max_xnorm = norms[0];
+        if (!std::isfinite(norms[0]))
+            return fail(LIDER_EINVAL, "lider_build: corpus holds a non-finite value or a row norm overflows FP32");
         if (P->score_mode == LIDER_SCORE_TENSOR) {
             ALLOC(ix->X_hi, (size_t)n * d * sizeof(float), "corpus TF32 head");
             ALLOC(ix->X_lo, (size_t)n * d * sizeof(float), "corpus TF32 tail");
             if ((rc = launch_split_tf32(ix->X, n * d, ix->X_hi, ix->X_lo, st))) return rc;
             if ((rc = make_tensor_map(&ix->map_xhi, ix->X_hi, n, d, 256))) return rc;
             if ((rc = make_tensor_map(&ix->map_xlo, ix->X_lo, n, d, 256))) return rc;
+        } else if (P->score_mode == LIDER_SCORE_BF16) {
+            ALLOC(ix->X_h16, (size_t)n * d * sizeof(uint16_t), "corpus BF16 copy");
+            if ((rc = launch_to_bf16(ix->X, n * d, ix->X_h16, st))) return rc;
+            if ((rc = make_tensor_map(&ix->map_xh16, ix->X_h16, n, d, 256, true))) return rc;
         } else {
-            ALLOC(ix->X_bf16, (size_t)n * d * sizeof(uint16_t), "corpus BF16 copy");
-            if ((rc = launch_to_bf16(ix->X, n * d, ix->X_bf16, st))) return rc;
-            if ((rc = make_tensor_map(&ix->map_xbf16, ix->X_bf16, n, d, 256, true))) return rc;
+            ix->x_scale = f16_scale_host(norms[1]);
+            ALLOC(ix->X_h16, (size_t)n * d * sizeof(uint16_t), "corpus FP16 copy");
+            if ((rc = launch_to_f16(ix->X, n * d, ix->x_scale, ix->X_h16, st))) return rc;
+            if ((rc = make_tensor_map(&ix->map_xh16, ix->X_h16, n, d, 256, true))) return rc;
         }
         ALLOC(ix->row_of, (size_t)n * sizeof(int32_t), "row of id");
         inverse_ids_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(ix->orig_id, n, ix->row_of);
         LIDER_LAUNCH_CHECK("inverse_ids_kernel");
-        DevBuf mx;
-        ALLOC(mx.p, sizeof(unsigned int), "row norm");
-        LIDER_CUDA_TRY(cudaMemsetAsync(mx.p, 0, sizeof(unsigned int), st));
-        max_row_norm_kernel<<<(unsigned)cdiv(n * 32, 256), 256, 0, st>>>(ix->X, n, d, mx.as<unsigned int>());
-        LIDER_LAUNCH_CHECK("max_row_norm_kernel");
-        unsigned int bits = 0;
-        LIDER_CUDA_TRY(cudaMemcpyAsync(&bits, mx.p, sizeof(bits), cudaMemcpyDeviceToHost, st));
-        LIDER_CUDA_TRY(cudaStreamSynchronize(st));
-        float xn;
-        std::memcpy(&xn, &bits, sizeof(xn));
-        ix->max_xnorm = xn;
-
     }
 
     // 5. RMI per (cluster, array)
@@ -466,7 +484,7 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
     g.W = P->W;
     g.X = ix->X; g.orig_id = ix->orig_id; g.cl_off = ix->cl_off; g.C = ix->C; g.half_norm = ix->half_norm;
     g.A = ix->A; g.bproj = ix->bproj; g.keys = ix->keys; g.pos = ix->pos; g.root = ix->root; g.leaf = ix->leaf;
-    g.X_hi = ix->X_hi; g.X_lo = ix->X_lo; g.row_of = ix->row_of; g.X_bf16 = ix->X_bf16;
+    g.X_hi = ix->X_hi; g.X_lo = ix->X_lo; g.row_of = ix->row_of; g.X_h16 = ix->X_h16;
     int64_t max_nc = 0;
     for (int j = 0; j < ncl; ++j) max_nc = std::max(max_nc, ix->h_cl_off[j + 1] - ix->h_cl_off[j]);
     g.max_row_tiles = (int32_t)cdiv(max_nc, 256);

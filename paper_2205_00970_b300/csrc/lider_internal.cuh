@@ -62,7 +62,7 @@ struct Geometry {         // everything a search kernel needs, passed by value
     const float* X_hi;      // n x d, TF32 head of X (tensor-core scoring)
     const float* X_lo;      // n x d, X - X_hi
     const int32_t* row_of;  // n, row of X holding corpus id i (inverse of orig_id)
-    const uint16_t* X_bf16; // n x d, BF16 copy of X (served mode)
+    const uint16_t* X_h16;  // n x d, 16-bit copy of X: BF16 (served form) or scaled FP16
 };
 
 }  // namespace lider
@@ -88,14 +88,15 @@ struct lider_index {
     float* X_hi = nullptr;
     float* X_lo = nullptr;
     int32_t* row_of = nullptr;
-    uint16_t* X_bf16 = nullptr;
+    uint16_t* X_h16 = nullptr;  // BF16 copy (served form) or FP16 copy of x_scale * X
     float* C_hi = nullptr;      // centroids, TF32 head / tail (tensor-core routing)
     float* C_lo = nullptr;
     float max_cnorm = 0.f;      // largest centroid norm (routing error guard)
     float max_xnorm = 0.f;      // largest corpus row norm (candidate error guard)
+    float x_scale = 1.f;        // FP16 mode: power of two applied to X before rounding
     CUtensorMap map_chi;        // TMA maps over C_hi / C_lo, boxes of 32 x 256
     CUtensorMap map_clo;
-    CUtensorMap map_xbf16;      // TMA map over X_bf16, boxes of 64 x 256
+    CUtensorMap map_xh16;       // TMA map over X_h16, boxes of 64 x 256
     CUtensorMap map_xhi;        // TMA maps over X_hi / X_lo, boxes of 32 x 256
     CUtensorMap map_xlo;
     cudaMemPool_t pool = nullptr;
@@ -210,6 +211,10 @@ int launch_scores(const float* X, int64_t n, int d, const float* C, const double
 int launch_split_tf32(const float* x, int64_t n, float* hi, float* lo, cudaStream_t s);
 int make_tensor_map(CUtensorMap* map, const void* base, int64_t rows, int d, int box_rows, bool bf16 = false);
 int launch_to_bf16(const float* x, int64_t n, uint16_t* out, cudaStream_t s);
+int launch_to_f16(const float* x, int64_t n, float scale, uint16_t* out, cudaStream_t s);
+// Power of two s with s * amax in [2^13, 2^14) (1 for amax == 0): scaled
+// values stay in FP16's normal range with room below its maximum.
+float f16_scale_host(float amax);
 int launch_pack(const double* t, int64_t n, int L, int m, int beta, int64_t row_offset,
                 int64_t key_stride_row, int64_t key_stride_arr, uint64_t* keys,
                 unsigned long long* n_boundary, unsigned long long* n_clamped, cudaStream_t s);

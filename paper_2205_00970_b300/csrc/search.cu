@@ -28,6 +28,7 @@
 #include <mutex>
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "lider_internal.cuh"
 #include "tc.cuh"
@@ -160,10 +161,49 @@ __device__ __forceinline__ double warp_exact_score(const float* __restrict__ q, 
     return __dadd_rn(v, -half_norm);
 }
 
+// Guard formula of a score mode (see candidate_guard).
+inline int guard_mode(int score_mode) {
+    return score_mode == LIDER_SCORE_TENSOR ? 1 : score_mode == LIDER_SCORE_F16 ? 2 : 0;
+}
+
+// Per-query scale and error bound of the approximate candidate scores.
+// qn: |q| as computed in FP32 (inflated here to bound the true norm);
+// amax: max |q_i|.  gmode 1 (3xTF32): guard = kTcGuard |q| |x|max.
+// gmode 2 (FP16): q and x are scaled by powers of two sq, sx (s = sq sx) and
+// rounded to FP16 (unit roundoff u = 2^-11, subnormal half-spacing
+// eta = 2^-25); the products are exact in FP32 and the tensor cores sum d of
+// them with an error below d 2^-23 of their absolute sum.  Then
+//   |approx - s q.x| <= s |q| |x| (2u + u^2 + d 2^-23 (1 + 2u))
+//                       + eta (1 + u) sqrt(d) (sq |q| + sx |x|) (1 + d 2^-23) + d eta^2,
+// with |x| <= |x|max.  gmode 0 (served BF16 form): no guard.
+__device__ void candidate_guard(int gmode, float qn, float amax, int d, float xmax, float sx, float* qscale,
+                                float* qguard) {
+    const double q = (double)qn * (1.0 + 1e-5);
+    double sq = 1.0, g = 0.0;
+    if (gmode == 1) {
+        g = (double)kTcGuard * q * (double)xmax;
+    } else if (gmode == 2) {
+        if (amax > 0.f && amax <= 3.0e38f) {
+            int e = 0;
+            frexpf(amax, &e);
+            e = max(-100, min(e, 127));
+            sq = ldexp(1.0, 14 - e);
+        }
+        const double u = 0x1p-11, eta = 0x1p-25, acc = (double)d * 0x1p-23;
+        const double s = sq * (double)sx;
+        g = s * q * (double)xmax * (2.0 * u + u * u + acc * (1.0 + 2.0 * u)) +
+            eta * (1.0 + u) * sqrt((double)d) * (sq * q + (double)sx * (double)xmax) * (1.0 + acc) +
+            (double)d * eta * eta;
+    }
+    *qscale = (float)sq;
+    *qguard = __double2float_ru(g * (1.0 + 0x1p-20));
+}
+
 __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __restrict__ Q,
                                   const float* __restrict__ C, const double* __restrict__ half_norm, int64_t nq,
                                   int ncl, int d, int c, float guard_scale, int32_t* __restrict__ route,
-                                  int32_t* __restrict__ trace_route, float* __restrict__ qnorm,
+                                  int32_t* __restrict__ trace_route, int gmode, float max_xnorm, float x_scale,
+                                  float* __restrict__ qscale, float* __restrict__ qguard,
                                   unsigned long long* fallbacks) {
     const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -234,7 +274,10 @@ __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __re
         }
     }
     const float guard = guard_scale * sqrtf(qn2);
-    if (lane == 0) qnorm[q] = sqrtf(qn2);
+    float amax = 0.f;
+    for (int i = lane; i < d; i += 32) amax = fmaxf(amax, fabsf(qv[i]));
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (lane == 0) candidate_guard(gmode, sqrtf(qn2), amax, d, max_xnorm, x_scale, qscale + q, qguard + q);
     if (nsl < ncl && (double)a_out + (double)guard >= e_c) {
         // a centroid outside the shortlist may beat the c-th: score them all exactly
         if (lane == 0) atomicAdd(fallbacks, 1ull);
@@ -791,6 +834,20 @@ __global__ void qgather_kernel(const float* __restrict__ Q, const int32_t* __res
     }
 }
 
+// FP16 path: the queries in pair order, scaled by their power of two and
+// rounded to FP16.
+__global__ void qgather_f16_kernel(const float* __restrict__ Q, const int32_t* __restrict__ pairs, int64_t np, int c,
+                                   int d, const float* __restrict__ qscale, uint16_t* __restrict__ qp) {
+    const int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (slot >= np) return;
+    const int64_t q = pairs[slot] / c;
+    const float s = qscale[q];
+    const float* src = Q + q * d;
+    uint16_t* dst = qp + slot * d;
+    for (int i = lane; i < d; i += 32) dst[i] = __half_as_ushort(__float2half_rn(src[i] * s));
+}
+
 // Served form: the queries in pair order, rounded to BF16.
 __global__ void qgather_bf16_kernel(const float* __restrict__ Q, const int32_t* __restrict__ pairs, int64_t np, int c,
                                     int d, uint16_t* __restrict__ qp) {
@@ -884,8 +941,17 @@ struct TcSched {
     }
 };
 
+// Keys of 16 columns at a time are staged per warp in shared memory (at most
+// 32 x 16) with their destination index in pbuf, then written 32 consecutive
+// staged keys per store instruction (runs of one row each, in row order).
+constexpr int kEpiStageKeys = 32 * 16;
+constexpr int kEpiStageBytes = 4 * kEpiStageKeys * (8 + 4);   // four epilogue warps
+constexpr uint32_t kNoSlot = 0xffffffffu;
+
 struct TcEpi {
     const TcArgs* a;
+    uint64_t* stage;            // this warp's kEpiStageKeys keys
+    uint32_t* gidx;             // and their pbuf indices (kNoSlot: list full)
     bool valid;
     int64_t pair;
     int p0, cursor;
@@ -913,19 +979,47 @@ struct TcEpi {
         cursor = total ? atomicAdd(&a->pcount[pair], total) : 0;
     }
 
+    // Called by all 32 lanes of the warp (lane = accumulator row).
     __device__ void operator()(int, int, int col0, const uint32_t (&v)[32]) {
-        if (!valid) return;
-        const uint32_t w = bits[col0 >> 5];
-        if (!w) return;
-        uint64_t* dst = a->pbuf + pair * a->T_cap;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
+        for (int h = 0; h < 2; ++h) half(col0 + 16 * h, v, h);
+    }
+
+    __device__ __forceinline__ void half(int c0, const uint32_t (&v)[32], int h) {
+        const int lane = threadIdx.x & 31;
+        const uint32_t w = valid ? (bits[c0 >> 5] >> (16 * h)) & 0xffffu : 0u;
+        const int n = __popc(w);
+        int incl = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total == 0) return;                              // the same in every lane
+        // stage this lane's run with its destinations: pbuf[pair * T_cap + cursor + i]
+        const uint32_t gbase = valid ? (uint32_t)(pair * a->T_cap + cursor) : 0u;
+        const int room = valid ? a->T_cap - cursor : 0;
+        int r = incl - n, i_run = 0;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
             if ((w >> i) & 1u) {
-                if (cursor < a->T_cap) dst[cursor] = score_key(__uint_as_float(v[i]), (uint32_t)(p0 + col0 + i));
-                else atomicAdd(a->bounds, 1ull);
-                ++cursor;
+                stage[r] = score_key(__uint_as_float(v[16 * h + i]), (uint32_t)(p0 + c0 + i));
+                gidx[r] = i_run < room ? gbase + (uint32_t)i_run : kNoSlot;
+                ++r;
+                ++i_run;
             }
         }
+        cursor += n;
+        __syncwarp();
+#pragma unroll 4
+        for (int t = lane; t < total; t += 32) {
+            const uint32_t gi = gidx[t];
+            const uint64_t kv = stage[t];
+            if (gi != kNoSlot) a->pbuf[gi] = kv;
+            else atomicAdd(a->bounds, 1ull);
+        }
+        __syncwarp();
     }
 
     __device__ void done(int, int) {}
@@ -941,6 +1035,12 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     TcSched sched{&args};
     TcEpi epi;
     epi.a = &args;
+    // key staging after the engine's shared memory, one slice per epilogue warp
+    {
+        unsigned char* mine = smem + tc::kSmemBytes + (size_t)((threadIdx.x >> 5) & 3) * kEpiStageKeys * 12;
+        epi.stage = reinterpret_cast<uint64_t*>(mine);
+        epi.gidx = reinterpret_cast<uint32_t*>(mine + kEpiStageKeys * 8);
+    }
     tc::gemm_tiles<Kind>(&mAhi, &mAlo, &mBhi, &mBlo, kchunks, sched, epi, err, smem, ctl);
 }
 
@@ -1018,7 +1118,7 @@ __global__ void __launch_bounds__(256) select_query_kernel(const uint64_t* __res
                                                            const int32_t* __restrict__ route,
                                                            const int64_t* __restrict__ cl_off,
                                                            const int64_t* __restrict__ orig_id, int c, int ks,
-                                                           const float* __restrict__ qnorm, float guard_scale, int so,
+                                                           const float* __restrict__ qguard, int guarded, int so,
                                                            int64_t* __restrict__ out_ids, float* __restrict__ out_scores,
                                                            int32_t* __restrict__ trace_ucount,
                                                            unsigned long long* counters) {
@@ -1132,11 +1232,11 @@ __global__ void __launch_bounds__(256) select_query_kernel(const uint64_t* __res
         // error bound of the chosen bucket's lower edge (and so of the ks-th
         // key) joins the list, so the exact re-score sees the exact top ks
         s_thr = INFINITY;
-        if (guard_scale > 0.f && levels > 0) {
+        if (guarded && levels > 0) {
             const int l = levels - 1;
             const float edge = lv_scale[l] > 0.f ? __fadd_rn(lv_hi[l], -(float)(lv_sel[l] + 1) / lv_scale[l])
                                                  : lv_lo[l];
-            s_thr = edge - 2.f * guard_scale * qnorm[q];
+            s_thr = edge - 2.f * qguard[q];
         }
     }
     __syncthreads();
@@ -1190,9 +1290,9 @@ __global__ void __launch_bounds__(256) select_query_kernel(const uint64_t* __res
     // guard mode: keep every key within twice the error bound of the ks-th
     // best approximate score (the exact top ks is among them); else the ks best
     int keep = min(need, n);
-    if (guard_scale > 0.f && keep > 0) {
+    if (guarded && keep > 0) {
         const float vk = float_from_order(~(uint32_t)(keys[keep - 1] >> 32));
-        const float t = vk - 2.f * guard_scale * qnorm[q];
+        const float t = vk - 2.f * qguard[q];
         if (tid == 0) s_band = keep;
         __syncthreads();
         for (int r = keep + tid; r < n; r += blockDim.x)
@@ -1280,7 +1380,8 @@ struct Workspace {
     uint64_t* pbuf;
     int64_t* sl_ids;            // tensor paths: per-query list before the re-score (nq x so)
     float* sl_scores;
-    float* qnorm;               // tensor paths: |q| (FP32), for the error guards
+    float* qscale;              // FP16 path: per-query power-of-two scale
+    float* qguard;              // tensor paths: error bound of a query's approximate scores
     int32_t* pcount;            // tensor path: candidates per pair (cleared)
     int32_t* unit_off;
     int64_t* bm_off;            // tensor paths: per-cluster bitmap offsets (words)
@@ -1320,7 +1421,8 @@ Shape search_shape(const lider_index* ix, int k, int64_t nq = 0, int c = 0) {
     } else {
         sh.ks = k;
         sh.kp = k;
-        sh.so = std::min(kSelCap, 2 * k + 32);
+        // room for the guard band: 3xTF32's is a few keys, FP16's ~1e-3 |q| |x|
+        sh.so = std::min(kSelCap, sh.mode == LIDER_SCORE_F16 ? 4 * k + 64 : 2 * k + 32);
     }
     return sh;
 }
@@ -1348,7 +1450,7 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, const
     // tiles <= sum_j ceil(cnt_j/128) * ceil(n_c/256) <= (np/128 + ncl) * max_row_tiles
     w.units = tensor ? (int4*)take((size_t)((np + tc::kBM - 1) / tc::kBM + g.ncl) * (size_t)g.max_row_tiles * 16)
                      : nullptr;
-    const size_t qelem = sh.mode == LIDER_SCORE_BF16 ? 2 : 4;
+    const size_t qelem = (sh.mode == LIDER_SCORE_BF16 || sh.mode == LIDER_SCORE_F16) ? 2 : 4;
     w.qp_hi = tensor ? (float*)take((size_t)np * g.d * qelem) : nullptr;
     w.qp_lo = sh.mode == LIDER_SCORE_TENSOR ? (float*)take((size_t)np * g.d * 4) : nullptr;
     w.qs_hi = tensor ? (float*)take((size_t)nq * g.d * 4) : nullptr;
@@ -1368,7 +1470,8 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, const
     w.pbuf = (uint64_t*)take((size_t)np * g.L * sh.R * 8);
     w.sl_ids = tensor ? (int64_t*)take((size_t)nq * sh.so * 8) : nullptr;
     w.sl_scores = tensor ? (float*)take((size_t)nq * sh.so * 4) : nullptr;
-    w.qnorm = tensor ? (float*)take((size_t)nq * 4) : nullptr;
+    w.qscale = tensor ? (float*)take((size_t)nq * 4) : nullptr;
+    w.qguard = tensor ? (float*)take((size_t)nq * 4) : nullptr;
     w.total = o;
     return w;
 }
@@ -1385,6 +1488,9 @@ int check_search_args(const lider_index* ix, const float* Q, int64_t nq, int k, 
     const int64_t R = (int64_t)ix->params.r0 * k;
     if (R * ix->g.L > LIDER_MAX_LR) return fail(LIDER_ELIMIT, "lider_search: L * r0 * k exceeds LIDER_MAX_LR");
     if (nq * c > (int64_t)INT32_MAX) return fail(LIDER_ELIMIT, "lider_search: nq * c exceeds 2^31-1");
+    if (ix->params.score_mode != LIDER_SCORE_SIMT && nq * c * R * ix->g.L >= (int64_t)UINT32_MAX)
+        return fail(LIDER_ELIMIT, "lider_search: nq * c * L * r0 * k reaches 2^32 (candidate list slots); search "
+                                  "fewer queries per call");
     if (ix->params.score_mode == LIDER_SCORE_BF16 && (int64_t)ix->params.rerank * k > 4096)
         return fail(LIDER_ELIMIT, "lider_search: rerank * k exceeds 4096");
     if (ix->params.score_mode != LIDER_SCORE_SIMT && c <= ix->g.ncl &&
@@ -1445,7 +1551,9 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         // guard: the tensor-core error of one score stays below kTcGuard |q| |mu|
         topc_exact_kernel<<<(unsigned)cdiv(nq * 32, 256), 256, 0, st>>>(
             S, Q, g.C, g.half_norm, nq, g.ncl, g.d, c, kTcGuard * ix->max_cnorm, w.route,
-            tr ? tr->route : nullptr, w.qnorm, &w.counters[CNT_ROUTE_FALLBACK]);
+            tr ? tr->route : nullptr,
+            guard_mode(ix->params.score_mode), ix->max_xnorm, ix->x_scale, w.qscale, w.qguard,
+            &w.counters[CNT_ROUTE_FALLBACK]);
         LIDER_LAUNCH_CHECK("topc_exact_kernel");
     } else {
     if ((rc = launch_scores(Q, nq, g.d, g.C, g.half_norm, g.ncl, w.rscore, st))) return rc;
@@ -1473,12 +1581,18 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
     const Shape sh = search_shape(ix, k);
     if ((rc = mark(LIDER_PHASE_GATHER))) return rc;
     if (sh.mode != LIDER_SCORE_SIMT) {
-        const bool bf16 = sh.mode == LIDER_SCORE_BF16;
+        const bool h16 = sh.mode == LIDER_SCORE_BF16 || sh.mode == LIDER_SCORE_F16;
         CUtensorMap mqh, mql;
-        if (bf16) {
+        if (h16) {
             uint16_t* qp = reinterpret_cast<uint16_t*>(w.qp_hi);
-            qgather_bf16_kernel<<<(unsigned)cdiv(np * 32, 256), 256, 0, st>>>(Q, w.pairs, np, c, g.d, qp);
-            LIDER_LAUNCH_CHECK("qgather_bf16_kernel");
+            if (sh.mode == LIDER_SCORE_BF16) {
+                qgather_bf16_kernel<<<(unsigned)cdiv(np * 32, 256), 256, 0, st>>>(Q, w.pairs, np, c, g.d, qp);
+                LIDER_LAUNCH_CHECK("qgather_bf16_kernel");
+            } else {
+                qgather_f16_kernel<<<(unsigned)cdiv(np * 32, 256), 256, 0, st>>>(Q, w.pairs, np, c, g.d, w.qscale,
+                                                                                 qp);
+                LIDER_LAUNCH_CHECK("qgather_f16_kernel");
+            }
             if ((rc = make_tensor_map(&mqh, qp, np, g.d, tc::kBM, true))) return rc;
             mql = mqh;
         } else {
@@ -1507,13 +1621,19 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         ta.pbuf = w.pbuf;
         ta.pcount = w.pcount;
         ta.bounds = &w.counters[CNT_BOUNDS];
-        const int tc_smem = tc::kSmemBytes;
+        const int tc_smem = tc::kSmemBytes + kEpiStageBytes;
         // A = queries of the tile (128 rows, box 128), B = cluster rows (256, box 256)
-        if (bf16) {
+        if (sh.mode == LIDER_SCORE_BF16) {
             LIDER_CUDA_TRY(cudaFuncSetAttribute(tc_score_kernel<tc::KindBf16>,
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem));
             tc_score_kernel<tc::KindBf16><<<ix->num_sms, tc::kThreads, tc_smem, st>>>(
-                mqh, mql, ix->map_xbf16, ix->map_xbf16, (g.d + tc::KindBf16::kBK - 1) / tc::KindBf16::kBK, ta,
+                mqh, mql, ix->map_xh16, ix->map_xh16, (g.d + tc::KindBf16::kBK - 1) / tc::KindBf16::kBK, ta,
+                w.tc_err);
+        } else if (sh.mode == LIDER_SCORE_F16) {
+            LIDER_CUDA_TRY(cudaFuncSetAttribute(tc_score_kernel<tc::KindF16>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem));
+            tc_score_kernel<tc::KindF16><<<ix->num_sms, tc::kThreads, tc_smem, st>>>(
+                mqh, mql, ix->map_xh16, ix->map_xh16, (g.d + tc::KindF16::kBK - 1) / tc::KindF16::kBK, ta,
                 w.tc_err);
         } else {
             LIDER_CUDA_TRY(cudaFuncSetAttribute(tc_score_kernel<tc::KindTf32x3>,
@@ -1524,11 +1644,11 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         }
         LIDER_LAUNCH_CHECK("tc_score_kernel");
         if ((rc = mark(LIDER_PHASE_SELECT))) return rc;
-        // plain tensor path: a guard band makes the re-scored top k exact; the
-        // served BF16 form keeps its approximate shortlist
-        const float cand_guard = sh.mode == LIDER_SCORE_TENSOR ? kTcGuard * ix->max_xnorm : 0.f;
+        // 3xTF32 and FP16 paths: a guard band makes the re-scored top k exact;
+        // the served BF16 form keeps its approximate shortlist
+        const int guarded = sh.mode != LIDER_SCORE_BF16;
         select_query_kernel<<<(unsigned)nq, 256, 0, st>>>(w.pbuf, g.L * R, w.pcount, w.route, g.cl_off, g.orig_id, c,
-                                                          sh.ks, w.qnorm, cand_guard, sh.so, w.sl_ids, w.sl_scores,
+                                                          sh.ks, w.qguard, guarded, sh.so, w.sl_ids, w.sl_scores,
                                                           tr ? tr->ucount : nullptr, w.counters);
         LIDER_LAUNCH_CHECK("select_query_kernel");
     } else {

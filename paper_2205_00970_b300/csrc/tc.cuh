@@ -55,6 +55,14 @@ struct KindBf16 {
     static constexpr uint32_t kIdesc = idesc(1);
 };
 
+struct KindF16 {
+    static constexpr int kStages = 4;
+    static constexpr int kOps = 1;
+    static constexpr int kElemBytes = 2;
+    static constexpr int kBK = kRowBytes / kElemBytes;   // 64 elements of K per stage
+    static constexpr uint32_t kIdesc = idesc(0);
+};
+
 enum {
     TC_OK = 0,
     TC_TIMEOUT_EMPTY = 1,
@@ -207,11 +215,13 @@ struct Ctl {
 // One unit = one 128 x 256 tile: A rows [a_row, a_row+128), B rows
 // [b_row, b_row+256), all of K.  Sched provides: int count() and
 // void coords(int u, int& a_row, int& b_row).  Epi provides, called by every
-// epilogue thread (row = its accumulator row): void begin(int u, int row)
-// before the first column group (it may use epi_sync), void operator()(int u,
-// int row, int col0, const uint32_t (&v)[32]) for columns col0..col0+31, and
-// void done(int u, int row) after the last group.  The epilogue warps leave
-// their loop only together, so their named barriers cannot be left waiting.
+// epilogue thread (row = its accumulator row, all 32 lanes of a warp
+// together): void begin(int u, int row) before the tile's accumulator is
+// waited for (it must not read TMEM; its loads overlap the tile's MMAs),
+// void operator()(int u, int row, int col0, const uint32_t (&v)[32]) for
+// columns col0..col0+31, and void done(int u, int row) after the last group.
+// The epilogue warps leave their loop only together, so their named barriers
+// cannot be left waiting.
 // mA0/mB0: the operands (KindTf32x3: their TF32 heads); mA1/mB1: the tails
 // (KindTf32x3 only; ignored otherwise).  kchunks = ceil(d / Kind::kBK).
 template <class Kind, class Sched, class Epi>
@@ -333,6 +343,7 @@ __device__ void gemm_tiles(const CUtensorMap* mAhi, const CUtensorMap* mAlo, con
         for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++ui) {
             const int ab = ui & 1;
             const uint32_t aph = (uint32_t)(ui >> 1) & 1u;
+            epi.begin(u, row);
             const bool ok = mbar_wait(&ctl.tfull[ab], aph, abort_flag);
             if (!ok && lane == 0) {
                 fail(TC_TIMEOUT_TFULL);
@@ -341,7 +352,6 @@ __device__ void gemm_tiles(const CUtensorMap* mAhi, const CUtensorMap* mAlo, con
             epi_sync();                                  // every epilogue warp arrives
             if (*(volatile int*)&ctl.epi_bad) break;     // same decision in all four
             tc_fence_after();
-            epi.begin(u, row);
             const uint32_t base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * kBN);
 #pragma unroll
             for (int cb = 0; cb < kBN / 32; ++cb) {

@@ -1,6 +1,10 @@
 // Tensor-core candidate scoring support: the TF32 hi/lo split, TMA tensor
 // maps, and a one-tile self-test of the tcgen05 engine (tc.cuh).
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
 
 #include <mutex>
 
@@ -21,6 +25,14 @@ __global__ void split_tf32_kernel(const float* __restrict__ x, int64_t n, float*
     const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
     hi[i] = h;
     lo[i] = __fsub_rn(v, h);
+}
+
+// Round scale * x to FP16 (nearest, ties to even); scale is a power of two,
+// so the scaling itself is exact.
+__global__ void to_f16_kernel(const float* __restrict__ x, int64_t n, float scale, uint16_t* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = __half_as_ushort(__float2half_rn(x[i] * scale));
 }
 
 // Round to BF16 (nearest, ties to even).
@@ -91,6 +103,21 @@ int launch_to_bf16(const float* x, int64_t n, uint16_t* out, cudaStream_t st) {
     return LIDER_OK;
 }
 
+int launch_to_f16(const float* x, int64_t n, float scale, uint16_t* out, cudaStream_t st) {
+    if (n <= 0) return LIDER_OK;
+    to_f16_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(x, n, scale, out);
+    LIDER_LAUNCH_CHECK("to_f16_kernel");
+    return LIDER_OK;
+}
+
+float f16_scale_host(float amax) {
+    if (!(amax > 0.f) || !std::isfinite(amax)) return 1.f;
+    int e = 0;
+    std::frexp(amax, &e);                 // amax in [2^(e-1), 2^e)
+    e = std::max(-100, std::min(e, 127));
+    return std::ldexp(1.f, 14 - e);       // scaled max in [2^13, 2^14)
+}
+
 int launch_split_tf32(const float* x, int64_t n, float* hi, float* lo, cudaStream_t st) {
     if (n <= 0) return LIDER_OK;
     split_tf32_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(x, n, hi, lo);
@@ -126,7 +153,7 @@ extern "C" int lider_debug_tc_tile(const float* A, int32_t m, const float* B, in
     using namespace lider;
     try {
         if (!A || !B || !out) return fail(LIDER_EINVAL, "lider_debug_tc_tile: NULL pointer");
-        if (kind != 0 && kind != 1) return fail(LIDER_EINVAL, "lider_debug_tc_tile: kind must be 0 or 1");
+        if (kind < 0 || kind > 2) return fail(LIDER_EINVAL, "lider_debug_tc_tile: kind must be 0, 1 or 2");
         if (m < 1 || m > tc::kBM || n < 1 || n > tc::kBN || d < (kind ? 8 : 4) || d % (kind ? 8 : 4) != 0)
             return fail(LIDER_EINVAL, "lider_debug_tc_tile: need 1<=m<=128, 1<=n<=256, d % 4 (BF16: 8) == 0");
         cudaStream_t st = (cudaStream_t)stream;
@@ -148,8 +175,13 @@ extern "C" int lider_debug_tc_tile(const float* A, int32_t m, const float* B, in
             } else {
                 uint16_t* a16 = reinterpret_cast<uint16_t*>(ahi);
                 uint16_t* b16 = reinterpret_cast<uint16_t*>(bhi);
-                if ((rc = launch_to_bf16(A, (int64_t)na, a16, st))) break;
-                if ((rc = launch_to_bf16(B, (int64_t)nb, b16, st))) break;
+                if (kind == 1) {
+                    if ((rc = launch_to_bf16(A, (int64_t)na, a16, st))) break;
+                    if ((rc = launch_to_bf16(B, (int64_t)nb, b16, st))) break;
+                } else {
+                    if ((rc = launch_to_f16(A, (int64_t)na, 1.f, a16, st))) break;
+                    if ((rc = launch_to_f16(B, (int64_t)nb, 1.f, b16, st))) break;
+                }
                 if ((rc = make_tensor_map(&mah, a16, m, d, tc::kBM, true))) break;
                 if ((rc = make_tensor_map(&mbh, b16, n, d, tc::kBN, true))) break;
                 mal = mah;
@@ -157,8 +189,9 @@ extern "C" int lider_debug_tc_tile(const float* A, int32_t m, const float* B, in
             }
             cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
             if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemsetAsync"); break; }
-            const void* kern = kind == 0 ? (const void*)tc_tile_test_kernel<tc::KindTf32x3>
-                                         : (const void*)tc_tile_test_kernel<tc::KindBf16>;
+            const void* kern = kind == 0   ? (const void*)tc_tile_test_kernel<tc::KindTf32x3>
+                               : kind == 1 ? (const void*)tc_tile_test_kernel<tc::KindBf16>
+                                           : (const void*)tc_tile_test_kernel<tc::KindF16>;
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes);
             if (e != cudaSuccess) { rc = cuda_fail(e, "cudaFuncSetAttribute"); break; }
             const int kbk = kind == 0 ? tc::KindTf32x3::kBK : tc::KindBf16::kBK;

@@ -76,15 +76,25 @@ def test_mid_counters(mid):
     assert st["select_overflow"] == 0
 
 
-def test_mid_tensor_equals_simt_exactly(mid):
-    """At full size, all 10,000 queries: the tensor-core path's results equal
-    the SIMT path's (the exact FP32 top-k of each candidate union) bit for bit."""
+def test_mid_tensor_modes_equal_simt_exactly(mid):
+    """At full size, all 10,000 queries: the 3xTF32 and FP16 tensor-core
+    paths' results equal the SIMT path's (the exact FP32 top-k of each
+    candidate union) bit for bit."""
     import torch
     cfg, X, Q, C, A, b = (mid[n] for n in ("cfg", "X", "Q", "C", "A", "b"))
+    Qd = torch.from_numpy(Q).cuda()
     g = F.gpu_index(dict(cfg, score_mode=1), X, C, A, b)
-    ids, sc = g.search(torch.from_numpy(Q).cuda(), cfg["k"], cfg["c"])
+    ids, sc = g.search(Qd, cfg["k"], cfg["c"])
     g.free()
     ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
     diff = np.nonzero(np.any(ids != mid["ids"], axis=1))[0]
     assert diff.size == 0, (diff[:10], diff.size)
     assert np.array_equal(sc.view(np.uint32), mid["sc"].view(np.uint32))
+    g = F.gpu_index(dict(cfg, score_mode=3), X, C, A, b)
+    fi, fs, st = g.search(Qd, cfg["k"], cfg["c"], stats=True)
+    g.free()
+    assert st["select_overflow"] == 0 and st["route_fallback"] == 0
+    fi, fs = fi.cpu().numpy(), fs.cpu().numpy()
+    diff = np.nonzero(np.any(fi != ids, axis=1))[0]
+    assert diff.size == 0, (diff[:10], diff.size)
+    assert np.array_equal(fs.view(np.uint32), sc.view(np.uint32))

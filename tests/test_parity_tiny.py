@@ -9,8 +9,8 @@ from tests import lider_fixtures as F
 pytestmark = pytest.mark.gpu
 
 
-MODES = [0, 1]          # tensor-core scoring, SIMT scoring
-MODE_IDS = ["tensor", "simt"]
+MODES = [0, 1, 3]       # 3xTF32 tensor-core scoring, SIMT scoring, FP16 tensor-core scoring
+MODE_IDS = ["tensor", "simt", "f16"]
 
 
 @pytest.fixture(scope="module", params=MODES, ids=MODE_IDS)
@@ -210,20 +210,21 @@ def test_served_bf16_form():
 
 
 @pytest.mark.parametrize("k", [1, 10, 37])
-def test_tensor_path_equals_simt_path_exactly(k):
-    """The tensor-core path (3xTF32 scores, a guard band around the k-th
-    approximate score, exact FP32 re-score) returns exactly the SIMT path's
-    results: the exact FP32 top-k of every query's candidate union, same ids,
-    same scores bit for bit, ties by lower id."""
+@pytest.mark.parametrize("mode", [0, 3], ids=["tensor", "f16"])
+def test_tensor_path_equals_simt_path_exactly(mode, k):
+    """The tensor-core paths (3xTF32 or FP16 scores, a guard band around the
+    k-th approximate score, exact FP32 re-score) return exactly the SIMT
+    path's results: the exact FP32 top-k of every query's candidate union,
+    same ids, same scores bit for bit, ties by lower id."""
     import torch
     cfg, X, Q, C, A, b = F.workload("tiny")
     Qd = torch.from_numpy(Q).cuda()
     out = {}
-    for mode in (0, 1):
-        g = F.gpu_index(dict(cfg, score_mode=mode), X, C, A, b)
+    for m in (mode, 1):
+        g = F.gpu_index(dict(cfg, score_mode=m), X, C, A, b)
         ids, sc, st = g.search(Qd, k, cfg["c"], stats=True)
-        out[mode] = (ids.cpu().numpy(), sc.cpu().numpy(), st)
+        out[m] = (ids.cpu().numpy(), sc.cpu().numpy(), st)
         g.free()
-    assert out[0][2]["select_overflow"] == 0
-    assert np.array_equal(out[0][0], out[1][0])
-    assert np.array_equal(out[0][1].view(np.uint32), out[1][1].view(np.uint32))
+    assert out[mode][2]["select_overflow"] == 0
+    assert np.array_equal(out[mode][0], out[1][0])
+    assert np.array_equal(out[mode][1].view(np.uint32), out[1][1].view(np.uint32))

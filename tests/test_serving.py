@@ -43,7 +43,7 @@ def _poisson(Q, srv, rate, seconds, ks, max_req, seed):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_served_mix_equals_alone(mode):
     """Each request's ids and scores, served in a Poisson mix of requests of
     several sizes and two k on overlapping streams, are bit-identical to the

@@ -21,6 +21,26 @@ def test_tc_tile_matches_fp64(m, n, d):
     assert np.max(err) < 2e-6, (float(np.max(err)), float(np.mean(err)))
 
 
+@pytest.mark.parametrize("m,n,d", [(128, 256, 768), (100, 200, 776), (5, 7, 64), (128, 256, 8), (128, 256, 4096)])
+def test_tc_tile_f16_accumulation_error(m, n, d):
+    """FP16 kind: the products of the FP16-rounded inputs are exact in FP32;
+    the tensor cores' FP32 accumulation stays far inside the d * 2^-23 (of the
+    absolute sum) that the FP16 guard band allows for it."""
+    import torch
+    from paper_2205_00970_b300 import lider
+    rng = np.random.default_rng(m * 13 + n + d)
+    A = rng.standard_normal((m, d)).astype(np.float32)
+    B = rng.standard_normal((n, d)).astype(np.float32)
+    At, Bt = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    out = lider.tc_tile(At, Bt, kind=2).cpu().numpy().astype(np.float64)
+    A16 = At.half().float().cpu().numpy().astype(np.float64)
+    B16 = Bt.half().float().cpu().numpy().astype(np.float64)
+    ref = A16 @ B16.T
+    scale = np.abs(A16) @ np.abs(B16).T
+    err = np.abs(out - ref) / scale
+    assert np.max(err) < d * 2.0 ** -23 / 8, (float(np.max(err)), float(np.mean(err)))
+
+
 @pytest.mark.parametrize("m,n,d", [(128, 256, 768), (100, 200, 776), (5, 7, 64), (128, 256, 8)])
 def test_tc_tile_bf16_matches_fp64_of_rounded_inputs(m, n, d):
     """BF16 kind: the products of the BF16-rounded inputs, accumulated in FP32."""
