@@ -175,13 +175,16 @@ inline int guard_mode(int score_mode) {
 // them with an error below d 2^-23 of their absolute sum.  Then
 //   |approx - s q.x| <= s |q| |x| (2u + u^2 + d 2^-23 (1 + 2u))
 //                       + eta (1 + u) sqrt(d) (sq |q| + sx |x|) (1 + d 2^-23) + d eta^2,
-// with |x| <= |x|max.  gmode 0 (served BF16 form): no guard.
+// with |x| <= |x|max.  gmode 0 (served BF16 form): no guard.  qbound bounds
+// |approximate score| (it sets the select histogram's range).
 __device__ void candidate_guard(int gmode, float qn, float amax, int d, float xmax, float sx, float* qscale,
-                                float* qguard) {
+                                float* qguard, float* qbound) {
     const double q = (double)qn * (1.0 + 1e-5);
     double sq = 1.0, g = 0.0;
     if (gmode == 1) {
         g = (double)kTcGuard * q * (double)xmax;
+    } else if (gmode == 0) {
+        g = 0x1p-6 * q * (double)xmax;        // BF16: only bounds the scores below
     } else if (gmode == 2) {
         if (amax > 0.f && amax <= 3.0e38f) {
             int e = 0;
@@ -196,14 +199,17 @@ __device__ void candidate_guard(int gmode, float qn, float amax, int d, float xm
             (double)d * eta * eta;
     }
     *qscale = (float)sq;
-    *qguard = __double2float_ru(g * (1.0 + 0x1p-20));
+    *qguard = gmode == 0 ? 0.f : __double2float_ru(g * (1.0 + 0x1p-20));
+    // |approximate score| <= s |q| |x|max + its error (s = 1 unless FP16)
+    const double s = gmode == 2 ? sq * (double)sx : 1.0;
+    *qbound = __double2float_ru((s * q * (double)xmax + g) * (1.0 + 0x1p-20));
 }
 
 __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __restrict__ Q,
                                   const float* __restrict__ C, const double* __restrict__ half_norm, int64_t nq,
                                   int ncl, int d, int c, float guard_scale, int32_t* __restrict__ route,
                                   int32_t* __restrict__ trace_route, int gmode, float max_xnorm, float x_scale,
-                                  float* __restrict__ qscale, float* __restrict__ qguard,
+                                  float* __restrict__ qscale, float* __restrict__ qguard, float* __restrict__ qbound,
                                   unsigned long long* fallbacks) {
     const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -277,7 +283,8 @@ __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __re
     float amax = 0.f;
     for (int i = lane; i < d; i += 32) amax = fmaxf(amax, fabsf(qv[i]));
     for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    if (lane == 0) candidate_guard(gmode, sqrtf(qn2), amax, d, max_xnorm, x_scale, qscale + q, qguard + q);
+    if (lane == 0)
+        candidate_guard(gmode, sqrtf(qn2), amax, d, max_xnorm, x_scale, qscale + q, qguard + q, qbound + q);
     if (nsl < ncl && (double)a_out + (double)guard >= e_c) {
         // a centroid outside the shortlist may beat the c-th: score them all exactly
         if (lane == 0) atomicAdd(fallbacks, 1ull);
@@ -1121,6 +1128,8 @@ __global__ void __launch_bounds__(256) select_query_kernel(const uint64_t* __res
                                                            const float* __restrict__ qguard, int guarded, int so,
                                                            int64_t* __restrict__ out_ids, float* __restrict__ out_scores,
                                                            int32_t* __restrict__ trace_ucount,
+                                                           const int32_t* __restrict__ redo,
+                                                           const int32_t* __restrict__ redo_count,
                                                            unsigned long long* counters) {
     __shared__ uint64_t keys[kSelCap];
     __shared__ uint32_t bins[kBins];
@@ -1130,7 +1139,10 @@ __global__ void __launch_bounds__(256) select_query_kernel(const uint64_t* __res
     __shared__ float s_thr;
     __shared__ int s_band;
     __shared__ uint32_t s_lo_ord, s_hi_ord;
-    const int64_t q = blockIdx.x;
+    // redo: the queries select_hist_kernel left to this kernel (block b takes
+    // redo[b]); otherwise block b takes query b
+    if (redo && (int)blockIdx.x >= *redo_count) return;
+    const int64_t q = redo ? redo[blockIdx.x] : blockIdx.x;
     const int tid = threadIdx.x;
     if (tid == 0) { s_lo_ord = 0xffffffffu; s_hi_ord = 0u; s_total = 0; s_n = 0; }
     __syncthreads();
@@ -1157,7 +1169,7 @@ __global__ void __launch_bounds__(256) select_query_kernel(const uint64_t* __res
     atomicMax(&s_hi_ord, kmax);
     if (tid == 0) {
         s_total = tot;
-        atomicAdd(&counters[CNT_CANDIDATES], (unsigned long long)tot);
+        if (!redo) atomicAdd(&counters[CNT_CANDIDATES], (unsigned long long)tot);
     }
     __syncthreads();
     const int total = s_total;
@@ -1314,6 +1326,162 @@ __global__ void __launch_bounds__(256) select_query_kernel(const uint64_t* __res
     }
 }
 
+// Per-query selection in two streaming passes (tensor paths).  The bins are
+// fixed by a bound B >= |approximate score| of the query (no range pass):
+// bin = floor((B - score) * kHistBins / 2B), bin 0 holding the best scores.
+// Pass 1 counts the keys per bin; the bin where the count reaches ks fixes a
+// threshold (lowered by the guard band and one bin for rounding); pass 2
+// collects the keys of the bins up to it as (score, corpus id), which are
+// sorted in shared memory.  A query whose collection would exceed kHistCand
+// is appended to `redo` and left to select_query_kernel.
+constexpr int kHistBins = 2048;
+constexpr int kHistCand = 2048;
+
+__global__ void __launch_bounds__(256) select_hist_kernel(
+        const uint64_t* __restrict__ pbuf, int T_cap, const int32_t* __restrict__ pcount,
+        const int32_t* __restrict__ route, const int64_t* __restrict__ cl_off, const int64_t* __restrict__ orig_id,
+        int c, int ks, const float* __restrict__ qguard, const float* __restrict__ qbound, int guarded, int so,
+        int64_t* __restrict__ out_ids, float* __restrict__ out_scores, int32_t* __restrict__ trace_ucount,
+        int32_t* __restrict__ redo, int32_t* __restrict__ redo_count, unsigned long long* counters) {
+    __shared__ uint32_t hist[kHistBins];
+    __shared__ uint64_t cand[kHistCand];
+    __shared__ int s_U[LIDER_MAX_C];
+    __shared__ int s_total, s_cnt, s_bt, s_band;
+    const int64_t q = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int b = tid; b < kHistBins; b += blockDim.x) hist[b] = 0u;
+    if (tid == 0) {
+        int o = 0;
+        for (int p = 0; p < c; ++p) {
+            const int64_t pair = q * c + p;
+            int U = pcount[pair];
+            if (U < 0 || U > T_cap) {
+                atomicAdd(&counters[CNT_BOUNDS], 1ull);
+                U = 0;
+            }
+            s_U[p] = U;
+            o += U;
+            if (trace_ucount) trace_ucount[pair] = U;
+        }
+        s_total = o;
+        s_cnt = 0;
+        atomicAdd(&counters[CNT_CANDIDATES], (unsigned long long)o);
+    }
+    __syncthreads();
+    const int total = s_total;
+    const int need = min(ks, total);
+    const float B = qbound[q];
+    const float scale = B > 0.f ? (float)kHistBins / (2.f * B) : 0.f;
+    auto bin_of = [&](float sc) -> int {
+        const float x = __fmul_rn(__fadd_rn(B, -sc), scale);
+        return (int)fminf(fmaxf(x, 0.f), (float)(kHistBins - 1));
+    };
+    // pass 1: histogram
+    if (need > 0) {
+        for (int p = 0; p < c; ++p) {
+            const int U = s_U[p];
+            const uint64_t* seg = pbuf + (q * c + p) * T_cap;
+            for (int u = tid; u < U; u += blockDim.x)
+                atomicAdd(&hist[bin_of(float_from_order(~(uint32_t)(seg[u] >> 32)))], 1u);
+        }
+    }
+    __syncthreads();
+    // the bin reaching `need`, then the last bin to collect
+    if (tid == 0) {
+        int bt = -1;
+        if (need > 0) {
+            uint32_t cum = 0;
+            int bsel = kHistBins - 1;
+            for (int b = 0; b < kHistBins; ++b) {
+                cum += hist[b];
+                if ((int)cum >= need) { bsel = b; break; }
+            }
+            bt = bsel;
+            if (guarded && scale > 0.f) {
+                // lower edge of bsel, minus the band and one bin of rounding
+                const float edge = __fadd_rn(B, -(float)(bsel + 1) / scale);
+                const float t = edge - 2.f * qguard[q] - 1.f / scale;
+                bt = max(bsel, bin_of(t));
+            }
+            uint32_t upto = 0;
+            for (int b = 0; b <= bt; ++b) upto += hist[b];
+            if ((int)upto > kHistCand) bt = -2;       // too many: the fallback kernel takes this query
+        }
+        s_bt = bt;
+    }
+    __syncthreads();
+    const int bt = s_bt;
+    if (bt == -2) {
+        if (tid == 0) redo[atomicAdd(redo_count, 1)] = (int32_t)q;
+        return;
+    }
+    // pass 2: collect the keys of bins 0..bt as (score word, corpus id)
+    if (bt >= 0) {
+        for (int p = 0; p < c; ++p) {
+            const int U = s_U[p];
+            if (U == 0) continue;
+            const int64_t pair = q * c + p;
+            const uint64_t* seg = pbuf + pair * T_cap;
+            const int rj = route[pair];
+            const int64_t cb = cl_off[rj];
+            const int64_t n_c = cl_off[rj + 1] - cb;
+            for (int u0 = 0; u0 < U; u0 += blockDim.x) {
+                const int u = u0 + tid;
+                uint64_t kv = 0;
+                bool take = false;
+                if (u < U) {
+                    kv = seg[u];
+                    take = bin_of(float_from_order(~(uint32_t)(kv >> 32))) <= bt;
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, take);
+                int base = 0;
+                if (lane == 0 && m) base = atomicAdd(&s_cnt, __popc(m));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (take) {
+                    const int slot = base + __popc(m & ((1u << lane) - 1u));
+                    const uint32_t pos = (uint32_t)kv;
+                    if (slot >= kHistCand || (int64_t)pos >= n_c) {
+                        atomicAdd(&counters[CNT_BOUNDS], 1ull);
+                    } else {
+                        cand[slot] = (kv & 0xffffffff00000000ull) | (uint64_t)(uint32_t)orig_id[cb + pos];
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int n = min(s_cnt, kHistCand);
+    const int SP = n > 1 ? next_pow2_dev(n) : 1;
+    for (int u = n + tid; u < SP; u += blockDim.x) cand[u] = ~0ull;
+    __syncthreads();
+    block_bitonic(cand, SP);
+    int keep = min(need, n);
+    if (guarded && keep > 0) {
+        // every key within twice the error bound of the ks-th best approximate
+        // score (the exact top ks is among them)
+        const float vk = float_from_order(~(uint32_t)(cand[keep - 1] >> 32));
+        const float t = vk - 2.f * qguard[q];
+        if (tid == 0) s_band = keep;
+        __syncthreads();
+        for (int r = keep + tid; r < n; r += blockDim.x)
+            if (float_from_order(~(uint32_t)(cand[r] >> 32)) >= t) atomicMax(&s_band, r + 1);
+        __syncthreads();
+        const int band = s_band;
+        if (tid == 0 && band > so) atomicAdd(&counters[CNT_SEL_OVERFLOW], 1ull);
+        keep = min(band, so);
+    }
+    for (int r = tid; r < so; r += blockDim.x) {
+        if (r < keep) {
+            const uint64_t kv = cand[r];
+            out_ids[q * so + r] = (int64_t)(uint32_t)kv;
+            out_scores[q * so + r] = float_from_order(~(uint32_t)(kv >> 32));
+        } else {
+            out_ids[q * so + r] = -1;
+            out_scores[q * so + r] = -INFINITY;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ merge --
 // Warp per query; lane p < c walks list p (kp entries, sorted best first);
 // the ks best heads are written out (score descending, id ascending).
@@ -1382,6 +1550,9 @@ struct Workspace {
     float* sl_scores;
     float* qscale;              // FP16 path: per-query power-of-two scale
     float* qguard;              // tensor paths: error bound of a query's approximate scores
+    float* qbound;              // tensor paths: bound on |approximate score| of a query
+    int32_t* redo;              // tensor paths: queries left to the multi-level select
+    int32_t* redo_count;        // (cleared)
     int32_t* pcount;            // tensor path: candidates per pair (cleared)
     int32_t* unit_off;
     int64_t* bm_off;            // tensor paths: per-cluster bitmap offsets (words)
@@ -1442,6 +1613,7 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, const
     w.cnt = (int32_t*)take((size_t)g.ncl * 4);
     w.tc_err = (int*)take(16);
     w.pcount = tensor ? (int32_t*)take((size_t)np * 4) : nullptr;
+    w.redo_count = tensor ? (int32_t*)take(16) : nullptr;
     w.zero_bytes = o;
     w.unit_off = (int32_t*)take((size_t)(g.ncl + 1) * 4);
     w.bm_off = (int64_t*)take((size_t)(g.ncl + 1) * 8);
@@ -1472,6 +1644,8 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, const
     w.sl_scores = tensor ? (float*)take((size_t)nq * sh.so * 4) : nullptr;
     w.qscale = tensor ? (float*)take((size_t)nq * 4) : nullptr;
     w.qguard = tensor ? (float*)take((size_t)nq * 4) : nullptr;
+    w.qbound = tensor ? (float*)take((size_t)nq * 4) : nullptr;
+    w.redo = tensor ? (int32_t*)take((size_t)nq * 4) : nullptr;
     w.total = o;
     return w;
 }
@@ -1552,7 +1726,7 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         topc_exact_kernel<<<(unsigned)cdiv(nq * 32, 256), 256, 0, st>>>(
             S, Q, g.C, g.half_norm, nq, g.ncl, g.d, c, kTcGuard * ix->max_cnorm, w.route,
             tr ? tr->route : nullptr,
-            guard_mode(ix->params.score_mode), ix->max_xnorm, ix->x_scale, w.qscale, w.qguard,
+            guard_mode(ix->params.score_mode), ix->max_xnorm, ix->x_scale, w.qscale, w.qguard, w.qbound,
             &w.counters[CNT_ROUTE_FALLBACK]);
         LIDER_LAUNCH_CHECK("topc_exact_kernel");
     } else {
@@ -1647,9 +1821,14 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         // 3xTF32 and FP16 paths: a guard band makes the re-scored top k exact;
         // the served BF16 form keeps its approximate shortlist
         const int guarded = sh.mode != LIDER_SCORE_BF16;
+        select_hist_kernel<<<(unsigned)nq, 256, 0, st>>>(
+            w.pbuf, g.L * R, w.pcount, w.route, g.cl_off, g.orig_id, c, sh.ks, w.qguard, w.qbound, guarded, sh.so,
+            w.sl_ids, w.sl_scores, tr ? tr->ucount : nullptr, w.redo, w.redo_count, w.counters);
+        LIDER_LAUNCH_CHECK("select_hist_kernel");
         select_query_kernel<<<(unsigned)nq, 256, 0, st>>>(w.pbuf, g.L * R, w.pcount, w.route, g.cl_off, g.orig_id, c,
                                                           sh.ks, w.qguard, guarded, sh.so, w.sl_ids, w.sl_scores,
-                                                          tr ? tr->ucount : nullptr, w.counters);
+                                                          tr ? tr->ucount : nullptr, w.redo, w.redo_count,
+                                                          w.counters);
         LIDER_LAUNCH_CHECK("select_query_kernel");
     } else {
         if ((rc = mark(LIDER_PHASE_SCORE))) return rc;

@@ -168,6 +168,37 @@ def test_duplicates_empty_and_singleton_clusters(mode):
             assert st["empty_pairs"] == len(Q)
 
 
+@pytest.mark.parametrize("mode", [0, 3], ids=["tensor", "f16"])
+def test_massive_ties_take_the_multi_level_select(mode):
+    """A corpus of 3,000 copies of one vector (plus 1,000 others): a query's
+    candidate scores all tie, so the two-pass histogram select cannot bound
+    its collection and hands the query to the multi-level select.  Results
+    still equal the SIMT path's bit for bit (ties by lower id)."""
+    import torch
+    rng = np.random.default_rng(11)
+    d, n = 32, 4000
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    X /= np.linalg.norm(X, axis=1, keepdims=True)
+    X[:3000] = X[0]
+    C = X[rng.choice(n, 4, replace=False)].astype(np.float32)
+    C[0] = X[0]
+    cfg = dict(L=1, m=8, W=0.7, leaves=8, r0=256, B=1, k=16)
+    A = rng.standard_normal((cfg["L"] * cfg["m"], d)).astype(np.float32)
+    b = (rng.random(cfg["L"] * cfg["m"]) * cfg["W"]).astype(np.float32)
+    Q = np.concatenate([X[:8] + 1e-3 * rng.standard_normal((8, d)).astype(np.float32),
+                        rng.standard_normal((8, d)).astype(np.float32)])
+    Qd = torch.from_numpy(Q).cuda()
+    out = {}
+    for m in (mode, 1):
+        g = F.gpu_index(dict(cfg, score_mode=m), X, C, A, b)
+        ids, sc, st, tr = g.search(Qd, cfg["k"], 2, stats=True, trace=True)
+        out[m] = (ids.cpu().numpy(), sc.cpu().numpy(), tr["ucount"].cpu().numpy().sum(axis=1))
+        g.free()
+    assert out[mode][2].max() > 2048          # some tied query exceeds the histogram collection
+    assert np.array_equal(out[mode][0], out[1][0])
+    assert np.array_equal(out[mode][1].view(np.uint32), out[1][1].view(np.uint32))
+
+
 def test_invalid_search_arguments(tiny):
     import torch
     from paper_2205_00970_b300 import lider
