@@ -871,20 +871,27 @@ constexpr int kMarkSmemWords = 8192;   // clusters up to 262,144 points mark in 
 
 // One block per pair slot (pairs in cluster order): the union of the pair's L
 // expansion windows as a bitmap over the cluster's positions, at
-// bitmap + bm_off[j] + (slot - off[j]) * words_j.
+// bitmap + bm_off[j] + (slot - off[j]) * words_j; also slot_of[pair] = slot
+// and ucount[pair] = the number of candidates (set bits).
 __global__ void __launch_bounds__(256) mark_kernel(const int32_t* __restrict__ pairs,
                                                    const int32_t* __restrict__ route, const int32_t* __restrict__ off,
                                                    const int64_t* __restrict__ cl_off,
                                                    const int64_t* __restrict__ bm_off,
                                                    const int32_t* __restrict__ wstart, const int32_t* __restrict__ pos,
-                                                   int64_t n, int L, int R, uint32_t* __restrict__ bitmap) {
+                                                   int64_t n, int L, int R, uint32_t* __restrict__ bitmap,
+                                                   int32_t* __restrict__ slot_of, int32_t* __restrict__ ucount) {
     __shared__ uint32_t sbits[kMarkSmemWords];
+    __shared__ int s_u;
     const int64_t slot = blockIdx.x;
     const int64_t pair = pairs[slot];
     const int j = route[pair];
     const int64_t base = cl_off[j];
     const int64_t n_c = cl_off[j + 1] - base;
-    if (n_c == 0) return;
+    if (threadIdx.x == 0) {
+        slot_of[pair] = (int32_t)slot;
+        s_u = 0;
+    }
+    if (n_c == 0) return;                 // ucount stays 0 (cleared)
     const int64_t words = bitmap_words(n_c);
     uint32_t* dst = bitmap + bm_off[j] + (slot - off[j]) * words;
     const int T = (int)min((int64_t)R, n_c);
@@ -900,10 +907,17 @@ __global__ void __launch_bounds__(256) mark_kernel(const int32_t* __restrict__ p
             atomicOr(&bits[p >> 5], 1u << (p & 31));
         }
     }
-    if (in_smem) {
-        __syncthreads();
-        for (int64_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = sbits[i];
+    __syncthreads();
+    int u = 0;
+    for (int64_t i = threadIdx.x; i < words; i += blockDim.x) {
+        const uint32_t wv = bits[i];
+        if (in_smem) dst[i] = wv;
+        u += __popc(wv);
     }
+    for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+    if ((threadIdx.x & 31) == 0 && u) atomicAdd(&s_u, u);
+    __syncthreads();
+    if (threadIdx.x == 0) ucount[pair] = s_u;       // candidates of the pair
 }
 
 // One tensor-core tile: A row (first query slot), B row (first corpus row),
@@ -931,11 +945,8 @@ struct TcArgs {
     const int64_t* cl_off;
     const int32_t* pairs;
     const int64_t* bm_off;
-    const uint32_t* bitmap;
-    int ncl, T_cap;
-    uint64_t* pbuf;
-    int32_t* pcount;
-    unsigned long long* bounds;
+    int ncl;
+    float* dense;               // per pair: approximate scores over its cluster's positions
 };
 
 struct TcSched {
@@ -948,83 +959,50 @@ struct TcSched {
     }
 };
 
-// Keys of 16 columns at a time are staged per warp in shared memory (at most
-// 32 x 16) with their destination index in pbuf, then written 32 consecutive
-// staged keys per store instruction (runs of one row each, in row order).
-constexpr int kEpiStageKeys = 32 * 16;
-constexpr int kEpiStageBytes = 4 * kEpiStageKeys * (8 + 4);   // four epilogue warps
-constexpr uint32_t kNoSlot = 0xffffffffu;
+// The epilogue writes every score of the tile, dense: row r of a pair slot s
+// in cluster j is dense + (bm_off[j] + (s - off[j]) * words_j) * 32, one
+// FP32 per cluster position (pitch 32 * words_j, a multiple of 32, so the
+// rows and every 32-column group are 128-byte aligned).  A warp transposes
+// its 32 rows x 32 columns through shared memory and stores them 4 rows x
+// 128 bytes per instruction.  Which positions are candidates is read later,
+// from the pair's bitmap, by the select.
+constexpr int kEpiPitch = 33;                              // padded row of the transpose
+constexpr int kEpiStageBytes = 4 * 32 * kEpiPitch * 4;     // four epilogue warps
 
 struct TcEpi {
     const TcArgs* a;
-    uint64_t* stage;            // this warp's kEpiStageKeys keys
-    uint32_t* gidx;             // and their pbuf indices (kNoSlot: list full)
-    bool valid;
-    int64_t pair;
-    int p0, cursor;
-    uint32_t bits[tc::kBN / 32];
+    float* stage;               // this warp's 32 x kEpiPitch floats
+    float* drow;                // this lane's dense row at the tile's first column (null: no pair)
+    int ncols;                  // columns of the tile inside the row pitch (a multiple of 32)
 
     __device__ void begin(int u, int row) {
         const int4 t = a->units[u];
         const int j = t.z, it = t.w >> 16, rt = t.w & 0xffff;
         const int in_tile = min(tc::kBM, a->cnt[j] - it * tc::kBM);
-        valid = row < in_tile;
-        if (!valid) return;
         const int64_t n_c = a->cl_off[j + 1] - a->cl_off[j];
         const int64_t words = bitmap_words(n_c);
-        const int64_t local = (int64_t)it * tc::kBM + row;
-        pair = a->pairs[a->off[j] + local];
-        p0 = rt * tc::kBN;
-        const uint32_t* src = a->bitmap + a->bm_off[j] + local * words + (p0 >> 5);
-        const int64_t nw = words - (p0 >> 5);
-        int total = 0;
-#pragma unroll
-        for (int w = 0; w < tc::kBN / 32; ++w) {
-            bits[w] = w < nw ? __ldg(src + w) : 0u;
-            total += __popc(bits[w]);
-        }
-        cursor = total ? atomicAdd(&a->pcount[pair], total) : 0;
+        const int p0 = rt * tc::kBN;
+        ncols = (int)min((int64_t)tc::kBN, words * 32 - p0);
+        drow = row < in_tile ? a->dense + (a->bm_off[j] + ((int64_t)it * tc::kBM + row) * words) * 32 + p0 : nullptr;
     }
 
     // Called by all 32 lanes of the warp (lane = accumulator row).
     __device__ void operator()(int, int, int col0, const uint32_t (&v)[32]) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) half(col0 + 16 * h, v, h);
-    }
-
-    __device__ __forceinline__ void half(int c0, const uint32_t (&v)[32], int h) {
+        if (col0 >= ncols) return;                           // the same in every lane (per tile)
         const int lane = threadIdx.x & 31;
-        const uint32_t w = valid ? (bits[c0 >> 5] >> (16 * h)) & 0xffffu : 0u;
-        const int n = __popc(w);
-        int incl = n;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        if (total == 0) return;                              // the same in every lane
-        // stage this lane's run with its destinations: pbuf[pair * T_cap + cursor + i]
-        const uint32_t gbase = valid ? (uint32_t)(pair * a->T_cap + cursor) : 0u;
-        const int room = valid ? a->T_cap - cursor : 0;
-        int r = incl - n, i_run = 0;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            if ((w >> i) & 1u) {
-                stage[r] = score_key(__uint_as_float(v[16 * h + i]), (uint32_t)(p0 + c0 + i));
-                gidx[r] = i_run < room ? gbase + (uint32_t)i_run : kNoSlot;
-                ++r;
-                ++i_run;
-            }
-        }
-        cursor += n;
+        for (int i = 0; i < 32; ++i) stage[lane * kEpiPitch + i] = __uint_as_float(v[i]);
         __syncwarp();
-#pragma unroll 4
-        for (int t = lane; t < total; t += 32) {
-            const uint32_t gi = gidx[t];
-            const uint64_t kv = stage[t];
-            if (gi != kNoSlot) a->pbuf[gi] = kv;
-            else atomicAdd(a->bounds, 1ull);
+        const int sub = lane >> 3, c4 = (lane & 7) * 4;
+#pragma unroll
+        for (int rr = 0; rr < 32; rr += 4) {
+            const int r = rr + sub;
+            float* dst = reinterpret_cast<float*>(
+                __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(drow), r));
+            if (dst) {
+                const float* sr = stage + r * kEpiPitch + c4;
+                *reinterpret_cast<float4*>(dst + col0 + c4) = make_float4(sr[0], sr[1], sr[2], sr[3]);
+            }
         }
         __syncwarp();
     }
@@ -1043,11 +1021,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     TcEpi epi;
     epi.a = &args;
     // key staging after the engine's shared memory, one slice per epilogue warp
-    {
-        unsigned char* mine = smem + tc::kSmemBytes + (size_t)((threadIdx.x >> 5) & 3) * kEpiStageKeys * 12;
-        epi.stage = reinterpret_cast<uint64_t*>(mine);
-        epi.gidx = reinterpret_cast<uint32_t*>(mine + kEpiStageKeys * 8);
-    }
+    epi.stage = reinterpret_cast<float*>(smem + tc::kSmemBytes) + (size_t)((threadIdx.x >> 5) & 3) * 32 * kEpiPitch;
     tc::gemm_tiles<Kind>(&mAhi, &mAlo, &mBhi, &mBlo, kchunks, sched, epi, err, smem, ctl);
 }
 
@@ -1111,20 +1085,71 @@ __global__ void __launch_bounds__(256) rescore_kernel(const float* __restrict__ 
     }
 }
 
-// Per-query selection (tensor paths): the ks best keys over the candidate
-// lists of the query's c pairs, without per-pair lists.  Bucket selection on
-// the score between the best and the worst candidate finds the bucket holding
-// the ks-th key; a crowded bucket is refined (up to three levels, each a new
-// histogram of that bucket's keys).  The selected keys, mapped to corpus ids,
-// are sorted (score descending, id ascending).  One block per query.
+// The candidates of one (query, probed cluster) pair for the selects: the
+// pair's dense row of approximate scores over its cluster's positions and its
+// candidate bitmap (both written per pair slot, see mark_kernel and TcEpi).
+struct DenseArgs {
+    const float* dense;
+    const uint32_t* bitmap;
+    const int64_t* bm_off;
+    const int32_t* off;
+    const int32_t* slot_of;
+    const int32_t* route;
+    const int64_t* cl_off;
+    const int64_t* orig_id;
+    const int32_t* ucount;      // candidates per pair
+};
+
+struct PairRow {
+    const float* row;
+    const uint32_t* bm;
+    int64_t cb;                 // first row of the cluster in the reordered corpus
+    int n_c;
+};
+
+__device__ __forceinline__ PairRow pair_row(const DenseArgs& d, int64_t pair) {
+    const int32_t slot = d.slot_of[pair];
+    const int j = d.route[pair];
+    const int64_t cb = d.cl_off[j];
+    const int64_t n_c = d.cl_off[j + 1] - cb;
+    const int64_t wbase = d.bm_off[j] + (int64_t)(slot - d.off[j]) * bitmap_words(n_c);
+    return PairRow{d.dense + wbase * 32, d.bitmap + wbase, cb, (int)n_c};
+}
+
+__device__ __forceinline__ bool is_cand(const PairRow& r, int pos) { return (r.bm[pos >> 5] >> (pos & 31)) & 1u; }
+
+__device__ __forceinline__ uint64_t sel_key(float sc, uint32_t low) {
+    return ((uint64_t)(~float_order(sc)) << 32) | (uint64_t)low;
+}
+
+// Load the pair rows of query q into s_pr (threads 0..c-1) and the candidate
+// total (thread 0); returns nothing, callers __syncthreads().
+__device__ __forceinline__ void load_pairs(const DenseArgs& d, int64_t q, int c, PairRow* s_pr, int* s_total,
+                                           int32_t* trace_ucount, bool count, unsigned long long* counters) {
+    const int tid = threadIdx.x;
+    if (tid < c) s_pr[tid] = pair_row(d, q * c + tid);
+    if (tid == 0) {
+        int o = 0;
+        for (int p = 0; p < c; ++p) {
+            const int U = d.ucount[q * c + p];
+            o += U;
+            if (trace_ucount) trace_ucount[q * c + p] = U;
+        }
+        *s_total = o;
+        if (count) atomicAdd(&counters[CNT_CANDIDATES], (unsigned long long)o);
+    }
+}
+
+// Per-query selection (tensor paths), multi-level fallback: the ks best keys
+// over the candidates of the query's c pairs.  Bucket selection on the score
+// between the best and the worst candidate finds the bucket holding the ks-th
+// key; a crowded bucket is refined (up to three levels, each a new histogram
+// of that bucket's keys).  The selected keys, mapped to corpus ids, are sorted
+// (score descending, id ascending).  One block per query of `redo`.
 constexpr int kSelCap = 4096;
 constexpr int kSelLevels = 3;
 
-__global__ void __launch_bounds__(256) select_query_kernel(const uint64_t* __restrict__ pbuf, int T_cap,
-                                                           const int32_t* __restrict__ pcount,
-                                                           const int32_t* __restrict__ route,
-                                                           const int64_t* __restrict__ cl_off,
-                                                           const int64_t* __restrict__ orig_id, int c, int ks,
+__global__ void __launch_bounds__(256) select_query_kernel(DenseArgs da, int c, int ks,
                                                            const float* __restrict__ qguard, int guarded, int so,
                                                            int64_t* __restrict__ out_ids, float* __restrict__ out_scores,
                                                            int32_t* __restrict__ trace_ucount,
@@ -1139,38 +1164,28 @@ __global__ void __launch_bounds__(256) select_query_kernel(const uint64_t* __res
     __shared__ float s_thr;
     __shared__ int s_band;
     __shared__ uint32_t s_lo_ord, s_hi_ord;
+    __shared__ PairRow s_pr[LIDER_MAX_C];
     // redo: the queries select_hist_kernel left to this kernel (block b takes
     // redo[b]); otherwise block b takes query b
     if (redo && (int)blockIdx.x >= *redo_count) return;
     const int64_t q = redo ? redo[blockIdx.x] : blockIdx.x;
     const int tid = threadIdx.x;
-    if (tid == 0) { s_lo_ord = 0xffffffffu; s_hi_ord = 0u; s_total = 0; s_n = 0; }
+    if (tid == 0) { s_lo_ord = 0xffffffffu; s_hi_ord = 0u; s_n = 0; }
+    load_pairs(da, q, c, s_pr, &s_total, redo ? nullptr : trace_ucount, !redo, counters);
     __syncthreads();
-    // pass 0: candidate count and score range (as ordered keys)
+    // pass 0: score range (as ordered keys)
     uint32_t kmin = 0xffffffffu, kmax = 0u;
-    int tot = 0;
     for (int p = 0; p < c; ++p) {
-        const int64_t pair = q * c + p;
-        int U = pcount[pair];
-        if (U < 0 || U > T_cap) {
-            if (threadIdx.x == 0) atomicAdd(&counters[CNT_BOUNDS], 1ull);
-            U = 0;
-        }
-        tot += U;
-        const uint64_t* seg = pbuf + pair * T_cap;
-        for (int u = tid; u < U; u += blockDim.x) {
-            const uint32_t h = (uint32_t)(seg[u] >> 32);
+        const PairRow pr = s_pr[p];
+        for (int pos = tid; pos < pr.n_c; pos += blockDim.x) {
+            if (!is_cand(pr, pos)) continue;
+            const uint32_t h = ~float_order(pr.row[pos]);
             kmin = min(kmin, h);
             kmax = max(kmax, h);
         }
-        if (tid == 0 && trace_ucount) trace_ucount[pair] = U;
     }
     atomicMin(&s_lo_ord, kmin);
     atomicMax(&s_hi_ord, kmax);
-    if (tid == 0) {
-        s_total = tot;
-        if (!redo) atomicAdd(&counters[CNT_CANDIDATES], (unsigned long long)tot);
-    }
     __syncthreads();
     const int total = s_total;
     const int need = min(ks, total);
@@ -1204,11 +1219,10 @@ __global__ void __launch_bounds__(256) select_query_kernel(const uint64_t* __res
         for (int b = tid; b < kBins; b += blockDim.x) bins[b] = 0u;
         __syncthreads();
         for (int p = 0; p < c; ++p) {
-            const int64_t pair = q * c + p;
-            const int U = min(max(pcount[pair], 0), T_cap);
-            const uint64_t* seg = pbuf + pair * T_cap;
-            for (int u = tid; u < U; u += blockDim.x) {
-                const float sc = float_from_order(~(uint32_t)(seg[u] >> 32));
+            const PairRow pr = s_pr[p];
+            for (int pos = tid; pos < pr.n_c; pos += blockDim.x) {
+                if (!is_cand(pr, pos)) continue;
+                const float sc = pr.row[pos];
                 if (status(sc, l) == 2) atomicAdd(&bins[bucket(l, sc)], 1u);
             }
         }
@@ -1259,16 +1273,10 @@ __global__ void __launch_bounds__(256) select_query_kernel(const uint64_t* __res
     // refinement's resolution)
     for (int pass = 0; pass < 2 && need > 0; ++pass) {
         for (int p = 0; p < c; ++p) {
-            const int64_t pair = q * c + p;
-            const int U = min(max(pcount[pair], 0), T_cap);
-            if (U == 0) continue;
-            const uint64_t* seg = pbuf + pair * T_cap;
-            const int rj = route[pair];
-            const int64_t base = cl_off[rj];
-            const int64_t n_c = cl_off[rj + 1] - base;
-            for (int u = tid; u < U; u += blockDim.x) {
-                const uint64_t kv = seg[u];
-                const float sc = float_from_order(~(uint32_t)(kv >> 32));
+            const PairRow pr = s_pr[p];
+            for (int pos = tid; pos < pr.n_c; pos += blockDim.x) {
+                if (!is_cand(pr, pos)) continue;
+                const float sc = pr.row[pos];
                 const int st = status(sc, levels);
                 bool take;
                 if (st == 2) {
@@ -1277,16 +1285,9 @@ __global__ void __launch_bounds__(256) select_query_kernel(const uint64_t* __res
                 } else {
                     take = pass == 0 ? st == 1 : (st == 0 && sc >= thr);
                 }
-                if (take && (int64_t)(uint32_t)kv >= n_c) {
-                    atomicAdd(&counters[CNT_BOUNDS], 1ull);
-                    take = false;
-                }
                 if (take) {
                     const int slot = atomicAdd(&s_n, 1);
-                    if (slot < kSelCap) {
-                        const int64_t id = orig_id[base + (int64_t)(uint32_t)kv];
-                        keys[slot] = (kv & 0xffffffff00000000ull) | (uint64_t)(uint32_t)id;
-                    }
+                    if (slot < kSelCap) keys[slot] = sel_key(sc, (uint32_t)da.orig_id[pr.cb + pos]);
                 }
             }
         }
@@ -1329,44 +1330,27 @@ __global__ void __launch_bounds__(256) select_query_kernel(const uint64_t* __res
 // Per-query selection in two streaming passes (tensor paths).  The bins are
 // fixed by a bound B >= |approximate score| of the query (no range pass):
 // bin = floor((B - score) * kHistBins / 2B), bin 0 holding the best scores.
-// Pass 1 counts the keys per bin; the bin where the count reaches ks fixes a
-// threshold (lowered by the guard band and one bin for rounding); pass 2
-// collects the keys of the bins up to it as (score, corpus id), which are
-// sorted in shared memory.  A query whose collection would exceed kHistCand
-// is appended to `redo` and left to select_query_kernel.
+// Pass 1 counts the candidates per bin; the bin where the count reaches ks
+// fixes a threshold (lowered by the guard band and one bin for rounding);
+// pass 2 collects the candidates of the bins up to it as (score, corpus id),
+// which are sorted in shared memory.  A query whose collection would exceed
+// kHistCand is appended to `redo` and left to select_query_kernel.
 constexpr int kHistBins = 2048;
 constexpr int kHistCand = 2048;
 
 __global__ void __launch_bounds__(256) select_hist_kernel(
-        const uint64_t* __restrict__ pbuf, int T_cap, const int32_t* __restrict__ pcount,
-        const int32_t* __restrict__ route, const int64_t* __restrict__ cl_off, const int64_t* __restrict__ orig_id,
-        int c, int ks, const float* __restrict__ qguard, const float* __restrict__ qbound, int guarded, int so,
-        int64_t* __restrict__ out_ids, float* __restrict__ out_scores, int32_t* __restrict__ trace_ucount,
+        DenseArgs da, int c, int ks, const float* __restrict__ qguard, const float* __restrict__ qbound, int guarded,
+        int so, int64_t* __restrict__ out_ids, float* __restrict__ out_scores, int32_t* __restrict__ trace_ucount,
         int32_t* __restrict__ redo, int32_t* __restrict__ redo_count, unsigned long long* counters) {
     __shared__ uint32_t hist[kHistBins];
     __shared__ uint64_t cand[kHistCand];
-    __shared__ int s_U[LIDER_MAX_C];
+    __shared__ PairRow s_pr[LIDER_MAX_C];
     __shared__ int s_total, s_cnt, s_bt, s_band;
     const int64_t q = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31;
     for (int b = tid; b < kHistBins; b += blockDim.x) hist[b] = 0u;
-    if (tid == 0) {
-        int o = 0;
-        for (int p = 0; p < c; ++p) {
-            const int64_t pair = q * c + p;
-            int U = pcount[pair];
-            if (U < 0 || U > T_cap) {
-                atomicAdd(&counters[CNT_BOUNDS], 1ull);
-                U = 0;
-            }
-            s_U[p] = U;
-            o += U;
-            if (trace_ucount) trace_ucount[pair] = U;
-        }
-        s_total = o;
-        s_cnt = 0;
-        atomicAdd(&counters[CNT_CANDIDATES], (unsigned long long)o);
-    }
+    if (tid == 0) s_cnt = 0;
+    load_pairs(da, q, c, s_pr, &s_total, trace_ucount, true, counters);
     __syncthreads();
     const int total = s_total;
     const int need = min(ks, total);
@@ -1376,13 +1360,39 @@ __global__ void __launch_bounds__(256) select_hist_kernel(
         const float x = __fmul_rn(__fadd_rn(B, -sc), scale);
         return (int)fminf(fmaxf(x, 0.f), (float)(kHistBins - 1));
     };
+    // The passes read a pair's row as float4 groups (4 positions; the row
+    // pitch is a multiple of 32 and positions past n_c have no bitmap bit),
+    // kU groups per thread in flight; the bitmap only decides which count.
+    constexpr int kU = 4;
+    const int bd = blockDim.x;
+    auto load_groups = [&](const PairRow& pr, int g0, float4 (&sc)[kU], uint32_t (&wv)[kU]) {
+        const int ng = (pr.n_c + 3) >> 2;
+#pragma unroll
+        for (int r = 0; r < kU; ++r) {
+            const int g = g0 + r * bd;
+            wv[r] = 0u;
+            if (g < ng) {
+                wv[r] = (__ldg(pr.bm + (g >> 3)) >> ((g & 7) * 4)) & 0xfu;
+                sc[r] = __ldg(reinterpret_cast<const float4*>(pr.row) + g);
+            }
+        }
+    };
+    auto comp = [](const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; };
     // pass 1: histogram
     if (need > 0) {
         for (int p = 0; p < c; ++p) {
-            const int U = s_U[p];
-            const uint64_t* seg = pbuf + (q * c + p) * T_cap;
-            for (int u = tid; u < U; u += blockDim.x)
-                atomicAdd(&hist[bin_of(float_from_order(~(uint32_t)(seg[u] >> 32)))], 1u);
+            const PairRow pr = s_pr[p];
+            const int ng = (pr.n_c + 3) >> 2;
+            for (int g0 = tid; g0 < ng; g0 += kU * bd) {
+                float4 sc[kU];
+                uint32_t wv[kU];
+                load_groups(pr, g0, sc, wv);
+#pragma unroll
+                for (int r = 0; r < kU; ++r)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if ((wv[r] >> i) & 1u) atomicAdd(&hist[bin_of(comp(sc[r], i))], 1u);
+            }
         }
     }
     __syncthreads();
@@ -1415,35 +1425,49 @@ __global__ void __launch_bounds__(256) select_hist_kernel(
         if (tid == 0) redo[atomicAdd(redo_count, 1)] = (int32_t)q;
         return;
     }
-    // pass 2: collect the keys of bins 0..bt as (score word, corpus id)
+    // pass 2: collect the candidates of bins 0..bt as (score word, corpus id);
+    // a warp reserves its keys with one atomic
     if (bt >= 0) {
         for (int p = 0; p < c; ++p) {
-            const int U = s_U[p];
-            if (U == 0) continue;
-            const int64_t pair = q * c + p;
-            const uint64_t* seg = pbuf + pair * T_cap;
-            const int rj = route[pair];
-            const int64_t cb = cl_off[rj];
-            const int64_t n_c = cl_off[rj + 1] - cb;
-            for (int u0 = 0; u0 < U; u0 += blockDim.x) {
-                const int u = u0 + tid;
-                uint64_t kv = 0;
-                bool take = false;
-                if (u < U) {
-                    kv = seg[u];
-                    take = bin_of(float_from_order(~(uint32_t)(kv >> 32))) <= bt;
+            const PairRow pr = s_pr[p];
+            const int ng = (pr.n_c + 3) >> 2;
+            for (int base0 = 0; base0 < ng; base0 += kU * bd) {
+                float4 sc[kU];
+                uint32_t wv[kU];
+                load_groups(pr, base0 + tid, sc, wv);
+                uint32_t take[kU];
+                int mine = 0;
+#pragma unroll
+                for (int r = 0; r < kU; ++r) {
+                    take[r] = 0u;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (((wv[r] >> i) & 1u) && bin_of(comp(sc[r], i)) <= bt) take[r] |= 1u << i;
+                    mine += __popc(take[r]);
                 }
-                const unsigned m = __ballot_sync(0xffffffffu, take);
+                int incl = mine;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                const int wtotal = __shfl_sync(0xffffffffu, incl, 31);
                 int base = 0;
-                if (lane == 0 && m) base = atomicAdd(&s_cnt, __popc(m));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (take) {
-                    const int slot = base + __popc(m & ((1u << lane) - 1u));
-                    const uint32_t pos = (uint32_t)kv;
-                    if (slot >= kHistCand || (int64_t)pos >= n_c) {
-                        atomicAdd(&counters[CNT_BOUNDS], 1ull);
-                    } else {
-                        cand[slot] = (kv & 0xffffffff00000000ull) | (uint64_t)(uint32_t)orig_id[cb + pos];
+                if (lane == 31 && wtotal) base = atomicAdd(&s_cnt, wtotal);
+                base = __shfl_sync(0xffffffffu, base, 31);
+                int slot = base + incl - mine;
+#pragma unroll
+                for (int r = 0; r < kU; ++r) {
+                    const int g = base0 + tid + r * bd;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if ((take[r] >> i) & 1u) {
+                            if (slot < kHistCand)
+                                cand[slot] = sel_key(comp(sc[r], i), (uint32_t)__ldg(da.orig_id + pr.cb + 4 * g + i));
+                            else
+                                atomicAdd(&counters[CNT_BOUNDS], 1ull);
+                            ++slot;
+                        }
                     }
                 }
             }
@@ -1553,7 +1577,9 @@ struct Workspace {
     float* qbound;              // tensor paths: bound on |approximate score| of a query
     int32_t* redo;              // tensor paths: queries left to the multi-level select
     int32_t* redo_count;        // (cleared)
-    int32_t* pcount;            // tensor path: candidates per pair (cleared)
+    int32_t* pcount;            // tensor path: candidates per pair (cleared; written by mark_kernel)
+    float* dense;               // tensor paths: per pair slot, approximate scores over its cluster
+    int32_t* slot_of;           // tensor paths: pair -> its slot in cluster order
     int32_t* unit_off;
     int64_t* bm_off;            // tensor paths: per-cluster bitmap offsets (words)
     uint32_t* bitmap;           // tensor paths: per-pair candidate bitmaps
@@ -1639,7 +1665,9 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, const
     w.wlen = (int32_t*)take((size_t)np * g.L * 4);
     w.pscore = tensor ? nullptr : (float*)take((size_t)np * sh.kp * 4);
     w.pid = tensor ? nullptr : (int64_t*)take((size_t)np * sh.kp * 8);
-    w.pbuf = (uint64_t*)take((size_t)np * g.L * sh.R * 8);
+    w.pbuf = tensor ? nullptr : (uint64_t*)take((size_t)np * g.L * sh.R * 8);
+    w.dense = tensor ? (float*)take((size_t)sh.bitmap_words * 32 * 4) : nullptr;
+    w.slot_of = tensor ? (int32_t*)take((size_t)np * 4) : nullptr;
     w.sl_ids = tensor ? (int64_t*)take((size_t)nq * sh.so * 8) : nullptr;
     w.sl_scores = tensor ? (float*)take((size_t)nq * sh.so * 4) : nullptr;
     w.qscale = tensor ? (float*)take((size_t)nq * 4) : nullptr;
@@ -1662,14 +1690,12 @@ int check_search_args(const lider_index* ix, const float* Q, int64_t nq, int k, 
     const int64_t R = (int64_t)ix->params.r0 * k;
     if (R * ix->g.L > LIDER_MAX_LR) return fail(LIDER_ELIMIT, "lider_search: L * r0 * k exceeds LIDER_MAX_LR");
     if (nq * c > (int64_t)INT32_MAX) return fail(LIDER_ELIMIT, "lider_search: nq * c exceeds 2^31-1");
-    if (ix->params.score_mode != LIDER_SCORE_SIMT && nq * c * R * ix->g.L >= (int64_t)UINT32_MAX)
-        return fail(LIDER_ELIMIT, "lider_search: nq * c * L * r0 * k reaches 2^32 (candidate list slots); search "
-                                  "fewer queries per call");
     if (ix->params.score_mode == LIDER_SCORE_BF16 && (int64_t)ix->params.rerank * k > 4096)
         return fail(LIDER_ELIMIT, "lider_search: rerank * k exceeds 4096");
+    // tensor paths: per pair, a bitmap word and 32 FP32 scores per 32 positions
     if (ix->params.score_mode != LIDER_SCORE_SIMT && c <= ix->g.ncl &&
-        nq * ix->top_words[c] > ((int64_t)1 << 32))
-        return fail(LIDER_ELIMIT, "lider_search: candidate bitmaps of this batch exceed 16 GiB; search fewer "
+        nq * ix->top_words[c] > ((int64_t)1 << 29))
+        return fail(LIDER_ELIMIT, "lider_search: the per-pair score rows of this batch exceed 64 GiB; search fewer "
                                   "queries per call");
     if (!buffers) return LIDER_OK;
     if (nq > 0 && (!Q || !ids || !scores)) return fail(LIDER_EINVAL, "lider_search: NULL buffer");
@@ -1776,7 +1802,7 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
             if ((rc = make_tensor_map(&mql, w.qp_lo, np, g.d, tc::kBM))) return rc;
         }
         mark_kernel<<<(unsigned)np, 256, 0, st>>>(w.pairs, w.route, w.off, g.cl_off, w.bm_off, w.wstart, g.pos, g.n,
-                                                  g.L, R, w.bitmap);
+                                                  g.L, R, w.bitmap, w.slot_of, w.pcount);
         LIDER_LAUNCH_CHECK("mark_kernel");
         if ((rc = mark(LIDER_PHASE_SCORE))) return rc;
         tc_units_kernel<<<g.ncl, 128, 0, st>>>(w.unit_off, w.off, g.cl_off, g.ncl, w.units);
@@ -1789,12 +1815,8 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         ta.cl_off = g.cl_off;
         ta.pairs = w.pairs;
         ta.bm_off = w.bm_off;
-        ta.bitmap = w.bitmap;
         ta.ncl = g.ncl;
-        ta.T_cap = g.L * R;
-        ta.pbuf = w.pbuf;
-        ta.pcount = w.pcount;
-        ta.bounds = &w.counters[CNT_BOUNDS];
+        ta.dense = w.dense;
         const int tc_smem = tc::kSmemBytes + kEpiStageBytes;
         // A = queries of the tile (128 rows, box 128), B = cluster rows (256, box 256)
         if (sh.mode == LIDER_SCORE_BF16) {
@@ -1821,13 +1843,22 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         // 3xTF32 and FP16 paths: a guard band makes the re-scored top k exact;
         // the served BF16 form keeps its approximate shortlist
         const int guarded = sh.mode != LIDER_SCORE_BF16;
-        select_hist_kernel<<<(unsigned)nq, 256, 0, st>>>(
-            w.pbuf, g.L * R, w.pcount, w.route, g.cl_off, g.orig_id, c, sh.ks, w.qguard, w.qbound, guarded, sh.so,
-            w.sl_ids, w.sl_scores, tr ? tr->ucount : nullptr, w.redo, w.redo_count, w.counters);
+        DenseArgs da;
+        da.dense = w.dense;
+        da.bitmap = w.bitmap;
+        da.bm_off = w.bm_off;
+        da.off = w.off;
+        da.slot_of = w.slot_of;
+        da.route = w.route;
+        da.cl_off = g.cl_off;
+        da.orig_id = g.orig_id;
+        da.ucount = w.pcount;
+        select_hist_kernel<<<(unsigned)nq, 256, 0, st>>>(da, c, sh.ks, w.qguard, w.qbound, guarded, sh.so, w.sl_ids,
+                                                         w.sl_scores, tr ? tr->ucount : nullptr, w.redo, w.redo_count,
+                                                         w.counters);
         LIDER_LAUNCH_CHECK("select_hist_kernel");
-        select_query_kernel<<<(unsigned)nq, 256, 0, st>>>(w.pbuf, g.L * R, w.pcount, w.route, g.cl_off, g.orig_id, c,
-                                                          sh.ks, w.qguard, guarded, sh.so, w.sl_ids, w.sl_scores,
-                                                          tr ? tr->ucount : nullptr, w.redo, w.redo_count,
+        select_query_kernel<<<(unsigned)nq, 256, 0, st>>>(da, c, sh.ks, w.qguard, guarded, sh.so, w.sl_ids,
+                                                          w.sl_scores, tr ? tr->ucount : nullptr, w.redo, w.redo_count,
                                                           w.counters);
         LIDER_LAUNCH_CHECK("select_query_kernel");
     } else {
