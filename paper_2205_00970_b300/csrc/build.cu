@@ -105,6 +105,17 @@ __global__ void max_norms_kernel(const float* __restrict__ X, int64_t n, int d, 
     }
 }
 
+// |row| of each of n rows (warp per row, FP64 sum of squares, rounded up).
+__global__ void row_norms_kernel(const float* __restrict__ X, int64_t n, int d, float* __restrict__ out) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    double s = 0.0;
+    for (int i = lane; i < d; i += 32) s = fma((double)X[row * d + i], (double)X[row * d + i], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[row] = __double2float_ru(sqrt(s));
+}
+
 __global__ void inverse_ids_kernel(const int64_t* __restrict__ orig_id, int64_t n, int32_t* __restrict__ row_of) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r < n) row_of[orig_id[r]] = (int32_t)r;
@@ -269,7 +280,8 @@ int dev_alloc(void** p, size_t bytes, const char* what) {
 void release(lider_index* ix) {
     if (!ix) return;
     void* bufs[] = {ix->X, ix->orig_id, ix->cl_off, ix->C, ix->half_norm, ix->A, ix->bproj,
-                    ix->keys, ix->pos, ix->root, ix->leaf, ix->X_hi, ix->X_lo, ix->row_of, ix->X_h16, ix->C_hi, ix->C_lo};
+                    ix->keys, ix->pos, ix->root, ix->leaf, ix->X_hi, ix->X_lo, ix->row_of, ix->X_h16, ix->C_hi, ix->C_lo,
+                    ix->A_hi, ix->A_lo, ix->a_norm};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (ix->pool) cudaMemPoolDestroy(ix->pool);
@@ -343,6 +355,15 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
         if ((rc = launch_split_tf32(ix->C, (int64_t)ncl * d, ix->C_hi, ix->C_lo, st))) return rc;
         if ((rc = make_tensor_map(&ix->map_chi, ix->C_hi, ncl, d, 256))) return rc;
         if ((rc = make_tensor_map(&ix->map_clo, ix->C_lo, ncl, d, 256))) return rc;
+        // tensor-core hashing: projections split like the centroids
+        ALLOC(ix->A_hi, (size_t)H * d * sizeof(float), "projection TF32 head");
+        ALLOC(ix->A_lo, (size_t)H * d * sizeof(float), "projection TF32 tail");
+        ALLOC(ix->a_norm, (size_t)H * sizeof(float), "projection norms");
+        if ((rc = launch_split_tf32(ix->A, (int64_t)H * d, ix->A_hi, ix->A_lo, st))) return rc;
+        if ((rc = make_tensor_map(&ix->map_ahi, ix->A_hi, H, d, 256))) return rc;
+        if ((rc = make_tensor_map(&ix->map_alo, ix->A_lo, H, d, 256))) return rc;
+        row_norms_kernel<<<(unsigned)cdiv((int64_t)H * 32, 256), 256, 0, st>>>(ix->A, H, d, ix->a_norm);
+        LIDER_LAUNCH_CHECK("row_norms_kernel");
         std::vector<double> hn(ncl);
         LIDER_CUDA_TRY(cudaMemcpyAsync(hn.data(), ix->half_norm, ncl * sizeof(double), cudaMemcpyDeviceToHost, st));
         LIDER_CUDA_TRY(cudaStreamSynchronize(st));

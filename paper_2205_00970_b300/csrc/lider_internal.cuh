@@ -89,6 +89,11 @@ struct lider_index {
     float* X_lo = nullptr;
     int32_t* row_of = nullptr;
     uint16_t* X_h16 = nullptr;  // BF16 copy (served form) or FP16 copy of x_scale * X
+    float* A_hi = nullptr;      // projections, TF32 head / tail (tensor-core hashing)
+    float* A_lo = nullptr;
+    float* a_norm = nullptr;    // |a_h| per projection (rounded up)
+    CUtensorMap map_ahi;        // TMA maps over A_hi / A_lo, boxes of 32 x 256
+    CUtensorMap map_alo;
     float* C_hi = nullptr;      // centroids, TF32 head / tail (tensor-core routing)
     float* C_lo = nullptr;
     float max_cnorm = 0.f;      // largest centroid norm (routing error guard)

@@ -150,6 +150,100 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     tc::gemm_tiles<tc::KindTf32x3>(&mQhi, &mQlo, &mChi, &mClo, kchunks, sched, epi, err, smem, ctl);
 }
 
+// ------------------------------------------------------------------- hash --
+// Tensor paths: t = (a_h . q + b_h) / W for all queries and projections as
+// 3xTF32 tiles (queries x projections).  Where floor(t) could depend on the
+// tile's error (t within its bound, or within 1e-6 for the boundary count, of
+// an integer) the (query, projection) goes to a list, and hash_recheck_kernel
+// recomputes t with exactly the arithmetic of the SIMT hashing kernel
+// (sequential Dot2 over k, finished in FP64), so the query keys are the same
+// bit for bit on every score path.
+struct HashSched {
+    int nq, H;
+    __device__ int count() const { return ((nq + 127) / 128) * ((H + 255) / 256); }
+    __device__ void coords(int u, int& arow, int& brow) const {
+        const int nht = (H + 255) / 256;
+        arow = (u / nht) * 128;
+        brow = (u % nht) * 256;
+    }
+};
+
+struct HashEpi {
+    double* t;                  // nq x H
+    const float* b;             // offsets b_h
+    const float* a_norm;        // |a_h|
+    const float* qnorm;         // |q| (rounded up)
+    int32_t* recheck;           // (q * H + h) of the undecided values
+    int32_t* n_recheck;
+    float W, guard;             // guard: kTcGuard
+    int nq, H;
+    int q, h0;
+    float qn;
+    __device__ void begin(int u, int row) {
+        const int nht = (H + 255) / 256;
+        q = (u / nht) * 128 + row;
+        h0 = (u % nht) * 256;
+        qn = q < nq ? qnorm[q] : 0.f;
+    }
+    __device__ void operator()(int, int, int col0, const uint32_t (&v)[32]) {
+        if (q >= nq) return;
+#pragma unroll 4
+        for (int i = 0; i < 32; ++i) {
+            const int h = h0 + col0 + i;
+            if (h >= H) break;
+            const float acc = __uint_as_float(v[i]);
+            const float bh = b[h];
+            const float tf = __fdiv_rn(__fadd_rn(acc, bh), W);
+            // |tf - t| <= (tile error + FP32 rounding of acc + b) / W + rounding of the division
+            const float eps = __fdiv_rn(guard * qn * a_norm[h] + 4.f * 0x1p-24f * (fabsf(acc) + fabsf(bh)), W) +
+                              0x1p-22f * fabsf(tf);
+            const float dist = fabsf(tf - rintf(tf));
+            t[(int64_t)q * H + h] = (double)tf;
+            if (!(dist > 1.01f * eps + 1.1e-6f)) recheck[atomicAdd(n_recheck, 1)] = q * H + h;
+        }
+    }
+    __device__ void done(int, int) {}
+};
+
+__global__ void __launch_bounds__(tc::kThreads, 1)
+    hash_tc_kernel(const __grid_constant__ CUtensorMap mQhi, const __grid_constant__ CUtensorMap mQlo,
+                   const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo, int kchunks,
+                   HashSched sched, HashEpi epi, int* err) {
+    extern __shared__ unsigned char smem[];
+    __shared__ tc::Ctl ctl;
+    tc::gemm_tiles<tc::KindTf32x3>(&mQhi, &mQlo, &mAhi, &mAlo, kchunks, sched, epi, err, smem, ctl);
+}
+
+// t of the listed (query, projection) values, with the SIMT hashing kernel's
+// arithmetic: Dot2 steps over k = 0..d-1 in order, FP64 finish.
+__global__ void hash_recheck_kernel(const float* __restrict__ Q, const float* __restrict__ A,
+                                    const float* __restrict__ b, double W, int d, int H,
+                                    const int32_t* __restrict__ recheck, const int32_t* __restrict__ n_recheck,
+                                    double* __restrict__ t) {
+    const int n = *n_recheck;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int idx = recheck[i];
+        const int64_t q = idx / H;
+        const int h = idx - (int)q * H;
+        const float* x = Q + q * d;
+        const float* a = A + (int64_t)h * d;
+        Dot2 acc{0.f, 0.f};
+        for (int k = 0; k < d; ++k) dot2_step(acc, x[k], a[k]);
+        t[idx] = __ddiv_rn(__dadd_rn(dot2_value(acc), (double)b[h]), W);
+    }
+}
+
+// |q| per query (warp per query, FP64 sum of squares, rounded up).
+__global__ void qnorm_kernel(const float* __restrict__ Q, int64_t nq, int d, float* __restrict__ out) {
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (q >= nq) return;
+    double s = 0.0;
+    for (int i = lane; i < d; i += 32) s = fma((double)Q[q * d + i], (double)Q[q * d + i], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[q] = __double2float_ru(sqrt(s));
+}
+
 // Exact q.mu - |mu|^2/2 by one warp: per-lane Dot2, lanes summed in FP64.
 __device__ __forceinline__ double warp_exact_score(const float* __restrict__ q, const float* __restrict__ mu, int d,
                                                    double half_norm) {
@@ -219,8 +313,10 @@ __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __re
     const int nsl = min(c + kRouteExtra, ncl);
     // shortlist: the nsl best approximate scores (ties -> lower index)
     int sl[LIDER_MAX_C + kRouteExtra];
+    float av[LIDER_MAX_C + kRouteExtra];
     float ps = INFINITY;
     int pj = -1;
+#pragma unroll 1
     for (int r = 0; r < nsl; ++r) {
         float best = -INFINITY;
         int bj = 0x7fffffff;
@@ -239,6 +335,7 @@ __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __re
         ps = best;
         pj = bj;
         sl[r] = bj;
+        av[r] = best;
     }
     // the best approximate score outside the shortlist
     float a_out = -INFINITY;
@@ -253,11 +350,34 @@ __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __re
         for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
         a_out = best;
     }
-    // exact scores of the shortlist, then the c best
-    double ex[LIDER_MAX_C + kRouteExtra];
     float qn2 = 0.f;
     for (int i = lane; i < d; i += 32) qn2 = fmaf(qv[i], qv[i], qn2);
     for (int o = 16; o > 0; o >>= 1) qn2 += __shfl_xor_sync(0xffffffffu, qn2, o);
+    const float guard = guard_scale * sqrtf(qn2);
+    float amax = 0.f;
+    for (int i = lane; i < d; i += 32) amax = fmaxf(amax, fabsf(qv[i]));
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (lane == 0)
+        candidate_guard(gmode, sqrtf(qn2), amax, d, max_xnorm, x_scale, qscale + q, qguard + q, qbound + q);
+    // When each of the c best approximate scores leads the next one by more
+    // than twice the error bound, the exact scores have the same order and no
+    // other centroid can enter: the route is the shortlist's head.
+    bool clear = true;
+    for (int r = 0; r < c; ++r) {
+        const float next = r + 1 < nsl ? av[r + 1] : (nsl < ncl ? a_out : -INFINITY);
+        if (!((double)av[r] - (double)next > 2.0 * (double)guard)) clear = false;
+    }
+    if (clear) {
+        if (lane == 0) {
+            for (int r = 0; r < c; ++r) {
+                route[q * c + r] = sl[r];
+                if (trace_route) trace_route[q * c + r] = sl[r];
+            }
+        }
+        return;
+    }
+    // exact scores of the shortlist, then the c best
+    double ex[LIDER_MAX_C + kRouteExtra];
     for (int r = 0; r < nsl; ++r) ex[r] = warp_exact_score(qv, C + (int64_t)sl[r] * d, d, half_norm[sl[r]]);
     int out[LIDER_MAX_C];
     double e_c = -INFINITY;
@@ -279,12 +399,6 @@ __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __re
             e_c = best;
         }
     }
-    const float guard = guard_scale * sqrtf(qn2);
-    float amax = 0.f;
-    for (int i = lane; i < d; i += 32) amax = fmaxf(amax, fabsf(qv[i]));
-    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    if (lane == 0)
-        candidate_guard(gmode, sqrtf(qn2), amax, d, max_xnorm, x_scale, qscale + q, qguard + q, qbound + q);
     if (nsl < ncl && (double)a_out + (double)guard >= e_c) {
         // a centroid outside the shortlist may beat the c-th: score them all exactly
         if (lane == 0) atomicAdd(fallbacks, 1ull);
@@ -1575,6 +1689,9 @@ struct Workspace {
     float* qscale;              // FP16 path: per-query power-of-two scale
     float* qguard;              // tensor paths: error bound of a query's approximate scores
     float* qbound;              // tensor paths: bound on |approximate score| of a query
+    float* qnorm;               // tensor paths: |q| rounded up (hash error bound)
+    int32_t* hrecheck;          // tensor paths: hash values recomputed exactly (q * H + h)
+    int32_t* n_hrecheck;        // (cleared)
     int32_t* redo;              // tensor paths: queries left to the multi-level select
     int32_t* redo_count;        // (cleared)
     int32_t* pcount;            // tensor path: candidates per pair (cleared; written by mark_kernel)
@@ -1640,6 +1757,7 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, const
     w.tc_err = (int*)take(16);
     w.pcount = tensor ? (int32_t*)take((size_t)np * 4) : nullptr;
     w.redo_count = tensor ? (int32_t*)take(16) : nullptr;
+    w.n_hrecheck = tensor ? (int32_t*)take(16) : nullptr;
     w.zero_bytes = o;
     w.unit_off = (int32_t*)take((size_t)(g.ncl + 1) * 4);
     w.bm_off = (int64_t*)take((size_t)(g.ncl + 1) * 8);
@@ -1673,6 +1791,8 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, const
     w.qscale = tensor ? (float*)take((size_t)nq * 4) : nullptr;
     w.qguard = tensor ? (float*)take((size_t)nq * 4) : nullptr;
     w.qbound = tensor ? (float*)take((size_t)nq * 4) : nullptr;
+    w.qnorm = tensor ? (float*)take((size_t)nq * 4) : nullptr;
+    w.hrecheck = tensor ? (int32_t*)take((size_t)nq * g.H * 4) : nullptr;
     w.redo = tensor ? (int32_t*)take((size_t)nq * 4) : nullptr;
     w.total = o;
     return w;
@@ -1692,6 +1812,8 @@ int check_search_args(const lider_index* ix, const float* Q, int64_t nq, int k, 
     if (nq * c > (int64_t)INT32_MAX) return fail(LIDER_ELIMIT, "lider_search: nq * c exceeds 2^31-1");
     if (ix->params.score_mode == LIDER_SCORE_BF16 && (int64_t)ix->params.rerank * k > 4096)
         return fail(LIDER_ELIMIT, "lider_search: rerank * k exceeds 4096");
+    if (ix->params.score_mode != LIDER_SCORE_SIMT && nq * ix->g.H > (int64_t)INT32_MAX)
+        return fail(LIDER_ELIMIT, "lider_search: nq * L * m exceeds 2^31-1; search fewer queries per call");
     // tensor paths: per pair, a bitmap word and 32 FP32 scores per 32 positions
     if (ix->params.score_mode != LIDER_SCORE_SIMT && c <= ix->g.ncl &&
         nq * ix->top_words[c] > ((int64_t)1 << 29))
@@ -1721,7 +1843,39 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
 
     // 1. hash
     if ((rc = mark(LIDER_PHASE_HASH))) return rc;
-    if ((rc = launch_hash_t(Q, nq, g.d, g.A, g.bproj, g.H, g.W, w.tq, st))) return rc;
+    const bool tensor_route = ix->params.score_mode != LIDER_SCORE_SIMT;
+    CUtensorMap mqs_h, mqs_l;      // tensor paths: the queries as TF32 head / tail
+    if (tensor_route) {
+        if ((rc = launch_split_tf32(Q, nq * g.d, w.qs_hi, w.qs_lo, st))) return rc;
+        if ((rc = make_tensor_map(&mqs_h, w.qs_hi, nq, g.d, tc::kBM))) return rc;
+        if ((rc = make_tensor_map(&mqs_l, w.qs_lo, nq, g.d, tc::kBM))) return rc;
+        qnorm_kernel<<<(unsigned)cdiv(nq * 32, 256), 256, 0, st>>>(Q, nq, g.d, w.qnorm);
+        LIDER_LAUNCH_CHECK("qnorm_kernel");
+        HashSched hs{(int)nq, g.H};
+        HashEpi he;
+        he.t = w.tq;
+        he.b = g.bproj;
+        he.a_norm = ix->a_norm;
+        he.qnorm = w.qnorm;
+        he.recheck = w.hrecheck;
+        he.n_recheck = w.n_hrecheck;
+        he.W = (float)g.W;
+        he.guard = kTcGuard;
+        he.nq = (int)nq;
+        he.H = g.H;
+        const int64_t tiles = cdiv(nq, tc::kBM) * cdiv(g.H, tc::kBN);
+        LIDER_CUDA_TRY(cudaFuncSetAttribute(hash_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            tc::kSmemBytes));
+        hash_tc_kernel<<<(unsigned)std::min<int64_t>(tiles, ix->num_sms), tc::kThreads, tc::kSmemBytes, st>>>(
+            mqs_h, mqs_l, ix->map_ahi, ix->map_alo, (g.d + tc::KindTf32x3::kBK - 1) / tc::KindTf32x3::kBK, hs, he,
+            w.tc_err);
+        LIDER_LAUNCH_CHECK("hash_tc_kernel");
+        hash_recheck_kernel<<<(unsigned)(2 * ix->num_sms), 256, 0, st>>>(Q, g.A, g.bproj, g.W, g.d, g.H, w.hrecheck,
+                                                                         w.n_hrecheck, w.tq);
+        LIDER_LAUNCH_CHECK("hash_recheck_kernel");
+    } else {
+        if ((rc = launch_hash_t(Q, nq, g.d, g.A, g.bproj, g.H, g.W, w.tq, st))) return rc;
+    }
     if ((rc = launch_pack(w.tq, nq, g.L, g.m, g.beta, 0, g.L, 1, w.qkeys, &w.counters[CNT_QBOUNDARY],
                           &w.counters[CNT_QCLAMPED], st)))
         return rc;
@@ -1731,10 +1885,8 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
     if ((rc = mark(LIDER_PHASE_ROUTE))) return rc;
     if (ix->params.score_mode != LIDER_SCORE_SIMT) {
         float* S = reinterpret_cast<float*>(w.rscore);
-        if ((rc = launch_split_tf32(Q, nq * g.d, w.qs_hi, w.qs_lo, st))) return rc;
-        CUtensorMap mqh, mql;
-        if ((rc = make_tensor_map(&mqh, w.qs_hi, nq, g.d, tc::kBM))) return rc;
-        if ((rc = make_tensor_map(&mql, w.qs_lo, nq, g.d, tc::kBM))) return rc;
+        const CUtensorMap& mqh = mqs_h;
+        const CUtensorMap& mql = mqs_l;
         RouteSched rs{(int)nq, g.ncl};
         RouteEpi re;
         re.S = S;
