@@ -13,6 +13,8 @@
 #include <cmath>
 #include <cstring>
 
+#include <cuda_fp16.h>
+
 #include "lider_internal.cuh"
 
 namespace lider {
@@ -114,6 +116,31 @@ __global__ void row_norms_kernel(const float* __restrict__ X, int64_t n, int d, 
     for (int i = lane; i < d; i += 32) s = fma((double)X[row * d + i], (double)X[row * d + i], s);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) out[row] = __double2float_ru(sqrt(s));
+}
+
+// FP16 copy's rounding: per row, |fp16(s x) - s x| into out[0] and |fp16(s x)|
+// into out[1], maxima as float bits (rounded up); warp per row, FP64 sums.
+__global__ void f16_residual_kernel(const float* __restrict__ X, int64_t n, int d, float scale,
+                                    unsigned int* __restrict__ out) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    double r2 = 0.0, h2 = 0.0;
+    for (int i = lane; i < d; i += 32) {
+        const float v = X[row * d + i] * scale;
+        const float h = __half2float(__float2half_rn(v));
+        const double r = (double)h - (double)v;
+        r2 = fma(r, r, r2);
+        h2 = fma((double)h, (double)h, h2);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+        h2 += __shfl_xor_sync(0xffffffffu, h2, o);
+    }
+    if (lane == 0) {
+        atomicMax(out, __float_as_uint(__double2float_ru(sqrt(r2))));
+        atomicMax(out + 1, __float_as_uint(__double2float_ru(sqrt(h2))));
+    }
 }
 
 __global__ void inverse_ids_kernel(const int64_t* __restrict__ orig_id, int64_t n, int32_t* __restrict__ row_of) {
@@ -469,6 +496,15 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
             if ((rc = make_tensor_map(&ix->map_xh16, ix->X_h16, n, d, 256, true))) return rc;
         } else {
             ix->x_scale = f16_scale_host(norms[1]);
+            LIDER_CUDA_TRY(cudaMemsetAsync(mx.p, 0, 2 * sizeof(unsigned int), st));
+            f16_residual_kernel<<<(unsigned)cdiv(n * 32, 256), 256, 0, st>>>(ix->X, n, d, ix->x_scale,
+                                                                             mx.as<unsigned int>());
+            LIDER_LAUNCH_CHECK("f16_residual_kernel");
+            LIDER_CUDA_TRY(cudaMemcpyAsync(bits, mx.p, sizeof(bits), cudaMemcpyDeviceToHost, st));
+            LIDER_CUDA_TRY(cudaStreamSynchronize(st));
+            std::memcpy(norms, bits, sizeof(norms));
+            ix->xres_max = norms[0];
+            ix->xhat_max = norms[1];
             ALLOC(ix->X_h16, (size_t)n * d * sizeof(uint16_t), "corpus FP16 copy");
             if ((rc = launch_to_f16(ix->X, n * d, ix->x_scale, ix->X_h16, st))) return rc;
             if ((rc = make_tensor_map(&ix->map_xh16, ix->X_h16, n, d, 256, true))) return rc;

@@ -99,6 +99,8 @@ struct lider_index {
     float max_cnorm = 0.f;      // largest centroid norm (routing error guard)
     float max_xnorm = 0.f;      // largest corpus row norm (candidate error guard)
     float x_scale = 1.f;        // FP16 mode: power of two applied to X before rounding
+    float xres_max = 0.f;       // FP16 mode: max over rows of |fp16(x_scale x) - x_scale x| (rounded up)
+    float xhat_max = 0.f;       // FP16 mode: max over rows of |fp16(x_scale x)| (rounded up)
     CUtensorMap map_chi;        // TMA maps over C_hi / C_lo, boxes of 32 x 256
     CUtensorMap map_clo;
     CUtensorMap map_xh16;       // TMA map over X_h16, boxes of 64 x 256

@@ -215,21 +215,34 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
 }
 
 // t of the listed (query, projection) values, with the SIMT hashing kernel's
-// arithmetic: Dot2 steps over k = 0..d-1 in order, FP64 finish.
-__global__ void hash_recheck_kernel(const float* __restrict__ Q, const float* __restrict__ A,
-                                    const float* __restrict__ b, double W, int d, int H,
-                                    const int32_t* __restrict__ recheck, const int32_t* __restrict__ n_recheck,
-                                    double* __restrict__ t) {
+// arithmetic: Dot2 steps over k = 0..d-1 in order, FP64 finish.  One warp
+// per value: the warp stages both rows in shared memory (2 d floats, dynamic)
+// and lane 0 runs the sequential Dot2 from there.
+__global__ void __launch_bounds__(32) hash_recheck_kernel(const float* __restrict__ Q, const float* __restrict__ A,
+                                                          const float* __restrict__ b, double W, int d, int H,
+                                                          const int32_t* __restrict__ recheck,
+                                                          const int32_t* __restrict__ n_recheck,
+                                                          double* __restrict__ t) {
+    extern __shared__ float rows[];        // x[0..d), a[0..d)
     const int n = *n_recheck;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x;
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
         const int idx = recheck[i];
         const int64_t q = idx / H;
         const int h = idx - (int)q * H;
         const float* x = Q + q * d;
         const float* a = A + (int64_t)h * d;
-        Dot2 acc{0.f, 0.f};
-        for (int k = 0; k < d; ++k) dot2_step(acc, x[k], a[k]);
-        t[idx] = __ddiv_rn(__dadd_rn(dot2_value(acc), (double)b[h]), W);
+        for (int k = lane; k < d; k += 32) {
+            rows[k] = x[k];
+            rows[d + k] = a[k];
+        }
+        __syncwarp();
+        if (lane == 0) {
+            Dot2 acc{0.f, 0.f};
+            for (int k = 0; k < d; ++k) dot2_step(acc, rows[k], rows[d + k]);
+            t[idx] = __ddiv_rn(__dadd_rn(dot2_value(acc), (double)b[h]), W);
+        }
+        __syncwarp();
     }
 }
 
@@ -260,42 +273,45 @@ inline int guard_mode(int score_mode) {
     return score_mode == LIDER_SCORE_TENSOR ? 1 : score_mode == LIDER_SCORE_F16 ? 2 : 0;
 }
 
+// Power of two sq with sq * amax in [2^13, 2^14) (1 for amax == 0): the
+// FP16 path's query scale.
+__device__ __forceinline__ double f16_query_scale(float amax) {
+    if (!(amax > 0.f) || !(amax <= 3.0e38f)) return 1.0;
+    int e = 0;
+    frexpf(amax, &e);
+    e = max(-100, min(e, 127));
+    return ldexp(1.0, 14 - e);
+}
+
 // Per-query scale and error bound of the approximate candidate scores.
-// qn: |q| as computed in FP32 (inflated here to bound the true norm);
-// amax: max |q_i|.  gmode 1 (3xTF32): guard = kTcGuard |q| |x|max.
-// gmode 2 (FP16): q and x are scaled by powers of two sq, sx (s = sq sx) and
-// rounded to FP16 (unit roundoff u = 2^-11, subnormal half-spacing
-// eta = 2^-25); the products are exact in FP32 and the tensor cores sum d of
-// them with an error below d 2^-23 of their absolute sum.  Then
-//   |approx - s q.x| <= s |q| |x| (2u + u^2 + d 2^-23 (1 + 2u))
-//                       + eta (1 + u) sqrt(d) (sq |q| + sx |x|) (1 + d 2^-23) + d eta^2,
-// with |x| <= |x|max.  gmode 0 (served BF16 form): no guard.  qbound bounds
-// |approximate score| (it sets the select histogram's range).
-__device__ void candidate_guard(int gmode, float qn, float amax, int d, float xmax, float sx, float* qscale,
-                                float* qguard, float* qbound) {
+// qn: |q| as computed in FP32 (inflated here to bound the true norm).
+// gmode 1 (3xTF32): guard = kTcGuard |q| |x|max.
+// gmode 2 (FP16): q and x are scaled by powers of two sq, sx and rounded to
+// FP16; with e_q = fp16(sq q) - sq q and e_x = fp16(sx x) - sx x (their norms
+// measured exactly: eq for this query, xres for the worst row), and the
+// products exact in FP32,
+//   fp16(sq q) . fp16(sx x) - sq sx q.x = e_q . fp16(sx x) + sq q . e_x,
+// bounded by eq |x^|max + sq |q| xres; the tensor cores sum the d products
+// with an error below d 2^-23 of their absolute sum <= (sq |q| + eq) |x^|max.
+// gmode 0 (served BF16 form): no guard.  qbound bounds |approximate score|
+// (it sets the select histogram's range).
+__device__ void candidate_guard(int gmode, float qn, double sq, double eq, int d, float xmax, float sx,
+                                float xres, float xhat, float* qscale, float* qguard, float* qbound) {
     const double q = (double)qn * (1.0 + 1e-5);
-    double sq = 1.0, g = 0.0;
+    double g = 0.0, s = 1.0;
     if (gmode == 1) {
         g = (double)kTcGuard * q * (double)xmax;
     } else if (gmode == 0) {
         g = 0x1p-6 * q * (double)xmax;        // BF16: only bounds the scores below
     } else if (gmode == 2) {
-        if (amax > 0.f && amax <= 3.0e38f) {
-            int e = 0;
-            frexpf(amax, &e);
-            e = max(-100, min(e, 127));
-            sq = ldexp(1.0, 14 - e);
-        }
-        const double u = 0x1p-11, eta = 0x1p-25, acc = (double)d * 0x1p-23;
-        const double s = sq * (double)sx;
-        g = s * q * (double)xmax * (2.0 * u + u * u + acc * (1.0 + 2.0 * u)) +
-            eta * (1.0 + u) * sqrt((double)d) * (sq * q + (double)sx * (double)xmax) * (1.0 + acc) +
-            (double)d * eta * eta;
+        const double acc = (double)d * 0x1p-23;
+        const double qs = sq * q;
+        g = eq * (double)xhat + qs * (double)xres + acc * (qs + eq) * (double)xhat;
+        s = sq * (double)sx;
     }
-    *qscale = (float)sq;
+    *qscale = (float)(gmode == 2 ? sq : 1.0);
     *qguard = gmode == 0 ? 0.f : __double2float_ru(g * (1.0 + 0x1p-20));
     // |approximate score| <= s |q| |x|max + its error (s = 1 unless FP16)
-    const double s = gmode == 2 ? sq * (double)sx : 1.0;
     *qbound = __double2float_ru((s * q * (double)xmax + g) * (1.0 + 0x1p-20));
 }
 
@@ -303,6 +319,7 @@ __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __re
                                   const float* __restrict__ C, const double* __restrict__ half_norm, int64_t nq,
                                   int ncl, int d, int c, float guard_scale, int32_t* __restrict__ route,
                                   int32_t* __restrict__ trace_route, int gmode, float max_xnorm, float x_scale,
+                                  float xres_max, float xhat_max,
                                   float* __restrict__ qscale, float* __restrict__ qguard, float* __restrict__ qbound,
                                   unsigned long long* fallbacks) {
     const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -357,8 +374,23 @@ __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __re
     float amax = 0.f;
     for (int i = lane; i < d; i += 32) amax = fmaxf(amax, fabsf(qv[i]));
     for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    // FP16 path: the query's scale and the norm of its rounding residual
+    const double sq = gmode == 2 ? f16_query_scale(amax) : 1.0;
+    // (r = fp16(v) - v is exact in FP32; the FP32 sum of the d squares is
+    // inflated by (1 + (d + 32) 2^-23) to bound the exact one)
+    float eq2 = 0.f;
+    if (gmode == 2) {
+        for (int i = lane; i < d; i += 32) {
+            const float v = qv[i] * (float)sq;
+            const float r = __half2float(__float2half_rn(v)) - v;
+            eq2 = fmaf(r, r, eq2);
+        }
+        for (int o = 16; o > 0; o >>= 1) eq2 += __shfl_xor_sync(0xffffffffu, eq2, o);
+    }
+    const double eq = sqrt((double)eq2 * (1.0 + (double)(d + 32) * 0x1p-23)) * (1.0 + 0x1p-40);
     if (lane == 0)
-        candidate_guard(gmode, sqrtf(qn2), amax, d, max_xnorm, x_scale, qscale + q, qguard + q, qbound + q);
+        candidate_guard(gmode, sqrtf(qn2), sq, eq, d, max_xnorm, x_scale, xres_max, xhat_max, qscale + q,
+                        qguard + q, qbound + q);
     // When each of the c best approximate scores leads the next one by more
     // than twice the error bound, the exact scores have the same order and no
     // other centroid can enter: the route is the shortlist's head.
@@ -982,19 +1014,21 @@ __global__ void qgather_bf16_kernel(const float* __restrict__ Q, const int32_t* 
 }
 
 constexpr int kMarkSmemWords = 8192;   // clusters up to 262,144 points mark in shared memory
+constexpr int kMarkThreads = 128;
 
 // One block per pair slot (pairs in cluster order): the union of the pair's L
 // expansion windows as a bitmap over the cluster's positions, at
 // bitmap + bm_off[j] + (slot - off[j]) * words_j; also slot_of[pair] = slot
 // and ucount[pair] = the number of candidates (set bits).
-__global__ void __launch_bounds__(256) mark_kernel(const int32_t* __restrict__ pairs,
+__global__ void __launch_bounds__(kMarkThreads) mark_kernel(const int32_t* __restrict__ pairs,
                                                    const int32_t* __restrict__ route, const int32_t* __restrict__ off,
                                                    const int64_t* __restrict__ cl_off,
                                                    const int64_t* __restrict__ bm_off,
                                                    const int32_t* __restrict__ wstart, const int32_t* __restrict__ pos,
                                                    int64_t n, int L, int R, uint32_t* __restrict__ bitmap,
-                                                   int32_t* __restrict__ slot_of, int32_t* __restrict__ ucount) {
-    __shared__ uint32_t sbits[kMarkSmemWords];
+                                                   int32_t* __restrict__ slot_of, int32_t* __restrict__ ucount,
+                                                   int smem_words) {
+    extern __shared__ uint32_t sbits[];         // smem_words (the largest cluster's words, or 0)
     __shared__ int s_u;
     const int64_t slot = blockIdx.x;
     const int64_t pair = pairs[slot];
@@ -1009,7 +1043,7 @@ __global__ void __launch_bounds__(256) mark_kernel(const int32_t* __restrict__ p
     const int64_t words = bitmap_words(n_c);
     uint32_t* dst = bitmap + bm_off[j] + (slot - off[j]) * words;
     const int T = (int)min((int64_t)R, n_c);
-    const bool in_smem = words <= kMarkSmemWords;
+    const bool in_smem = words <= smem_words;
     uint32_t* bits = in_smem ? sbits : dst;
     for (int64_t i = threadIdx.x; i < words; i += blockDim.x) bits[i] = 0u;
     __syncthreads();
@@ -1140,55 +1174,76 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
 }
 
 
-// Exact re-score of the final lists (tensor-core paths).  The tensor cores'
-// FP32 accumulation is biased toward zero by about 1e-5 relative, uniformly,
-// so 3xTF32 scores select the same candidates up to near-ties, and the served
-// BF16 form selects a shortlist of S = rerank * k; the S chosen per query are
-// scored again here on the CUDA cores with exactly the SIMT path's arithmetic,
-// re-sorted (score descending, id ascending) and the best k kept.  One block
-// per query; in_ids may alias out_ids when S == k.
+// Exact re-score of the selected lists (tensor-core paths): the 3xTF32 and
+// FP16 paths select the ks best approximate scores plus a guard band of twice
+// their error bound, the served BF16 form a shortlist of rerank * k; every
+// listed id is scored again here on the CUDA cores with exactly the SIMT
+// path's arithmetic, the list re-sorted (score descending, id ascending) and
+// the best k kept.  One block per query; a list holds its entries first, then
+// -1s (S slots).
 __global__ void __launch_bounds__(256) rescore_kernel(const float* __restrict__ Q, const float* __restrict__ X,
                                                       const int32_t* __restrict__ row_of, int d, int S,
                                                       const int64_t* in_ids, int k, int64_t* out_ids,
                                                       float* out_scores, int64_t n,
                                                       unsigned long long* bounds) {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_nr;
     float* qv = reinterpret_cast<float*>(smem);
     uint64_t* key = reinterpret_cast<uint64_t*>(smem + align_up_dev((size_t)d * 4, 16));
     const int64_t q = blockIdx.x;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int d4 = d / 4;
+    if (tid == 0) s_nr = 0;
     for (int i = tid; i < d4; i += blockDim.x)
         reinterpret_cast<float4*>(qv)[i] = reinterpret_cast<const float4*>(Q + q * d)[i];
-    const int SP = next_pow2_dev(S);
     __syncthreads();
-    for (int r = warp; r < SP; r += blockDim.x / 32) {
-        int64_t id = r < S ? in_ids[q * S + r] : -1;
-        if (id >= n) {
-            if (lane == 0) atomicAdd(bounds, 1ull);
-            id = -1;
-        }
-        uint64_t kv = ~0ull;
-        if (id >= 0) {
-            const float4* x4 = reinterpret_cast<const float4*>(X + (int64_t)row_of[id] * d);
-            const float4* y4 = reinterpret_cast<const float4*>(qv);
-            float acc = 0.f;
-            for (int i = lane; i < d4; i += 32) {
-                const float4 x = __ldg(x4 + i), y = y4[i];
-                acc = fmaf(x.x, y.x, acc);
-                acc = fmaf(x.y, y.y, acc);
-                acc = fmaf(x.z, y.z, acc);
-                acc = fmaf(x.w, y.w, acc);
+    // the list holds its entries first, then -1s
+    for (int r = tid; r < S; r += blockDim.x)
+        if (in_ids[q * S + r] >= 0) atomicMax(&s_nr, r + 1);
+    __syncthreads();
+    const int nr = s_nr;
+    // two rows per warp at a time (each row's sum in the SIMT path's order)
+    const float4* y4 = reinterpret_cast<const float4*>(qv);
+    for (int r0 = 2 * warp; r0 < nr; r0 += 2 * nwarps) {
+        int64_t id[2];
+        const float4* x4[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            id[h] = r0 + h < nr ? in_ids[q * S + r0 + h] : -1;
+            if (id[h] >= n) {
+                if (lane == 0) atomicAdd(bounds, 1ull);
+                id[h] = -1;
             }
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            kv = ((uint64_t)(~float_order(acc)) << 32) | (uint64_t)(uint32_t)id;
+            x4[h] = id[h] >= 0 ? reinterpret_cast<const float4*>(X + (int64_t)row_of[id[h]] * d) : nullptr;
         }
-        if (lane == 0) key[r] = kv;
+        float acc[2] = {0.f, 0.f};
+        for (int i = lane; i < d4; i += 32) {
+            const float4 y = y4[i];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (!x4[h]) continue;
+                const float4 x = __ldg(x4[h] + i);
+                acc[h] = fmaf(x.x, y.x, acc[h]);
+                acc[h] = fmaf(x.y, y.y, acc[h]);
+                acc[h] = fmaf(x.z, y.z, acc[h]);
+                acc[h] = fmaf(x.w, y.w, acc[h]);
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            for (int o = 16; o > 0; o >>= 1) acc[h] += __shfl_xor_sync(0xffffffffu, acc[h], o);
+            if (lane == 0 && r0 + h < nr)
+                key[r0 + h] = id[h] >= 0 ? ((uint64_t)(~float_order(acc[h])) << 32) | (uint64_t)(uint32_t)id[h]
+                                         : ~0ull;
+        }
     }
+    const int SP = nr > 1 ? next_pow2_dev(nr) : 1;
+    for (int u = nr + tid; u < SP; u += blockDim.x) key[u] = ~0ull;
+    if (nr == 0 && tid == 0) key[0] = ~0ull;
     __syncthreads();
     block_bitonic(key, SP);
     for (int r = tid; r < k; r += blockDim.x) {
-        const uint64_t kv = key[r];
+        const uint64_t kv = r < nr ? key[r] : ~0ull;
         if (kv == ~0ull) {
             out_ids[q * k + r] = -1;
             out_scores[q * k + r] = -INFINITY;
@@ -1452,14 +1507,30 @@ __global__ void __launch_bounds__(256) select_query_kernel(DenseArgs da, int c, 
 constexpr int kHistBins = 2048;
 constexpr int kHistCand = 2048;
 
+__device__ void block_bitonic32(uint32_t* key, int n) {
+    for (int size = 2; size <= n; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < n / 2; i += blockDim.x) {
+                const int lo_i = 2 * stride * (i / stride) + (i % stride);
+                const int hi_i = lo_i + stride;
+                const bool up = (lo_i & size) == 0;
+                const uint32_t x0 = key[lo_i], x1 = key[hi_i];
+                if ((x0 > x1) == up) { key[lo_i] = x1; key[hi_i] = x0; }
+            }
+            __syncthreads();
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) select_hist_kernel(
         DenseArgs da, int c, int ks, const float* __restrict__ qguard, const float* __restrict__ qbound, int guarded,
         int so, int64_t* __restrict__ out_ids, float* __restrict__ out_scores, int32_t* __restrict__ trace_ucount,
         int32_t* __restrict__ redo, int32_t* __restrict__ redo_count, unsigned long long* counters) {
-    __shared__ uint32_t hist[kHistBins];
+    __shared__ uint32_t hist[kHistBins];          // also: the threads' maxima (need <= blockDim)
     __shared__ uint64_t cand[kHistCand];
     __shared__ PairRow s_pr[LIDER_MAX_C];
     __shared__ int s_total, s_cnt, s_bt, s_band;
+    __shared__ float s_thr;
     const int64_t q = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31;
     for (int b = tid; b < kHistBins; b += blockDim.x) hist[b] = 0u;
@@ -1492,8 +1563,101 @@ __global__ void __launch_bounds__(256) select_hist_kernel(
         }
     };
     auto comp = [](const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; };
-    // pass 1: histogram
-    if (need > 0) {
+    // Way 1 (need <= 4 * blockDim): one pass in which every thread keeps its
+    // 4 best candidates (score, list, position).  The need-th best of those
+    // 4 * blockDim scores is a candidate score with at least `need` candidates
+    // at or above it, so the ks-th best is not below it: every candidate at or
+    // above it less twice the guard is collected, from the kept four, or by a
+    // second look at its own positions for a thread whose 4th best already
+    // clears that threshold (it may hold more).
+    constexpr int kKeep = 4;
+    bool small_lists = true;                        // positions fit the (list, position) packing
+    for (int p = 0; p < c; ++p) small_lists = small_lists && s_pr[p].n_c < (1 << 27);
+    const bool by_max = need > 0 && need <= kKeep * bd && small_lists;
+    float ts[kKeep];
+    uint32_t tp[kKeep];                            // (list << 27) | position
+#pragma unroll
+    for (int j = 0; j < kKeep; ++j) { ts[j] = -INFINITY; tp[j] = 0u; }
+    if (by_max) {
+        for (int p = 0; p < c; ++p) {
+            const PairRow pr = s_pr[p];
+            const int ng = (pr.n_c + 3) >> 2;
+            for (int g0 = tid; g0 < ng; g0 += kU * bd) {
+                float4 sc[kU];
+                uint32_t wv[kU];
+                load_groups(pr, g0, sc, wv);
+#pragma unroll
+                for (int r = 0; r < kU; ++r) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float v = comp(sc[r], i);
+                        if (((wv[r] >> i) & 1u) && v > ts[kKeep - 1]) {
+                            uint32_t pv = ((uint32_t)p << 27) | (uint32_t)(4 * (g0 + r * bd) + i);
+                            float vv = v;
+#pragma unroll
+                            for (int j = 0; j < kKeep; ++j) {   // insert, best first
+                                if (vv > ts[j]) {
+                                    const float t0 = ts[j];
+                                    const uint32_t p0 = tp[j];
+                                    ts[j] = vv;
+                                    tp[j] = pv;
+                                    vv = t0;
+                                    pv = p0;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        // the kept scores as sortable words, best first (none: the largest word)
+        for (int u = tid; u < kHistBins; u += bd) hist[u] = 0xffffffffu;
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kKeep; ++j) hist[tid * kKeep + j] = ts[j] == -INFINITY ? 0xffffffffu : ~float_order(ts[j]);
+        __syncthreads();
+        block_bitonic32(hist, next_pow2_dev(kKeep * bd));
+        if (tid == 0) {
+            const uint32_t wk = hist[need - 1];
+            float thr = -INFINITY;                 // fewer kept scores than need: take all
+            if (wk != 0xffffffffu) {
+                thr = float_from_order(~wk);
+                if (guarded) thr = thr - 2.f * qguard[q];
+            }
+            s_thr = thr;
+            s_bt = 0;
+        }
+        __syncthreads();
+        const float thr = s_thr;
+        auto emit = [&](float v, int p, int pos) {
+            const int slot = atomicAdd(&s_cnt, 1);
+            if (slot < kHistCand) cand[slot] = sel_key(v, (uint32_t)__ldg(da.orig_id + s_pr[p].cb + pos));
+        };
+        if (ts[kKeep - 1] >= thr && ts[kKeep - 1] != -INFINITY) {
+            // this thread may hold more than four: look at its positions again
+            for (int p = 0; p < c; ++p) {
+                const PairRow pr = s_pr[p];
+                const int ng = (pr.n_c + 3) >> 2;
+                for (int g0 = tid; g0 < ng; g0 += kU * bd) {
+                    float4 sc[kU];
+                    uint32_t wv[kU];
+                    load_groups(pr, g0, sc, wv);
+#pragma unroll
+                    for (int r = 0; r < kU; ++r)
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            if (((wv[r] >> i) & 1u) && comp(sc[r], i) >= thr)
+                                emit(comp(sc[r], i), p, 4 * (g0 + r * bd) + i);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kKeep; ++j)
+                if (ts[j] != -INFINITY && ts[j] >= thr) emit(ts[j], (int)(tp[j] >> 27), (int)(tp[j] & 0x7ffffffu));
+        }
+    }
+    // Threshold, way 2 (larger need): histogram
+    if (need > 0 && !by_max) {
         for (int p = 0; p < c; ++p) {
             const PairRow pr = s_pr[p];
             const int ng = (pr.n_c + 3) >> 2;
@@ -1511,7 +1675,7 @@ __global__ void __launch_bounds__(256) select_hist_kernel(
     }
     __syncthreads();
     // the bin reaching `need`, then the last bin to collect
-    if (tid == 0) {
+    if (tid == 0 && !by_max) {
         int bt = -1;
         if (need > 0) {
             uint32_t cum = 0;
@@ -1539,9 +1703,10 @@ __global__ void __launch_bounds__(256) select_hist_kernel(
         if (tid == 0) redo[atomicAdd(redo_count, 1)] = (int32_t)q;
         return;
     }
-    // pass 2: collect the candidates of bins 0..bt as (score word, corpus id);
-    // a warp reserves its keys with one atomic
-    if (bt >= 0) {
+    // pass 2: collect the candidates above the threshold (way 1) or in bins
+    // 0..bt (way 2) as (score word, corpus id); a warp reserves its keys with
+    // one atomic
+    if (bt >= 0 && !by_max) {
         for (int p = 0; p < c; ++p) {
             const PairRow pr = s_pr[p];
             const int ng = (pr.n_c + 3) >> 2;
@@ -1555,8 +1720,10 @@ __global__ void __launch_bounds__(256) select_hist_kernel(
                 for (int r = 0; r < kU; ++r) {
                     take[r] = 0u;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        if (((wv[r] >> i) & 1u) && bin_of(comp(sc[r], i)) <= bt) take[r] |= 1u << i;
+                    for (int i = 0; i < 4; ++i) {
+                        if (!((wv[r] >> i) & 1u)) continue;
+                        if (bin_of(comp(sc[r], i)) <= bt) take[r] |= 1u << i;
+                    }
                     mine += __popc(take[r]);
                 }
                 int incl = mine;
@@ -1578,8 +1745,6 @@ __global__ void __launch_bounds__(256) select_hist_kernel(
                         if ((take[r] >> i) & 1u) {
                             if (slot < kHistCand)
                                 cand[slot] = sel_key(comp(sc[r], i), (uint32_t)__ldg(da.orig_id + pr.cb + 4 * g + i));
-                            else
-                                atomicAdd(&counters[CNT_BOUNDS], 1ull);
                             ++slot;
                         }
                     }
@@ -1588,6 +1753,10 @@ __global__ void __launch_bounds__(256) select_hist_kernel(
         }
     }
     __syncthreads();
+    if (s_cnt > kHistCand) {                           // way 1 collected too many: fallback kernel
+        if (tid == 0) redo[atomicAdd(redo_count, 1)] = (int32_t)q;
+        return;
+    }
     const int n = min(s_cnt, kHistCand);
     const int SP = n > 1 ? next_pow2_dev(n) : 1;
     for (int u = n + tid; u < SP; u += blockDim.x) cand[u] = ~0ull;
@@ -1870,8 +2039,8 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
             mqs_h, mqs_l, ix->map_ahi, ix->map_alo, (g.d + tc::KindTf32x3::kBK - 1) / tc::KindTf32x3::kBK, hs, he,
             w.tc_err);
         LIDER_LAUNCH_CHECK("hash_tc_kernel");
-        hash_recheck_kernel<<<(unsigned)(2 * ix->num_sms), 256, 0, st>>>(Q, g.A, g.bproj, g.W, g.d, g.H, w.hrecheck,
-                                                                         w.n_hrecheck, w.tq);
+        hash_recheck_kernel<<<(unsigned)(16 * ix->num_sms), 32, (size_t)2 * g.d * sizeof(float), st>>>(
+            Q, g.A, g.bproj, g.W, g.d, g.H, w.hrecheck, w.n_hrecheck, w.tq);
         LIDER_LAUNCH_CHECK("hash_recheck_kernel");
     } else {
         if ((rc = launch_hash_t(Q, nq, g.d, g.A, g.bproj, g.H, g.W, w.tq, st))) return rc;
@@ -1904,7 +2073,8 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         topc_exact_kernel<<<(unsigned)cdiv(nq * 32, 256), 256, 0, st>>>(
             S, Q, g.C, g.half_norm, nq, g.ncl, g.d, c, kTcGuard * ix->max_cnorm, w.route,
             tr ? tr->route : nullptr,
-            guard_mode(ix->params.score_mode), ix->max_xnorm, ix->x_scale, w.qscale, w.qguard, w.qbound,
+            guard_mode(ix->params.score_mode), ix->max_xnorm, ix->x_scale, ix->xres_max, ix->xhat_max, w.qscale,
+            w.qguard, w.qbound,
             &w.counters[CNT_ROUTE_FALLBACK]);
         LIDER_LAUNCH_CHECK("topc_exact_kernel");
     } else {
@@ -1953,8 +2123,12 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
             if ((rc = make_tensor_map(&mqh, w.qp_hi, np, g.d, tc::kBM))) return rc;
             if ((rc = make_tensor_map(&mql, w.qp_lo, np, g.d, tc::kBM))) return rc;
         }
-        mark_kernel<<<(unsigned)np, 256, 0, st>>>(w.pairs, w.route, w.off, g.cl_off, w.bm_off, w.wstart, g.pos, g.n,
-                                                  g.L, R, w.bitmap, w.slot_of, w.pcount);
+        // bitmaps of clusters up to kMarkSmemWords words are built in shared memory
+        const int max_words = g.max_row_tiles * (tc::kBN / 32);
+        const int mark_words = max_words <= kMarkSmemWords ? max_words : 0;
+        mark_kernel<<<(unsigned)np, kMarkThreads, (size_t)mark_words * 4, st>>>(
+            w.pairs, w.route, w.off, g.cl_off, w.bm_off, w.wstart, g.pos, g.n, g.L, R, w.bitmap, w.slot_of, w.pcount,
+            mark_words);
         LIDER_LAUNCH_CHECK("mark_kernel");
         if ((rc = mark(LIDER_PHASE_SCORE))) return rc;
         tc_units_kernel<<<g.ncl, 128, 0, st>>>(w.unit_off, w.off, g.cl_off, g.ncl, w.units);
