@@ -10,8 +10,10 @@ merge) with the index and queries resident in HBM.  Prints one JSON line.
   value     queries/s over all ranks (device-resident inputs, CUDA events)
   e2e       the same through lider_search_host: queries copied from pinned
             host memory and results copied back inside the timed region
-  roofline  the gather/score kernel: algorithmic bytes (unique candidates x
-            (d*4 + 4)) per launch / its event-timed duration vs measured HBM
+  roofline  the tensor-core score kernel (tc_score_kernel): executed tensor
+            FLOPs per launch (tiles x 128 x 256 x K x 2, x3 for 3xTF32) / its
+            event-timed duration vs the measured dense peak of its type
+            (--score simt: the FP32 CUDA-core peak)
   cpu_baseline  the FP64 oracle on a bounded query sample on host cores
 
 --impl reference times the FP64 oracle itself (there is no released
@@ -38,7 +40,7 @@ from paper_2205_00970_b300 import configs, synth  # noqa: E402
 
 METRIC = "queries/s at fixed recall@10 vs FP64 oracle (plain vs served BF16); p50/p99 ms"
 # our kernels per lider_search (phase list in search.cu; confirmed by the ncu launch list)
-LAUNCHES_PER_SEARCH = {"tensor": 15, "simt": 10, "bf16": 15, "f16": 15}
+LAUNCHES_PER_SEARCH = {"tensor": 18, "simt": 10, "bf16": 18, "f16": 18}
 MODES = {"tensor": 0, "simt": 1, "bf16": 2, "f16": 3}
 DTYPES = {"tensor": "f32", "simt": "f32", "bf16": "bf16", "f16": "f16"}
 
@@ -336,11 +338,9 @@ def run_lider(args, cfg):
                     "frac": achieved / peak, "traffic": None, "kernel": "tc_score_kernel",
                     "peak_source": psrc,
                     "tensor_flop_per_launch": tc_flop,
+                    "tiles_per_launch": stats["tc_tiles"],
                     "useful_flop_per_launch": useful_flop,
-                    "useful_tflops": useful_flop / score_s / 1e12,
-                    "gather_bytes_per_launch": gather_bytes,
-                    "gather_gbs_vs_hbm": {"achieved": gather_bytes / score_s / 1e9, "peak": hbm,
-                                          "frac": gather_bytes / score_s / 1e9 / hbm}}
+                    "useful_tflops": useful_flop / score_s / 1e12}
     else:
         peak = fp32_simt_peak_tflops(clk.get("sm_max_mhz") or 2032.0)
         achieved = useful_flop / score_s / 1e12
@@ -366,6 +366,10 @@ def run_lider(args, cfg):
                 "d2h_bytes_per_step": int(nq * k * (8 + 4))},
         "gpu_launches": LAUNCHES_PER_SEARCH[args.score] * args.steps,
         "score_mode": args.score,
+        "results": ("exact FP32 top-k of each query's candidate union (approximate tensor scores select with a "
+                    "proven guard band, every listed id is re-scored in FP32; equal bit for bit across "
+                    "f16/tensor/simt)") if args.score != "bf16" else
+                   f"served shortlist: BF16 scores, FP32 re-rank of the best {args.rerank} * k",
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -452,7 +456,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["lider", "reference"], default="lider")
     ap.add_argument("--workload", default="mid")
-    ap.add_argument("--score", choices=list(MODES), default="tensor")
+    ap.add_argument("--score", choices=list(MODES), default="f16",
+                    help="f16 (default), tensor (3xTF32) and simt give the same exact top-k; bf16 is the served "
+                         "shortlist form")
     ap.add_argument("--rerank", type=int, default=2, help="served BF16 form: shortlist = rerank * k")
     ap.add_argument("--serve", type=float, default=None,
                     help="serving mode: offered load in queries/s (Poisson arrivals)")
