@@ -25,6 +25,7 @@
 //               its c lists (Sec. 6.2, heap of list heads); tensor modes:
 //               rescore_kernel, exact FP32 scores of the selected lists
 #include <algorithm>
+#include <map>
 #include <mutex>
 
 #include <cuda_bf16.h>
@@ -52,6 +53,22 @@ enum {
     CNT_SEL_OVERFLOW,  // queries whose guarded candidate band did not fit (result may be inexact)
     CNT_SLOTS = 9
 };
+
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per (kernel, device,
+// size): a search repeated under stream capture then makes no such call.
+std::mutex g_attr_mutex;
+std::map<std::pair<const void*, int>, int> g_attr_set;
+
+int smem_attr(const void* fn, int bytes) {
+    int dev = 0;
+    LIDER_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    int& have = g_attr_set[{fn, dev}];
+    if (have >= bytes) return LIDER_OK;
+    LIDER_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    have = bytes;
+    return LIDER_OK;
+}
 
 inline int next_pow2(int x) {
     int p = 1;
@@ -2033,8 +2050,7 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         he.nq = (int)nq;
         he.H = g.H;
         const int64_t tiles = cdiv(nq, tc::kBM) * cdiv(g.H, tc::kBN);
-        LIDER_CUDA_TRY(cudaFuncSetAttribute(hash_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            tc::kSmemBytes));
+        if ((rc = smem_attr((const void*)hash_tc_kernel, (int)(tc::kSmemBytes)))) return rc;
         hash_tc_kernel<<<(unsigned)std::min<int64_t>(tiles, ix->num_sms), tc::kThreads, tc::kSmemBytes, st>>>(
             mqs_h, mqs_l, ix->map_ahi, ix->map_alo, (g.d + tc::KindTf32x3::kBK - 1) / tc::KindTf32x3::kBK, hs, he,
             w.tc_err);
@@ -2063,8 +2079,7 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         re.nq = (int)nq;
         re.ncl = g.ncl;
         const int64_t tiles = cdiv(nq, tc::kBM) * cdiv(g.ncl, tc::kBN);
-        LIDER_CUDA_TRY(cudaFuncSetAttribute(route_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            tc::kSmemBytes));
+        if ((rc = smem_attr((const void*)route_tc_kernel, (int)(tc::kSmemBytes)))) return rc;
         route_tc_kernel<<<(unsigned)std::min<int64_t>(tiles, ix->num_sms), tc::kThreads, tc::kSmemBytes, st>>>(
             mqh, mql, ix->map_chi, ix->map_clo, (g.d + tc::KindTf32x3::kBK - 1) / tc::KindTf32x3::kBK, rs, re,
             w.tc_err);
@@ -2146,20 +2161,17 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         const int tc_smem = tc::kSmemBytes + kEpiStageBytes;
         // A = queries of the tile (128 rows, box 128), B = cluster rows (256, box 256)
         if (sh.mode == LIDER_SCORE_BF16) {
-            LIDER_CUDA_TRY(cudaFuncSetAttribute(tc_score_kernel<tc::KindBf16>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem));
+            if ((rc = smem_attr((const void*)tc_score_kernel<tc::KindBf16>, (int)(tc_smem)))) return rc;
             tc_score_kernel<tc::KindBf16><<<ix->num_sms, tc::kThreads, tc_smem, st>>>(
                 mqh, mql, ix->map_xh16, ix->map_xh16, (g.d + tc::KindBf16::kBK - 1) / tc::KindBf16::kBK, ta,
                 w.tc_err);
         } else if (sh.mode == LIDER_SCORE_F16) {
-            LIDER_CUDA_TRY(cudaFuncSetAttribute(tc_score_kernel<tc::KindF16>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem));
+            if ((rc = smem_attr((const void*)tc_score_kernel<tc::KindF16>, (int)(tc_smem)))) return rc;
             tc_score_kernel<tc::KindF16><<<ix->num_sms, tc::kThreads, tc_smem, st>>>(
                 mqh, mql, ix->map_xh16, ix->map_xh16, (g.d + tc::KindF16::kBK - 1) / tc::KindF16::kBK, ta,
                 w.tc_err);
         } else {
-            LIDER_CUDA_TRY(cudaFuncSetAttribute(tc_score_kernel<tc::KindTf32x3>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem));
+            if ((rc = smem_attr((const void*)tc_score_kernel<tc::KindTf32x3>, (int)(tc_smem)))) return rc;
             tc_score_kernel<tc::KindTf32x3><<<ix->num_sms, tc::kThreads, tc_smem, st>>>(
                 mqh, mql, ix->map_xhi, ix->map_xlo, (g.d + tc::KindTf32x3::kBK - 1) / tc::KindTf32x3::kBK, ta,
                 w.tc_err);
@@ -2221,7 +2233,7 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
             case 8: kern = (const void*)score_group_kernel<8>; break;
             default: kern = (const void*)score_group_kernel<0>; break;
         }
-        LIDER_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if ((rc = smem_attr((const void*)kern, (int)smem))) return rc;
         int per_sm = 0;
         LIDER_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kScoreThreads, smem));
         if (per_sm < 1) return fail(LIDER_ELIMIT, "lider_search: score kernel does not fit on an SM");
@@ -2239,7 +2251,7 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         LIDER_LAUNCH_CHECK("merge_kernel");
     } else {
         const size_t rs_smem = align_up((size_t)g.d * 4, 16) + (size_t)next_pow2(sh.so) * 8;
-        LIDER_CUDA_TRY(cudaFuncSetAttribute(rescore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem));
+        if ((rc = smem_attr((const void*)rescore_kernel, (int)rs_smem))) return rc;
         rescore_kernel<<<(unsigned)nq, 256, rs_smem, st>>>(Q, g.X, g.row_of, g.d, sh.so, w.sl_ids, k, out_ids,
                                                            out_scores, g.n, &w.counters[CNT_BOUNDS]);
         LIDER_LAUNCH_CHECK("rescore_kernel");
@@ -2276,7 +2288,11 @@ int read_stats(const Workspace& w, int64_t nq, int c, lider_search_stats* stats,
 }
 
 int pool_alloc(const lider_index* ix, void** p, size_t bytes, cudaStream_t st) {
-    cudaError_t e = cudaMallocFromPoolAsync(p, bytes ? bytes : 256, ix->pool, st);
+    // under stream capture the scratch becomes a graph allocation node
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cap == cudaStreamCaptureStatusActive ? cudaMallocAsync(p, bytes ? bytes : 256, st)
+                                                        : cudaMallocFromPoolAsync(p, bytes ? bytes : 256, ix->pool, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(LIDER_ENOMEM, std::string("lider_search: scratch allocation of ") + std::to_string(bytes) +
