@@ -262,6 +262,11 @@ def run_lider(args, cfg):
     k, c, nq = cfg["k"], cfg["c"], cfg["nq"]
     ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
     sc = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    tuning = None
+    if not args.no_autotune:
+        # launch shapes picked by timing searches of this batch (outside the timed region)
+        tune, tune_ms = idx.autotune(Qd, k, c, reps=3)
+        tuning = dict(tune, ms_per_search=tune_ms)
     _, _, stats = idx.search(Qd, k, c, stats=True, out=(ids, sc))
     gpu_ids = ids.cpu().numpy()
 
@@ -389,6 +394,7 @@ def run_lider(args, cfg):
                 "d2h_bytes_per_step": int(nq * k * (8 + 4))},
         "gpu_launches": LAUNCHES_PER_SEARCH[args.score] * args.steps,
         "graph_replay": graph,
+        "tuning": tuning,
         "score_mode": args.score,
         "results": ("exact FP32 top-k of each query's candidate union (approximate tensor scores select with a "
                     "proven guard band, every listed id is re-scored in FP32; equal bit for bit across "
@@ -493,6 +499,7 @@ def main():
     ap.add_argument("--serve-mem-gb", type=int, default=16)
     ap.add_argument("--serve-wait-us", type=float, default=200.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-queries-per-step", type=int, default=8)
     ap.add_argument("--n", type=int, default=None, help="profiling size: first n corpus rows")

@@ -303,6 +303,34 @@ int lider_server_latencies(lider_server* server, double* out_ms, int64_t cap,
  * is accepted. */
 void lider_server_destroy(lider_server* server);
 
+/* ---------------------------------------------------------------------------
+ * Launch shapes of the tensor-path kernels (the paper has no counterpart).
+ * They change speed only: results are the same for every setting. */
+typedef struct {
+    int32_t select_threads;   /* per-query select block: 64, 128, 256 or 512           */
+    int32_t rescore_threads;  /* per-query re-score block: 64, 128, 256 or 512         */
+    int32_t mark_threads;     /* per-pair bitmap block: 32, 64, 128 or 256             */
+    int32_t tile_order;       /* tensor tiles of a cluster: 0 query tiles outer, 1 row
+                                 tiles outer (a row tile's query tiles run together)   */
+} lider_tuning;
+
+/* Current launch shapes of the index (host output). */
+int lider_get_tuning(const lider_index* index, lider_tuning* tuning);
+
+/* Set them; LIDER_EINVAL for a value outside the sets above.  Not thread-safe
+ * against searches running on the same index. */
+int lider_set_tuning(lider_index* index, const lider_tuning* tuning);
+
+/* Pick the launch shapes by measurement: starting from the current ones, each
+ * field in turn takes the value whose searches of `queries` (device, nq x d,
+ * with k and c) run fastest (median of `reps` timed searches after one
+ * warm-up, CUDA events on `stream`), two rounds.  Keeps the best in the index
+ * and returns it in *chosen (may be NULL) with its median time in *best_ms
+ * (may be NULL).  Synchronous.  Errors: those of lider_search; LIDER_EINVAL
+ * for reps < 1. */
+int lider_autotune(lider_index* index, const float* queries, int64_t nq, int32_t k, int32_t c,
+                   int32_t reps, lider_tuning* chosen, double* best_ms, void* stream);
+
 /* Index shape, host outputs (any may be NULL). */
 int lider_index_info(const lider_index* index, int64_t* n, int32_t* d,
                      int32_t* n_clusters, lider_params* params);

@@ -32,6 +32,8 @@ void destroy_index(lider_index*);
 int search_entry(const lider_index*, const float*, int64_t, int, int, int64_t*, float*, const lider_trace*,
                  lider_search_stats*, void*);
 int search_scratch_entry(const lider_index*, int64_t, int, int, size_t*);
+bool tuning_valid(const lider_tuning&);
+int autotune_entry(lider_index*, const float*, int64_t, int, int, int, lider_tuning*, double*, void*);
 int server_create_entry(const lider_index*, const lider_server_params*, lider_server**);
 int server_submit_entry(lider_server*, const float*, int64_t, int32_t, int64_t*, float*, int64_t*);
 int server_wait_entry(lider_server*, int64_t, double);
@@ -117,6 +119,24 @@ void lider_server_destroy(lider_server* server) {
         server_destroy_entry(server);
     } catch (...) {
     }
+}
+
+int lider_get_tuning(const lider_index* index, lider_tuning* tuning) {
+    if (!index || !tuning) return fail(LIDER_EINVAL, "lider_get_tuning: NULL argument");
+    *tuning = index->tune;
+    return LIDER_OK;
+}
+
+int lider_set_tuning(lider_index* index, const lider_tuning* tuning) {
+    if (!index || !tuning) return fail(LIDER_EINVAL, "lider_set_tuning: NULL argument");
+    if (!tuning_valid(*tuning)) return fail(LIDER_EINVAL, "lider_set_tuning: a value is outside its allowed set");
+    index->tune = *tuning;
+    return LIDER_OK;
+}
+
+int lider_autotune(lider_index* index, const float* queries, int64_t nq, int32_t k, int32_t c, int32_t reps,
+                   lider_tuning* chosen, double* best_ms, void* stream) {
+    return guarded([&] { return autotune_entry(index, queries, nq, k, c, reps, chosen, best_ms, stream); });
 }
 
 int lider_index_info(const lider_index* index, int64_t* n, int32_t* d, int32_t* n_clusters, lider_params* params) {

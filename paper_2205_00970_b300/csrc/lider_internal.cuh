@@ -107,6 +107,7 @@ struct lider_index {
     CUtensorMap map_xhi;        // TMA maps over X_hi / X_lo, boxes of 32 x 256
     CUtensorMap map_xlo;
     cudaMemPool_t pool = nullptr;
+    lider_tuning tune{128, 128, 64, 1};    // launch shapes (lider_autotune; defaults measured on mid)
     int score_blocks_per_sm = 1;
     int num_sms = 148;
 };

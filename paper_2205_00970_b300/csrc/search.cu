@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <vector>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -1031,13 +1032,12 @@ __global__ void qgather_bf16_kernel(const float* __restrict__ Q, const int32_t* 
 }
 
 constexpr int kMarkSmemWords = 8192;   // clusters up to 262,144 points mark in shared memory
-constexpr int kMarkThreads = 128;
 
 // One block per pair slot (pairs in cluster order): the union of the pair's L
 // expansion windows as a bitmap over the cluster's positions, at
 // bitmap + bm_off[j] + (slot - off[j]) * words_j; also slot_of[pair] = slot
 // and ucount[pair] = the number of candidates (set bits).
-__global__ void __launch_bounds__(kMarkThreads) mark_kernel(const int32_t* __restrict__ pairs,
+__global__ void __launch_bounds__(256) mark_kernel(const int32_t* __restrict__ pairs,
                                                    const int32_t* __restrict__ route, const int32_t* __restrict__ off,
                                                    const int64_t* __restrict__ cl_off,
                                                    const int64_t* __restrict__ bm_off,
@@ -1089,7 +1089,7 @@ __global__ void __launch_bounds__(kMarkThreads) mark_kernel(const int32_t* __res
 // cluster, and (query tile << 16 | row tile).  Written once per search so the
 // producer, MMA and epilogue warps each read a tile's coordinates with one load.
 __global__ void tc_units_kernel(const int32_t* __restrict__ unit_off, const int32_t* __restrict__ off,
-                                const int64_t* __restrict__ cl_off, int ncl, int4* __restrict__ units) {
+                                const int64_t* __restrict__ cl_off, int ncl, int order, int4* __restrict__ units) {
     const int j = blockIdx.x;
     const int64_t n_c = cl_off[j + 1] - cl_off[j];
     const int u0 = unit_off[j], u1 = unit_off[j + 1];
@@ -1097,7 +1097,10 @@ __global__ void tc_units_kernel(const int32_t* __restrict__ unit_off, const int3
     const int nrt = (int)((n_c + tc::kBN - 1) / tc::kBN);
     for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
         const int local = u - u0;
-        const int it = local / nrt, rt = local - it * nrt;
+        // order 0: query tiles outer; 1: row tiles outer
+        const int nit = (u1 - u0) / nrt;
+        const int it = order ? local % nit : local / nrt;
+        const int rt = order ? local / nit : local % nrt;
         units[u] = make_int4(off[j] + it * tc::kBM, (int)(cl_off[j] + (int64_t)rt * tc::kBN), j, (it << 16) | rt);
     }
 }
@@ -1198,7 +1201,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
 // path's arithmetic, the list re-sorted (score descending, id ascending) and
 // the best k kept.  One block per query; a list holds its entries first, then
 // -1s (S slots).
-__global__ void __launch_bounds__(256) rescore_kernel(const float* __restrict__ Q, const float* __restrict__ X,
+__global__ void __launch_bounds__(512) rescore_kernel(const float* __restrict__ Q, const float* __restrict__ X,
                                                       const int32_t* __restrict__ row_of, int d, int S,
                                                       const int64_t* in_ids, int k, int64_t* out_ids,
                                                       float* out_scores, int64_t n,
@@ -1539,7 +1542,7 @@ __device__ void block_bitonic32(uint32_t* key, int n) {
     }
 }
 
-__global__ void __launch_bounds__(256) select_hist_kernel(
+__global__ void __launch_bounds__(512) select_hist_kernel(
         DenseArgs da, int c, int ks, const float* __restrict__ qguard, const float* __restrict__ qbound, int guarded,
         int so, int64_t* __restrict__ out_ids, float* __restrict__ out_scores, int32_t* __restrict__ trace_ucount,
         int32_t* __restrict__ redo, int32_t* __restrict__ redo_count, unsigned long long* counters) {
@@ -2141,12 +2144,12 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         // bitmaps of clusters up to kMarkSmemWords words are built in shared memory
         const int max_words = g.max_row_tiles * (tc::kBN / 32);
         const int mark_words = max_words <= kMarkSmemWords ? max_words : 0;
-        mark_kernel<<<(unsigned)np, kMarkThreads, (size_t)mark_words * 4, st>>>(
+        mark_kernel<<<(unsigned)np, (unsigned)ix->tune.mark_threads, (size_t)mark_words * 4, st>>>(
             w.pairs, w.route, w.off, g.cl_off, w.bm_off, w.wstart, g.pos, g.n, g.L, R, w.bitmap, w.slot_of, w.pcount,
             mark_words);
         LIDER_LAUNCH_CHECK("mark_kernel");
         if ((rc = mark(LIDER_PHASE_SCORE))) return rc;
-        tc_units_kernel<<<g.ncl, 128, 0, st>>>(w.unit_off, w.off, g.cl_off, g.ncl, w.units);
+        tc_units_kernel<<<g.ncl, 128, 0, st>>>(w.unit_off, w.off, g.cl_off, g.ncl, ix->tune.tile_order, w.units);
         LIDER_LAUNCH_CHECK("tc_units_kernel");
         TcArgs ta;
         ta.units = w.units;
@@ -2191,7 +2194,7 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         da.cl_off = g.cl_off;
         da.orig_id = g.orig_id;
         da.ucount = w.pcount;
-        select_hist_kernel<<<(unsigned)nq, 256, 0, st>>>(da, c, sh.ks, w.qguard, w.qbound, guarded, sh.so, w.sl_ids,
+        select_hist_kernel<<<(unsigned)nq, (unsigned)ix->tune.select_threads, 0, st>>>(da, c, sh.ks, w.qguard, w.qbound, guarded, sh.so, w.sl_ids,
                                                          w.sl_scores, tr ? tr->ucount : nullptr, w.redo, w.redo_count,
                                                          w.counters);
         LIDER_LAUNCH_CHECK("select_hist_kernel");
@@ -2252,7 +2255,7 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
     } else {
         const size_t rs_smem = align_up((size_t)g.d * 4, 16) + (size_t)next_pow2(sh.so) * 8;
         if ((rc = smem_attr((const void*)rescore_kernel, (int)rs_smem))) return rc;
-        rescore_kernel<<<(unsigned)nq, 256, rs_smem, st>>>(Q, g.X, g.row_of, g.d, sh.so, w.sl_ids, k, out_ids,
+        rescore_kernel<<<(unsigned)nq, (unsigned)ix->tune.rescore_threads, rs_smem, st>>>(Q, g.X, g.row_of, g.d, sh.so, w.sl_ids, k, out_ids,
                                                            out_scores, g.n, &w.counters[CNT_BOUNDS]);
         LIDER_LAUNCH_CHECK("rescore_kernel");
     }
@@ -2327,6 +2330,94 @@ int search_scratch_entry(const lider_index* ix, int64_t nq, int k, int c, size_t
     int rc = check_search_args(ix, nullptr, nq, k, c, nullptr, nullptr, false);
     if (rc) return rc;
     if (nq > 0) *bytes = carve(nullptr, ix->g, nq, c, search_shape(ix, k, nq, c)).total;
+    return LIDER_OK;
+}
+
+bool tuning_valid(const lider_tuning& t) {
+    auto in = [](int v, std::initializer_list<int> set) {
+        for (int x : set)
+            if (v == x) return true;
+        return false;
+    };
+    return in(t.select_threads, {64, 128, 256, 512}) && in(t.rescore_threads, {64, 128, 256, 512}) &&
+           in(t.mark_threads, {32, 64, 128, 256}) && in(t.tile_order, {0, 1});
+}
+
+// Coordinate descent over the launch shapes, timing whole searches.
+int autotune_entry(lider_index* ix, const float* Q, int64_t nq, int k, int c, int reps, lider_tuning* chosen,
+                   double* best_ms, void* stream) {
+    if (!ix) return fail(LIDER_EINVAL, "lider_autotune: index is NULL");
+    if (reps < 1) return fail(LIDER_EINVAL, "lider_autotune: reps must be >= 1");
+    if (nq < 1) return fail(LIDER_EINVAL, "lider_autotune: nq must be >= 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t* ids = nullptr;
+    float* sc = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = LIDER_OK;
+    const lider_tuning start = ix->tune;
+    auto cleanup = [&] {
+        if (ids) cudaFree(ids);
+        if (sc) cudaFree(sc);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    cudaError_t e = cudaMalloc(&ids, (size_t)nq * k * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&sc, (size_t)nq * k * sizeof(float));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "lider_autotune: setup");
+    }
+    auto time_it = [&](const lider_tuning& t, double* ms) -> int {
+        ix->tune = t;
+        int r = search_entry(ix, Q, nq, k, c, ids, sc, nullptr, nullptr, st);
+        if (r) return r;
+        std::vector<float> v(reps);
+        for (int i = 0; i < reps; ++i) {
+            LIDER_CUDA_TRY(cudaEventRecord(e0, st));
+            if ((r = search_entry(ix, Q, nq, k, c, ids, sc, nullptr, nullptr, st))) return r;
+            LIDER_CUDA_TRY(cudaEventRecord(e1, st));
+            LIDER_CUDA_TRY(cudaEventSynchronize(e1));
+            LIDER_CUDA_TRY(cudaEventElapsedTime(&v[i], e0, e1));
+        }
+        std::sort(v.begin(), v.end());
+        *ms = v[reps / 2];
+        return LIDER_OK;
+    };
+    lider_tuning best = start;
+    double best_t = 0;
+    if ((rc = time_it(best, &best_t))) {
+        ix->tune = start;
+        cleanup();
+        return rc;
+    }
+    static const int sel_v[] = {64, 128, 256, 512}, res_v[] = {64, 128, 256, 512}, mark_v[] = {32, 64, 128, 256},
+                     ord_v[] = {0, 1};
+    for (int round = 0; round < 2 && rc == LIDER_OK; ++round) {
+        for (int f = 0; f < 4 && rc == LIDER_OK; ++f) {
+            const int* vals = f == 0 ? sel_v : f == 1 ? res_v : f == 2 ? mark_v : ord_v;
+            const int nv = f == 3 ? 2 : 4;
+            for (int i = 0; i < nv && rc == LIDER_OK; ++i) {
+                lider_tuning cand = best;
+                int* field = f == 0 ? &cand.select_threads : f == 1 ? &cand.rescore_threads
+                                                           : f == 2 ? &cand.mark_threads : &cand.tile_order;
+                if (*field == vals[i]) continue;
+                *field = vals[i];
+                double t = 0;
+                rc = time_it(cand, &t);
+                if (rc == LIDER_OK && t < best_t) {
+                    best = cand;
+                    best_t = t;
+                }
+            }
+        }
+    }
+    ix->tune = rc == LIDER_OK ? best : start;
+    cleanup();
+    if (rc) return rc;
+    if (chosen) *chosen = best;
+    if (best_ms) *best_ms = best_t;
     return LIDER_OK;
 }
 

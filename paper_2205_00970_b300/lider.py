@@ -52,6 +52,14 @@ class Trace(ctypes.Structure):
                 ("wstart", ctypes.c_void_p), ("wlen", ctypes.c_void_p), ("ucount", ctypes.c_void_p),
                 ("events", ctypes.POINTER(ctypes.c_void_p))]
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("select_threads", ctypes.c_int32), ("rescore_threads", ctypes.c_int32),
+                ("mark_threads", ctypes.c_int32), ("tile_order", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
 class ServerParams(ctypes.Structure):
     _fields_ = [("c", ctypes.c_int32), ("slots", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("max_k", ctypes.c_int32), ("mem_budget", ctypes.c_int64), ("max_wait_us", ctypes.c_double)]
@@ -85,6 +93,10 @@ def _load():
         "lider_search_host": ([P, P, I64, I32, I32, P, P, ctypes.POINTER(Stats), P], ctypes.c_int),
         "lider_search_noalloc": ([P, P, I64, I32, I32, P, P, ctypes.POINTER(Stats), P], ctypes.c_int),
         "lider_search_scratch_bytes": ([P, I64, I32, I32, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+        "lider_get_tuning": ([P, ctypes.POINTER(Tuning)], ctypes.c_int),
+        "lider_set_tuning": ([P, ctypes.POINTER(Tuning)], ctypes.c_int),
+        "lider_autotune": ([P, P, I64, I32, I32, I32, ctypes.POINTER(Tuning), ctypes.POINTER(ctypes.c_double), P],
+                           ctypes.c_int),
         "lider_index_info": ([P, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I32),
                               ctypes.POINTER(Params)], ctypes.c_int),
         "lider_cluster_offsets": ([P, P], ctypes.c_int),
@@ -113,6 +125,7 @@ _lib = _load()
 def exported_symbols() -> list[str]:
     return [n for n in ("lider_build", "lider_search", "lider_search_trace", "lider_search_host",
                         "lider_search_noalloc", "lider_search_scratch_bytes", "lider_debug_tc_tile",
+                        "lider_get_tuning", "lider_set_tuning", "lider_autotune",
                         "lider_index_info", "lider_cluster_offsets", "lider_export_array",
                         "lider_export_rmi", "lider_server_create", "lider_server_submit", "lider_server_wait",
                         "lider_server_stats", "lider_server_latencies", "lider_server_destroy",
@@ -238,6 +251,26 @@ class Index:
         _check(_lib.lider_search_host(self._h, Q.data_ptr(), nq, k, c, ids.data_ptr(), scores.data_ptr(),
                                       ctypes.byref(st) if stats else None, _stream_ptr(stream)))
         return (ids, scores, st.as_dict()) if stats else (ids, scores)
+
+    def tuning(self) -> dict:
+        t = Tuning()
+        _check(_lib.lider_get_tuning(self._h, ctypes.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, **fields):
+        cur = self.tuning()
+        cur.update(fields)
+        _check(_lib.lider_set_tuning(self._h, ctypes.byref(Tuning(**cur))))
+
+    def autotune(self, Q: torch.Tensor, k: int, c: int, reps: int = 5, stream=None):
+        """Pick the kernels' launch shapes by timing searches of Q; returns
+        (tuning dict, median ms of one search with it)."""
+        Q = _dev(Q, torch.float32, "queries")
+        t = Tuning()
+        ms = ctypes.c_double()
+        _check(_lib.lider_autotune(self._h, Q.data_ptr(), Q.shape[0], k, c, reps, ctypes.byref(t), ctypes.byref(ms),
+                                   _stream_ptr(stream)))
+        return t.as_dict(), ms.value
 
     def search_bytes(self, nq: int, k: int, c: int) -> int:
         """Device scratch one search of nq queries takes from the index's pool."""

@@ -65,3 +65,12 @@ def test_binding_loads_and_validates_without_gpu():
     rc = lider.raw_call("lider_build", dummy, 10, 8, dummy, 2, dummy, dummy,
                         ctypes.byref(lider.Params(17, 8, 16, 2, 1, 0, 1.0, 0, 0)), None, ctypes.byref(out))
     assert rc == -4 and "L <= 16" in lider.last_error()
+
+
+def test_tuning_abi_validates_without_gpu():
+    import ctypes
+    from paper_2205_00970_b300 import lider
+    t = lider.Tuning(256, 256, 128, 1)
+    assert lider.raw_call("lider_set_tuning", None, ctypes.byref(t)) == -1
+    assert lider.raw_call("lider_get_tuning", None, ctypes.byref(t)) == -1
+    assert lider.raw_call("lider_autotune", None, None, 1, 10, 1, 1, None, None, None) == -1
