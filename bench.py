@@ -48,7 +48,8 @@ DTYPES = {"tensor": "f32", "simt": "f32", "bf16": "bf16", "f16": "f16"}
 def workload_desc(cfg) -> dict:
     return {
         "workload": (f"{cfg['name']}: corpus {cfg['n']:,} x {cfg['d']} FP32 ({cfg['n_comp']:,}-component "
-                     f"Gaussian mixture, sigma {cfg['sigma']}, L2-normalised), {cfg['nq']:,} queries; "
+                     f"Gaussian mixture{', Zipf(%s) component sizes' % cfg['zipf_s'] if cfg['zipf_s'] else ''}, "
+                     f"sigma {cfg['sigma']}, L2-normalised), {cfg['nq']:,} queries; "
                      f"{cfg['n_clusters']} k-means clusters, c={cfg['c']}; L={cfg['L']}, m={cfg['m']}, "
                      f"W={cfg['W']}; RMI {cfg['leaves']} leaves; k={cfg['k']}, R=r0*k={cfg['R']}; seed {cfg['seed']}"),
         "nq_per_step": cfg["nq"],
@@ -262,21 +263,35 @@ def run_lider(args, cfg):
     k, c, nq = cfg["k"], cfg["c"], cfg["nq"]
     ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
     sc = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    # a step searches the whole batch, in lider_search calls of at most
+    # --sub-batch queries (the per-call scratch grows with the batch)
+    sub = args.sub_batch or nq
+    chunks = [(lo, min(nq, lo + sub)) for lo in range(0, nq, sub)]
+
+    def search_all(stream=None):
+        for lo, hi in chunks:
+            idx.search(Qd[lo:hi], k, c, out=(ids[lo:hi], sc[lo:hi]), stream=stream)
+
     tuning = None
     if not args.no_autotune:
-        # launch shapes picked by timing searches of this batch (outside the timed region)
-        tune, tune_ms = idx.autotune(Qd, k, c, reps=3)
-        tuning = dict(tune, ms_per_search=tune_ms)
-    _, _, stats = idx.search(Qd, k, c, stats=True, out=(ids, sc))
+        # launch shapes picked by timing searches of the first call's queries (outside the timed region)
+        lo, hi = chunks[0]
+        tune, tune_ms = idx.autotune(Qd[lo:hi], k, c, reps=3)
+        tuning = dict(tune, ms_per_search=tune_ms, queries_per_call=hi - lo)
+    stats = None
+    for lo, hi in chunks:
+        _, _, st = idx.search(Qd[lo:hi], k, c, stats=True, out=(ids[lo:hi], sc[lo:hi]))
+        stats = st if stats is None else {key: stats[key] + st[key] for key in stats}
     gpu_ids = ids.cpu().numpy()
 
     for _ in range(args.warmup):
-        idx.search(Qd, k, c, out=(ids, sc))
+        search_all()
     nph = lider.NUM_PHASES + 1
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nph)] for _ in range(args.steps)]
-    for row in evs:
-        for e in row:
-            e.record()
+    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(nph)] for _ in chunks] for _ in range(args.steps)]
+    for step in evs:
+        for row in step:
+            for e in row:
+                e.record()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     if world > 1:
@@ -286,15 +301,17 @@ def run_lider(args, cfg):
     time.sleep(0.3)
     t0.record()
     for s in range(args.steps):
-        idx.search_phased(Qd, k, c, evs[s], out=(ids, sc))
+        for ci, (lo, hi) in enumerate(chunks):
+            idx.search_phased(Qd[lo:hi], k, c, evs[s][ci], out=(ids[lo:hi], sc[lo:hi]))
     t1.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
     total_ms = t0.elapsed_time(t1)
-    step_ms = [evs[s][0].elapsed_time(evs[s][nph - 1]) for s in range(args.steps)]
-    phase_ms = {name: float(np.mean([evs[s][i].elapsed_time(evs[s][i + 1]) for s in range(args.steps)]))
+    step_ms = [evs[s][0][0].elapsed_time(evs[s][-1][nph - 1]) for s in range(args.steps)]
+    phase_ms = {name: float(np.mean([sum(evs[s][ci][i].elapsed_time(evs[s][ci][i + 1]) for ci in range(len(chunks)))
+                                     for s in range(args.steps)]))
                 for i, name in enumerate(lider.PHASES)}
     if world > 1:
         tt = torch.tensor([total_ms], device=dev)
@@ -308,7 +325,7 @@ def run_lider(args, cfg):
         gs = torch.cuda.Stream()
         cg = torch.cuda.CUDAGraph()
         with torch.cuda.graph(cg, stream=gs):
-            idx.search(Qd, k, c, out=(ids, sc), stream=gs)
+            search_all(stream=gs)
         for _ in range(args.warmup):
             cg.replay()
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -329,13 +346,17 @@ def run_lider(args, cfg):
     Qh = torch.from_numpy(Q).pin_memory()
     ids_h = torch.empty((nq, k), dtype=torch.int64).pin_memory()
     sc_h = torch.empty((nq, k), dtype=torch.float32).pin_memory()
+    def search_host_all():
+        for lo, hi in chunks:
+            idx.search_host(Qh[lo:hi], k, c, ids_h[lo:hi], sc_h[lo:hi])
+
     for _ in range(max(1, args.warmup // 2)):
-        idx.search_host(Qh, k, c, ids_h, sc_h)
+        search_host_all()
     if world > 1:
         dist.barrier()
     te = time.perf_counter()
     for _ in range(args.steps):
-        idx.search_host(Qh, k, c, ids_h, sc_h)
+        search_host_all()
     e2e_s = time.perf_counter() - te
     if world > 1:
         tt = torch.tensor([e2e_s], device=dev)
@@ -489,7 +510,8 @@ def main():
     ap.add_argument("--score", choices=list(MODES), default="f16",
                     help="f16 (default), tensor (3xTF32) and simt give the same exact top-k; bf16 is the served "
                          "shortlist form")
-    ap.add_argument("--rerank", type=int, default=2, help="served BF16 form: shortlist = rerank * k")
+    ap.add_argument("--rerank", type=int, default=None,
+                    help="served BF16 form: shortlist = rerank * k (default 2; precision workload: 40)")
     ap.add_argument("--serve", type=float, default=None,
                     help="serving mode: offered load in queries/s (Poisson arrivals)")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -504,6 +526,8 @@ def main():
     ap.add_argument("--ref-queries-per-step", type=int, default=8)
     ap.add_argument("--n", type=int, default=None, help="profiling size: first n corpus rows")
     ap.add_argument("--nq", type=int, default=None, help="profiling size: first nq queries")
+    ap.add_argument("--sub-batch", type=int, default=None,
+                    help="queries per lider_search call (default: the whole batch; batched/precision: 6,250)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -512,6 +536,10 @@ def main():
         cfg["n"] = min(cfg["n"], args.n)
     if args.nq:
         cfg["nq"] = min(cfg["nq"], args.nq)
+    if args.rerank is None:
+        args.rerank = cfg.get("rerank", 2)
+    if args.sub_batch is None and cfg["name"] in ("batched", "precision"):
+        args.sub_batch = 6250
     if args.impl == "reference":
         return run_reference(args, cfg)
     if args.serve:

@@ -18,6 +18,16 @@ CONFIGS = {
     "mid": dict(n=1_000_000, d=768, n_comp=1_024, sigma=0.3, zipf_s=None, nq=10_000,
                 n_clusters=256, c=8, L=8, m=16, W=1.0, leaves=1_024, k=100, r0=3,
                 B=1, kmeans_iters=10, kmeans_sample=65_536, seed=0),
+    # Batched uneven: 8.8M x 768 with Zipf(1.1) component sizes (so uneven
+    # clusters), 1,024 clusters, c=16, 50,000 queries, k=100.
+    "batched": dict(n=8_800_000, d=768, n_comp=1_024, sigma=0.3, zipf_s=1.1, nq=50_000,
+                    n_clusters=1_024, c=16, L=8, m=16, W=1.0, leaves=1_024, k=100, r0=3,
+                    B=1, kmeans_iters=10, kmeans_sample=131_072, seed=0),
+    # Precision: 21M x 768, same generator, 100,000 queries; the served forms
+    # keep a shortlist of 4,000 (rerank 40 at k=100) re-ranked in FP32.
+    "precision": dict(n=21_000_000, d=768, n_comp=1_024, sigma=0.3, zipf_s=1.1, nq=100_000,
+                      n_clusters=1_024, c=16, L=8, m=16, W=1.0, leaves=1_024, k=100, r0=3,
+                      B=1, kmeans_iters=10, kmeans_sample=131_072, seed=0, rerank=40),
 }
 
 

@@ -6,7 +6,10 @@ k-means).  They are computed here by the FP64 oracle's Lloyd iterations
 seeded by ``synth.init_rows``, and stored as FP32 so that the CUDA path and the
 oracle build from the same clustering.
 
-usage: python tests/golden/make_centroids.py tiny mid
+usage: python tests/golden/make_centroids.py tiny mid batched precision
+
+(batched and precision share the generator, the seed and kmeans_sample, so
+their sample rows and centroids are identical.)
 """
 import os
 import sys
