@@ -40,9 +40,10 @@ from paper_2205_00970_b300 import configs, synth  # noqa: E402
 
 METRIC = "queries/s at fixed recall@10 vs FP64 oracle (plain vs served BF16); p50/p99 ms"
 # our kernels per lider_search (phase list in search.cu; confirmed by the ncu launch list)
-LAUNCHES_PER_SEARCH = {"tensor": 18, "simt": 10, "bf16": 18, "f16": 18}
-MODES = {"tensor": 0, "simt": 1, "bf16": 2, "f16": 3}
-DTYPES = {"tensor": "f32", "simt": "f32", "bf16": "bf16", "f16": "f16"}
+LAUNCHES_PER_SEARCH = {"tensor": 18, "simt": 10, "bf16": 18, "f16": 18, "fp8": 18}
+MODES = {"tensor": 0, "simt": 1, "bf16": 2, "f16": 3, "fp8": 4}
+DTYPES = {"tensor": "f32", "simt": "f32", "bf16": "bf16", "f16": "f16", "fp8": "fp8-e4m3"}
+FP8_PER_BF16 = 4.5 / 2.25     # nominal dense FP8 / BF16 tensor rate (B300)
 
 
 def workload_desc(cfg) -> dict:
@@ -371,12 +372,17 @@ def run_lider(args, cfg):
     score_s = phase_ms["score"] / 1e3
     hbm, bf16, bf16_sus, peak_kind = measured_peaks()
     src = "MEASURED_PEAKS.json" if peak_kind == "measured" else "fallback figures"
-    if args.score in ("tensor", "bf16", "f16"):
+    if args.score in ("tensor", "bf16", "f16", "fp8"):
         if args.score == "tensor":
             kpad = -(-d // 32) * 32
             tc_flop = stats["tc_tiles"] * 128 * 256 * kpad * 2.0 * 3   # three TF32 products per FP32 product
             peak = bf16 * TF32_PER_BF16
             psrc = f"{src}: bf16 burst {bf16} x {TF32_PER_BF16:.3f} (nominal TF32/BF16)"
+        elif args.score == "fp8":
+            kpad = -(-d // 128) * 128
+            tc_flop = stats["tc_tiles"] * 128 * 256 * kpad * 2.0       # one FP8 product
+            peak = bf16 * FP8_PER_BF16
+            psrc = f"{src}: bf16 burst {bf16} x {FP8_PER_BF16:.1f} (nominal FP8/BF16)"
         else:
             kpad = -(-d // 64) * 64
             tc_flop = stats["tc_tiles"] * 128 * 256 * kpad * 2.0       # one BF16 product
@@ -419,8 +425,8 @@ def run_lider(args, cfg):
         "score_mode": args.score,
         "results": ("exact FP32 top-k of each query's candidate union (approximate tensor scores select with a "
                     "proven guard band, every listed id is re-scored in FP32; equal bit for bit across "
-                    "f16/tensor/simt)") if args.score != "bf16" else
-                   f"served shortlist: BF16 scores, FP32 re-rank of the best {args.rerank} * k",
+                    "f16/tensor/simt)") if args.score not in ("bf16", "fp8") else
+                   f"served shortlist: {DTYPES[args.score]} scores, FP32 re-rank of the best {args.rerank} * k",
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

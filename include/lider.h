@@ -53,6 +53,10 @@ extern "C" {
 #define LIDER_SCORE_F16    3   /* tcgen05 tensor cores on FP16 copies of the corpus and
                                   queries (each scaled by a power of two), FP32
                                   accumulation, guard band, exact FP32 re-score      */
+#define LIDER_SCORE_FP8    4   /* served form: FP8 e4m3 corpus copy with one scale per
+                                  row (max|x|/448), queries likewise, FP32
+                                  accumulation, then an FP32 re-rank of a shortlist
+                                  of rerank * k (not exact); needs d % 16 == 0      */
 
 /* Implementation caps (checked; LIDER_ELIMIT beyond them). */
 #define LIDER_MAX_L        32      /* hashkey arrays per core model (H)     */
@@ -73,10 +77,10 @@ typedef struct lider_index lider_index;   /* opaque; owns its device memory */
  *        (Sec. 4.2); floor(64/m) * B must be <= 56;
  *   hash_kind = LIDER_HASH_PSTABLE;
  *   W  = p-stable bucket width (> 0);
- *   score_mode = LIDER_SCORE_TENSOR, LIDER_SCORE_SIMT, LIDER_SCORE_BF16 or
- *        LIDER_SCORE_F16 (tensor modes need L <= 16; BF16 and F16 need
- *        d % 8 == 0);
- *   rerank = shortlist factor of LIDER_SCORE_BF16: rerank * k candidates per
+ *   score_mode = LIDER_SCORE_TENSOR, LIDER_SCORE_SIMT, LIDER_SCORE_BF16,
+ *        LIDER_SCORE_F16 or LIDER_SCORE_FP8 (tensor modes need L <= 16; BF16
+ *        and F16 need d % 8 == 0, FP8 d % 16 == 0);
+ *   rerank = shortlist factor of LIDER_SCORE_BF16 / FP8: rerank * k candidates per
  *        query are re-scored in FP32 (0 means 4). */
 typedef struct {
     int32_t L;

@@ -308,7 +308,7 @@ void release(lider_index* ix) {
     if (!ix) return;
     void* bufs[] = {ix->X, ix->orig_id, ix->cl_off, ix->C, ix->half_norm, ix->A, ix->bproj,
                     ix->keys, ix->pos, ix->root, ix->leaf, ix->X_hi, ix->X_lo, ix->row_of, ix->X_h16, ix->C_hi, ix->C_lo,
-                    ix->A_hi, ix->A_lo, ix->a_norm};
+                    ix->A_hi, ix->A_lo, ix->a_norm, ix->X_f8, ix->x_rowscale};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (ix->pool) cudaMemPoolDestroy(ix->pool);
@@ -335,12 +335,14 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
     if (P->L > LIDER_MAX_L) return fail(LIDER_ELIMIT, "lider_build: L exceeds LIDER_MAX_L");
     if (P->rmi_leaves > (1 << 24)) return fail(LIDER_ELIMIT, "lider_build: rmi_leaves too large");
     if (P->score_mode != LIDER_SCORE_TENSOR && P->score_mode != LIDER_SCORE_SIMT && P->score_mode != LIDER_SCORE_BF16 &&
-        P->score_mode != LIDER_SCORE_F16)
+        P->score_mode != LIDER_SCORE_F16 && P->score_mode != LIDER_SCORE_FP8)
         return fail(LIDER_EINVAL, "lider_build: unknown score_mode");
     if (P->score_mode != LIDER_SCORE_SIMT && P->L > 16)
         return fail(LIDER_ELIMIT, "lider_build: tensor-core scoring supports L <= 16 (use LIDER_SCORE_SIMT)");
     if ((P->score_mode == LIDER_SCORE_BF16 || P->score_mode == LIDER_SCORE_F16) && d % 8 != 0)
         return fail(LIDER_EINVAL, "lider_build: 16-bit tensor-core scoring needs d % 8 == 0");
+    if (P->score_mode == LIDER_SCORE_FP8 && d % 16 != 0)
+        return fail(LIDER_EINVAL, "lider_build: FP8 tensor-core scoring needs d % 16 == 0");
     if (P->rerank < 0 || P->rerank > 64) return fail(LIDER_EINVAL, "lider_build: rerank must be in [0, 64]");
 
     int dev = 0;
@@ -490,6 +492,11 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
             if ((rc = launch_split_tf32(ix->X, n * d, ix->X_hi, ix->X_lo, st))) return rc;
             if ((rc = make_tensor_map(&ix->map_xhi, ix->X_hi, n, d, 256))) return rc;
             if ((rc = make_tensor_map(&ix->map_xlo, ix->X_lo, n, d, 256))) return rc;
+        } else if (P->score_mode == LIDER_SCORE_FP8) {
+            ALLOC(ix->X_f8, (size_t)n * d, "corpus FP8 copy");
+            ALLOC(ix->x_rowscale, (size_t)n * sizeof(float), "corpus FP8 row scales");
+            if ((rc = launch_to_f8_rows(ix->X, n, d, ix->x_rowscale, ix->X_f8, st))) return rc;
+            if ((rc = make_tensor_map8(&ix->map_xf8, ix->X_f8, n, d, 256))) return rc;
         } else if (P->score_mode == LIDER_SCORE_BF16) {
             ALLOC(ix->X_h16, (size_t)n * d * sizeof(uint16_t), "corpus BF16 copy");
             if ((rc = launch_to_bf16(ix->X, n * d, ix->X_h16, st))) return rc;

@@ -104,6 +104,9 @@ struct lider_index {
     CUtensorMap map_chi;        // TMA maps over C_hi / C_lo, boxes of 32 x 256
     CUtensorMap map_clo;
     CUtensorMap map_xh16;       // TMA map over X_h16, boxes of 64 x 256
+    uint8_t* X_f8 = nullptr;    // FP8 e4m3 copy of X, one scale per row (served FP8 form)
+    float* x_rowscale = nullptr;
+    CUtensorMap map_xf8;        // TMA map over X_f8, boxes of 128 x 256
     CUtensorMap map_xhi;        // TMA maps over X_hi / X_lo, boxes of 32 x 256
     CUtensorMap map_xlo;
     cudaMemPool_t pool = nullptr;
@@ -220,6 +223,8 @@ int launch_split_tf32(const float* x, int64_t n, float* hi, float* lo, cudaStrea
 int make_tensor_map(CUtensorMap* map, const void* base, int64_t rows, int d, int box_rows, bool bf16 = false);
 int launch_to_bf16(const float* x, int64_t n, uint16_t* out, cudaStream_t s);
 int launch_to_f16(const float* x, int64_t n, float scale, uint16_t* out, cudaStream_t s);
+int launch_to_f8_rows(const float* x, int64_t n, int d, float* scale, uint8_t* out, cudaStream_t s);
+int make_tensor_map8(CUtensorMap* map, const void* base, int64_t rows, int d, int box_rows);
 // Power of two s with s * amax in [2^13, 2^14) (1 for amax == 0): scaled
 // values stay in FP16's normal range with room below its maximum.
 float f16_scale_host(float amax);

@@ -31,6 +31,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "lider_internal.cuh"
 #include "tc.cuh"
@@ -288,7 +289,8 @@ __device__ __forceinline__ double warp_exact_score(const float* __restrict__ q, 
 
 // Guard formula of a score mode (see candidate_guard).
 inline int guard_mode(int score_mode) {
-    return score_mode == LIDER_SCORE_TENSOR ? 1 : score_mode == LIDER_SCORE_F16 ? 2 : 0;
+    return score_mode == LIDER_SCORE_TENSOR ? 1 : score_mode == LIDER_SCORE_F16 ? 2
+                                                : score_mode == LIDER_SCORE_FP8 ? 3 : 0;
 }
 
 // Power of two sq with sq * amax in [2^13, 2^14) (1 for amax == 0): the
@@ -321,6 +323,8 @@ __device__ void candidate_guard(int gmode, float qn, double sq, double eq, int d
         g = (double)kTcGuard * q * (double)xmax;
     } else if (gmode == 0) {
         g = 0x1p-6 * q * (double)xmax;        // BF16: only bounds the scores below
+    } else if (gmode == 3) {
+        g = 0.3 * q * (double)xmax;           // FP8: only bounds the scores below
     } else if (gmode == 2) {
         const double acc = (double)d * 0x1p-23;
         const double qs = sq * q;
@@ -328,7 +332,7 @@ __device__ void candidate_guard(int gmode, float qn, double sq, double eq, int d
         s = sq * (double)sx;
     }
     *qscale = (float)(gmode == 2 ? sq : 1.0);
-    *qguard = gmode == 0 ? 0.f : __double2float_ru(g * (1.0 + 0x1p-20));
+    *qguard = (gmode == 0 || gmode == 3) ? 0.f : __double2float_ru(g * (1.0 + 0x1p-20));
     // |approximate score| <= s |q| |x|max + its error (s = 1 unless FP16)
     *qbound = __double2float_ru((s * q * (double)xmax + g) * (1.0 + 0x1p-20));
 }
@@ -1019,6 +1023,24 @@ __global__ void qgather_f16_kernel(const float* __restrict__ Q, const int32_t* _
     for (int i = lane; i < d; i += 32) dst[i] = __half_as_ushort(__float2half_rn(src[i] * s));
 }
 
+// Served FP8 form: the queries in pair order as e4m3 with one scale per query
+// (max|q| / 448), recorded per slot for the epilogue.
+__global__ void qgather_f8_kernel(const float* __restrict__ Q, const int32_t* __restrict__ pairs, int64_t np, int c,
+                                  int d, float* __restrict__ slot_scale, uint8_t* __restrict__ qp) {
+    const int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (slot >= np) return;
+    const int64_t q = pairs[slot] / c;
+    const float* src = Q + q * d;
+    float amax = 0.f;
+    for (int i = lane; i < d; i += 32) amax = fmaxf(amax, fabsf(src[i]));
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    const float inv = amax > 0.f ? 448.f / amax : 1.f;
+    if (lane == 0) slot_scale[slot] = amax > 0.f ? amax / 448.f : 1.f;
+    uint8_t* dst = qp + slot * d;
+    for (int i = lane; i < d; i += 32) dst[i] = (uint8_t)__nv_cvt_float_to_fp8(src[i] * inv, __NV_SATFINITE, __NV_E4M3);
+}
+
 // Served form: the queries in pair order, rounded to BF16.
 __global__ void qgather_bf16_kernel(const float* __restrict__ Q, const int32_t* __restrict__ pairs, int64_t np, int c,
                                     int d, uint16_t* __restrict__ qp) {
@@ -1115,6 +1137,8 @@ struct TcArgs {
     const int64_t* bm_off;
     int ncl;
     float* dense;               // per pair: approximate scores over its cluster's positions
+    const float* slot_scale;    // FP8 form: per slot query scale (else null)
+    const float* col_scale;     // FP8 form: per corpus row scale, reordered rows
 };
 
 struct TcSched {
@@ -1142,6 +1166,9 @@ struct TcEpi {
     float* stage;               // this warp's 32 x kEpiPitch floats
     float* drow;                // this lane's dense row at the tile's first column (null: no pair)
     int ncols;                  // columns of the tile inside the row pitch (a multiple of 32)
+    float rs;                   // FP8 form: this row's query scale
+    const float* cs;            // FP8 form: row scales of the tile's corpus rows (null: unscaled)
+    int ncs;                    // rows of the tile inside the cluster
 
     __device__ void begin(int u, int row) {
         const int4 t = a->units[u];
@@ -1152,14 +1179,29 @@ struct TcEpi {
         const int p0 = rt * tc::kBN;
         ncols = (int)min((int64_t)tc::kBN, words * 32 - p0);
         drow = row < in_tile ? a->dense + (a->bm_off[j] + ((int64_t)it * tc::kBM + row) * words) * 32 + p0 : nullptr;
+        cs = nullptr;
+        if (a->slot_scale) {
+            rs = row < in_tile ? a->slot_scale[a->off[j] + it * tc::kBM + row] : 0.f;
+            cs = a->col_scale + a->cl_off[j] + p0;
+            ncs = (int)min((int64_t)tc::kBN, n_c - p0);
+        }
     }
 
     // Called by all 32 lanes of the warp (lane = accumulator row).
     __device__ void operator()(int, int, int col0, const uint32_t (&v)[32]) {
         if (col0 >= ncols) return;                           // the same in every lane (per tile)
         const int lane = threadIdx.x & 31;
+        if (cs) {
+            // FP8 form: score = acc * query scale * row scale (rows past the cluster: 0)
 #pragma unroll
-        for (int i = 0; i < 32; ++i) stage[lane * kEpiPitch + i] = __uint_as_float(v[i]);
+            for (int i = 0; i < 32; ++i) {
+                const float sc = col0 + i < ncs ? __ldg(cs + col0 + i) : 0.f;
+                stage[lane * kEpiPitch + i] = __uint_as_float(v[i]) * rs * sc;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) stage[lane * kEpiPitch + i] = __uint_as_float(v[i]);
+        }
         __syncwarp();
         const int sub = lane >> 3, c4 = (lane & 7) * 4;
 #pragma unroll
@@ -1894,6 +1936,7 @@ struct Workspace {
     float* qs_lo;
     float* qp_hi;               // tensor path: queries in pair order, TF32 head / tail
     float* qp_lo;
+    float* slot_scale;          // FP8 path: per pair slot, the query's scale
     int* tc_err;
     int ncl;
     size_t zero_bytes;   // counters + cnt, cleared at the start of a search
@@ -1917,7 +1960,7 @@ Shape search_shape(const lider_index* ix, int k, int64_t nq = 0, int c = 0) {
     // words of the c largest clusters
     sh.bitmap_words = (c > 0 && c <= ix->g.ncl) ? nq * ix->top_words[c] : 0;
     const int T_cap = ix->g.L * sh.R;
-    if (sh.mode == LIDER_SCORE_BF16) {
+    if (sh.mode == LIDER_SCORE_BF16 || sh.mode == LIDER_SCORE_FP8) {
         sh.ks = ix->params.rerank * k;
         sh.kp = std::min(sh.ks, T_cap);
         sh.so = sh.ks;
@@ -1955,9 +1998,10 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, const
     // tiles <= sum_j ceil(cnt_j/128) * ceil(n_c/256) <= (np/128 + ncl) * max_row_tiles
     w.units = tensor ? (int4*)take((size_t)((np + tc::kBM - 1) / tc::kBM + g.ncl) * (size_t)g.max_row_tiles * 16)
                      : nullptr;
-    const size_t qelem = (sh.mode == LIDER_SCORE_BF16 || sh.mode == LIDER_SCORE_F16) ? 2 : 4;
+    const size_t qelem = sh.mode == LIDER_SCORE_FP8 ? 1 : (sh.mode == LIDER_SCORE_BF16 || sh.mode == LIDER_SCORE_F16) ? 2 : 4;
     w.qp_hi = tensor ? (float*)take((size_t)np * g.d * qelem) : nullptr;
     w.qp_lo = sh.mode == LIDER_SCORE_TENSOR ? (float*)take((size_t)np * g.d * 4) : nullptr;
+    w.slot_scale = sh.mode == LIDER_SCORE_FP8 ? (float*)take((size_t)np * 4) : nullptr;
     w.qs_hi = tensor ? (float*)take((size_t)nq * g.d * 4) : nullptr;
     w.qs_lo = tensor ? (float*)take((size_t)nq * g.d * 4) : nullptr;
     w.off = (int32_t*)take((size_t)(g.ncl + 1) * 4);
@@ -1999,7 +2043,8 @@ int check_search_args(const lider_index* ix, const float* Q, int64_t nq, int k, 
     const int64_t R = (int64_t)ix->params.r0 * k;
     if (R * ix->g.L > LIDER_MAX_LR) return fail(LIDER_ELIMIT, "lider_search: L * r0 * k exceeds LIDER_MAX_LR");
     if (nq * c > (int64_t)INT32_MAX) return fail(LIDER_ELIMIT, "lider_search: nq * c exceeds 2^31-1");
-    if (ix->params.score_mode == LIDER_SCORE_BF16 && (int64_t)ix->params.rerank * k > 4096)
+    if ((ix->params.score_mode == LIDER_SCORE_BF16 || ix->params.score_mode == LIDER_SCORE_FP8) &&
+        (int64_t)ix->params.rerank * k > 4096)
         return fail(LIDER_ELIMIT, "lider_search: rerank * k exceeds 4096");
     if (ix->params.score_mode != LIDER_SCORE_SIMT && nq * ix->g.H > (int64_t)INT32_MAX)
         return fail(LIDER_ELIMIT, "lider_search: nq * L * m exceeds 2^31-1; search fewer queries per call");
@@ -2123,7 +2168,13 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
     if (sh.mode != LIDER_SCORE_SIMT) {
         const bool h16 = sh.mode == LIDER_SCORE_BF16 || sh.mode == LIDER_SCORE_F16;
         CUtensorMap mqh, mql;
-        if (h16) {
+        if (sh.mode == LIDER_SCORE_FP8) {
+            uint8_t* qp = reinterpret_cast<uint8_t*>(w.qp_hi);
+            qgather_f8_kernel<<<(unsigned)cdiv(np * 32, 256), 256, 0, st>>>(Q, w.pairs, np, c, g.d, w.slot_scale, qp);
+            LIDER_LAUNCH_CHECK("qgather_f8_kernel");
+            if ((rc = make_tensor_map8(&mqh, qp, np, g.d, tc::kBM))) return rc;
+            mql = mqh;
+        } else if (h16) {
             uint16_t* qp = reinterpret_cast<uint16_t*>(w.qp_hi);
             if (sh.mode == LIDER_SCORE_BF16) {
                 qgather_bf16_kernel<<<(unsigned)cdiv(np * 32, 256), 256, 0, st>>>(Q, w.pairs, np, c, g.d, qp);
@@ -2161,9 +2212,15 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         ta.bm_off = w.bm_off;
         ta.ncl = g.ncl;
         ta.dense = w.dense;
+        ta.slot_scale = sh.mode == LIDER_SCORE_FP8 ? w.slot_scale : nullptr;
+        ta.col_scale = ix->x_rowscale;
         const int tc_smem = tc::kSmemBytes + kEpiStageBytes;
         // A = queries of the tile (128 rows, box 128), B = cluster rows (256, box 256)
-        if (sh.mode == LIDER_SCORE_BF16) {
+        if (sh.mode == LIDER_SCORE_FP8) {
+            if ((rc = smem_attr((const void*)tc_score_kernel<tc::KindF8>, (int)(tc_smem)))) return rc;
+            tc_score_kernel<tc::KindF8><<<ix->num_sms, tc::kThreads, tc_smem, st>>>(
+                mqh, mql, ix->map_xf8, ix->map_xf8, (g.d + tc::KindF8::kBK - 1) / tc::KindF8::kBK, ta, w.tc_err);
+        } else if (sh.mode == LIDER_SCORE_BF16) {
             if ((rc = smem_attr((const void*)tc_score_kernel<tc::KindBf16>, (int)(tc_smem)))) return rc;
             tc_score_kernel<tc::KindBf16><<<ix->num_sms, tc::kThreads, tc_smem, st>>>(
                 mqh, mql, ix->map_xh16, ix->map_xh16, (g.d + tc::KindBf16::kBK - 1) / tc::KindBf16::kBK, ta,
@@ -2183,7 +2240,7 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         if ((rc = mark(LIDER_PHASE_SELECT))) return rc;
         // 3xTF32 and FP16 paths: a guard band makes the re-scored top k exact;
         // the served BF16 form keeps its approximate shortlist
-        const int guarded = sh.mode != LIDER_SCORE_BF16;
+        const int guarded = sh.mode != LIDER_SCORE_BF16 && sh.mode != LIDER_SCORE_FP8;
         DenseArgs da;
         da.dense = w.dense;
         da.bitmap = w.bitmap;

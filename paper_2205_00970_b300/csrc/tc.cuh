@@ -45,6 +45,7 @@ struct KindTf32x3 {
     static constexpr int kElemBytes = 4;
     static constexpr int kBK = kRowBytes / kElemBytes;   // 32 elements of K per stage
     static constexpr uint32_t kIdesc = idesc(2);
+    static constexpr bool kF8 = false;
 };
 
 struct KindBf16 {
@@ -53,6 +54,18 @@ struct KindBf16 {
     static constexpr int kElemBytes = 2;
     static constexpr int kBK = kRowBytes / kElemBytes;   // 64 elements of K per stage
     static constexpr uint32_t kIdesc = idesc(1);
+    static constexpr bool kF8 = false;
+};
+
+// FP8 e4m3 operands (kind::f8f6f4; a/b format code 0 = E4M3), 128 elements of
+// K per 128-byte row, 32 per MMA (32 bytes, as the 16-bit kinds).
+struct KindF8 {
+    static constexpr int kStages = 4;
+    static constexpr int kOps = 1;
+    static constexpr int kElemBytes = 1;
+    static constexpr int kBK = kRowBytes / kElemBytes;   // 128 elements of K per stage
+    static constexpr uint32_t kIdesc = idesc(0);
+    static constexpr bool kF8 = true;
 };
 
 struct KindF16 {
@@ -61,7 +74,13 @@ struct KindF16 {
     static constexpr int kElemBytes = 2;
     static constexpr int kBK = kRowBytes / kElemBytes;   // 64 elements of K per stage
     static constexpr uint32_t kIdesc = idesc(0);
+    static constexpr bool kF8 = false;
 };
+
+template <class Kind>
+__host__ __device__ constexpr bool is_f8() {
+    return Kind::kF8;
+}
 
 enum {
     TC_OK = 0,
@@ -148,6 +167,15 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
@@ -327,7 +355,8 @@ __device__ void gemm_tiles(const CUtensorMap* mAhi, const CUtensorMap* mAlo, con
                             mma_tf32(d, dal, dbh, Kind::kIdesc, 1u);
                         } else {
                             const uint64_t da = sdesc_sw128(sa + off), db = sdesc_sw128(sa + kTileA + off);
-                            mma_f16(d, da, db, Kind::kIdesc, acc);
+                            if constexpr (is_f8<Kind>()) mma_f8(d, da, db, Kind::kIdesc, acc);
+                            else mma_f16(d, da, db, Kind::kIdesc, acc);
                         }
                     }
                     mma_commit(&ctl.empty[s]);                 // stage reusable once these finish

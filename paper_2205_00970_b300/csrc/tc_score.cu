@@ -2,6 +2,7 @@
 // maps, and a one-tile self-test of the tcgen05 engine (tc.cuh).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 #include <cmath>
@@ -33,6 +34,31 @@ __global__ void to_f16_kernel(const float* __restrict__ x, int64_t n, float scal
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     out[i] = __half_as_ushort(__float2half_rn(x[i] * scale));
+}
+
+// FP8 e4m3 with one scale per row: s = max|x_row| / 448 (1 for a zero row),
+// out = e4m3(x / s) (nearest, saturating to the finite range), so x ~ s * out.
+// Warp per row.
+__global__ void to_f8_rows_kernel(const float* __restrict__ x, int64_t n, int d, float* __restrict__ scale,
+                                  uint8_t* __restrict__ out) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const float* xr = x + row * d;
+    float amax = 0.f;
+    for (int i = lane; i < d; i += 32) amax = fmaxf(amax, fabsf(xr[i]));
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    const float inv = amax > 0.f ? 448.f / amax : 1.f;
+    if (lane == 0) scale[row] = amax > 0.f ? amax / 448.f : 1.f;
+    for (int i = lane; i < d; i += 32)
+        out[row * d + i] = (uint8_t)__nv_cvt_float_to_fp8(xr[i] * inv, __NV_SATFINITE, __NV_E4M3);
+}
+
+// FP8 e4m3 without scaling (engine self-test).
+__global__ void to_f8_kernel(const float* __restrict__ x, int64_t n, uint8_t* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = (uint8_t)__nv_cvt_float_to_fp8(x[i], __NV_SATFINITE, __NV_E4M3);
 }
 
 // Round to BF16 (nearest, ties to even).
@@ -110,6 +136,13 @@ int launch_to_f16(const float* x, int64_t n, float scale, uint16_t* out, cudaStr
     return LIDER_OK;
 }
 
+int launch_to_f8_rows(const float* x, int64_t n, int d, float* scale, uint8_t* out, cudaStream_t st) {
+    if (n <= 0) return LIDER_OK;
+    to_f8_rows_kernel<<<(unsigned)cdiv(n * 32, 256), 256, 0, st>>>(x, n, d, scale, out);
+    LIDER_LAUNCH_CHECK("to_f8_rows_kernel");
+    return LIDER_OK;
+}
+
 float f16_scale_host(float amax) {
     if (!(amax > 0.f) || !std::isfinite(amax)) return 1.f;
     int e = 0;
@@ -127,6 +160,22 @@ int launch_split_tf32(const float* x, int64_t n, float* hi, float* lo, cudaStrea
 
 // 2-D tensor map over rows x d (row-major FP32, or BF16 when bf16), box of
 // one 128-byte row of K (32 FP32 / 64 BF16) x box_rows, 128-byte swizzle.
+// The same over 1-byte elements (FP8): box of one 128-byte row of K (128 elements).
+int make_tensor_map8(CUtensorMap* map, const void* base, int64_t rows, int d, int box_rows) {
+    EncodeTiledFn fn;
+    int rc = encode_fn(&fn);
+    if (rc) return rc;
+    const cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)d};
+    const cuuint32_t box[2] = {(cuuint32_t)tc::kRowBytes, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void*)base, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(LIDER_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return LIDER_OK;
+}
+
 int make_tensor_map(CUtensorMap* map, const void* base, int64_t rows, int d, int box_rows, bool bf16) {
     EncodeTiledFn fn;
     int rc = encode_fn(&fn);
@@ -153,9 +202,10 @@ extern "C" int lider_debug_tc_tile(const float* A, int32_t m, const float* B, in
     using namespace lider;
     try {
         if (!A || !B || !out) return fail(LIDER_EINVAL, "lider_debug_tc_tile: NULL pointer");
-        if (kind < 0 || kind > 2) return fail(LIDER_EINVAL, "lider_debug_tc_tile: kind must be 0, 1 or 2");
-        if (m < 1 || m > tc::kBM || n < 1 || n > tc::kBN || d < (kind ? 8 : 4) || d % (kind ? 8 : 4) != 0)
-            return fail(LIDER_EINVAL, "lider_debug_tc_tile: need 1<=m<=128, 1<=n<=256, d % 4 (BF16: 8) == 0");
+        if (kind < 0 || kind > 3) return fail(LIDER_EINVAL, "lider_debug_tc_tile: kind must be 0, 1, 2 or 3");
+        const int dmul = kind == 0 ? 4 : kind == 3 ? 16 : 8;
+        if (m < 1 || m > tc::kBM || n < 1 || n > tc::kBN || d < dmul || d % dmul != 0)
+            return fail(LIDER_EINVAL, "lider_debug_tc_tile: need 1<=m<=128, 1<=n<=256, d % 4 (16-bit: 8, FP8: 16) == 0");
         cudaStream_t st = (cudaStream_t)stream;
         float* buf = nullptr;
         const size_t na = (size_t)m * d, nb = (size_t)n * d;
@@ -172,6 +222,15 @@ extern "C" int lider_debug_tc_tile(const float* A, int32_t m, const float* B, in
                 if ((rc = make_tensor_map(&mal, alo, m, d, tc::kBM))) break;
                 if ((rc = make_tensor_map(&mbh, bhi, n, d, tc::kBN))) break;
                 if ((rc = make_tensor_map(&mbl, blo, n, d, tc::kBN))) break;
+            } else if (kind == 3) {
+                uint8_t* a8 = reinterpret_cast<uint8_t*>(ahi);
+                uint8_t* b8 = reinterpret_cast<uint8_t*>(bhi);
+                to_f8_kernel<<<(unsigned)cdiv((int64_t)na, 256), 256, 0, st>>>(A, (int64_t)na, a8);
+                to_f8_kernel<<<(unsigned)cdiv((int64_t)nb, 256), 256, 0, st>>>(B, (int64_t)nb, b8);
+                if ((rc = make_tensor_map8(&mah, a8, m, d, tc::kBM))) break;
+                if ((rc = make_tensor_map8(&mbh, b8, n, d, tc::kBN))) break;
+                mal = mah;
+                mbl = mbh;
             } else {
                 uint16_t* a16 = reinterpret_cast<uint16_t*>(ahi);
                 uint16_t* b16 = reinterpret_cast<uint16_t*>(bhi);
@@ -191,10 +250,11 @@ extern "C" int lider_debug_tc_tile(const float* A, int32_t m, const float* B, in
             if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemsetAsync"); break; }
             const void* kern = kind == 0   ? (const void*)tc_tile_test_kernel<tc::KindTf32x3>
                                : kind == 1 ? (const void*)tc_tile_test_kernel<tc::KindBf16>
-                                           : (const void*)tc_tile_test_kernel<tc::KindF16>;
+                               : kind == 2 ? (const void*)tc_tile_test_kernel<tc::KindF16>
+                                           : (const void*)tc_tile_test_kernel<tc::KindF8>;
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes);
             if (e != cudaSuccess) { rc = cuda_fail(e, "cudaFuncSetAttribute"); break; }
-            const int kbk = kind == 0 ? tc::KindTf32x3::kBK : tc::KindBf16::kBK;
+            const int kbk = kind == 0 ? tc::KindTf32x3::kBK : kind == 3 ? tc::KindF8::kBK : tc::KindBf16::kBK;
             int kchunks = (d + kbk - 1) / kbk;
             void* args[] = {&mah, &mal, &mbh, &mbl, &kchunks, &out, &m, &n, &err};
             e = cudaLaunchKernel(kern, dim3(1), dim3(tc::kThreads), args, tc::kSmemBytes, st);

@@ -29,7 +29,7 @@ class LiderError(RuntimeError):
         self.code = code
 
 
-SCORE_TENSOR, SCORE_SIMT, SCORE_BF16, SCORE_F16 = 0, 1, 2, 3
+SCORE_TENSOR, SCORE_SIMT, SCORE_BF16, SCORE_F16, SCORE_FP8 = 0, 1, 2, 3, 4
 
 
 class Params(ctypes.Structure):
@@ -305,7 +305,8 @@ class Index:
 
 def tc_tile(A: torch.Tensor, B: torch.Tensor, kind: int = 0, stream=None) -> torch.Tensor:
     """A . B^T through the tensor-core engine (self-test entry); kind 0:
-    three TF32 products, kind 1: BF16 operands, kind 2: FP16 operands."""
+    three TF32 products, kind 1: BF16 operands, kind 2: FP16 operands,
+    kind 3: FP8 e4m3 operands (d % 16 == 0)."""
     A = _dev(A, torch.float32, "A")
     B = _dev(B, torch.float32, "B")
     out = torch.empty((A.shape[0], B.shape[0]), dtype=torch.float32, device=A.device)

@@ -52,9 +52,10 @@ def test_binding_loads_and_validates_without_gpu():
         (10, 8, 2, lider.Params(4, 8, 16, 2, 8, 0, 1.0, 0, 0), "<= 56"),
         (10, 8, 2, lider.Params(4, 8, 16, 2, 1, 7, 1.0, 0, 0), "hash_kind"),
         (10, 8, 2, lider.Params(0, 8, 16, 2, 1, 0, 1.0, 0, 0), ">= 1"),
-        (10, 8, 2, lider.Params(4, 8, 16, 2, 1, 0, 1.0, 5, 0), "score_mode"),
+        (10, 8, 2, lider.Params(4, 8, 16, 2, 1, 0, 1.0, 7, 0), "score_mode"),
         (10, 12, 2, lider.Params(4, 8, 16, 2, 1, 0, 1.0, 2, 0), "d % 8"),
         (10, 8, 2, lider.Params(4, 8, 16, 2, 1, 0, 1.0, 2, 65), "rerank"),
+        (10, 8, 2, lider.Params(4, 8, 16, 2, 1, 0, 1.0, 4, 0), "d % 16"),
     ]:
         rc = lider.raw_call("lider_build", dummy, n, d, dummy, ncl, dummy, dummy, ctypes.byref(pp), None,
                             ctypes.byref(out))

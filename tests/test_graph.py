@@ -9,11 +9,11 @@ from tests import lider_fixtures as F
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2, 3], ids=["tensor", "simt", "bf16", "f16"])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4], ids=["tensor", "simt", "bf16", "f16", "fp8"])
 def test_search_replays_as_cuda_graph(mode):
     import torch
     cfg, X, Q, C, A, b = F.workload("tiny")
-    cfg = dict(cfg, score_mode=mode, rerank=2 if mode == 2 else 0)
+    cfg = dict(cfg, score_mode=mode, rerank=2 if mode in (2, 4) else 0)
     ix = F.gpu_index(cfg, X, C, A, b)
     nq, k, c = 256, cfg["k"], cfg["c"]
     Qbuf = torch.from_numpy(Q[:nq].copy()).cuda()

@@ -209,14 +209,15 @@ def test_invalid_search_arguments(tiny):
         assert e.value.code == code
 
 
-def test_served_bf16_form():
-    """Served form (BF16 scoring + FP32 re-rank of a shortlist of rerank * k):
-    every returned id is a candidate of its query, scores are the exact FP32
-    inner products, results are sorted, batch-invariant, and agree with the
-    plain top-k on almost every rank."""
+@pytest.mark.parametrize("mode,min_agree", [(2, 0.995), (4, 0.98)], ids=["bf16", "fp8"])
+def test_served_forms(mode, min_agree):
+    """Served forms (BF16 or FP8-e4m3 scoring + FP32 re-rank of a shortlist of
+    rerank * k): every returned id is a candidate of its query, scores are the
+    exact FP32 inner products, results are sorted, batch-invariant, and agree
+    with the plain top-k on almost every rank."""
     import torch
     cfg, X, Q, C, A, b = F.workload("tiny")
-    cfg["score_mode"] = 2
+    cfg["score_mode"] = mode
     cfg["rerank"] = 4
     g = F.gpu_index(cfg, X, C, A, b)
     Qd = torch.from_numpy(Q).cuda()
@@ -235,7 +236,7 @@ def test_served_bf16_form():
         assert np.all(np.diff(sc[i, :nv]) <= 0)
         agree += len(set(ids[i, :nv].tolist()) & set(ref.ids[i, :nv].tolist()))
     total = int(np.sum(ref.ids >= 0))
-    assert agree / total > 0.995, agree / total
+    assert agree / total > min_agree, agree / total
     sub_ids, sub_sc = g.search(Qd[37:291].contiguous(), cfg["k"], cfg["c"])
     assert np.array_equal(sub_ids.cpu().numpy(), ids[37:291])
 

@@ -43,7 +43,7 @@ def _poisson(Q, srv, rate, seconds, ks, max_req, seed):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4])
 def test_served_mix_equals_alone(mode):
     """Each request's ids and scores, served in a Poisson mix of requests of
     several sizes and two k on overlapping streams, are bit-identical to the
@@ -53,7 +53,7 @@ def test_served_mix_equals_alone(mode):
     from tests.lider_fixtures import gpu_index, workload
 
     cfg, X, Q, C, A, b = workload("tiny")
-    cfg = dict(cfg, score_mode=mode, rerank=2 if mode == 2 else 0)
+    cfg = dict(cfg, score_mode=mode, rerank=2 if mode in (2, 4) else 0)
     ix = gpu_index(cfg, X, C, A, b)
     srv = Server(ix, cfg["c"], slots=3, max_batch=512, max_k=20, mem_budget=256 << 20, max_wait_us=300)
     sent = _poisson(Q, srv, 300000, 0.5, (10, 20), 128, 7)

@@ -41,6 +41,25 @@ def test_tc_tile_f16_accumulation_error(m, n, d):
     assert np.max(err) < d * 2.0 ** -23 / 8, (float(np.max(err)), float(np.mean(err)))
 
 
+@pytest.mark.parametrize("m,n,d", [(128, 256, 768), (100, 200, 784), (5, 7, 64), (128, 256, 16)])
+def test_tc_tile_fp8_matches_fp64_of_rounded_inputs(m, n, d):
+    """FP8 e4m3 kind (kind::f8f6f4): the products of the e4m3-rounded inputs
+    (exact in FP32), accumulated in FP32."""
+    import torch
+    from paper_2205_00970_b300 import lider
+    rng = np.random.default_rng(m * 31 + n + d)
+    A = rng.standard_normal((m, d)).astype(np.float32)
+    B = rng.standard_normal((n, d)).astype(np.float32)
+    At, Bt = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    out = lider.tc_tile(At, Bt, kind=3).cpu().numpy().astype(np.float64)
+    A8 = At.to(torch.float8_e4m3fn).float().cpu().numpy().astype(np.float64)
+    B8 = Bt.to(torch.float8_e4m3fn).float().cpu().numpy().astype(np.float64)
+    ref = A8 @ B8.T
+    scale = np.abs(A8) @ np.abs(B8).T
+    err = np.abs(out - ref) / scale
+    assert np.max(err) < d * 2.0 ** -23 / 4, (float(np.max(err)), float(np.mean(err)))
+
+
 @pytest.mark.parametrize("m,n,d", [(128, 256, 768), (100, 200, 776), (5, 7, 64), (128, 256, 8)])
 def test_tc_tile_bf16_matches_fp64_of_rounded_inputs(m, n, d):
     """BF16 kind: the products of the BF16-rounded inputs, accumulated in FP32."""
