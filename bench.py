@@ -266,7 +266,7 @@ def run_lider(args, cfg):
     sc = torch.empty((nq, k), dtype=torch.float32, device=dev)
     # a step searches the whole batch, in lider_search calls of at most
     # --sub-batch queries (the per-call scratch grows with the batch)
-    sub = args.sub_batch or nq
+    sub = call_size(idx, nq, k, c, args.sub_batch or nq)
     chunks = [(lo, min(nq, lo + sub)) for lo in range(0, nq, sub)]
 
     def search_all(stream=None):
@@ -506,6 +506,95 @@ def run_serve(args, cfg):
     return 0
 
 
+def call_size(idx, nq, k, c, want):
+    """Largest queries-per-call up to `want` that the search's per-call caps
+    accept (halving from `want`)."""
+    from paper_2205_00970_b300 import lider
+    sub = max(1, min(nq, want))
+    while sub > 1:
+        try:
+            idx.search_bytes(sub, k, c)
+            return sub
+        except lider.LiderError:
+            sub //= 2
+    return sub
+
+
+def run_precision(args, cfg):
+    """Precision mode: the workload's corpus indexed once per dtype (the exact
+    FP16-guarded mode, the served BF16 and FP8-e4m3 forms with a shortlist of
+    rerank * k re-ranked in FP32), every query searched; reports per dtype the
+    queries/s, recall@10 against the exact mode, and, on a query sample
+    against FP64 brute force (the oracle's exact_knn), recall@10 and the
+    largest relative error of the returned scores."""
+    import torch
+
+    from oracle import lider_oracle as O
+    from paper_2205_00970_b300 import lider
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    X, Q, C, A, b = load_inputs(cfg)
+    k, c, nq = cfg["k"], cfg["c"], cfg["nq"]
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    Qd = t(Q)
+    out = {}
+    for name in ("f16", "bf16", "fp8"):
+        Xd = t(X)
+        idx = lider.Index(Xd, t(C), t(A), t(b), L=cfg["L"], m=cfg["m"], W=cfg["W"], rmi_leaves=cfg["leaves"],
+                          r0=cfg["r0"], B=cfg["B"], score_mode=MODES[name], rerank=args.rerank)
+        del Xd
+        torch.cuda.empty_cache()
+        sub = call_size(idx, nq, k, c, args.sub_batch or nq)
+        chunks = [(lo, min(nq, lo + sub)) for lo in range(0, nq, sub)]
+        ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
+        sc = torch.empty((nq, k), dtype=torch.float32, device=dev)
+        for lo, hi in chunks:                                   # warm-up
+            idx.search(Qd[lo:hi], k, c, out=(ids[lo:hi], sc[lo:hi]))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            for lo, hi in chunks:
+                idx.search(Qd[lo:hi], k, c, out=(ids[lo:hi], sc[lo:hi]))
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        out[name] = {"ids": ids.cpu().numpy(), "scores": sc.cpu().numpy(), "ms": ms, "sub": sub}
+        idx.free()
+        del idx, ids, sc
+        torch.cuda.empty_cache()
+    plain = out["f16"]["ids"][:, :10]
+    ns = min(args.precision_sample, nq)
+    truth = O.exact_knn(X, Q[:ns], 10)[0]
+    q64 = Q[:ns].astype(np.float64)
+    report = {}
+    for name, r in out.items():
+        top = r["ids"][:, :10]
+        agree = np.mean([len(set(top[i].tolist()) & set(plain[i].tolist())) / 10 for i in range(nq)])
+        err = 0.0
+        for i in range(ns):
+            sel = r["ids"][i][r["ids"][i] >= 0]
+            ex = X[sel].astype(np.float64) @ q64[i]
+            got = r["scores"][i][:len(sel)].astype(np.float64)
+            err = max(err, float(np.max(np.abs(got - ex) / np.maximum(np.abs(ex), 1e-30))) if len(sel) else 0.0)
+        report[name] = {
+            "queries_per_s": nq / (r["ms"] / 1e3), "ms_per_batch": r["ms"], "queries_per_call": r["sub"],
+            "storage": {"f16": "FP16 (power-of-two scaled), guarded, exact", "bf16": "BF16",
+                        "fp8": "FP8 e4m3, one scale per row (max|x|/448)"}[name],
+            "recall_at_10_vs_plain": float(agree),
+            "recall_at_10_vs_fp64_knn": O.recall_at(r["ids"][:ns], truth, 10),
+            "max_rel_score_error_vs_fp64": err,
+        }
+    line = {
+        "metric": "recall@10 and score error per dtype; queries/s", "n_gpus": 1, "steps": args.steps,
+        "data": "synthetic", "config": dict(workload_desc(cfg), shortlist=f"{args.rerank} * k"),
+        "sample": f"first {ns} queries against FP64 brute force over the whole corpus", "dtypes": report,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -526,6 +615,9 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=3)
     ap.add_argument("--serve-mem-gb", type=int, default=16)
     ap.add_argument("--serve-wait-us", type=float, default=200.0)
+    ap.add_argument("--precision", action="store_true",
+                    help="per-dtype recall and score error (f16 exact, bf16 and fp8 served forms)")
+    ap.add_argument("--precision-sample", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
@@ -550,6 +642,8 @@ def main():
         return run_reference(args, cfg)
     if args.serve:
         return run_serve(args, cfg)
+    if args.precision:
+        return run_precision(args, cfg)
     return run_lider(args, cfg)
 
 
