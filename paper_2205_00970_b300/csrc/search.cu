@@ -1137,6 +1137,8 @@ struct TcArgs {
     const int64_t* bm_off;
     int ncl;
     float* dense;               // per pair: approximate scores over its cluster's positions
+    const uint32_t* bitmap;     // per pair: candidate bitmap (mark_kernel)
+    float* cmax;                // per pair and bitmap word: best candidate score of those 32 positions
     const float* slot_scale;    // FP8 form: per slot query scale (else null)
     const float* col_scale;     // FP8 form: per corpus row scale, reordered rows
 };
@@ -1169,6 +1171,8 @@ struct TcEpi {
     float rs;                   // FP8 form: this row's query scale
     const float* cs;            // FP8 form: row scales of the tile's corpus rows (null: unscaled)
     int ncs;                    // rows of the tile inside the cluster
+    float* crow;                // this lane's chunk maxima at the tile's first word (null: no pair)
+    uint32_t bits[tc::kBN / 32];  // this lane's candidate bits over the tile's 256 columns
 
     __device__ void begin(int u, int row) {
         const int4 t = a->units[u];
@@ -1178,7 +1182,12 @@ struct TcEpi {
         const int64_t words = bitmap_words(n_c);
         const int p0 = rt * tc::kBN;
         ncols = (int)min((int64_t)tc::kBN, words * 32 - p0);
-        drow = row < in_tile ? a->dense + (a->bm_off[j] + ((int64_t)it * tc::kBM + row) * words) * 32 + p0 : nullptr;
+        const int64_t wrow = a->bm_off[j] + ((int64_t)it * tc::kBM + row) * words;   // the pair's first word
+        drow = row < in_tile ? a->dense + wrow * 32 + p0 : nullptr;
+        crow = row < in_tile ? a->cmax + wrow + (p0 >> 5) : nullptr;
+#pragma unroll
+        for (int w = 0; w < tc::kBN / 32; ++w)
+            bits[w] = (row < in_tile && 32 * w < ncols) ? __ldg(a->bitmap + wrow + (p0 >> 5) + w) : 0u;
         cs = nullptr;
         if (a->slot_scale) {
             rs = row < in_tile ? a->slot_scale[a->off[j] + it * tc::kBM + row] : 0.f;
@@ -1201,6 +1210,15 @@ struct TcEpi {
         } else {
 #pragma unroll
             for (int i = 0; i < 32; ++i) stage[lane * kEpiPitch + i] = __uint_as_float(v[i]);
+        }
+        // the best candidate score of these 32 positions of this lane's row
+        {
+            const uint32_t w = bits[col0 >> 5];
+            float m = -INFINITY;
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+                if ((w >> i) & 1u) m = fmaxf(m, stage[lane * kEpiPitch + i]);
+            if (crow) crow[col0 >> 5] = m;
         }
         __syncwarp();
         const int sub = lane >> 3, c4 = (lane & 7) * 4;
@@ -1321,6 +1339,7 @@ __global__ void __launch_bounds__(512) rescore_kernel(const float* __restrict__ 
 // candidate bitmap (both written per pair slot, see mark_kernel and TcEpi).
 struct DenseArgs {
     const float* dense;
+    const float* cmax;
     const uint32_t* bitmap;
     const int64_t* bm_off;
     const int32_t* off;
@@ -1334,6 +1353,7 @@ struct DenseArgs {
 struct PairRow {
     const float* row;
     const uint32_t* bm;
+    const float* cm;            // best candidate score per bitmap word
     int64_t cb;                 // first row of the cluster in the reordered corpus
     int n_c;
 };
@@ -1344,7 +1364,7 @@ __device__ __forceinline__ PairRow pair_row(const DenseArgs& d, int64_t pair) {
     const int64_t cb = d.cl_off[j];
     const int64_t n_c = d.cl_off[j + 1] - cb;
     const int64_t wbase = d.bm_off[j] + (int64_t)(slot - d.off[j]) * bitmap_words(n_c);
-    return PairRow{d.dense + wbase * 32, d.bitmap + wbase, cb, (int)n_c};
+    return PairRow{d.dense + wbase * 32, d.bitmap + wbase, d.cmax + wbase, cb, (int)n_c};
 }
 
 __device__ __forceinline__ bool is_cand(const PairRow& r, int pos) { return (r.bm[pos >> 5] >> (pos & 31)) & 1u; }
@@ -1625,54 +1645,37 @@ __global__ void __launch_bounds__(512) select_hist_kernel(
         }
     };
     auto comp = [](const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; };
-    // Way 1 (need <= 4 * blockDim): one pass in which every thread keeps its
-    // 4 best candidates (score, list, position).  The need-th best of those
-    // 4 * blockDim scores is a candidate score with at least `need` candidates
-    // at or above it, so the ks-th best is not below it: every candidate at or
-    // above it less twice the guard is collected, from the kept four, or by a
-    // second look at its own positions for a thread whose 4th best already
-    // clears that threshold (it may hold more).
+    // Way 1 (need <= 4 * blockDim), on the chunk maxima the tensor epilogue
+    // wrote (per pair and 32 positions, the best candidate score there).  Every
+    // thread keeps its 4 best maxima; the need-th best of those 4 * blockDim
+    // values is a score reached by at least `need` distinct candidates (one per
+    // chunk), so the ks-th best is not below it.  Every candidate at or above it
+    // less twice the guard lies in a chunk whose maximum clears that threshold:
+    // only those chunks are read.
     constexpr int kKeep = 4;
     bool small_lists = true;                        // positions fit the (list, position) packing
     for (int p = 0; p < c; ++p) small_lists = small_lists && s_pr[p].n_c < (1 << 27);
     const bool by_max = need > 0 && need <= kKeep * bd && small_lists;
-    float ts[kKeep];
-    uint32_t tp[kKeep];                            // (list << 27) | position
-#pragma unroll
-    for (int j = 0; j < kKeep; ++j) { ts[j] = -INFINITY; tp[j] = 0u; }
     if (by_max) {
+        float ts[kKeep];
+#pragma unroll
+        for (int j = 0; j < kKeep; ++j) ts[j] = -INFINITY;
         for (int p = 0; p < c; ++p) {
             const PairRow pr = s_pr[p];
-            const int ng = (pr.n_c + 3) >> 2;
-            for (int g0 = tid; g0 < ng; g0 += kU * bd) {
-                float4 sc[kU];
-                uint32_t wv[kU];
-                load_groups(pr, g0, sc, wv);
+            const int nw = (pr.n_c + 31) >> 5;
+            for (int w = tid; w < nw; w += bd) {
+                float vv = __ldg(pr.cm + w);
 #pragma unroll
-                for (int r = 0; r < kU; ++r) {
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float v = comp(sc[r], i);
-                        if (((wv[r] >> i) & 1u) && v > ts[kKeep - 1]) {
-                            uint32_t pv = ((uint32_t)p << 27) | (uint32_t)(4 * (g0 + r * bd) + i);
-                            float vv = v;
-#pragma unroll
-                            for (int j = 0; j < kKeep; ++j) {   // insert, best first
-                                if (vv > ts[j]) {
-                                    const float t0 = ts[j];
-                                    const uint32_t p0 = tp[j];
-                                    ts[j] = vv;
-                                    tp[j] = pv;
-                                    vv = t0;
-                                    pv = p0;
-                                }
-                            }
-                        }
+                for (int j = 0; j < kKeep; ++j) {   // insert, best first
+                    if (vv > ts[j]) {
+                        const float t0 = ts[j];
+                        ts[j] = vv;
+                        vv = t0;
                     }
                 }
             }
         }
-        // the kept scores as sortable words, best first (none: the largest word)
+        // the kept maxima as sortable words, best first (none: the largest word)
         for (int u = tid; u < kHistBins; u += bd) hist[u] = 0xffffffffu;
         __syncthreads();
 #pragma unroll
@@ -1681,7 +1684,7 @@ __global__ void __launch_bounds__(512) select_hist_kernel(
         block_bitonic32(hist, next_pow2_dev(kKeep * bd));
         if (tid == 0) {
             const uint32_t wk = hist[need - 1];
-            float thr = -INFINITY;                 // fewer kept scores than need: take all
+            float thr = -INFINITY;                 // fewer chunks with candidates than need: take all
             if (wk != 0xffffffffu) {
                 thr = float_from_order(~wk);
                 if (guarded) thr = thr - 2.f * qguard[q];
@@ -1691,31 +1694,36 @@ __global__ void __launch_bounds__(512) select_hist_kernel(
         }
         __syncthreads();
         const float thr = s_thr;
-        auto emit = [&](float v, int p, int pos) {
-            const int slot = atomicAdd(&s_cnt, 1);
-            if (slot < kHistCand) cand[slot] = sel_key(v, (uint32_t)__ldg(da.orig_id + s_pr[p].cb + pos));
-        };
-        if (ts[kKeep - 1] >= thr && ts[kKeep - 1] != -INFINITY) {
-            // this thread may hold more than four: look at its positions again
-            for (int p = 0; p < c; ++p) {
-                const PairRow pr = s_pr[p];
-                const int ng = (pr.n_c + 3) >> 2;
-                for (int g0 = tid; g0 < ng; g0 += kU * bd) {
-                    float4 sc[kU];
-                    uint32_t wv[kU];
-                    load_groups(pr, g0, sc, wv);
+        // read the chunks whose maximum clears the threshold; a thread reserves
+        // its chunk's keys with one atomic
+        for (int p = 0; p < c; ++p) {
+            const PairRow pr = s_pr[p];
+            const int nw = (pr.n_c + 31) >> 5;
+            for (int w = tid; w < nw; w += bd) {
+                if (!(__ldg(pr.cm + w) >= thr)) continue;
+                const uint32_t bw = __ldg(pr.bm + w);
+                float v[32];
 #pragma unroll
-                    for (int r = 0; r < kU; ++r)
+                for (int g4 = 0; g4 < 8; ++g4) {
+                    const float4 f = __ldg(reinterpret_cast<const float4*>(pr.row + 32 * w) + g4);
+                    v[4 * g4] = f.x; v[4 * g4 + 1] = f.y; v[4 * g4 + 2] = f.z; v[4 * g4 + 3] = f.w;
+                }
+                uint32_t take = 0u;
 #pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            if (((wv[r] >> i) & 1u) && comp(sc[r], i) >= thr)
-                                emit(comp(sc[r], i), p, 4 * (g0 + r * bd) + i);
+                for (int i = 0; i < 32; ++i)
+                    if (((bw >> i) & 1u) && v[i] >= thr) take |= 1u << i;
+                const int nt = __popc(take);
+                if (nt == 0) continue;
+                int slot = atomicAdd(&s_cnt, nt);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    if ((take >> i) & 1u) {
+                        if (slot < kHistCand)
+                            cand[slot] = sel_key(v[i], (uint32_t)__ldg(da.orig_id + pr.cb + 32 * w + i));
+                        ++slot;
+                    }
                 }
             }
-        } else {
-#pragma unroll
-            for (int j = 0; j < kKeep; ++j)
-                if (ts[j] != -INFINITY && ts[j] >= thr) emit(ts[j], (int)(tp[j] >> 27), (int)(tp[j] & 0x7ffffffu));
         }
     }
     // Threshold, way 2 (larger need): histogram
@@ -1927,6 +1935,7 @@ struct Workspace {
     int32_t* redo_count;        // (cleared)
     int32_t* pcount;            // tensor path: candidates per pair (cleared; written by mark_kernel)
     float* dense;               // tensor paths: per pair slot, approximate scores over its cluster
+    float* cmax;                // tensor paths: per pair slot and bitmap word, the best candidate score
     int32_t* slot_of;           // tensor paths: pair -> its slot in cluster order
     int32_t* unit_off;
     int64_t* bm_off;            // tensor paths: per-cluster bitmap offsets (words)
@@ -2018,6 +2027,7 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, const
     w.pid = tensor ? nullptr : (int64_t*)take((size_t)np * sh.kp * 8);
     w.pbuf = tensor ? nullptr : (uint64_t*)take((size_t)np * g.L * sh.R * 8);
     w.dense = tensor ? (float*)take((size_t)sh.bitmap_words * 32 * 4) : nullptr;
+    w.cmax = tensor ? (float*)take((size_t)sh.bitmap_words * 4) : nullptr;
     w.slot_of = tensor ? (int32_t*)take((size_t)np * 4) : nullptr;
     w.sl_ids = tensor ? (int64_t*)take((size_t)nq * sh.so * 8) : nullptr;
     w.sl_scores = tensor ? (float*)take((size_t)nq * sh.so * 4) : nullptr;
@@ -2212,6 +2222,8 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         ta.bm_off = w.bm_off;
         ta.ncl = g.ncl;
         ta.dense = w.dense;
+        ta.bitmap = w.bitmap;
+        ta.cmax = w.cmax;
         ta.slot_scale = sh.mode == LIDER_SCORE_FP8 ? w.slot_scale : nullptr;
         ta.col_scale = ix->x_rowscale;
         const int tc_smem = tc::kSmemBytes + kEpiStageBytes;
@@ -2243,6 +2255,7 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         const int guarded = sh.mode != LIDER_SCORE_BF16 && sh.mode != LIDER_SCORE_FP8;
         DenseArgs da;
         da.dense = w.dense;
+        da.cmax = w.cmax;
         da.bitmap = w.bitmap;
         da.bm_off = w.bm_off;
         da.off = w.off;
