@@ -350,13 +350,13 @@ __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __re
     const float* srow = S + q * ncl;
     const float* qv = Q + q * d;
     const int nsl = min(c + kRouteExtra, ncl);
-    // shortlist: the nsl best approximate scores (ties -> lower index)
+    // shortlist: the nsl best approximate scores (ties -> lower index), built
+    // in rounds; the first c + 1 usually settle the route (see below)
     int sl[LIDER_MAX_C + kRouteExtra];
     float av[LIDER_MAX_C + kRouteExtra];
     float ps = INFINITY;
     int pj = -1;
-#pragma unroll 1
-    for (int r = 0; r < nsl; ++r) {
+    auto next_best = [&](int r) {
         float best = -INFINITY;
         int bj = 0x7fffffff;
         for (int j = lane; j < ncl; j += 32) {
@@ -375,20 +375,10 @@ __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __re
         pj = bj;
         sl[r] = bj;
         av[r] = best;
-    }
-    // the best approximate score outside the shortlist
-    float a_out = -INFINITY;
-    if (nsl < ncl) {
-        float best = -INFINITY;
-        for (int j = lane; j < ncl; j += 32) {
-            float v = srow[j];
-            if (v != v) v = -INFINITY;
-            const bool after = (v < ps) || (v == ps && j > pj);
-            if (after && v > best) best = v;
-        }
-        for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
-        a_out = best;
-    }
+    };
+    const int n_first = min(c + 1, nsl);
+#pragma unroll 1
+    for (int r = 0; r < n_first; ++r) next_best(r);
     float qn2 = 0.f;
     for (int i = lane; i < d; i += 32) qn2 = fmaf(qv[i], qv[i], qn2);
     for (int o = 16; o > 0; o >>= 1) qn2 += __shfl_xor_sync(0xffffffffu, qn2, o);
@@ -418,7 +408,7 @@ __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __re
     // other centroid can enter: the route is the shortlist's head.
     bool clear = true;
     for (int r = 0; r < c; ++r) {
-        const float next = r + 1 < nsl ? av[r + 1] : (nsl < ncl ? a_out : -INFINITY);
+        const float next = r + 1 < n_first ? av[r + 1] : -INFINITY;     // c + 1 <= ncl: av[c] is the next
         if (!((double)av[r] - (double)next > 2.0 * (double)guard)) clear = false;
     }
     if (clear) {
@@ -429,6 +419,21 @@ __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __re
             }
         }
         return;
+    }
+#pragma unroll 1
+    for (int r = n_first; r < nsl; ++r) next_best(r);
+    // the best approximate score outside the shortlist
+    float a_out = -INFINITY;
+    if (nsl < ncl) {
+        float best = -INFINITY;
+        for (int j = lane; j < ncl; j += 32) {
+            float v = srow[j];
+            if (v != v) v = -INFINITY;
+            const bool after = (v < ps) || (v == ps && j > pj);
+            if (after && v > best) best = v;
+        }
+        for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+        a_out = best;
     }
     // exact scores of the shortlist, then the c best
     double ex[LIDER_MAX_C + kRouteExtra];
@@ -1053,12 +1058,13 @@ __global__ void qgather_bf16_kernel(const float* __restrict__ Q, const int32_t* 
     for (int i = lane; i < d; i += 32) dst[i] = __bfloat16_as_ushort(__float2bfloat16_rn(src[i]));
 }
 
-constexpr int kMarkSmemWords = 8192;   // clusters up to 262,144 points mark in shared memory
 
-// One block per pair slot (pairs in cluster order): the union of the pair's L
-// expansion windows as a bitmap over the cluster's positions, at
-// bitmap + bm_off[j] + (slot - off[j]) * words_j; also slot_of[pair] = slot
-// and ucount[pair] = the number of candidates (set bits).
+// One warp per pair slot (pairs in cluster order; blockDim / 32 slots per
+// block): the union of the pair's L expansion windows as a bitmap over the
+// cluster's positions, at bitmap + bm_off[j] + (slot - off[j]) * words_j; also
+// slot_of[pair] = slot and ucount[pair] = the number of candidates (set bits).
+// A bitmap of up to smem_words words is built in the warp's shared memory,
+// a larger one in place with global atomics.
 __global__ void __launch_bounds__(256) mark_kernel(const int32_t* __restrict__ pairs,
                                                    const int32_t* __restrict__ route, const int32_t* __restrict__ off,
                                                    const int64_t* __restrict__ cl_off,
@@ -1066,45 +1072,40 @@ __global__ void __launch_bounds__(256) mark_kernel(const int32_t* __restrict__ p
                                                    const int32_t* __restrict__ wstart, const int32_t* __restrict__ pos,
                                                    int64_t n, int L, int R, uint32_t* __restrict__ bitmap,
                                                    int32_t* __restrict__ slot_of, int32_t* __restrict__ ucount,
-                                                   int smem_words) {
-    extern __shared__ uint32_t sbits[];         // smem_words (the largest cluster's words, or 0)
-    __shared__ int s_u;
-    const int64_t slot = blockIdx.x;
+                                                   int smem_words, int64_t np) {
+    extern __shared__ uint32_t sbits[];         // (blockDim / 32) x smem_words
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t slot = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (slot >= np) return;                     // the whole warp
     const int64_t pair = pairs[slot];
     const int j = route[pair];
     const int64_t base = cl_off[j];
     const int64_t n_c = cl_off[j + 1] - base;
-    if (threadIdx.x == 0) {
-        slot_of[pair] = (int32_t)slot;
-        s_u = 0;
-    }
-    if (n_c == 0) return;                 // ucount stays 0 (cleared)
+    if (lane == 0) slot_of[pair] = (int32_t)slot;
+    if (n_c == 0) return;                       // ucount stays 0 (cleared)
     const int64_t words = bitmap_words(n_c);
     uint32_t* dst = bitmap + bm_off[j] + (slot - off[j]) * words;
     const int T = (int)min((int64_t)R, n_c);
     const bool in_smem = words <= smem_words;
-    uint32_t* bits = in_smem ? sbits : dst;
-    for (int64_t i = threadIdx.x; i < words; i += blockDim.x) bits[i] = 0u;
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int l = warp; l < L; l += blockDim.x / 32) {
+    uint32_t* bits = in_smem ? sbits + (size_t)warp * smem_words : dst;
+    for (int64_t i = lane; i < words; i += 32) bits[i] = 0u;
+    __syncwarp();
+    for (int l = 0; l < L; ++l) {
         const int32_t* P = pos + (int64_t)l * n + base + wstart[pair * L + l];
         for (int t = lane; t < T; t += 32) {
             const uint32_t p = (uint32_t)P[t];
             atomicOr(&bits[p >> 5], 1u << (p & 31));
         }
     }
-    __syncthreads();
+    __syncwarp();
     int u = 0;
-    for (int64_t i = threadIdx.x; i < words; i += blockDim.x) {
+    for (int64_t i = lane; i < words; i += 32) {
         const uint32_t wv = bits[i];
         if (in_smem) dst[i] = wv;
         u += __popc(wv);
     }
     for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
-    if ((threadIdx.x & 31) == 0 && u) atomicAdd(&s_u, u);
-    __syncthreads();
-    if (threadIdx.x == 0) ucount[pair] = s_u;       // candidates of the pair
+    if (lane == 0) ucount[pair] = u;            // candidates of the pair
 }
 
 // One tensor-core tile: A row (first query slot), B row (first corpus row),
@@ -1161,7 +1162,9 @@ struct TcSched {
 // 128 bytes per instruction.  Which positions are candidates is read later,
 // from the pair's bitmap, by the select.
 constexpr int kEpiPitch = 33;                              // padded row of the transpose
-constexpr int kEpiStageBytes = 4 * 32 * kEpiPitch * 4;     // four epilogue warps
+constexpr int kScoreEpiWarps = 8;                          // epilogue warps of tc_score_kernel
+constexpr int kScoreThreads8 = tc::threads_for(kScoreEpiWarps);
+constexpr int kEpiStageBytes = kScoreEpiWarps * 32 * kEpiPitch * 4;
 
 struct TcEpi {
     const TcArgs* a;
@@ -1185,9 +1188,13 @@ struct TcEpi {
         const int64_t wrow = a->bm_off[j] + ((int64_t)it * tc::kBM + row) * words;   // the pair's first word
         drow = row < in_tile ? a->dense + wrow * 32 + p0 : nullptr;
         crow = row < in_tile ? a->cmax + wrow + (p0 >> 5) : nullptr;
+        // this warp's column groups of the tile (two warps share each row)
+        constexpr int kGpw = (tc::kBN / 32) / (kScoreEpiWarps / 4);
+        const int g0 = ((((int)threadIdx.x >> 5) - 2) >> 2) * kGpw;
 #pragma unroll
         for (int w = 0; w < tc::kBN / 32; ++w)
-            bits[w] = (row < in_tile && 32 * w < ncols) ? __ldg(a->bitmap + wrow + (p0 >> 5) + w) : 0u;
+            bits[w] = (row < in_tile && 32 * w < ncols && w >= g0 && w < g0 + kGpw)
+                          ? __ldg(a->bitmap + wrow + (p0 >> 5) + w) : 0u;
         cs = nullptr;
         if (a->slot_scale) {
             rs = row < in_tile ? a->slot_scale[a->off[j] + it * tc::kBM + row] : 0.f;
@@ -1213,7 +1220,10 @@ struct TcEpi {
         }
         // the best candidate score of these 32 positions of this lane's row
         {
-            const uint32_t w = bits[col0 >> 5];
+            uint32_t w = 0;
+#pragma unroll
+            for (int i = 0; i < tc::kBN / 32; ++i)           // a select, not a local-memory index
+                if (i == (col0 >> 5)) w = bits[i];
             float m = -INFINITY;
 #pragma unroll
             for (int i = 0; i < 32; ++i)
@@ -1239,7 +1249,7 @@ struct TcEpi {
 };
 
 template <class Kind>
-__global__ void __launch_bounds__(tc::kThreads, 1)
+__global__ void __launch_bounds__(kScoreThreads8, 1)
     tc_score_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                     const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, int kchunks,
                     TcArgs args, int* err) {
@@ -1248,9 +1258,10 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     TcSched sched{&args};
     TcEpi epi;
     epi.a = &args;
-    // key staging after the engine's shared memory, one slice per epilogue warp
-    epi.stage = reinterpret_cast<float*>(smem + tc::kSmemBytes) + (size_t)((threadIdx.x >> 5) & 3) * 32 * kEpiPitch;
-    tc::gemm_tiles<Kind>(&mAhi, &mAlo, &mBhi, &mBlo, kchunks, sched, epi, err, smem, ctl);
+    // transpose staging after the engine's shared memory, one slice per epilogue warp
+    epi.stage = reinterpret_cast<float*>(smem + tc::kSmemBytes) +
+                (size_t)(threadIdx.x >= 64 ? (threadIdx.x >> 5) - 2 : 0) * 32 * kEpiPitch;
+    tc::gemm_tiles<Kind, TcSched, TcEpi, kScoreEpiWarps>(&mAhi, &mAlo, &mBhi, &mBlo, kchunks, sched, epi, err, smem, ctl);
 }
 
 
@@ -2202,12 +2213,14 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
             if ((rc = make_tensor_map(&mqh, w.qp_hi, np, g.d, tc::kBM))) return rc;
             if ((rc = make_tensor_map(&mql, w.qp_lo, np, g.d, tc::kBM))) return rc;
         }
-        // bitmaps of clusters up to kMarkSmemWords words are built in shared memory
+        // a warp per pair; bitmaps up to 48 KB per block of warps are built in shared memory
+        const int mark_wpb = ix->tune.mark_threads / 32;
         const int max_words = g.max_row_tiles * (tc::kBN / 32);
-        const int mark_words = max_words <= kMarkSmemWords ? max_words : 0;
-        mark_kernel<<<(unsigned)np, (unsigned)ix->tune.mark_threads, (size_t)mark_words * 4, st>>>(
+        const int mark_words = std::min(max_words, (48 * 1024 / 4) / mark_wpb);
+        mark_kernel<<<(unsigned)cdiv(np, mark_wpb), (unsigned)ix->tune.mark_threads,
+                      (size_t)mark_wpb * mark_words * 4, st>>>(
             w.pairs, w.route, w.off, g.cl_off, w.bm_off, w.wstart, g.pos, g.n, g.L, R, w.bitmap, w.slot_of, w.pcount,
-            mark_words);
+            mark_words, np);
         LIDER_LAUNCH_CHECK("mark_kernel");
         if ((rc = mark(LIDER_PHASE_SCORE))) return rc;
         tc_units_kernel<<<g.ncl, 128, 0, st>>>(w.unit_off, w.off, g.cl_off, g.ncl, ix->tune.tile_order, w.units);
@@ -2230,21 +2243,21 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         // A = queries of the tile (128 rows, box 128), B = cluster rows (256, box 256)
         if (sh.mode == LIDER_SCORE_FP8) {
             if ((rc = smem_attr((const void*)tc_score_kernel<tc::KindF8>, (int)(tc_smem)))) return rc;
-            tc_score_kernel<tc::KindF8><<<ix->num_sms, tc::kThreads, tc_smem, st>>>(
+            tc_score_kernel<tc::KindF8><<<ix->num_sms, kScoreThreads8, tc_smem, st>>>(
                 mqh, mql, ix->map_xf8, ix->map_xf8, (g.d + tc::KindF8::kBK - 1) / tc::KindF8::kBK, ta, w.tc_err);
         } else if (sh.mode == LIDER_SCORE_BF16) {
             if ((rc = smem_attr((const void*)tc_score_kernel<tc::KindBf16>, (int)(tc_smem)))) return rc;
-            tc_score_kernel<tc::KindBf16><<<ix->num_sms, tc::kThreads, tc_smem, st>>>(
+            tc_score_kernel<tc::KindBf16><<<ix->num_sms, kScoreThreads8, tc_smem, st>>>(
                 mqh, mql, ix->map_xh16, ix->map_xh16, (g.d + tc::KindBf16::kBK - 1) / tc::KindBf16::kBK, ta,
                 w.tc_err);
         } else if (sh.mode == LIDER_SCORE_F16) {
             if ((rc = smem_attr((const void*)tc_score_kernel<tc::KindF16>, (int)(tc_smem)))) return rc;
-            tc_score_kernel<tc::KindF16><<<ix->num_sms, tc::kThreads, tc_smem, st>>>(
+            tc_score_kernel<tc::KindF16><<<ix->num_sms, kScoreThreads8, tc_smem, st>>>(
                 mqh, mql, ix->map_xh16, ix->map_xh16, (g.d + tc::KindF16::kBK - 1) / tc::KindF16::kBK, ta,
                 w.tc_err);
         } else {
             if ((rc = smem_attr((const void*)tc_score_kernel<tc::KindTf32x3>, (int)(tc_smem)))) return rc;
-            tc_score_kernel<tc::KindTf32x3><<<ix->num_sms, tc::kThreads, tc_smem, st>>>(
+            tc_score_kernel<tc::KindTf32x3><<<ix->num_sms, kScoreThreads8, tc_smem, st>>>(
                 mqh, mql, ix->map_xhi, ix->map_xlo, (g.d + tc::KindTf32x3::kBK - 1) / tc::KindTf32x3::kBK, ta,
                 w.tc_err);
         }

@@ -27,7 +27,9 @@ constexpr int kTileA = kBM * kRowBytes;        // 16 KB
 constexpr int kTileB = kBN * kRowBytes;        // 32 KB
 constexpr int kMaxStages = 4;
 constexpr int kSmemBytes = 2 * (2 * kTileA + 2 * kTileB) + 1024;  // both kinds: 192 KB + alignment slack
-constexpr int kThreads = 192;
+constexpr int kThreads = 192;       // producer + MMA warps + 4 epilogue warps
+// threads of a block with kEpiWarps epilogue warps (4 or 8)
+constexpr int threads_for(int epi_warps) { return 64 + 32 * epi_warps; }
 constexpr int kTmemCols = 2 * kBN;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 
@@ -227,7 +229,8 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
 }
 
 // Named barrier of the four epilogue warps (barrier 0 is __syncthreads).
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+template <int kEpiWarps>
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory"); }
 
 // Shared state of one block.
 struct Ctl {
@@ -252,7 +255,7 @@ struct Ctl {
 // cannot be left waiting.
 // mA0/mB0: the operands (KindTf32x3: their TF32 heads); mA1/mB1: the tails
 // (KindTf32x3 only; ignored otherwise).  kchunks = ceil(d / Kind::kBK).
-template <class Kind, class Sched, class Epi>
+template <class Kind, class Sched, class Epi, int kEpiWarps = 4>
 __device__ void gemm_tiles(const CUtensorMap* mAhi, const CUtensorMap* mAlo, const CUtensorMap* mBhi,
                            const CUtensorMap* mBlo, int kchunks, Sched& sched, Epi& epi, int* err,
                            unsigned char* smem_raw, Ctl& ctl) {
@@ -273,7 +276,7 @@ __device__ void gemm_tiles(const CUtensorMap* mAhi, const CUtensorMap* mAlo, con
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&ctl.tfull[b], 1);
-            mbar_init(&ctl.tempty[b], 4);
+            mbar_init(&ctl.tempty[b], kEpiWarps);
         }
         ctl.abort = 0;
         ctl.epi_bad = 0;
@@ -365,8 +368,13 @@ __device__ void gemm_tiles(const CUtensorMap* mAhi, const CUtensorMap* mAlo, con
                 mma_commit(&ctl.tfull[ab]);                    // accumulator ready
             }
         }
-    } else {                                                     // epilogue warps 2..5
+    } else {                                                     // epilogue warps 2..
+        // warp w reads TMEM lanes 32 (w % 4) ..; with 8 epilogue warps two of
+        // them share those lanes and take 4 of the 8 column groups each
+        static_assert(kEpiWarps == 4 || kEpiWarps == 8, "4 or 8 epilogue warps");
+        constexpr int kGroups = (kBN / 32) / (kEpiWarps / 4);
         const int quarter = warp & 3;
+        const int cb0 = ((warp - 2) >> 2) * kGroups;
         const int row = quarter * 32 + lane;
         int ui = 0;
         for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++ui) {
@@ -378,12 +386,13 @@ __device__ void gemm_tiles(const CUtensorMap* mAhi, const CUtensorMap* mAlo, con
                 fail(TC_TIMEOUT_TFULL);
                 atomicOr(&ctl.epi_bad, 1);
             }
-            epi_sync();                                  // every epilogue warp arrives
-            if (*(volatile int*)&ctl.epi_bad) break;     // same decision in all four
+            epi_sync<kEpiWarps>();                       // every epilogue warp arrives
+            if (*(volatile int*)&ctl.epi_bad) break;     // same decision in all of them
             tc_fence_after();
             const uint32_t base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * kBN);
 #pragma unroll
-            for (int cb = 0; cb < kBN / 32; ++cb) {
+            for (int g = 0; g < kGroups; ++g) {
+                const int cb = cb0 + g;
                 uint32_t v[32];
                 tmem_ld32(base + (uint32_t)(cb * 32), v);
                 epi(u, row, cb * 32, v);
