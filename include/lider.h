@@ -38,7 +38,18 @@ extern "C" {
 #define LIDER_ELIMIT   -4   /* a size exceeds a documented implementation cap */
 #define LIDER_ETIMEDOUT -5  /* lider_server_wait: the request is still running */
 
-#define LIDER_HASH_PSTABLE 0   /* h = floor((a.x + b) / W), Sec. 4.1 (p-stable) */
+#define LIDER_HASH_PSTABLE    0  /* h = floor((a.x + b) / W), Sec. 4.1 (p-stable)    */
+#define LIDER_HASH_HYPERPLANE 1  /* h = [a.x >= 0], Sec. 4.1 (random hyperplane, one
+                                    bit per hash; b and W are not used)          */
+
+/* How a query picks its c clusters (Sec. 3.2 and Sec. 3.3.2). */
+#define LIDER_ROUTE_EXACT 0   /* exact scan: the c best scores q.mu - |mu|^2/2 over
+                                 all centroids                                     */
+#define LIDER_ROUTE_CORE  1   /* Layer-1 centroids retriever: a core model (the same
+                                 ESK-LSH projections, sorted arrays and RMIs) over
+                                 the centroids; the query is located and expanded
+                                 by r0 * c positions in each array and the c best of
+                                 the centroids found, by the same score, are probed */
 
 /* How candidates are scored.  SIMT, TENSOR and F16 return the same results
  * bit for bit: the exact FP32 top-k of each query's candidate union (the two
@@ -69,19 +80,25 @@ typedef struct lider_index lider_index;   /* opaque; owns its device memory */
 
 /* Index parameters, in the paper's notation (Table 1):
  *   L  = H, number of hashkey arrays (LSH repetitions) per core model;
- *   m  = M, hashes per hashkey; each packs into floor(64/m) bits with offset
- *        2^(floor(64/m)-1) and clamping (a 64-bit sortable key);
+ *   m  = M, hashes per hashkey; p-stable: each packs into floor(64/m) bits
+ *        with offset 2^(floor(64/m)-1) and clamping; hyperplane: one bit each
+ *        (a 64-bit sortable key either way);
  *   rmi_leaves = width of the RMI second stage (linear models per array);
  *   r0 = expansion factor, R = r0 * k positions per array (Sec. 6.1);
  *   B  = elements read by KD_e in the extended hashkey distance dist_e
- *        (Sec. 4.2); floor(64/m) * B must be <= 56;
- *   hash_kind = LIDER_HASH_PSTABLE;
+ *        (Sec. 4.2); (bits per element) * B must be <= 56;
+ *   hash_kind = LIDER_HASH_PSTABLE or LIDER_HASH_HYPERPLANE;
  *   W  = p-stable bucket width (> 0);
  *   score_mode = LIDER_SCORE_TENSOR, LIDER_SCORE_SIMT, LIDER_SCORE_BF16,
  *        LIDER_SCORE_F16 or LIDER_SCORE_FP8 (tensor modes need L <= 16; BF16
  *        and F16 need d % 8 == 0, FP8 d % 16 == 0);
  *   rerank = shortlist factor of LIDER_SCORE_BF16 / FP8: rerank * k candidates per
- *        query are re-scored in FP32 (0 means 4). */
+ *        query are re-scored in FP32 (0 means 4);
+ *   route_kind = LIDER_ROUTE_EXACT (0) or LIDER_ROUTE_CORE (1, needs
+ *        n_clusters <= 16384);
+ *   raw_keys = 0: the RMIs learn re-scaled keys (Sec. 5.1, the method);
+ *        1: they learn the raw 64-bit key values converted to FP64, without
+ *        re-scaling (the ablation of Sec. 7.4; see rmi_oor below). */
 typedef struct {
     int32_t L;
     int32_t m;
@@ -92,6 +109,8 @@ typedef struct {
     double  W;
     int32_t score_mode;
     int32_t rerank;
+    int32_t route_kind;
+    int32_t raw_keys;
 } lider_params;
 
 /* Counters of one search (host struct, filled when the call returns). */
@@ -111,6 +130,13 @@ typedef struct {
                                   near-tied candidates did not fit the re-score
                                   list (their top k may then differ from the exact
                                   one by near-ties; 0 in normal operation)       */
+    /* RMI diagnostics of Sec. 7.4, over every (query, probed cluster, array):
+     * the prediction p^ is out of range (OOR) when it was clamped to 0 or
+     * n_c - 1, i.e. it equals either end; it is a large error (LE) when
+     * |p^ - p*| > k, p* being the exact lower bound of the query key. */
+    int64_t rmi_oor;
+    int64_t rmi_le;
+    int64_t rmi_oor_le;        /* both */
 } lider_search_stats;
 
 /* Phases of one search, in order; events[i] is recorded when phase i starts
@@ -162,8 +188,10 @@ typedef struct {
  *   out        host, receives the new index.
  * The corpus, centroids and projections are copied; the caller keeps
  * ownership of its buffers.  Errors: LIDER_EINVAL for null pointers, n < 1,
- * d % 4 != 0, n_clusters < 1, L/m/r0/B/rmi_leaves < 1, W <= 0, an unknown
- * hash_kind, or floor(64/m)*B > 56; LIDER_ELIMIT past the caps above;
+ * d % 4 != 0, n_clusters < 1, L/m/r0/B/rmi_leaves < 1, W <= 0 (p-stable),
+ * an unknown hash_kind, route_kind or raw_keys, or (bits per element)*B > 56;
+ * LIDER_ELIMIT past the caps above (and n_clusters > 16384 with
+ * LIDER_ROUTE_CORE);
  * LIDER_ENOMEM / LIDER_ECUDA from the device.  On error *out is NULL. */
 int lider_build(const float* corpus, int64_t n, int32_t d,
                 const float* centroids, int32_t n_clusters,

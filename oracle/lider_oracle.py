@@ -48,6 +48,9 @@ BOUNDARY_EPS = 1e-6  # |t - round(t)| below this (in units of W) flags a hash
 HASH_PSTABLE = 0
 HASH_HYPERPLANE = 1
 
+ROUTE_EXACT = 0   # scan every centroid (Sec. 3.3.2 routing, reading R4)
+ROUTE_CORE = 1    # Layer-1 centroids retriever: a core model over the centroids
+
 
 # ----------------------------------------------------------------------------
 # Sec. 4.1 -- LSH functions.  t = (a.x + b) / W; h = floor(t)  (p-stable), or
@@ -164,7 +167,11 @@ def dist_e_value(k1: int, k2: int, m: int, beta: int, B: int) -> float:
 # FP64 rounds to nearest.  Reading R5: a query key below x_min gives r < 0.
 # ----------------------------------------------------------------------------
 
-def rescale(x: int, x_min: int, x_max: int, n_c: int) -> float:
+def rescale(x: int, x_min: int, x_max: int, n_c: int, raw: bool = False) -> float:
+    """raw: no re-scaling; the key value itself rounded to FP64 (the
+    configuration Sec. 7.4 compares against)."""
+    if raw:
+        return float(int(x))
     if x_max == x_min:
         return 0.0
     return float(int(x) - int(x_min)) / float(int(x_max) - int(x_min)) * float(n_c - 1)
@@ -173,7 +180,7 @@ def rescale(x: int, x_min: int, x_max: int, n_c: int) -> float:
 # ----------------------------------------------------------------------------
 # Sec. 5.2 -- simplified two-stage RMI of linear models.  The root predicts a
 # position; it selects leaf floor(pred * F / n_c) (clamped), whose linear model
-# gives the final prediction, floored and clamped to [0, n_c - 1] (Sec. 7.3:
+# gives the final prediction, floored and clamped to [0, n_c - 1] (Sec. 7.4:
 # big predictions truncate to L_array - 1, negative ones to 0).
 # ----------------------------------------------------------------------------
 
@@ -367,6 +374,8 @@ class Index:
     kflags: np.ndarray      # (n, L) bool
     clamped: int
     cores: dict = field(default_factory=dict)
+    raw_keys: bool = False          # RMIs learn raw key values (Sec. 7.4 ablation)
+    centroid_model: "CoreModel | None" = None
 
     @property
     def beta(self) -> int:
@@ -393,14 +402,14 @@ def hash_keys(X, A, b, L, m, W, hash_kind=HASH_PSTABLE):
     return keys, key_flags(hflag, L, m), clamped
 
 
-def build_index(X, C, A, b, L, m, W, F, B=None, hash_kind=HASH_PSTABLE) -> Index:
+def build_index(X, C, A, b, L, m, W, F, B=None, hash_kind=HASH_PSTABLE, raw_keys=False) -> Index:
     """Partition by nearest centroid, hash every point (projections shared by
     all clusters, reading R3).  Core models are built per cluster on demand."""
     if B is None:
         B = 3 if hash_kind == HASH_HYPERPLANE else 1
     asg, near = assign(X, C)
     keys, kflags, clamped = hash_keys(X, A, b, L, m, W, hash_kind)
-    return Index(X, C, A, b, L, m, W, F, B, hash_kind, asg, near, keys, kflags, clamped)
+    return Index(X, C, A, b, L, m, W, F, B, hash_kind, asg, near, keys, kflags, clamped, raw_keys=raw_keys)
 
 
 def build_core(index: Index, j: int, fit: bool = True) -> CoreModel:
@@ -424,7 +433,7 @@ def build_core(index: Index, j: int, fit: bool = True) -> CoreModel:
         cm.x_min.append(x_min)
         cm.x_max.append(x_max)
         if fit:
-            r = np.array([rescale(int(x), x_min, x_max, n_c) for x in ks])
+            r = np.array([rescale(int(x), x_min, x_max, n_c, index.raw_keys) for x in ks])
             lb = np.searchsorted(ks, ks, side="left")
             cm.rmi.append(fit_rmi(r, lb, index.F))
         else:
@@ -446,13 +455,19 @@ class SearchResult:
     ucount: np.ndarray         # (nq, c) unique candidates per probed cluster
 
 
-def search(index: Index, Q: np.ndarray, k: int, c: int, R: int) -> SearchResult:
+def search(index: Index, Q: np.ndarray, k: int, c: int, R: int, route_kind: int = ROUTE_EXACT,
+           Rc: int | None = None) -> SearchResult:
     """LIDER batched search (Sec. 3.3.2): route, per probed cluster locate and
-    expand on each array, union of candidates, exact scores, top-k."""
+    expand on each array, union of candidates, exact scores, top-k.
+    route_kind = ROUTE_CORE routes with the Layer-1 centroids retriever,
+    expanding Rc positions per array (default r0 * c with r0 = R // k)."""
     nq = Q.shape[0]
     L, m, beta, B = index.L, index.m, index.beta, index.B
-    rt, near, _ = route(Q, index.C, c)
     qkeys, qflags, _ = hash_keys(Q, index.A, index.b, L, m, index.W, index.hash_kind)
+    if route_kind == ROUTE_CORE:
+        rt, near = route_core(index, Q, qkeys, qflags, c, (R // k) * c if Rc is None else Rc)
+    else:
+        rt, near, _ = route(Q, index.C, c)
     ids_out = np.full((nq, k), -1, dtype=np.int64)
     sc_out = np.full((nq, k), -np.inf)
     pstar = np.zeros((nq, c, L), dtype=np.int64)
@@ -483,6 +498,95 @@ def search(index: Index, Q: np.ndarray, k: int, c: int, R: int) -> SearchResult:
         ids_out[i, :len(order)] = cid[order]
         sc_out[i, :len(order)] = s[order]
     return SearchResult(ids_out, sc_out, rt, near, qkeys, qflags, pstar, wstart, wlen, ucount)
+
+
+# ----------------------------------------------------------------------------
+# Layer-1 centroids retriever (Sec. 3.2; Sec. 3.3.2 "a core model is created
+# on the collection of the cluster centroids").  The same ESK-LSH projections
+# hash the centroids into L sorted arrays; a query is located (exact lower
+# bound) and expanded by Rc positions in each array (for this core model
+# k_m = c_0, so Rc = r_0 * c_0, Sec. 6.2), and the
+# candidates found are ranked by the routing score of reading R4.
+# ----------------------------------------------------------------------------
+
+def centroid_core(index: Index) -> CoreModel:
+    """The centroids retriever's sorted arrays (entries are centroid indices,
+    equal keys in ascending index order) and the centroids' key flags."""
+    if index.centroid_model is None:
+        ncl = index.C.shape[0]
+        keys, kflags, _ = hash_keys(index.C, index.A, index.b, index.L, index.m, index.W, index.hash_kind)
+        ids = np.arange(ncl, dtype=np.int64)
+        cm = CoreModel(ids=ids)
+        for l in range(index.L):
+            order = np.lexsort((ids, keys[:, l]))
+            cm.keys.append(keys[order, l])
+            cm.sorted_ids.append(ids[order])
+            cm.flags.append(kflags[order, l])
+        index.centroid_model = cm
+    return index.centroid_model
+
+
+def route_core(index: Index, Q: np.ndarray, qkeys: np.ndarray, qflags: np.ndarray, c: int, Rc: int):
+    """Top-c centroids found by the centroids retriever, score descending,
+    ties -> smaller index.  Also returns a flag per query: its c-th and
+    (c+1)-th candidate scores are within 1e-6 relative, or one of its query
+    keys or of the centroid keys lies on a hash boundary (then a correct
+    implementation may route it differently)."""
+    cm = centroid_core(index)
+    any_cflag = any(bool(np.any(f)) for f in cm.flags)
+    nq = Q.shape[0]
+    out = np.empty((nq, c), dtype=np.int64)
+    near = np.zeros(nq, dtype=bool)
+    for i in range(nq):
+        cand = set()
+        for l in range(index.L):
+            ks = cm.keys[l]
+            qk = int(qkeys[i, l])
+            p = lower_bound(ks, qk)
+            s, e = expand(ks, p, qk, Rc, index.m, index.beta, index.B)
+            cand.update(int(j) for j in cm.sorted_ids[l][s:e])
+        cid = np.array(sorted(cand), dtype=np.int64)
+        S = centroid_scores(Q[i:i + 1], index.C[cid])[0]
+        order = np.lexsort((cid, -S))
+        out[i] = cid[order[:c]]
+        flag = any_cflag or bool(np.any(qflags[i]))
+        if len(cid) > c:
+            a, b = S[order[c - 1]], S[order[c]]
+            flag = flag or abs(a - b) <= 1e-6 * max(abs(a), abs(b), 1e-300)
+        near[i] = flag
+    return out, near
+
+
+# ----------------------------------------------------------------------------
+# RMI diagnostics (Sec. 7.4): a prediction is out of range (OOR) when it sits
+# at either end of the array (where the clamp of negative and too-large
+# predictions lands); it is a large error (LE) when it is more than k
+# positions from the true location, the exact lower bound of the query key.
+# ----------------------------------------------------------------------------
+
+def rmi_diagnostics(index: Index, qkeys: np.ndarray, route: np.ndarray, k: int) -> tuple[int, int, int]:
+    """(N_OOR, N_LE, N_overlap) over every (query, probed cluster, array) of a
+    search whose routes are `route` (nq, c); empty clusters are skipped.  The
+    RMIs are fitted here (re-scaled keys, or raw ones if index.raw_keys)."""
+    n_oor = n_le = n_both = 0
+    for i in range(route.shape[0]):
+        for j in route[i]:
+            cm = index.core(int(j), fit=True)
+            for l in range(index.L):
+                ks = cm.keys[l]
+                n_c = len(ks)
+                if n_c == 0:
+                    continue
+                qk = int(qkeys[i, l])
+                r = rescale(qk, cm.x_min[l], cm.x_max[l], n_c, index.raw_keys)
+                _, ph = cm.rmi[l].predict(r)
+                p = lower_bound(ks, qk)
+                oor = ph == 0 or ph == n_c - 1
+                le = abs(ph - p) > k
+                n_oor += oor
+                n_le += le
+                n_both += oor and le
+    return n_oor, n_le, n_both
 
 
 def exact_knn(X: np.ndarray, Q: np.ndarray, k: int, chunk: int = 262144):

@@ -188,10 +188,11 @@ __device__ __forceinline__ int64_t seg_lower_bound(const uint64_t* K, int64_t n,
 // non-negative, every leaf owns one contiguous run of positions, found here by
 // binary search.  Each leaf fits its own least squares (zero variance: slope
 // 0, intercept = mean position; empty: copy of the root) and records
-// [min, max] of (first position of key_i) - prediction_i.
+// [min, max] of (first position of key_i) - prediction_i.  raw: the model
+// learns the raw key values instead of re-scaled ones (Sec. 7.4 ablation).
 __global__ void __launch_bounds__(256) rmi_fit_kernel(
         const uint64_t* __restrict__ keys, const int64_t* __restrict__ cl_off, int64_t n,
-        int L, int F, RmiRoot* __restrict__ roots, RmiLeaf* __restrict__ leaves,
+        int L, int F, bool raw, RmiRoot* __restrict__ roots, RmiLeaf* __restrict__ leaves,
         int* __restrict__ err_flag) {
     __shared__ double red[33];
     const int j = blockIdx.x, l = blockIdx.y;
@@ -210,21 +211,21 @@ __global__ void __launch_bounds__(256) rmi_fit_kernel(
     // root least squares, two passes
     double sr = 0.0, sy = 0.0;
     for (int64_t i = threadIdx.x; i < n_c; i += blockDim.x) {
-        sr += rescale_key(K[i], x_min, x_max, n_c);
+        sr += rescale_key(K[i], x_min, x_max, n_c, raw);
         sy += (double)i;
     }
     sr = block_sum(sr, red);
     sy = block_sum(sy, red);
     const double rbar = sr / (double)n_c, ybar = sy / (double)n_c;
-    const double r_first = rescale_key(K[0], x_min, x_max, n_c);
-    const double r_last = rescale_key(K[n_c - 1], x_min, x_max, n_c);
+    const double r_first = rescale_key(K[0], x_min, x_max, n_c, raw);
+    const double r_last = rescale_key(K[n_c - 1], x_min, x_max, n_c, raw);
     double a0, b0;
     if (r_first == r_last) {
         a0 = ybar; b0 = 0.0;
     } else {
         double sxx = 0.0, sxy = 0.0;
         for (int64_t i = threadIdx.x; i < n_c; i += blockDim.x) {
-            const double dr = rescale_key(K[i], x_min, x_max, n_c) - rbar;
+            const double dr = rescale_key(K[i], x_min, x_max, n_c, raw) - rbar;
             sxx += dr * dr;
             sxy += dr * ((double)i - ybar);
         }
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(256) rmi_fit_kernel(
             int64_t lo = 0, hi = n_c;
             while (lo < hi) {
                 const int64_t mid = (lo + hi) >> 1;
-                const double r = rescale_key(K[mid], x_min, x_max, n_c);
+                const double r = rescale_key(K[mid], x_min, x_max, n_c, raw);
                 if (rmi_leaf(a0, b0, r, F, n_c) < f + e) lo = mid + 1; else hi = mid;
             }
             bounds[e] = lo;
@@ -259,17 +260,17 @@ __global__ void __launch_bounds__(256) rmi_fit_kernel(
         const int64_t cnt = t - s;
         double lr = 0.0, ly = 0.0;
         for (int64_t i = s; i < t; ++i) {
-            lr += rescale_key(K[i], x_min, x_max, n_c);
+            lr += rescale_key(K[i], x_min, x_max, n_c, raw);
             ly += (double)i;
         }
         const double lrbar = lr / (double)cnt, lybar = ly / (double)cnt;
         double a, b;
-        if (rescale_key(K[s], x_min, x_max, n_c) == rescale_key(K[t - 1], x_min, x_max, n_c)) {
+        if (rescale_key(K[s], x_min, x_max, n_c, raw) == rescale_key(K[t - 1], x_min, x_max, n_c, raw)) {
             a = lybar; b = 0.0;
         } else {
             double sxx = 0.0, sxy = 0.0;
             for (int64_t i = s; i < t; ++i) {
-                const double dr = rescale_key(K[i], x_min, x_max, n_c) - lrbar;
+                const double dr = rescale_key(K[i], x_min, x_max, n_c, raw) - lrbar;
                 sxx += dr * dr;
                 sxy += dr * ((double)i - lybar);
             }
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(256) rmi_fit_kernel(
         }
         int64_t elo = INT64_MAX, ehi = INT64_MIN;
         for (int64_t i = s; i < t; ++i) {
-            const double r = rescale_key(K[i], x_min, x_max, n_c);
+            const double r = rescale_key(K[i], x_min, x_max, n_c, raw);
             const int64_t lb = (i > s && K[i - 1] != K[i]) ? i : seg_lower_bound(K, i, K[i]);
             const int64_t e = lb - rmi_predict(a, b, r, n_c);
             elo = min(elo, e);
@@ -308,7 +309,8 @@ void release(lider_index* ix) {
     if (!ix) return;
     void* bufs[] = {ix->X, ix->orig_id, ix->cl_off, ix->C, ix->half_norm, ix->A, ix->bproj,
                     ix->keys, ix->pos, ix->root, ix->leaf, ix->X_hi, ix->X_lo, ix->row_of, ix->X_h16, ix->C_hi, ix->C_lo,
-                    ix->A_hi, ix->A_lo, ix->a_norm, ix->X_f8, ix->x_rowscale};
+                    ix->A_hi, ix->A_lo, ix->a_norm, ix->X_f8, ix->x_rowscale, ix->ckeys, ix->cpos, ix->croot,
+                    ix->cleaf};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (ix->pool) cudaMemPoolDestroy(ix->pool);
@@ -327,11 +329,22 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
     if (ncl < 1) return fail(LIDER_EINVAL, "lider_build: n_clusters must be >= 1");
     if (P->L < 1 || P->m < 1 || P->rmi_leaves < 1 || P->r0 < 1 || P->B < 1)
         return fail(LIDER_EINVAL, "lider_build: L, m, rmi_leaves, r0 and B must be >= 1");
-    if (!(P->W > 0.0) || !std::isfinite(P->W)) return fail(LIDER_EINVAL, "lider_build: W must be > 0");
-    if (P->hash_kind != LIDER_HASH_PSTABLE) return fail(LIDER_EINVAL, "lider_build: unknown hash_kind");
+    if (P->hash_kind != LIDER_HASH_PSTABLE && P->hash_kind != LIDER_HASH_HYPERPLANE)
+        return fail(LIDER_EINVAL, "lider_build: unknown hash_kind");
+    const bool hyper = P->hash_kind == LIDER_HASH_HYPERPLANE;
+    if (!hyper && (!(P->W > 0.0) || !std::isfinite(P->W))) return fail(LIDER_EINVAL, "lider_build: W must be > 0");
     if (P->m > 64) return fail(LIDER_EINVAL, "lider_build: m must be <= 64");
-    const int beta = 64 / P->m;
-    if ((int64_t)beta * P->B > 56) return fail(LIDER_EINVAL, "lider_build: floor(64/m) * B must be <= 56");
+    const int beta = hyper ? 1 : 64 / P->m;
+    if ((int64_t)beta * P->B > 56)
+        return fail(LIDER_EINVAL, "lider_build: (bits per element) * B must be <= 56 (p-stable: floor(64/m) bits)");
+    if (P->route_kind != LIDER_ROUTE_EXACT && P->route_kind != LIDER_ROUTE_CORE)
+        return fail(LIDER_EINVAL, "lider_build: unknown route_kind");
+    if (P->raw_keys != 0 && P->raw_keys != 1) return fail(LIDER_EINVAL, "lider_build: raw_keys must be 0 or 1");
+    if (P->route_kind == LIDER_ROUTE_CORE && ncl > kRouteCoreMaxClusters)
+        return fail(LIDER_ELIMIT, "lider_build: LIDER_ROUTE_CORE supports n_clusters <= 16384");
+    // hyperplane hashes take t = a.x: no offset, unit width
+    const double W = hyper ? 1.0 : P->W;
+    const bool raw = P->raw_keys != 0;
     if (P->L > LIDER_MAX_L) return fail(LIDER_ELIMIT, "lider_build: L exceeds LIDER_MAX_L");
     if (P->rmi_leaves > (1 << 24)) return fail(LIDER_ELIMIT, "lider_build: rmi_leaves too large");
     if (P->score_mode != LIDER_SCORE_TENSOR && P->score_mode != LIDER_SCORE_SIMT && P->score_mode != LIDER_SCORE_BF16 &&
@@ -375,7 +388,8 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
 
     LIDER_CUDA_TRY(cudaMemcpyAsync(ix->C, centroids, (size_t)ncl * d * sizeof(float), cudaMemcpyDefault, st));
     LIDER_CUDA_TRY(cudaMemcpyAsync(ix->A, A, (size_t)H * d * sizeof(float), cudaMemcpyDefault, st));
-    LIDER_CUDA_TRY(cudaMemcpyAsync(ix->bproj, b, (size_t)H * sizeof(float), cudaMemcpyDefault, st));
+    if (hyper) LIDER_CUDA_TRY(cudaMemsetAsync(ix->bproj, 0, (size_t)H * sizeof(float), st));
+    else LIDER_CUDA_TRY(cudaMemcpyAsync(ix->bproj, b, (size_t)H * sizeof(float), cudaMemcpyDefault, st));
     half_norm_kernel<<<(unsigned)cdiv(ncl, 128), 128, 0, st>>>(ix->C, ncl, d, ix->half_norm);
     LIDER_LAUNCH_CHECK("half_norm_kernel");
     if (P->score_mode != LIDER_SCORE_SIMT) {      // tensor-core routing
@@ -444,9 +458,9 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
     ALLOC(pos_tmp.p, (size_t)L * n * sizeof(int32_t), "position scratch");
     for (int64_t r0 = 0; r0 < n; r0 += chunk) {
         const int64_t rows = std::min(chunk, n - r0);
-        if ((rc = launch_hash_t(ix->X + r0 * d, rows, d, ix->A, ix->bproj, H, P->W, sbuf.as<double>(), st))) return rc;
-        if ((rc = launch_pack(sbuf.as<double>(), rows, L, m, beta, r0, 1, n, keys_tmp.as<uint64_t>(), nullptr,
-                              nullptr, st)))
+        if ((rc = launch_hash_t(ix->X + r0 * d, rows, d, ix->A, ix->bproj, H, W, sbuf.as<double>(), st))) return rc;
+        if ((rc = launch_pack(sbuf.as<double>(), rows, L, m, beta, P->hash_kind, r0, 1, n, keys_tmp.as<uint64_t>(),
+                              nullptr, nullptr, st)))
             return rc;
     }
     local_pos_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(asg_sorted.as<int32_t>(), ix->cl_off, n, L,
@@ -522,9 +536,48 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
     }
 
     // 5. RMI per (cluster, array)
-    rmi_fit_kernel<<<dim3(ncl, L), 256, 0, st>>>(ix->keys, ix->cl_off, n, L, F, ix->root, ix->leaf,
+    rmi_fit_kernel<<<dim3(ncl, L), 256, 0, st>>>(ix->keys, ix->cl_off, n, L, F, raw, ix->root, ix->leaf,
                                                 errf.as<int>());
     LIDER_LAUNCH_CHECK("rmi_fit_kernel");
+
+    // 6. Layer-1 centroids retriever (Sec. 3.2): a core model over the
+    //    centroids with the same projections, laid out as one cluster
+    std::vector<int32_t> h_cid;
+    int64_t h_coff[2] = {0, ncl};
+    DevBuf ct, ckt, cpt, coff;
+    if (P->route_kind == LIDER_ROUTE_CORE) {
+        ALLOC(ix->ckeys, (size_t)L * ncl * sizeof(uint64_t), "centroid keys");
+        ALLOC(ix->cpos, (size_t)L * ncl * sizeof(int32_t), "centroid entries");
+        ALLOC(ix->croot, (size_t)L * sizeof(RmiRoot), "centroid rmi roots");
+        ALLOC(ix->cleaf, (size_t)L * F * sizeof(RmiLeaf), "centroid rmi leaves");
+        ALLOC(ct.p, (size_t)ncl * H * sizeof(double), "centroid projections");
+        ALLOC(ckt.p, (size_t)L * ncl * sizeof(uint64_t), "centroid key scratch");
+        ALLOC(cpt.p, (size_t)L * ncl * sizeof(int32_t), "centroid entry scratch");
+        ALLOC(coff.p, sizeof(h_coff), "centroid offsets");
+        h_cid.resize((size_t)L * ncl);
+        for (int l = 0; l < L; ++l)
+            for (int j = 0; j < ncl; ++j) h_cid[(size_t)l * ncl + j] = j;
+        LIDER_CUDA_TRY(cudaMemcpyAsync(cpt.p, h_cid.data(), h_cid.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        LIDER_CUDA_TRY(cudaMemcpyAsync(coff.p, h_coff, sizeof(h_coff), cudaMemcpyHostToDevice, st));
+        if ((rc = launch_hash_t(ix->C, ncl, d, ix->A, ix->bproj, H, W, ct.as<double>(), st))) return rc;
+        if ((rc = launch_pack(ct.as<double>(), ncl, L, m, beta, P->hash_kind, 0, 1, ncl, ckt.as<uint64_t>(), nullptr,
+                              nullptr, st)))
+            return rc;
+        // stable radix sort: equal keys stay in ascending centroid order
+        size_t tmp_bytes = 0;
+        LIDER_CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, ckt.as<uint64_t>(), ix->ckeys,
+                                                       cpt.as<int32_t>(), ix->cpos, ncl, 0, 64, st));
+        DevBuf tmp;
+        ALLOC(tmp.p, tmp_bytes, "centroid sort scratch");
+        for (int l = 0; l < L; ++l)
+            LIDER_CUDA_TRY(cub::DeviceRadixSort::SortPairs(
+                tmp.p, tmp_bytes, ckt.as<uint64_t>() + (int64_t)l * ncl, ix->ckeys + (int64_t)l * ncl,
+                cpt.as<int32_t>() + (int64_t)l * ncl, ix->cpos + (int64_t)l * ncl, ncl, 0, 64, st));
+        rmi_fit_kernel<<<dim3(1, L), 256, 0, st>>>(ix->ckeys, coff.as<int64_t>(), ncl, L, F, raw, ix->croot,
+                                                  ix->cleaf, errf.as<int>());
+        LIDER_LAUNCH_CHECK("rmi_fit_kernel<centroids>");
+        LIDER_CUDA_TRY(cudaStreamSynchronize(st));   // the temporaries above are freed on return
+    }
 
     ix->h_cl_off.resize(ncl + 1);
     LIDER_CUDA_TRY(cudaMemcpyAsync(ix->h_cl_off.data(), ix->cl_off, (ncl + 1) * sizeof(int64_t),
@@ -545,7 +598,9 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
 
     Geometry& g = ix->g;
     g.n = n; g.d = d; g.ncl = ncl; g.L = L; g.m = m; g.F = F; g.beta = beta; g.B = P->B; g.H = H;
-    g.W = P->W;
+    g.W = W;
+    g.hash_kind = P->hash_kind;
+    g.raw_keys = P->raw_keys;
     g.X = ix->X; g.orig_id = ix->orig_id; g.cl_off = ix->cl_off; g.C = ix->C; g.half_norm = ix->half_norm;
     g.A = ix->A; g.bproj = ix->bproj; g.keys = ix->keys; g.pos = ix->pos; g.root = ix->root; g.leaf = ix->leaf;
     g.X_hi = ix->X_hi; g.X_lo = ix->X_lo; g.row_of = ix->row_of; g.X_h16 = ix->X_h16;

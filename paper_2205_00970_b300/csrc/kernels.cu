@@ -93,7 +93,10 @@ __global__ void __launch_bounds__(256) dot2_tile_kernel(
 
 // Pack the m hash values of (row, array l) into one key (Sec. 4.2 linear
 // order; reading R2 for the element width) and count boundary/clamped values.
-__global__ void pack_kernel(const double* __restrict__ t, int64_t n, int L, int m, int beta,
+// p-stable: element floor(t) + 2^(beta-1), clamped; boundary when t lies
+// within 1e-6 of an integer.  Hyperplane (t = a.x): element [t >= 0], one
+// bit; boundary when |t| < 1e-6.
+__global__ void pack_kernel(const double* __restrict__ t, int64_t n, int L, int m, int beta, int hash_kind,
                             int64_t row_offset, int64_t stride_row, int64_t stride_arr,
                             uint64_t* __restrict__ keys,
                             unsigned long long* n_boundary, unsigned long long* n_clamped) {
@@ -106,17 +109,26 @@ __global__ void pack_kernel(const double* __restrict__ t, int64_t n, int L, int 
         const int64_t off = 1ll << (beta - 1);
         const int64_t vmax = (beta >= 63) ? INT64_MAX : ((1ll << beta) - 1);
         uint64_t key = 0;
-        for (int j = 0; j < m; ++j) {
-            const double tj = tr[j];
-            if (fabs(__dadd_rn(tj, -rint(tj))) < 1e-6) ++nb;
-            double fl = floor(tj);
-            fl = fmin(fmax(fl, -4.0e18), 4.0e18);
-            int64_t v = (int64_t)fl + off;
-            if (v < 0) { v = 0; ++nc; }
-            if (v > vmax) { v = vmax; ++nc; }
-            key |= (uint64_t)v << (beta * (m - 1 - j));
+        if (hash_kind == LIDER_HASH_HYPERPLANE) {
+            for (int j = 0; j < m; ++j) {
+                const double tj = tr[j];
+                if (fabs(tj) < 1e-6) ++nb;
+                key |= (uint64_t)(tj >= 0.0 ? 1u : 0u) << (m - 1 - j);
+            }
+            keys[(row_offset + row) * stride_row + (int64_t)l * stride_arr] = key;
+        } else {
+            for (int j = 0; j < m; ++j) {
+                const double tj = tr[j];
+                if (fabs(__dadd_rn(tj, -rint(tj))) < 1e-6) ++nb;
+                double fl = floor(tj);
+                fl = fmin(fmax(fl, -4.0e18), 4.0e18);
+                int64_t v = (int64_t)fl + off;
+                if (v < 0) { v = 0; ++nc; }
+                if (v > vmax) { v = vmax; ++nc; }
+                key |= (uint64_t)v << (beta * (m - 1 - j));
+            }
+            keys[(row_offset + row) * stride_row + (int64_t)l * stride_arr] = key;
         }
-        keys[(row_offset + row) * stride_row + (int64_t)l * stride_arr] = key;
     }
     // warp-aggregated counters
     for (int o = 16; o > 0; o >>= 1) {
@@ -149,12 +161,12 @@ int launch_scores(const float* X, int64_t n, int d, const float* C, const double
     return LIDER_OK;
 }
 
-int launch_pack(const double* t, int64_t n, int L, int m, int beta, int64_t row_offset,
+int launch_pack(const double* t, int64_t n, int L, int m, int beta, int hash_kind, int64_t row_offset,
                 int64_t stride_row, int64_t stride_arr, uint64_t* keys,
                 unsigned long long* n_boundary, unsigned long long* n_clamped, cudaStream_t s) {
     if (n <= 0) return LIDER_OK;
     const int64_t total = n * L;
-    pack_kernel<<<(unsigned)cdiv(total, 256), 256, 0, s>>>(t, n, L, m, beta, row_offset, stride_row,
+    pack_kernel<<<(unsigned)cdiv(total, 256), 256, 0, s>>>(t, n, L, m, beta, hash_kind, row_offset, stride_row,
                                                          stride_arr, keys, n_boundary, n_clamped);
     LIDER_LAUNCH_CHECK("pack_kernel");
     return LIDER_OK;

@@ -43,10 +43,14 @@ struct RmiRoot {          // first stage and re-scaling range of one (cluster, a
     uint64_t x_min, x_max;
 };
 
+constexpr int kRouteCoreMaxClusters = 16384;   // LIDER_ROUTE_CORE cap on n_clusters
+
 struct Geometry {         // everything a search kernel needs, passed by value
     int64_t n;
     int32_t d, ncl, L, m, F, beta, B, H;
     int32_t max_row_tiles;  // ceil(largest cluster / 256)
+    int32_t hash_kind;      // LIDER_HASH_PSTABLE or LIDER_HASH_HYPERPLANE
+    int32_t raw_keys;       // 1: the RMIs take raw key values (no re-scaling)
     double W;
     const float* X;         // n x d, rows grouped by cluster
     const int64_t* orig_id; // n
@@ -109,6 +113,12 @@ struct lider_index {
     CUtensorMap map_xf8;        // TMA map over X_f8, boxes of 128 x 256
     CUtensorMap map_xhi;        // TMA maps over X_hi / X_lo, boxes of 32 x 256
     CUtensorMap map_xlo;
+    // Layer-1 centroids retriever (LIDER_ROUTE_CORE): one core model over the
+    // centroids, laid out like one cluster of ncl entries
+    uint64_t* ckeys = nullptr;          // L x ncl sorted keys of the centroids
+    int32_t* cpos = nullptr;            // L x ncl centroid index of each entry
+    lider::RmiRoot* croot = nullptr;    // L
+    lider::RmiLeaf* cleaf = nullptr;    // L x F
     cudaMemPool_t pool = nullptr;
     lider_tuning tune{128, 128, 64, 1};    // launch shapes (lider_autotune; defaults measured on mid)
     int score_blocks_per_sm = 1;
@@ -183,8 +193,11 @@ __device__ __forceinline__ float float_from_order(uint32_t u) {
 // ------------------------------------------------------------ re-scaling ----
 // r = (x - x_min) / (x_max - x_min) * (n_c - 1), Sec. 5.1; the difference is an
 // exact integer, converted to FP64 with round-to-nearest; a key below x_min
-// gives r < 0 (query keys only).
-__device__ __forceinline__ double rescale_key(uint64_t x, uint64_t x_min, uint64_t x_max, int64_t n_c) {
+// gives r < 0 (query keys only).  raw: no re-scaling, r = x rounded to FP64
+// (the ablation of Sec. 7.4).
+__device__ __forceinline__ double rescale_key(uint64_t x, uint64_t x_min, uint64_t x_max, int64_t n_c,
+                                              bool raw = false) {
+    if (raw) return __ull2double_rn(x);
     if (x_max == x_min) return 0.0;
     double num = (x >= x_min) ? __ull2double_rn(x - x_min) : -__ull2double_rn(x_min - x);
     double den = __ull2double_rn(x_max - x_min);
@@ -208,6 +221,60 @@ __device__ __forceinline__ int64_t rmi_predict(double a, double b, double r, int
     return (int64_t)p;
 }
 
+// ---------------------------------------------------- locate and expand ----
+// One sorted array K[0..n_c) of a core model and a query key x: the RMI
+// prediction ph (Sec. 5.2), the exact lower bound p searched inside the
+// leaf's error window, with a fallback to the whole array when the window
+// misses it (counted in fb), and the expansion window [s, s + T),
+// T = min(R, n_c): the first T picks of the greedy merge of the left run
+// (p-1, p-2, ...) and the right run (p, p+1, ...) by dist_e, ties to the left
+// (Sec. 4.2, Sec. 4.3).  Both runs are non-decreasing in dist_e (Lemmas 2
+// and 3), so the picks form one window [p - t, p - t + T) whose t is found by
+// a co-rank search: the largest count such that left item t-1 precedes right
+// item T-t.  n_c >= 1.
+struct Located {
+    int64_t ph, p, s, T;
+};
+
+__device__ __forceinline__ Located locate_window(const uint64_t* __restrict__ K, int64_t n_c, const RmiRoot& rt,
+                                                 const RmiLeaf* __restrict__ leaves, int F, uint64_t x, int64_t R,
+                                                 int m, int beta, int B, bool raw, unsigned& fb) {
+    Located o;
+    const double r = rescale_key(x, rt.x_min, rt.x_max, n_c, raw);
+    const int f = rmi_leaf(rt.a0, rt.b0, r, F, n_c);
+    const RmiLeaf lf = leaves[f];
+    o.ph = rmi_predict(lf.a, lf.b, r, n_c);
+    int64_t lo = max((int64_t)0, o.ph + lf.lo);
+    int64_t hi = min(n_c, o.ph + (int64_t)lf.hi + 1);
+    if (lo > hi) lo = hi = min(max(o.ph, (int64_t)0), n_c);
+    // the lower bound lies in [lo, hi] iff K[lo-1] < x and K[hi] >= x
+    if (lo > 0 && K[lo - 1] >= x) {
+        ++fb;
+        hi = lo - 1;
+        lo = 0;
+    } else if (hi < n_c && K[hi] < x) {
+        ++fb;
+        lo = hi + 1;
+        hi = n_c;
+    }
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (K[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    o.p = lo;
+    o.T = min(R, n_c);
+    const int64_t nr = n_c - o.p;
+    int64_t tlo = max((int64_t)0, o.T - nr), thi = min(o.T, o.p);
+    while (tlo < thi) {
+        const int64_t mid = (tlo + thi + 1) >> 1;
+        const uint64_t dl = dist_code(K[o.p - mid], x, m, beta, B);
+        const uint64_t dr = dist_code(K[o.p + (o.T - mid)], x, m, beta, B);
+        if (dl <= dr) tlo = mid; else thi = mid - 1;
+    }
+    o.s = o.p - tlo;
+    return o;
+}
+
 // ------------------------------------------------------- small utilities ----
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -228,7 +295,7 @@ int make_tensor_map8(CUtensorMap* map, const void* base, int64_t rows, int d, in
 // Power of two s with s * amax in [2^13, 2^14) (1 for amax == 0): scaled
 // values stay in FP16's normal range with room below its maximum.
 float f16_scale_host(float amax);
-int launch_pack(const double* t, int64_t n, int L, int m, int beta, int64_t row_offset,
+int launch_pack(const double* t, int64_t n, int L, int m, int beta, int hash_kind, int64_t row_offset,
                 int64_t key_stride_row, int64_t key_stride_arr, uint64_t* keys,
                 unsigned long long* n_boundary, unsigned long long* n_clamped, cudaStream_t s);
 

@@ -9,7 +9,7 @@
 //               into work items of up to G pairs of one cluster
 //   4. locate   locate_kernel, one thread per (pair, array): re-scale the key
 //               (Sec. 5.1), two-stage RMI prediction (Sec. 5.2), clamp
-//               (Sec. 7.3), lower bound searched inside the leaf's recorded
+//               (Sec. 7.4), lower bound searched inside the leaf's recorded
 //               error window (with a counted fallback outside it), then the
 //               bi-directional expansion window of Sec. 4 by co-rank search
 //   5. score    tensor score modes: mark_kernel (each pair's candidate
@@ -53,7 +53,10 @@ enum {
     CNT_ROUTE_FALLBACK,
     CNT_BOUNDS,     // accesses skipped by a failed bounds check (must stay 0)
     CNT_SEL_OVERFLOW,  // queries whose guarded candidate band did not fit (result may be inexact)
-    CNT_SLOTS = 9
+    CNT_OOR,        // RMI predictions at either end of the array (Sec. 7.4)
+    CNT_LE,         // RMI predictions more than k from the lower bound
+    CNT_OOR_LE,     // both
+    CNT_SLOTS = 12
 };
 
 // cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per (kernel, device,
@@ -173,7 +176,8 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
 // Tensor paths: t = (a_h . q + b_h) / W for all queries and projections as
 // 3xTF32 tiles (queries x projections).  Where floor(t) could depend on the
 // tile's error (t within its bound, or within 1e-6 for the boundary count, of
-// an integer) the (query, projection) goes to a list, and hash_recheck_kernel
+// an integer; of zero for hyperplane hashes, whose b is 0 and W 1) the
+// (query, projection) goes to a list, and hash_recheck_kernel
 // recomputes t with exactly the arithmetic of the SIMT hashing kernel
 // (sequential Dot2 over k, finished in FP64), so the query keys are the same
 // bit for bit on every score path.
@@ -196,6 +200,7 @@ struct HashEpi {
     int32_t* n_recheck;
     float W, guard;             // guard: kTcGuard
     int nq, H;
+    bool hyper;                 // hyperplane hashes: only the sign of t decides
     int q, h0;
     float qn;
     __device__ void begin(int u, int row) {
@@ -216,7 +221,7 @@ struct HashEpi {
             // |tf - t| <= (tile error + FP32 rounding of acc + b) / W + rounding of the division
             const float eps = __fdiv_rn(guard * qn * a_norm[h] + 4.f * 0x1p-24f * (fabsf(acc) + fabsf(bh)), W) +
                               0x1p-22f * fabsf(tf);
-            const float dist = fabsf(tf - rintf(tf));
+            const float dist = hyper ? fabsf(tf) : fabsf(tf - rintf(tf));
             t[(int64_t)q * H + h] = (double)tf;
             if (!(dist > 1.01f * eps + 1.1e-6f)) recheck[atomicAdd(n_recheck, 1)] = q * H + h;
         }
@@ -560,14 +565,16 @@ __global__ void group_fill_kernel(const int32_t* __restrict__ route, int64_t npa
 }
 
 // ----------------------------------------------------------------- locate --
-// One thread per (pair, array l).  pair = q * c + probe.
-__global__ void locate_kernel(Geometry g, int64_t npairs, int c, int R,
+// One thread per (pair, array l).  pair = q * c + probe.  Also counts the RMI
+// diagnostics of Sec. 7.4: predictions at either end of the array (OOR) and
+// predictions more than k from the lower bound (LE).
+__global__ void locate_kernel(Geometry g, int64_t npairs, int c, int R, int k,
                               const int32_t* __restrict__ route, const uint64_t* __restrict__ qkeys,
                               int32_t* __restrict__ wstart, int32_t* __restrict__ wlen,
                               int32_t* __restrict__ trace_pstar, int32_t* __restrict__ trace_wstart,
                               int32_t* __restrict__ trace_wlen, unsigned long long* __restrict__ counters) {
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned fb = 0, empty = 0;
+    unsigned fb = 0, empty = 0, oor = 0, le = 0, both = 0;
     if (gid < npairs * g.L) {
         const int64_t pair = gid / g.L;
         const int l = (int)(gid % g.L);
@@ -576,65 +583,149 @@ __global__ void locate_kernel(Geometry g, int64_t npairs, int c, int R,
         const int64_t base = g.cl_off[j];
         const int64_t n_c = g.cl_off[j + 1] - base;
         const uint64_t x = qkeys[q * g.L + l];
-        int64_t p = 0, s = 0, T = 0;
+        Located o{0, 0, 0, 0};
         if (n_c == 0) {
             empty = (l == 0);
         } else {
-            const uint64_t* K = g.keys + (int64_t)l * g.n + base;
-            const RmiRoot rt = g.root[(int64_t)j * g.L + l];
-            const double r = rescale_key(x, rt.x_min, rt.x_max, n_c);
-            const int f = rmi_leaf(rt.a0, rt.b0, r, g.F, n_c);
-            const RmiLeaf lf = g.leaf[((int64_t)j * g.L + l) * g.F + f];
-            const int64_t ph = rmi_predict(lf.a, lf.b, r, n_c);
-            int64_t lo = max((int64_t)0, ph + lf.lo);
-            int64_t hi = min(n_c, ph + (int64_t)lf.hi + 1);
-            if (lo > hi) lo = hi = min(max(ph, (int64_t)0), n_c);
-            // the lower bound lies in [lo, hi] iff K[lo-1] < x and K[hi] >= x
-            if (lo > 0 && K[lo - 1] >= x) {
-                ++fb;
-                hi = lo - 1;
-                lo = 0;
-            } else if (hi < n_c && K[hi] < x) {
-                ++fb;
-                lo = hi + 1;
-                hi = n_c;
-            }
-            while (lo < hi) {
-                const int64_t mid = (lo + hi) >> 1;
-                if (K[mid] < x) lo = mid + 1; else hi = mid;
-            }
-            p = lo;
-            // Bi-directional expansion: the first T = min(R, n_c) picks of the
-            // greedy merge of the left run (p-1, p-2, ...) and the right run
-            // (p, p+1, ...) by dist_e, ties to the left.  Both runs are
-            // non-decreasing in dist_e (Lemmas 2 and 3), so the picks form one
-            // window [p - t, p - t + T) with t found by co-rank search: t is
-            // the largest count such that left item t-1 precedes right item T-t.
-            T = min((int64_t)R, n_c);
-            const int64_t nr = n_c - p;
-            int64_t tlo = max((int64_t)0, T - nr), thi = min(T, p);
-            while (tlo < thi) {
-                const int64_t mid = (tlo + thi + 1) >> 1;
-                const uint64_t dl = dist_code(K[p - mid], x, g.m, g.beta, g.B);
-                const uint64_t dr = dist_code(K[p + (T - mid)], x, g.m, g.beta, g.B);
-                if (dl <= dr) tlo = mid; else thi = mid - 1;
-            }
-            s = p - tlo;
+            o = locate_window(g.keys + (int64_t)l * g.n + base, n_c, g.root[(int64_t)j * g.L + l],
+                              g.leaf + ((int64_t)j * g.L + l) * g.F, g.F, x, R, g.m, g.beta, g.B, g.raw_keys != 0,
+                              fb);
+            oor = (o.ph == 0 || o.ph == n_c - 1);
+            le = (o.ph - o.p > k || o.p - o.ph > k);
+            both = oor & le;
         }
-        wstart[gid] = (int32_t)s;
-        wlen[gid] = (int32_t)T;
-        if (trace_pstar) trace_pstar[gid] = (int32_t)p;
-        if (trace_wstart) trace_wstart[gid] = (int32_t)s;
-        if (trace_wlen) trace_wlen[gid] = (int32_t)T;
+        wstart[gid] = (int32_t)o.s;
+        wlen[gid] = (int32_t)o.T;
+        if (trace_pstar) trace_pstar[gid] = (int32_t)o.p;
+        if (trace_wstart) trace_wstart[gid] = (int32_t)o.s;
+        if (trace_wlen) trace_wlen[gid] = (int32_t)o.T;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        fb += __shfl_xor_sync(0xffffffffu, fb, o);
-        empty += __shfl_xor_sync(0xffffffffu, empty, o);
+    for (int s = 16; s > 0; s >>= 1) {
+        fb += __shfl_xor_sync(0xffffffffu, fb, s);
+        empty += __shfl_xor_sync(0xffffffffu, empty, s);
+        oor += __shfl_xor_sync(0xffffffffu, oor, s);
+        le += __shfl_xor_sync(0xffffffffu, le, s);
+        both += __shfl_xor_sync(0xffffffffu, both, s);
     }
     if ((threadIdx.x & 31) == 0) {
         if (fb) atomicAdd(&counters[CNT_FALLBACK], (unsigned long long)fb);
         if (empty) atomicAdd(&counters[CNT_EMPTY], (unsigned long long)empty);
+        if (oor) atomicAdd(&counters[CNT_OOR], (unsigned long long)oor);
+        if (le) atomicAdd(&counters[CNT_LE], (unsigned long long)le);
+        if (both) atomicAdd(&counters[CNT_OOR_LE], (unsigned long long)both);
     }
+}
+
+// ------------------------------------------------- Layer-1 route (core) --
+// The centroids retriever of Sec. 3.2 as a core model: the query key of each
+// array is located in the sorted centroid keys of that array and expanded by
+// Rc = r0 * c positions (locate_window, as in every cluster), the union of the
+// L windows is scored exactly with the arithmetic of the exact scan
+// (sequential Dot2 of q.mu finished in FP64, minus |mu|^2/2), and the c best,
+// ties to the lower index, become the query's route.  One warp per query;
+// lane l handles array l.  Per warp, shared memory holds the union as a
+// bitmap (words), then as an ascending list of up to cap centroids with
+// their scores.  Every window holds min(Rc, n_clusters) >= c distinct
+// centroids, so the union never has fewer than c.
+__global__ void route_core_kernel(Geometry g, const uint64_t* __restrict__ ckeys, const int32_t* __restrict__ cpos,
+                                  const RmiRoot* __restrict__ croot, const RmiLeaf* __restrict__ cleaf,
+                                  const uint64_t* __restrict__ qkeys, const float* __restrict__ Q, int64_t nq,
+                                  int c, int Rc, int words, int cap, int warp_bytes, int32_t* __restrict__ route,
+                                  int32_t* __restrict__ trace_route) {
+    extern __shared__ __align__(16) unsigned char route_smem[];
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= nq) return;                                   // whole warps leave together
+    unsigned char* base = route_smem + (size_t)(threadIdx.x >> 5) * warp_bytes;
+    uint32_t* bm = reinterpret_cast<uint32_t*>(base);
+    int32_t* list = reinterpret_cast<int32_t*>(base + align_up_dev((size_t)words * 4, 16));
+    double* sc = reinterpret_cast<double*>(base + align_up_dev((size_t)words * 4, 16) + align_up_dev((size_t)cap * 4, 16));
+    const int ncl = g.ncl;
+    for (int w = lane; w < words; w += 32) bm[w] = 0u;
+    __syncwarp();
+    unsigned fb = 0;
+    for (int l = lane; l < g.L; l += 32) {
+        const Located o = locate_window(ckeys + (int64_t)l * ncl, ncl, croot[l], cleaf + (int64_t)l * g.F, g.F,
+                                        qkeys[q * g.L + l], Rc, g.m, g.beta, g.B, g.raw_keys != 0, fb);
+        const int32_t* P = cpos + (int64_t)l * ncl;
+        for (int64_t i = o.s; i < o.s + o.T; ++i) {
+            const int j = P[i];
+            atomicOr(&bm[j >> 5], 1u << (j & 31));
+        }
+    }
+    __syncwarp();
+    // the union as an ascending list
+    int n = 0;
+    for (int w0 = 0; w0 < words; w0 += 32) {
+        const int w = w0 + lane;
+        const uint32_t bits = w < words ? bm[w] : 0u;
+        const int cnt = __popc(bits);
+        int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int pos = n + incl - cnt;
+        for (uint32_t b = bits; b && pos < cap; b &= b - 1) list[pos++] = w * 32 + (__ffs(b) - 1);
+        n += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    n = min(n, cap);
+    __syncwarp();
+    const float* qv = Q + q * g.d;
+    for (int i = lane; i < n; i += 32) {
+        const int j = list[i];
+        const float* mu = g.C + (int64_t)j * g.d;
+        Dot2 acc{0.f, 0.f};
+        for (int t = 0; t < g.d; ++t) dot2_step(acc, qv[t], mu[t]);
+        double v = __dadd_rn(dot2_value(acc), -g.half_norm[j]);
+        if (v != v) v = -INFINITY;
+        sc[i] = v;
+    }
+    __syncwarp();
+    // c rounds of a warp arg-max over the entries after the previous pick
+    double ps = INFINITY;
+    int pj = -1;
+    for (int r = 0; r < c; ++r) {
+        double best = -INFINITY;
+        int bj = 0x7fffffff;
+        for (int i = lane; i < n; i += 32) {
+            const double v = sc[i];
+            const int j = list[i];
+            const bool after = (v < ps) || (v == ps && j > pj);
+            if (after && (v > best || (v == best && j < bj))) { best = v; bj = j; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+            if (ov > best || (ov == best && oj < bj)) { best = ov; bj = oj; }
+        }
+        if (bj >= ncl) bj = 0;                             // unreachable: the union holds >= c centroids
+        ps = best;
+        pj = bj;
+        if (lane == 0) {
+            route[q * c + r] = bj;
+            if (trace_route) trace_route[q * c + r] = bj;
+        }
+    }
+}
+
+// Launch shape of route_core_kernel: per-warp shared memory for the bitmap,
+// the list and its FP64 scores (n_clusters <= 16384 keeps one warp under
+// 200 KB), up to 8 warps per block.
+struct RouteCoreShape {
+    int Rc, words, cap, warp_bytes, wpb;
+};
+
+RouteCoreShape route_core_shape(const Geometry& g, int r0, int c) {
+    RouteCoreShape s;
+    s.Rc = r0 * c;
+    const int T = std::min(s.Rc, g.ncl);
+    s.words = (int)cdiv(g.ncl, 32);
+    s.cap = (int)std::min<int64_t>(g.ncl, (int64_t)T * g.L);
+    s.warp_bytes = (int)align_up(align_up((size_t)s.words * 4, 16) + align_up((size_t)s.cap * 4, 16) +
+                                     (size_t)s.cap * 8, 16);
+    s.wpb = std::max(1, std::min(8, (200 * 1024) / s.warp_bytes));
+    return s;
 }
 
 // ------------------------------------------------------------------ score --
@@ -2115,6 +2206,7 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         he.recheck = w.hrecheck;
         he.n_recheck = w.n_hrecheck;
         he.W = (float)g.W;
+        he.hyper = g.hash_kind == LIDER_HASH_HYPERPLANE;
         he.guard = kTcGuard;
         he.nq = (int)nq;
         he.H = g.H;
@@ -2130,7 +2222,7 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
     } else {
         if ((rc = launch_hash_t(Q, nq, g.d, g.A, g.bproj, g.H, g.W, w.tq, st))) return rc;
     }
-    if ((rc = launch_pack(w.tq, nq, g.L, g.m, g.beta, 0, g.L, 1, w.qkeys, &w.counters[CNT_QBOUNDARY],
+    if ((rc = launch_pack(w.tq, nq, g.L, g.m, g.beta, g.hash_kind, 0, g.L, 1, w.qkeys, &w.counters[CNT_QBOUNDARY],
                           &w.counters[CNT_QCLAMPED], st)))
         return rc;
     if (tr && tr->qkeys)
@@ -2167,6 +2259,16 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
                                                               tr ? tr->route : nullptr);
     LIDER_LAUNCH_CHECK("topc_kernel");
     }
+    if (ix->params.route_kind == LIDER_ROUTE_CORE) {
+        // Layer-1 centroids retriever: replaces the route of the exact scan
+        // (whose per-query error bounds the tensor paths still use)
+        const RouteCoreShape rcs = route_core_shape(g, ix->params.r0, c);
+        if ((rc = smem_attr((const void*)route_core_kernel, rcs.wpb * rcs.warp_bytes))) return rc;
+        route_core_kernel<<<(unsigned)cdiv(nq, rcs.wpb), (unsigned)(32 * rcs.wpb), (size_t)rcs.wpb * rcs.warp_bytes,
+                            st>>>(g, ix->ckeys, ix->cpos, ix->croot, ix->cleaf, w.qkeys, Q, nq, c, rcs.Rc, rcs.words,
+                                  rcs.cap, rcs.warp_bytes, w.route, tr ? tr->route : nullptr);
+        LIDER_LAUNCH_CHECK("route_core_kernel");
+    }
     // 3. group
     if ((rc = mark(LIDER_PHASE_GROUP))) return rc;
     const int G = std::max(1, std::min(kMaxGroup, (96 * 1024) / (g.d * 4)));
@@ -2180,7 +2282,7 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
     // 4. locate + expand
     if ((rc = mark(LIDER_PHASE_LOCATE))) return rc;
     locate_kernel<<<(unsigned)cdiv(np * g.L, 256), 256, 0, st>>>(
-        g, np, c, R, w.route, w.qkeys, w.wstart, w.wlen, tr ? tr->pstar : nullptr, tr ? tr->wstart : nullptr,
+        g, np, c, R, k, w.route, w.qkeys, w.wstart, w.wlen, tr ? tr->pstar : nullptr, tr ? tr->wstart : nullptr,
         tr ? tr->wlen : nullptr, w.counters);
     LIDER_LAUNCH_CHECK("locate_kernel");
     // 5. candidate union, exact scores and per-pair top-k
@@ -2370,6 +2472,9 @@ int read_stats(const Workspace& w, int64_t nq, int c, lider_search_stats* stats,
     stats->tc_tiles = tiles;
     stats->route_fallback = (int64_t)h[CNT_ROUTE_FALLBACK];
     stats->select_overflow = (int64_t)h[CNT_SEL_OVERFLOW];
+    stats->rmi_oor = (int64_t)h[CNT_OOR];
+    stats->rmi_le = (int64_t)h[CNT_LE];
+    stats->rmi_oor_le = (int64_t)h[CNT_OOR_LE];
     return LIDER_OK;
 }
 

@@ -30,18 +30,22 @@ class LiderError(RuntimeError):
 
 
 SCORE_TENSOR, SCORE_SIMT, SCORE_BF16, SCORE_F16, SCORE_FP8 = 0, 1, 2, 3, 4
+HASH_PSTABLE, HASH_HYPERPLANE = 0, 1
+ROUTE_EXACT, ROUTE_CORE = 0, 1
 
 
 class Params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("m", ctypes.c_int32), ("rmi_leaves", ctypes.c_int32),
                 ("r0", ctypes.c_int32), ("B", ctypes.c_int32), ("hash_kind", ctypes.c_int32),
-                ("W", ctypes.c_double), ("score_mode", ctypes.c_int32), ("rerank", ctypes.c_int32)]
+                ("W", ctypes.c_double), ("score_mode", ctypes.c_int32), ("rerank", ctypes.c_int32),
+                ("route_kind", ctypes.c_int32), ("raw_keys", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in
                 ("n_queries", "pairs", "candidates", "qkey_boundary", "qkey_clamped",
-                 "locate_fallback", "empty_pairs", "tc_tiles", "route_fallback", "select_overflow")]
+                 "locate_fallback", "empty_pairs", "tc_tiles", "route_fallback", "select_overflow",
+                 "rmi_oor", "rmi_le", "rmi_oor_le")]
 
     def as_dict(self) -> dict:
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
@@ -155,14 +159,18 @@ class Index:
     """A LIDER index resident on the current CUDA device (owns its memory)."""
 
     def __init__(self, corpus: torch.Tensor, centroids: torch.Tensor, A: torch.Tensor, b: torch.Tensor,
-                 L: int, m: int, W: float, rmi_leaves: int, r0: int = 2, B: int = 1,
-                 score_mode: int = SCORE_TENSOR, rerank: int = 0, stream=None):
+                 L: int, m: int, W: float, rmi_leaves: int, r0: int = 2, B: int | None = None,
+                 score_mode: int = SCORE_TENSOR, rerank: int = 0, hash_kind: int = HASH_PSTABLE,
+                 route_kind: int = ROUTE_EXACT, raw_keys: bool = False, stream=None):
+        """B defaults to 1 for p-stable hashes and 3 for hyperplane bits."""
+        if B is None:
+            B = 3 if hash_kind == HASH_HYPERPLANE else 1
         corpus = _dev(corpus, torch.float32, "corpus")
         centroids = _dev(centroids, torch.float32, "centroids")
         A = _dev(A, torch.float32, "A")
         b = _dev(b, torch.float32, "b")
         n, d = corpus.shape
-        p = Params(L, m, rmi_leaves, r0, B, 0, float(W), score_mode, rerank)
+        p = Params(L, m, rmi_leaves, r0, B, hash_kind, float(W), score_mode, rerank, route_kind, int(raw_keys))
         h = ctypes.c_void_p()
         _check(_lib.lider_build(corpus.data_ptr(), n, d, centroids.data_ptr(), centroids.shape[0],
                                 A.data_ptr(), b.data_ptr(), ctypes.byref(p), _stream_ptr(stream),
@@ -172,6 +180,7 @@ class Index:
         self.L, self.m, self.W, self.rmi_leaves, self.r0, self.B = L, m, W, rmi_leaves, r0, B
         self.score_mode = score_mode
         self.rerank = rerank
+        self.hash_kind, self.route_kind, self.raw_keys = hash_kind, route_kind, bool(raw_keys)
 
     @property
     def handle(self) -> int:

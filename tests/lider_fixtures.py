@@ -29,7 +29,8 @@ def workload(name: str, nq: int | None = None):
 
 
 def oracle_index(cfg, X, C, A, b):
-    return O.build_index(X, C, A, b, cfg["L"], cfg["m"], cfg["W"], cfg["leaves"], B=cfg["B"])
+    return O.build_index(X, C, A, b, cfg["L"], cfg["m"], cfg["W"], cfg["leaves"], B=cfg["B"],
+                         hash_kind=cfg.get("hash_kind", O.HASH_PSTABLE), raw_keys=bool(cfg.get("raw_keys", 0)))
 
 
 def gpu_index(cfg, X, C, A, b, device="cuda"):
@@ -38,7 +39,9 @@ def gpu_index(cfg, X, C, A, b, device="cuda"):
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
     return lider.Index(t(X), t(C), t(A), t(b), L=cfg["L"], m=cfg["m"], W=cfg["W"],
                        rmi_leaves=cfg["leaves"], r0=cfg["r0"], B=cfg["B"],
-                       score_mode=cfg.get("score_mode", lider.SCORE_TENSOR), rerank=cfg.get("rerank", 0))
+                       score_mode=cfg.get("score_mode", lider.SCORE_TENSOR), rerank=cfg.get("rerank", 0),
+                       hash_kind=cfg.get("hash_kind", lider.HASH_PSTABLE),
+                       route_kind=cfg.get("route_kind", lider.ROUTE_EXACT), raw_keys=bool(cfg.get("raw_keys", 0)))
 
 
 def check_topk(gpu_ids, gpu_sc, ref_ids, ref_sc, X, Q, rows=None):
