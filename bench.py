@@ -44,6 +44,7 @@ LAUNCHES_PER_SEARCH = {"tensor": 18, "simt": 10, "bf16": 18, "f16": 18, "fp8": 1
 MODES = {"tensor": 0, "simt": 1, "bf16": 2, "f16": 3, "fp8": 4}
 DTYPES = {"tensor": "f32", "simt": "f32", "bf16": "bf16", "f16": "f16", "fp8": "fp8-e4m3"}
 FP8_PER_BF16 = 4.5 / 2.25     # nominal dense FP8 / BF16 tensor rate (B300)
+F16_TC_DRAM_BYTES_PER_TILE = (674.204928e6 + 305.550592e6) / 3782   # ncu, tc_score_kernel<KindF16>
 
 
 def workload_desc(cfg) -> dict:
@@ -239,6 +240,24 @@ def run_reference(args, cfg):
 
 # ------------------------------------------------------------------ lider ---
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest x over all ranks of the job (its time is its slowest
+    rank's); x itself when there is one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(nq_per_rank: int, steps: int, world: int, job_ms: float) -> float:
+    """Queries/s of the whole job: every rank searches its own replica of the
+    index over nq_per_rank queries per step (replicas: weak scaling)."""
+    return world * nq_per_rank * steps / (job_ms / 1e3)
+
+
 def run_lider(args, cfg):
     import torch
     import torch.distributed as dist
@@ -314,11 +333,8 @@ def run_lider(args, cfg):
     phase_ms = {name: float(np.mean([sum(evs[s][ci][i].elapsed_time(evs[s][ci][i + 1]) for ci in range(len(chunks)))
                                      for s in range(args.steps)]))
                 for i, name in enumerate(lider.PHASES)}
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = world * nq * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, dev)
+    value = job_throughput(nq, args.steps, world, total_ms)
 
     # the same search captured once into a CUDA graph and replayed
     graph = None
@@ -358,12 +374,8 @@ def run_lider(args, cfg):
     te = time.perf_counter()
     for _ in range(args.steps):
         search_host_all()
-    e2e_s = time.perf_counter() - te
-    if world > 1:
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e_value = world * nq * args.steps / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - te, dev)
+    e2e_value = job_throughput(nq, args.steps, world, e2e_s * 1e3)
 
     cand = stats["candidates"]
     d = cfg["d"]
@@ -389,13 +401,21 @@ def run_lider(args, cfg):
             peak = bf16
             psrc = f"{src}: bf16 burst" + (" (FP16 has the same dense rate)" if args.score == "f16" else "")
         achieved = tc_flop / score_s / 1e12
+        # DRAM bytes per launch: ncu dram__bytes_read.sum + dram__bytes_write.sum of
+        # tc_score_kernel<KindF16> at 400,000 x 768 / 4,000 queries (3,782 tiles), per
+        # tile, times this launch's tiles (FP16 mode only; other kinds not captured)
+        traffic = F16_TC_DRAM_BYTES_PER_TILE * stats["tc_tiles"] if args.score == "f16" else None
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "kernel": "tc_score_kernel",
+                    "frac": achieved / peak, "traffic": traffic, "kernel": "tc_score_kernel",
                     "peak_source": psrc,
                     "tensor_flop_per_launch": tc_flop,
                     "tiles_per_launch": stats["tc_tiles"],
                     "useful_flop_per_launch": useful_flop,
                     "useful_tflops": useful_flop / score_s / 1e12}
+        if traffic is not None:
+            roofline["traffic_note"] = "scaled by tiles from an ncu capture at 400,000 x 768, 4,000 queries"
+            roofline["dram_gbs_vs_hbm"] = {"achieved": traffic / score_s / 1e9, "peak": hbm,
+                                           "frac": traffic / score_s / 1e9 / hbm}
     else:
         peak = fp32_simt_peak_tflops(clk.get("sm_max_mhz") or 2032.0)
         achieved = useful_flop / score_s / 1e12
@@ -520,16 +540,120 @@ def call_size(idx, nq, k, c, want):
     return sub
 
 
+def fp64_knn(X, Q, k: int, chunk: int = 262_144) -> np.ndarray:
+    """Ground truth for recall: the k largest FP64 inner products of each
+    query over the whole corpus (ties to the lower id), computed on the GPU
+    with plain FP64 matrix products, chunk by chunk."""
+    import torch
+    dev = torch.device("cuda", 0)
+    q = torch.from_numpy(np.ascontiguousarray(Q)).to(dev, torch.float64)
+    best_s = torch.full((len(Q), 0), 0.0, dtype=torch.float64, device=dev)
+    best_i = torch.zeros((len(Q), 0), dtype=torch.int64, device=dev)
+    for lo in range(0, X.shape[0], chunk):
+        x = torch.from_numpy(np.ascontiguousarray(X[lo:lo + chunk])).to(dev, torch.float64)
+        s = q @ x.T
+        ids = torch.arange(lo, lo + x.shape[0], device=dev).expand(len(Q), -1)
+        cs, ci = torch.cat([best_s, s], 1), torch.cat([best_i, ids], 1)
+        # order by score descending, then id ascending (stable sort on id first)
+        o1 = torch.argsort(ci, dim=1, stable=True)
+        cs, ci = cs.gather(1, o1), ci.gather(1, o1)
+        o2 = torch.argsort(-cs, dim=1, stable=True)[:, :k]
+        best_s, best_i = cs.gather(1, o2), ci.gather(1, o2)
+    return best_i.cpu().numpy()
+
+
+def recall10(found: np.ndarray, truth: np.ndarray) -> float:
+    return float(np.mean([len(set(f[:10].tolist()) & set(t[:10].tolist())) / 10 for f, t in zip(found, truth)]))
+
+
+def run_variants(args, cfg):
+    """Fidelity variants of the paper on the workload, each built as its own
+    index in the FP16 exact mode and searched over every query: the plain
+    method (p-stable hashkeys, exact routing scan, re-scaled keys), hyperplane
+    hashkeys (Sec. 4.1, one bit per hash, B = 3), the Layer-1 centroids
+    retriever (Sec. 3.2), and RMIs on raw keys (the Sec. 7.4 ablation).
+    Reports queries/s, recall@10 against FP64 brute force on a query sample
+    and against the plain method on all queries, and the RMI diagnostics of
+    Sec. 7.4 (OOR, LE = more than k from the lower bound, and both)."""
+    import torch
+
+    from paper_2205_00970_b300 import lider
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    X, Q, C, A, b = load_inputs(cfg)
+    k, c, nq = cfg["k"], cfg["c"], cfg["nq"]
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    Qd, Xd, Cd = t(Q), t(X), t(C)
+    variants = {
+        "plain": {},
+        "hyperplane": dict(hash_kind=lider.HASH_HYPERPLANE, m=args.hyper_m),
+        "core_route": dict(route_kind=lider.ROUTE_CORE),
+        "raw_keys": dict(raw_keys=True),
+    }
+    ns = min(args.precision_sample * 16, nq)
+    truth = fp64_knn(X, Q[:ns], 10)
+    out = {}
+    for name, v in variants.items():
+        m = v.get("m", cfg["m"])
+        if m != cfg["m"]:
+            from paper_2205_00970_b300 import synth
+            A2, b2 = synth.projections(cfg["seed"], cfg["L"], m, cfg["d"], cfg["W"])
+        else:
+            A2, b2 = A, b
+        idx = lider.Index(Xd, Cd, t(A2), t(b2), L=cfg["L"], m=m, W=cfg["W"], rmi_leaves=cfg["leaves"],
+                          r0=cfg["r0"], score_mode=lider.SCORE_F16, hash_kind=v.get("hash_kind", 0),
+                          route_kind=v.get("route_kind", 0), raw_keys=v.get("raw_keys", False),
+                          B=3 if v.get("hash_kind", 0) == lider.HASH_HYPERPLANE else cfg["B"])
+        ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
+        sc = torch.empty((nq, k), dtype=torch.float32, device=dev)
+        for _ in range(args.warmup):
+            idx.search(Qd, k, c, out=(ids, sc))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            idx.search(Qd, k, c, out=(ids, sc))
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        _, _, st = idx.search(Qd, k, c, stats=True)
+        out[name] = {"ids": ids.cpu().numpy(), "ms": ms, "stats": st, "m": m}
+        idx.free()
+        del idx, ids, sc
+        torch.cuda.empty_cache()
+    plain = out["plain"]["ids"]
+    report = {}
+    for name, r in out.items():
+        st = r["stats"]
+        triples = st["pairs"] * cfg["L"] - st["empty_pairs"] * cfg["L"]
+        report[name] = {
+            "queries_per_s": nq / (r["ms"] / 1e3), "ms_per_batch": r["ms"], "m": r["m"],
+            "recall_at_10_vs_fp64_knn": recall10(r["ids"][:ns], truth),
+            "recall_at_10_vs_plain": recall10(r["ids"], plain),
+            "candidates_per_query": st["candidates"] / nq,
+            "rmi": {"triples": triples, "oor": st["rmi_oor"], "le": st["rmi_le"], "oor_and_le": st["rmi_oor_le"],
+                    "le_threshold": k, "locate_fallback": st["locate_fallback"]},
+        }
+    line = {
+        "metric": "fidelity variants: queries/s, recall@10, RMI OOR/LE", "n_gpus": 1, "steps": args.steps,
+        "data": "synthetic", "config": workload_desc(cfg), "score_mode": "f16",
+        "sample": f"recall vs FP64 brute force on the first {ns} queries; vs plain on all {nq}",
+        "variants": report,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_precision(args, cfg):
     """Precision mode: the workload's corpus indexed once per dtype (the exact
     FP16-guarded mode, the served BF16 and FP8-e4m3 forms with a shortlist of
     rerank * k re-ranked in FP32), every query searched; reports per dtype the
     queries/s, recall@10 against the exact mode, and, on a query sample
-    against FP64 brute force (the oracle's exact_knn), recall@10 and the
-    largest relative error of the returned scores."""
+    against FP64 brute force (fp64_knn), recall@10 and the largest relative
+    error of the returned scores."""
     import torch
 
-    from oracle import lider_oracle as O
     from paper_2205_00970_b300 import lider
 
     dev = torch.device("cuda", 0)
@@ -566,7 +690,7 @@ def run_precision(args, cfg):
         torch.cuda.empty_cache()
     plain = out["f16"]["ids"][:, :10]
     ns = min(args.precision_sample, nq)
-    truth = O.exact_knn(X, Q[:ns], 10)[0]
+    truth = fp64_knn(X, Q[:ns], 10)
     q64 = Q[:ns].astype(np.float64)
     report = {}
     for name, r in out.items():
@@ -583,7 +707,7 @@ def run_precision(args, cfg):
             "storage": {"f16": "FP16 (power-of-two scaled), guarded, exact", "bf16": "BF16",
                         "fp8": "FP8 e4m3, one scale per row (max|x|/448)"}[name],
             "recall_at_10_vs_plain": float(agree),
-            "recall_at_10_vs_fp64_knn": O.recall_at(r["ids"][:ns], truth, 10),
+            "recall_at_10_vs_fp64_knn": recall10(r["ids"][:ns], truth),
             "max_rel_score_error_vs_fp64": err,
         }
     line = {
@@ -618,6 +742,9 @@ def main():
     ap.add_argument("--precision", action="store_true",
                     help="per-dtype recall and score error (f16 exact, bf16 and fp8 served forms)")
     ap.add_argument("--precision-sample", type=int, default=16)
+    ap.add_argument("--variants", action="store_true",
+                    help="fidelity variants: hyperplane hashkeys, Layer-1 centroids retriever, raw-key RMIs")
+    ap.add_argument("--hyper-m", type=int, default=32, help="--variants: bits per hyperplane hashkey")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
@@ -644,6 +771,8 @@ def main():
         return run_serve(args, cfg)
     if args.precision:
         return run_precision(args, cfg)
+    if args.variants:
+        return run_variants(args, cfg)
     return run_lider(args, cfg)
 
 

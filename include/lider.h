@@ -199,7 +199,7 @@ int lider_build(const float* corpus, int64_t n, int32_t d,
                 const lider_params* params, void* stream, lider_index** out);
 
 /* Batched k-NN search (Sec. 3.3.2 "When using LIDER for ANN queries"; Sec. 6).
- *   queries     device, nq x d FP32;
+ *   queries     device, nq x d FP32, starting on a 16-byte boundary;
  *   k           results per query (1..LIDER_MAX_K); R = r0*k, L*R <= LIDER_MAX_LR;
  *   c           clusters probed per query, c_0 (1..min(n_clusters, LIDER_MAX_C));
  *   out_ids     device, nq x k int64: corpus row ids, best first (score

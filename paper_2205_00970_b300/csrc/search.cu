@@ -620,13 +620,16 @@ __global__ void locate_kernel(Geometry g, int64_t npairs, int c, int R, int k,
 // The centroids retriever of Sec. 3.2 as a core model: the query key of each
 // array is located in the sorted centroid keys of that array and expanded by
 // Rc = r0 * c positions (locate_window, as in every cluster), the union of the
-// L windows is scored exactly with the arithmetic of the exact scan
-// (sequential Dot2 of q.mu finished in FP64, minus |mu|^2/2), and the c best,
-// ties to the lower index, become the query's route.  One warp per query;
-// lane l handles array l.  Per warp, shared memory holds the union as a
+// L windows is scored in compensated arithmetic (q.mu by Dot2 over each
+// lane's share of the row, the lanes merged by TwoSum, finished in FP64,
+// minus |mu|^2/2; about twice FP32 precision, like the exact scan), and the
+// c best, ties to the lower index, become the query's route.  One warp per
+// query; lane l handles array l.  Per warp, shared memory holds the union as a
 // bitmap (words), then as an ascending list of up to cap centroids with
-// their scores.  Every window holds min(Rc, n_clusters) >= c distinct
+// their score keys.  Every window holds min(Rc, n_clusters) >= c distinct
 // centroids, so the union never has fewer than c.
+constexpr int kRouteQ4 = 8;       // query float4 groups per lane held in registers (d <= 1024)
+
 __global__ void route_core_kernel(Geometry g, const uint64_t* __restrict__ ckeys, const int32_t* __restrict__ cpos,
                                   const RmiRoot* __restrict__ croot, const RmiLeaf* __restrict__ cleaf,
                                   const uint64_t* __restrict__ qkeys, const float* __restrict__ Q, int64_t nq,
@@ -639,7 +642,8 @@ __global__ void route_core_kernel(Geometry g, const uint64_t* __restrict__ ckeys
     unsigned char* base = route_smem + (size_t)(threadIdx.x >> 5) * warp_bytes;
     uint32_t* bm = reinterpret_cast<uint32_t*>(base);
     int32_t* list = reinterpret_cast<int32_t*>(base + align_up_dev((size_t)words * 4, 16));
-    double* sc = reinterpret_cast<double*>(base + align_up_dev((size_t)words * 4, 16) + align_up_dev((size_t)cap * 4, 16));
+    uint64_t* key = reinterpret_cast<uint64_t*>(base + align_up_dev((size_t)words * 4, 16) +
+                                                align_up_dev((size_t)cap * 4, 16));
     const int ncl = g.ncl;
     for (int w = lane; w < words; w += 32) bm[w] = 0u;
     __syncwarp();
@@ -671,31 +675,88 @@ __global__ void route_core_kernel(Geometry g, const uint64_t* __restrict__ ckeys
     }
     n = min(n, cap);
     __syncwarp();
+    // Scores across the warp, two candidates at a time: lane t holds the
+    // query's float4 groups t, t + 32, ... in registers (d <= 1024), loads the
+    // same groups of both centroid rows at once and runs Dot2 over them in
+    // order; the 32 lanes' Dot2 pairs are merged by TwoSum in a fixed
+    // butterfly order (FP32: the FP64 rate of this GPU is low), and lane 0
+    // finishes in FP64.  Each score is kept as an order-preserving 64-bit key.
+    // Larger d: one candidate at a time with warp_exact_score.
     const float* qv = Q + q * g.d;
-    for (int i = lane; i < n; i += 32) {
-        const int j = list[i];
-        const float* mu = g.C + (int64_t)j * g.d;
-        Dot2 acc{0.f, 0.f};
-        for (int t = 0; t < g.d; ++t) dot2_step(acc, qv[t], mu[t]);
-        double v = __dadd_rn(dot2_value(acc), -g.half_norm[j]);
+    const int d4 = g.d >> 2;
+    auto merge_lanes = [&](Dot2& a) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const float os = __shfl_xor_sync(0xffffffffu, a.s, o);
+            const float oc = __shfl_xor_sync(0xffffffffu, a.c, o);
+            const float t = __fadd_rn(a.s, os);
+            const float z = __fadd_rn(t, -a.s);
+            const float e = __fadd_rn(__fadd_rn(a.s, -__fadd_rn(t, -z)), __fadd_rn(os, -z));   // a.s + os = t + e
+            a.s = t;
+            a.c = __fadd_rn(__fadd_rn(a.c, oc), e);
+        }
+    };
+    auto key_of = [](double v) -> uint64_t {       // ascending in v; NaN as -inf
         if (v != v) v = -INFINITY;
-        sc[i] = v;
+        const uint64_t u = (uint64_t)__double_as_longlong(v);
+        return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+    };
+    if (d4 <= 32 * kRouteQ4) {
+        float4 qr[kRouteQ4];
+#pragma unroll
+        for (int u = 0; u < kRouteQ4; ++u) {
+            const int t = lane + 32 * u;
+            qr[u] = t < d4 ? __ldg(reinterpret_cast<const float4*>(qv) + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        for (int i = 0; i < n; i += 2) {
+            const int j0 = list[i], j1 = i + 1 < n ? list[i + 1] : j0;
+            const float4* m0 = reinterpret_cast<const float4*>(g.C + (int64_t)j0 * g.d);
+            const float4* m1 = reinterpret_cast<const float4*>(g.C + (int64_t)j1 * g.d);
+            float4 a[kRouteQ4], b[kRouteQ4];
+#pragma unroll
+            for (int u = 0; u < kRouteQ4; ++u) {
+                const int t = lane + 32 * u;
+                if (t < d4) { a[u] = __ldg(m0 + t); b[u] = __ldg(m1 + t); }
+            }
+            Dot2 acc0{0.f, 0.f}, acc1{0.f, 0.f};
+#pragma unroll
+            for (int u = 0; u < kRouteQ4; ++u) {
+                if (lane + 32 * u < d4) {
+                    dot2_step(acc0, qr[u].x, a[u].x); dot2_step(acc0, qr[u].y, a[u].y);
+                    dot2_step(acc0, qr[u].z, a[u].z); dot2_step(acc0, qr[u].w, a[u].w);
+                    dot2_step(acc1, qr[u].x, b[u].x); dot2_step(acc1, qr[u].y, b[u].y);
+                    dot2_step(acc1, qr[u].z, b[u].z); dot2_step(acc1, qr[u].w, b[u].w);
+                }
+            }
+            merge_lanes(acc0);
+            merge_lanes(acc1);
+            if (lane == 0) {
+                key[i] = key_of(__dadd_rn(dot2_value(acc0), -g.half_norm[j0]));
+                if (i + 1 < n) key[i + 1] = key_of(__dadd_rn(dot2_value(acc1), -g.half_norm[j1]));
+            }
+        }
+    } else {
+        for (int i = 0; i < n; ++i) {
+            const int j = list[i];
+            const double v = warp_exact_score(qv, g.C + (int64_t)j * g.d, g.d, g.half_norm[j]);
+            if (lane == 0) key[i] = key_of(v);
+        }
     }
     __syncwarp();
     // c rounds of a warp arg-max over the entries after the previous pick
-    double ps = INFINITY;
+    // (score key descending, index ascending)
+    uint64_t ps = ~0ull;
     int pj = -1;
     for (int r = 0; r < c; ++r) {
-        double best = -INFINITY;
+        uint64_t best = 0ull;
         int bj = 0x7fffffff;
         for (int i = lane; i < n; i += 32) {
-            const double v = sc[i];
+            const uint64_t v = key[i];
             const int j = list[i];
             const bool after = (v < ps) || (v == ps && j > pj);
             if (after && (v > best || (v == best && j < bj))) { best = v; bj = j; }
         }
         for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const uint64_t ov = __shfl_xor_sync(0xffffffffu, best, o);
             const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
             if (ov > best || (ov == best && oj < bj)) { best = ov; bj = oj; }
         }
@@ -1706,6 +1767,57 @@ __device__ void block_bitonic32(uint32_t* key, int n) {
     }
 }
 
+// The r-th smallest (1-based, counting repeats) of n 32-bit words word(i),
+// i < n, by a block-wide radix select: four passes over 8-bit digits, most
+// significant first, each counting the words that match the digits chosen so
+// far in a 256-bin shared histogram.  All threads call it; r in [1, n].
+template <class Word>
+__device__ uint32_t block_kth_smallest(Word word, int n, int r, uint32_t* hist256, int* s_pick) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    uint32_t prefix = 0u, mask = 0u;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int b = tid; b < 256; b += blockDim.x) hist256[b] = 0u;
+        __syncthreads();
+        for (int i = tid; i < n; i += blockDim.x) {
+            const uint32_t v = word(i);
+            if ((v & mask) == prefix) atomicAdd(&hist256[(v >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (tid < 32) {
+            // lane owns bins 8 lane .. 8 lane + 7; the first bin whose running
+            // count reaches r holds the r-th smallest
+            uint32_t cnt[8], sum = 0u;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) { cnt[b] = hist256[8 * lane + b]; sum += cnt[b]; }
+            uint32_t incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            uint32_t run = incl - sum;
+            const bool mine = run < (uint32_t)r && incl >= (uint32_t)r;
+            if (mine) {
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    if (run + cnt[b] >= (uint32_t)r) {
+                        s_pick[0] = 8 * lane + b;
+                        s_pick[1] = r - (int)run;
+                        break;
+                    }
+                    run += cnt[b];
+                }
+            }
+        }
+        __syncthreads();
+        prefix |= (uint32_t)s_pick[0] << shift;
+        mask |= 255u << shift;
+        r = s_pick[1];
+        __syncthreads();                           // every thread has read s_pick
+    }
+    return prefix;
+}
+
 __global__ void __launch_bounds__(512) select_hist_kernel(
         DenseArgs da, int c, int ks, const float* __restrict__ qguard, const float* __restrict__ qbound, int guarded,
         int so, int64_t* __restrict__ out_ids, float* __restrict__ out_scores, int32_t* __restrict__ trace_ucount,
@@ -1715,6 +1827,8 @@ __global__ void __launch_bounds__(512) select_hist_kernel(
     __shared__ PairRow s_pr[LIDER_MAX_C];
     __shared__ int s_total, s_cnt, s_bt, s_band;
     __shared__ float s_thr;
+    __shared__ uint32_t s_rhist[256];              // radix select
+    __shared__ int s_pick[2];
     const int64_t q = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31;
     for (int b = tid; b < kHistBins; b += blockDim.x) hist[b] = 0u;
@@ -1783,9 +1897,9 @@ __global__ void __launch_bounds__(512) select_hist_kernel(
 #pragma unroll
         for (int j = 0; j < kKeep; ++j) hist[tid * kKeep + j] = ts[j] == -INFINITY ? 0xffffffffu : ~float_order(ts[j]);
         __syncthreads();
-        block_bitonic32(hist, next_pow2_dev(kKeep * bd));
+        // the need-th best kept maximum (need <= kKeep * bd words)
+        const uint32_t wk = block_kth_smallest([&](int i) { return hist[i]; }, kKeep * bd, need, s_rhist, s_pick);
         if (tid == 0) {
-            const uint32_t wk = hist[need - 1];
             float thr = -INFINITY;                 // fewer chunks with candidates than need: take all
             if (wk != 0xffffffffu) {
                 thr = float_from_order(~wk);
@@ -1930,6 +2044,42 @@ __global__ void __launch_bounds__(512) select_hist_kernel(
         return;
     }
     const int n = min(s_cnt, kHistCand);
+    if (guarded && need > 0 && n > 0) {
+        // Guarded modes: the list is every key within twice the error bound of
+        // the need-th best approximate score, in no particular order (the
+        // re-score orders it).  The need-th best score comes from a radix
+        // select over the keys' score words; only a band longer than the list
+        // (counted as an overflow) needs the sort below to keep the best `so`.
+        const int keep0 = min(need, n);
+        const uint32_t wk = block_kth_smallest([&](int i) { return (uint32_t)(cand[i] >> 32); }, n, keep0,
+                                               s_rhist, s_pick);
+        const float t = float_from_order(~wk) - 2.f * qguard[q];
+        if (tid == 0) { s_band = 0; s_bt = 0; }
+        __syncthreads();
+        int mine = 0;
+        for (int r = tid; r < n; r += blockDim.x)
+            mine += float_from_order(~(uint32_t)(cand[r] >> 32)) >= t;
+        if (mine) atomicAdd(&s_band, mine);
+        __syncthreads();
+        const int band = s_band;
+        if (band <= so) {
+            for (int r = tid; r < n; r += blockDim.x) {
+                const uint64_t kv = cand[r];
+                const float sc = float_from_order(~(uint32_t)(kv >> 32));
+                if (sc >= t) {
+                    const int slot = atomicAdd(&s_bt, 1);
+                    out_ids[q * so + slot] = (int64_t)(uint32_t)kv;
+                    out_scores[q * so + slot] = sc;
+                }
+            }
+            for (int r = band + tid; r < so; r += blockDim.x) {
+                out_ids[q * so + r] = -1;
+                out_scores[q * so + r] = -INFINITY;
+            }
+            return;
+        }
+        __syncthreads();
+    }
     const int SP = n > 1 ? next_pow2_dev(n) : 1;
     for (int u = n + tid; u < SP; u += blockDim.x) cand[u] = ~0ull;
     __syncthreads();
@@ -2167,6 +2317,8 @@ int check_search_args(const lider_index* ix, const float* Q, int64_t nq, int k, 
                                   "queries per call");
     if (!buffers) return LIDER_OK;
     if (nq > 0 && (!Q || !ids || !scores)) return fail(LIDER_EINVAL, "lider_search: NULL buffer");
+    if (reinterpret_cast<uintptr_t>(Q) % 16 != 0)
+        return fail(LIDER_EINVAL, "lider_search: queries must start on a 16-byte boundary");
     int dev = -1;
     LIDER_CUDA_TRY(cudaGetDevice(&dev));
     if (dev != ix->device) return fail(LIDER_EINVAL, "lider_search: index lives on another device");

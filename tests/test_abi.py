@@ -56,6 +56,9 @@ def test_binding_loads_and_validates_without_gpu():
         (10, 12, 2, lider.Params(4, 8, 16, 2, 1, 0, 1.0, 2, 0), "d % 8"),
         (10, 8, 2, lider.Params(4, 8, 16, 2, 1, 0, 1.0, 2, 65), "rerank"),
         (10, 8, 2, lider.Params(4, 8, 16, 2, 1, 0, 1.0, 4, 0), "d % 16"),
+        (10, 8, 2, lider.Params(4, 8, 16, 2, 1, 0, 1.0, 0, 0, 2, 0), "route_kind"),
+        (10, 8, 2, lider.Params(4, 8, 16, 2, 1, 0, 1.0, 0, 0, 0, 2), "raw_keys"),
+        (10, 8, 2, lider.Params(4, 65, 16, 2, 1, 1, 1.0, 1, 0), "m must be <= 64"),
     ]:
         rc = lider.raw_call("lider_build", dummy, n, d, dummy, ncl, dummy, dummy, ctypes.byref(pp), None,
                             ctypes.byref(out))
@@ -66,6 +69,13 @@ def test_binding_loads_and_validates_without_gpu():
     rc = lider.raw_call("lider_build", dummy, 10, 8, dummy, 2, dummy, dummy,
                         ctypes.byref(lider.Params(17, 8, 16, 2, 1, 0, 1.0, 0, 0)), None, ctypes.byref(out))
     assert rc == -4 and "L <= 16" in lider.last_error()
+    rc = lider.raw_call("lider_build", dummy, 10, 8, dummy, 20000, dummy, dummy,
+                        ctypes.byref(lider.Params(4, 8, 16, 2, 1, 0, 1.0, 0, 0, 1, 0)), None, ctypes.byref(out))
+    assert rc == -4 and "16384" in lider.last_error()
+    # hyperplane bits: B is limited by one bit per element, not floor(64/m)
+    rc = lider.raw_call("lider_build", dummy, 10, 8, dummy, 2, dummy, dummy,
+                        ctypes.byref(lider.Params(4, 8, 16, 2, 57, 1, 1.0, 0, 0)), None, ctypes.byref(out))
+    assert rc == -1 and "<= 56" in lider.last_error()
 
 
 def test_tuning_abi_validates_without_gpu():

@@ -207,6 +207,13 @@ def test_invalid_search_arguments(tiny):
         with pytest.raises(lider.LiderError) as e:
             g.search(Qd, k, c)
         assert e.value.code == code
+    # queries not on a 16-byte boundary are refused before any launch
+    import ctypes
+    ids = torch.empty((3, 10), dtype=torch.int64, device="cuda")
+    sc = torch.empty((3, 10), dtype=torch.float32, device="cuda")
+    rc = lider.raw_call("lider_search", g.handle, Qd.data_ptr() + 4, 3, 10, 1, ids.data_ptr(), sc.data_ptr(),
+                        None, None)
+    assert rc == -1 and "16-byte" in lider.last_error()
 
 
 @pytest.mark.parametrize("mode,min_agree", [(2, 0.995), (4, 0.98)], ids=["bf16", "fp8"])
