@@ -282,14 +282,37 @@ __global__ void qnorm_kernel(const float* __restrict__ Q, int64_t nq, int d, flo
 }
 
 // Exact q.mu - |mu|^2/2 by one warp: per-lane Dot2, lanes summed in FP64.
+// Merge the 32 lanes' Dot2 accumulators (s, c) by TwoSum in a fixed
+// butterfly order; every lane ends with the same pair.  FP32 throughout: the
+// FP64 rate of this GPU is a small fraction of its FP32 rate.
+__device__ __forceinline__ void warp_merge_dot2(Dot2& a) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const float os = __shfl_xor_sync(0xffffffffu, a.s, o);
+        const float oc = __shfl_xor_sync(0xffffffffu, a.c, o);
+        const float t = __fadd_rn(a.s, os);
+        const float z = __fadd_rn(t, -a.s);
+        const float e = __fadd_rn(__fadd_rn(a.s, -__fadd_rn(t, -z)), __fadd_rn(os, -z));   // a.s + os = t + e
+        a.s = t;
+        a.c = __fadd_rn(__fadd_rn(a.c, oc), e);
+    }
+}
+
+// Order-preserving 64-bit key of an FP64 score (ascending in the score;
+// NaN as -inf), compared with integer instructions.
+__device__ __forceinline__ uint64_t score_key(double v) {
+    uint64_t u = (uint64_t)__double_as_longlong(v);
+    if ((u & 0x7fffffffffffffffull) > 0x7ff0000000000000ull) u = 0xfff0000000000000ull;   // NaN -> -inf
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
 __device__ __forceinline__ double warp_exact_score(const float* __restrict__ q, const float* __restrict__ mu, int d,
                                                    double half_norm) {
     const int lane = threadIdx.x & 31;
     Dot2 acc{0.f, 0.f};
-    for (int i = lane; i < d; i += 32) dot2_step(acc, q[i], mu[i]);
-    double v = dot2_value(acc);
-    for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return __dadd_rn(v, -half_norm);
+#pragma unroll 8
+    for (int i = lane; i < d; i += 32) dot2_step(acc, __ldg(q + i), __ldg(mu + i));
+    warp_merge_dot2(acc);
+    return __dadd_rn(dot2_value(acc), -half_norm);
 }
 
 // Guard formula of a score mode (see candidate_guard).
@@ -411,10 +434,12 @@ __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __re
     // When each of the c best approximate scores leads the next one by more
     // than twice the error bound, the exact scores have the same order and no
     // other centroid can enter: the route is the shortlist's head.
+    // (the gap is rounded down and twice the guard is exact, so a gap that
+    // passes also passes in exact arithmetic)
     bool clear = true;
     for (int r = 0; r < c; ++r) {
         const float next = r + 1 < n_first ? av[r + 1] : -INFINITY;     // c + 1 <= ncl: av[c] is the next
-        if (!((double)av[r] - (double)next > 2.0 * (double)guard)) clear = false;
+        if (!(__fsub_rd(av[r], next) > 2.f * guard)) clear = false;
     }
     if (clear) {
         if (lane == 0) {
@@ -442,25 +467,30 @@ __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __re
     }
     // exact scores of the shortlist, then the c best
     double ex[LIDER_MAX_C + kRouteExtra];
-    for (int r = 0; r < nsl; ++r) ex[r] = warp_exact_score(qv, C + (int64_t)sl[r] * d, d, half_norm[sl[r]]);
+    uint64_t ek[LIDER_MAX_C + kRouteExtra];
+    for (int r = 0; r < nsl; ++r) {
+        ex[r] = warp_exact_score(qv, C + (int64_t)sl[r] * d, d, half_norm[sl[r]]);
+        ek[r] = score_key(ex[r]);
+    }
     int out[LIDER_MAX_C];
     double e_c = -INFINITY;
     {
-        double pe = INFINITY;
+        // c rounds over the shortlist on integer keys (score descending, index ascending)
+        uint64_t pe = ~0ull;
         int pjj = -1;
         for (int r = 0; r < c; ++r) {
-            double best = -INFINITY;
-            int bj = 0x7fffffff;
+            uint64_t best = 0ull;
+            int bj = 0x7fffffff, bt = 0;
             for (int t = 0; t < nsl; ++t) {
-                const double v = ex[t];
+                const uint64_t v = ek[t];
                 const int j = sl[t];
                 const bool after = (v < pe) || (v == pe && j > pjj);
-                if (after && (v > best || (v == best && j < bj))) { best = v; bj = j; }
+                if (after && (v > best || (v == best && j < bj))) { best = v; bj = j; bt = t; }
             }
             out[r] = bj;
             pe = best;
             pjj = bj;
-            e_c = best;
+            e_c = ex[bt];
         }
     }
     if (nsl < ncl && (double)a_out + (double)guard >= e_c) {
@@ -619,21 +649,30 @@ __global__ void locate_kernel(Geometry g, int64_t npairs, int c, int R, int k,
 // ------------------------------------------------- Layer-1 route (core) --
 // The centroids retriever of Sec. 3.2 as a core model: the query key of each
 // array is located in the sorted centroid keys of that array and expanded by
-// Rc = r0 * c positions (locate_window, as in every cluster), the union of the
-// L windows is scored in compensated arithmetic (q.mu by Dot2 over each
-// lane's share of the row, the lanes merged by TwoSum, finished in FP64,
-// minus |mu|^2/2; about twice FP32 precision, like the exact scan), and the
-// c best, ties to the lower index, become the query's route.  One warp per
-// query; lane l handles array l.  Per warp, shared memory holds the union as a
-// bitmap (words), then as an ascending list of up to cap centroids with
-// their score keys.  Every window holds min(Rc, n_clusters) >= c distinct
-// centroids, so the union never has fewer than c.
-constexpr int kRouteQ4 = 8;       // query float4 groups per lane held in registers (d <= 1024)
-
+// Rc = r0 * c positions (locate_window, as in every cluster); the c best of
+// the union of the L windows by the routing score, ties to the lower index,
+// become the query's route.  Every window holds min(Rc, n_clusters) >= c
+// distinct centroids, so the union never has fewer than c.
+//
+// Scores come from the routing step's score matrix, which this path computes
+// for every query anyway (its per-query error bounds serve the tensor score
+// modes):
+//   - exact FP64 scores (SIMT mode, S_exact): the c best candidates directly;
+//   - tensor-core scores within `guard` of the exact ones (S_approx): the c+1
+//     best candidates by approximate score; when every gap among them exceeds
+//     twice the guard, their order is the exact one; otherwise every candidate
+//     within twice the guard of the c-th approximate score (a set that holds
+//     the exact c best) is re-scored exactly (warp_exact_score) and the c best
+//     taken from those.
+// One warp per query; lane l handles array l.  Per warp, shared memory holds
+// the union as a bitmap (words), then as an ascending list of up to cap
+// centroids, with an FP32 and a 64-bit score key per entry.
 __global__ void route_core_kernel(Geometry g, const uint64_t* __restrict__ ckeys, const int32_t* __restrict__ cpos,
                                   const RmiRoot* __restrict__ croot, const RmiLeaf* __restrict__ cleaf,
                                   const uint64_t* __restrict__ qkeys, const float* __restrict__ Q, int64_t nq,
-                                  int c, int Rc, int words, int cap, int warp_bytes, int32_t* __restrict__ route,
+                                  int c, int Rc, int words, int cap, int warp_bytes,
+                                  const float* __restrict__ S_approx, float guard_scale,
+                                  const double* __restrict__ S_exact, int32_t* __restrict__ route,
                                   int32_t* __restrict__ trace_route) {
     extern __shared__ __align__(16) unsigned char route_smem[];
     const int lane = threadIdx.x & 31;
@@ -641,9 +680,12 @@ __global__ void route_core_kernel(Geometry g, const uint64_t* __restrict__ ckeys
     if (q >= nq) return;                                   // whole warps leave together
     unsigned char* base = route_smem + (size_t)(threadIdx.x >> 5) * warp_bytes;
     uint32_t* bm = reinterpret_cast<uint32_t*>(base);
-    int32_t* list = reinterpret_cast<int32_t*>(base + align_up_dev((size_t)words * 4, 16));
-    uint64_t* key = reinterpret_cast<uint64_t*>(base + align_up_dev((size_t)words * 4, 16) +
-                                                align_up_dev((size_t)cap * 4, 16));
+    base += align_up_dev((size_t)words * 4, 16);
+    int32_t* list = reinterpret_cast<int32_t*>(base);
+    base += align_up_dev((size_t)cap * 4, 16);
+    float* av = reinterpret_cast<float*>(base);
+    base += align_up_dev((size_t)cap * 4, 16);
+    uint64_t* key = reinterpret_cast<uint64_t*>(base);
     const int ncl = g.ncl;
     for (int w = lane; w < words; w += 32) bm[w] = 0u;
     __syncwarp();
@@ -675,83 +717,15 @@ __global__ void route_core_kernel(Geometry g, const uint64_t* __restrict__ ckeys
     }
     n = min(n, cap);
     __syncwarp();
-    // Scores across the warp, two candidates at a time: lane t holds the
-    // query's float4 groups t, t + 32, ... in registers (d <= 1024), loads the
-    // same groups of both centroid rows at once and runs Dot2 over them in
-    // order; the 32 lanes' Dot2 pairs are merged by TwoSum in a fixed
-    // butterfly order (FP32: the FP64 rate of this GPU is low), and lane 0
-    // finishes in FP64.  Each score is kept as an order-preserving 64-bit key.
-    // Larger d: one candidate at a time with warp_exact_score.
-    const float* qv = Q + q * g.d;
-    const int d4 = g.d >> 2;
-    auto merge_lanes = [&](Dot2& a) {
-        for (int o = 16; o > 0; o >>= 1) {
-            const float os = __shfl_xor_sync(0xffffffffu, a.s, o);
-            const float oc = __shfl_xor_sync(0xffffffffu, a.c, o);
-            const float t = __fadd_rn(a.s, os);
-            const float z = __fadd_rn(t, -a.s);
-            const float e = __fadd_rn(__fadd_rn(a.s, -__fadd_rn(t, -z)), __fadd_rn(os, -z));   // a.s + os = t + e
-            a.s = t;
-            a.c = __fadd_rn(__fadd_rn(a.c, oc), e);
-        }
-    };
-    auto key_of = [](double v) -> uint64_t {       // ascending in v; NaN as -inf
-        if (v != v) v = -INFINITY;
-        const uint64_t u = (uint64_t)__double_as_longlong(v);
-        return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
-    };
-    if (d4 <= 32 * kRouteQ4) {
-        float4 qr[kRouteQ4];
-#pragma unroll
-        for (int u = 0; u < kRouteQ4; ++u) {
-            const int t = lane + 32 * u;
-            qr[u] = t < d4 ? __ldg(reinterpret_cast<const float4*>(qv) + t) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        for (int i = 0; i < n; i += 2) {
-            const int j0 = list[i], j1 = i + 1 < n ? list[i + 1] : j0;
-            const float4* m0 = reinterpret_cast<const float4*>(g.C + (int64_t)j0 * g.d);
-            const float4* m1 = reinterpret_cast<const float4*>(g.C + (int64_t)j1 * g.d);
-            float4 a[kRouteQ4], b[kRouteQ4];
-#pragma unroll
-            for (int u = 0; u < kRouteQ4; ++u) {
-                const int t = lane + 32 * u;
-                if (t < d4) { a[u] = __ldg(m0 + t); b[u] = __ldg(m1 + t); }
-            }
-            Dot2 acc0{0.f, 0.f}, acc1{0.f, 0.f};
-#pragma unroll
-            for (int u = 0; u < kRouteQ4; ++u) {
-                if (lane + 32 * u < d4) {
-                    dot2_step(acc0, qr[u].x, a[u].x); dot2_step(acc0, qr[u].y, a[u].y);
-                    dot2_step(acc0, qr[u].z, a[u].z); dot2_step(acc0, qr[u].w, a[u].w);
-                    dot2_step(acc1, qr[u].x, b[u].x); dot2_step(acc1, qr[u].y, b[u].y);
-                    dot2_step(acc1, qr[u].z, b[u].z); dot2_step(acc1, qr[u].w, b[u].w);
-                }
-            }
-            merge_lanes(acc0);
-            merge_lanes(acc1);
-            if (lane == 0) {
-                key[i] = key_of(__dadd_rn(dot2_value(acc0), -g.half_norm[j0]));
-                if (i + 1 < n) key[i + 1] = key_of(__dadd_rn(dot2_value(acc1), -g.half_norm[j1]));
-            }
-        }
-    } else {
-        for (int i = 0; i < n; ++i) {
-            const int j = list[i];
-            const double v = warp_exact_score(qv, g.C + (int64_t)j * g.d, g.d, g.half_norm[j]);
-            if (lane == 0) key[i] = key_of(v);
-        }
-    }
-    __syncwarp();
-    // c rounds of a warp arg-max over the entries after the previous pick
-    // (score key descending, index ascending)
-    uint64_t ps = ~0ull;
-    int pj = -1;
-    for (int r = 0; r < c; ++r) {
+    // rounds of a warp arg-max over the entries after the previous pick
+    // (key descending, centroid index ascending); rounds beyond the list give -1
+    auto pick = [&](uint64_t& ps, int& pj, auto skip) {
         uint64_t best = 0ull;
         int bj = 0x7fffffff;
         for (int i = lane; i < n; i += 32) {
             const uint64_t v = key[i];
             const int j = list[i];
+            if (skip(v)) continue;
             const bool after = (v < ps) || (v == ps && j > pj);
             if (after && (v > best || (v == best && j < bj))) { best = v; bj = j; }
         }
@@ -760,19 +734,72 @@ __global__ void route_core_kernel(Geometry g, const uint64_t* __restrict__ ckeys
             const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
             if (ov > best || (ov == best && oj < bj)) { best = ov; bj = oj; }
         }
-        if (bj >= ncl) bj = 0;                             // unreachable: the union holds >= c centroids
         ps = best;
         pj = bj;
-        if (lane == 0) {
-            route[q * c + r] = bj;
-            if (trace_route) trace_route[q * c + r] = bj;
+    };
+    auto none = [](uint64_t) { return false; };
+    auto absent = [](uint64_t v) { return v == 0ull; };
+    int out[LIDER_MAX_C];
+    if (S_exact) {
+        for (int i = lane; i < n; i += 32) key[i] = score_key(S_exact[q * ncl + list[i]]);
+        __syncwarp();
+        uint64_t ps = ~0ull;
+        int pj = -1;
+        for (int r = 0; r < c; ++r) { pick(ps, pj, none); out[r] = pj; }
+    } else {
+        const float* srow = S_approx + q * ncl;
+        for (int i = lane; i < n; i += 32) {
+            float v = srow[list[i]];
+            if (v != v) v = -INFINITY;
+            av[i] = v;
+            key[i] = (uint64_t)float_order(v);
+        }
+        __syncwarp();
+        const float* qv = Q + q * g.d;
+        float qn2 = 0.f;
+        for (int t = lane; t < g.d; t += 32) qn2 = fmaf(qv[t], qv[t], qn2);
+        for (int o = 16; o > 0; o >>= 1) qn2 += __shfl_xor_sync(0xffffffffu, qn2, o);
+        const float guard = guard_scale * sqrtf(qn2);
+        // the c + 1 best approximate scores (the (c+1)-th is -inf when n == c)
+        uint64_t ps = ~0ull;
+        int pj = -1;
+        float a[LIDER_MAX_C + 1];
+        for (int r = 0; r < c + 1; ++r) {
+            if (r == n) { a[r] = -INFINITY; break; }
+            pick(ps, pj, none);
+            if (r < c) out[r] = pj;
+            a[r] = float_from_order((uint32_t)ps);
+        }
+        bool clear = true;
+        for (int r = 0; r < c; ++r)
+            if (!(__fsub_rd(a[r], a[r + 1]) > 2.f * guard)) clear = false;
+        if (!clear) {
+            // exact scores of the band; entries outside it are left out (key 0)
+            const float t = __fsub_rd(a[c - 1], 2.f * guard);
+            for (int i = 0; i < n; ++i) {
+                const bool in = av[i] >= t;
+                double v = 0.0;
+                if (in) v = warp_exact_score(qv, g.C + (int64_t)list[i] * g.d, g.d, g.half_norm[list[i]]);
+                if (lane == 0) key[i] = in ? score_key(v) : 0ull;
+            }
+            __syncwarp();
+            ps = ~0ull;
+            pj = -1;
+            for (int r = 0; r < c; ++r) { pick(ps, pj, absent); out[r] = pj; }
+        }
+    }
+    if (lane == 0) {
+        for (int r = 0; r < c; ++r) {
+            const int j = out[r] < ncl ? out[r] : 0;       // unreachable: the union holds >= c centroids
+            route[q * c + r] = j;
+            if (trace_route) trace_route[q * c + r] = j;
         }
     }
 }
 
 // Launch shape of route_core_kernel: per-warp shared memory for the bitmap,
-// the list and its FP64 scores (n_clusters <= 16384 keeps one warp under
-// 200 KB), up to 8 warps per block.
+// the list, its FP32 scores and 64-bit keys (n_clusters <= 16384 keeps one
+// warp under 216 KB), up to 8 warps per block.
 struct RouteCoreShape {
     int Rc, words, cap, warp_bytes, wpb;
 };
@@ -783,9 +810,9 @@ RouteCoreShape route_core_shape(const Geometry& g, int r0, int c) {
     const int T = std::min(s.Rc, g.ncl);
     s.words = (int)cdiv(g.ncl, 32);
     s.cap = (int)std::min<int64_t>(g.ncl, (int64_t)T * g.L);
-    s.warp_bytes = (int)align_up(align_up((size_t)s.words * 4, 16) + align_up((size_t)s.cap * 4, 16) +
+    s.warp_bytes = (int)align_up(align_up((size_t)s.words * 4, 16) + 2 * align_up((size_t)s.cap * 4, 16) +
                                      (size_t)s.cap * 8, 16);
-    s.wpb = std::max(1, std::min(8, (200 * 1024) / s.warp_bytes));
+    s.wpb = std::max(1, std::min(8, (216 * 1024) / s.warp_bytes));
     return s;
 }
 
@@ -1752,21 +1779,6 @@ __global__ void __launch_bounds__(256) select_query_kernel(DenseArgs da, int c, 
 constexpr int kHistBins = 2048;
 constexpr int kHistCand = 2048;
 
-__device__ void block_bitonic32(uint32_t* key, int n) {
-    for (int size = 2; size <= n; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = threadIdx.x; i < n / 2; i += blockDim.x) {
-                const int lo_i = 2 * stride * (i / stride) + (i % stride);
-                const int hi_i = lo_i + stride;
-                const bool up = (lo_i & size) == 0;
-                const uint32_t x0 = key[lo_i], x1 = key[hi_i];
-                if ((x0 > x1) == up) { key[lo_i] = x1; key[hi_i] = x0; }
-            }
-            __syncthreads();
-        }
-    }
-}
-
 // The r-th smallest (1-based, counting repeats) of n 32-bit words word(i),
 // i < n, by a block-wide radix select: four passes over 8-bit digits, most
 // significant first, each counting the words that match the digits chosen so
@@ -2418,7 +2430,10 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         if ((rc = smem_attr((const void*)route_core_kernel, rcs.wpb * rcs.warp_bytes))) return rc;
         route_core_kernel<<<(unsigned)cdiv(nq, rcs.wpb), (unsigned)(32 * rcs.wpb), (size_t)rcs.wpb * rcs.warp_bytes,
                             st>>>(g, ix->ckeys, ix->cpos, ix->croot, ix->cleaf, w.qkeys, Q, nq, c, rcs.Rc, rcs.words,
-                                  rcs.cap, rcs.warp_bytes, w.route, tr ? tr->route : nullptr);
+                                  rcs.cap, rcs.warp_bytes,
+                                  tensor_route ? reinterpret_cast<const float*>(w.rscore) : nullptr,
+                                  kTcGuard * ix->max_cnorm, tensor_route ? nullptr : w.rscore, w.route,
+                                  tr ? tr->route : nullptr);
         LIDER_LAUNCH_CHECK("route_core_kernel");
     }
     // 3. group
