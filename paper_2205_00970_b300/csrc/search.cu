@@ -56,7 +56,8 @@ enum {
     CNT_OOR,        // RMI predictions at either end of the array (Sec. 7.4)
     CNT_LE,         // RMI predictions more than k from the lower bound
     CNT_OOR_LE,     // both
-    CNT_SLOTS = 12
+    CNT_QORDER,     // queries placed by primary_order_kernel
+    CNT_SLOTS = 13
 };
 
 // cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per (kernel, device,
@@ -270,18 +271,22 @@ __global__ void __launch_bounds__(32) hash_recheck_kernel(const float* __restric
     }
 }
 
-// |q| per query (warp per query, FP64 sum of squares, rounded up).
+// |q| per query, rounded up (warp per query).
 __global__ void qnorm_kernel(const float* __restrict__ Q, int64_t nq, int d, float* __restrict__ out) {
     const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (q >= nq) return;
-    double s = 0.0;
-    for (int i = lane; i < d; i += 32) s = fma((double)Q[q * d + i], (double)Q[q * d + i], s);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) out[q] = __double2float_ru(sqrt(s));
+    // every step rounds up and every term is non-negative, so the FP32 sum
+    // bounds the exact sum of squares from above (no FP64: its rate is low here)
+    float s = 0.f;
+    for (int i = lane; i < d; i += 32) {
+        const float v = Q[q * d + i];
+        s = __fmaf_ru(v, v, s);
+    }
+    for (int o = 16; o > 0; o >>= 1) s = __fadd_ru(s, __shfl_xor_sync(0xffffffffu, s, o));
+    if (lane == 0) out[q] = __fsqrt_ru(s);
 }
 
-// Exact q.mu - |mu|^2/2 by one warp: per-lane Dot2, lanes summed in FP64.
 // Merge the 32 lanes' Dot2 accumulators (s, c) by TwoSum in a fixed
 // butterfly order; every lane ends with the same pair.  FP32 throughout: the
 // FP64 rate of this GPU is a small fraction of its FP32 rate.
@@ -305,6 +310,8 @@ __device__ __forceinline__ uint64_t score_key(double v) {
     return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
 }
 
+// q.mu - |mu|^2/2 by one warp in compensated arithmetic: per-lane Dot2 over
+// elements lane, lane + 32, ..., lanes merged by TwoSum, FP64 finish.
 __device__ __forceinline__ double warp_exact_score(const float* __restrict__ q, const float* __restrict__ mu, int d,
                                                    double half_norm) {
     const int lane = threadIdx.x & 31;
@@ -592,6 +599,32 @@ __global__ void group_fill_kernel(const int32_t* __restrict__ route, int64_t npa
                                   int32_t* __restrict__ pairs) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < npairs) pairs[atomicAdd(&cursor[route[i]], 1)] = (int32_t)i;
+}
+
+// The queries grouped by their best cluster (probe 0), one block per
+// cluster: block j reserves a contiguous range for the queries whose first
+// probe is cluster j and fills it (order inside the range is free).  The
+// re-score runs its blocks in this order, so queries with neighbouring
+// candidates gather their rows close together in time and share them
+// through L2.  Every query has exactly one probe 0, so the ranges cover
+// 0..nq-1.
+__global__ void primary_order_kernel(const int32_t* __restrict__ pairs, const int32_t* __restrict__ off, int c,
+                                     int32_t* __restrict__ qorder, unsigned long long* __restrict__ counter) {
+    __shared__ int s_cnt, s_base, s_pos;
+    const int j = blockIdx.x;
+    const int lo = off[j], hi = off[j + 1];
+    if (threadIdx.x == 0) { s_cnt = 0; s_pos = 0; }
+    __syncthreads();
+    int mine = 0;
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) mine += (pairs[i] % c) == 0;
+    if (mine) atomicAdd(&s_cnt, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) s_base = s_cnt ? (int)atomicAdd(counter, (unsigned long long)s_cnt) : 0;
+    __syncthreads();
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const int p = pairs[i];
+        if (p % c == 0) qorder[s_base + atomicAdd(&s_pos, 1)] = p / c;
+    }
 }
 
 // ----------------------------------------------------------------- locate --
@@ -1455,12 +1488,12 @@ __global__ void __launch_bounds__(512) rescore_kernel(const float* __restrict__ 
                                                       const int32_t* __restrict__ row_of, int d, int S,
                                                       const int64_t* in_ids, int k, int64_t* out_ids,
                                                       float* out_scores, int64_t n,
-                                                      unsigned long long* bounds) {
+                                                      unsigned long long* bounds, const int32_t* __restrict__ qorder) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_nr;
     float* qv = reinterpret_cast<float*>(smem);
     uint64_t* key = reinterpret_cast<uint64_t*>(smem + align_up_dev((size_t)d * 4, 16));
-    const int64_t q = blockIdx.x;
+    const int64_t q = qorder ? qorder[blockIdx.x] : blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int d4 = d / 4;
     if (tid == 0) s_nr = 0;
@@ -2182,6 +2215,7 @@ struct Workspace {
     double* rscore;
     int32_t* route;
     int32_t* pairs;
+    int32_t* qorder;        // tensor modes: queries grouped by their best cluster (re-score order)
     int32_t* wstart;
     int32_t* wlen;
     float* pscore;
@@ -2285,6 +2319,7 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, const
     w.rscore = (double*)take((size_t)nq * g.ncl * 8);
     w.route = (int32_t*)take((size_t)np * 4);
     w.pairs = (int32_t*)take((size_t)np * 4);
+    w.qorder = tensor ? (int32_t*)take((size_t)nq * 4) : nullptr;
     w.wstart = (int32_t*)take((size_t)np * g.L * 4);
     w.wlen = (int32_t*)take((size_t)np * g.L * 4);
     w.pscore = tensor ? nullptr : (float*)take((size_t)np * sh.kp * 4);
@@ -2446,6 +2481,10 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
     LIDER_LAUNCH_CHECK("group_scan_kernel");
     group_fill_kernel<<<(unsigned)cdiv(np, 256), 256, 0, st>>>(w.route, np, w.cursor, w.pairs);
     LIDER_LAUNCH_CHECK("group_fill_kernel");
+    if (w.qorder) {
+        primary_order_kernel<<<(unsigned)g.ncl, 256, 0, st>>>(w.pairs, w.off, c, w.qorder, &w.counters[CNT_QORDER]);
+        LIDER_LAUNCH_CHECK("primary_order_kernel");
+    }
     // 4. locate + expand
     if ((rc = mark(LIDER_PHASE_LOCATE))) return rc;
     locate_kernel<<<(unsigned)cdiv(np * g.L, 256), 256, 0, st>>>(
@@ -2608,7 +2647,7 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         const size_t rs_smem = align_up((size_t)g.d * 4, 16) + (size_t)next_pow2(sh.so) * 8;
         if ((rc = smem_attr((const void*)rescore_kernel, (int)rs_smem))) return rc;
         rescore_kernel<<<(unsigned)nq, (unsigned)ix->tune.rescore_threads, rs_smem, st>>>(Q, g.X, g.row_of, g.d, sh.so, w.sl_ids, k, out_ids,
-                                                           out_scores, g.n, &w.counters[CNT_BOUNDS]);
+                                                           out_scores, g.n, &w.counters[CNT_BOUNDS], w.qorder);
         LIDER_LAUNCH_CHECK("rescore_kernel");
     }
     return mark(LIDER_NUM_PHASES);
