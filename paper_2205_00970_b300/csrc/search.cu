@@ -1302,10 +1302,22 @@ __global__ void __launch_bounds__(256) mark_kernel(const int32_t* __restrict__ p
     uint32_t* bits = in_smem ? sbits + (size_t)warp * smem_words : dst;
     for (int64_t i = lane; i < words; i += 32) bits[i] = 0u;
     __syncwarp();
+    // window starts of the L arrays loaded at once (L <= 32), then each
+    // window's positions four loads ahead of their shared-memory atomics
+    const int ws_lane = lane < L ? wstart[pair * L + lane] : 0;
     for (int l = 0; l < L; ++l) {
-        const int32_t* P = pos + (int64_t)l * n + base + wstart[pair * L + l];
-        for (int t = lane; t < T; t += 32) {
-            const uint32_t p = (uint32_t)P[t];
+        const int32_t* P = pos + (int64_t)l * n + base + __shfl_sync(0xffffffffu, ws_lane, l);
+        int t = lane;
+        for (; t + 96 < T; t += 128) {
+            const uint32_t p0 = (uint32_t)__ldg(P + t), p1 = (uint32_t)__ldg(P + t + 32);
+            const uint32_t p2 = (uint32_t)__ldg(P + t + 64), p3 = (uint32_t)__ldg(P + t + 96);
+            atomicOr(&bits[p0 >> 5], 1u << (p0 & 31));
+            atomicOr(&bits[p1 >> 5], 1u << (p1 & 31));
+            atomicOr(&bits[p2 >> 5], 1u << (p2 & 31));
+            atomicOr(&bits[p3 >> 5], 1u << (p3 & 31));
+        }
+        for (; t < T; t += 32) {
+            const uint32_t p = (uint32_t)__ldg(P + t);
             atomicOr(&bits[p >> 5], 1u << (p & 31));
         }
     }
