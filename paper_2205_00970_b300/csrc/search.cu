@@ -2137,6 +2137,42 @@ __global__ void __launch_bounds__(512) select_hist_kernel(
         }
         __syncthreads();
     }
+    if (!guarded && need > 0 && n > 0) {
+        // Served forms: the list is the `keep` best keys by (score descending,
+        // id ascending), in no particular order (the re-rank orders it).  The
+        // keep-th smallest 64-bit key comes from two radix selects: its score
+        // word, then its id among the keys of that score word.
+        const int keep = min(need, n);
+        const uint32_t whi = block_kth_smallest([&](int i) { return (uint32_t)(cand[i] >> 32); }, n, keep,
+                                                s_rhist, s_pick);
+        if (tid == 0) { s_band = 0; s_bt = 0; }
+        __syncthreads();
+        int less = 0;
+        for (int r = tid; r < n; r += blockDim.x) less += (uint32_t)(cand[r] >> 32) < whi;
+        if (less) atomicAdd(&s_band, less);
+        __syncthreads();
+        const int r2 = keep - s_band;                  // >= 1: whi is the keep-th smallest word
+        const uint32_t wlo = block_kth_smallest(
+            [&](int i) {
+                const uint64_t kv = cand[i];
+                return (uint32_t)(kv >> 32) == whi ? (uint32_t)kv : 0xffffffffu;   // ids stay below 2^31
+            },
+            n, r2, s_rhist, s_pick);
+        const uint64_t kstar = ((uint64_t)whi << 32) | wlo;
+        for (int r = tid; r < n; r += blockDim.x) {
+            const uint64_t kv = cand[r];
+            if (kv <= kstar) {
+                const int slot = atomicAdd(&s_bt, 1);
+                out_ids[q * so + slot] = (int64_t)(uint32_t)kv;
+                out_scores[q * so + slot] = float_from_order(~(uint32_t)(kv >> 32));
+            }
+        }
+        for (int r = keep + tid; r < so; r += blockDim.x) {
+            out_ids[q * so + r] = -1;
+            out_scores[q * so + r] = -INFINITY;
+        }
+        return;
+    }
     const int SP = n > 1 ? next_pow2_dev(n) : 1;
     for (int u = n + tid; u < SP; u += blockDim.x) cand[u] = ~0ull;
     __syncthreads();
