@@ -1,29 +1,39 @@
 // LIDER batched search (Sec. 3.3.2, Sec. 6.2) on one GPU.
 //
-// Steps and kernels, in order, for nq queries probing c clusters each:
-//   1. hash     dot2_tile_kernel<hash> + pack_kernel: packed query hashkeys
-//               for the L arrays (projections shared by all clusters)
-//   2. route    dot2_tile_kernel<score> + topc_kernel: the c best centroids,
-//               score x.mu - |mu|^2/2, ties -> lower cluster index
-//   3. group    group_*_kernel: (query, probe) pairs bucketed by cluster, cut
-//               into work items of up to G pairs of one cluster
+// Steps and kernels, in order, for nq queries probing c clusters each
+// (tensor score modes; SIMT mode in brackets):
+//   1. hash     split_tf32 + qnorm_kernel + hash_tc_kernel (3xTF32 tiles of
+//               queries x projections) + hash_recheck_kernel (values near a
+//               bucket edge recomputed exactly) + pack_kernel: packed query
+//               hashkeys for the L arrays, p-stable or hyperplane (Sec. 4.1,
+//               4.2) [dot2_tile_kernel<hash> + pack_kernel]
+//   2. route    route_tc_kernel (3xTF32 tiles of queries x centroids) +
+//               topc_exact_kernel: the c best centroids by x.mu - |mu|^2/2,
+//               ties -> lower index, exact despite approximate scores
+//               [dot2_tile_kernel<score> + topc_kernel]; with the Layer-1
+//               centroids retriever, route_core_kernel then routes instead
+//   3. group    group_*_kernel: (query, probe) pairs bucketed by cluster;
+//               primary_order_kernel: queries grouped by best cluster (the
+//               re-score's order)
 //   4. locate   locate_kernel, one thread per (pair, array): re-scale the key
 //               (Sec. 5.1), two-stage RMI prediction (Sec. 5.2), clamp
-//               (Sec. 7.4), lower bound searched inside the leaf's recorded
-//               error window (with a counted fallback outside it), then the
-//               bi-directional expansion window of Sec. 4 by co-rank search
-//   5. score    tensor score modes: mark_kernel (each pair's candidate
-//               union as a bitmap), tc_score_kernel (dense 128 x 256 tiles on
-//               tcgen05, candidates kept by the bitmap), select_query_kernel
-//               (each query's best by bucket selection);
-//               SIMT mode: score_group_kernel, persistent, one work item (G
-//               pairs of one cluster) at a time: union of each pair's L
-//               windows as bits of a shared-memory position mask, the marked
-//               rows streamed once and scored by exact FP32 inner products
-//               with every query that marked them, then each pair's top-k
-//   6. merge    SIMT mode: merge_kernel, one warp per query, k-way merge of
-//               its c lists (Sec. 6.2, heap of list heads); tensor modes:
-//               rescore_kernel, exact FP32 scores of the selected lists
+//               (Sec. 7.4, counted as OOR/LE), lower bound searched inside
+//               the leaf's recorded error window (with a counted fallback
+//               outside it), then the bi-directional expansion window of
+//               Sec. 4 by co-rank search
+//   5. gather   qgather_*_kernel (the queries in pair order, in the mode's
+//               operand format) + mark_kernel (each pair's candidate union as
+//               a bitmap over its cluster's positions)
+//   6. score    tc_units_kernel + tc_score_kernel: dense 128 x 256 tiles on
+//               tcgen05 written as per-pair score rows, with per-32-position
+//               candidate maxima [score_group_kernel: union, exact FP32
+//               scores and per-pair top-k in one persistent kernel]
+//   7. select   select_hist_kernel (per query: the ks best approximate scores
+//               plus the guard band, by radix selects) and select_query_kernel
+//               (fallback for massive ties)
+//   8. merge    rescore_kernel: exact FP32 scores of each query's list, sorted
+//               [merge_kernel: k-way merge of the c per-pair lists]
+
 #include <algorithm>
 #include <map>
 #include <mutex>
