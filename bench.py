@@ -44,7 +44,9 @@ LAUNCHES_PER_SEARCH = {"tensor": 19, "simt": 10, "bf16": 19, "f16": 19, "fp8": 1
 MODES = {"tensor": 0, "simt": 1, "bf16": 2, "f16": 3, "fp8": 4}
 DTYPES = {"tensor": "f32", "simt": "f32", "bf16": "bf16", "f16": "f16", "fp8": "fp8-e4m3"}
 FP8_PER_BF16 = 4.5 / 2.25     # nominal dense FP8 / BF16 tensor rate (B300)
-F16_TC_DRAM_BYTES_PER_TILE = (674.204928e6 + 305.550592e6) / 3782   # ncu, tc_score_kernel<KindF16>
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one warm tc_score_kernel<KindF16>
+# launch on the full mid workload (18,211 tiles), per tile
+F16_TC_DRAM_BYTES_PER_TILE = (1731677184 + 2064019200) / 18211
 
 
 def workload_desc(cfg) -> dict:
@@ -401,9 +403,8 @@ def run_lider(args, cfg):
             peak = bf16
             psrc = f"{src}: bf16 burst" + (" (FP16 has the same dense rate)" if args.score == "f16" else "")
         achieved = tc_flop / score_s / 1e12
-        # DRAM bytes per launch: ncu dram__bytes_read.sum + dram__bytes_write.sum of
-        # tc_score_kernel<KindF16> at 400,000 x 768 / 4,000 queries (3,782 tiles), per
-        # tile, times this launch's tiles (FP16 mode only; other kinds not captured)
+        # DRAM bytes per launch: the full-size capture's bytes per tile times this
+        # launch's tiles (exact for the mid workload; FP16 mode only)
         traffic = F16_TC_DRAM_BYTES_PER_TILE * stats["tc_tiles"] if args.score == "f16" else None
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": traffic, "kernel": "tc_score_kernel",
@@ -413,7 +414,8 @@ def run_lider(args, cfg):
                     "useful_flop_per_launch": useful_flop,
                     "useful_tflops": useful_flop / score_s / 1e12}
         if traffic is not None:
-            roofline["traffic_note"] = "scaled by tiles from an ncu capture at 400,000 x 768, 4,000 queries"
+            roofline["traffic_note"] = ("ncu DRAM bytes of one full-size mid launch (18,211 tiles), per tile, "
+                                        "times this launch's tiles")
             roofline["dram_gbs_vs_hbm"] = {"achieved": traffic / score_s / 1e9, "peak": hbm,
                                            "frac": traffic / score_s / 1e9 / hbm}
     else:
