@@ -429,6 +429,10 @@ def run_lider(args, cfg):
                     "gather_gbs_vs_hbm": {"achieved": gather_bytes / score_s / 1e9, "peak": hbm,
                                           "frac": gather_bytes / score_s / 1e9 / hbm}}
 
+    served = None
+    if world == 1 and args.score in ("f16", "tensor", "simt") and not args.no_served:
+        served = served_compare(args, cfg, X, C, A, b, Qd, chunks, gpu_ids, dev)
+
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -451,6 +455,8 @@ def run_lider(args, cfg):
                    f"served shortlist: {DTYPES[args.score]} scores, FP32 re-rank of the best {args.rerank} * k",
         "clocks": clk,
     }
+    if served is not None:
+        line["served_bf16"] = served
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, X, Q, C, A, b, gpu_ids, args.cpu_budget)
     if rank == 0:
@@ -459,6 +465,52 @@ def run_lider(args, cfg):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def served_compare(args, cfg, X, C, A, b, Qd, chunks, plain_ids, dev) -> dict:
+    """The metric's other side: the served BF16 form (BF16 corpus copy scored
+    on the tensor cores, FP32 re-rank of the best rerank * k) on the same
+    queries, timed the same way, with recall@10 against the plain (exact)
+    search's top-10.  Errors are reported in the line, not raised."""
+    import torch
+
+    from paper_2205_00970_b300 import lider
+    try:
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        Xd = t(X)
+        sidx = lider.Index(Xd, t(C), t(A), t(b), L=cfg["L"], m=cfg["m"], W=cfg["W"], rmi_leaves=cfg["leaves"],
+                           r0=cfg["r0"], B=cfg["B"], score_mode=lider.SCORE_BF16, rerank=args.rerank)
+        del Xd
+        k, c, nq = cfg["k"], cfg["c"], Qd.shape[0]
+        ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
+        sc = torch.empty((nq, k), dtype=torch.float32, device=dev)
+
+        def once():
+            for lo, hi in chunks:
+                sidx.search(Qd[lo:hi], k, c, out=(ids[lo:hi], sc[lo:hi]))
+
+        if not args.no_autotune:
+            lo, hi = chunks[0]
+            sidx.autotune(Qd[lo:hi], k, c, reps=3)
+        for _ in range(args.warmup):
+            once()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            once()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        got = ids.cpu().numpy()
+        sidx.free()
+        del sidx
+        torch.cuda.empty_cache()
+        return {"value": nq / (ms / 1e3), "unit": "queries/s", "ms_per_step": ms,
+                "shortlist": f"{args.rerank} * k", "recall_at_10_vs_plain": recall10(got, plain_ids),
+                "tuning": "autotuned" if not args.no_autotune else "default launch shapes"}
+    except Exception as e:                               # the main line must still print
+        return {"error": f"{type(e).__name__}: {e}"[:300]}
 
 
 def run_serve(args, cfg):
@@ -749,6 +801,8 @@ def main():
     ap.add_argument("--hyper-m", type=int, default=32, help="--variants: bits per hyperplane hashkey")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--no-served", action="store_true",
+                    help="skip the served BF16 comparison run on the same queries")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-queries-per-step", type=int, default=8)
     ap.add_argument("--n", type=int, default=None, help="profiling size: first n corpus rows")
