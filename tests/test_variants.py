@@ -93,3 +93,38 @@ def test_core_route_differs_from_exact_scan_but_stays_close():
     assert all(len(set(r)) == cfg["c"] for r in route.tolist())
     overlap = np.mean([len(set(a) & set(e)) / cfg["c"] for a, e in zip(route.tolist(), exact.tolist())])
     assert 0.5 < overlap <= 1.0, overlap
+
+
+@pytest.mark.parametrize("case", ["core_route_all_clusters", "hyperplane_64_bits"])
+def test_variant_edge_cases(case):
+    """Edges of the variants on tiny: the Layer-1 route probing every cluster
+    (c = n_clusters = 16, each window spans all centroids, so the route is the
+    exact scan's order), and hyperplane keys that use all 64 bits (m = 64)."""
+    import torch
+    cfg, X, Q, C, A, b = F.workload("tiny")
+    if case == "core_route_all_clusters":
+        cfg = dict(cfg, route_kind=O.ROUTE_CORE, c=cfg["n_clusters"])
+    else:
+        cfg = dict(cfg, hash_kind=O.HASH_HYPERPLANE, m=64, B=3)
+        A, b = F.synth.projections(cfg["seed"], cfg["L"], cfg["m"], cfg["d"], cfg["W"])
+    nq = 200
+    ref_idx = F.oracle_index(cfg, X, C, A, b)
+    ref = O.search(ref_idx, Q[:nq], cfg["k"], cfg["c"], cfg["R"], route_kind=cfg.get("route_kind", O.ROUTE_EXACT))
+    out = []
+    for mode in MODES:
+        g = F.gpu_index(dict(cfg, score_mode=mode), X, C, A, b)
+        ids, sc, _, tr = g.search(torch.from_numpy(Q[:nq]).cuda(), cfg["k"], cfg["c"], stats=True, trace=True)
+        g.free()
+        bad, exempt = F.check_trace(tr, ref)
+        assert not bad, (case, mode, bad[:5])
+        assert len(exempt) <= 2
+        ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+        rows = [i for i in range(nq) if i not in exempt]
+        bad = F.check_topk(ids, sc, ref.ids, ref.scores, X, Q[:nq], rows=rows)
+        assert not bad, (case, mode, bad[:5])
+        out.append((ids, sc))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1].view(np.uint32), out[1][1].view(np.uint32))
+    if case == "core_route_all_clusters":
+        exact, _, _ = O.route(Q[:nq], C, cfg["c"])
+        np.testing.assert_array_equal(ref.route, exact)
