@@ -162,7 +162,18 @@ class Index:
                  L: int, m: int, W: float, rmi_leaves: int, r0: int = 2, B: int | None = None,
                  score_mode: int = SCORE_TENSOR, rerank: int = 0, hash_kind: int = HASH_PSTABLE,
                  route_kind: int = ROUTE_EXACT, raw_keys: bool = False, stream=None):
-        """B defaults to 1 for p-stable hashes and 3 for hyperplane bits."""
+        """Build the index (lider_build): corpus (n, d), centroids (n_clusters,
+        d), projections A (L*m, d) and offsets b (L*m), all FP32 CUDA tensors.
+
+        L, m, W, rmi_leaves, r0, B: the core models' parameters (hashkey arrays,
+        hashes per key, p-stable bucket width, RMI leaves, expansion factor
+        R = r0 * k, elements read by dist_e; B defaults to 1 for p-stable
+        hashes and 3 for hyperplane bits).  score_mode: SCORE_F16, SCORE_TENSOR
+        or SCORE_SIMT (exact FP32 top-k, equal across the three), SCORE_BF16 or
+        SCORE_FP8 (served forms, FP32 re-rank of rerank * k).  hash_kind:
+        HASH_PSTABLE or HASH_HYPERPLANE.  route_kind: ROUTE_EXACT (scan every
+        centroid) or ROUTE_CORE (the Layer-1 centroids retriever).  raw_keys:
+        the RMIs learn raw key values instead of re-scaled ones."""
         if B is None:
             B = 3 if hash_kind == HASH_HYPERPLANE else 1
         corpus = _dev(corpus, torch.float32, "corpus")
