@@ -147,3 +147,25 @@ def test_rmi_diagnostics_match_polyfit_line():
         got = O.rmi_diagnostics(idx, kept.reshape(-1, 1), np.zeros((len(kept), 1), np.int64), k)
         assert got == tuple(exp), (raw, got, exp)
         assert got[1] > 100                                # the clumps defeat a single line
+
+
+# --- L = 1, c = 1: one SK-LSH core model ------------------------------------------
+
+def test_single_array_single_cluster_is_one_core_model():
+    """With one hashkey array and one probed cluster the search is a single
+    SK-LSH core model: a query's candidates are exactly the ids of its one
+    expansion window (no union to take), and its top-k is the best of them by
+    FP64 score, ties to the lower id."""
+    X, Q, C, A, b, _, m = _problem(seed=13, n=800, nclu=4, L=1)
+    idx = O.build_index(X, C, A[:m], b[:m], 1, m, W=0.8, F=8)
+    k, R = 7, 25
+    res = O.search(idx, Q, k=k, c=1, R=R)
+    for i in range(Q.shape[0]):
+        j = int(res.route[i, 0])
+        cm = idx.core(j, fit=False)
+        s, ln = int(res.wstart[i, 0, 0]), int(res.wlen[i, 0, 0])
+        window = [int(x) for x in cm.sorted_ids[0][s:s + ln]]
+        assert ln == min(R, len(cm.ids)) and res.ucount[i, 0] == len(set(window)) == ln
+        sc = {x: float(np.dot(X[x].astype(np.float64), Q[i].astype(np.float64))) for x in window}
+        best = sorted(window, key=lambda x: (-sc[x], x))[:k]
+        assert list(res.ids[i][:len(best)]) == best
