@@ -91,14 +91,20 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, keep_dir: str | None = None):
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.keep_dir = keep_dir        # where the raw samples stay (default: a temporary file)
 
     def start(self):
-        os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{self.gpu}.csv")
+        if self.keep_dir:
+            os.makedirs(self.keep_dir, exist_ok=True)
+            self.path = os.path.join(self.keep_dir, f"clocks_gpu{self.gpu}.csv")
+        else:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(prefix=f"clocks_gpu{self.gpu}_", suffix=".csv")
+            os.close(fd)
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -126,6 +132,11 @@ class ClockSampler:
             for name, v in zip(names[1:], f[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(name)
+        if not self.keep_dir:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
@@ -318,7 +329,7 @@ def run_lider(args, cfg):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, args.clocks_dir)
     clocks.start()
     time.sleep(0.3)
     t0.record()
@@ -543,7 +554,7 @@ def run_serve(args, cfg):
     srv.latencies_ms(clear=True)
     s0 = srv.stats()
     sch = poisson_schedule(args.serve, args.serve_seconds, ks=ks, max_req=args.serve_max_req, n_queries=nq, seed=2)
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(0, args.clocks_dir)
     clocks.start()
     t0 = time.perf_counter()
     sent = run_load(srv, Q, sch)
@@ -801,6 +812,8 @@ def main():
     ap.add_argument("--hyper-m", type=int, default=32, help="--variants: bits per hyperplane hashkey")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--clocks-dir", default=None,
+                    help="keep the raw nvidia-smi clock samples of the timed region in this directory")
     ap.add_argument("--no-served", action="store_true",
                     help="skip the served BF16 comparison run on the same queries")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
