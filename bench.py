@@ -114,6 +114,11 @@ class ClockSampler:
 
     def stop(self) -> dict:
         if self.proc is None:
+            if not self.keep_dir and self.path:
+                try:
+                    os.unlink(self.path)
+                except OSError:
+                    pass
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         time.sleep(0.25)
         self.proc.terminate()
