@@ -95,7 +95,7 @@ typedef struct lider_index lider_index;   /* opaque; owns its device memory */
  *   rerank = shortlist factor of LIDER_SCORE_BF16 / FP8: rerank * k candidates per
  *        query are re-scored in FP32 (0 means 4);
  *   route_kind = LIDER_ROUTE_EXACT (0) or LIDER_ROUTE_CORE (1, needs
- *        n_clusters <= 16384);
+ *        n_clusters <= 8192);
  *   raw_keys = 0: the RMIs learn re-scaled keys (Sec. 5.1, the method);
  *        1: they learn the raw 64-bit key values converted to FP64, without
  *        re-scaling (the ablation of Sec. 7.4; see rmi_oor below). */
@@ -190,7 +190,7 @@ typedef struct {
  * ownership of its buffers.  Errors: LIDER_EINVAL for null pointers, n < 1,
  * d % 4 != 0, n_clusters < 1, L/m/r0/B/rmi_leaves < 1, W <= 0 (p-stable),
  * an unknown hash_kind, route_kind or raw_keys, or (bits per element)*B > 56;
- * LIDER_ELIMIT past the caps above (and n_clusters > 16384 with
+ * LIDER_ELIMIT past the caps above (and n_clusters > 8192 with
  * LIDER_ROUTE_CORE);
  * LIDER_ENOMEM / LIDER_ECUDA from the device.  On error *out is NULL. */
 int lider_build(const float* corpus, int64_t n, int32_t d,

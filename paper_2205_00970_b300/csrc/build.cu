@@ -341,7 +341,7 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
         return fail(LIDER_EINVAL, "lider_build: unknown route_kind");
     if (P->raw_keys != 0 && P->raw_keys != 1) return fail(LIDER_EINVAL, "lider_build: raw_keys must be 0 or 1");
     if (P->route_kind == LIDER_ROUTE_CORE && ncl > kRouteCoreMaxClusters)
-        return fail(LIDER_ELIMIT, "lider_build: LIDER_ROUTE_CORE supports n_clusters <= 16384");
+        return fail(LIDER_ELIMIT, "lider_build: LIDER_ROUTE_CORE supports n_clusters <= 8192");
     // hyperplane hashes take t = a.x: no offset, unit width
     const double W = hyper ? 1.0 : P->W;
     const bool raw = P->raw_keys != 0;

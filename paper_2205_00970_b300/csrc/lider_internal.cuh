@@ -43,7 +43,7 @@ struct RmiRoot {          // first stage and re-scaling range of one (cluster, a
     uint64_t x_min, x_max;
 };
 
-constexpr int kRouteCoreMaxClusters = 16384;   // LIDER_ROUTE_CORE cap on n_clusters
+constexpr int kRouteCoreMaxClusters = 8192;    // LIDER_ROUTE_CORE cap on n_clusters (shared memory of one warp)
 
 struct Geometry {         // everything a search kernel needs, passed by value
     int64_t n;

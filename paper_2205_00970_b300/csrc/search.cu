@@ -841,8 +841,8 @@ __global__ void route_core_kernel(Geometry g, const uint64_t* __restrict__ ckeys
 }
 
 // Launch shape of route_core_kernel: per-warp shared memory for the bitmap,
-// the list, its FP32 scores and 64-bit keys (n_clusters <= 16384 keeps one
-// warp under 216 KB), up to 8 warps per block.
+// the list, its FP32 scores and 64-bit keys, 16 bytes per listed centroid
+// (n_clusters <= 8192 keeps one warp under 133 KB), up to 8 warps per block.
 struct RouteCoreShape {
     int Rc, words, cap, warp_bytes, wpb;
 };

@@ -71,7 +71,7 @@ def test_binding_loads_and_validates_without_gpu():
     assert rc == -4 and "L <= 16" in lider.last_error()
     rc = lider.raw_call("lider_build", dummy, 10, 8, dummy, 20000, dummy, dummy,
                         ctypes.byref(lider.Params(4, 8, 16, 2, 1, 0, 1.0, 0, 0, 1, 0)), None, ctypes.byref(out))
-    assert rc == -4 and "16384" in lider.last_error()
+    assert rc == -4 and "8192" in lider.last_error()
     # hyperplane bits: B is limited by one bit per element, not floor(64/m)
     rc = lider.raw_call("lider_build", dummy, 10, 8, dummy, 2, dummy, dummy,
                         ctypes.byref(lider.Params(4, 8, 16, 2, 57, 1, 1.0, 0, 0)), None, ctypes.byref(out))
