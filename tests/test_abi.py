@@ -85,3 +85,18 @@ def test_tuning_abi_validates_without_gpu():
     assert lider.raw_call("lider_set_tuning", None, ctypes.byref(t)) == -1
     assert lider.raw_call("lider_get_tuning", None, ctypes.byref(t)) == -1
     assert lider.raw_call("lider_autotune", None, None, 1, 10, 1, 1, None, None, None) == -1
+
+
+def test_header_is_plain_c_and_links(tmp_path):
+    """A C99 client (tests/c_abi_check.c) compiles against include/lider.h
+    alone with -pedantic, links liblider.so and gets argument errors back
+    without touching a GPU."""
+    import subprocess
+    pkg = os.path.join(ROOT, "paper_2205_00970_b300")
+    exe = tmp_path / "c_abi_check"
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        os.path.join(ROOT, "tests", "c_abi_check.c"), "-L", pkg, "-llider",
+                        f"-Wl,-rpath,{pkg}", "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and "c abi checks passed" in r.stdout, r.stdout + r.stderr
