@@ -610,12 +610,12 @@ def call_size(idx, nq, k, c, want):
     return sub
 
 
-def fp64_knn(X, Q, k: int, chunk: int = 262_144) -> np.ndarray:
+def fp64_knn(X, Q, k: int, chunk: int = 262_144, device: str = "cuda:0") -> np.ndarray:
     """Ground truth for recall: the k largest FP64 inner products of each
-    query over the whole corpus (ties to the lower id), computed on the GPU
-    with plain FP64 matrix products, chunk by chunk."""
+    query over the whole corpus (ties to the lower id), computed with plain
+    FP64 matrix products (on the GPU by default), chunk by chunk."""
     import torch
-    dev = torch.device("cuda", 0)
+    dev = torch.device(device)
     q = torch.from_numpy(np.ascontiguousarray(Q)).to(dev, torch.float64)
     best_s = torch.full((len(Q), 0), 0.0, dtype=torch.float64, device=dev)
     best_i = torch.zeros((len(Q), 0), dtype=torch.int64, device=dev)
