@@ -32,7 +32,8 @@ projections are shared by all clusters; R4 routing by x.mu - |mu|^2/2;
 R5 query keys outside [x_min, x_max] re-scale outside [0, n_c-1];
 R6 search starts at the exact lower bound; R8 expansion ties go left;
 R9 B=1 for p-stable, B=3 for hyperplane; R10 least squares, floor, clamp,
-empty leaf copies the root; R11 equal keys ordered by id.
+empty leaf copies the root; R11 equal keys ordered by id; R24 k-means starts
+from Forgy rows drawn by SplitMix64; R25 k-means stores FP32 centroids.
 
 Parity pins for every function live in ``tests/test_oracle_*.py``.
 """
@@ -310,17 +311,53 @@ def assign(X: np.ndarray, C: np.ndarray, chunk: int = 65536):
     return asg, near
 
 
+# Reading R24: the paper does not say how k-means starts.  Forgy
+# initialisation: the initial centroids are `count` distinct rows of the
+# training rows, drawn by Floyd's sampling algorithm (Bentley and Floyd, 1987)
+# from the counter-based SplitMix64 generator (Steele, Lea and Flood, 2014):
+# draw i (from 0) is mix64(seed + (i + 1) * GAMMA mod 2^64), and the integer
+# uniform on [0, j] is that draw mod (j + 1).
+
+SPLITMIX_GAMMA = 0x9E3779B97F4A7C15
+_M64 = (1 << 64) - 1
+
+
+def splitmix64(seed: int, i: int) -> int:
+    """Draw i of the SplitMix64 stream that starts from state `seed`."""
+    z = (seed + (i + 1) * SPLITMIX_GAMMA) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def forgy_rows(seed: int, n: int, count: int) -> np.ndarray:
+    """`count` distinct indices of [0, n), ascending (Floyd's algorithm: for
+    j = n - count .. n - 1 take t uniform on [0, j]; keep t, or j if t is
+    already taken)."""
+    if not 0 < count <= n:
+        raise ValueError("forgy_rows: need 0 < count <= n")
+    chosen: set[int] = set()
+    for i, j in enumerate(range(n - count, n)):
+        t = splitmix64(seed, i) % (j + 1)
+        chosen.add(j if t in chosen else t)
+    return np.array(sorted(chosen), dtype=np.int64)
+
+
 def kmeans(X: np.ndarray, init: np.ndarray, iters: int) -> np.ndarray:
-    """Lloyd's k-means in FP64 from the given initial centroids (Sec. 3.2).
-    An emptied cluster keeps its previous centroid."""
-    C = init.astype(np.float64).copy()
+    """Lloyd's k-means from the given initial centroids (Sec. 3.2): `iters`
+    rounds of assigning every row to its nearest centroid (FP64 scores) and
+    moving each centroid to the mean of its rows.  Reading R25: centroids are
+    stored in FP32, as the index keeps them, so each mean is taken in FP64 and
+    rounded to FP32.  An emptied cluster keeps its previous centroid.  Returns
+    the FP32 centroids."""
+    C = init.astype(np.float32).copy()
     X64 = X.astype(np.float64)
     for _ in range(iters):
         asg, _ = assign(X, C)
         for j in range(C.shape[0]):
             sel = asg == j
             if np.any(sel):
-                C[j] = X64[sel].mean(axis=0)
+                C[j] = X64[sel].mean(axis=0).astype(np.float32)
     return C
 
 

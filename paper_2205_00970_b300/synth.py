@@ -35,7 +35,6 @@ STREAM_CORPUS = 2
 STREAM_QUERIES = 3
 STREAM_PROJ = 4
 STREAM_COMPONENT = 5
-STREAM_INIT = 6
 
 
 def _rng(seed: int, stream: int, chunk: int = 0) -> np.random.Generator:
@@ -118,9 +117,3 @@ def projections(seed: int, L: int, m: int, d: int, W: float):
     b = (rng.random(L * m) * W).astype(np.float32)
     b = np.minimum(b, np.nextafter(np.float32(W), np.float32(0)))
     return A, b
-
-
-def init_rows(seed: int, n: int, count: int) -> np.ndarray:
-    """`count` distinct row indices of [0, n), ascending: k-means (Forgy) seeds."""
-    rng = _rng(seed, STREAM_INIT)
-    return np.sort(rng.choice(n, size=count, replace=False)).astype(np.int64)

@@ -304,8 +304,63 @@ def test_kmeans_recovers_separated_blob_means():
     X = (centers[lab] + rng.standard_normal((200, 6))).astype(np.float32)
     init = X[[0, 50, 100, 150]]
     C = O.kmeans(X, init, iters=5)
+    assert C.dtype == np.float32
     for j in range(4):
-        np.testing.assert_allclose(C[j], X[lab == j].astype(np.float64).mean(axis=0), atol=1e-12)
+        exact = [math.fsum(float(v) for v in X[lab == j][:, i]) / 50 for i in range(6)]
+        np.testing.assert_array_equal(C[j], np.float32(exact))
+
+
+def _exact_lloyd_step(X, C):
+    """One Lloyd update written out by hand: nearest centroid by squared L2
+    distance (ties to the lower index), exact member sums (math.fsum), mean
+    rounded to FP32; an empty cluster keeps its centroid."""
+    Xd = X.astype(np.float64)
+    out = C.copy()
+    lab = []
+    for x in Xd:
+        dist = [math.fsum((x - c.astype(np.float64)) ** 2) for c in C]
+        lab.append(min(range(len(C)), key=lambda j: (dist[j], j)))
+    lab = np.array(lab)
+    for j in range(len(C)):
+        rows = Xd[lab == j]
+        if len(rows):
+            out[j] = np.float32([math.fsum(rows[:, i]) / len(rows) for i in range(X.shape[1])])
+    return out
+
+
+def test_kmeans_steps_equal_hand_lloyd_updates():
+    """Overlapping clusters, three iterations, an initial centroid far away
+    (its cluster empties and keeps its place): each iteration equals a
+    hand-written Lloyd step."""
+    rng = np.random.default_rng(12)
+    X = rng.standard_normal((120, 5)).astype(np.float32)
+    init = np.concatenate([X[:3], np.full((1, 5), 50.0, np.float32)])
+    C = init.copy()
+    for it in range(1, 4):
+        C = _exact_lloyd_step(X, C)
+        np.testing.assert_array_equal(O.kmeans(X, init, iters=it), C)
+    np.testing.assert_array_equal(C[3], init[3])
+
+
+def test_splitmix64_published_sequence():
+    """The generator's first outputs from state 0, as published with the
+    reference implementation of SplitMix64 (Steele, Lea and Flood, 2014)."""
+    assert [O.splitmix64(0, i) for i in range(3)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4,
+                                                       0x06C45D188009454F]
+
+
+def test_forgy_rows_distinct_sorted_and_uniform():
+    assert O.forgy_rows(3, 7, 7).tolist() == list(range(7))
+    for seed in range(20):
+        r = O.forgy_rows(seed, 50, 10)
+        assert len(set(r.tolist())) == 10 and np.all(np.diff(r) > 0) and r[0] >= 0 and r[-1] < 50
+    # every row is chosen with probability count/n: 4,000 draws of 5 of 20 rows
+    counts = np.zeros(20)
+    for seed in range(4000):
+        counts[O.forgy_rows(seed, 20, 5)] += 1
+    p = 5 / 20
+    mean, sd = 4000 * p, math.sqrt(4000 * p * (1 - p))
+    assert np.all(np.abs(counts - mean) < 5 * sd)
 
 
 # --- whole search --------------------------------------------------------------------
