@@ -45,8 +45,9 @@ MODES = {"tensor": 0, "simt": 1, "bf16": 2, "f16": 3, "fp8": 4}
 DTYPES = {"tensor": "f32", "simt": "f32", "bf16": "bf16", "f16": "f16", "fp8": "fp8-e4m3"}
 FP8_PER_BF16 = 4.5 / 2.25     # nominal dense FP8 / BF16 tensor rate (B300)
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one warm tc_score_kernel<KindF16>
-# launch on the full mid workload (18,211 tiles), per tile
+# launch on the full mid workload, per tile (None: no capture of the current kernel)
 F16_TC_DRAM_BYTES_PER_TILE = (1731677184 + 2064019200) / 18211
+F16_TC_DRAM_NOTE = "ncu DRAM bytes of one full-size mid launch (18,211 tiles), per tile, times this launch's tiles"
 
 
 def workload_desc(cfg) -> dict:
@@ -62,11 +63,29 @@ def workload_desc(cfg) -> dict:
 
 
 def load_inputs(cfg):
+    """Corpus, queries and the LSH draws of the workload (seeded, synthetic).
+    The clustering is not an input: lider_build runs k-means itself."""
     X = synth.corpus(cfg["seed"], cfg["n"], cfg["d"], cfg["n_comp"], cfg["sigma"], cfg["zipf_s"])
     Q = synth.queries(cfg["seed"], cfg["nq"], cfg["d"], cfg["n_comp"], cfg["sigma"], cfg["zipf_s"])
-    C = np.load(os.path.join(ROOT, "tests", "golden", f"centroids_{cfg['name']}.npy"))
     A, b = synth.projections(cfg["seed"], cfg["L"], cfg["m"], cfg["d"], cfg["W"])
-    return X, Q, C, A, b
+    return X, Q, A, b
+
+
+def build_gpu_index(cfg, Xd, A, b, centroids=None, **kw):
+    """lider_build with k-means on the device (the workload's n_clusters,
+    kmeans_iters, kmeans_sample and seed), or lider_build_centroids when the
+    centroids of an earlier build are given.  Returns the index."""
+    import torch
+
+    from paper_2205_00970_b300 import lider
+    dev = Xd.device
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    opts = dict(L=cfg["L"], m=cfg["m"], W=cfg["W"], rmi_leaves=cfg["leaves"], r0=cfg["r0"], B=cfg["B"])
+    opts.update(kw)
+    if centroids is not None:
+        return lider.Index(Xd, t(centroids), t(A), t(b), **opts)
+    return lider.Index(Xd, None, t(A), t(b), n_clusters=cfg["n_clusters"], kmeans_iters=cfg["kmeans_iters"],
+                       kmeans_sample=cfg["kmeans_sample"], seed=cfg["seed"], **opts)
 
 
 TF32_PER_BF16 = 1.1 / 2.25     # nominal dense TF32 / BF16 tensor rate (B300)
@@ -188,62 +207,163 @@ class blas_threads:
             self.set(self.prev)
 
 
-def cpu_baseline(cfg, X, Q, C, A, b, gpu_ids, budget_s: float = 20.0) -> dict:
-    """The FP64 oracle as it stands, on host cores, on a bounded query sample;
-    also recall@10 of the GPU results on that sample against exact FP64 kNN."""
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+_POOL_INDEX = None     # the oracle index the forked pool workers search
+
+
+def _pool_init():
+    global _POOL_LIMIT
+    _POOL_LIMIT = blas_threads(1)       # one BLAS thread per worker: the pool owns the cores
+    _POOL_LIMIT.__enter__()
+
+
+def _pool_search(job):
+    from oracle import lider_oracle as O
+    Q, k, c, R = job
+    r = O.search(_POOL_INDEX, Q, k, c, R)
+    return r.ids
+
+
+def oracle_build(cfg, X, A, b):
+    """The oracle's own index: its k-means from the same seed (Forgy rows,
+    Lloyd iterations), the partition and hashes, and every cluster's sorted
+    arrays (the search builds them on first use otherwise).  Returns
+    (index, seconds of k-means, seconds of the rest)."""
     from oracle import lider_oracle as O
     t = time.perf_counter()
+    ns = min(cfg["kmeans_sample"], cfg["n"])
+    C = O.kmeans(X[:ns], X[:ns][O.forgy_rows(cfg["seed"], ns, cfg["n_clusters"])], cfg["kmeans_iters"])
+    t_km = time.perf_counter() - t
+    t = time.perf_counter()
     idx = O.build_index(X, C, A, b, cfg["L"], cfg["m"], cfg["W"], cfg["leaves"], B=cfg["B"])
-    build_s = time.perf_counter() - t
-    done = 0
-    ref_ids = []
-    limiter = blas_threads(1)
-    with limiter:
+    for j in range(cfg["n_clusters"]):
+        idx.core(j, fit=False)
+    return idx, t_km, time.perf_counter() - t
+
+
+def oracle_pool_search(idx, Q, cfg, cores: int, batch: int, budget_s: float | None, min_queries: int = 0):
+    """Search queries Q[0], Q[1], ... with the oracle on `cores` forked
+    workers (batches of `batch` queries, in order) until all are done or,
+    with a budget, at least min_queries are done and budget_s has passed.
+    Returns (ids of the queries done, seconds)."""
+    import multiprocessing as mp
+    global _POOL_INDEX
+    _POOL_INDEX = idx
+    jobs = [(Q[i:i + batch], cfg["k"], cfg["c"], cfg["R"]) for i in range(0, len(Q), batch)]
+    out = []
+    with mp.get_context("fork").Pool(cores, initializer=_pool_init) as pool:
         t = time.perf_counter()
-        while done < len(Q) and (time.perf_counter() - t < budget_s or done < 4):
-            r = O.search(idx, Q[done:done + 1], cfg["k"], cfg["c"], cfg["R"])
-            ref_ids.append(r.ids[0])
-            done += 1
-        search_s = time.perf_counter() - t
-    ref_ids = np.array(ref_ids)
-    truth, _ = O.exact_knn(X, Q[:done], 10)
-    out = {
-        "value": done / search_s, "unit": "queries/s", "cores": 1 if limiter.active else os.cpu_count(),
-        "kind": "oracle",
-        "sample": (f"first {done} of {len(Q)} queries of the same workload, FP64 oracle search "
-                   f"(Python/numpy{', BLAS limited to 1 thread' if limiter.active else ''}), {search_s:.1f} s; "
-                   f"oracle build {build_s:.1f} s on {os.cpu_count()} cores not timed"),
-        "recall_at_10_gpu": O.recall_at(gpu_ids[:done], truth, 10),
-        "recall_at_10_oracle": O.recall_at(ref_ids, truth, 10),
-        "gpu_eq_oracle_top10": float(np.mean([np.array_equal(gpu_ids[i, :10], ref_ids[i, :10])
-                                              for i in range(done)])),
-    }
-    return out
+        for ids in pool.imap(_pool_search, jobs, chunksize=1):
+            out.append(ids)
+            done = sum(len(o) for o in out)
+            if budget_s is not None and done >= min_queries and time.perf_counter() - t >= budget_s:
+                break
+        elapsed = time.perf_counter() - t
+        pool.terminate()
+    return np.concatenate(out) if out else np.zeros((0, cfg["k"]), np.int64), elapsed
+
+
+class OracleBaseline:
+    """The FP64 oracle timed on every host core, in a child process forked
+    before this process starts CUDA (so its worker pool forks from a process
+    without a CUDA context).  The child waits until the GPU measurement is
+    over, then builds the oracle's own index (k-means from the same seed) and
+    searches a bounded sample of the queries: at least `min_queries` and at
+    least `budget_s` seconds of search, on a fork pool of one worker per core
+    (BLAS one thread each); its ids come back to this process.  Nothing in
+    the child touches the GPU."""
+
+    def __init__(self, cfg, X, Q, A, b, budget_s: float, min_queries: int):
+        import multiprocessing as mp
+        self.conn, child = mp.Pipe()
+        self.pid = os.fork()
+        if self.pid == 0:                                   # child: no CUDA here
+            code = 0
+            try:
+                msg = child.recv()
+                if msg is not None:
+                    child.send(self._run(cfg, X, Q, A, b, budget_s, min_queries, msg))
+            except Exception as e:  # noqa: BLE001 - reported in the line
+                try:
+                    child.send({"error": f"{type(e).__name__}: {e}"[:300]})
+                except Exception:  # noqa: BLE001
+                    code = 1
+            os._exit(code)
+        child.close()
+
+    @staticmethod
+    def _run(cfg, X, Q, A, b, budget_s, min_queries, _go):
+        cores = host_cores()
+        idx, t_km, t_build = oracle_build(cfg, X, A, b)
+        ref_ids, search_s = oracle_pool_search(idx, Q, cfg, cores, 4, budget_s, min_queries)
+        return {"ids": ref_ids, "search_s": search_s, "cores": cores, "t_km": t_km, "t_build": t_build}
+
+    def result(self, gpu_ids, X, Q) -> dict:
+        """Start the oracle, wait for it, and report its throughput with
+        recall@10 of both sides on its sample against FP64 brute force (on the
+        device, for at most the first 2,000 sampled queries)."""
+        self.conn.send(True)
+        r = self.conn.recv()
+        os.waitpid(self.pid, 0)
+        if "error" in r:
+            return r
+        ref_ids, search_s, cores = r["ids"], r["search_s"], r["cores"]
+        done = len(ref_ids)
+        nt = min(done, 2000)
+        truth = fp64_knn(X, Q[:nt], 10)
+        extrapolated = done < len(Q)
+        return {
+            "value": done / search_s, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": (f"first {done:,} of {len(Q):,} queries of the same workload, FP64 oracle search "
+                       f"(Python/numpy) on {cores} worker processes (one BLAS thread each), {search_s:.1f} s"
+                       f"{'; queries/s extrapolated from the sample' if extrapolated else ''}; the oracle's own "
+                       f"k-means ({r['t_km']:.1f} s) and index build ({r['t_build']:.1f} s) not timed"),
+            "oracle_build_s": {"kmeans": r["t_km"], "index": r["t_build"]},
+            "recall_sample": f"first {nt:,} queries against FP64 brute force",
+            "recall_at_10_gpu": recall10(gpu_ids[:nt], truth),
+            "recall_at_10_oracle": recall10(ref_ids[:nt], truth),
+            "gpu_eq_oracle_top10": float(np.mean([np.array_equal(gpu_ids[i, :10], ref_ids[i, :10])
+                                                  for i in range(done)])),
+        }
+
+    def cancel(self):
+        try:
+            self.conn.send(None)
+            os.waitpid(self.pid, 0)
+        except Exception:  # noqa: BLE001
+            pass
 
 
 def run_reference(args, cfg):
-    """--impl reference: the FP64 oracle timed on host cores (rank 0 only)."""
+    """--impl reference: the FP64 oracle timed on every host core (rank 0
+    only): its own k-means and index build (not timed), then per step one
+    batch of --ref-queries-per-step queries per core, searched by a fork pool
+    of one worker per core."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    from oracle import lider_oracle as O
-    X, Q, C, A, b = load_inputs(cfg)
-    idx = O.build_index(X, C, A, b, cfg["L"], cfg["m"], cfg["W"], cfg["leaves"], B=cfg["B"])
-    per_step = args.ref_queries_per_step
+    X, Q, A, b = load_inputs(cfg)
+    idx, t_km, t_build = oracle_build(cfg, X, A, b)
+    cores = host_cores()
+    per_step = args.ref_queries_per_step * cores
     times = []
-    limiter = blas_threads(1)
-    with limiter:
-        for s in range(args.warmup + args.steps):
-            q0 = (s * per_step) % len(Q)
-            t = time.perf_counter()
-            O.search(idx, Q[q0:q0 + per_step], cfg["k"], cfg["c"], cfg["R"])
-            if s >= args.warmup:
-                times.append(time.perf_counter() - t)
+    for s in range(args.warmup + args.steps):
+        q0 = (s * per_step) % len(Q)
+        Qs = Q[q0:q0 + per_step]
+        _, sec = oracle_pool_search(idx, Qs, cfg, cores, args.ref_queries_per_step, None)
+        if s >= args.warmup:
+            times.append(sec)
     total = sum(times)
     value = per_step * len(times) / total
-    cores = 1 if limiter.active else os.cpu_count()
-    sample = (f"{per_step} queries per step of the {cfg['nq']:,}-query batch, FP64 oracle "
-              f"(Python/numpy{', BLAS limited to 1 thread' if limiter.active else ''})")
+    sample = (f"{per_step} queries per step of the {cfg['nq']:,}-query batch ({args.ref_queries_per_step} per "
+              f"worker), FP64 oracle (Python/numpy) on {cores} worker processes (one BLAS thread each); its "
+              f"k-means ({t_km:.1f} s) and index build ({t_build:.1f} s) not timed")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
@@ -276,6 +396,64 @@ def job_throughput(nq_per_rank: int, steps: int, world: int, job_ms: float) -> f
     return world * nq_per_rank * steps / (job_ms / 1e3)
 
 
+def score_roofline(score: str, stats: dict, route: np.ndarray, cl_off: np.ndarray, d: int, score_s: float,
+                   clk: dict) -> dict:
+    """Roofline of the score phase (tc_units_kernel + tc_score_kernel, or the
+    SIMT score_group_kernel) on the method's own work:
+      achieved  useful FLOPs, 2 x (unique candidates) x d, per second;
+      peak      the measured dense tensor peak of the contraction's type
+                (TF32 and FP8 from the BF16 figure by the nominal ratios);
+      executed  the FLOPs of the dense tiles actually run (padding included);
+      unique_bytes  what the phase must read at least once: the rows of the
+                probed clusters and the gathered queries in the operand type,
+                plus one candidate bitmap word per 32 cluster positions per
+                (query, cluster) pair; against the measured copy bandwidth."""
+    cand = stats["candidates"]
+    useful = 2.0 * cand * d
+    hbm, bf16, _, peak_kind = measured_peaks()
+    src = "of measured (MEASURED_PEAKS.json)" if peak_kind == "measured" else "of fallback"
+    sizes = np.diff(cl_off)
+    probed = np.unique(route[route >= 0])
+    pair_sizes = sizes[route.ravel()]
+    operand = {"tensor": 8, "f16": 2, "bf16": 2, "fp8": 1, "simt": 4}[score]
+    ub = float(sizes[probed].sum() * d * operand + route.size * d * operand + np.sum(-(-pair_sizes // 32)) * 4)
+    if score == "simt":
+        peak = fp32_simt_peak_tflops(clk.get("sm_max_mhz") or 2032.0)
+        r = {"bound": "alu", "kernel": "score_group_kernel", "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+        executed = None
+    else:
+        if score == "tensor":
+            kpad, mult, peak = -(-d // 32) * 32, 3, bf16 * TF32_PER_BF16
+            psrc = f"bf16 burst {bf16} x {TF32_PER_BF16:.3f} (nominal TF32/BF16), {src}"
+        elif score == "fp8":
+            kpad, mult, peak = -(-d // 128) * 128, 1, bf16 * FP8_PER_BF16
+            psrc = f"bf16 burst {bf16} x {FP8_PER_BF16:.1f} (nominal FP8/BF16), {src}"
+        else:
+            kpad, mult, peak = -(-d // 64) * 64, 1, bf16
+            psrc = f"bf16 burst {bf16}" + (" (FP16 has the same dense rate)" if score == "f16" else "") + f", {src}"
+        executed = stats["tc_tiles"] * 128 * 256 * kpad * 2.0 * mult
+        r = {"bound": "tensor", "kernel": "tc_score_kernel", "peak_source": psrc}
+    achieved = useful / score_s / 1e12
+    # DRAM bytes per launch: the full-size capture's bytes per tile times this
+    # launch's tiles (the FP16 mode's kernel at the time of the capture)
+    traffic = F16_TC_DRAM_BYTES_PER_TILE * stats["tc_tiles"] if (score == "f16" and F16_TC_DRAM_BYTES_PER_TILE) else None
+    r.update({
+        "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+        "work": "useful: 2 x unique candidates x d per launch", "useful_flop_per_launch": useful,
+        "phase_ms": score_s * 1e3,
+        "unique_bytes": {"bytes_per_launch": ub, "achieved_gbs": ub / score_s / 1e9, "peak_gbs": hbm,
+                         "frac": ub / score_s / 1e9 / hbm},
+    })
+    if executed is not None:
+        r["executed"] = {"flop_per_launch": executed, "tiles_per_launch": stats["tc_tiles"],
+                         "tflops": executed / score_s / 1e12, "frac": executed / score_s / 1e12 / peak,
+                         "useful_share": useful / executed}
+    if traffic is not None:
+        r["traffic_gbs"] = {"achieved": traffic / score_s / 1e9, "peak": hbm, "frac": traffic / score_s / 1e9 / hbm,
+                            "note": F16_TC_DRAM_NOTE}
+    return r
+
+
 def run_lider(args, cfg):
     import torch
     import torch.distributed as dist
@@ -285,17 +463,22 @@ def run_lider(args, cfg):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    X, Q, A, b = load_inputs(cfg)
+    # the CPU baseline's process forks now, before this process starts CUDA
+    oracle = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        oracle = OracleBaseline(cfg, X, Q, A, b, args.cpu_budget, args.cpu_min_queries)
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
 
-    X, Q, C, A, b = load_inputs(cfg)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     Xd = t(X)
     mode = MODES[args.score]
-    idx = lider.Index(Xd, t(C), t(A), t(b), L=cfg["L"], m=cfg["m"], W=cfg["W"], rmi_leaves=cfg["leaves"],
-                      r0=cfg["r0"], B=cfg["B"], score_mode=mode, rerank=args.rerank)
+    idx = build_gpu_index(cfg, Xd, A, b, score_mode=mode, rerank=args.rerank)
+    build = idx.build_info()
+    C = idx.centroids()          # reused by the served comparison's index
     del Xd
     Qd = t(Q)
     k, c, nq = cfg["k"], cfg["c"], cfg["nq"]
@@ -317,8 +500,10 @@ def run_lider(args, cfg):
         tune, tune_ms = idx.autotune(Qd[lo:hi], k, c, reps=3)
         tuning = dict(tune, ms_per_search=tune_ms, queries_per_call=hi - lo)
     stats = None
+    route = np.zeros((nq, c), dtype=np.int32)
     for lo, hi in chunks:
-        _, _, st = idx.search(Qd[lo:hi], k, c, stats=True, out=(ids[lo:hi], sc[lo:hi]))
+        _, _, st, tr = idx.search(Qd[lo:hi], k, c, stats=True, trace=True, out=(ids[lo:hi], sc[lo:hi]))
+        route[lo:hi] = tr["route"].cpu().numpy()
         stats = st if stats is None else {key: stats[key] + st[key] for key in stats}
     gpu_ids = ids.cpu().numpy()
 
@@ -395,59 +580,16 @@ def run_lider(args, cfg):
     e2e_s = max_over_ranks(time.perf_counter() - te, dev)
     e2e_value = job_throughput(nq, args.steps, world, e2e_s * 1e3)
 
-    cand = stats["candidates"]
-    d = cfg["d"]
-    gather_bytes = cand * (d * 4 + 4)                 # candidate rows + ids, per launch
-    useful_flop = 2.0 * cand * d                      # exact inner products of the candidates
-    score_s = phase_ms["score"] / 1e3
-    hbm, bf16, bf16_sus, peak_kind = measured_peaks()
-    src = "MEASURED_PEAKS.json" if peak_kind == "measured" else "fallback figures"
-    if args.score in ("tensor", "bf16", "f16", "fp8"):
-        if args.score == "tensor":
-            kpad = -(-d // 32) * 32
-            tc_flop = stats["tc_tiles"] * 128 * 256 * kpad * 2.0 * 3   # three TF32 products per FP32 product
-            peak = bf16 * TF32_PER_BF16
-            psrc = f"{src}: bf16 burst {bf16} x {TF32_PER_BF16:.3f} (nominal TF32/BF16)"
-        elif args.score == "fp8":
-            kpad = -(-d // 128) * 128
-            tc_flop = stats["tc_tiles"] * 128 * 256 * kpad * 2.0       # one FP8 product
-            peak = bf16 * FP8_PER_BF16
-            psrc = f"{src}: bf16 burst {bf16} x {FP8_PER_BF16:.1f} (nominal FP8/BF16)"
-        else:
-            kpad = -(-d // 64) * 64
-            tc_flop = stats["tc_tiles"] * 128 * 256 * kpad * 2.0       # one BF16 product
-            peak = bf16
-            psrc = f"{src}: bf16 burst" + (" (FP16 has the same dense rate)" if args.score == "f16" else "")
-        achieved = tc_flop / score_s / 1e12
-        # DRAM bytes per launch: the full-size capture's bytes per tile times this
-        # launch's tiles (exact for the mid workload; FP16 mode only)
-        traffic = F16_TC_DRAM_BYTES_PER_TILE * stats["tc_tiles"] if args.score == "f16" else None
-        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": traffic, "kernel": "tc_score_kernel",
-                    "peak_source": psrc,
-                    "tensor_flop_per_launch": tc_flop,
-                    "tiles_per_launch": stats["tc_tiles"],
-                    "useful_flop_per_launch": useful_flop,
-                    "useful_tflops": useful_flop / score_s / 1e12}
-        if traffic is not None:
-            roofline["traffic_note"] = ("ncu DRAM bytes of one full-size mid launch (18,211 tiles), per tile, "
-                                        "times this launch's tiles")
-            roofline["dram_gbs_vs_hbm"] = {"achieved": traffic / score_s / 1e9, "peak": hbm,
-                                           "frac": traffic / score_s / 1e9 / hbm}
-    else:
-        peak = fp32_simt_peak_tflops(clk.get("sm_max_mhz") or 2032.0)
-        achieved = useful_flop / score_s / 1e12
-        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "kernel": "score_group_kernel",
-                    "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x max SM clock",
-                    "useful_flop_per_launch": useful_flop,
-                    "gather_bytes_per_launch": gather_bytes,
-                    "gather_gbs_vs_hbm": {"achieved": gather_bytes / score_s / 1e9, "peak": hbm,
-                                          "frac": gather_bytes / score_s / 1e9 / hbm}}
-
+    roofline = score_roofline(args.score, stats, route, idx.cluster_offsets(), cfg["d"], phase_ms["score"] / 1e3,
+                              clk)
     served = None
     if world == 1 and args.score in ("f16", "tensor", "simt") and not args.no_served:
         served = served_compare(args, cfg, X, C, A, b, Qd, chunks, gpu_ids, dev)
+    build_line = {"kmeans_ms": build["kmeans_ms"], "build_ms": build["build_ms"],
+                  "clustering": (f"k-means on the device: {build['n_clusters']} clusters, {build['kmeans_iters']} "
+                                 f"Lloyd iterations on the first {build['train_rows']:,} rows, Forgy rows from "
+                                 f"seed {build['seed']}"),
+                  "empty_clusters": build["empty_clusters"], "timed": False}
 
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
@@ -471,10 +613,11 @@ def run_lider(args, cfg):
                    f"served shortlist: {DTYPES[args.score]} scores, FP32 re-rank of the best {args.rerank} * k",
         "clocks": clk,
     }
+    line["build"] = build_line
     if served is not None:
         line["served_bf16"] = served
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cfg, X, Q, C, A, b, gpu_ids, args.cpu_budget)
+    if oracle is not None:
+        line["cpu_baseline"] = oracle.result(gpu_ids, X, Q)
     if rank == 0:
         print(json.dumps(line), flush=True)
     idx.free()
@@ -542,12 +685,11 @@ def run_serve(args, cfg):
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    X, Q, C, A, b = load_inputs(cfg)
+    X, Q, A, b = load_inputs(cfg)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     Xd = t(X)
     mode = MODES[args.score]
-    idx = lider.Index(Xd, t(C), t(A), t(b), L=cfg["L"], m=cfg["m"], W=cfg["W"], rmi_leaves=cfg["leaves"],
-                      r0=cfg["r0"], B=cfg["B"], score_mode=mode, rerank=args.rerank)
+    idx = build_gpu_index(cfg, Xd, A, b, score_mode=mode, rerank=args.rerank)
     del Xd
     ks = (10, cfg["k"])
     srv = Server(idx, cfg["c"], slots=args.serve_slots, max_batch=args.serve_max_batch, max_k=max(ks),
@@ -651,10 +793,13 @@ def run_variants(args, cfg):
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    X, Q, C, A, b = load_inputs(cfg)
+    X, Q, A, b = load_inputs(cfg)
     k, c, nq = cfg["k"], cfg["c"], cfg["nq"]
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    Qd, Xd, Cd = t(Q), t(X), t(C)
+    Qd, Xd = t(Q), t(X)
+    first = build_gpu_index(cfg, Xd, A, b, score_mode=lider.SCORE_F16)   # k-means once; the variants share it
+    Cd = t(first.centroids())
+    first.free()
     variants = {
         "plain": {},
         "hyperplane": dict(hash_kind=lider.HASH_HYPERPLANE, m=args.hyper_m),
@@ -728,15 +873,17 @@ def run_precision(args, cfg):
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    X, Q, C, A, b = load_inputs(cfg)
+    X, Q, A, b = load_inputs(cfg)
     k, c, nq = cfg["k"], cfg["c"], cfg["nq"]
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     Qd = t(Q)
     out = {}
+    C = None                          # k-means runs in the first build; the others reuse its centroids
     for name in ("f16", "bf16", "fp8"):
         Xd = t(X)
-        idx = lider.Index(Xd, t(C), t(A), t(b), L=cfg["L"], m=cfg["m"], W=cfg["W"], rmi_leaves=cfg["leaves"],
-                          r0=cfg["r0"], B=cfg["B"], score_mode=MODES[name], rerank=args.rerank)
+        idx = build_gpu_index(cfg, Xd, A, b, centroids=C, score_mode=MODES[name], rerank=args.rerank)
+        if C is None:
+            C = idx.centroids()
         del Xd
         torch.cuda.empty_cache()
         sub = call_size(idx, nq, k, c, args.sub_batch or nq)
@@ -821,7 +968,10 @@ def main():
                     help="keep the raw nvidia-smi clock samples of the timed region in this directory")
     ap.add_argument("--no-served", action="store_true",
                     help="skip the served BF16 comparison run on the same queries")
-    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--cpu-budget", type=float, default=15.0,
+                    help="CPU baseline: seconds of oracle search at least (after --cpu-min-queries)")
+    ap.add_argument("--cpu-min-queries", type=int, default=1000,
+                    help="CPU baseline: queries the oracle searches at least")
     ap.add_argument("--ref-queries-per-step", type=int, default=8)
     ap.add_argument("--n", type=int, default=None, help="profiling size: first n corpus rows")
     ap.add_argument("--nq", type=int, default=None, help="profiling size: first nq queries")

@@ -176,13 +176,59 @@ typedef struct {
     void* const* events;
 } lider_trace;
 
-/* Build an index (Sec. 3.3.2 "LIDER is built as follows"; Sec. 3.3.1 for one
- * core model; Table 5 stages 2-3).
+/* How lider_build clusters the corpus (Sec. 3.2: k-means) and seeds its
+ * random draws.
+ *   n_clusters    the paper's c, number of k-means clusters (1 .. training rows);
+ *   kmeans_iters  Lloyd iterations (0 keeps the initial rows as centroids);
+ *   kmeans_sample k-means learns from the first min(kmeans_sample, n) corpus
+ *                 rows (0: all n); every row is then partitioned;
+ *   seed          the initial centroids are the Forgy rows of the training
+ *                 rows that Floyd's sampling algorithm draws from SplitMix64
+ *                 started at `seed` (draw i = mix64(seed + (i+1)*0x9E3779B97F4A7C15),
+ *                 uniform integer on [0, j] = draw mod (j+1); rows in ascending
+ *                 order become centroids 0, 1, ...); when lider_build gets no
+ *                 projections it also draws them from `seed`. */
+typedef struct {
+    int32_t  n_clusters;
+    int32_t  kmeans_iters;
+    int64_t  kmeans_sample;
+    uint64_t seed;
+} lider_cluster_params;
+
+/* Build an index from a corpus alone (Sec. 3.3.2 "LIDER is built as follows";
+ * Sec. 3.2 for the clustering, Sec. 3.3.1 for one core model; Table 5 stages
+ * 1-3), on the device:
+ *   1. k-means: Lloyd iterations from the Forgy rows of `cluster`; each round
+ *      assigns every training row to the centroid maximising x.mu - |mu|^2/2
+ *      (exact up to FP64 rounding: compensated dot products finished in FP64;
+ *      ties to the lower index) and moves each centroid to the FP64 mean of its
+ *      rows, rounded to FP32 (a cluster left empty keeps its centroid);
+ *   2. partition of all n rows by the same nearest-centroid rule;
+ *   3. hashing, segment sorts and RMI fits, as for lider_build_centroids.
+ *   corpus     device, n x d FP32, the embeddings (n >= 1, d % 4 == 0);
+ *   cluster    host, see lider_cluster_params;
+ *   A, b       device, (L*m) x d and (L*m) FP32: row l*m+j of A and entry
+ *              l*m+j of b define hash j of array l (the LSH draws, Sec. 4.1);
+ *              both NULL: drawn on the device from cluster->seed (A ~ N(0,1)
+ *              by Box-Muller from SplitMix64 draws, b ~ U[0, W)); the draws
+ *              can be read back with lider_export_projections;
+ *   params     host, see lider_params;
+ *   stream     the build runs on it and is synchronised before returning;
+ *   out        host, receives the new index.
+ * The caller keeps ownership of its buffers.  Errors: those of
+ * lider_build_centroids; LIDER_EINVAL also for a NULL `cluster`, only one of
+ * A and b given, kmeans_iters outside [0, 100000], kmeans_sample < 0, or
+ * n_clusters above the training rows.  On error *out is NULL. */
+int lider_build(const float* corpus, int64_t n, int32_t d, const lider_cluster_params* cluster,
+                const float* A, const float* b, const lider_params* params, void* stream,
+                lider_index** out);
+
+/* Build an index from given centroids (Sec. 3.3.2; Sec. 3.3.1 for one core
+ * model; Table 5 stages 2-3): no clustering runs.
  *   corpus     device, n x d FP32, the embeddings (n >= 1, d % 4 == 0);
  *   centroids  device, n_clusters x d FP32, the k-means centroids; every point
  *              joins the centroid maximising x.mu - |mu|^2/2 (ties: lower index);
- *   A, b       device, (L*m) x d and (L*m) FP32: row l*m+j of A and entry
- *              l*m+j of b define hash j of array l (the LSH draws, Sec. 4.1);
+ *   A, b       device, (L*m) x d and (L*m) FP32, as for lider_build (required);
  *   params     host, see lider_params;
  *   stream     the build runs on it and is synchronised before returning;
  *   out        host, receives the new index.
@@ -193,10 +239,32 @@ typedef struct {
  * LIDER_ELIMIT past the caps above (and n_clusters > 8192 with
  * LIDER_ROUTE_CORE);
  * LIDER_ENOMEM / LIDER_ECUDA from the device.  On error *out is NULL. */
-int lider_build(const float* corpus, int64_t n, int32_t d,
-                const float* centroids, int32_t n_clusters,
-                const float* A, const float* b,
-                const lider_params* params, void* stream, lider_index** out);
+int lider_build_centroids(const float* corpus, int64_t n, int32_t d,
+                          const float* centroids, int32_t n_clusters,
+                          const float* A, const float* b,
+                          const lider_params* params, void* stream, lider_index** out);
+
+/* How an index was built (host output). */
+typedef struct {
+    int32_t  clustered;          /* 1: k-means ran in lider_build; 0: centroids given */
+    int32_t  projections_drawn;  /* 1: A and b were drawn from the seed               */
+    lider_cluster_params cluster;/* the clustering parameters (clustered == 1)         */
+    int64_t  train_rows;         /* rows k-means learned from (clustered == 1)         */
+    int32_t  empty_clusters;     /* clusters that hold no corpus row                   */
+    int32_t  reserved;
+    double   kmeans_ms;          /* host wall time of the k-means iterations           */
+    double   build_ms;           /* host wall time of the whole build                  */
+} lider_build_info;
+
+int lider_get_build_info(const lider_index* index, lider_build_info* info);
+
+/* Copy the index's FP32 centroids (n_clusters x d, host) / the cluster of
+ * every corpus row (n int32, host, indexed by corpus row id) / the LSH draws
+ * (A: (L*m) x d FP32 and b: L*m FP32, host; either may be NULL).
+ * Synchronous. */
+int lider_export_centroids(const lider_index* index, float* centroids_host);
+int lider_export_assignment(const lider_index* index, int32_t* asg_host);
+int lider_export_projections(const lider_index* index, float* A_host, float* b_host);
 
 /* Batched k-NN search (Sec. 3.3.2 "When using LIDER for ANN queries"; Sec. 6).
  *   queries     device, nq x d FP32, starting on a 16-byte boundary;

@@ -1,7 +1,9 @@
 // extern "C" entry points of liblider.so (declared in include/lider.h) and the
 // thread-local error message.  No C++ exception crosses this boundary.
+#include <algorithm>
 #include <exception>
 #include <string>
+#include <vector>
 
 #include "lider_internal.cuh"
 
@@ -26,8 +28,8 @@ int cuda_fail(cudaError_t e, const char* what) {
     return e == cudaErrorMemoryAllocation ? LIDER_ENOMEM : LIDER_ECUDA;
 }
 
-int build_entry(const float*, int64_t, int32_t, const float*, int32_t, const float*, const float*,
-                const lider_params*, void*, lider_index**);
+int build_entry(const float*, int64_t, int32_t, const float*, int32_t, const lider_cluster_params*, const float*,
+                const float*, const lider_params*, void*, lider_index**);
 void destroy_index(lider_index*);
 int search_entry(const lider_index*, const float*, int64_t, int, int, int64_t*, float*, const lider_trace*,
                  lider_search_stats*, void*);
@@ -62,9 +64,75 @@ using namespace lider;
 
 extern "C" {
 
-int lider_build(const float* corpus, int64_t n, int32_t d, const float* centroids, int32_t n_clusters,
-                const float* A, const float* b, const lider_params* params, void* stream, lider_index** out) {
-    return guarded([&] { return build_entry(corpus, n, d, centroids, n_clusters, A, b, params, stream, out); });
+int lider_build(const float* corpus, int64_t n, int32_t d, const lider_cluster_params* cluster, const float* A,
+                const float* b, const lider_params* params, void* stream, lider_index** out) {
+    return guarded([&]() -> int {
+        if (!cluster) {
+            if (out) *out = nullptr;
+            return fail(LIDER_EINVAL, "lider_build: cluster is NULL");
+        }
+        return build_entry(corpus, n, d, nullptr, 0, cluster, A, b, params, stream, out);
+    });
+}
+
+int lider_build_centroids(const float* corpus, int64_t n, int32_t d, const float* centroids, int32_t n_clusters,
+                          const float* A, const float* b, const lider_params* params, void* stream,
+                          lider_index** out) {
+    return guarded([&] {
+        return build_entry(corpus, n, d, centroids, n_clusters, nullptr, A, b, params, stream, out);
+    });
+}
+
+int lider_get_build_info(const lider_index* index, lider_build_info* info) {
+    if (!index || !info) return fail(LIDER_EINVAL, "lider_get_build_info: NULL argument");
+    *info = lider_build_info{};
+    info->clustered = index->clustered ? 1 : 0;
+    info->projections_drawn = index->projections_drawn ? 1 : 0;
+    info->cluster = index->cluster;
+    if (index->clustered)
+        info->train_rows = index->cluster.kmeans_sample == 0 ? index->g.n
+                                                              : std::min<int64_t>(index->cluster.kmeans_sample, index->g.n);
+    int32_t empty = 0;
+    for (int j = 0; j < index->g.ncl; ++j) empty += index->h_cl_off[j + 1] == index->h_cl_off[j];
+    info->empty_clusters = empty;
+    info->kmeans_ms = index->kmeans_ms;
+    info->build_ms = index->build_ms;
+    return LIDER_OK;
+}
+
+int lider_export_centroids(const lider_index* index, float* centroids_host) {
+    return guarded([&]() -> int {
+        if (!index || !centroids_host) return fail(LIDER_EINVAL, "lider_export_centroids: NULL argument");
+        LIDER_CUDA_TRY(cudaMemcpy(centroids_host, index->g.C, (size_t)index->g.ncl * index->g.d * sizeof(float),
+                                  cudaMemcpyDeviceToHost));
+        return LIDER_OK;
+    });
+}
+
+int lider_export_assignment(const lider_index* index, int32_t* asg_host) {
+    return guarded([&]() -> int {
+        if (!index || !asg_host) return fail(LIDER_EINVAL, "lider_export_assignment: NULL argument");
+        const Geometry& g = index->g;
+        std::vector<int64_t> orig((size_t)g.n);
+        LIDER_CUDA_TRY(cudaMemcpy(orig.data(), g.orig_id, (size_t)g.n * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        for (int j = 0; j < g.ncl; ++j)
+            for (int64_t r = index->h_cl_off[j]; r < index->h_cl_off[j + 1]; ++r) {
+                if (orig[r] < 0 || orig[r] >= g.n) return fail(LIDER_ECUDA, "lider_export_assignment: corrupt id");
+                asg_host[orig[r]] = j;
+            }
+        return LIDER_OK;
+    });
+}
+
+int lider_export_projections(const lider_index* index, float* A_host, float* b_host) {
+    return guarded([&]() -> int {
+        if (!index) return fail(LIDER_EINVAL, "lider_export_projections: index is NULL");
+        const Geometry& g = index->g;
+        if (A_host)
+            LIDER_CUDA_TRY(cudaMemcpy(A_host, g.A, (size_t)g.H * g.d * sizeof(float), cudaMemcpyDeviceToHost));
+        if (b_host) LIDER_CUDA_TRY(cudaMemcpy(b_host, g.bproj, (size_t)g.H * sizeof(float), cudaMemcpyDeviceToHost));
+        return LIDER_OK;
+    });
 }
 
 int lider_search(const lider_index* index, const float* queries, int64_t nq, int32_t k, int32_t c,

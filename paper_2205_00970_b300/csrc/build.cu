@@ -1,17 +1,21 @@
 // Index construction (Sec. 3.3.2 "LIDER is built as follows", Sec. 3.3.1 for
-// one core model): partition the corpus by nearest centroid, hash every point
-// into L packed hashkeys, sort each (cluster, array) segment by key (ties by
-// id), then fit one two-stage linear RMI per segment on re-scaled keys
-// (Sec. 5.1, Sec. 5.2) and record each leaf's error window.
+// one core model): cluster the corpus by k-means (Sec. 3.2; Lloyd iterations
+// on the device from Forgy rows, unless the caller gives the centroids),
+// partition it by nearest centroid, hash every point into L packed hashkeys
+// (projections given, or drawn from the seed), sort each (cluster, array)
+// segment by key (ties by id), then fit one two-stage linear RMI per segment
+// on re-scaled keys (Sec. 5.1, Sec. 5.2) and record each leaf's error window.
 //
 // Build is not on the search hot path; its sorts use CUB.
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_segmented_radix_sort.cuh>
 
 #include <algorithm>
-#include <functional>
+#include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
+#include <unordered_set>
 
 #include <cuda_fp16.h>
 
@@ -155,6 +159,96 @@ __global__ void local_pos_kernel(const int32_t* __restrict__ sorted_asg, const i
     if (row >= n) return;
     const int32_t p = (int32_t)(row - cl_off[sorted_asg[row]]);
     for (int l = 0; l < L; ++l) pos[(int64_t)l * n + row] = p;
+}
+
+// ---------------------------------------------------------------- k-means ----
+// Forgy initialisation: the n_clusters initial centroids are distinct rows of
+// the training rows, drawn by Floyd's sampling algorithm (Bentley and Floyd,
+// 1987) from the counter-based SplitMix64 generator (Steele, Lea and Flood,
+// 2014): draw i is mix64(seed + (i + 1) * 0x9E3779B97F4A7C15 mod 2^64), and the
+// integer uniform on [0, j] is that draw mod (j + 1).  Rows ascending.
+uint64_t splitmix64(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t splitmix64_dev(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+std::vector<int64_t> forgy_rows(uint64_t seed, int64_t n, int64_t count) {
+    std::unordered_set<int64_t> chosen;
+    chosen.reserve((size_t)count * 2);
+    uint64_t i = 0;
+    for (int64_t j = n - count; j < n; ++j, ++i) {
+        const int64_t t = (int64_t)(splitmix64(seed, i) % (uint64_t)(j + 1));
+        chosen.insert(chosen.count(t) ? j : t);
+    }
+    std::vector<int64_t> rows(chosen.begin(), chosen.end());
+    std::sort(rows.begin(), rows.end());
+    return rows;
+}
+
+// Lloyd update (Sec. 3.2): centroid j becomes the mean of its rows, summed in
+// FP64 over the rows in ascending order (four interleaved partial sums joined
+// in a fixed order, so the result does not depend on scheduling) and rounded to
+// FP32, the precision the index keeps; a cluster without rows keeps its
+// centroid.  Block (cluster, 128 dimensions), thread per dimension: the
+// member rows' loads are coalesced across the block.
+__global__ void __launch_bounds__(128) centroid_mean_kernel(const float* __restrict__ X, int d,
+                                                            const int64_t* __restrict__ rows,
+                                                            const int64_t* __restrict__ off, float* __restrict__ C) {
+    const int j = blockIdx.x;
+    const int i = blockIdx.y * blockDim.x + threadIdx.x;
+    if (i >= d) return;
+    const int64_t s = off[j], e = off[j + 1];
+    if (s >= e) return;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int64_t r = s;
+    for (; r + 4 <= e; r += 4) {
+        a0 = __dadd_rn(a0, (double)X[rows[r] * d + i]);
+        a1 = __dadd_rn(a1, (double)X[rows[r + 1] * d + i]);
+        a2 = __dadd_rn(a2, (double)X[rows[r + 2] * d + i]);
+        a3 = __dadd_rn(a3, (double)X[rows[r + 3] * d + i]);
+    }
+    for (; r < e; ++r) a0 = __dadd_rn(a0, (double)X[rows[r] * d + i]);
+    const double sum = __dadd_rn(__dadd_rn(a0, a1), __dadd_rn(a2, a3));
+    C[(int64_t)j * d + i] = __double2float_rn(__ddiv_rn(sum, (double)(e - s)));
+}
+
+// LSH draws from the seed when the caller gives none (Sec. 4.1: the hash
+// family is random): a_hi ~ N(0, 1) by the Box-Muller transform of two
+// SplitMix64 draws, b_h ~ U[0, W) (kept below W after rounding to FP32); the
+// two streams start from states derived from the seed.  Hyperplane hashes take
+// no offsets (b = 0).
+constexpr uint64_t kStreamA = 0x4C49444552000001ull;   // derived-state indices of
+constexpr uint64_t kStreamB = 0x4C49444552000002ull;   // the two streams
+
+__global__ void draw_projections_kernel(uint64_t seed, int H, int d, float W, bool hyper, float* __restrict__ A,
+                                        float* __restrict__ b) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t sa = splitmix64_dev(seed, kStreamA), sb = splitmix64_dev(seed, kStreamB);
+    if (e < (int64_t)H * d) {
+        const uint64_t r1 = splitmix64_dev(sa, 2 * (uint64_t)e), r2 = splitmix64_dev(sa, 2 * (uint64_t)e + 1);
+        const double u1 = ((double)(r1 >> 11) + 1.0) * 0x1.0p-53;    // (0, 1]
+        const double u2 = (double)(r2 >> 11) * 0x1.0p-53;            // [0, 1)
+        A[e] = (float)(sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2));
+    }
+    if (e < H) {
+        if (hyper) {
+            b[e] = 0.f;
+        } else {
+            const double u = (double)(splitmix64_dev(sb, (uint64_t)e) >> 11) * 0x1.0p-53;
+            float v = (float)(u * (double)W);
+            if (!(v < W)) v = nextafterf(W, 0.f);
+            b[e] = v;
+        }
+    }
 }
 
 // ---------------------------------------------------------------- RMI fit ----
@@ -317,16 +411,78 @@ void release(lider_index* ix) {
     delete ix;
 }
 
+// Lloyd's k-means (Sec. 3.2) over the first ns rows of X: Forgy rows, then
+// `iters` rounds of exact nearest-centroid assignment (Dot2 scores of
+// x.mu - |mu|^2/2 finished in FP64, ties to the lower index; the same
+// arithmetic as the partition below) and centroid means (centroid_mean_kernel).
+// C receives the FP32 centroids.  The other buffers are scratch: asg and
+// asg_sorted hold ns int32, ids_in and ids_sorted ns int64, off ncl + 1 int64,
+// sbuf chunk x ncl FP64.
+int kmeans_run(const float* X, int64_t ns, int d, int ncl, int iters, uint64_t seed, float* C, double* hn,
+               double* sbuf, int64_t chunk, int32_t* asg, int32_t* asg_sorted, int64_t* ids_in, int64_t* ids_sorted,
+               int64_t* off, cudaStream_t st) {
+    {
+        const std::vector<int64_t> init = forgy_rows(seed, ns, ncl);
+        LIDER_CUDA_TRY(cudaMemcpyAsync(ids_in, init.data(), init.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        gather_rows_kernel<<<(unsigned)cdiv((int64_t)ncl * 32, 256), 256, 0, st>>>(X, ids_in, ncl, d, C);
+        LIDER_LAUNCH_CHECK("gather_rows_kernel<forgy>");
+        LIDER_CUDA_TRY(cudaStreamSynchronize(st));   // `init` is host memory of this scope
+    }
+    int end_bit = 1;
+    while ((1ll << end_bit) <= ncl) ++end_bit;
+    size_t tmp_bytes = 0;
+    LIDER_CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, asg, asg_sorted, ids_in, ids_sorted, ns, 0,
+                                                   end_bit, st));
+    DevBuf tmp;
+    int rc;
+    if ((rc = dev_alloc(&tmp.p, tmp_bytes, "k-means sort scratch"))) return rc;
+    for (int it = 0; it < iters; ++it) {
+        half_norm_kernel<<<(unsigned)cdiv(ncl, 128), 128, 0, st>>>(C, ncl, d, hn);
+        LIDER_LAUNCH_CHECK("half_norm_kernel");
+        for (int64_t r0 = 0; r0 < ns; r0 += chunk) {
+            const int64_t rows = std::min(chunk, ns - r0);
+            if ((rc = launch_scores(X + r0 * d, rows, d, C, hn, ncl, sbuf, st))) return rc;
+            argmax_rows_kernel<<<(unsigned)cdiv(rows * 32, 256), 256, 0, st>>>(sbuf, rows, ncl, r0, asg);
+            LIDER_LAUNCH_CHECK("argmax_rows_kernel");
+        }
+        iota_kernel<<<(unsigned)cdiv(ns, 256), 256, 0, st>>>(ids_in, ns);
+        LIDER_LAUNCH_CHECK("iota_kernel");
+        LIDER_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp.p, tmp_bytes, asg, asg_sorted, ids_in, ids_sorted, ns, 0,
+                                                       end_bit, st));
+        cluster_offsets_kernel<<<(unsigned)cdiv(ncl + 1, 128), 128, 0, st>>>(asg_sorted, ns, ncl, off);
+        LIDER_LAUNCH_CHECK("cluster_offsets_kernel");
+        centroid_mean_kernel<<<dim3((unsigned)ncl, (unsigned)cdiv(d, 128)), 128, 0, st>>>(X, d, ids_sorted, off, C);
+        LIDER_LAUNCH_CHECK("centroid_mean_kernel");
+    }
+    LIDER_CUDA_TRY(cudaStreamSynchronize(st));    // tmp is freed on return
+    return LIDER_OK;
+}
+
 int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids, int32_t ncl,
-               const float* A, const float* b, const lider_params* P, cudaStream_t st,
-               lider_index** out) {
+               const lider_cluster_params* cp, const float* A, const float* b, const lider_params* P,
+               cudaStream_t st, lider_index** out) {
+    using clock = std::chrono::steady_clock;
+    const auto t_start = clock::now();
     if (!out) return fail(LIDER_EINVAL, "lider_build: out is NULL");
     *out = nullptr;
-    if (!corpus || !centroids || !A || !b || !P) return fail(LIDER_EINVAL, "lider_build: NULL argument");
+    if (!corpus || !P) return fail(LIDER_EINVAL, "lider_build: NULL argument");
+    if (cp) {
+        if (centroids) return fail(LIDER_EINVAL, "lider_build: centroids are given and would also be clustered");
+        if ((A == nullptr) != (b == nullptr)) return fail(LIDER_EINVAL, "lider_build: give both A and b, or neither");
+        ncl = cp->n_clusters;
+        if (cp->kmeans_iters < 0 || cp->kmeans_iters > 100000)
+            return fail(LIDER_EINVAL, "lider_build: kmeans_iters must be in [0, 100000]");
+        if (cp->kmeans_sample < 0) return fail(LIDER_EINVAL, "lider_build: kmeans_sample must be >= 0");
+    } else if (!centroids || !A || !b) {
+        return fail(LIDER_EINVAL, "lider_build: NULL argument");
+    }
     if (n < 1 || n > (int64_t)INT32_MAX) return fail(LIDER_EINVAL, "lider_build: n must be in [1, 2^31-1]");
     if (d < 4 || d % 4 != 0) return fail(LIDER_EINVAL, "lider_build: d must be a positive multiple of 4");
     if (d > LIDER_MAX_D) return fail(LIDER_ELIMIT, "lider_build: d exceeds LIDER_MAX_D");
     if (ncl < 1) return fail(LIDER_EINVAL, "lider_build: n_clusters must be >= 1");
+    const int64_t n_train = cp ? (cp->kmeans_sample == 0 ? n : std::min<int64_t>(cp->kmeans_sample, n)) : 0;
+    if (cp && ncl > n_train)
+        return fail(LIDER_EINVAL, "lider_build: n_clusters exceeds the rows k-means learns from");
     if (P->L < 1 || P->m < 1 || P->rmi_leaves < 1 || P->r0 < 1 || P->B < 1)
         return fail(LIDER_EINVAL, "lider_build: L, m, rmi_leaves, r0 and B must be >= 1");
     if (P->hash_kind != LIDER_HASH_PSTABLE && P->hash_kind != LIDER_HASH_HYPERPLANE)
@@ -386,10 +542,40 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
     ALLOC(ix->root, (size_t)ncl * L * sizeof(RmiRoot), "rmi roots");
     ALLOC(ix->leaf, (size_t)ncl * L * F * sizeof(RmiLeaf), "rmi leaves");
 
-    LIDER_CUDA_TRY(cudaMemcpyAsync(ix->C, centroids, (size_t)ncl * d * sizeof(float), cudaMemcpyDefault, st));
-    LIDER_CUDA_TRY(cudaMemcpyAsync(ix->A, A, (size_t)H * d * sizeof(float), cudaMemcpyDefault, st));
-    if (hyper) LIDER_CUDA_TRY(cudaMemsetAsync(ix->bproj, 0, (size_t)H * sizeof(float), st));
-    else LIDER_CUDA_TRY(cudaMemcpyAsync(ix->bproj, b, (size_t)H * sizeof(float), cudaMemcpyDefault, st));
+    // scratch of the partition (and of k-means)
+    const int64_t chunk = std::min<int64_t>(n, kRowChunk);
+    DevBuf asg, asg_sorted, ids_in, tbuf, sbuf, errf;
+    ALLOC(asg.p, (size_t)n * sizeof(int32_t), "assignment");
+    ALLOC(asg_sorted.p, (size_t)n * sizeof(int32_t), "sorted assignment");
+    ALLOC(ids_in.p, (size_t)n * sizeof(int64_t), "ids");
+    ALLOC(sbuf.p, (size_t)chunk * std::max(ncl, H) * sizeof(double), "score chunk");
+    ALLOC(errf.p, 64, "flags");
+    LIDER_CUDA_TRY(cudaMemsetAsync(errf.p, 0, 64, st));
+
+    if (cp) {
+        // 0. k-means (Sec. 3.2); orig_id and cl_off serve as its scratch
+        LIDER_CUDA_TRY(cudaStreamSynchronize(st));
+        const auto t0 = clock::now();
+        if ((rc = kmeans_run(corpus, n_train, d, ncl, cp->kmeans_iters, cp->seed, ix->C, ix->half_norm,
+                             sbuf.as<double>(), std::min<int64_t>(n_train, kRowChunk), asg.as<int32_t>(),
+                             asg_sorted.as<int32_t>(), ids_in.as<int64_t>(), ix->orig_id, ix->cl_off, st)))
+            return rc;
+        ix->kmeans_ms = std::chrono::duration<double, std::milli>(clock::now() - t0).count();
+        ix->cluster = *cp;
+        ix->clustered = true;
+    } else {
+        LIDER_CUDA_TRY(cudaMemcpyAsync(ix->C, centroids, (size_t)ncl * d * sizeof(float), cudaMemcpyDefault, st));
+    }
+    if (A) {
+        LIDER_CUDA_TRY(cudaMemcpyAsync(ix->A, A, (size_t)H * d * sizeof(float), cudaMemcpyDefault, st));
+        if (hyper) LIDER_CUDA_TRY(cudaMemsetAsync(ix->bproj, 0, (size_t)H * sizeof(float), st));
+        else LIDER_CUDA_TRY(cudaMemcpyAsync(ix->bproj, b, (size_t)H * sizeof(float), cudaMemcpyDefault, st));
+    } else {
+        draw_projections_kernel<<<(unsigned)cdiv((int64_t)H * d, 256), 256, 0, st>>>(cp->seed, H, d, (float)P->W,
+                                                                                  hyper, ix->A, ix->bproj);
+        LIDER_LAUNCH_CHECK("draw_projections_kernel");
+        ix->projections_drawn = true;
+    }
     half_norm_kernel<<<(unsigned)cdiv(ncl, 128), 128, 0, st>>>(ix->C, ncl, d, ix->half_norm);
     LIDER_LAUNCH_CHECK("half_norm_kernel");
     if (P->score_mode != LIDER_SCORE_SIMT) {      // tensor-core routing
@@ -416,14 +602,6 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
     }
 
     // 1. partition: nearest centroid of every point
-    const int64_t chunk = std::min<int64_t>(n, kRowChunk);
-    DevBuf asg, asg_sorted, ids_in, tbuf, sbuf, errf;
-    ALLOC(asg.p, (size_t)n * sizeof(int32_t), "assignment");
-    ALLOC(asg_sorted.p, (size_t)n * sizeof(int32_t), "sorted assignment");
-    ALLOC(ids_in.p, (size_t)n * sizeof(int64_t), "ids");
-    ALLOC(sbuf.p, (size_t)chunk * std::max(ncl, H) * sizeof(double), "score chunk");
-    ALLOC(errf.p, 64, "flags");
-    LIDER_CUDA_TRY(cudaMemsetAsync(errf.p, 0, 64, st));
     for (int64_t r0 = 0; r0 < n; r0 += chunk) {
         const int64_t rows = std::min(chunk, n - r0);
         if ((rc = launch_scores(corpus + r0 * d, rows, d, ix->C, ix->half_norm, ncl, sbuf.as<double>(), st)))
@@ -615,6 +793,7 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
         for (int j = 0; j < ncl; ++j) ix->top_words[j + 1] = ix->top_words[j] + wv[j];
     }
 #undef ALLOC
+    ix->build_ms = std::chrono::duration<double, std::milli>(clock::now() - t_start).count();
     guard.ix = nullptr;
     *out = ix;
     return LIDER_OK;
@@ -625,8 +804,9 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
 void destroy_index(lider_index* ix) { release(ix); }
 
 int build_entry(const float* corpus, int64_t n, int32_t d, const float* centroids, int32_t ncl,
-                const float* A, const float* b, const lider_params* P, void* stream, lider_index** out) {
-    return build_impl(corpus, n, d, centroids, ncl, A, b, P, (cudaStream_t)stream, out);
+                const lider_cluster_params* cp, const float* A, const float* b, const lider_params* P, void* stream,
+                lider_index** out) {
+    return build_impl(corpus, n, d, centroids, ncl, cp, A, b, P, (cudaStream_t)stream, out);
 }
 
 }  // namespace lider

@@ -120,6 +120,12 @@ struct lider_index {
     lider::RmiRoot* croot = nullptr;    // L
     lider::RmiLeaf* cleaf = nullptr;    // L x F
     cudaMemPool_t pool = nullptr;
+    // how the index was built (lider_build_info)
+    lider_cluster_params cluster{};     // k-means parameters (clustered only)
+    bool clustered = false;             // k-means ran inside the build
+    bool projections_drawn = false;     // A and b were drawn from the seed
+    double kmeans_ms = 0.0;             // host wall time of the k-means iterations
+    double build_ms = 0.0;              // host wall time of the whole build
     lider_tuning tune{128, 128, 64, 1};    // launch shapes (lider_autotune; defaults measured on mid)
     int score_blocks_per_sm = 1;
     int num_sms = 148;

@@ -41,6 +41,25 @@ class Params(ctypes.Structure):
                 ("route_kind", ctypes.c_int32), ("raw_keys", ctypes.c_int32)]
 
 
+class ClusterParams(ctypes.Structure):
+    _fields_ = [("n_clusters", ctypes.c_int32), ("kmeans_iters", ctypes.c_int32),
+                ("kmeans_sample", ctypes.c_int64), ("seed", ctypes.c_uint64)]
+
+
+class BuildInfo(ctypes.Structure):
+    _fields_ = [("clustered", ctypes.c_int32), ("projections_drawn", ctypes.c_int32),
+                ("cluster", ClusterParams), ("train_rows", ctypes.c_int64), ("empty_clusters", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("kmeans_ms", ctypes.c_double), ("build_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        c = self.cluster
+        return {"clustered": bool(self.clustered), "projections_drawn": bool(self.projections_drawn),
+                "n_clusters": int(c.n_clusters), "kmeans_iters": int(c.kmeans_iters),
+                "kmeans_sample": int(c.kmeans_sample), "seed": int(c.seed), "train_rows": int(self.train_rows),
+                "empty_clusters": int(self.empty_clusters), "kmeans_ms": float(self.kmeans_ms),
+                "build_ms": float(self.build_ms)}
+
+
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in
                 ("n_queries", "pairs", "candidates", "qkey_boundary", "qkey_clamped",
@@ -90,7 +109,14 @@ def _load():
     lib = ctypes.CDLL(LIB_PATH)
     P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
     sig = {
-        "lider_build": ([P, I64, I32, P, I32, P, P, ctypes.POINTER(Params), P, ctypes.POINTER(P)], ctypes.c_int),
+        "lider_build": ([P, I64, I32, ctypes.POINTER(ClusterParams), P, P, ctypes.POINTER(Params), P,
+                         ctypes.POINTER(P)], ctypes.c_int),
+        "lider_build_centroids": ([P, I64, I32, P, I32, P, P, ctypes.POINTER(Params), P, ctypes.POINTER(P)],
+                                  ctypes.c_int),
+        "lider_get_build_info": ([P, ctypes.POINTER(BuildInfo)], ctypes.c_int),
+        "lider_export_centroids": ([P, P], ctypes.c_int),
+        "lider_export_assignment": ([P, P], ctypes.c_int),
+        "lider_export_projections": ([P, P, P], ctypes.c_int),
         "lider_search": ([P, P, I64, I32, I32, P, P, ctypes.POINTER(Stats), P], ctypes.c_int),
         "lider_search_trace": ([P, P, I64, I32, I32, P, P, ctypes.POINTER(Trace), ctypes.POINTER(Stats), P],
                                ctypes.c_int),
@@ -127,7 +153,8 @@ _lib = _load()
 
 
 def exported_symbols() -> list[str]:
-    return [n for n in ("lider_build", "lider_search", "lider_search_trace", "lider_search_host",
+    return [n for n in ("lider_build", "lider_build_centroids", "lider_get_build_info", "lider_export_centroids",
+                        "lider_export_assignment", "lider_export_projections", "lider_search", "lider_search_trace", "lider_search_host",
                         "lider_search_noalloc", "lider_search_scratch_bytes", "lider_debug_tc_tile",
                         "lider_get_tuning", "lider_set_tuning", "lider_autotune",
                         "lider_index_info", "lider_cluster_offsets", "lider_export_array",
@@ -158,12 +185,20 @@ def _dev(t: torch.Tensor, dtype, name: str) -> torch.Tensor:
 class Index:
     """A LIDER index resident on the current CUDA device (owns its memory)."""
 
-    def __init__(self, corpus: torch.Tensor, centroids: torch.Tensor, A: torch.Tensor, b: torch.Tensor,
-                 L: int, m: int, W: float, rmi_leaves: int, r0: int = 2, B: int | None = None,
-                 score_mode: int = SCORE_TENSOR, rerank: int = 0, hash_kind: int = HASH_PSTABLE,
-                 route_kind: int = ROUTE_EXACT, raw_keys: bool = False, stream=None):
-        """Build the index (lider_build): corpus (n, d), centroids (n_clusters,
-        d), projections A (L*m, d) and offsets b (L*m), all FP32 CUDA tensors.
+    def __init__(self, corpus: torch.Tensor, centroids: torch.Tensor | None = None, A: torch.Tensor | None = None,
+                 b: torch.Tensor | None = None, *, L: int, m: int, W: float, rmi_leaves: int, r0: int = 2,
+                 B: int | None = None, score_mode: int = SCORE_TENSOR, rerank: int = 0,
+                 hash_kind: int = HASH_PSTABLE, route_kind: int = ROUTE_EXACT, raw_keys: bool = False,
+                 n_clusters: int | None = None, kmeans_iters: int = 10, kmeans_sample: int = 0, seed: int = 0,
+                 stream=None):
+        """Build the index from an FP32 CUDA corpus (n, d).
+
+        With centroids (n_clusters, d) the index partitions by them
+        (lider_build_centroids; A and b required).  Without, lider_build runs
+        k-means on the device: n_clusters clusters, kmeans_iters Lloyd
+        iterations on the first kmeans_sample rows (0: all) from the Forgy rows
+        drawn from `seed`; A (L*m, d) and b (L*m) may then be None, and are
+        drawn from `seed`.
 
         L, m, W, rmi_leaves, r0, B: the core models' parameters (hashkey arrays,
         hashes per key, p-stable bucket width, RMI leaves, expansion factor
@@ -177,21 +212,55 @@ class Index:
         if B is None:
             B = 3 if hash_kind == HASH_HYPERPLANE else 1
         corpus = _dev(corpus, torch.float32, "corpus")
-        centroids = _dev(centroids, torch.float32, "centroids")
-        A = _dev(A, torch.float32, "A")
-        b = _dev(b, torch.float32, "b")
+        if (A is None) != (b is None):
+            raise ValueError("give both A and b, or neither")
+        A = None if A is None else _dev(A, torch.float32, "A")
+        b = None if b is None else _dev(b, torch.float32, "b")
         n, d = corpus.shape
         p = Params(L, m, rmi_leaves, r0, B, hash_kind, float(W), score_mode, rerank, route_kind, int(raw_keys))
         h = ctypes.c_void_p()
-        _check(_lib.lider_build(corpus.data_ptr(), n, d, centroids.data_ptr(), centroids.shape[0],
-                                A.data_ptr(), b.data_ptr(), ctypes.byref(p), _stream_ptr(stream),
-                                ctypes.byref(h)))
+        if centroids is not None:
+            centroids = _dev(centroids, torch.float32, "centroids")
+            if A is None:
+                raise ValueError("a build from given centroids needs A and b")
+            _check(_lib.lider_build_centroids(corpus.data_ptr(), n, d, centroids.data_ptr(), centroids.shape[0],
+                                              A.data_ptr(), b.data_ptr(), ctypes.byref(p), _stream_ptr(stream),
+                                              ctypes.byref(h)))
+            n_clusters = int(centroids.shape[0])
+        else:
+            if n_clusters is None:
+                raise ValueError("n_clusters is required when k-means runs in the build")
+            cp = ClusterParams(int(n_clusters), int(kmeans_iters), int(kmeans_sample), int(seed))
+            _check(_lib.lider_build(corpus.data_ptr(), n, d, ctypes.byref(cp),
+                                    None if A is None else A.data_ptr(), None if b is None else b.data_ptr(),
+                                    ctypes.byref(p), _stream_ptr(stream), ctypes.byref(h)))
         self._h = h
-        self.n, self.d, self.n_clusters = int(n), int(d), int(centroids.shape[0])
+        self.n, self.d, self.n_clusters = int(n), int(d), int(n_clusters)
         self.L, self.m, self.W, self.rmi_leaves, self.r0, self.B = L, m, W, rmi_leaves, r0, B
         self.score_mode = score_mode
         self.rerank = rerank
         self.hash_kind, self.route_kind, self.raw_keys = hash_kind, route_kind, bool(raw_keys)
+
+    def build_info(self) -> dict:
+        bi = BuildInfo()
+        _check(_lib.lider_get_build_info(self._h, ctypes.byref(bi)))
+        return bi.as_dict()
+
+    def centroids(self) -> np.ndarray:
+        out = np.zeros((self.n_clusters, self.d), dtype=np.float32)
+        _check(_lib.lider_export_centroids(self._h, out.ctypes.data))
+        return out
+
+    def assignment(self) -> np.ndarray:
+        out = np.zeros(self.n, dtype=np.int32)
+        _check(_lib.lider_export_assignment(self._h, out.ctypes.data))
+        return out
+
+    def projections(self):
+        A = np.zeros((self.L * self.m, self.d), dtype=np.float32)
+        b = np.zeros(self.L * self.m, dtype=np.float32)
+        _check(_lib.lider_export_projections(self._h, A.ctypes.data, b.ctypes.data))
+        return A, b
 
     @property
     def handle(self) -> int:

@@ -23,9 +23,20 @@ int main(void) {
     p.hash_kind = LIDER_HASH_PSTABLE; p.W = 1.0; p.score_mode = LIDER_SCORE_SIMT;
     p.route_kind = LIDER_ROUTE_EXACT; p.raw_keys = 0;
 
-    expect(lider_build(0, 10, 8, 0, 2, 0, 0, &p, 0, 0) == LIDER_EINVAL, "build: NULL out");
-    expect(lider_build(0, 10, 8, 0, 2, 0, 0, &p, 0, &ix) == LIDER_EINVAL && ix == 0, "build: NULL inputs");
+    lider_cluster_params cp;
+    memset(&cp, 0, sizeof cp);
+    cp.n_clusters = 2; cp.kmeans_iters = 10; cp.kmeans_sample = 0; cp.seed = 0;
+
+    expect(lider_build(0, 10, 8, &cp, 0, 0, &p, 0, 0) == LIDER_EINVAL, "build: NULL out");
+    expect(lider_build(0, 10, 8, &cp, 0, 0, &p, 0, &ix) == LIDER_EINVAL && ix == 0, "build: NULL corpus");
+    expect(lider_build_centroids(0, 10, 8, 0, 2, 0, 0, &p, 0, &ix) == LIDER_EINVAL && ix == 0,
+           "build_centroids: NULL inputs");
     expect(lider_last_error() != 0 && strlen(lider_last_error()) > 0, "last_error is set");
+    {
+        lider_build_info bi;
+        expect(lider_get_build_info(0, &bi) == LIDER_EINVAL, "build_info: NULL index");
+        expect(lider_export_centroids(0, 0) == LIDER_EINVAL, "export_centroids: NULL index");
+    }
 
     lider_search_stats st;
     expect(lider_search(0, 0, 0, 10, 1, 0, 0, &st, 0) == LIDER_EINVAL, "search: NULL index");

@@ -33,7 +33,7 @@ def test_binding_loads_and_validates_without_gpu():
     from paper_2205_00970_b300 import lider
     assert set(declared_symbols()) <= set(lider.exported_symbols())
     # NULL out pointer / NULL index are rejected before any CUDA call
-    rc = lider.raw_call("lider_build", None, 10, 8, None, 2, None, None, None, None, None)
+    rc = lider.raw_call("lider_build_centroids", None, 10, 8, None, 2, None, None, None, None, None)
     assert rc == -1 and "out is NULL" in lider.last_error()
     rc = lider.raw_call("lider_search", None, None, 0, 10, 1, None, None, None, None)
     assert rc == -1 and "index is NULL" in lider.last_error()
@@ -60,22 +60,44 @@ def test_binding_loads_and_validates_without_gpu():
         (10, 8, 2, lider.Params(4, 8, 16, 2, 1, 0, 1.0, 0, 0, 0, 2), "raw_keys"),
         (10, 8, 2, lider.Params(4, 65, 16, 2, 1, 1, 1.0, 1, 0), "m must be <= 64"),
     ]:
-        rc = lider.raw_call("lider_build", dummy, n, d, dummy, ncl, dummy, dummy, ctypes.byref(pp), None,
+        rc = lider.raw_call("lider_build_centroids", dummy, n, d, dummy, ncl, dummy, dummy, ctypes.byref(pp), None,
                             ctypes.byref(out))
         assert rc == -1 and msg in lider.last_error(), (msg, lider.last_error())
-    rc = lider.raw_call("lider_build", dummy, 10, 8, dummy, 2, dummy, dummy,
+    rc = lider.raw_call("lider_build_centroids", dummy, 10, 8, dummy, 2, dummy, dummy,
                         ctypes.byref(lider.Params(33, 8, 16, 2, 1, 0, 1.0, 1, 0)), None, ctypes.byref(out))
     assert rc == -4
-    rc = lider.raw_call("lider_build", dummy, 10, 8, dummy, 2, dummy, dummy,
+    rc = lider.raw_call("lider_build_centroids", dummy, 10, 8, dummy, 2, dummy, dummy,
                         ctypes.byref(lider.Params(17, 8, 16, 2, 1, 0, 1.0, 0, 0)), None, ctypes.byref(out))
     assert rc == -4 and "L <= 16" in lider.last_error()
-    rc = lider.raw_call("lider_build", dummy, 10, 8, dummy, 20000, dummy, dummy,
+    rc = lider.raw_call("lider_build_centroids", dummy, 10, 8, dummy, 20000, dummy, dummy,
                         ctypes.byref(lider.Params(4, 8, 16, 2, 1, 0, 1.0, 0, 0, 1, 0)), None, ctypes.byref(out))
     assert rc == -4 and "8192" in lider.last_error()
     # hyperplane bits: B is limited by one bit per element, not floor(64/m)
-    rc = lider.raw_call("lider_build", dummy, 10, 8, dummy, 2, dummy, dummy,
+    rc = lider.raw_call("lider_build_centroids", dummy, 10, 8, dummy, 2, dummy, dummy,
                         ctypes.byref(lider.Params(4, 8, 16, 2, 57, 1, 1.0, 0, 0)), None, ctypes.byref(out))
     assert rc == -1 and "<= 56" in lider.last_error()
+
+
+def test_kmeans_build_validates_without_gpu():
+    """lider_build (k-means inside) rejects inconsistent clustering arguments
+    before any device work."""
+    from paper_2205_00970_b300 import lider
+    out = ctypes.c_void_p()
+    p = lider.Params(4, 8, 16, 2, 1, 0, 1.0, 0, 0)
+    dummy = ctypes.c_void_p(16)
+    rc = lider.raw_call("lider_build", dummy, 10, 8, None, None, None, ctypes.byref(p), None, ctypes.byref(out))
+    assert rc == -1 and "cluster is NULL" in lider.last_error()
+    for cp, A, b, msg in [
+        (lider.ClusterParams(20, 5, 0, 0), None, None, "n_clusters exceeds"),
+        (lider.ClusterParams(4, 5, 3, 0), None, None, "n_clusters exceeds"),
+        (lider.ClusterParams(0, 5, 0, 0), None, None, "n_clusters must be"),
+        (lider.ClusterParams(2, -1, 0, 0), None, None, "kmeans_iters"),
+        (lider.ClusterParams(2, 5, -4, 0), None, None, "kmeans_sample"),
+        (lider.ClusterParams(2, 5, 0, 0), dummy, None, "both A and b"),
+    ]:
+        rc = lider.raw_call("lider_build", dummy, 10, 8, ctypes.byref(cp), A, b, ctypes.byref(p), None,
+                            ctypes.byref(out))
+        assert rc == -1 and msg in lider.last_error() and not out.value, (msg, lider.last_error())
 
 
 def test_tuning_abi_validates_without_gpu():

@@ -22,3 +22,39 @@ def test_recall10_counts_overlap():
     found[0, :3] = [100, 101, 102]
     found[1] = found[1][::-1]
     assert bench.recall10(found, truth) == (7 / 10 + 10 / 10) / 2
+
+
+def test_oracle_pool_search_equals_serial_search():
+    """The CPU baseline's fork pool returns what one oracle search over the
+    same queries returns, in query order."""
+    import bench
+    from oracle import lider_oracle as O
+    rng = np.random.default_rng(6)
+    X = rng.standard_normal((600, 16)).astype(np.float32)
+    X /= np.linalg.norm(X, axis=1, keepdims=True)
+    Q = rng.standard_normal((11, 16)).astype(np.float32)
+    A = rng.standard_normal((3 * 8, 16)).astype(np.float32)
+    b = rng.random(3 * 8).astype(np.float32)
+    C = X[:5]
+    idx = O.build_index(X, C, A, b, 3, 8, 1.0, 4)
+    cfg = {"k": 7, "c": 2, "R": 14}
+    got, sec = bench.oracle_pool_search(idx, Q, cfg, cores=2, batch=3, budget_s=None)
+    np.testing.assert_array_equal(got, O.search(idx, Q, 7, 2, 14).ids)
+    assert sec > 0
+
+
+def test_score_roofline_counts_the_methods_work():
+    """frac = 2 x candidates x d / phase time / peak; the executed tiles and
+    the unique bytes are reported beside it."""
+    import bench
+    hbm, bf16, _, _ = bench.measured_peaks()
+    stats = {"candidates": 1_000_000, "tc_tiles": 100}
+    route = np.array([[0, 1], [1, 2]], dtype=np.int32)
+    cl_off = np.array([0, 100, 300, 364, 500])
+    r = bench.score_roofline("f16", stats, route, cl_off, 768, 1e-3, {})
+    assert r["bound"] == "tensor" and r["peak"] == bf16
+    assert abs(r["achieved"] - 2 * 1e6 * 768 / 1e-3 / 1e12) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / bf16) < 1e-12
+    assert r["executed"]["flop_per_launch"] == 100 * 128 * 256 * 768 * 2
+    # probed clusters 0, 1, 2 (364 rows), 4 gathered queries, bitmap words 4 + 7 + 7 + 2
+    assert r["unique_bytes"]["bytes_per_launch"] == (364 * 768 * 2 + 4 * 768 * 2 + (4 + 7 + 7 + 2) * 4)
