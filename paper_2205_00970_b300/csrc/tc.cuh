@@ -28,7 +28,7 @@ constexpr int kTileB = kBN * kRowBytes;        // 32 KB
 constexpr int kMaxStages = 4;
 constexpr int kSmemBytes = 2 * (2 * kTileA + 2 * kTileB) + 1024;  // both kinds: 192 KB + alignment slack
 constexpr int kThreads = 192;       // producer + MMA warps + 4 epilogue warps
-// threads of a block with kEpiWarps epilogue warps (4 or 8)
+// threads of a block with kEpiWarps epilogue warps (4, 8 or 16)
 constexpr int threads_for(int epi_warps) { return 64 + 32 * epi_warps; }
 constexpr int kTmemCols = 2 * kBN;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
@@ -128,14 +128,16 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Wait for the phase of `parity` to complete; false on timeout or abort.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+// Wait for the phase of `parity` to complete; false on timeout (after
+// timeout_ns) or abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          uint64_t timeout_ns = kTimeoutNs) {
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     for (;;) {
         if (mbar_try(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (globaltimer() - t0 > kTimeoutNs) return false;
+        if (globaltimer() - t0 > timeout_ns) return false;
     }
 }
 
@@ -243,6 +245,14 @@ struct Ctl {
     int epi_bad;        // an epilogue warp's wait failed (read only after epi_sync)
 };
 
+// Test hook of the bounded waits (engine self-test only): every wait gives up
+// after timeout_ns, and with skip_first the producer leaves the first stage
+// of the first tile unloaded, so the MMA warp's wait for it runs out.
+struct WaitTest {
+    uint64_t timeout_ns = kTimeoutNs;
+    bool skip_first = false;
+};
+
 // One unit = one 128 x 256 tile: A rows [a_row, a_row+128), B rows
 // [b_row, b_row+256), all of K.  Sched provides: int count() and
 // void coords(int u, int& a_row, int& b_row).  Epi provides, called by every
@@ -255,11 +265,16 @@ struct Ctl {
 // cannot be left waiting.
 // mA0/mB0: the operands (KindTf32x3: their TF32 heads); mA1/mB1: the tails
 // (KindTf32x3 only; ignored otherwise).  kchunks = ceil(d / Kind::kBK).
-template <class Kind, class Sched, class Epi, int kEpiWarps = 4>
+// kStagesUse: shared-memory stages of K (at most Kind::kStages, the plan the
+// block's shared memory is sized for; a kernel with a larger epilogue can use
+// fewer).
+template <class Kind, class Sched, class Epi, int kEpiWarps = 4, int kStagesUse = Kind::kStages>
 __device__ void gemm_tiles(const CUtensorMap* mAhi, const CUtensorMap* mAlo, const CUtensorMap* mBhi,
                            const CUtensorMap* mBlo, int kchunks, Sched& sched, Epi& epi, int* err,
-                           unsigned char* smem_raw, Ctl& ctl) {
-    constexpr int kStages = Kind::kStages;
+                           unsigned char* smem_raw, Ctl& ctl, const WaitTest wt = WaitTest{}) {
+    const uint64_t tmo = wt.timeout_ns;
+    static_assert(kStagesUse >= 2 && kStagesUse <= Kind::kStages, "stages");
+    constexpr int kStages = kStagesUse;
     constexpr int kStageBytes = Kind::kOps * (kTileA + kTileB);
     constexpr int kBK = Kind::kBK;
     static_assert(kStages * kStageBytes + 1024 <= kSmemBytes, "stages exceed the shared memory plan");
@@ -305,7 +320,8 @@ __device__ void gemm_tiles(const CUtensorMap* mAhi, const CUtensorMap* mAlo, con
                 for (int kc = 0; kc < kchunks; ++kc, ++it) {
                     const int s = it % kStages;
                     const uint32_t ph = (uint32_t)(it / kStages) & 1u;
-                    if (!mbar_wait(&ctl.empty[s], ph ^ 1u, abort_flag)) { fail(TC_TIMEOUT_EMPTY); break; }
+                    if (!mbar_wait(&ctl.empty[s], ph ^ 1u, abort_flag, tmo)) { fail(TC_TIMEOUT_EMPTY); break; }
+                    if (wt.skip_first && it == 0) continue;      // test hook: this stage never fills
                     unsigned char* st = stage_ptr(s);
                     mbar_expect_tx(&ctl.full[s], (uint32_t)kStageBytes);
                     const int k0 = kc * kBK;
@@ -320,11 +336,12 @@ __device__ void gemm_tiles(const CUtensorMap* mAhi, const CUtensorMap* mAlo, con
             // drain: wait until every issued stage has landed (bounded)
             const int issued = it;
             for (int j = (issued > kStages ? issued - kStages : 0); j < issued; ++j) {
+                if (wt.skip_first && j == 0) continue;           // never issued
                 const int s = j % kStages;
                 const uint32_t ph = (uint32_t)(j / kStages) & 1u;
                 const uint64_t t0 = globaltimer();
                 while (!mbar_try(&ctl.full[s], ph)) {
-                    if (globaltimer() - t0 > kTimeoutNs) { atomicCAS(err, 0, TC_TIMEOUT_DRAIN); break; }
+                    if (globaltimer() - t0 > tmo) { atomicCAS(err, 0, TC_TIMEOUT_DRAIN); break; }
                 }
             }
         }
@@ -334,14 +351,14 @@ __device__ void gemm_tiles(const CUtensorMap* mAhi, const CUtensorMap* mAlo, con
             for (int u = blockIdx.x; u < nunits && !*abort_flag; u += gridDim.x, ++ui) {
                 const int ab = ui & 1;
                 const uint32_t aph = (uint32_t)(ui >> 1) & 1u;
-                if (!mbar_wait(&ctl.tempty[ab], aph ^ 1u, abort_flag)) { fail(TC_TIMEOUT_TEMPTY); break; }
+                if (!mbar_wait(&ctl.tempty[ab], aph ^ 1u, abort_flag, tmo)) { fail(TC_TIMEOUT_TEMPTY); break; }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(ab * kBN);
                 bool ok = true;
                 for (int kc = 0; kc < kchunks; ++kc, ++it) {
                     const int s = it % kStages;
                     const uint32_t ph = (uint32_t)(it / kStages) & 1u;
-                    if (!mbar_wait(&ctl.full[s], ph, abort_flag)) { fail(TC_TIMEOUT_FULL); ok = false; break; }
+                    if (!mbar_wait(&ctl.full[s], ph, abort_flag, tmo)) { fail(TC_TIMEOUT_FULL); ok = false; break; }
                     tc_fence_after();
                     const uint32_t sa = smem_u32(stage_ptr(s));
 #pragma unroll
@@ -369,9 +386,10 @@ __device__ void gemm_tiles(const CUtensorMap* mAhi, const CUtensorMap* mAlo, con
             }
         }
     } else {                                                     // epilogue warps 2..
-        // warp w reads TMEM lanes 32 (w % 4) ..; with 8 epilogue warps two of
-        // them share those lanes and take 4 of the 8 column groups each
-        static_assert(kEpiWarps == 4 || kEpiWarps == 8, "4 or 8 epilogue warps");
+        // warp w reads TMEM lanes 32 (w % 4) ..; with 8 (16) epilogue warps
+        // two (four) of them share those lanes and take 4 (2) of the 8
+        // column groups each
+        static_assert(kEpiWarps == 4 || kEpiWarps == 8 || kEpiWarps == 16, "4, 8 or 16 epilogue warps");
         constexpr int kGroups = (kBN / 32) / (kEpiWarps / 4);
         const int quarter = warp & 3;
         const int cb0 = ((warp - 2) >> 2) * kGroups;
@@ -381,7 +399,7 @@ __device__ void gemm_tiles(const CUtensorMap* mAhi, const CUtensorMap* mAlo, con
             const int ab = ui & 1;
             const uint32_t aph = (uint32_t)(ui >> 1) & 1u;
             epi.begin(u, row);
-            const bool ok = mbar_wait(&ctl.tfull[ab], aph, abort_flag);
+            const bool ok = mbar_wait(&ctl.tfull[ab], aph, abort_flag, tmo);
             if (!ok && lane == 0) {
                 fail(TC_TIMEOUT_TFULL);
                 atomicOr(&ctl.epi_bad, 1);

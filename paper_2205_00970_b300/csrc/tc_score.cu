@@ -112,12 +112,12 @@ template <class Kind>
 __global__ void __launch_bounds__(tc::kThreads, 1)
     tc_tile_test_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                         const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
-                        int kchunks, float* out, int m, int n, int* err) {
+                        int kchunks, float* out, int m, int n, int* err, tc::WaitTest wt) {
     extern __shared__ unsigned char smem[];
     __shared__ tc::Ctl ctl;
     OneTile sched;
     WriteTile epi{out, m, n};
-    tc::gemm_tiles<Kind>(&mAhi, &mAlo, &mBhi, &mBlo, kchunks, sched, epi, err, smem, ctl);
+    tc::gemm_tiles<Kind>(&mAhi, &mAlo, &mBhi, &mBlo, kchunks, sched, epi, err, smem, ctl, wt);
 }
 
 }  // namespace
@@ -195,11 +195,14 @@ int make_tensor_map(CUtensorMap* map, const void* base, int64_t rows, int d, int
 
 }  // namespace lider
 
+namespace lider {
+namespace {
+
 // Self-test of the tensor-core engine: out[m x n] = A[m x d] . B[n x d]^T with
-// m <= 128, n <= 256, through the same TMA / tcgen05 / TMEM path as search.
-extern "C" int lider_debug_tc_tile(const float* A, int32_t m, const float* B, int32_t n, int32_t d, int32_t kind,
-                                   float* out, void* stream) {
-    using namespace lider;
+// m <= 128, n <= 256, through the same TMA / tcgen05 / TMEM path as search;
+// wt: the waits' limit and the test hook that leaves one stage unloaded.
+int tc_tile_impl(const float* A, int32_t m, const float* B, int32_t n, int32_t d, int32_t kind, float* out,
+                 tc::WaitTest wt, void* stream) {
     try {
         if (!A || !B || !out) return fail(LIDER_EINVAL, "lider_debug_tc_tile: NULL pointer");
         if (kind < 0 || kind > 3) return fail(LIDER_EINVAL, "lider_debug_tc_tile: kind must be 0, 1, 2 or 3");
@@ -256,7 +259,7 @@ extern "C" int lider_debug_tc_tile(const float* A, int32_t m, const float* B, in
             if (e != cudaSuccess) { rc = cuda_fail(e, "cudaFuncSetAttribute"); break; }
             const int kbk = kind == 0 ? tc::KindTf32x3::kBK : kind == 3 ? tc::KindF8::kBK : tc::KindBf16::kBK;
             int kchunks = (d + kbk - 1) / kbk;
-            void* args[] = {&mah, &mal, &mbh, &mbl, &kchunks, &out, &m, &n, &err};
+            void* args[] = {&mah, &mal, &mbh, &mbl, &kchunks, &out, &m, &n, &err, &wt};
             e = cudaLaunchKernel(kern, dim3(1), dim3(tc::kThreads), args, tc::kSmemBytes, st);
             if (e != cudaSuccess) { rc = cuda_fail(e, "tc_tile_test_kernel launch"); break; }
             e = cudaGetLastError();
@@ -272,4 +275,22 @@ extern "C" int lider_debug_tc_tile(const float* A, int32_t m, const float* B, in
     } catch (...) {
         return fail(LIDER_ECUDA, "lider_debug_tc_tile: internal error");
     }
+}
+
+}  // namespace
+}  // namespace lider
+
+extern "C" int lider_debug_tc_tile(const float* A, int32_t m, const float* B, int32_t n, int32_t d, int32_t kind,
+                                   float* out, void* stream) {
+    return lider::tc_tile_impl(A, m, B, n, d, kind, out, lider::tc::WaitTest{}, stream);
+}
+
+extern "C" int lider_debug_tc_wait_expiry(const float* A, int32_t m, const float* B, int32_t n, int32_t d,
+                                          int32_t kind, float* out, double limit_ms, void* stream) {
+    if (!(limit_ms > 0.0) || limit_ms > 10000.0)
+        return lider::fail(LIDER_EINVAL, "lider_debug_tc_wait_expiry: limit_ms must be in (0, 10000]");
+    lider::tc::WaitTest wt;
+    wt.timeout_ns = (uint64_t)(limit_ms * 1e6);
+    wt.skip_first = true;
+    return lider::tc_tile_impl(A, m, B, n, d, kind, out, wt, stream);
 }

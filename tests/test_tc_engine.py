@@ -76,3 +76,28 @@ def test_tc_tile_bf16_matches_fp64_of_rounded_inputs(m, n, d):
     scale = np.abs(A16) @ np.abs(B16).T
     err = np.abs(out - ref) / scale
     assert np.max(err) < 3e-5, (float(np.max(err)), float(np.mean(err)))
+
+
+@pytest.mark.parametrize("kind,d", [(0, 768), (1, 768), (1, 64), (3, 256)])
+def test_bounded_wait_runs_out_and_the_device_stays_usable(kind, d):
+    """A stage that never fills (the producer leaves it unloaded): the MMA
+    warp's wait gives up after its 5 ms limit, the kernel returns on its own
+    and the call reports LIDER_ECUDA with the wait's code; the next engine
+    call on the same device still gives correct results."""
+    import time
+
+    import torch
+    from paper_2205_00970_b300 import lider
+    rng = np.random.default_rng(d + kind)
+    A = torch.from_numpy(rng.standard_normal((128, d)).astype(np.float32)).cuda()
+    B = torch.from_numpy(rng.standard_normal((256, d)).astype(np.float32)).cuda()
+    t0 = time.perf_counter()
+    rc = lider.tc_wait_expiry(A, B, kind=kind, limit_ms=5.0)
+    elapsed = time.perf_counter() - t0
+    assert rc == -3, rc
+    msg = lider.last_error()
+    assert "wait timed out (code 2)" in msg, msg           # the full-stage wait of the MMA warp
+    assert elapsed < 5.0
+    out = lider.tc_tile(A, B, kind=0).cpu().numpy().astype(np.float64)
+    ref = A.cpu().numpy().astype(np.float64) @ B.cpu().numpy().astype(np.float64).T
+    assert np.max(np.abs(out - ref)) < 1e-3
