@@ -466,6 +466,19 @@ int lider_export_rmi(const lider_index* index, int32_t cluster, int32_t array,
 int lider_debug_tc_tile(const float* A, int32_t m, const float* B, int32_t n, int32_t d,
                         int32_t kind, float* out, void* stream);
 
+/* Test of the engine's bounded waits (the paper has no counterpart): the same
+ * one-tile run as lider_debug_tc_tile, but every wait of the engine gives up
+ * after limit_ms milliseconds (0 < limit_ms <= 10000) and the TMA producer
+ * leaves the first stage of K unloaded, so the MMA warp's wait for it runs
+ * out.  The kernel records the code of the first wait that gave up, raises
+ * its abort flag, lets the other warps leave, waits (with the same limit) for
+ * the stages it did load, frees its TMEM and returns; the call then returns
+ * LIDER_ECUDA with "wait timed out (code N)" in lider_last_error() (N: 1 empty
+ * stage, 2 full stage, 3 accumulator full, 4 accumulator empty, 5 drain).  No
+ * memory access is skipped or faults; the device stays usable.  Synchronous. */
+int lider_debug_tc_wait_expiry(const float* A, int32_t m, const float* B, int32_t n, int32_t d,
+                               int32_t kind, float* out, double limit_ms, void* stream);
+
 /* Release the index and its device memory.  NULL is accepted. */
 void lider_free(lider_index* index);
 

@@ -207,10 +207,11 @@ struct HashEpi {
     const float* b;             // offsets b_h
     const float* a_norm;        // |a_h|
     const float* qnorm;         // |q| (rounded up)
-    int32_t* recheck;           // (q * H + h) of the undecided values
+    int32_t* recheck;           // ((q0 + q) * H + h) of the undecided values
     int32_t* n_recheck;
     float W, guard;             // guard: kTcGuard
     int nq, H;
+    int q0;                     // index of this launch's first query in the whole batch
     bool hyper;                 // hyperplane hashes: only the sign of t decides
     int q, h0;
     float qn;
@@ -234,7 +235,7 @@ struct HashEpi {
                               0x1p-22f * fabsf(tf);
             const float dist = hyper ? fabsf(tf) : fabsf(tf - rintf(tf));
             t[(int64_t)q * H + h] = (double)tf;
-            if (!(dist > 1.01f * eps + 1.1e-6f)) recheck[atomicAdd(n_recheck, 1)] = q * H + h;
+            if (!(dist > 1.01f * eps + 1.1e-6f)) recheck[atomicAdd(n_recheck, 1)] = (q0 + q) * H + h;
         }
     }
     __device__ void done(int, int) {}
@@ -376,10 +377,24 @@ __device__ void candidate_guard(int gmode, float qn, double sq, double eq, int d
         g = eq * (double)xhat + qs * (double)xres + acc * (qs + eq) * (double)xhat;
         s = sq * (double)sx;
     }
-    *qscale = (float)(gmode == 2 ? sq : 1.0);
-    *qguard = (gmode == 0 || gmode == 3) ? 0.f : __double2float_ru(g * (1.0 + 0x1p-20));
     // |approximate score| <= s |q| |x|max + its error (s = 1 unless FP16)
-    *qbound = __double2float_ru((s * q * (double)xmax + g) * (1.0 + 0x1p-20));
+    const float B = __double2float_ru((s * q * (double)xmax + g) * (1.0 + 0x1p-20));
+    *qscale = (float)(gmode == 2 ? sq : 1.0);
+    // the select reads scores as 16-bit codes over [-B, B] (score_code), each
+    // within 0.51 of a step 2B/65535 of the score: one step joins the guard
+    *qguard = (gmode == 0 || gmode == 3) ? 0.f
+                                         : __double2float_ru((g + 2.0 * (double)B / 65535.0) * (1.0 + 0x1p-20));
+    *qbound = B;
+}
+
+// 16-bit score codes of the tensor paths: code = rint((B - s) * 65535 / 2B),
+// saturated to [0, 65535], for |s| <= B (B = qbound of the query; the score
+// kernel's score_code_sat); code_score maps a code back (B - code * 2B/65535).
+// Every kernel maps codes back with code_score, so a code means the same
+// float everywhere, and the float decreases as the code grows.
+__device__ __forceinline__ float code_step(float B) { return __fdiv_rn(__fmul_rn(2.f, B), 65535.f); }
+__device__ __forceinline__ float code_score(uint32_t code, float B, float step) {
+    return __fsub_rn(B, __fmul_rn((float)code, step));
 }
 
 __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __restrict__ Q,
@@ -1371,7 +1386,9 @@ struct TcArgs {
     const int32_t* pairs;
     const int64_t* bm_off;
     int ncl;
-    float* dense;               // per pair: approximate scores over its cluster's positions
+    uint16_t* dense;            // per pair: approximate score codes over its cluster's positions
+    const float* qbound;        // per query: the codes' range bound B
+    int c;                      // probes per query (pair = query * c + probe)
     const uint32_t* bitmap;     // per pair: candidate bitmap (mark_kernel)
     float* cmax;                // per pair and bitmap word: best candidate score of those 32 positions
     const float* slot_scale;    // FP8 form: per slot query scale (else null)
@@ -1388,22 +1405,47 @@ struct TcSched {
     }
 };
 
-// The epilogue writes every score of the tile, dense: row r of a pair slot s
-// in cluster j is dense + (bm_off[j] + (s - off[j]) * words_j) * 32, one
-// FP32 per cluster position (pitch 32 * words_j, a multiple of 32, so the
-// rows and every 32-column group are 128-byte aligned).  A warp transposes
-// its 32 rows x 32 columns through shared memory and stores them 4 rows x
-// 128 bytes per instruction.  Which positions are candidates is read later,
-// from the pair's bitmap, by the select.
-constexpr int kEpiPitch = 33;                              // padded row of the transpose
-constexpr int kScoreEpiWarps = 8;                          // epilogue warps of tc_score_kernel
-constexpr int kScoreThreads8 = tc::threads_for(kScoreEpiWarps);
-constexpr int kEpiStageBytes = kScoreEpiWarps * 32 * kEpiPitch * 4;
+// The epilogue writes every score of the tile, dense, as a 16-bit code
+// (score_code over the query's [-B, B]): row r of a pair slot s in cluster j
+// is dense + (bm_off[j] + (s - off[j]) * words_j) * 32, one code per cluster
+// position (pitch 32 * words_j, a multiple of 32, so the rows and every
+// 32-column group are 64-byte aligned).  A warp converts its 32 rows x 32
+// columns (one row per lane), transposes them through shared memory and
+// stores them 8 rows x 64 bytes per instruction.  It also writes, per pair
+// and 32 positions, the best candidate's score as its code maps back
+// (code_score of the smallest candidate code).  Which positions are
+// candidates is read from the pair's bitmap, here and in the select.
+//
+// Epilogue warps of tc_score_kernel: 16 (four per scheduler, so that their
+// TMEM loads, transposes and stores hide one another's latency; each takes 2
+// of the 8 column groups of its TMEM lane quarter) with three stages of K;
+// the 3xTF32 kind's two 96 KB stages leave room for 8 only.
+constexpr int kEpiPitch = 33;                              // padded row of the transpose (32-bit words)
+template <class Kind> struct ScorePlan {
+    static constexpr bool kTf32 = Kind::kOps == 2;
+    static constexpr int kEpiWarps = kTf32 ? 8 : 16;
+    static constexpr int kStages = kTf32 ? 2 : 3;
+    static constexpr int kThreads = tc::threads_for(kEpiWarps);
+    static constexpr int kStageBytes = kStages * Kind::kOps * (tc::kTileA + tc::kTileB) + 1024;
+    static constexpr int kSmem = kStageBytes + kEpiWarps * 32 * kEpiPitch * 4;
+    static_assert(kSmem <= 227 * 1024, "score kernel shared memory");
+};
 
+// 16-bit code of s in one instruction after the FMA: rint((B - s) * inv),
+// saturated to [0, 65535] by the conversion.
+__device__ __forceinline__ uint32_t score_code_sat(float s, float inv, float binv) {
+    const float x = __fmaf_rn(-s, inv, binv);
+    unsigned short h;
+    asm("cvt.rni.sat.u16.f32 %0, %1;" : "=h"(h) : "f"(x));
+    return h;
+}
+
+template <int kEpiWarps>
 struct TcEpi {
     const TcArgs* a;
-    float* stage;               // this warp's 32 x kEpiPitch floats
-    float* drow;                // this lane's dense row at the tile's first column (null: no pair)
+    uint32_t* stage;            // this warp's 32 x kEpiPitch words
+    uint16_t* drow;             // this lane's dense row at the tile's first column (null: no pair)
+    float B, inv, binv, step;   // this row's code range: bound, 65535 / 2B, B * inv, 2B / 65535
     int ncols;                  // columns of the tile inside the row pitch (a multiple of 32)
     float rs;                   // FP8 form: this row's query scale
     const float* cs;            // FP8 form: row scales of the tile's corpus rows (null: unscaled)
@@ -1421,9 +1463,14 @@ struct TcEpi {
         ncols = (int)min((int64_t)tc::kBN, words * 32 - p0);
         const int64_t wrow = a->bm_off[j] + ((int64_t)it * tc::kBM + row) * words;   // the pair's first word
         drow = row < in_tile ? a->dense + wrow * 32 + p0 : nullptr;
+        B = row < in_tile ? a->qbound[a->pairs[a->off[j] + it * tc::kBM + row] / a->c] : 1.f;
+        if (!(B > 0.f)) B = 1.f;                              // no scores to code (|q| = 0)
+        inv = __fdiv_rn(65535.f, __fmul_rn(2.f, B));
+        binv = __fmul_rn(B, inv);
+        step = code_step(B);
         crow = row < in_tile ? a->cmax + wrow + (p0 >> 5) : nullptr;
-        // this warp's column groups of the tile (two warps share each row)
-        constexpr int kGpw = (tc::kBN / 32) / (kScoreEpiWarps / 4);
+        // this warp's column groups of the tile (kEpiWarps / 4 warps share each row)
+        constexpr int kGpw = (tc::kBN / 32) / (kEpiWarps / 4);
         const int g0 = ((((int)threadIdx.x >> 5) - 2) >> 2) * kGpw;
 #pragma unroll
         for (int w = 0; w < tc::kBN / 32; ++w)
@@ -1440,40 +1487,35 @@ struct TcEpi {
     // Called by all 32 lanes of the warp (lane = accumulator row).
     __device__ void operator()(int, int, int col0, const uint32_t (&v)[32]) {
         if (col0 >= ncols) return;                           // the same in every lane (per tile)
+        uint32_t w = 0;
+#pragma unroll
+        for (int i = 0; i < tc::kBN / 32; ++i)               // a select, not a local-memory index
+            if (i == (col0 >> 5)) w = bits[i];
+        // this lane's row as codes (FP8 form: score = acc * query scale * row
+        // scale; rows past the cluster: 0) into the stage, and its best
+        // candidate's score
         const int lane = threadIdx.x & 31;
-        if (cs) {
-            // FP8 form: score = acc * query scale * row scale (rows past the cluster: 0)
+        float m = -INFINITY;
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                const float sc = col0 + i < ncs ? __ldg(cs + col0 + i) : 0.f;
-                stage[lane * kEpiPitch + i] = __uint_as_float(v[i]) * rs * sc;
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < 32; ++i) stage[lane * kEpiPitch + i] = __uint_as_float(v[i]);
+        for (int i = 0; i < 32; ++i) {
+            float x = __uint_as_float(v[i]);
+            if (cs) x = x * rs * (col0 + i < ncs ? __ldg(cs + col0 + i) : 0.f);
+            stage[lane * kEpiPitch + i] = score_code_sat(x, inv, binv);
+            m = fmaxf(m, ((w >> i) & 1u) ? x : -INFINITY);
         }
-        // the best candidate score of these 32 positions of this lane's row
-        {
-            uint32_t w = 0;
-#pragma unroll
-            for (int i = 0; i < tc::kBN / 32; ++i)           // a select, not a local-memory index
-                if (i == (col0 >> 5)) w = bits[i];
-            float m = -INFINITY;
-#pragma unroll
-            for (int i = 0; i < 32; ++i)
-                if ((w >> i) & 1u) m = fmaxf(m, stage[lane * kEpiPitch + i]);
-            if (crow) crow[col0 >> 5] = m;
-        }
+        if (crow) crow[col0 >> 5] = m > -INFINITY ? code_score(score_code_sat(m, inv, binv), B, step) : -INFINITY;
         __syncwarp();
-        const int sub = lane >> 3, c4 = (lane & 7) * 4;
+        const int sub = lane >> 2, c8 = (lane & 3) * 8;
 #pragma unroll
-        for (int rr = 0; rr < 32; rr += 4) {
+        for (int rr = 0; rr < 32; rr += 8) {
             const int r = rr + sub;
-            float* dst = reinterpret_cast<float*>(
+            uint16_t* dst = reinterpret_cast<uint16_t*>(
                 __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(drow), r));
             if (dst) {
-                const float* sr = stage + r * kEpiPitch + c4;
-                *reinterpret_cast<float4*>(dst + col0 + c4) = make_float4(sr[0], sr[1], sr[2], sr[3]);
+                const uint32_t* sr = stage + r * kEpiPitch + c8;
+                *reinterpret_cast<uint4*>(dst + col0 + c8) =
+                    make_uint4(__byte_perm(sr[0], sr[1], 0x5410), __byte_perm(sr[2], sr[3], 0x5410),
+                               __byte_perm(sr[4], sr[5], 0x5410), __byte_perm(sr[6], sr[7], 0x5410));
             }
         }
         __syncwarp();
@@ -1483,19 +1525,23 @@ struct TcEpi {
 };
 
 template <class Kind>
-__global__ void __launch_bounds__(kScoreThreads8, 1)
+__global__ void __launch_bounds__(ScorePlan<Kind>::kThreads, 1)
     tc_score_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                     const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, int kchunks,
                     TcArgs args, int* err) {
+    using Plan = ScorePlan<Kind>;
     extern __shared__ unsigned char smem[];
     __shared__ tc::Ctl ctl;
     TcSched sched{&args};
-    TcEpi epi;
+    TcEpi<Plan::kEpiWarps> epi;
     epi.a = &args;
-    // transpose staging after the engine's shared memory, one slice per epilogue warp
-    epi.stage = reinterpret_cast<float*>(smem + tc::kSmemBytes) +
+    // transpose staging after the engine's stages (1024-byte aligned start), one slice per epilogue warp
+    unsigned char* aligned = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem) + 1023) &
+                                                              ~(uintptr_t)1023);
+    epi.stage = reinterpret_cast<uint32_t*>(aligned + (Plan::kStageBytes - 1024)) +
                 (size_t)(threadIdx.x >= 64 ? (threadIdx.x >> 5) - 2 : 0) * 32 * kEpiPitch;
-    tc::gemm_tiles<Kind, TcSched, TcEpi, kScoreEpiWarps>(&mAhi, &mAlo, &mBhi, &mBlo, kchunks, sched, epi, err, smem, ctl);
+    tc::gemm_tiles<Kind, TcSched, TcEpi<Plan::kEpiWarps>, Plan::kEpiWarps, Plan::kStages>(
+        &mAhi, &mAlo, &mBhi, &mBlo, kchunks, sched, epi, err, smem, ctl);
 }
 
 
@@ -1583,7 +1629,8 @@ __global__ void __launch_bounds__(512) rescore_kernel(const float* __restrict__ 
 // pair's dense row of approximate scores over its cluster's positions and its
 // candidate bitmap (both written per pair slot, see mark_kernel and TcEpi).
 struct DenseArgs {
-    const float* dense;
+    const uint16_t* dense;
+    const float* qbound;        // per query: the codes' range bound B
     const float* cmax;
     const uint32_t* bitmap;
     const int64_t* bm_off;
@@ -1596,7 +1643,7 @@ struct DenseArgs {
 };
 
 struct PairRow {
-    const float* row;
+    const uint16_t* row;        // score codes (score_code)
     const uint32_t* bm;
     const float* cm;            // best candidate score per bitmap word
     int64_t cb;                 // first row of the cluster in the reordered corpus
@@ -1666,6 +1713,7 @@ __global__ void __launch_bounds__(256) select_query_kernel(DenseArgs da, int c, 
     if (redo && (int)blockIdx.x >= *redo_count) return;
     const int64_t q = redo ? redo[blockIdx.x] : blockIdx.x;
     const int tid = threadIdx.x;
+    const float cB = da.qbound[q] > 0.f ? da.qbound[q] : 1.f, cstep = code_step(cB);   // the codes' range
     if (tid == 0) { s_lo_ord = 0xffffffffu; s_hi_ord = 0u; s_n = 0; }
     load_pairs(da, q, c, s_pr, &s_total, redo ? nullptr : trace_ucount, !redo, counters);
     __syncthreads();
@@ -1675,7 +1723,7 @@ __global__ void __launch_bounds__(256) select_query_kernel(DenseArgs da, int c, 
         const PairRow pr = s_pr[p];
         for (int pos = tid; pos < pr.n_c; pos += blockDim.x) {
             if (!is_cand(pr, pos)) continue;
-            const uint32_t h = ~float_order(pr.row[pos]);
+            const uint32_t h = ~float_order(code_score(pr.row[pos], cB, cstep));
             kmin = min(kmin, h);
             kmax = max(kmax, h);
         }
@@ -1718,7 +1766,7 @@ __global__ void __launch_bounds__(256) select_query_kernel(DenseArgs da, int c, 
             const PairRow pr = s_pr[p];
             for (int pos = tid; pos < pr.n_c; pos += blockDim.x) {
                 if (!is_cand(pr, pos)) continue;
-                const float sc = pr.row[pos];
+                const float sc = code_score(pr.row[pos], cB, cstep);
                 if (status(sc, l) == 2) atomicAdd(&bins[bucket(l, sc)], 1u);
             }
         }
@@ -1772,7 +1820,7 @@ __global__ void __launch_bounds__(256) select_query_kernel(DenseArgs da, int c, 
             const PairRow pr = s_pr[p];
             for (int pos = tid; pos < pr.n_c; pos += blockDim.x) {
                 if (!is_cand(pr, pos)) continue;
-                const float sc = pr.row[pos];
+                const float sc = code_score(pr.row[pos], cB, cstep);
                 const int st = status(sc, levels);
                 bool take;
                 if (st == 2) {
@@ -1906,6 +1954,7 @@ __global__ void __launch_bounds__(512) select_hist_kernel(
     const int need = min(ks, total);
     const float B = qbound[q];
     const float scale = B > 0.f ? (float)kHistBins / (2.f * B) : 0.f;
+    const float cB = B > 0.f ? B : 1.f, cstep = code_step(cB);   // the score codes' range
     auto bin_of = [&](float sc) -> int {
         const float x = __fmul_rn(__fadd_rn(B, -sc), scale);
         return (int)fminf(fmaxf(x, 0.f), (float)(kHistBins - 1));
@@ -1923,7 +1972,9 @@ __global__ void __launch_bounds__(512) select_hist_kernel(
             wv[r] = 0u;
             if (g < ng) {
                 wv[r] = (__ldg(pr.bm + (g >> 3)) >> ((g & 7) * 4)) & 0xfu;
-                sc[r] = __ldg(reinterpret_cast<const float4*>(pr.row) + g);
+                const uint2 cd = __ldg(reinterpret_cast<const uint2*>(pr.row) + g);
+                sc[r] = make_float4(code_score(cd.x & 0xffffu, cB, cstep), code_score(cd.x >> 16, cB, cstep),
+                                    code_score(cd.y & 0xffffu, cB, cstep), code_score(cd.y >> 16, cB, cstep));
             }
         }
     };
@@ -1987,9 +2038,14 @@ __global__ void __launch_bounds__(512) select_hist_kernel(
                 const uint32_t bw = __ldg(pr.bm + w);
                 float v[32];
 #pragma unroll
-                for (int g4 = 0; g4 < 8; ++g4) {
-                    const float4 f = __ldg(reinterpret_cast<const float4*>(pr.row + 32 * w) + g4);
-                    v[4 * g4] = f.x; v[4 * g4 + 1] = f.y; v[4 * g4 + 2] = f.z; v[4 * g4 + 3] = f.w;
+                for (int g8 = 0; g8 < 4; ++g8) {
+                    const uint4 cd = __ldg(reinterpret_cast<const uint4*>(pr.row + 32 * w) + g8);
+                    const uint32_t u[4] = {cd.x, cd.y, cd.z, cd.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        v[8 * g8 + 2 * e] = code_score(u[e] & 0xffffu, cB, cstep);
+                        v[8 * g8 + 2 * e + 1] = code_score(u[e] >> 16, cB, cstep);
+                    }
                 }
                 uint32_t take = 0u;
 #pragma unroll
@@ -2290,7 +2346,7 @@ struct Workspace {
     int32_t* redo;              // tensor paths: queries left to the multi-level select
     int32_t* redo_count;        // (cleared)
     int32_t* pcount;            // tensor path: candidates per pair (cleared; written by mark_kernel)
-    float* dense;               // tensor paths: per pair slot, approximate scores over its cluster
+    uint16_t* dense;            // tensor paths: per pair slot, approximate score codes over its cluster
     float* cmax;                // tensor paths: per pair slot and bitmap word, the best candidate score
     int32_t* slot_of;           // tensor paths: pair -> its slot in cluster order
     int32_t* unit_off;
@@ -2383,7 +2439,7 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, const
     w.pscore = tensor ? nullptr : (float*)take((size_t)np * sh.kp * 4);
     w.pid = tensor ? nullptr : (int64_t*)take((size_t)np * sh.kp * 8);
     w.pbuf = tensor ? nullptr : (uint64_t*)take((size_t)np * g.L * sh.R * 8);
-    w.dense = tensor ? (float*)take((size_t)sh.bitmap_words * 32 * 4) : nullptr;
+    w.dense = tensor ? (uint16_t*)take((size_t)sh.bitmap_words * 32 * 2) : nullptr;
     w.cmax = tensor ? (float*)take((size_t)sh.bitmap_words * 4) : nullptr;
     w.slot_of = tensor ? (int32_t*)take((size_t)np * 4) : nullptr;
     w.sl_ids = tensor ? (int64_t*)take((size_t)nq * sh.so * 8) : nullptr;
@@ -2430,9 +2486,20 @@ int check_search_args(const lider_index* ix, const float* Q, int64_t nq, int k, 
     return LIDER_OK;
 }
 
-// Enqueue steps 1-6 on `st` using workspace `w`.
+// Queries that reach the device in chunks (lider_search_host): chunk i holds
+// queries [bounds[i], bounds[i+1]) and is in device memory once event ready[i]
+// has completed.  The per-query front of the search (hash, route) runs chunk by
+// chunk as they arrive; the rest waits for the whole batch.
+struct FrontFeed {
+    int n;
+    const int64_t* bounds;
+    const cudaEvent_t* ready;
+};
+
+// Enqueue the search on `st` using workspace `w`.
 int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int c, int64_t* out_ids,
-                   float* out_scores, const lider_trace* tr, const Workspace& w, cudaStream_t st) {
+                   float* out_scores, const lider_trace* tr, const Workspace& w, cudaStream_t st,
+                   const FrontFeed* feed = nullptr) {
     const Geometry& g = ix->g;
     const int R = ix->params.r0 * k;
     const int64_t np = nq * c;
@@ -2444,78 +2511,97 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
     };
     LIDER_CUDA_TRY(cudaMemsetAsync(w.counters, 0, w.zero_bytes, st));
 
-    // 1. hash
-    if ((rc = mark(LIDER_PHASE_HASH))) return rc;
+    // 1-2. hash and route, chunk by chunk: queries [q0, q1)
     const bool tensor_route = ix->params.score_mode != LIDER_SCORE_SIMT;
-    CUtensorMap mqs_h, mqs_l;      // tensor paths: the queries as TF32 head / tail
-    if (tensor_route) {
-        if ((rc = launch_split_tf32(Q, nq * g.d, w.qs_hi, w.qs_lo, st))) return rc;
-        if ((rc = make_tensor_map(&mqs_h, w.qs_hi, nq, g.d, tc::kBM))) return rc;
-        if ((rc = make_tensor_map(&mqs_l, w.qs_lo, nq, g.d, tc::kBM))) return rc;
-        qnorm_kernel<<<(unsigned)cdiv(nq * 32, 256), 256, 0, st>>>(Q, nq, g.d, w.qnorm);
+    auto hash_chunk = [&](int64_t q0, int64_t q1) -> int {
+        const int64_t n = q1 - q0;
+        const float* Qc = Q + q0 * g.d;
+        if (!tensor_route) return launch_hash_t(Qc, n, g.d, g.A, g.bproj, g.H, g.W, w.tq + q0 * g.H, st);
+        CUtensorMap mqs_h, mqs_l;      // the chunk's queries as TF32 head / tail
+        if ((rc = launch_split_tf32(Qc, n * g.d, w.qs_hi + q0 * g.d, w.qs_lo + q0 * g.d, st))) return rc;
+        if ((rc = make_tensor_map(&mqs_h, w.qs_hi + q0 * g.d, n, g.d, tc::kBM))) return rc;
+        if ((rc = make_tensor_map(&mqs_l, w.qs_lo + q0 * g.d, n, g.d, tc::kBM))) return rc;
+        qnorm_kernel<<<(unsigned)cdiv(n * 32, 256), 256, 0, st>>>(Qc, n, g.d, w.qnorm + q0);
         LIDER_LAUNCH_CHECK("qnorm_kernel");
-        HashSched hs{(int)nq, g.H};
+        HashSched hs{(int)n, g.H};
         HashEpi he;
-        he.t = w.tq;
+        he.t = w.tq + q0 * g.H;
         he.b = g.bproj;
         he.a_norm = ix->a_norm;
-        he.qnorm = w.qnorm;
+        he.qnorm = w.qnorm + q0;
         he.recheck = w.hrecheck;
         he.n_recheck = w.n_hrecheck;
         he.W = (float)g.W;
         he.hyper = g.hash_kind == LIDER_HASH_HYPERPLANE;
         he.guard = kTcGuard;
-        he.nq = (int)nq;
+        he.nq = (int)n;
         he.H = g.H;
-        const int64_t tiles = cdiv(nq, tc::kBM) * cdiv(g.H, tc::kBN);
+        he.q0 = (int)q0;
+        const int64_t tiles = cdiv(n, tc::kBM) * cdiv(g.H, tc::kBN);
         if ((rc = smem_attr((const void*)hash_tc_kernel, (int)(tc::kSmemBytes)))) return rc;
         hash_tc_kernel<<<(unsigned)std::min<int64_t>(tiles, ix->num_sms), tc::kThreads, tc::kSmemBytes, st>>>(
             mqs_h, mqs_l, ix->map_ahi, ix->map_alo, (g.d + tc::KindTf32x3::kBK - 1) / tc::KindTf32x3::kBK, hs, he,
             w.tc_err);
         LIDER_LAUNCH_CHECK("hash_tc_kernel");
-        hash_recheck_kernel<<<(unsigned)(16 * ix->num_sms), 32, (size_t)2 * g.d * sizeof(float), st>>>(
-            Q, g.A, g.bproj, g.W, g.d, g.H, w.hrecheck, w.n_hrecheck, w.tq);
-        LIDER_LAUNCH_CHECK("hash_recheck_kernel");
-    } else {
-        if ((rc = launch_hash_t(Q, nq, g.d, g.A, g.bproj, g.H, g.W, w.tq, st))) return rc;
-    }
-    if ((rc = launch_pack(w.tq, nq, g.L, g.m, g.beta, g.hash_kind, 0, g.L, 1, w.qkeys, &w.counters[CNT_QBOUNDARY],
-                          &w.counters[CNT_QCLAMPED], st)))
-        return rc;
-    if (tr && tr->qkeys)
-        LIDER_CUDA_TRY(cudaMemcpyAsync(tr->qkeys, w.qkeys, (size_t)nq * g.L * 8, cudaMemcpyDeviceToDevice, st));
-    // 2. route
-    if ((rc = mark(LIDER_PHASE_ROUTE))) return rc;
-    if (ix->params.score_mode != LIDER_SCORE_SIMT) {
-        float* S = reinterpret_cast<float*>(w.rscore);
-        const CUtensorMap& mqh = mqs_h;
-        const CUtensorMap& mql = mqs_l;
-        RouteSched rs{(int)nq, g.ncl};
+        return LIDER_OK;
+    };
+    auto route_chunk = [&](int64_t q0, int64_t q1) -> int {
+        const int64_t n = q1 - q0;
+        const float* Qc = Q + q0 * g.d;
+        int32_t* trace_route = tr && tr->route ? tr->route + q0 * c : nullptr;
+        if (!tensor_route) {
+            if ((rc = launch_scores(Qc, n, g.d, g.C, g.half_norm, g.ncl, w.rscore + q0 * g.ncl, st))) return rc;
+            topc_kernel<<<(unsigned)cdiv(n * 32, 256), 256, 0, st>>>(w.rscore + q0 * g.ncl, n, g.ncl, c,
+                                                                     w.route + q0 * c, trace_route);
+            LIDER_LAUNCH_CHECK("topc_kernel");
+            return LIDER_OK;
+        }
+        float* S = reinterpret_cast<float*>(w.rscore) + q0 * g.ncl;
+        CUtensorMap mqh, mql;
+        if ((rc = make_tensor_map(&mqh, w.qs_hi + q0 * g.d, n, g.d, tc::kBM))) return rc;
+        if ((rc = make_tensor_map(&mql, w.qs_lo + q0 * g.d, n, g.d, tc::kBM))) return rc;
+        RouteSched rs{(int)n, g.ncl};
         RouteEpi re;
         re.S = S;
         re.half_norm = g.half_norm;
-        re.nq = (int)nq;
+        re.nq = (int)n;
         re.ncl = g.ncl;
-        const int64_t tiles = cdiv(nq, tc::kBM) * cdiv(g.ncl, tc::kBN);
+        const int64_t tiles = cdiv(n, tc::kBM) * cdiv(g.ncl, tc::kBN);
         if ((rc = smem_attr((const void*)route_tc_kernel, (int)(tc::kSmemBytes)))) return rc;
         route_tc_kernel<<<(unsigned)std::min<int64_t>(tiles, ix->num_sms), tc::kThreads, tc::kSmemBytes, st>>>(
             mqh, mql, ix->map_chi, ix->map_clo, (g.d + tc::KindTf32x3::kBK - 1) / tc::KindTf32x3::kBK, rs, re,
             w.tc_err);
         LIDER_LAUNCH_CHECK("route_tc_kernel");
         // guard: the tensor-core error of one score stays below kTcGuard |q| |mu|
-        topc_exact_kernel<<<(unsigned)cdiv(nq * 32, 256), 256, 0, st>>>(
-            S, Q, g.C, g.half_norm, nq, g.ncl, g.d, c, kTcGuard * ix->max_cnorm, w.route,
-            tr ? tr->route : nullptr,
-            guard_mode(ix->params.score_mode), ix->max_xnorm, ix->x_scale, ix->xres_max, ix->xhat_max, w.qscale,
-            w.qguard, w.qbound,
-            &w.counters[CNT_ROUTE_FALLBACK]);
+        topc_exact_kernel<<<(unsigned)cdiv(n * 32, 256), 256, 0, st>>>(
+            S, Qc, g.C, g.half_norm, n, g.ncl, g.d, c, kTcGuard * ix->max_cnorm, w.route + q0 * c, trace_route,
+            guard_mode(ix->params.score_mode), ix->max_xnorm, ix->x_scale, ix->xres_max, ix->xhat_max,
+            w.qscale + q0, w.qguard + q0, w.qbound + q0, &w.counters[CNT_ROUTE_FALLBACK]);
         LIDER_LAUNCH_CHECK("topc_exact_kernel");
-    } else {
-    if ((rc = launch_scores(Q, nq, g.d, g.C, g.half_norm, g.ncl, w.rscore, st))) return rc;
-    topc_kernel<<<(unsigned)cdiv(nq * 32, 256), 256, 0, st>>>(w.rscore, nq, g.ncl, c, w.route,
-                                                              tr ? tr->route : nullptr);
-    LIDER_LAUNCH_CHECK("topc_kernel");
+        return LIDER_OK;
+    };
+    if ((rc = mark(LIDER_PHASE_HASH))) return rc;
+    const int nch = feed ? feed->n : 1;
+    for (int i = 0; i < nch; ++i) {
+        const int64_t q0 = feed ? feed->bounds[i] : 0, q1 = feed ? feed->bounds[i + 1] : nq;
+        if (feed) LIDER_CUDA_TRY(cudaStreamWaitEvent(st, feed->ready[i], 0));
+        if (q1 <= q0) continue;
+        if ((rc = hash_chunk(q0, q1))) return rc;
+        if (i == nch - 1 && (rc = mark(LIDER_PHASE_ROUTE))) return rc;
+        if ((rc = route_chunk(q0, q1))) return rc;
     }
+    // hash values too close to a bucket edge for the tiles' error, recomputed
+    // exactly; then the packed keys of the whole batch
+    if (tensor_route) {
+        hash_recheck_kernel<<<(unsigned)(16 * ix->num_sms), 32, (size_t)2 * g.d * sizeof(float), st>>>(
+            Q, g.A, g.bproj, g.W, g.d, g.H, w.hrecheck, w.n_hrecheck, w.tq);
+        LIDER_LAUNCH_CHECK("hash_recheck_kernel");
+    }
+    if ((rc = launch_pack(w.tq, nq, g.L, g.m, g.beta, g.hash_kind, 0, g.L, 1, w.qkeys, &w.counters[CNT_QBOUNDARY],
+                          &w.counters[CNT_QCLAMPED], st)))
+        return rc;
+    if (tr && tr->qkeys)
+        LIDER_CUDA_TRY(cudaMemcpyAsync(tr->qkeys, w.qkeys, (size_t)nq * g.L * 8, cudaMemcpyDeviceToDevice, st));
     if (ix->params.route_kind == LIDER_ROUTE_CORE) {
         // Layer-1 centroids retriever: replaces the route of the exact scan
         // (whose per-query error bounds the tensor paths still use)
@@ -2601,39 +2687,34 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         ta.bm_off = w.bm_off;
         ta.ncl = g.ncl;
         ta.dense = w.dense;
+        ta.qbound = w.qbound;
+        ta.c = c;
         ta.bitmap = w.bitmap;
         ta.cmax = w.cmax;
         ta.slot_scale = sh.mode == LIDER_SCORE_FP8 ? w.slot_scale : nullptr;
         ta.col_scale = ix->x_rowscale;
-        const int tc_smem = tc::kSmemBytes + kEpiStageBytes;
         // A = queries of the tile (128 rows, box 128), B = cluster rows (256, box 256)
-        if (sh.mode == LIDER_SCORE_FP8) {
-            if ((rc = smem_attr((const void*)tc_score_kernel<tc::KindF8>, (int)(tc_smem)))) return rc;
-            tc_score_kernel<tc::KindF8><<<ix->num_sms, kScoreThreads8, tc_smem, st>>>(
-                mqh, mql, ix->map_xf8, ix->map_xf8, (g.d + tc::KindF8::kBK - 1) / tc::KindF8::kBK, ta, w.tc_err);
-        } else if (sh.mode == LIDER_SCORE_BF16) {
-            if ((rc = smem_attr((const void*)tc_score_kernel<tc::KindBf16>, (int)(tc_smem)))) return rc;
-            tc_score_kernel<tc::KindBf16><<<ix->num_sms, kScoreThreads8, tc_smem, st>>>(
-                mqh, mql, ix->map_xh16, ix->map_xh16, (g.d + tc::KindBf16::kBK - 1) / tc::KindBf16::kBK, ta,
-                w.tc_err);
-        } else if (sh.mode == LIDER_SCORE_F16) {
-            if ((rc = smem_attr((const void*)tc_score_kernel<tc::KindF16>, (int)(tc_smem)))) return rc;
-            tc_score_kernel<tc::KindF16><<<ix->num_sms, kScoreThreads8, tc_smem, st>>>(
-                mqh, mql, ix->map_xh16, ix->map_xh16, (g.d + tc::KindF16::kBK - 1) / tc::KindF16::kBK, ta,
-                w.tc_err);
-        } else {
-            if ((rc = smem_attr((const void*)tc_score_kernel<tc::KindTf32x3>, (int)(tc_smem)))) return rc;
-            tc_score_kernel<tc::KindTf32x3><<<ix->num_sms, kScoreThreads8, tc_smem, st>>>(
-                mqh, mql, ix->map_xhi, ix->map_xlo, (g.d + tc::KindTf32x3::kBK - 1) / tc::KindTf32x3::kBK, ta,
-                w.tc_err);
-        }
-        LIDER_LAUNCH_CHECK("tc_score_kernel");
+        auto launch_score = [&](auto kind, const CUtensorMap& mb0, const CUtensorMap& mb1) -> int {
+            using Kind = decltype(kind);
+            using Plan = ScorePlan<Kind>;
+            if ((rc = smem_attr((const void*)tc_score_kernel<Kind>, Plan::kSmem))) return rc;
+            tc_score_kernel<Kind><<<ix->num_sms, Plan::kThreads, Plan::kSmem, st>>>(
+                mqh, mql, mb0, mb1, (g.d + Kind::kBK - 1) / Kind::kBK, ta, w.tc_err);
+            LIDER_LAUNCH_CHECK("tc_score_kernel");
+            return LIDER_OK;
+        };
+        if (sh.mode == LIDER_SCORE_FP8) rc = launch_score(tc::KindF8{}, ix->map_xf8, ix->map_xf8);
+        else if (sh.mode == LIDER_SCORE_BF16) rc = launch_score(tc::KindBf16{}, ix->map_xh16, ix->map_xh16);
+        else if (sh.mode == LIDER_SCORE_F16) rc = launch_score(tc::KindF16{}, ix->map_xh16, ix->map_xh16);
+        else rc = launch_score(tc::KindTf32x3{}, ix->map_xhi, ix->map_xlo);
+        if (rc) return rc;
         if ((rc = mark(LIDER_PHASE_SELECT))) return rc;
         // 3xTF32 and FP16 paths: a guard band makes the re-scored top k exact;
         // the served BF16 form keeps its approximate shortlist
         const int guarded = sh.mode != LIDER_SCORE_BF16 && sh.mode != LIDER_SCORE_FP8;
         DenseArgs da;
         da.dense = w.dense;
+        da.qbound = w.qbound;
         da.cmax = w.cmax;
         da.bitmap = w.bitmap;
         da.bm_off = w.bm_off;
@@ -2873,6 +2954,25 @@ int autotune_entry(lider_index* ix, const float* Q, int64_t nq, int k, int c, in
     return LIDER_OK;
 }
 
+// The address a kernel can use for host memory that is pinned and mapped into
+// the device's address space (cudaHostAlloc, torch's pinned memory), or null.
+void* device_view(const void* host) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+// End to end on host buffers.  The queries go to the device in up to
+// kHostChunks copies on a second stream, and the hash and route of each chunk
+// start as soon as it has landed, so the copy overlaps the per-query front of
+// the search.  When the result buffers are pinned and mapped, the final
+// re-score writes the ids and scores into them directly (no copy back);
+// otherwise they are copied after the search.
+constexpr int kHostChunks = 4;
+
 int search_host_entry(const lider_index* ix, const float* Qh, int64_t nq, int k, int c, int64_t* ids_h,
                       float* scores_h, lider_search_stats* stats, void* stream) {
     int rc = check_search_args(ix, Qh, nq, k, c, ids_h, scores_h);
@@ -2880,28 +2980,58 @@ int search_host_entry(const lider_index* ix, const float* Qh, int64_t nq, int k,
     if (stats) *stats = lider_search_stats{};
     if (nq == 0) return LIDER_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t qb = (size_t)nq * ix->g.d * 4, ib = (size_t)nq * k * 8, sb = (size_t)nq * k * 4;
+    int64_t* ids_view = static_cast<int64_t*>(device_view(ids_h));
+    float* scores_view = static_cast<float*>(device_view(scores_h));
+    const bool direct = ids_view && scores_view;
+    const size_t qb = (size_t)nq * ix->g.d * 4, ib = direct ? 0 : (size_t)nq * k * 8, sb = direct ? 0 : (size_t)nq * k * 4;
     const size_t o_ids = align_up(qb, 256), o_sc = align_up(o_ids + ib, 256);
-    Workspace sz = carve(nullptr, ix->g, nq, c, search_shape(ix, k, nq, c));
+    const Shape sh = search_shape(ix, k, nq, c);
+    Workspace sz = carve(nullptr, ix->g, nq, c, sh);
     const size_t o_ws = align_up(o_sc + sb, 256);
     void* mem = nullptr;
     if ((rc = pool_alloc(ix, &mem, o_ws + sz.total, st))) return rc;
     unsigned char* m = (unsigned char*)mem;
     float* Qd = (float*)m;
-    int64_t* idd = (int64_t*)(m + o_ids);
-    float* scd = (float*)(m + o_sc);
-    Workspace w = carve(m + o_ws, ix->g, nq, c, search_shape(ix, k, nq, c));
-    cudaError_t e = cudaMemcpyAsync(Qd, Qh, qb, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync(queries)");
-    if (!rc) rc = enqueue_search(ix, Qd, nq, k, c, idd, scd, nullptr, w, st);
-    if (!rc && (e = cudaMemcpyAsync(ids_h, idd, ib, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    int64_t* idd = direct ? ids_view : (int64_t*)(m + o_ids);
+    float* scd = direct ? scores_view : (float*)(m + o_sc);
+    Workspace w = carve(m + o_ws, ix->g, nq, c, sh);
+
+    // chunked copy-in on a stream of its own, ordered after the caller's stream
+    const int nch = (int)std::max<int64_t>(1, std::min<int64_t>(kHostChunks, nq / 2048));
+    int64_t bounds[kHostChunks + 1];
+    for (int i = 0; i <= nch; ++i) bounds[i] = nq * i / nch;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t evs[kHostChunks + 1] = {};
+    auto cleanup = [&]() {
+        for (cudaEvent_t e : evs)
+            if (e) cudaEventDestroy(e);
+        if (cs) cudaStreamDestroy(cs);
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    for (int i = 0; e == cudaSuccess && i <= nch; ++i) e = cudaEventCreateWithFlags(&evs[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(evs[nch], st);        // the caller's earlier work comes first
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, evs[nch], 0);
+    for (int i = 0; e == cudaSuccess && i < nch; ++i) {
+        const size_t off = (size_t)bounds[i] * ix->g.d, len = (size_t)(bounds[i + 1] - bounds[i]) * ix->g.d;
+        e = cudaMemcpyAsync(Qd + off, Qh + off, len * 4, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(evs[i], cs);
+    }
+    if (e != cudaSuccess) rc = cuda_fail(e, "lider_search_host: copying the queries in");
+    const FrontFeed feed{nch, bounds, evs};
+    if (!rc) rc = enqueue_search(ix, Qd, nq, k, c, idd, scd, nullptr, w, st, &feed);
+    if (!rc && !direct && (e = cudaMemcpyAsync(ids_h, idd, (size_t)nq * k * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         rc = cuda_fail(e, "cudaMemcpyAsync(ids)");
-    if (!rc && (e = cudaMemcpyAsync(scores_h, scd, sb, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    if (!rc && !direct &&
+        (e = cudaMemcpyAsync(scores_h, scd, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         rc = cuda_fail(e, "cudaMemcpyAsync(scores)");
     if (!rc && stats) rc = read_stats(w, nq, c, stats, st);
+    // a complete search waited for every chunk's event on st; after a failure
+    // the copies may still run, so they finish before the memory is released
+    if (rc && cs) cudaStreamSynchronize(cs);
     e = cudaFreeAsync(mem, st);
     if (!rc && e != cudaSuccess) rc = cuda_fail(e, "cudaFreeAsync");
-    if (!rc && (e = cudaStreamSynchronize(st)) != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess && !rc) rc = cuda_fail(e, "cudaStreamSynchronize");
+    cleanup();
     return rc;
 }
 

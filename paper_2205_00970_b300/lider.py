@@ -133,6 +133,7 @@ def _load():
         "lider_export_array": ([P, I32, I32, P, P], ctypes.c_int),
         "lider_export_rmi": ([P, I32, I32, P, P, P, P], ctypes.c_int),
         "lider_debug_tc_tile": ([P, I32, P, I32, I32, I32, P, P], ctypes.c_int),
+        "lider_debug_tc_wait_expiry": ([P, I32, P, I32, I32, I32, P, ctypes.c_double, P], ctypes.c_int),
         "lider_server_create": ([P, ctypes.POINTER(ServerParams), ctypes.POINTER(P)], ctypes.c_int),
         "lider_server_submit": ([P, P, I64, I32, P, P, ctypes.POINTER(I64)], ctypes.c_int),
         "lider_server_wait": ([P, I64, ctypes.c_double], ctypes.c_int),
@@ -156,6 +157,7 @@ def exported_symbols() -> list[str]:
     return [n for n in ("lider_build", "lider_build_centroids", "lider_get_build_info", "lider_export_centroids",
                         "lider_export_assignment", "lider_export_projections", "lider_search", "lider_search_trace", "lider_search_host",
                         "lider_search_noalloc", "lider_search_scratch_bytes", "lider_debug_tc_tile",
+                        "lider_debug_tc_wait_expiry",
                         "lider_get_tuning", "lider_set_tuning", "lider_autotune",
                         "lider_index_info", "lider_cluster_offsets", "lider_export_array",
                         "lider_export_rmi", "lider_server_create", "lider_server_submit", "lider_server_wait",
@@ -402,6 +404,17 @@ def tc_tile(A: torch.Tensor, B: torch.Tensor, kind: int = 0, stream=None) -> tor
     _check(_lib.lider_debug_tc_tile(A.data_ptr(), A.shape[0], B.data_ptr(), B.shape[0], A.shape[1], kind,
                                     out.data_ptr(), _stream_ptr(stream)))
     return out
+
+
+def tc_wait_expiry(A: torch.Tensor, B: torch.Tensor, kind: int = 1, limit_ms: float = 5.0, stream=None) -> int:
+    """Run the engine's one-tile self-test with a stage left unloaded and every
+    wait limited to limit_ms; returns the C return code (the wait must run out:
+    LIDER_ECUDA, message in last_error())."""
+    A = _dev(A, torch.float32, "A")
+    B = _dev(B, torch.float32, "B")
+    out = torch.empty((A.shape[0], B.shape[0]), dtype=torch.float32, device=A.device)
+    return _lib.lider_debug_tc_wait_expiry(A.data_ptr(), A.shape[0], B.data_ptr(), B.shape[0], A.shape[1], kind,
+                                           out.data_ptr(), float(limit_ms), _stream_ptr(stream))
 
 
 def raw_call(name: str, *args):

@@ -92,6 +92,26 @@ def test_host_path_equals_device_path(tiny):
     assert torch.equal(hid, ids.cpu()) and torch.equal(hsc, sc.cpu())
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_path_in_chunks_equals_device_path(tiny, pinned):
+    """9,000 queries reach the device in four chunks whose hash and route
+    start as each lands; results go straight into pinned (mapped) result
+    buffers, or are copied back into pageable ones: either way bit-equal to
+    the search of the same queries already on the device."""
+    import torch
+    from paper_2205_00970_b300 import synth
+    cfg = tiny["cfg"]
+    Q = synth.queries(cfg["seed"] + 1, 9_000, cfg["d"], cfg["n_comp"], cfg["sigma"], cfg["zipf_s"])
+    ids, sc = tiny["gidx"].search(torch.from_numpy(Q).cuda(), cfg["k"], cfg["c"])
+    Qh = torch.from_numpy(Q)
+    hid = torch.full((len(Q), cfg["k"]), 7, dtype=torch.int64)
+    hsc = torch.zeros((len(Q), cfg["k"]), dtype=torch.float32)
+    if pinned:
+        Qh, hid, hsc = Qh.pin_memory(), hid.pin_memory(), hsc.pin_memory()
+    hid, hsc = tiny["gidx"].search_host(Qh, cfg["k"], cfg["c"], hid, hsc)
+    assert torch.equal(hid, ids.cpu()) and torch.equal(hsc, sc.cpu())
+
+
 @pytest.mark.parametrize("nq", [0, 1, 7, 33, 257])
 def test_ragged_batches_are_batch_invariant(tiny, nq):
     """A query's result does not depend on its batch-mates or batch size."""
