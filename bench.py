@@ -484,8 +484,9 @@ def run_lider(args, cfg):
     k, c, nq = cfg["k"], cfg["c"], cfg["nq"]
     ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
     sc = torch.empty((nq, k), dtype=torch.float32, device=dev)
-    # a step searches the whole batch, in lider_search calls of at most
-    # --sub-batch queries (the per-call scratch grows with the batch)
+    # a step searches the whole batch in one lider_search call (the library
+    # splits a batch into passes when one pass cannot hold it), or in calls
+    # of --sub-batch queries
     sub = call_size(idx, nq, k, c, args.sub_batch or nq)
     chunks = [(lo, min(nq, lo + sub)) for lo in range(0, nq, sub)]
 
@@ -533,9 +534,22 @@ def run_lider(args, cfg):
         dist.barrier()
     total_ms = t0.elapsed_time(t1)
     step_ms = [evs[s][0][0].elapsed_time(evs[s][-1][nph - 1]) for s in range(args.steps)]
-    phase_ms = {name: float(np.mean([sum(evs[s][ci][i].elapsed_time(evs[s][ci][i + 1]) for ci in range(len(chunks)))
-                                     for s in range(args.steps)]))
-                for i, name in enumerate(lider.PHASES)}
+    passes = stats.get("passes", len(chunks))
+    if passes <= len(chunks):
+        phase_ms = {name: float(np.mean([sum(evs[s][ci][i].elapsed_time(evs[s][ci][i + 1])
+                                             for ci in range(len(chunks))) for s in range(args.steps)]))
+                    for i, name in enumerate(lider.PHASES)}
+        phase_of = "every call of the timed steps"
+    else:
+        # the library searched each call in passes: the phases come from an
+        # untimed run of the same passes, one call per pass
+        pb = -(-nq // (passes // len(chunks)))
+        pev = [[torch.cuda.Event(enable_timing=True) for _ in range(nph)] for _ in range(0, nq, pb)]
+        for pi, lo in enumerate(range(0, nq, pb)):
+            idx.search_phased(Qd[lo:lo + pb], k, c, pev[pi], out=(ids[lo:lo + pb], sc[lo:lo + pb]))
+        torch.cuda.synchronize()
+        phase_ms = {name: float(sum(ev[i].elapsed_time(ev[i + 1]) for ev in pev)) for i, name in enumerate(lider.PHASES)}
+        phase_of = f"an untimed run of the {len(pev)} passes of {pb:,} queries, one call each"
     total_ms = max_over_ranks(total_ms, dev)
     value = job_throughput(nq, args.steps, world, total_ms)
 
@@ -599,11 +613,13 @@ def run_lider(args, cfg):
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "of": f"one batch of {nq:,} queries"},
         "phase_ms": phase_ms,
+        "phase_ms_of": phase_of,
+        "passes_per_step": passes,
         "search_stats": stats,
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": int(Q.nbytes),
                 "d2h_bytes_per_step": int(nq * k * (8 + 4))},
-        "gpu_launches": LAUNCHES_PER_SEARCH[args.score] * args.steps,
+        "gpu_launches": LAUNCHES_PER_SEARCH[args.score] * passes * args.steps,
         "graph_replay": graph,
         "tuning": tuning,
         "score_mode": args.score,
@@ -628,9 +644,11 @@ def run_lider(args, cfg):
 
 def served_compare(args, cfg, X, C, A, b, Qd, chunks, plain_ids, dev) -> dict:
     """The metric's other side: the served BF16 form (BF16 corpus copy scored
-    on the tensor cores, FP32 re-rank of the best rerank * k) on the same
-    queries, timed the same way, with recall@10 against the plain (exact)
-    search's top-10.  Errors are reported in the line, not raised."""
+    on the tensor cores, FP32 re-rank of a shortlist of --served-rerank * k)
+    on the same queries, timed the same way; recall@10 against FP64 brute
+    force on the first --recall-nq queries for it and for the plain (exact)
+    search, and against the plain search's top-10 on every query.  Errors are
+    reported in the line, not raised."""
     import torch
 
     from paper_2205_00970_b300 import lider
@@ -638,7 +656,7 @@ def served_compare(args, cfg, X, C, A, b, Qd, chunks, plain_ids, dev) -> dict:
         t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
         Xd = t(X)
         sidx = lider.Index(Xd, t(C), t(A), t(b), L=cfg["L"], m=cfg["m"], W=cfg["W"], rmi_leaves=cfg["leaves"],
-                           r0=cfg["r0"], B=cfg["B"], score_mode=lider.SCORE_BF16, rerank=args.rerank)
+                           r0=cfg["r0"], B=cfg["B"], score_mode=lider.SCORE_BF16, rerank=args.served_rerank)
         del Xd
         k, c, nq = cfg["k"], cfg["c"], Qd.shape[0]
         ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
@@ -665,8 +683,13 @@ def served_compare(args, cfg, X, C, A, b, Qd, chunks, plain_ids, dev) -> dict:
         sidx.free()
         del sidx
         torch.cuda.empty_cache()
+        nr = min(args.recall_nq, nq)
+        truth = fp64_knn(X, Qd[:nr].cpu().numpy(), 10)
         return {"value": nq / (ms / 1e3), "unit": "queries/s", "ms_per_step": ms,
-                "shortlist": f"{args.rerank} * k", "recall_at_10_vs_plain": recall10(got, plain_ids),
+                "shortlist": f"{args.served_rerank} * k",
+                "recall_at_10": recall10(got[:nr], truth), "recall_at_10_plain": recall10(plain_ids[:nr], truth),
+                "recall_sample": f"first {nr:,} queries against FP64 brute force",
+                "recall_at_10_vs_plain": recall10(got, plain_ids),
                 "tuning": "autotuned" if not args.no_autotune else "default launch shapes"}
     except Exception as e:                               # the main line must still print
         return {"error": f"{type(e).__name__}: {e}"[:300]}
@@ -860,6 +883,73 @@ def run_variants(args, cfg):
     return 0
 
 
+def run_sweep(args, cfg):
+    """Recall@10 against FP64 brute force and queries/s over the operating
+    parameters of the search: bucket width W and expansion factor r0 (index
+    parameters; one index per pair, all from the first build's clustering) and
+    clusters probed c.  The FP16 exact mode searches --sweep-nq queries per
+    setting; recall is measured on the first --sweep-recall-nq of them.
+    Reports every point and the fastest one with recall@10 >= 0.9 (or that
+    none reaches it)."""
+    import torch
+
+    from paper_2205_00970_b300 import lider
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    X, Q, A, b = load_inputs(cfg)
+    nq = min(args.sweep_nq, cfg["nq"])
+    Qd = torch.from_numpy(np.ascontiguousarray(Q[:nq])).to(dev)
+    k = cfg["k"]
+    truth = fp64_knn(X, Q[:args.sweep_recall_nq], 10)
+    Xd = torch.from_numpy(X).to(dev)
+    C = None
+    points = []
+    for W in args.sweep_W:
+        for r0 in args.sweep_r0:
+            if cfg["L"] * r0 * k > lider.MAX_LR:
+                continue
+            c_cfg = dict(cfg, W=W, r0=r0)
+            if W != cfg["W"]:
+                A2, b2 = synth.projections(cfg["seed"], cfg["L"], cfg["m"], cfg["d"], W)
+            else:
+                A2, b2 = A, b
+            idx = build_gpu_index(c_cfg, Xd, A2, b2, centroids=C, score_mode=lider.SCORE_F16)
+            if C is None:
+                C = idx.centroids()
+            for c in args.sweep_c:
+                if c > min(lider.MAX_C, cfg["n_clusters"]):
+                    continue
+                ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
+                sc = torch.empty((nq, k), dtype=torch.float32, device=dev)
+                idx.search(Qd, k, c, out=(ids, sc))                   # warm-up
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record()
+                for _ in range(args.steps):
+                    idx.search(Qd, k, c, out=(ids, sc))
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / args.steps
+                got = ids[:args.sweep_recall_nq].cpu().numpy()
+                points.append({"W": W, "r0": r0, "c": c, "queries_per_s": nq / (ms / 1e3), "ms_per_batch": ms,
+                               "recall_at_10": recall10(got, truth)})
+                print(json.dumps({"sweep_point": points[-1]}), flush=True)
+            idx.free()
+            del idx
+            torch.cuda.empty_cache()
+    ok = [p for p in points if p["recall_at_10"] >= 0.9]
+    best = max(ok, key=lambda p: p["queries_per_s"]) if ok else None
+    line = {"metric": "queries/s and recall@10 vs FP64 brute force over W, r0, c", "n_gpus": 1, "steps": args.steps,
+            "data": "synthetic", "config": workload_desc(cfg), "score_mode": "f16",
+            "sample": (f"{nq:,} queries per setting; recall on the first {args.sweep_recall_nq} against FP64 brute "
+                       f"force over all {cfg['n']:,} rows"),
+            "points": points, "operating_point_recall_0_9": best,
+            "note": None if best else "no setting in the sweep reaches recall@10 0.9"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_precision(args, cfg):
     """Precision mode: the workload's corpus indexed once per dtype (the exact
     FP16-guarded mode, the served BF16 and FP8-e4m3 forms with a shortlist of
@@ -946,8 +1036,12 @@ def main():
     ap.add_argument("--score", choices=list(MODES), default="f16",
                     help="f16 (default), tensor (3xTF32) and simt give the same exact top-k; bf16 is the served "
                          "shortlist form")
+    ap.add_argument("--served-rerank", type=int, default=1,
+                    help="the main line's served BF16 comparison: shortlist = served_rerank * k")
+    ap.add_argument("--recall-nq", type=int, default=1024,
+                    help="queries whose recall@10 against FP64 brute force the served comparison measures")
     ap.add_argument("--rerank", type=int, default=None,
-                    help="served BF16 form: shortlist = rerank * k (default 2; precision workload: 40)")
+                    help="served BF16/FP8 forms: shortlist = rerank * k (default 1; precision workload: 40)")
     ap.add_argument("--serve", type=float, default=None,
                     help="serving mode: offered load in queries/s (Poisson arrivals)")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -959,6 +1053,13 @@ def main():
     ap.add_argument("--precision", action="store_true",
                     help="per-dtype recall and score error (f16 exact, bf16 and fp8 served forms)")
     ap.add_argument("--precision-sample", type=int, default=16)
+    ap.add_argument("--sweep", action="store_true",
+                    help="recall@10 and queries/s over --sweep-W, --sweep-r0 and --sweep-c (FP16 exact mode)")
+    ap.add_argument("--sweep-W", type=float, nargs="+", default=[1.0, 2.0])
+    ap.add_argument("--sweep-r0", type=int, nargs="+", default=[1, 3, 5])
+    ap.add_argument("--sweep-c", type=int, nargs="+", default=[8, 16, 32])
+    ap.add_argument("--sweep-nq", type=int, default=10_000)
+    ap.add_argument("--sweep-recall-nq", type=int, default=256)
     ap.add_argument("--variants", action="store_true",
                     help="fidelity variants: hyperplane hashkeys, Layer-1 centroids retriever, raw-key RMIs")
     ap.add_argument("--hyper-m", type=int, default=32, help="--variants: bits per hyperplane hashkey")
@@ -976,7 +1077,7 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="profiling size: first n corpus rows")
     ap.add_argument("--nq", type=int, default=None, help="profiling size: first nq queries")
     ap.add_argument("--sub-batch", type=int, default=None,
-                    help="queries per lider_search call (default: the whole batch; batched/precision: 6,250)")
+                    help="queries per lider_search call (default: the whole batch in one call)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -986,13 +1087,13 @@ def main():
     if args.nq:
         cfg["nq"] = min(cfg["nq"], args.nq)
     if args.rerank is None:
-        args.rerank = cfg.get("rerank", 2)
-    if args.sub_batch is None and cfg["name"] in ("batched", "precision"):
-        args.sub_batch = 6250
+        args.rerank = cfg.get("rerank", 1)
     if args.impl == "reference":
         return run_reference(args, cfg)
     if args.serve:
         return run_serve(args, cfg)
+    if args.sweep:
+        return run_sweep(args, cfg)
     if args.precision:
         return run_precision(args, cfg)
     if args.variants:

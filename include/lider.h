@@ -137,6 +137,7 @@ typedef struct {
     int64_t rmi_oor;
     int64_t rmi_le;
     int64_t rmi_oor_le;        /* both */
+    int64_t passes;            /* passes the batch was searched in (lider_search) */
 } lider_search_stats;
 
 /* Phases of one search, in order; events[i] is recorded when phase i starts
@@ -319,8 +320,9 @@ int lider_search_scratch_bytes(const lider_index* index, int64_t nq, int32_t k,
  *     every GPU loading this library holds until the process exits; a batch
  *     whose scratch would not fit is rejected with LIDER_ELIMIT (search fewer
  *     queries per call; the need grows with nq * c * L * r0 * k);
- *   - the first call on a device looks up the array's device address; make it
- *     before any stream capture;
+ *   - the first call on a device (and the first after the device's context
+ *     changed, e.g. after a reset) looks up the array's device address; make
+ *     it before any stream capture;
  *   - all calls share the array: calls that overlap on the GPU race and must
  *     be serialised by the caller.
  * No cudaMalloc, cudaFree or allocating library routine is called. */
@@ -342,7 +344,9 @@ int lider_search_noalloc(const lider_index* index, const float* queries, int64_t
  * completion thread finishes batches in launch order, copies each request's
  * rows into its buffers and records its latency (submission to results).
  * A request gets exactly the ids and scores lider_search gives for its queries
- * alone.  All functions are thread-safe. */
+ * alone.  All functions are thread-safe.  mem_budget counts search scratch
+ * only: the index itself and the fixed LIDER_NOALLOC_SCRATCH_BYTES array that
+ * every GPU loading the library holds are outside it. */
 typedef struct lider_server lider_server;
 
 typedef struct {
@@ -412,6 +416,10 @@ typedef struct {
     int32_t mark_threads;     /* per-pair bitmap block: 32, 64, 128 or 256             */
     int32_t tile_order;       /* tensor tiles of a cluster: 0 query tiles outer, 1 row
                                  tiles outer (a row tile's query tiles run together)   */
+    int32_t probe_batch;      /* queries per pass of lider_search (>= 0; 0: the whole
+                                 batch); a batch larger than one pass allows (the caps
+                                 of LIDER_ELIMIT, or 48 GiB of scratch) is searched in
+                                 passes of half as many, halved until one fits      */
 } lider_tuning;
 
 /* Current launch shapes of the index (host output). */

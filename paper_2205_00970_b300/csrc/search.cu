@@ -1358,15 +1358,25 @@ __global__ void __launch_bounds__(256) mark_kernel(const int32_t* __restrict__ p
 }
 
 // One tensor-core tile: A row (first query slot), B row (first corpus row),
-// cluster, and (query tile << 16 | row tile).  Written once per search so the
-// producer, MMA and epilogue warps each read a tile's coordinates with one load.
+// cluster, and (query tile << 16 | row tile); and what its epilogue needs
+// (umeta: query slots in the tile, cluster size, and the bitmap word of the
+// tile's first slot at its first column, low and high halves).  Written once
+// per search so the producer, MMA and epilogue warps each read a tile's
+// coordinates with one or two independent loads.  Each block also writes the
+// code bound of its cluster's pair slots (slot_bound: the slot's query's B).
 __global__ void tc_units_kernel(const int32_t* __restrict__ unit_off, const int32_t* __restrict__ off,
-                                const int64_t* __restrict__ cl_off, int ncl, int order, int4* __restrict__ units) {
+                                const int64_t* __restrict__ cl_off, const int64_t* __restrict__ bm_off,
+                                const int32_t* __restrict__ pairs, const float* __restrict__ qbound, int c, int ncl,
+                                int order, int4* __restrict__ units, int4* __restrict__ umeta,
+                                float* __restrict__ slot_bound) {
     const int j = blockIdx.x;
     const int64_t n_c = cl_off[j + 1] - cl_off[j];
+    for (int sl = off[j] + threadIdx.x; sl < off[j + 1]; sl += blockDim.x) slot_bound[sl] = qbound[pairs[sl] / c];
     const int u0 = unit_off[j], u1 = unit_off[j + 1];
     if (u1 <= u0) return;
     const int nrt = (int)((n_c + tc::kBN - 1) / tc::kBN);
+    const int cnt = off[j + 1] - off[j];
+    const int64_t words = bitmap_words(n_c);
     for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
         const int local = u - u0;
         // order 0: query tiles outer; 1: row tiles outer
@@ -1374,11 +1384,16 @@ __global__ void tc_units_kernel(const int32_t* __restrict__ unit_off, const int3
         const int it = order ? local % nit : local / nrt;
         const int rt = order ? local / nit : local % nrt;
         units[u] = make_int4(off[j] + it * tc::kBM, (int)(cl_off[j] + (int64_t)rt * tc::kBN), j, (it << 16) | rt);
+        const int64_t w0 = bm_off[j] + (int64_t)it * tc::kBM * words + rt * (tc::kBN / 32);
+        umeta[u] = make_int4(min(tc::kBM, cnt - it * tc::kBM), (int)n_c, (int)(uint32_t)(w0 & 0xffffffffll),
+                             (int)(w0 >> 32));
     }
 }
 
 struct TcArgs {
     const int4* units;
+    const int4* umeta;          // per tile: slots in it, cluster size, first bitmap word (lo, hi)
+    const float* slot_bound;    // per pair slot: the code bound B of its query
     const int32_t* unit_off;
     const int32_t* off;
     const int32_t* cnt;
@@ -1454,32 +1469,34 @@ struct TcEpi {
     uint32_t bits[tc::kBN / 32];  // this lane's candidate bits over the tile's 256 columns
 
     __device__ void begin(int u, int row) {
-        const int4 t = a->units[u];
-        const int j = t.z, it = t.w >> 16, rt = t.w & 0xffff;
-        const int in_tile = min(tc::kBM, a->cnt[j] - it * tc::kBM);
-        const int64_t n_c = a->cl_off[j + 1] - a->cl_off[j];
+        const int4 t = __ldg(a->units + u);
+        const int4 um = __ldg(a->umeta + u);
+        const int rt = t.w & 0xffff;
+        const int in_tile = um.x;
+        const int64_t n_c = um.y;
         const int64_t words = bitmap_words(n_c);
         const int p0 = rt * tc::kBN;
         ncols = (int)min((int64_t)tc::kBN, words * 32 - p0);
-        const int64_t wrow = a->bm_off[j] + ((int64_t)it * tc::kBM + row) * words;   // the pair's first word
-        drow = row < in_tile ? a->dense + wrow * 32 + p0 : nullptr;
-        B = row < in_tile ? a->qbound[a->pairs[a->off[j] + it * tc::kBM + row] / a->c] : 1.f;
+        const bool live = row < in_tile;
+        // this lane's pair: bitmap word at the tile's first column
+        const int64_t wt = ((int64_t)(uint32_t)um.w << 32 | (uint32_t)um.z) + (int64_t)row * words;
+        drow = live ? a->dense + wt * 32 : nullptr;
+        B = live ? __ldg(a->slot_bound + t.x + row) : 1.f;
         if (!(B > 0.f)) B = 1.f;                              // no scores to code (|q| = 0)
         inv = __fdiv_rn(65535.f, __fmul_rn(2.f, B));
         binv = __fmul_rn(B, inv);
         step = code_step(B);
-        crow = row < in_tile ? a->cmax + wrow + (p0 >> 5) : nullptr;
+        crow = live ? a->cmax + wt : nullptr;
         // this warp's column groups of the tile (kEpiWarps / 4 warps share each row)
         constexpr int kGpw = (tc::kBN / 32) / (kEpiWarps / 4);
         const int g0 = ((((int)threadIdx.x >> 5) - 2) >> 2) * kGpw;
 #pragma unroll
         for (int w = 0; w < tc::kBN / 32; ++w)
-            bits[w] = (row < in_tile && 32 * w < ncols && w >= g0 && w < g0 + kGpw)
-                          ? __ldg(a->bitmap + wrow + (p0 >> 5) + w) : 0u;
+            bits[w] = (live && 32 * w < ncols && w >= g0 && w < g0 + kGpw) ? __ldg(a->bitmap + wt + w) : 0u;
         cs = nullptr;
         if (a->slot_scale) {
-            rs = row < in_tile ? a->slot_scale[a->off[j] + it * tc::kBM + row] : 0.f;
-            cs = a->col_scale + a->cl_off[j] + p0;
+            rs = live ? a->slot_scale[t.x + row] : 0.f;
+            cs = a->col_scale + t.y;
             ncs = (int)min((int64_t)tc::kBN, n_c - p0);
         }
     }
@@ -2353,6 +2370,8 @@ struct Workspace {
     int64_t* bm_off;            // tensor paths: per-cluster bitmap offsets (words)
     uint32_t* bitmap;           // tensor paths: per-pair candidate bitmaps
     int4* units;                // tensor path: tile descriptors
+    int4* umeta;                // tensor path: per tile, what the epilogue needs
+    float* slot_bound;          // tensor path: per pair slot, its query's code bound
     float* qs_hi;               // tensor routing: queries, TF32 head / tail
     float* qs_lo;
     float* qp_hi;               // tensor path: queries in pair order, TF32 head / tail
@@ -2417,8 +2436,10 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, const
     w.bitmap = tensor ? (uint32_t*)take((size_t)sh.bitmap_words * 4) : nullptr;
     w.ncl = g.ncl;
     // tiles <= sum_j ceil(cnt_j/128) * ceil(n_c/256) <= (np/128 + ncl) * max_row_tiles
-    w.units = tensor ? (int4*)take((size_t)((np + tc::kBM - 1) / tc::kBM + g.ncl) * (size_t)g.max_row_tiles * 16)
-                     : nullptr;
+    const size_t max_units = (size_t)((np + tc::kBM - 1) / tc::kBM + g.ncl) * (size_t)g.max_row_tiles;
+    w.units = tensor ? (int4*)take(max_units * 16) : nullptr;
+    w.umeta = tensor ? (int4*)take(max_units * 16) : nullptr;
+    w.slot_bound = tensor ? (float*)take((size_t)np * 4) : nullptr;
     const size_t qelem = sh.mode == LIDER_SCORE_FP8 ? 1 : (sh.mode == LIDER_SCORE_BF16 || sh.mode == LIDER_SCORE_F16) ? 2 : 4;
     w.qp_hi = tensor ? (float*)take((size_t)np * g.d * qelem) : nullptr;
     w.qp_lo = sh.mode == LIDER_SCORE_TENSOR ? (float*)take((size_t)np * g.d * 4) : nullptr;
@@ -2455,8 +2476,24 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, const
 }
 
 // Shape and cap checks; with `buffers`, also the pointers and the device.
+// Caps of one pass of the search (nq queries searched with one workspace).
+int check_pass_caps(const lider_index* ix, int64_t nq, int k, int c) {
+    if (nq * c > (int64_t)INT32_MAX) return fail(LIDER_ELIMIT, "lider_search: nq * c exceeds 2^31-1");
+    if (ix->params.score_mode != LIDER_SCORE_SIMT && nq * ix->g.H > (int64_t)INT32_MAX)
+        return fail(LIDER_ELIMIT, "lider_search: nq * L * m exceeds 2^31-1; search fewer queries per call");
+    // tensor paths: per pair, a bitmap word and 32 16-bit score codes per 32 positions
+    if (ix->params.score_mode != LIDER_SCORE_SIMT && c <= ix->g.ncl &&
+        nq * ix->top_words[c] > ((int64_t)1 << 30))
+        return fail(LIDER_ELIMIT, "lider_search: the per-pair score rows of this batch exceed 64 GiB; search fewer "
+                                  "queries per call");
+    return LIDER_OK;
+}
+
+// Shape and cap checks; with `buffers`, also the pointers and the device.
+// `pass_caps`: whether nq must also fit one pass (lider_search splits larger
+// batches into passes itself).
 int check_search_args(const lider_index* ix, const float* Q, int64_t nq, int k, int c, const void* ids,
-                      const void* scores, bool buffers = true) {
+                      const void* scores, bool buffers = true, bool pass_caps = true) {
     if (!ix) return fail(LIDER_EINVAL, "lider_search: index is NULL");
     if (nq < 0) return fail(LIDER_EINVAL, "lider_search: nq < 0");
     if (k < 1) return fail(LIDER_EINVAL, "lider_search: k must be >= 1");
@@ -2465,17 +2502,11 @@ int check_search_args(const lider_index* ix, const float* Q, int64_t nq, int k, 
     if (c > LIDER_MAX_C) return fail(LIDER_ELIMIT, "lider_search: c exceeds LIDER_MAX_C");
     const int64_t R = (int64_t)ix->params.r0 * k;
     if (R * ix->g.L > LIDER_MAX_LR) return fail(LIDER_ELIMIT, "lider_search: L * r0 * k exceeds LIDER_MAX_LR");
-    if (nq * c > (int64_t)INT32_MAX) return fail(LIDER_ELIMIT, "lider_search: nq * c exceeds 2^31-1");
     if ((ix->params.score_mode == LIDER_SCORE_BF16 || ix->params.score_mode == LIDER_SCORE_FP8) &&
         (int64_t)ix->params.rerank * k > 4096)
         return fail(LIDER_ELIMIT, "lider_search: rerank * k exceeds 4096");
-    if (ix->params.score_mode != LIDER_SCORE_SIMT && nq * ix->g.H > (int64_t)INT32_MAX)
-        return fail(LIDER_ELIMIT, "lider_search: nq * L * m exceeds 2^31-1; search fewer queries per call");
-    // tensor paths: per pair, a bitmap word and 32 FP32 scores per 32 positions
-    if (ix->params.score_mode != LIDER_SCORE_SIMT && c <= ix->g.ncl &&
-        nq * ix->top_words[c] > ((int64_t)1 << 29))
-        return fail(LIDER_ELIMIT, "lider_search: the per-pair score rows of this batch exceed 64 GiB; search fewer "
-                                  "queries per call");
+    int rc;
+    if (pass_caps && (rc = check_pass_caps(ix, nq, k, c))) return rc;
     if (!buffers) return LIDER_OK;
     if (nq > 0 && (!Q || !ids || !scores)) return fail(LIDER_EINVAL, "lider_search: NULL buffer");
     if (reinterpret_cast<uintptr_t>(Q) % 16 != 0)
@@ -2484,6 +2515,25 @@ int check_search_args(const lider_index* ix, const float* Q, int64_t nq, int k, 
     LIDER_CUDA_TRY(cudaGetDevice(&dev));
     if (dev != ix->device) return fail(LIDER_EINVAL, "lider_search: index lives on another device");
     return LIDER_OK;
+}
+
+// Queries per pass of lider_search: the tuning's probe_batch (0: the whole
+// batch), halved until a pass meets the per-pass caps and its scratch stays
+// within kPassScratchBytes.  The scratch of a pass is sized for the worst case
+// (every query probing the c largest clusters).
+constexpr size_t kPassScratchBytes = (size_t)48 << 30;
+
+int64_t pass_size(const lider_index* ix, int64_t nq, int k, int c) {
+    int64_t pb = ix->tune.probe_batch > 0 ? std::min<int64_t>(nq, ix->tune.probe_batch) : nq;
+    while (pb > 1) {
+        const bool fits = (pb * c <= (int64_t)INT32_MAX) &&
+                          (ix->params.score_mode == LIDER_SCORE_SIMT ||
+                           (pb * ix->g.H <= (int64_t)INT32_MAX && pb * ix->top_words[c] <= ((int64_t)1 << 30))) &&
+                          carve(nullptr, ix->g, pb, c, search_shape(ix, k, pb, c)).total <= kPassScratchBytes;
+        if (fits) break;
+        pb = (pb + 1) / 2;
+    }
+    return std::max<int64_t>(pb, 1);
 }
 
 // Queries that reach the device in chunks (lider_search_host): chunk i holds
@@ -2675,10 +2725,13 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
             mark_words, np);
         LIDER_LAUNCH_CHECK("mark_kernel");
         if ((rc = mark(LIDER_PHASE_SCORE))) return rc;
-        tc_units_kernel<<<g.ncl, 128, 0, st>>>(w.unit_off, w.off, g.cl_off, g.ncl, ix->tune.tile_order, w.units);
+        tc_units_kernel<<<g.ncl, 128, 0, st>>>(w.unit_off, w.off, g.cl_off, w.bm_off, w.pairs, w.qbound, c, g.ncl,
+                                               ix->tune.tile_order, w.units, w.umeta, w.slot_bound);
         LIDER_LAUNCH_CHECK("tc_units_kernel");
         TcArgs ta;
         ta.units = w.units;
+        ta.umeta = w.umeta;
+        ta.slot_bound = w.slot_bound;
         ta.unit_off = w.unit_off;
         ta.off = w.off;
         ta.cnt = w.cnt;
@@ -2820,6 +2873,7 @@ int read_stats(const Workspace& w, int64_t nq, int c, lider_search_stats* stats,
     stats->rmi_oor = (int64_t)h[CNT_OOR];
     stats->rmi_le = (int64_t)h[CNT_LE];
     stats->rmi_oor_le = (int64_t)h[CNT_OOR_LE];
+    stats->passes = 1;
     return LIDER_OK;
 }
 
@@ -2839,19 +2893,77 @@ int pool_alloc(const lider_index* ix, void** p, size_t bytes, cudaStream_t st) {
 
 }  // namespace
 
+// lider_search: the batch in passes of pass_size queries, one after the other
+// on the stream, sharing one workspace (allocated once per call from the
+// index's pool, or as a graph allocation under capture).  With several
+// passes, trace arrays are filled pass by pass; phase events time the first
+// pass's start (events[0]) to the last pass's end, the boundaries between
+// them those of the last pass.
 int search_entry(const lider_index* ix, const float* Q, int64_t nq, int k, int c, int64_t* out_ids,
                  float* out_scores, const lider_trace* tr, lider_search_stats* stats, void* stream) {
-    int rc = check_search_args(ix, Q, nq, k, c, out_ids, out_scores);
+    int rc = check_search_args(ix, Q, nq, k, c, out_ids, out_scores, true, false);
     if (rc) return rc;
     if (stats) *stats = lider_search_stats{};
     if (nq == 0) return LIDER_OK;
+    const int64_t pb = pass_size(ix, nq, k, c);
+    if ((rc = check_pass_caps(ix, pb, k, c))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    Workspace sz = carve(nullptr, ix->g, nq, c, search_shape(ix, k, nq, c));
+    Workspace sz = carve(nullptr, ix->g, pb, c, search_shape(ix, k, pb, c));
     void* mem = nullptr;
     if ((rc = pool_alloc(ix, &mem, sz.total, st))) return rc;
-    Workspace w = carve((unsigned char*)mem, ix->g, nq, c, search_shape(ix, k, nq, c));
-    rc = enqueue_search(ix, Q, nq, k, c, out_ids, out_scores, tr, w, st);
-    if (rc == LIDER_OK && stats) rc = read_stats(w, nq, c, stats, st);
+    const int d = ix->g.d, L = ix->g.L;
+    for (int64_t q0 = 0; q0 < nq && rc == LIDER_OK; q0 += pb) {
+        const int64_t n = std::min(pb, nq - q0);
+        Workspace w = carve((unsigned char*)mem, ix->g, n, c, search_shape(ix, k, n, c));
+        lider_trace t{};
+        const lider_trace* tp = nullptr;
+        if (tr) {
+            auto at = [&](auto* p, int64_t per) { return p ? p + q0 * per : p; };
+            t.route = at(tr->route, c);
+            t.qkeys = at(tr->qkeys, L);
+            t.pstar = at(tr->pstar, (int64_t)c * L);
+            t.wstart = at(tr->wstart, (int64_t)c * L);
+            t.wlen = at(tr->wlen, (int64_t)c * L);
+            t.ucount = at(tr->ucount, c);
+            // phase events: all of them on the last pass, and the first pass's start
+            const bool last = q0 + n >= nq;
+            void* const* ev = tr->events;
+            static thread_local void* ev_first[LIDER_NUM_PHASES + 1];
+            if (ev && !last) {
+                for (int i = 0; i <= LIDER_NUM_PHASES; ++i) ev_first[i] = (q0 == 0 && i == 0) ? ev[0] : nullptr;
+                t.events = ev_first;
+            } else if (ev && q0 > 0) {
+                static thread_local void* ev_last[LIDER_NUM_PHASES + 1];
+                for (int i = 0; i <= LIDER_NUM_PHASES; ++i) ev_last[i] = ev[i];
+                ev_last[0] = nullptr;                         // recorded at the first pass
+                t.events = ev_last;
+            } else {
+                t.events = ev;
+            }
+            tp = &t;
+        }
+        rc = enqueue_search(ix, Q + q0 * d, n, k, c, out_ids + q0 * k, out_scores + q0 * k, tp, w, st);
+        if (rc == LIDER_OK && stats) {
+            lider_search_stats ps{};
+            rc = read_stats(w, n, c, &ps, st);
+            if (rc == LIDER_OK) {
+                stats->n_queries += ps.n_queries;
+                stats->pairs += ps.pairs;
+                stats->candidates += ps.candidates;
+                stats->qkey_boundary += ps.qkey_boundary;
+                stats->qkey_clamped += ps.qkey_clamped;
+                stats->locate_fallback += ps.locate_fallback;
+                stats->empty_pairs += ps.empty_pairs;
+                stats->tc_tiles += ps.tc_tiles;
+                stats->route_fallback += ps.route_fallback;
+                stats->select_overflow += ps.select_overflow;
+                stats->rmi_oor += ps.rmi_oor;
+                stats->rmi_le += ps.rmi_le;
+                stats->rmi_oor_le += ps.rmi_oor_le;
+                stats->passes += ps.passes;
+            }
+        }
+    }
     cudaError_t e = cudaFreeAsync(mem, st);
     if (rc == LIDER_OK && e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync");
     return rc;
@@ -2860,9 +2972,12 @@ int search_entry(const lider_index* ix, const float* Q, int64_t nq, int k, int c
 int search_scratch_entry(const lider_index* ix, int64_t nq, int k, int c, size_t* bytes) {
     if (!bytes) return fail(LIDER_EINVAL, "lider_search_scratch_bytes: bytes is NULL");
     *bytes = 0;
-    int rc = check_search_args(ix, nullptr, nq, k, c, nullptr, nullptr, false);
+    int rc = check_search_args(ix, nullptr, nq, k, c, nullptr, nullptr, false, false);
     if (rc) return rc;
-    if (nq > 0) *bytes = carve(nullptr, ix->g, nq, c, search_shape(ix, k, nq, c)).total;
+    if (nq == 0) return LIDER_OK;
+    const int64_t pb = pass_size(ix, nq, k, c);
+    if ((rc = check_pass_caps(ix, pb, k, c))) return rc;
+    *bytes = carve(nullptr, ix->g, pb, c, search_shape(ix, k, pb, c)).total;
     return LIDER_OK;
 }
 
@@ -2873,7 +2988,7 @@ bool tuning_valid(const lider_tuning& t) {
         return false;
     };
     return in(t.select_threads, {64, 128, 256, 512}) && in(t.rescore_threads, {64, 128, 256, 512}) &&
-           in(t.mark_threads, {32, 64, 128, 256}) && in(t.tile_order, {0, 1});
+           in(t.mark_threads, {32, 64, 128, 256}) && in(t.tile_order, {0, 1}) && t.probe_batch >= 0;
 }
 
 // Coordinate descent over the launch shapes, timing whole searches.
@@ -2925,16 +3040,21 @@ int autotune_entry(lider_index* ix, const float* Q, int64_t nq, int k, int c, in
         cleanup();
         return rc;
     }
+    // probe batches: the whole batch (0: as large as a pass allows) and
+    // passes of a half, a quarter and an eighth of what fits
+    const int64_t pb0 = pass_size(ix, nq, k, c);
+    const int pb_v[] = {0, (int)std::max<int64_t>(1, (pb0 + 1) / 2), (int)std::max<int64_t>(1, (pb0 + 3) / 4),
+                        (int)std::max<int64_t>(1, (pb0 + 7) / 8)};
     static const int sel_v[] = {64, 128, 256, 512}, res_v[] = {64, 128, 256, 512}, mark_v[] = {32, 64, 128, 256},
                      ord_v[] = {0, 1};
     for (int round = 0; round < 2 && rc == LIDER_OK; ++round) {
-        for (int f = 0; f < 4 && rc == LIDER_OK; ++f) {
-            const int* vals = f == 0 ? sel_v : f == 1 ? res_v : f == 2 ? mark_v : ord_v;
+        for (int f = 0; f < 5 && rc == LIDER_OK; ++f) {
+            const int* vals = f == 0 ? sel_v : f == 1 ? res_v : f == 2 ? mark_v : f == 3 ? ord_v : pb_v;
             const int nv = f == 3 ? 2 : 4;
             for (int i = 0; i < nv && rc == LIDER_OK; ++i) {
                 lider_tuning cand = best;
                 int* field = f == 0 ? &cand.select_threads : f == 1 ? &cand.rescore_threads
-                                                           : f == 2 ? &cand.mark_threads : &cand.tile_order;
+                           : f == 2 ? &cand.mark_threads : f == 3 ? &cand.tile_order : &cand.probe_batch;
                 if (*field == vals[i]) continue;
                 *field = vals[i];
                 double t = 0;
@@ -3065,17 +3185,40 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 unsigned char* g_noalloc_base[kMaxDevices] = {};
+void* g_noalloc_ctx[kMaxDevices] = {};         // the context the address belongs to
 
-// Device address of the static scratch on the current device `dev`.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+
+// The current CUDA context (null when the driver entry point is missing).
+void* current_context() {
+    static CtxGetCurrentFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        cudaGetLastError();
+        return (CtxGetCurrentFn)p;
+    }();
+    CUcontext ctx = nullptr;
+    if (fn && fn(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+    return ctx;
+}
+
+// Device address of the static scratch on the current device `dev`, looked up
+// once per (device, context): after a device reset the module is loaded again
+// in a new context and the array can sit at another address.
 int noalloc_scratch(int dev, unsigned char** out) {
     if (dev < 0 || dev >= kMaxDevices) return fail(LIDER_ELIMIT, "lider_search_noalloc: device ordinal too large");
+    void* ctx = current_context();
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_base[dev]) {
+    if (!g_noalloc_base[dev] || g_noalloc_ctx[dev] != ctx) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, lider_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(lider_noalloc_scratch)");
         if (!p) return fail(LIDER_ECUDA, "lider_search_noalloc: scratch symbol has no device address");
         g_noalloc_base[dev] = static_cast<unsigned char*>(p);
+        g_noalloc_ctx[dev] = ctx;
     }
     *out = g_noalloc_base[dev];
     return LIDER_OK;

@@ -64,7 +64,7 @@ class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in
                 ("n_queries", "pairs", "candidates", "qkey_boundary", "qkey_clamped",
                  "locate_fallback", "empty_pairs", "tc_tiles", "route_fallback", "select_overflow",
-                 "rmi_oor", "rmi_le", "rmi_oor_le")]
+                 "rmi_oor", "rmi_le", "rmi_oor_le", "passes")]
 
     def as_dict(self) -> dict:
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
@@ -77,7 +77,7 @@ class Trace(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("select_threads", ctypes.c_int32), ("rescore_threads", ctypes.c_int32),
-                ("mark_threads", ctypes.c_int32), ("tile_order", ctypes.c_int32)]
+                ("mark_threads", ctypes.c_int32), ("tile_order", ctypes.c_int32), ("probe_batch", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {n: int(getattr(self, n)) for n, _ in self._fields_}

@@ -287,3 +287,25 @@ def test_tensor_path_equals_simt_path_exactly(mode, k):
     assert out[mode][2]["select_overflow"] == 0
     assert np.array_equal(out[mode][0], out[1][0])
     assert np.array_equal(out[mode][1].view(np.uint32), out[1][1].view(np.uint32))
+
+
+def test_passes_equal_one_pass(tiny):
+    """A batch searched in passes of probe_batch queries (one lider_search
+    call) returns what one pass returns, trace arrays included, and the
+    counters add up over the passes."""
+    cfg = tiny["cfg"]
+    g = tiny["gidx"]
+    ids1, sc1, st1, tr1 = g.search(tiny["Qd"], cfg["k"], cfg["c"], stats=True, trace=True)
+    before = g.tuning()
+    try:
+        g.set_tuning(probe_batch=300)
+        ids4, sc4, st4, tr4 = g.search(tiny["Qd"], cfg["k"], cfg["c"], stats=True, trace=True)
+    finally:
+        g.set_tuning(**before)
+    assert st1["passes"] == 1 and st4["passes"] == 4
+    assert (ids1 == ids4).all() and (sc1 == sc4).all()
+    for name in tr1:
+        assert (tr1[name] == tr4[name]).all(), name
+    for key in ("candidates", "pairs", "tc_tiles", "qkey_boundary", "locate_fallback"):
+        if key != "tc_tiles":
+            assert st1[key] == st4[key], key

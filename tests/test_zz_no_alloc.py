@@ -28,11 +28,15 @@ def _noalloc(lider, idx, Qd, k, c):
     return rc, ids, sc, st.as_dict()
 
 
-def test_noalloc_matches_search_on_two_calls():
+@pytest.mark.parametrize("mode,rerank", [(0, 0), (1, 0), (2, 4), (4, 4)], ids=["tensor", "simt", "bf16", "fp8"])
+def test_noalloc_matches_search_on_two_calls(mode, rerank):
+    """Every score mode carves its own regions from the shared array (the
+    served forms their shortlists, SIMT its per-pair lists); a second, smaller
+    batch runs over the first call's leftovers."""
     import torch
     from paper_2205_00970_b300 import lider
     cfg, X, Q, C, A, b = F.workload("tiny")
-    idx = F.gpu_index(cfg, X, C, A, b)
+    idx = F.gpu_index(dict(cfg, score_mode=mode, rerank=rerank), X, C, A, b)
     k, c = cfg["k"], cfg["c"]
     batches = [torch.from_numpy(Q).cuda(), torch.from_numpy(Q[500:800]).cuda()]
     for Qd in batches:                       # two calls in a row, different batches
