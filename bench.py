@@ -969,9 +969,11 @@ def run_precision(args, cfg):
     Qd = t(Q)
     out = {}
     C = None                          # k-means runs in the first build; the others reuse its centroids
-    for name in ("f16", "bf16", "fp8"):
+    runs = [("f16", 0)] + [(f"{name}@{rr}", rr) for rr in (args.precision_reranks or [args.rerank])
+                            for name in ("bf16", "fp8")]
+    for name, rr in runs:
         Xd = t(X)
-        idx = build_gpu_index(cfg, Xd, A, b, centroids=C, score_mode=MODES[name], rerank=args.rerank)
+        idx = build_gpu_index(cfg, Xd, A, b, centroids=C, score_mode=MODES[name.split("@")[0]], rerank=max(rr, 1))
         if C is None:
             C = idx.centroids()
         del Xd
@@ -1009,17 +1011,19 @@ def run_precision(args, cfg):
             ex = X[sel].astype(np.float64) @ q64[i]
             got = r["scores"][i][:len(sel)].astype(np.float64)
             err = max(err, float(np.max(np.abs(got - ex) / np.maximum(np.abs(ex), 1e-30))) if len(sel) else 0.0)
+        base, rr = (name.split("@") + ["0"])[:2]
         report[name] = {
             "queries_per_s": nq / (r["ms"] / 1e3), "ms_per_batch": r["ms"], "queries_per_call": r["sub"],
             "storage": {"f16": "FP16 (power-of-two scaled), guarded, exact", "bf16": "BF16",
-                        "fp8": "FP8 e4m3, one scale per row (max|x|/448)"}[name],
+                        "fp8": "FP8 e4m3, one scale per row (max|x|/448)"}[base],
+            "shortlist": "guard band (exact)" if base == "f16" else f"{rr} * k",
             "recall_at_10_vs_plain": float(agree),
             "recall_at_10_vs_fp64_knn": recall10(r["ids"][:ns], truth),
             "max_rel_score_error_vs_fp64": err,
         }
     line = {
         "metric": "recall@10 and score error per dtype; queries/s", "n_gpus": 1, "steps": args.steps,
-        "data": "synthetic", "config": dict(workload_desc(cfg), shortlist=f"{args.rerank} * k"),
+        "data": "synthetic", "config": workload_desc(cfg),
         "sample": f"first {ns} queries against FP64 brute force over the whole corpus", "dtypes": report,
     }
     print(json.dumps(line), flush=True)
@@ -1053,6 +1057,8 @@ def main():
     ap.add_argument("--precision", action="store_true",
                     help="per-dtype recall and score error (f16 exact, bf16 and fp8 served forms)")
     ap.add_argument("--precision-sample", type=int, default=16)
+    ap.add_argument("--precision-reranks", type=int, nargs="+", default=None,
+                    help="--precision: shortlist factors of the served forms (default: --rerank)")
     ap.add_argument("--sweep", action="store_true",
                     help="recall@10 and queries/s over --sweep-W, --sweep-r0 and --sweep-c (FP16 exact mode)")
     ap.add_argument("--sweep-W", type=float, nargs="+", default=[1.0, 2.0])

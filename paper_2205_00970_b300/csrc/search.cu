@@ -1431,19 +1431,21 @@ struct TcSched {
 // (code_score of the smallest candidate code).  Which positions are
 // candidates is read from the pair's bitmap, here and in the select.
 //
-// Epilogue warps of tc_score_kernel: 16 (four per scheduler, so that their
-// TMEM loads, transposes and stores hide one another's latency; each takes 2
-// of the 8 column groups of its TMEM lane quarter) with three stages of K;
-// the 3xTF32 kind's two 96 KB stages leave room for 8 only.
-constexpr int kEpiPitch = 33;                              // padded row of the transpose (32-bit words)
+// Epilogue warps of tc_score_kernel: 12 (three per TMEM lane quarter, taking
+// 3, 3 and 2 of its 8 column groups; with the producer and MMA warps at most
+// four warps per scheduler, which leaves each thread 128 registers), with all
+// of the kind's stages of K.  A warp's transpose stage is 32 rows x 16 words (two codes per
+// word): word j of row r sits at r * 16 + (j ^ (r >> 1)), so the 32 lanes'
+// row writes hit 32 banks, and a row's four aligned 16-byte groups stay
+// aligned (their words permuted inside) for the 16-byte reads.
+constexpr int kEpiWords = 16;
 template <class Kind> struct ScorePlan {
-    static constexpr bool kTf32 = Kind::kOps == 2;
-    static constexpr int kEpiWarps = kTf32 ? 8 : 16;
-    static constexpr int kStages = kTf32 ? 2 : 3;
+    static constexpr int kEpiWarps = 12;
+    static constexpr int kStages = Kind::kStages;
     static constexpr int kThreads = tc::threads_for(kEpiWarps);
     static constexpr int kStageBytes = kStages * Kind::kOps * (tc::kTileA + tc::kTileB) + 1024;
-    static constexpr int kSmem = kStageBytes + kEpiWarps * 32 * kEpiPitch * 4;
-    static_assert(kSmem <= 227 * 1024, "score kernel shared memory");
+    static constexpr int kSmem = kStageBytes + kEpiWarps * 32 * kEpiWords * 4;
+    static_assert(kSmem + 1024 <= 227 * 1024, "score kernel shared memory (with room for the static part)");
 };
 
 // 16-bit code of s in one instruction after the FMA: rint((B - s) * inv),
@@ -1458,7 +1460,7 @@ __device__ __forceinline__ uint32_t score_code_sat(float s, float inv, float bin
 template <int kEpiWarps>
 struct TcEpi {
     const TcArgs* a;
-    uint32_t* stage;            // this warp's 32 x kEpiPitch words
+    uint32_t* stage;            // this warp's 32 x kEpiWords words (packed code pairs, swizzled)
     uint16_t* drow;             // this lane's dense row at the tile's first column (null: no pair)
     float B, inv, binv, step;   // this row's code range: bound, 65535 / 2B, B * inv, 2B / 65535
     int ncols;                  // columns of the tile inside the row pitch (a multiple of 32)
@@ -1487,8 +1489,9 @@ struct TcEpi {
         binv = __fmul_rn(B, inv);
         step = code_step(B);
         crow = live ? a->cmax + wt : nullptr;
-        // this warp's column groups of the tile (kEpiWarps / 4 warps share each row)
-        constexpr int kGpw = (tc::kBN / 32) / (kEpiWarps / 4);
+        // this warp's column groups of the tile (kEpiWarps / 4 warps share each row;
+        // the same split as the engine's)
+        constexpr int kGpw = ((tc::kBN / 32) + kEpiWarps / 4 - 1) / (kEpiWarps / 4);
         const int g0 = ((((int)threadIdx.x >> 5) - 2) >> 2) * kGpw;
 #pragma unroll
         for (int w = 0; w < tc::kBN / 32; ++w)
@@ -1513,27 +1516,40 @@ struct TcEpi {
         // candidate's score
         const int lane = threadIdx.x & 31;
         float m = -INFINITY;
+        const int swz = lane >> 1;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            float x = __uint_as_float(v[i]);
-            if (cs) x = x * rs * (col0 + i < ncs ? __ldg(cs + col0 + i) : 0.f);
-            stage[lane * kEpiPitch + i] = score_code_sat(x, inv, binv);
-            m = fmaxf(m, ((w >> i) & 1u) ? x : -INFINITY);
+        for (int i = 0; i < 32; i += 2) {
+            float x0 = __uint_as_float(v[i]), x1 = __uint_as_float(v[i + 1]);
+            if (cs) {
+                x0 = x0 * rs * (col0 + i < ncs ? __ldg(cs + col0 + i) : 0.f);
+                x1 = x1 * rs * (col0 + i + 1 < ncs ? __ldg(cs + col0 + i + 1) : 0.f);
+            }
+            stage[lane * kEpiWords + ((i >> 1) ^ swz)] =
+                __byte_perm(score_code_sat(x0, inv, binv), score_code_sat(x1, inv, binv), 0x5410);
+            m = fmaxf(m, ((w >> i) & 1u) ? x0 : -INFINITY);
+            m = fmaxf(m, ((w >> (i + 1)) & 1u) ? x1 : -INFINITY);
         }
         if (crow) crow[col0 >> 5] = m > -INFINITY ? code_score(score_code_sat(m, inv, binv), B, step) : -INFINITY;
         __syncwarp();
-        const int sub = lane >> 2, c8 = (lane & 3) * 8;
+        // lane: row rr + lane / 4, 16-byte group lane % 4 (8 codes) of it
+        const int sub = lane >> 2, cg = lane & 3;
 #pragma unroll
         for (int rr = 0; rr < 32; rr += 8) {
             const int r = rr + sub;
             uint16_t* dst = reinterpret_cast<uint16_t*>(
                 __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(drow), r));
-            if (dst) {
-                const uint32_t* sr = stage + r * kEpiPitch + c8;
-                *reinterpret_cast<uint4*>(dst + col0 + c8) =
-                    make_uint4(__byte_perm(sr[0], sr[1], 0x5410), __byte_perm(sr[2], sr[3], 0x5410),
-                               __byte_perm(sr[4], sr[5], 0x5410), __byte_perm(sr[6], sr[7], 0x5410));
+            const int rs2 = r >> 1;
+            uint4 q = reinterpret_cast<const uint4*>(stage + r * kEpiWords)[cg ^ (rs2 >> 2)];
+            // logical word e of the group is physical word e ^ (rs2 & 3): undo the XOR by two swaps
+            if (rs2 & 1) {
+                const uint32_t t0 = q.x, t2 = q.z;
+                q.x = q.y; q.y = t0; q.z = q.w; q.w = t2;
             }
+            if (rs2 & 2) {
+                const uint32_t t0 = q.x, t1 = q.y;
+                q.x = q.z; q.y = q.w; q.z = t0; q.w = t1;
+            }
+            if (dst) *reinterpret_cast<uint4*>(dst + col0 + cg * 8) = q;
         }
         __syncwarp();
     }
@@ -1556,7 +1572,7 @@ __global__ void __launch_bounds__(ScorePlan<Kind>::kThreads, 1)
     unsigned char* aligned = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem) + 1023) &
                                                               ~(uintptr_t)1023);
     epi.stage = reinterpret_cast<uint32_t*>(aligned + (Plan::kStageBytes - 1024)) +
-                (size_t)(threadIdx.x >= 64 ? (threadIdx.x >> 5) - 2 : 0) * 32 * kEpiPitch;
+                (size_t)(threadIdx.x >= 64 ? (threadIdx.x >> 5) - 2 : 0) * 32 * kEpiWords;
     tc::gemm_tiles<Kind, TcSched, TcEpi<Plan::kEpiWarps>, Plan::kEpiWarps, Plan::kStages>(
         &mAhi, &mAlo, &mBhi, &mBlo, kchunks, sched, epi, err, smem, ctl);
 }

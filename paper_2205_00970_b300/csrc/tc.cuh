@@ -230,10 +230,6 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
     return d;
 }
 
-// Named barrier of the four epilogue warps (barrier 0 is __syncthreads).
-template <int kEpiWarps>
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory"); }
-
 // Shared state of one block.
 struct Ctl {
     uint64_t full[kMaxStages];
@@ -242,7 +238,6 @@ struct Ctl {
     uint64_t tempty[2];
     uint32_t tmem_base;
     int abort;
-    int epi_bad;        // an epilogue warp's wait failed (read only after epi_sync)
 };
 
 // Test hook of the bounded waits (engine self-test only): every wait gives up
@@ -261,8 +256,8 @@ struct WaitTest {
 // waited for (it must not read TMEM; its loads overlap the tile's MMAs),
 // void operator()(int u, int row, int col0, const uint32_t (&v)[32]) for
 // columns col0..col0+31, and void done(int u, int row) after the last group.
-// The epilogue warps leave their loop only together, so their named barriers
-// cannot be left waiting.
+// Each epilogue warp leaves its loop as a whole warp (Epi must not use
+// barriers across warps); the warps of a tile need not run in step.
 // mA0/mB0: the operands (KindTf32x3: their TF32 heads); mA1/mB1: the tails
 // (KindTf32x3 only; ignored otherwise).  kchunks = ceil(d / Kind::kBK).
 // kStagesUse: shared-memory stages of K (at most Kind::kStages, the plan the
@@ -294,7 +289,6 @@ __device__ void gemm_tiles(const CUtensorMap* mAhi, const CUtensorMap* mAlo, con
             mbar_init(&ctl.tempty[b], kEpiWarps);
         }
         ctl.abort = 0;
-        ctl.epi_bad = 0;
         fence_mbar_init();
     }
     if (warp == 0) {
@@ -386,11 +380,12 @@ __device__ void gemm_tiles(const CUtensorMap* mAhi, const CUtensorMap* mAlo, con
             }
         }
     } else {                                                     // epilogue warps 2..
-        // warp w reads TMEM lanes 32 (w % 4) ..; with 8 (16) epilogue warps
-        // two (four) of them share those lanes and take 4 (2) of the 8
-        // column groups each
-        static_assert(kEpiWarps == 4 || kEpiWarps == 8 || kEpiWarps == 16, "4, 8 or 16 epilogue warps");
-        constexpr int kGroups = (kBN / 32) / (kEpiWarps / 4);
+        // warp w reads TMEM lanes 32 (w % 4) ..; with more than 4 epilogue
+        // warps, kEpiWarps / 4 of them share those lanes and split the 8
+        // column groups (contiguous runs of kGroups, the last run shorter)
+        static_assert(kEpiWarps % 4 == 0 && kEpiWarps >= 4 && kEpiWarps <= 32, "a multiple of 4 epilogue warps");
+        constexpr int kWpq = kEpiWarps / 4;
+        constexpr int kGroups = ((kBN / 32) + kWpq - 1) / kWpq;
         const int quarter = warp & 3;
         const int cb0 = ((warp - 2) >> 2) * kGroups;
         const int row = quarter * 32 + lane;
@@ -399,18 +394,20 @@ __device__ void gemm_tiles(const CUtensorMap* mAhi, const CUtensorMap* mAlo, con
             const int ab = ui & 1;
             const uint32_t aph = (uint32_t)(ui >> 1) & 1u;
             epi.begin(u, row);
-            const bool ok = mbar_wait(&ctl.tfull[ab], aph, abort_flag, tmo);
-            if (!ok && lane == 0) {
-                fail(TC_TIMEOUT_TFULL);
-                atomicOr(&ctl.epi_bad, 1);
+            // the warp leaves as one (a timed-out wait on any lane), so its
+            // .sync.aligned TMEM loads never see a partial warp; the other
+            // warps' waits end by the abort flag or their own limit
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&ctl.tfull[ab], aph, abort_flag, tmo));
+            if (!ok) {
+                if (lane == 0) fail(TC_TIMEOUT_TFULL);
+                break;
             }
-            epi_sync<kEpiWarps>();                       // every epilogue warp arrives
-            if (*(volatile int*)&ctl.epi_bad) break;     // same decision in all of them
             tc_fence_after();
             const uint32_t base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * kBN);
 #pragma unroll
             for (int g = 0; g < kGroups; ++g) {
                 const int cb = cb0 + g;
+                if (cb >= kBN / 32) break;               // the same in every lane
                 uint32_t v[32];
                 tmem_ld32(base + (uint32_t)(cb * 32), v);
                 epi(u, row, cb * 32, v);
