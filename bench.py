@@ -46,8 +46,8 @@ DTYPES = {"tensor": "f32", "simt": "f32", "bf16": "bf16", "f16": "f16", "fp8": "
 FP8_PER_BF16 = 4.5 / 2.25     # nominal dense FP8 / BF16 tensor rate (B300)
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one warm tc_score_kernel<KindF16>
 # launch on the full mid workload, per tile (None: no capture of the current kernel)
-F16_TC_DRAM_BYTES_PER_TILE = (1731677184 + 2064019200) / 18211
-F16_TC_DRAM_NOTE = "ncu DRAM bytes of one full-size mid launch (18,211 tiles), per tile, times this launch's tiles"
+F16_TC_DRAM_BYTES_PER_TILE = (1739497472 + 1207282432) / 20234
+F16_TC_DRAM_NOTE = "ncu DRAM bytes of one full-size mid launch (20,234 tiles), per tile, times this launch's tiles"
 
 
 def workload_desc(cfg) -> dict:
@@ -545,6 +545,9 @@ def run_lider(args, cfg):
         # untimed run of the same passes, one call per pass
         pb = -(-nq // (passes // len(chunks)))
         pev = [[torch.cuda.Event(enable_timing=True) for _ in range(nph)] for _ in range(0, nq, pb)]
+        for row in pev:
+            for e in row:
+                e.record()          # creates the event, so the library gets a handle to record
         for pi, lo in enumerate(range(0, nq, pb)):
             idx.search_phased(Qd[lo:lo + pb], k, c, pev[pi], out=(ids[lo:lo + pb], sc[lo:lo + pb]))
         torch.cuda.synchronize()

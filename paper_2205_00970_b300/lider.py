@@ -324,7 +324,10 @@ class Index:
         ids, sc = out if out is not None else (
             torch.empty((nq, k), dtype=torch.int64, device=Q.device),
             torch.empty((nq, k), dtype=torch.float32, device=Q.device))
-        arr = (ctypes.c_void_p * (NUM_PHASES + 1))(*[e.cuda_event for e in events])
+        handles = [e.cuda_event for e in events]
+        if len(handles) != NUM_PHASES + 1 or not all(handles):
+            raise ValueError(f"search_phased needs {NUM_PHASES + 1} created events (record each once first)")
+        arr = (ctypes.c_void_p * (NUM_PHASES + 1))(*handles)
         tr = Trace(None, None, None, None, None, None, ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)))
         _check(_lib.lider_search_trace(self._h, Q.data_ptr(), nq, k, c, ids.data_ptr(), sc.data_ptr(),
                                        ctypes.byref(tr), None, _stream_ptr(stream)))
