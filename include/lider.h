@@ -295,7 +295,12 @@ int lider_search_trace(const lider_index* index, const float* queries, int64_t n
 /* End-to-end form of lider_search on HOST buffers: copies queries (host,
  * nq x d FP32; pinned memory gives asynchronous copies) to the device,
  * searches, copies ids/scores back into host arrays of nq x k, and
- * synchronises `stream` before returning.  Same arguments and errors. */
+ * synchronises `stream` before returning.  Same arguments, errors and passes
+ * as lider_search; the copies of each pass's queries run on a second stream
+ * in up to four chunks, each chunk's hash and route starting when it lands.
+ * Result arrays in pinned, mapped host memory are written by the search
+ * itself (no copy back).  Device memory: the whole batch's queries (and,
+ * unless the results are mapped, its results) plus one pass's scratch. */
 int lider_search_host(const lider_index* index, const float* queries_host, int64_t nq,
                       int32_t k, int32_t c, int64_t* ids_host, float* scores_host,
                       lider_search_stats* stats, void* stream);

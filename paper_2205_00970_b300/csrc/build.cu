@@ -402,8 +402,8 @@ int dev_alloc(void** p, size_t bytes, const char* what) {
 void release(lider_index* ix) {
     if (!ix) return;
     void* bufs[] = {ix->X, ix->orig_id, ix->cl_off, ix->C, ix->half_norm, ix->A, ix->bproj,
-                    ix->keys, ix->pos, ix->root, ix->leaf, ix->X_hi, ix->X_lo, ix->row_of, ix->X_h16, ix->C_hi, ix->C_lo,
-                    ix->A_hi, ix->A_lo, ix->a_norm, ix->X_f8, ix->x_rowscale, ix->ckeys, ix->cpos, ix->croot,
+                    ix->keys, ix->pos, ix->root, ix->leaf, ix->X_hi, ix->X_lo, ix->row_of, ix->X_h16, ix->F_hi, ix->F_lo,
+                    ix->a_norm, ix->X_f8, ix->x_rowscale, ix->ckeys, ix->cpos, ix->croot,
                     ix->cleaf};
     for (void* p : bufs)
         if (p) cudaFree(p);
@@ -578,19 +578,23 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
     }
     half_norm_kernel<<<(unsigned)cdiv(ncl, 128), 128, 0, st>>>(ix->C, ncl, d, ix->half_norm);
     LIDER_LAUNCH_CHECK("half_norm_kernel");
-    if (P->score_mode != LIDER_SCORE_SIMT) {      // tensor-core routing
-        ALLOC(ix->C_hi, (size_t)ncl * d * sizeof(float), "centroid TF32 head");
-        ALLOC(ix->C_lo, (size_t)ncl * d * sizeof(float), "centroid TF32 tail");
-        if ((rc = launch_split_tf32(ix->C, (int64_t)ncl * d, ix->C_hi, ix->C_lo, st))) return rc;
-        if ((rc = make_tensor_map(&ix->map_chi, ix->C_hi, ncl, d, 256))) return rc;
-        if ((rc = make_tensor_map(&ix->map_clo, ix->C_lo, ncl, d, 256))) return rc;
-        // tensor-core hashing: projections split like the centroids
-        ALLOC(ix->A_hi, (size_t)H * d * sizeof(float), "projection TF32 head");
-        ALLOC(ix->A_lo, (size_t)H * d * sizeof(float), "projection TF32 tail");
+    if (P->score_mode != LIDER_SCORE_SIMT) {      // tensor-core hashing and routing
+        // one front operand: the projections, zero rows up to a 256-row
+        // boundary, then the centroids, each split into TF32 head and tail
+        const int hp = (int)cdiv(H, 256) * 256;
+        const int64_t frows = (int64_t)hp + ncl;
+        ALLOC(ix->F_hi, (size_t)frows * d * sizeof(float), "front operand TF32 head");
+        ALLOC(ix->F_lo, (size_t)frows * d * sizeof(float), "front operand TF32 tail");
+        ix->front_hp = hp;
+        LIDER_CUDA_TRY(cudaMemsetAsync(ix->F_hi, 0, (size_t)hp * d * sizeof(float), st));
+        LIDER_CUDA_TRY(cudaMemsetAsync(ix->F_lo, 0, (size_t)hp * d * sizeof(float), st));
+        if ((rc = launch_split_tf32(ix->A, (int64_t)H * d, ix->F_hi, ix->F_lo, st))) return rc;
+        if ((rc = launch_split_tf32(ix->C, (int64_t)ncl * d, ix->F_hi + (int64_t)hp * d, ix->F_lo + (int64_t)hp * d,
+                                    st)))
+            return rc;
+        if ((rc = make_tensor_map(&ix->map_fhi, ix->F_hi, frows, d, 256))) return rc;
+        if ((rc = make_tensor_map(&ix->map_flo, ix->F_lo, frows, d, 256))) return rc;
         ALLOC(ix->a_norm, (size_t)H * sizeof(float), "projection norms");
-        if ((rc = launch_split_tf32(ix->A, (int64_t)H * d, ix->A_hi, ix->A_lo, st))) return rc;
-        if ((rc = make_tensor_map(&ix->map_ahi, ix->A_hi, H, d, 256))) return rc;
-        if ((rc = make_tensor_map(&ix->map_alo, ix->A_lo, H, d, 256))) return rc;
         row_norms_kernel<<<(unsigned)cdiv((int64_t)H * 32, 256), 256, 0, st>>>(ix->A, H, d, ix->a_norm);
         LIDER_LAUNCH_CHECK("row_norms_kernel");
         std::vector<double> hn(ncl);

@@ -93,20 +93,20 @@ struct lider_index {
     float* X_lo = nullptr;
     int32_t* row_of = nullptr;
     uint16_t* X_h16 = nullptr;  // BF16 copy (served form) or FP16 copy of x_scale * X
-    float* A_hi = nullptr;      // projections, TF32 head / tail (tensor-core hashing)
-    float* A_lo = nullptr;
+    // front operand of the tensor modes, TF32 head / tail: projections in rows
+    // [0, H), zero rows up to front_hp (H rounded up to 256), centroids in rows
+    // [front_hp, front_hp + n_clusters)
+    float* F_hi = nullptr;
+    float* F_lo = nullptr;
+    int front_hp = 0;
+    CUtensorMap map_fhi;        // TMA maps over F_hi / F_lo, boxes of 32 x 256
+    CUtensorMap map_flo;
     float* a_norm = nullptr;    // |a_h| per projection (rounded up)
-    CUtensorMap map_ahi;        // TMA maps over A_hi / A_lo, boxes of 32 x 256
-    CUtensorMap map_alo;
-    float* C_hi = nullptr;      // centroids, TF32 head / tail (tensor-core routing)
-    float* C_lo = nullptr;
     float max_cnorm = 0.f;      // largest centroid norm (routing error guard)
     float max_xnorm = 0.f;      // largest corpus row norm (candidate error guard)
     float x_scale = 1.f;        // FP16 mode: power of two applied to X before rounding
     float xres_max = 0.f;       // FP16 mode: max over rows of |fp16(x_scale x) - x_scale x| (rounded up)
     float xhat_max = 0.f;       // FP16 mode: max over rows of |fp16(x_scale x)| (rounded up)
-    CUtensorMap map_chi;        // TMA maps over C_hi / C_lo, boxes of 32 x 256
-    CUtensorMap map_clo;
     CUtensorMap map_xh16;       // TMA map over X_h16, boxes of 64 x 256
     uint8_t* X_f8 = nullptr;    // FP8 e4m3 copy of X, one scale per row (served FP8 form)
     float* x_rowscale = nullptr;

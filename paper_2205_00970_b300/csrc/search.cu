@@ -2,16 +2,16 @@
 //
 // Steps and kernels, in order, for nq queries probing c clusters each
 // (tensor score modes; SIMT mode in brackets):
-//   1. hash     split_tf32 + qnorm_kernel + hash_tc_kernel (3xTF32 tiles of
-//               queries x projections) + hash_recheck_kernel (values near a
-//               bucket edge recomputed exactly) + pack_kernel: packed query
-//               hashkeys for the L arrays, p-stable or hyperplane (Sec. 4.1,
-//               4.2) [dot2_tile_kernel<hash> + pack_kernel]
-//   2. route    route_tc_kernel (3xTF32 tiles of queries x centroids) +
-//               topc_exact_kernel: the c best centroids by x.mu - |mu|^2/2,
+//   1. hash     split_tf32 + qnorm_kernel + front_tc_kernel (3xTF32 tiles of
+//               queries x [projections; centroids]: the hash values and the
+//               routing scores in one launch) [dot2_tile_kernel<hash>]
+//   2. route    topc_exact_kernel: the c best centroids by x.mu - |mu|^2/2,
 //               ties -> lower index, exact despite approximate scores
 //               [dot2_tile_kernel<score> + topc_kernel]; with the Layer-1
-//               centroids retriever, route_core_kernel then routes instead
+//               centroids retriever, route_core_kernel then routes instead;
+//               hash_recheck_kernel (hash values near a bucket edge
+//               recomputed exactly) + pack_kernel: packed query hashkeys for
+//               the L arrays, p-stable or hyperplane (Sec. 4.1, 4.2)
 //   3. group    group_*_kernel: (query, probe) pairs bucketed by cluster;
 //               primary_order_kernel: queries grouped by best cluster (the
 //               re-score's order)
@@ -135,6 +135,9 @@ __global__ void topc_kernel(const double* __restrict__ S, int64_t nq, int ncl, i
 // error guard of the c-th exact score, every centroid of that query is scored
 // exactly instead.
 constexpr int kRouteExtra = 8;
+// topc_exact_kernel stages a query's routing scores in shared memory when the
+// row has at most this many centroids (8 warps x 4 KB per block)
+constexpr int kTopcStageCols = 1024;
 // Bound on the error of one 3xTF32 tensor-core score, relative to |q| |x|
 // (the product of the two norms).  The dropped lo*lo term and the TF32
 // rounding of the tails contribute about 3 * 2^-22 of sum |q_i x_i| <= |q| |x|;
@@ -143,66 +146,37 @@ constexpr int kRouteExtra = 8;
 // route and candidate guards use it.
 constexpr float kTcGuard = 3e-5f;
 
-struct RouteSched {
-    int nq, ncl;
-    __device__ int count() const { return ((nq + 127) / 128) * ((ncl + 255) / 256); }
+// ----------------------------------------------------------- hash + route --
+// Both the hash values t = (a_h . q + b_h) / W and the routing scores
+// q.mu - |mu|^2/2 are contractions of the queries with a fixed matrix, so one
+// launch of the tcgen05 engine (three TF32 products per FP32 product) runs
+// them together over the front operand F: rows [0, H) are the projections,
+// rows [Hp, Hp + ncl) the centroids (Hp = H rounded up to 256; the rows
+// between are zero), and every 256-row tile of F is either a hash tile or a
+// route tile.  The tiles of one query tile are adjacent in the schedule, so
+// its queries are read from L2 by the CTAs that share them.
+//
+// Hash tiles: where floor(t) could depend on the tile's error (t within its
+// bound, or within 1e-6 for the boundary count, of an integer; of zero for
+// hyperplane hashes, whose b is 0 and W 1) the (query, projection) goes to a
+// list, and hash_recheck_kernel recomputes t with exactly the arithmetic of
+// the SIMT hashing kernel (sequential Dot2 over k, finished in FP64), so the
+// query keys are the same bit for bit on every score path.
+// Route tiles: approximate scores for topc_exact_kernel.
+struct FrontSched {
+    int nq;
+    int nth, ntr;               // hash tiles (Hp / 256) and route tiles per query tile
+    int Hp;
+    __device__ int count() const { return ((nq + 127) / 128) * (nth + ntr); }
     __device__ void coords(int u, int& arow, int& brow) const {
-        const int nct = (ncl + 255) / 256;
-        arow = (u / nct) * 128;
-        brow = (u % nct) * 256;
+        const int nt = nth + ntr, t = u % nt;
+        arow = (u / nt) * 128;
+        brow = t < nth ? t * 256 : Hp + (t - nth) * 256;
     }
 };
 
-struct RouteEpi {
-    float* S;                   // nq x ncl approximate scores
-    const double* half_norm;
-    int nq, ncl;
-    int q, c0;
-    __device__ void begin(int u, int row) {
-        const int nct = (ncl + 255) / 256;
-        q = (u / nct) * 128 + row;
-        c0 = (u % nct) * 256;
-    }
-    __device__ void operator()(int, int, int col0, const uint32_t (&v)[32]) {
-        if (q >= nq) return;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            const int j = c0 + col0 + i;
-            if (j < ncl) S[(int64_t)q * ncl + j] = __uint_as_float(v[i]) - (float)half_norm[j];
-        }
-    }
-    __device__ void done(int, int) {}
-};
-
-__global__ void __launch_bounds__(tc::kThreads, 1)
-    route_tc_kernel(const __grid_constant__ CUtensorMap mQhi, const __grid_constant__ CUtensorMap mQlo,
-                    const __grid_constant__ CUtensorMap mChi, const __grid_constant__ CUtensorMap mClo, int kchunks,
-                    RouteSched sched, RouteEpi epi, int* err) {
-    extern __shared__ unsigned char smem[];
-    __shared__ tc::Ctl ctl;
-    tc::gemm_tiles<tc::KindTf32x3>(&mQhi, &mQlo, &mChi, &mClo, kchunks, sched, epi, err, smem, ctl);
-}
-
-// ------------------------------------------------------------------- hash --
-// Tensor paths: t = (a_h . q + b_h) / W for all queries and projections as
-// 3xTF32 tiles (queries x projections).  Where floor(t) could depend on the
-// tile's error (t within its bound, or within 1e-6 for the boundary count, of
-// an integer; of zero for hyperplane hashes, whose b is 0 and W 1) the
-// (query, projection) goes to a list, and hash_recheck_kernel
-// recomputes t with exactly the arithmetic of the SIMT hashing kernel
-// (sequential Dot2 over k, finished in FP64), so the query keys are the same
-// bit for bit on every score path.
-struct HashSched {
-    int nq, H;
-    __device__ int count() const { return ((nq + 127) / 128) * ((H + 255) / 256); }
-    __device__ void coords(int u, int& arow, int& brow) const {
-        const int nht = (H + 255) / 256;
-        arow = (u / nht) * 128;
-        brow = (u % nht) * 256;
-    }
-};
-
-struct HashEpi {
+struct FrontEpi {
+    // hash tiles
     double* t;                  // nq x H
     const float* b;             // offsets b_h
     const float* a_norm;        // |a_h|
@@ -210,44 +184,60 @@ struct HashEpi {
     int32_t* recheck;           // ((q0 + q) * H + h) of the undecided values
     int32_t* n_recheck;
     float W, guard;             // guard: kTcGuard
-    int nq, H;
+    int H;
     int q0;                     // index of this launch's first query in the whole batch
     bool hyper;                 // hyperplane hashes: only the sign of t decides
-    int q, h0;
+    // route tiles
+    float* S;                   // nq x ncl approximate scores
+    const double* half_norm;
+    int ncl;
+    int nq, nth, ntr;
+    // this tile and row
+    int q, n0;
+    bool hash;
     float qn;
     __device__ void begin(int u, int row) {
-        const int nht = (H + 255) / 256;
-        q = (u / nht) * 128 + row;
-        h0 = (u % nht) * 256;
-        qn = q < nq ? qnorm[q] : 0.f;
+        const int nt = nth + ntr, tt = u % nt;
+        q = (u / nt) * 128 + row;
+        hash = tt < nth;
+        n0 = (hash ? tt : tt - nth) * 256;
+        qn = (hash && q < nq) ? qnorm[q] : 0.f;
     }
     __device__ void operator()(int, int, int col0, const uint32_t (&v)[32]) {
         if (q >= nq) return;
+        if (hash) {
 #pragma unroll 4
-        for (int i = 0; i < 32; ++i) {
-            const int h = h0 + col0 + i;
-            if (h >= H) break;
-            const float acc = __uint_as_float(v[i]);
-            const float bh = b[h];
-            const float tf = __fdiv_rn(__fadd_rn(acc, bh), W);
-            // |tf - t| <= (tile error + FP32 rounding of acc + b) / W + rounding of the division
-            const float eps = __fdiv_rn(guard * qn * a_norm[h] + 4.f * 0x1p-24f * (fabsf(acc) + fabsf(bh)), W) +
-                              0x1p-22f * fabsf(tf);
-            const float dist = hyper ? fabsf(tf) : fabsf(tf - rintf(tf));
-            t[(int64_t)q * H + h] = (double)tf;
-            if (!(dist > 1.01f * eps + 1.1e-6f)) recheck[atomicAdd(n_recheck, 1)] = (q0 + q) * H + h;
+            for (int i = 0; i < 32; ++i) {
+                const int h = n0 + col0 + i;
+                if (h >= H) break;
+                const float acc = __uint_as_float(v[i]);
+                const float bh = b[h];
+                const float tf = __fdiv_rn(__fadd_rn(acc, bh), W);
+                // |tf - t| <= (tile error + FP32 rounding of acc + b) / W + rounding of the division
+                const float eps = __fdiv_rn(guard * qn * a_norm[h] + 4.f * 0x1p-24f * (fabsf(acc) + fabsf(bh)), W) +
+                                  0x1p-22f * fabsf(tf);
+                const float dist = hyper ? fabsf(tf) : fabsf(tf - rintf(tf));
+                t[(int64_t)q * H + h] = (double)tf;
+                if (!(dist > 1.01f * eps + 1.1e-6f)) recheck[atomicAdd(n_recheck, 1)] = (q0 + q) * H + h;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const int j = n0 + col0 + i;
+                if (j < ncl) S[(int64_t)q * ncl + j] = __uint_as_float(v[i]) - (float)half_norm[j];
+            }
         }
     }
     __device__ void done(int, int) {}
 };
 
 __global__ void __launch_bounds__(tc::kThreads, 1)
-    hash_tc_kernel(const __grid_constant__ CUtensorMap mQhi, const __grid_constant__ CUtensorMap mQlo,
-                   const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo, int kchunks,
-                   HashSched sched, HashEpi epi, int* err) {
+    front_tc_kernel(const __grid_constant__ CUtensorMap mQhi, const __grid_constant__ CUtensorMap mQlo,
+                    const __grid_constant__ CUtensorMap mFhi, const __grid_constant__ CUtensorMap mFlo, int kchunks,
+                    FrontSched sched, FrontEpi epi, int* err) {
     extern __shared__ unsigned char smem[];
     __shared__ tc::Ctl ctl;
-    tc::gemm_tiles<tc::KindTf32x3>(&mQhi, &mQlo, &mAhi, &mAlo, kchunks, sched, epi, err, smem, ctl);
+    tc::gemm_tiles<tc::KindTf32x3>(&mQhi, &mQlo, &mFhi, &mFlo, kchunks, sched, epi, err, smem, ctl);
 }
 
 // t of the listed (query, projection) values, with the SIMT hashing kernel's
@@ -333,6 +323,33 @@ __device__ __forceinline__ double warp_exact_score(const float* __restrict__ q, 
     return __dadd_rn(dot2_value(acc), -half_norm);
 }
 
+// warp_exact_score of four centroids at once (the same arithmetic per
+// centroid, so the same values; their loads overlap).  Centroid t is
+// C + rows[t] * d.
+__device__ __forceinline__ void warp_exact_scores4(const float* __restrict__ q, const float* __restrict__ C,
+                                                   const int (&rows)[4], int d, const double* __restrict__ half_norm,
+                                                   double (&out)[4]) {
+    const int lane = threadIdx.x & 31;
+    Dot2 acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    const float* mu[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) mu[t] = C + (int64_t)rows[t] * d;
+#pragma unroll 2
+    for (int i = lane; i < d; i += 32) {
+        const float qi = __ldg(q + i);
+        float m[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) m[t] = __ldg(mu[t] + i);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) dot2_step(acc[t], qi, m[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        warp_merge_dot2(acc[t]);
+        out[t] = __dadd_rn(dot2_value(acc[t]), -half_norm[rows[t]]);
+    }
+}
+
 // Guard formula of a score mode (see candidate_guard).
 inline int guard_mode(int score_mode) {
     return score_mode == LIDER_SCORE_TENSOR ? 1 : score_mode == LIDER_SCORE_F16 ? 2
@@ -341,12 +358,12 @@ inline int guard_mode(int score_mode) {
 
 // Power of two sq with sq * amax in [2^13, 2^14) (1 for amax == 0): the
 // FP16 path's query scale.
-__device__ __forceinline__ double f16_query_scale(float amax) {
-    if (!(amax > 0.f) || !(amax <= 3.0e38f)) return 1.0;
+__device__ __forceinline__ float f16_query_scale(float amax) {
+    if (!(amax > 0.f) || !(amax <= 3.0e38f)) return 1.f;
     int e = 0;
     frexpf(amax, &e);
     e = max(-100, min(e, 127));
-    return ldexp(1.0, 14 - e);
+    return ldexpf(1.f, 14 - e);
 }
 
 // Per-query scale and error bound of the approximate candidate scores.
@@ -361,29 +378,33 @@ __device__ __forceinline__ double f16_query_scale(float amax) {
 // with an error below d 2^-23 of their absolute sum <= (sq |q| + eq) |x^|max.
 // gmode 0 (served BF16 form): no guard.  qbound bounds |approximate score|
 // (it sets the select histogram's range).
-__device__ void candidate_guard(int gmode, float qn, double sq, double eq, int d, float xmax, float sx,
+// FP32 throughout, every rounding upward (products by powers of two are
+// exact), so each result bounds its exact expression from above; this GPU's
+// FP64 rate is a small fraction of its FP32 rate.
+__device__ void candidate_guard(int gmode, float qn, float sq, float eq, int d, float xmax, float sx,
                                 float xres, float xhat, float* qscale, float* qguard, float* qbound) {
-    const double q = (double)qn * (1.0 + 1e-5);
-    double g = 0.0, s = 1.0;
+    const float q = __fmul_ru(qn, 1.00001f);
+    float g = 0.f, s = 1.f;
     if (gmode == 1) {
-        g = (double)kTcGuard * q * (double)xmax;
+        g = __fmul_ru(__fmul_ru(kTcGuard, q), xmax);
     } else if (gmode == 0) {
-        g = 0x1p-6 * q * (double)xmax;        // BF16: only bounds the scores below
+        g = __fmul_ru(0x1p-6f * q, xmax);              // BF16: only bounds the scores below
     } else if (gmode == 3) {
-        g = 0.3 * q * (double)xmax;           // FP8: only bounds the scores below
+        g = __fmul_ru(__fmul_ru(0.3f, q), xmax);       // FP8: only bounds the scores below
     } else if (gmode == 2) {
-        const double acc = (double)d * 0x1p-23;
-        const double qs = sq * q;
-        g = eq * (double)xhat + qs * (double)xres + acc * (qs + eq) * (double)xhat;
-        s = sq * (double)sx;
+        const float acc = (float)d * 0x1p-23f;
+        const float qs = sq * q;
+        g = __fadd_ru(__fadd_ru(__fmul_ru(eq, xhat), __fmul_ru(qs, xres)),
+                      __fmul_ru(__fmul_ru(acc, __fadd_ru(qs, eq)), xhat));
+        s = sq * sx;
     }
     // |approximate score| <= s |q| |x|max + its error (s = 1 unless FP16)
-    const float B = __double2float_ru((s * q * (double)xmax + g) * (1.0 + 0x1p-20));
-    *qscale = (float)(gmode == 2 ? sq : 1.0);
+    const float B = __fmul_ru(__fadd_ru(__fmul_ru(s * q, xmax), g), 1.f + 0x1p-20f);
+    *qscale = gmode == 2 ? sq : 1.f;
     // the select reads scores as 16-bit codes over [-B, B] (score_code), each
     // within 0.51 of a step 2B/65535 of the score: one step joins the guard
     *qguard = (gmode == 0 || gmode == 3) ? 0.f
-                                         : __double2float_ru((g + 2.0 * (double)B / 65535.0) * (1.0 + 0x1p-20));
+                                         : __fmul_ru(__fadd_ru(g, __fdiv_ru(2.f * B, 65535.f)), 1.f + 0x1p-20f);
     *qbound = B;
 }
 
@@ -404,16 +425,26 @@ __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __re
                                   float xres_max, float xhat_max,
                                   float* __restrict__ qscale, float* __restrict__ qguard, float* __restrict__ qbound,
                                   unsigned long long* fallbacks) {
+    constexpr unsigned kFull = 0xffffffffu;
+    extern __shared__ float s_rows[];      // per warp: its query's ncl scores (when staged)
     const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (q >= nq) return;
     const float* srow = S + q * ncl;
+    if (ncl <= kTopcStageCols) {
+        // every round below scans the row: stage it once (same values, same order)
+        float* own = s_rows + (threadIdx.x >> 5) * ncl;
+        for (int j = lane; j < ncl; j += 32) own[j] = srow[j];
+        __syncwarp();
+        srow = own;
+    }
     const float* qv = Q + q * d;
     const int nsl = min(c + kRouteExtra, ncl);
     // shortlist: the nsl best approximate scores (ties -> lower index), built
-    // in rounds; the first c + 1 usually settle the route (see below)
-    int sl[LIDER_MAX_C + kRouteExtra];
-    float av[LIDER_MAX_C + kRouteExtra];
+    // in rounds; the first c + 1 usually settle the route (see below).
+    // Entry e (e < nsl <= 40) is held by lane e % 32 in register slot e / 32.
+    int sl0 = 0, sl1 = 0;
+    float av0 = -INFINITY, av1 = -INFINITY;
     float ps = INFINITY;
     int pj = -1;
     auto next_best = [&](int r) {
@@ -426,106 +457,155 @@ __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __re
             if (after && (v > best || (v == best && j < bj))) { best = v; bj = j; }
         }
         for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+            const float ov = __shfl_xor_sync(kFull, best, o);
+            const int oj = __shfl_xor_sync(kFull, bj, o);
             if (ov > best || (ov == best && oj < bj)) { best = ov; bj = oj; }
         }
         if (bj >= ncl) bj = 0;
         ps = best;
         pj = bj;
-        sl[r] = bj;
-        av[r] = best;
+        if ((r & 31) == lane) {
+            if (r < 32) { sl0 = bj; av0 = best; } else { sl1 = bj; av1 = best; }
+        }
     };
+    auto entry_sl = [&](int e) { return __shfl_sync(kFull, e < 32 ? sl0 : sl1, e & 31); };
     const int n_first = min(c + 1, nsl);
 #pragma unroll 1
     for (int r = 0; r < n_first; ++r) next_best(r);
-    float qn2 = 0.f;
-    for (int i = lane; i < d; i += 32) qn2 = fmaf(qv[i], qv[i], qn2);
-    for (int o = 16; o > 0; o >>= 1) qn2 += __shfl_xor_sync(0xffffffffu, qn2, o);
+    float qn2 = 0.f, amax = 0.f;
+    for (int i = lane; i < d; i += 32) {
+        const float v = qv[i];
+        qn2 = fmaf(v, v, qn2);
+        amax = fmaxf(amax, fabsf(v));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        qn2 += __shfl_xor_sync(kFull, qn2, o);
+        amax = fmaxf(amax, __shfl_xor_sync(kFull, amax, o));
+    }
     const float guard = guard_scale * sqrtf(qn2);
-    float amax = 0.f;
-    for (int i = lane; i < d; i += 32) amax = fmaxf(amax, fabsf(qv[i]));
-    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     // FP16 path: the query's scale and the norm of its rounding residual
-    const double sq = gmode == 2 ? f16_query_scale(amax) : 1.0;
+    const float sq = gmode == 2 ? f16_query_scale(amax) : 1.f;
     // (r = fp16(v) - v is exact in FP32; the FP32 sum of the d squares is
     // inflated by (1 + (d + 32) 2^-23) to bound the exact one)
     float eq2 = 0.f;
     if (gmode == 2) {
         for (int i = lane; i < d; i += 32) {
-            const float v = qv[i] * (float)sq;
+            const float v = qv[i] * sq;
             const float r = __half2float(__float2half_rn(v)) - v;
             eq2 = fmaf(r, r, eq2);
         }
-        for (int o = 16; o > 0; o >>= 1) eq2 += __shfl_xor_sync(0xffffffffu, eq2, o);
+        for (int o = 16; o > 0; o >>= 1) eq2 += __shfl_xor_sync(kFull, eq2, o);
     }
-    const double eq = sqrt((double)eq2 * (1.0 + (double)(d + 32) * 0x1p-23)) * (1.0 + 0x1p-40);
+    const float eq = __fsqrt_ru(__fmul_ru(eq2, __fadd_ru(1.f, (float)(d + 32) * 0x1p-23f)));
     if (lane == 0)
         candidate_guard(gmode, sqrtf(qn2), sq, eq, d, max_xnorm, x_scale, xres_max, xhat_max, qscale + q,
                         qguard + q, qbound + q);
-    // When each of the c best approximate scores leads the next one by more
-    // than twice the error bound, the exact scores have the same order and no
-    // other centroid can enter: the route is the shortlist's head.
-    // (the gap is rounded down and twice the guard is exact, so a gap that
-    // passes also passes in exact arithmetic)
-    bool clear = true;
-    for (int r = 0; r < c; ++r) {
-        const float next = r + 1 < n_first ? av[r + 1] : -INFINITY;     // c + 1 <= ncl: av[c] is the next
-        if (!(__fsub_rd(av[r], next) > 2.f * guard)) clear = false;
+    // Entries e and e + 1 are "separated" when the approximate score of e leads
+    // that of e + 1 by more than twice the error bound: then every exact score
+    // of an entry up to e exceeds every exact score after it (the gap is
+    // rounded down and twice the guard is exact, so a gap that passes also
+    // passes in exact arithmetic).  Maximal runs of unseparated entries keep
+    // their place in the order; only their members' order is open.  So: find
+    // E, the first separated entry at or after c - 1 (the top-c set is then
+    // entries 0..E), score exactly the members of runs of two or more up to
+    // E, and order each such run by exact score (ties -> lower index).  When
+    // the shortlist ends before such an E, every centroid is scored exactly.
+    int n_cur = n_first;
+    int E = -1;
+    uint64_t sep = 0ull;                      // bit e: entries e and e + 1 separated
+    for (;;) {
+        // entry e + 1's score, or the end of the row (nothing after: separated)
+        float next0 = __shfl_down_sync(kFull, av0, 1);
+        const float a32 = __shfl_sync(kFull, av1, 0);
+        if (lane == 31) next0 = a32;
+        const float next1 = __shfl_down_sync(kFull, av1, 1);
+        const auto separated = [&](int e, float a, float nx) {
+            if (e >= n_cur) return false;
+            if (e + 1 >= n_cur) return n_cur == ncl;
+            return __fsub_rd(a, nx) > 2.f * guard;
+        };
+        const unsigned m0 = __ballot_sync(kFull, separated(lane, av0, next0));
+        const unsigned m1 = __ballot_sync(kFull, separated(lane + 32, av1, next1));
+        sep = (uint64_t)m0 | ((uint64_t)m1 << 32);
+        const uint64_t cand = sep & (~0ull << (c - 1));
+        if (cand) {
+            E = __ffsll((long long)cand) - 1;
+            break;
+        }
+        if (n_cur >= nsl) break;
+        next_best(n_cur++);
     }
-    if (clear) {
-        if (lane == 0) {
-            for (int r = 0; r < c; ++r) {
-                route[q * c + r] = sl[r];
-                if (trace_route) trace_route[q * c + r] = sl[r];
+    // (E = -1: the open run reaches the end of the shortlist)
+    int outv = 0;                             // lane r < c: the route's r-th centroid
+    if (E >= 0) {
+        const uint64_t upto = (2ull << E) - 1;        // entries 0..E (E < 40)
+        const uint64_t open = ~sep;                   // bit e: e and e + 1 not separated
+        // members of runs of two or more: e with e - 1 or e + 1 in its run
+        const uint64_t need = ((open << 1) | open) & upto;
+        if (!need) {
+            outv = sl0;                               // the approximate order is the exact one
+        } else {
+            // exact scores of the open runs' members, four at a time
+            uint64_t ek0 = 0ull, ek1 = 0ull;
+            uint64_t rest = need;
+            while (rest) {
+                int rows[4], ent[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    ent[t] = rest ? __ffsll((long long)rest) - 1 : -1;
+                    if (rest) rest &= rest - 1;
+                    rows[t] = entry_sl(ent[t] >= 0 ? ent[t] : ent[0]);
+                }
+                double e4[4];
+                warp_exact_scores4(qv, C, rows, d, half_norm, e4);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int e = ent[t];
+                    if (e >= 0 && (e & 31) == lane) {
+                        if (e < 32) ek0 = score_key(e4[t]); else ek1 = score_key(e4[t]);
+                    }
+                }
+            }
+            // the longest open run (warp-uniform loop bound below)
+            int run_len = 0;
+            for (uint64_t r = need; r;) {
+                const int a = __ffsll((long long)r) - 1;
+                const int b = __ffsll((long long)(sep & (~0ull << a))) - 1;     // run [a, b], b <= E
+                run_len = max(run_len, b - a + 1);
+                r &= ~0ull << (b + 1);
+            }
+            const uint64_t starts = (sep << 1) | 1ull;  // bit e: a run starts at e
+#pragma unroll
+            for (int slot = 0; slot < 2; ++slot) {
+                // final place of entry e = lane + 32 slot: its run's start plus its
+                // rank in the run by (exact score descending, index ascending)
+                const int e = lane + 32 * slot;
+                const bool mine = e <= E;
+                const int a = mine ? 63 - __clzll((long long)(starts & ((2ull << e) - 1))) : 0;
+                const int b = mine ? __ffsll((long long)(sep & (~0ull << e))) - 1 : -1;
+                const uint64_t my_key = slot ? ek1 : ek0;
+                const int my_j = slot ? sl1 : sl0;
+                const bool open_e = mine && b > a;
+                int rank = 0;
+                for (int t = 0; t < run_len; ++t) {
+                    const int f = min(a + t, 63);
+                    const uint64_t k0 = __shfl_sync(kFull, ek0, f & 31), k1 = __shfl_sync(kFull, ek1, f & 31);
+                    const int j0 = __shfl_sync(kFull, sl0, f & 31), j1 = __shfl_sync(kFull, sl1, f & 31);
+                    const uint64_t fk = f < 32 ? k0 : k1;
+                    const int fj = f < 32 ? j0 : j1;
+                    if (open_e && f != e && a + t <= b && (fk > my_key || (fk == my_key && fj < my_j))) ++rank;
+                }
+                const int pos = mine ? a + rank : -1;
+                // the lane of place pos (< c) takes entry e's centroid
+                const int hi = slot ? E - 32 : min(E, 31);
+                for (int src = 0; src <= hi; ++src) {
+                    const int p = __shfl_sync(kFull, pos, src);
+                    const int jv = __shfl_sync(kFull, my_j, src);
+                    if (p == lane && p < c) outv = jv;
+                }
             }
         }
-        return;
-    }
-#pragma unroll 1
-    for (int r = n_first; r < nsl; ++r) next_best(r);
-    // the best approximate score outside the shortlist
-    float a_out = -INFINITY;
-    if (nsl < ncl) {
-        float best = -INFINITY;
-        for (int j = lane; j < ncl; j += 32) {
-            float v = srow[j];
-            if (v != v) v = -INFINITY;
-            const bool after = (v < ps) || (v == ps && j > pj);
-            if (after && v > best) best = v;
-        }
-        for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
-        a_out = best;
-    }
-    // exact scores of the shortlist, then the c best
-    double ex[LIDER_MAX_C + kRouteExtra];
-    uint64_t ek[LIDER_MAX_C + kRouteExtra];
-    for (int r = 0; r < nsl; ++r) {
-        ex[r] = warp_exact_score(qv, C + (int64_t)sl[r] * d, d, half_norm[sl[r]]);
-        ek[r] = score_key(ex[r]);
-    }
-    int out[LIDER_MAX_C];
-    double e_c = -INFINITY;
-    {
-        // c rounds over the shortlist on integer keys (score descending, index ascending)
-        uint64_t pe = ~0ull;
-        int pjj = -1;
-        for (int r = 0; r < c; ++r) {
-            uint64_t best = 0ull;
-            int bj = 0x7fffffff, bt = 0;
-            for (int t = 0; t < nsl; ++t) {
-                const uint64_t v = ek[t];
-                const int j = sl[t];
-                const bool after = (v < pe) || (v == pe && j > pjj);
-                if (after && (v > best || (v == best && j < bj))) { best = v; bj = j; bt = t; }
-            }
-            out[r] = bj;
-            pe = best;
-            pjj = bj;
-            e_c = ex[bt];
-        }
-    }
-    if (nsl < ncl && (double)a_out + (double)guard >= e_c) {
+    } else {
         // a centroid outside the shortlist may beat the c-th: score them all exactly
         if (lane == 0) atomicAdd(fallbacks, 1ull);
         double pe = INFINITY;
@@ -538,16 +618,14 @@ __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __re
                 const bool after = (v < pe) || (v == pe && j > pjj);
                 if (after && (v > best || (v == best && j < bj))) { best = v; bj = j; }
             }
-            out[r] = bj < ncl ? bj : 0;
+            if (lane == r) outv = bj < ncl ? bj : 0;
             pe = best;
             pjj = bj;
         }
     }
-    if (lane == 0) {
-        for (int r = 0; r < c; ++r) {
-            route[q * c + r] = out[r];
-            if (trace_route) trace_route[q * c + r] = out[r];
-        }
+    if (lane < c) {
+        route[q * c + lane] = outv;
+        if (trace_route) trace_route[q * c + lane] = outv;
     }
 }
 
@@ -2579,67 +2657,60 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
 
     // 1-2. hash and route, chunk by chunk: queries [q0, q1)
     const bool tensor_route = ix->params.score_mode != LIDER_SCORE_SIMT;
-    auto hash_chunk = [&](int64_t q0, int64_t q1) -> int {
+    // SIMT mode: Dot2 hash values, then exact FP64 routing scores and top-c
+    auto simt_chunk = [&](int64_t q0, int64_t q1, bool last) -> int {
         const int64_t n = q1 - q0;
         const float* Qc = Q + q0 * g.d;
-        if (!tensor_route) return launch_hash_t(Qc, n, g.d, g.A, g.bproj, g.H, g.W, w.tq + q0 * g.H, st);
+        int32_t* trace_route = tr && tr->route ? tr->route + q0 * c : nullptr;
+        if ((rc = launch_hash_t(Qc, n, g.d, g.A, g.bproj, g.H, g.W, w.tq + q0 * g.H, st))) return rc;
+        if (last && (rc = mark(LIDER_PHASE_ROUTE))) return rc;
+        if ((rc = launch_scores(Qc, n, g.d, g.C, g.half_norm, g.ncl, w.rscore + q0 * g.ncl, st))) return rc;
+        topc_kernel<<<(unsigned)cdiv(n * 32, 256), 256, 0, st>>>(w.rscore + q0 * g.ncl, n, g.ncl, c,
+                                                                 w.route + q0 * c, trace_route);
+        LIDER_LAUNCH_CHECK("topc_kernel");
+        return LIDER_OK;
+    };
+    // tensor modes: one front_tc_kernel launch for the chunk's hash values and
+    // routing scores, then the top-c of each query (with its guards)
+    auto tensor_chunk = [&](int64_t q0, int64_t q1, bool last) -> int {
+        const int64_t n = q1 - q0;
+        const float* Qc = Q + q0 * g.d;
+        int32_t* trace_route = tr && tr->route ? tr->route + q0 * c : nullptr;
         CUtensorMap mqs_h, mqs_l;      // the chunk's queries as TF32 head / tail
         if ((rc = launch_split_tf32(Qc, n * g.d, w.qs_hi + q0 * g.d, w.qs_lo + q0 * g.d, st))) return rc;
         if ((rc = make_tensor_map(&mqs_h, w.qs_hi + q0 * g.d, n, g.d, tc::kBM))) return rc;
         if ((rc = make_tensor_map(&mqs_l, w.qs_lo + q0 * g.d, n, g.d, tc::kBM))) return rc;
         qnorm_kernel<<<(unsigned)cdiv(n * 32, 256), 256, 0, st>>>(Qc, n, g.d, w.qnorm + q0);
         LIDER_LAUNCH_CHECK("qnorm_kernel");
-        HashSched hs{(int)n, g.H};
-        HashEpi he;
-        he.t = w.tq + q0 * g.H;
-        he.b = g.bproj;
-        he.a_norm = ix->a_norm;
-        he.qnorm = w.qnorm + q0;
-        he.recheck = w.hrecheck;
-        he.n_recheck = w.n_hrecheck;
-        he.W = (float)g.W;
-        he.hyper = g.hash_kind == LIDER_HASH_HYPERPLANE;
-        he.guard = kTcGuard;
-        he.nq = (int)n;
-        he.H = g.H;
-        he.q0 = (int)q0;
-        const int64_t tiles = cdiv(n, tc::kBM) * cdiv(g.H, tc::kBN);
-        if ((rc = smem_attr((const void*)hash_tc_kernel, (int)(tc::kSmemBytes)))) return rc;
-        hash_tc_kernel<<<(unsigned)std::min<int64_t>(tiles, ix->num_sms), tc::kThreads, tc::kSmemBytes, st>>>(
-            mqs_h, mqs_l, ix->map_ahi, ix->map_alo, (g.d + tc::KindTf32x3::kBK - 1) / tc::KindTf32x3::kBK, hs, he,
-            w.tc_err);
-        LIDER_LAUNCH_CHECK("hash_tc_kernel");
-        return LIDER_OK;
-    };
-    auto route_chunk = [&](int64_t q0, int64_t q1) -> int {
-        const int64_t n = q1 - q0;
-        const float* Qc = Q + q0 * g.d;
-        int32_t* trace_route = tr && tr->route ? tr->route + q0 * c : nullptr;
-        if (!tensor_route) {
-            if ((rc = launch_scores(Qc, n, g.d, g.C, g.half_norm, g.ncl, w.rscore + q0 * g.ncl, st))) return rc;
-            topc_kernel<<<(unsigned)cdiv(n * 32, 256), 256, 0, st>>>(w.rscore + q0 * g.ncl, n, g.ncl, c,
-                                                                     w.route + q0 * c, trace_route);
-            LIDER_LAUNCH_CHECK("topc_kernel");
-            return LIDER_OK;
-        }
         float* S = reinterpret_cast<float*>(w.rscore) + q0 * g.ncl;
-        CUtensorMap mqh, mql;
-        if ((rc = make_tensor_map(&mqh, w.qs_hi + q0 * g.d, n, g.d, tc::kBM))) return rc;
-        if ((rc = make_tensor_map(&mql, w.qs_lo + q0 * g.d, n, g.d, tc::kBM))) return rc;
-        RouteSched rs{(int)n, g.ncl};
-        RouteEpi re;
-        re.S = S;
-        re.half_norm = g.half_norm;
-        re.nq = (int)n;
-        re.ncl = g.ncl;
-        const int64_t tiles = cdiv(n, tc::kBM) * cdiv(g.ncl, tc::kBN);
-        if ((rc = smem_attr((const void*)route_tc_kernel, (int)(tc::kSmemBytes)))) return rc;
-        route_tc_kernel<<<(unsigned)std::min<int64_t>(tiles, ix->num_sms), tc::kThreads, tc::kSmemBytes, st>>>(
-            mqh, mql, ix->map_chi, ix->map_clo, (g.d + tc::KindTf32x3::kBK - 1) / tc::KindTf32x3::kBK, rs, re,
+        FrontSched fs{(int)n, ix->front_hp / tc::kBN, (int)cdiv(g.ncl, tc::kBN), ix->front_hp};
+        FrontEpi fe;
+        fe.t = w.tq + q0 * g.H;
+        fe.b = g.bproj;
+        fe.a_norm = ix->a_norm;
+        fe.qnorm = w.qnorm + q0;
+        fe.recheck = w.hrecheck;
+        fe.n_recheck = w.n_hrecheck;
+        fe.W = (float)g.W;
+        fe.guard = kTcGuard;
+        fe.H = g.H;
+        fe.q0 = (int)q0;
+        fe.hyper = g.hash_kind == LIDER_HASH_HYPERPLANE;
+        fe.S = S;
+        fe.half_norm = g.half_norm;
+        fe.ncl = g.ncl;
+        fe.nq = (int)n;
+        fe.nth = fs.nth;
+        fe.ntr = fs.ntr;
+        const int64_t tiles = cdiv(n, tc::kBM) * (fs.nth + fs.ntr);
+        if ((rc = smem_attr((const void*)front_tc_kernel, (int)(tc::kSmemBytes)))) return rc;
+        front_tc_kernel<<<(unsigned)std::min<int64_t>(tiles, ix->num_sms), tc::kThreads, tc::kSmemBytes, st>>>(
+            mqs_h, mqs_l, ix->map_fhi, ix->map_flo, (g.d + tc::KindTf32x3::kBK - 1) / tc::KindTf32x3::kBK, fs, fe,
             w.tc_err);
-        LIDER_LAUNCH_CHECK("route_tc_kernel");
+        LIDER_LAUNCH_CHECK("front_tc_kernel");
+        if (last && (rc = mark(LIDER_PHASE_ROUTE))) return rc;
         // guard: the tensor-core error of one score stays below kTcGuard |q| |mu|
-        topc_exact_kernel<<<(unsigned)cdiv(n * 32, 256), 256, 0, st>>>(
+        topc_exact_kernel<<<(unsigned)cdiv(n * 32, 256), 256, g.ncl <= kTopcStageCols ? 8 * g.ncl * 4 : 0, st>>>(
             S, Qc, g.C, g.half_norm, n, g.ncl, g.d, c, kTcGuard * ix->max_cnorm, w.route + q0 * c, trace_route,
             guard_mode(ix->params.score_mode), ix->max_xnorm, ix->x_scale, ix->xres_max, ix->xhat_max,
             w.qscale + q0, w.qguard + q0, w.qbound + q0, &w.counters[CNT_ROUTE_FALLBACK]);
@@ -2651,10 +2722,12 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
     for (int i = 0; i < nch; ++i) {
         const int64_t q0 = feed ? feed->bounds[i] : 0, q1 = feed ? feed->bounds[i + 1] : nq;
         if (feed) LIDER_CUDA_TRY(cudaStreamWaitEvent(st, feed->ready[i], 0));
-        if (q1 <= q0) continue;
-        if ((rc = hash_chunk(q0, q1))) return rc;
-        if (i == nch - 1 && (rc = mark(LIDER_PHASE_ROUTE))) return rc;
-        if ((rc = route_chunk(q0, q1))) return rc;
+        const bool last = i == nch - 1;
+        if (q1 > q0) {
+            if ((rc = tensor_route ? tensor_chunk(q0, q1, last) : simt_chunk(q0, q1, last))) return rc;
+        } else if (last && (rc = mark(LIDER_PHASE_ROUTE))) {
+            return rc;
+        }
     }
     // hash values too close to a bucket edge for the tiles' error, recomputed
     // exactly; then the packed keys of the whole batch
@@ -2893,6 +2966,24 @@ int read_stats(const Workspace& w, int64_t nq, int c, lider_search_stats* stats,
     return LIDER_OK;
 }
 
+// Counters of one more pass added to a search's.
+void add_stats(lider_search_stats* acc, const lider_search_stats& ps) {
+    acc->n_queries += ps.n_queries;
+    acc->pairs += ps.pairs;
+    acc->candidates += ps.candidates;
+    acc->qkey_boundary += ps.qkey_boundary;
+    acc->qkey_clamped += ps.qkey_clamped;
+    acc->locate_fallback += ps.locate_fallback;
+    acc->empty_pairs += ps.empty_pairs;
+    acc->tc_tiles += ps.tc_tiles;
+    acc->route_fallback += ps.route_fallback;
+    acc->select_overflow += ps.select_overflow;
+    acc->rmi_oor += ps.rmi_oor;
+    acc->rmi_le += ps.rmi_le;
+    acc->rmi_oor_le += ps.rmi_oor_le;
+    acc->passes += ps.passes;
+}
+
 int pool_alloc(const lider_index* ix, void** p, size_t bytes, cudaStream_t st) {
     // under stream capture the scratch becomes a graph allocation node
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -2961,23 +3052,7 @@ int search_entry(const lider_index* ix, const float* Q, int64_t nq, int k, int c
         rc = enqueue_search(ix, Q + q0 * d, n, k, c, out_ids + q0 * k, out_scores + q0 * k, tp, w, st);
         if (rc == LIDER_OK && stats) {
             lider_search_stats ps{};
-            rc = read_stats(w, n, c, &ps, st);
-            if (rc == LIDER_OK) {
-                stats->n_queries += ps.n_queries;
-                stats->pairs += ps.pairs;
-                stats->candidates += ps.candidates;
-                stats->qkey_boundary += ps.qkey_boundary;
-                stats->qkey_clamped += ps.qkey_clamped;
-                stats->locate_fallback += ps.locate_fallback;
-                stats->empty_pairs += ps.empty_pairs;
-                stats->tc_tiles += ps.tc_tiles;
-                stats->route_fallback += ps.route_fallback;
-                stats->select_overflow += ps.select_overflow;
-                stats->rmi_oor += ps.rmi_oor;
-                stats->rmi_le += ps.rmi_le;
-                stats->rmi_oor_le += ps.rmi_oor_le;
-                stats->passes += ps.passes;
-            }
+            if ((rc = read_stats(w, n, c, &ps, st)) == LIDER_OK) add_stats(stats, ps);
         }
     }
     cudaError_t e = cudaFreeAsync(mem, st);
@@ -3101,28 +3176,32 @@ void* device_view(const void* host) {
     return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
-// End to end on host buffers.  The queries go to the device in up to
-// kHostChunks copies on a second stream, and the hash and route of each chunk
-// start as soon as it has landed, so the copy overlaps the per-query front of
-// the search.  When the result buffers are pinned and mapped, the final
-// re-score writes the ids and scores into them directly (no copy back);
-// otherwise they are copied after the search.
+// End to end on host buffers, in the passes lider_search would make.  The
+// queries go to the device on a second stream, each pass's in up to
+// kHostChunks copies, and the hash and route of each chunk start as soon as
+// it has landed, so the copies overlap the per-query front of the search (and
+// a later pass's copies the earlier passes).  When the result buffers are
+// pinned and mapped, each pass's final re-score writes its ids and scores into
+// them directly (no copy back); otherwise each pass's results are copied back
+// after it.
 constexpr int kHostChunks = 4;
 
 int search_host_entry(const lider_index* ix, const float* Qh, int64_t nq, int k, int c, int64_t* ids_h,
                       float* scores_h, lider_search_stats* stats, void* stream) {
-    int rc = check_search_args(ix, Qh, nq, k, c, ids_h, scores_h);
+    int rc = check_search_args(ix, Qh, nq, k, c, ids_h, scores_h, true, false);
     if (rc) return rc;
     if (stats) *stats = lider_search_stats{};
     if (nq == 0) return LIDER_OK;
+    const int64_t pb = pass_size(ix, nq, k, c);
+    if ((rc = check_pass_caps(ix, pb, k, c))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
+    const int d = ix->g.d;
     int64_t* ids_view = static_cast<int64_t*>(device_view(ids_h));
     float* scores_view = static_cast<float*>(device_view(scores_h));
     const bool direct = ids_view && scores_view;
-    const size_t qb = (size_t)nq * ix->g.d * 4, ib = direct ? 0 : (size_t)nq * k * 8, sb = direct ? 0 : (size_t)nq * k * 4;
+    const size_t qb = (size_t)nq * d * 4, ib = direct ? 0 : (size_t)nq * k * 8, sb = direct ? 0 : (size_t)nq * k * 4;
     const size_t o_ids = align_up(qb, 256), o_sc = align_up(o_ids + ib, 256);
-    const Shape sh = search_shape(ix, k, nq, c);
-    Workspace sz = carve(nullptr, ix->g, nq, c, sh);
+    Workspace sz = carve(nullptr, ix->g, pb, c, search_shape(ix, k, pb, c));
     const size_t o_ws = align_up(o_sc + sb, 256);
     void* mem = nullptr;
     if ((rc = pool_alloc(ix, &mem, o_ws + sz.total, st))) return rc;
@@ -3130,37 +3209,59 @@ int search_host_entry(const lider_index* ix, const float* Qh, int64_t nq, int k,
     float* Qd = (float*)m;
     int64_t* idd = direct ? ids_view : (int64_t*)(m + o_ids);
     float* scd = direct ? scores_view : (float*)(m + o_sc);
-    Workspace w = carve(m + o_ws, ix->g, nq, c, sh);
 
-    // chunked copy-in on a stream of its own, ordered after the caller's stream
-    const int nch = (int)std::max<int64_t>(1, std::min<int64_t>(kHostChunks, nq / 2048));
-    int64_t bounds[kHostChunks + 1];
-    for (int i = 0; i <= nch; ++i) bounds[i] = nq * i / nch;
+    // chunk bounds, pass by pass: pass p owns chunks [first[p], first[p+1])
+    const int64_t npass = (nq + pb - 1) / pb;
+    std::vector<int64_t> bounds;              // absolute query offsets
+    std::vector<int> first;
+    for (int64_t q0 = 0; q0 < nq; q0 += pb) {
+        const int64_t n = std::min(pb, nq - q0);
+        const int nch = (int)std::max<int64_t>(1, std::min<int64_t>(kHostChunks, n / 2048));
+        first.push_back((int)bounds.size());
+        for (int i = 0; i < nch; ++i) bounds.push_back(q0 + n * i / nch);
+    }
+    first.push_back((int)bounds.size());
+    bounds.push_back(nq);
+    const int nchunks = (int)bounds.size() - 1;
     cudaStream_t cs = nullptr;
-    cudaEvent_t evs[kHostChunks + 1] = {};
+    std::vector<cudaEvent_t> evs(nchunks + 1, nullptr);
     auto cleanup = [&]() {
         for (cudaEvent_t e : evs)
             if (e) cudaEventDestroy(e);
         if (cs) cudaStreamDestroy(cs);
     };
+    // copy-in on a stream of its own, ordered after the caller's stream
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-    for (int i = 0; e == cudaSuccess && i <= nch; ++i) e = cudaEventCreateWithFlags(&evs[i], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventRecord(evs[nch], st);        // the caller's earlier work comes first
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, evs[nch], 0);
-    for (int i = 0; e == cudaSuccess && i < nch; ++i) {
-        const size_t off = (size_t)bounds[i] * ix->g.d, len = (size_t)(bounds[i + 1] - bounds[i]) * ix->g.d;
+    for (int i = 0; e == cudaSuccess && i <= nchunks; ++i) e = cudaEventCreateWithFlags(&evs[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(evs[nchunks], st);        // the caller's earlier work comes first
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, evs[nchunks], 0);
+    for (int i = 0; e == cudaSuccess && i < nchunks; ++i) {
+        const size_t off = (size_t)bounds[i] * d, len = (size_t)(bounds[i + 1] - bounds[i]) * d;
         e = cudaMemcpyAsync(Qd + off, Qh + off, len * 4, cudaMemcpyHostToDevice, cs);
         if (e == cudaSuccess) e = cudaEventRecord(evs[i], cs);
     }
     if (e != cudaSuccess) rc = cuda_fail(e, "lider_search_host: copying the queries in");
-    const FrontFeed feed{nch, bounds, evs};
-    if (!rc) rc = enqueue_search(ix, Qd, nq, k, c, idd, scd, nullptr, w, st, &feed);
-    if (!rc && !direct && (e = cudaMemcpyAsync(ids_h, idd, (size_t)nq * k * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-        rc = cuda_fail(e, "cudaMemcpyAsync(ids)");
-    if (!rc && !direct &&
-        (e = cudaMemcpyAsync(scores_h, scd, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-        rc = cuda_fail(e, "cudaMemcpyAsync(scores)");
-    if (!rc && stats) rc = read_stats(w, nq, c, stats, st);
+    for (int64_t p = 0; p < npass && !rc; ++p) {
+        const int64_t q0 = p * pb, n = std::min(pb, nq - q0);
+        int64_t rel[kHostChunks + 1];
+        const int nch = first[p + 1] - first[p];
+        for (int i = 0; i <= nch; ++i) rel[i] = bounds[first[p] + i] - q0;
+        const FrontFeed feed{nch, rel, evs.data() + first[p]};
+        Workspace w = carve(m + o_ws, ix->g, n, c, search_shape(ix, k, n, c));
+        rc = enqueue_search(ix, Qd + q0 * d, n, k, c, idd + q0 * k, scd + q0 * k, nullptr, w, st, &feed);
+        if (!rc && !direct &&
+            (e = cudaMemcpyAsync(ids_h + q0 * k, idd + q0 * k, (size_t)n * k * 8, cudaMemcpyDeviceToHost, st)) !=
+                cudaSuccess)
+            rc = cuda_fail(e, "cudaMemcpyAsync(ids)");
+        if (!rc && !direct &&
+            (e = cudaMemcpyAsync(scores_h + q0 * k, scd + q0 * k, (size_t)n * k * 4, cudaMemcpyDeviceToHost, st)) !=
+                cudaSuccess)
+            rc = cuda_fail(e, "cudaMemcpyAsync(scores)");
+        if (!rc && stats) {
+            lider_search_stats ps{};
+            if (!(rc = read_stats(w, n, c, &ps, st))) add_stats(stats, ps);
+        }
+    }
     // a complete search waited for every chunk's event on st; after a failure
     // the copies may still run, so they finish before the memory is released
     if (rc && cs) cudaStreamSynchronize(cs);

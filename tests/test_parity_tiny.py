@@ -112,6 +112,34 @@ def test_host_path_in_chunks_equals_device_path(tiny, pinned):
     assert torch.equal(hid, ids.cpu()) and torch.equal(hsc, sc.cpu())
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_path_in_passes_equals_device_path(tiny, pinned):
+    """With a probe batch of 2,500 the host path searches 9,000 queries in
+    four passes (chunks of 2,500 and 1,500 queries whose copies land on a
+    second stream); results and summed counters equal the device search."""
+    import torch
+    from paper_2205_00970_b300 import synth
+    cfg = tiny["cfg"]
+    g = tiny["gidx"]
+    Q = synth.queries(cfg["seed"] + 2, 9_000, cfg["d"], cfg["n_comp"], cfg["sigma"], cfg["zipf_s"])
+    ids, sc, st = g.search(torch.from_numpy(Q).cuda(), cfg["k"], cfg["c"], stats=True)
+    Qh = torch.from_numpy(Q)
+    hid = torch.full((len(Q), cfg["k"]), 7, dtype=torch.int64)
+    hsc = torch.zeros((len(Q), cfg["k"]), dtype=torch.float32)
+    if pinned:
+        Qh, hid, hsc = Qh.pin_memory(), hid.pin_memory(), hsc.pin_memory()
+    before = g.tuning()
+    try:
+        g.set_tuning(probe_batch=2_500)
+        hid, hsc, hst = g.search_host(Qh, cfg["k"], cfg["c"], hid, hsc, stats=True)
+    finally:
+        g.set_tuning(**before)
+    assert hst["passes"] == 4 and st["passes"] == 1
+    assert torch.equal(hid, ids.cpu()) and torch.equal(hsc, sc.cpu())
+    for key in ("candidates", "pairs", "qkey_boundary", "locate_fallback", "n_queries"):
+        assert hst[key] == st[key], key
+
+
 @pytest.mark.parametrize("nq", [0, 1, 7, 33, 257])
 def test_ragged_batches_are_batch_invariant(tiny, nq):
     """A query's result does not depend on its batch-mates or batch size."""
@@ -217,6 +245,37 @@ def test_massive_ties_take_the_multi_level_select(mode):
     assert out[mode][2].max() > 2048          # some tied query exceeds the histogram collection
     assert np.array_equal(out[mode][0], out[1][0])
     assert np.array_equal(out[mode][1].view(np.uint32), out[1][1].view(np.uint32))
+
+
+@pytest.mark.parametrize("mode", [0, 3], ids=["tensor", "f16"])
+def test_route_with_tied_centroids_equals_simt(mode):
+    """Centroids in groups of equal rows (exactly tied routing scores) and of
+    rows 1e-7 apart (within the tensor-core error guard): the tensor path
+    scores exactly only the entries whose approximate order is open, and its
+    route equals the SIMT path's (exact scores, ties to the lower index) for
+    every query and every c."""
+    import torch
+    rng = np.random.default_rng(21)
+    d, n = 64, 3000
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    X /= np.linalg.norm(X, axis=1, keepdims=True)
+    base = X[rng.choice(n, 12, replace=False)]
+    C = np.concatenate([base, base[:6], base[:6] + 1e-7 * rng.standard_normal((6, d))]).astype(np.float32)
+    cfg = dict(L=2, m=8, W=0.7, leaves=8, r0=3, B=1, k=10)
+    A = rng.standard_normal((cfg["L"] * cfg["m"], d)).astype(np.float32)
+    b = (rng.random(cfg["L"] * cfg["m"]) * cfg["W"]).astype(np.float32)
+    Q = np.concatenate([X[:60], base + 1e-3 * rng.standard_normal((12, d)).astype(np.float32),
+                        rng.standard_normal((20, d)).astype(np.float32)]).astype(np.float32)
+    Qd = torch.from_numpy(Q).cuda()
+    routes = {}
+    for m in (mode, 1):
+        g = F.gpu_index(dict(cfg, score_mode=m), X, C, A, b)
+        for c in (1, 3, 8, 17, 24):
+            _, _, _, tr = g.search(Qd, cfg["k"], c, stats=True, trace=True)
+            routes[m, c] = tr["route"].cpu().numpy()
+        g.free()
+    for c in (1, 3, 8, 17, 24):
+        assert np.array_equal(routes[mode, c], routes[1, c]), c
 
 
 def test_invalid_search_arguments(tiny):
