@@ -126,10 +126,11 @@ typedef struct {
     int64_t route_fallback;    /* tensor paths: queries whose routing shortlist was
                                   too close to call and were routed by an exact
                                   scan of all centroids                          */
-    int64_t select_overflow;   /* plain tensor path: queries whose guard band of
-                                  near-tied candidates did not fit the re-score
-                                  list (their top k may then differ from the exact
-                                  one by near-ties; 0 in normal operation)       */
+    int64_t select_overflow;   /* guarded tensor paths (TENSOR, F16): queries whose
+                                  guard band of near-tied candidates did not fit
+                                  the re-score list; their whole band is then
+                                  re-scored exactly by a second kernel, so the
+                                  top k stays exact (0 in normal operation)      */
     /* RMI diagnostics of Sec. 7.4, over every (query, probed cluster, array):
      * the prediction p^ is out of range (OOR) when it was clamped to 0 or
      * n_c - 1, i.e. it equals either end; it is a large error (LE) when

@@ -535,12 +535,20 @@ __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __re
         if (n_cur >= nsl) break;
         next_best(n_cur++);
     }
-    // (E = -1: the open run reaches the end of the shortlist)
+    // No separation at or after c - 1 within the shortlist: the run holding
+    // entry c - 1 reaches the shortlist's end.  Its members are scored
+    // exactly as well, and the result stands when the best approximate score
+    // outside the shortlist, plus the guard, stays below the exact c-th score;
+    // otherwise every centroid is scored exactly.
+    const bool open_tail = E < 0;
+    if (open_tail) E = nsl - 1;
     int outv = 0;                             // lane r < c: the route's r-th centroid
-    if (E >= 0) {
+    uint64_t kc = 0ull;                       // open tail: the exact key of the route's c-th
+    {
         const uint64_t upto = (2ull << E) - 1;        // entries 0..E (E < 40)
         const uint64_t open = ~sep;                   // bit e: e and e + 1 not separated
         // members of runs of two or more: e with e - 1 or e + 1 in its run
+        // (the open tail's last entry counts as unseparated from what follows)
         const uint64_t need = ((open << 1) | open) & upto;
         if (!need) {
             outv = sl0;                               // the approximate order is the exact one
@@ -566,13 +574,15 @@ __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __re
                     }
                 }
             }
+            // runs end at a separated entry or at E
+            const uint64_t ends = sep | (1ull << E);
             // the longest open run (warp-uniform loop bound below)
             int run_len = 0;
             for (uint64_t r = need; r;) {
                 const int a = __ffsll((long long)r) - 1;
-                const int b = __ffsll((long long)(sep & (~0ull << a))) - 1;     // run [a, b], b <= E
+                const int b = __ffsll((long long)(ends & (~0ull << a))) - 1;    // run [a, b], b <= E
                 run_len = max(run_len, b - a + 1);
-                r &= ~0ull << (b + 1);
+                r &= (b >= 63) ? 0ull : (~0ull << (b + 1));
             }
             const uint64_t starts = (sep << 1) | 1ull;  // bit e: a run starts at e
 #pragma unroll
@@ -582,7 +592,7 @@ __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __re
                 const int e = lane + 32 * slot;
                 const bool mine = e <= E;
                 const int a = mine ? 63 - __clzll((long long)(starts & ((2ull << e) - 1))) : 0;
-                const int b = mine ? __ffsll((long long)(sep & (~0ull << e))) - 1 : -1;
+                const int b = mine ? __ffsll((long long)(ends & (~0ull << e))) - 1 : -1;
                 const uint64_t my_key = slot ? ek1 : ek0;
                 const int my_j = slot ? sl1 : sl0;
                 const bool open_e = mine && b > a;
@@ -596,6 +606,8 @@ __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __re
                     if (open_e && f != e && a + t <= b && (fk > my_key || (fk == my_key && fj < my_j))) ++rank;
                 }
                 const int pos = mine ? a + rank : -1;
+                const unsigned at_c = __ballot_sync(kFull, pos == c - 1);
+                if (at_c) kc = __shfl_sync(kFull, my_key, __ffs(at_c) - 1);
                 // the lane of place pos (< c) takes entry e's centroid
                 const int hi = slot ? E - 32 : min(E, 31);
                 for (int src = 0; src <= hi; ++src) {
@@ -605,7 +617,21 @@ __global__ void topc_exact_kernel(const float* __restrict__ S, const float* __re
                 }
             }
         }
-    } else {
+    }
+    bool rescan = false;
+    if (open_tail) {
+        // the best approximate score outside the shortlist
+        float best = -INFINITY;
+        for (int j = lane; j < ncl; j += 32) {
+            float v = srow[j];
+            if (v != v) v = -INFINITY;
+            const bool after = (v < ps) || (v == ps && j > pj);
+            if (after && v > best) best = v;
+        }
+        for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(kFull, best, o));
+        rescan = score_key((double)best + (double)guard) >= kc;
+    }
+    if (rescan) {
         // a centroid outside the shortlist may beat the c-th: score them all exactly
         if (lane == 0) atomicAdd(fallbacks, 1ull);
         double pe = INFINITY;
@@ -1751,7 +1777,21 @@ struct DenseArgs {
     const int64_t* cl_off;
     const int64_t* orig_id;
     const int32_t* ucount;      // candidates per pair
+    // guarded modes: queries whose band did not fit their list, each with the
+    // band's lower score bound (rescore_band_kernel re-scores them)
+    int32_t* ovf;
+    float* ovf_thr;
+    int32_t* ovf_count;
 };
+
+// A guarded query whose band (every candidate scoring at least t) outgrew its
+// list: listed for the exact re-score of the whole band.
+__device__ __forceinline__ void record_overflow(const DenseArgs& d, int64_t q, float t) {
+    if (!d.ovf) return;
+    const int i = atomicAdd(d.ovf_count, 1);
+    d.ovf[i] = (int32_t)q;
+    d.ovf_thr[i] = t;
+}
 
 struct PairRow {
     const uint16_t* row;        // score codes (score_code)
@@ -1774,6 +1814,90 @@ __device__ __forceinline__ bool is_cand(const PairRow& r, int pos) { return (r.b
 
 __device__ __forceinline__ uint64_t sel_key(float sc, uint32_t low) {
     return ((uint64_t)(~float_order(sc)) << 32) | (uint64_t)low;
+}
+
+// Exact re-score of a guarded query's whole band, for the queries whose band
+// outgrew the list the selects hand to rescore_kernel (listed by
+// record_overflow; none in ordinary workloads, many under massive near-ties):
+// every candidate of the query's c pairs whose approximate score (its code
+// mapped back) is at least the band's bound t is scored exactly, with
+// rescore_kernel's arithmetic, and the k best (score descending, id ascending)
+// replace what rescore_kernel wrote.  One block per listed query (grid-stride
+// over the list); candidates are taken kBandChunk positions of the pairs at a
+// time, scored, and merged with the k best so far by a block sort.
+constexpr int kBandChunk = 1024;
+
+__global__ void __launch_bounds__(256) rescore_band_kernel(DenseArgs da, const float* __restrict__ Q,
+                                                           const float* __restrict__ X, int d, int c, int k,
+                                                           int64_t* __restrict__ out_ids,
+                                                           float* __restrict__ out_scores) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ PairRow s_pr[LIDER_MAX_C];
+    __shared__ int s_n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    // key: the KB (>= k) best so far, then the chunk's keys, then leftovers of
+    // earlier sorts (all exact, none twice); 2 kBandChunk >= KB + kBandChunk
+    const int KB = next_pow2_dev(k);
+    constexpr int kSort = 2 * kBandChunk;
+    float* qv = reinterpret_cast<float*>(smem);
+    uint64_t* key = reinterpret_cast<uint64_t*>(smem + align_up_dev((size_t)d * 4, 16));
+    int32_t* crow = reinterpret_cast<int32_t*>(key + kSort);            // the chunk's cluster positions
+    const int n_ovf = *da.ovf_count;
+    const int d4 = d / 4;
+    for (int oi = blockIdx.x; oi < n_ovf; oi += gridDim.x) {
+        const int64_t q = da.ovf[oi];
+        const float t = da.ovf_thr[oi];
+        const float cB = da.qbound[q] > 0.f ? da.qbound[q] : 1.f, cstep = code_step(cB);
+        __syncthreads();                              // the previous query's reads are done
+        for (int i = tid; i < d4; i += blockDim.x)
+            reinterpret_cast<float4*>(qv)[i] = reinterpret_cast<const float4*>(Q + q * d)[i];
+        for (int i = tid; i < kSort; i += blockDim.x) key[i] = ~0ull;
+        if (tid < c) s_pr[tid] = pair_row(da, q * c + tid);
+        __syncthreads();
+        for (int p = 0; p < c; ++p) {
+            const PairRow pr = s_pr[p];
+            for (int base = 0; base < pr.n_c; base += kBandChunk) {
+                if (tid == 0) s_n = 0;
+                __syncthreads();
+                for (int pos = base + tid; pos < min(pr.n_c, base + kBandChunk); pos += blockDim.x) {
+                    if (is_cand(pr, pos) && code_score(pr.row[pos], cB, cstep) >= t)
+                        crow[atomicAdd(&s_n, 1)] = pos;
+                }
+                __syncthreads();
+                const int nb = s_n;
+                __syncthreads();                       // every thread has read s_n
+                if (nb == 0) continue;                 // the same in every thread
+                // exact scores, one row per warp, in rescore_kernel's order
+                const float4* y4 = reinterpret_cast<const float4*>(qv);
+                for (int r = warp; r < kBandChunk; r += nwarps) {
+                    if (r >= nb) {
+                        if (lane == 0) key[KB + r] = ~0ull;
+                        continue;
+                    }
+                    const int64_t row = pr.cb + crow[r];
+                    const float4* x4 = reinterpret_cast<const float4*>(X + row * d);
+                    float acc = 0.f;
+                    for (int i = lane; i < d4; i += 32) {
+                        const float4 y = y4[i];
+                        const float4 x = __ldg(x4 + i);
+                        acc = fmaf(x.x, y.x, acc);
+                        acc = fmaf(x.y, y.y, acc);
+                        acc = fmaf(x.z, y.z, acc);
+                        acc = fmaf(x.w, y.w, acc);
+                    }
+                    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                    if (lane == 0) key[KB + r] = sel_key(acc, (uint32_t)__ldg(da.orig_id + row));
+                }
+                __syncthreads();
+                block_bitonic(key, kSort);             // the KB best of all lead
+            }
+        }
+        for (int r = tid; r < k; r += blockDim.x) {
+            const uint64_t kv = key[r];
+            out_ids[q * k + r] = kv == ~0ull ? -1 : (int64_t)(uint32_t)kv;
+            out_scores[q * k + r] = kv == ~0ull ? -INFINITY : float_from_order(~(uint32_t)(kv >> 32));
+        }
+    }
 }
 
 // Load the pair rows of query q into s_pr (threads 0..c-1) and the candidate
@@ -1967,7 +2091,10 @@ __global__ void __launch_bounds__(256) select_query_kernel(DenseArgs da, int c, 
             if (float_from_order(~(uint32_t)(keys[r] >> 32)) >= t) atomicMax(&s_band, r + 1);
         __syncthreads();
         const int band = s_band;
-        if (tid == 0 && (spilled || band > so)) atomicAdd(&counters[CNT_SEL_OVERFLOW], 1ull);
+        if (tid == 0 && (spilled || band > so)) {
+            atomicAdd(&counters[CNT_SEL_OVERFLOW], 1ull);
+            record_overflow(da, q, t);
+        }
         keep = min(band, so);
     }
     for (int r = tid; r < so; r += blockDim.x) {
@@ -2366,7 +2493,10 @@ __global__ void __launch_bounds__(512) select_hist_kernel(
             if (float_from_order(~(uint32_t)(cand[r] >> 32)) >= t) atomicMax(&s_band, r + 1);
         __syncthreads();
         const int band = s_band;
-        if (tid == 0 && band > so) atomicAdd(&counters[CNT_SEL_OVERFLOW], 1ull);
+        if (tid == 0 && band > so) {
+            atomicAdd(&counters[CNT_SEL_OVERFLOW], 1ull);
+            record_overflow(da, q, t);
+        }
         keep = min(band, so);
     }
     for (int r = tid; r < so; r += blockDim.x) {
@@ -2456,6 +2586,9 @@ struct Workspace {
     int32_t* n_hrecheck;        // (cleared)
     int32_t* redo;              // tensor paths: queries left to the multi-level select
     int32_t* redo_count;        // (cleared)
+    int32_t* ovf_count;         // guarded modes: queries whose band outgrew the list (cleared)
+    int32_t* ovf;               //   those queries
+    float* ovf_thr;             //   and their bands' lower score bounds
     int32_t* pcount;            // tensor path: candidates per pair (cleared; written by mark_kernel)
     uint16_t* dense;            // tensor paths: per pair slot, approximate score codes over its cluster
     float* cmax;                // tensor paths: per pair slot and bitmap word, the best candidate score
@@ -2523,6 +2656,7 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, const
     w.tc_err = (int*)take(16);
     w.pcount = tensor ? (int32_t*)take((size_t)np * 4) : nullptr;
     w.redo_count = tensor ? (int32_t*)take(16) : nullptr;
+    w.ovf_count = tensor ? (int32_t*)take(16) : nullptr;
     w.n_hrecheck = tensor ? (int32_t*)take(16) : nullptr;
     w.zero_bytes = o;
     w.unit_off = (int32_t*)take((size_t)(g.ncl + 1) * 4);
@@ -2565,6 +2699,8 @@ Workspace carve(unsigned char* base, const Geometry& g, int64_t nq, int c, const
     w.qnorm = tensor ? (float*)take((size_t)nq * 4) : nullptr;
     w.hrecheck = tensor ? (int32_t*)take((size_t)nq * g.H * 4) : nullptr;
     w.redo = tensor ? (int32_t*)take((size_t)nq * 4) : nullptr;
+    w.ovf = tensor ? (int32_t*)take((size_t)nq * 4) : nullptr;
+    w.ovf_thr = tensor ? (float*)take((size_t)nq * 4) : nullptr;
     w.total = o;
     return w;
 }
@@ -2776,6 +2912,7 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
     LIDER_LAUNCH_CHECK("locate_kernel");
     // 5. candidate union, exact scores and per-pair top-k
     const Shape sh = search_shape(ix, k);
+    DenseArgs da{};                    // tensor paths: what the selects (and the band re-score) read
     if ((rc = mark(LIDER_PHASE_GATHER))) return rc;
     if (sh.mode != LIDER_SCORE_SIMT) {
         const bool h16 = sh.mode == LIDER_SCORE_BF16 || sh.mode == LIDER_SCORE_F16;
@@ -2854,7 +2991,6 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         // 3xTF32 and FP16 paths: a guard band makes the re-scored top k exact;
         // the served BF16 form keeps its approximate shortlist
         const int guarded = sh.mode != LIDER_SCORE_BF16 && sh.mode != LIDER_SCORE_FP8;
-        DenseArgs da;
         da.dense = w.dense;
         da.qbound = w.qbound;
         da.cmax = w.cmax;
@@ -2866,6 +3002,9 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         da.cl_off = g.cl_off;
         da.orig_id = g.orig_id;
         da.ucount = w.pcount;
+        da.ovf = guarded ? w.ovf : nullptr;
+        da.ovf_thr = w.ovf_thr;
+        da.ovf_count = w.ovf_count;
         select_hist_kernel<<<(unsigned)nq, (unsigned)ix->tune.select_threads, 0, st>>>(da, c, sh.ks, w.qguard, w.qbound, guarded, sh.so, w.sl_ids,
                                                          w.sl_scores, tr ? tr->ucount : nullptr, w.redo, w.redo_count,
                                                          w.counters);
@@ -2930,6 +3069,14 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         rescore_kernel<<<(unsigned)nq, (unsigned)ix->tune.rescore_threads, rs_smem, st>>>(Q, g.X, g.row_of, g.d, sh.so, w.sl_ids, k, out_ids,
                                                            out_scores, g.n, &w.counters[CNT_BOUNDS], w.qorder);
         LIDER_LAUNCH_CHECK("rescore_kernel");
+        if (da.ovf) {
+            // the listed queries' whole bands, exactly (returns at once when none is listed)
+            const size_t bd_smem = align_up((size_t)g.d * 4, 16) + (size_t)2 * kBandChunk * 8 + (size_t)kBandChunk * 4;
+            if ((rc = smem_attr((const void*)rescore_band_kernel, (int)bd_smem))) return rc;
+            rescore_band_kernel<<<(unsigned)std::min<int64_t>(nq, 2 * ix->num_sms), 256, bd_smem, st>>>(
+                da, Q, g.X, g.d, c, k, out_ids, out_scores);
+            LIDER_LAUNCH_CHECK("rescore_band_kernel");
+        }
     }
     return mark(LIDER_NUM_PHASES);
 }

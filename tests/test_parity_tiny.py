@@ -248,6 +248,46 @@ def test_massive_ties_take_the_multi_level_select(mode):
 
 
 @pytest.mark.parametrize("mode", [0, 3], ids=["tensor", "f16"])
+def test_near_tied_kth_scores_at_d768_equal_simt(mode):
+    """d = 768: 1,500 rows within 1e-6 of one unit vector (and 300 within
+    1e-6 of its negation) among 4,000, with queries near that vector, so the
+    k-th best score has hundreds of neighbours inside the guard band and
+    scores of opposite sign cancel in the accumulation.  The band holds them
+    all (it outgrows the re-score list, so the second kernel re-scores the
+    whole band) and the exact re-score orders them: ids and scores equal the
+    SIMT path's bit for bit."""
+    import torch
+    rng = np.random.default_rng(31)
+    d, n = 768, 4000
+    base = rng.standard_normal(d)
+    base /= np.linalg.norm(base)
+    X = rng.standard_normal((n, d))
+    X /= np.linalg.norm(X, axis=1, keepdims=True)
+    X[:1500] = base + 1e-6 * rng.standard_normal((1500, d))
+    X[1500:1800] = -base + 1e-6 * rng.standard_normal((300, d))
+    X = X.astype(np.float32)
+    C = np.concatenate([base[None], X[rng.choice(np.arange(1800, n), 5, replace=False)]]).astype(np.float32)
+    cfg = dict(L=2, m=8, W=0.7, leaves=8, r0=100, B=1, k=16)
+    A = rng.standard_normal((cfg["L"] * cfg["m"], d)).astype(np.float32)
+    b = (rng.random(cfg["L"] * cfg["m"]) * cfg["W"]).astype(np.float32)
+    Q = np.concatenate([base + 1e-3 * rng.standard_normal((12, d)),
+                        rng.standard_normal((4, d))]).astype(np.float32)
+    Qd = torch.from_numpy(Q).cuda()
+    out, overflow = {}, 0
+    for m in (mode, 1):
+        g = F.gpu_index(dict(cfg, score_mode=m), X, C, A, b)
+        for c in (1, 3):
+            ids, sc, st = g.search(Qd, cfg["k"], c, stats=True)
+            out[m, c] = (ids.cpu().numpy(), sc.cpu().numpy())
+            overflow += st["select_overflow"] if m == mode else 0
+        g.free()
+    assert mode == 0 or overflow > 0          # the FP16 band outgrows the list
+    for c in (1, 3):
+        assert np.array_equal(out[mode, c][0], out[1, c][0]), c
+        assert np.array_equal(out[mode, c][1].view(np.uint32), out[1, c][1].view(np.uint32)), c
+
+
+@pytest.mark.parametrize("mode", [0, 3], ids=["tensor", "f16"])
 def test_route_with_tied_centroids_equals_simt(mode):
     """Centroids in groups of equal rows (exactly tied routing scores) and of
     rows 1e-7 apart (within the tensor-core error guard): the tensor path

@@ -101,3 +101,44 @@ def test_bounded_wait_runs_out_and_the_device_stays_usable(kind, d):
     out = lider.tc_tile(A, B, kind=0).cpu().numpy().astype(np.float64)
     ref = A.cpu().numpy().astype(np.float64) @ B.cpu().numpy().astype(np.float64).T
     assert np.max(np.abs(out - ref)) < 1e-3
+
+
+def _adversarial_rows(rng, m, n, d):
+    """Operands that stress FP32 accumulation: terms spanning 2^-8..2^8 in
+    magnitude with alternating signs, rows whose second half cancels the
+    first exactly, and rows whose products shrink along K (large partial
+    sums first, then terms near their rounding unit)."""
+    e = rng.integers(-8, 9, size=(m, d)).astype(np.float64)
+    A = np.where(rng.random((m, d)) < 0.5, -1.0, 1.0) * np.exp2(e)
+    B = np.where(rng.random((n, d)) < 0.5, -1.0, 1.0) * np.exp2(rng.integers(-8, 9, size=(n, d)))
+    h = d // 2
+    A[: m // 3, h:2 * h] = -A[: m // 3, :h]                  # exact cancellation against equal B halves
+    B[: n // 3, h:2 * h] = B[: n // 3, :h]
+    decay = np.exp2(-np.floor(np.linspace(0, 16, d)))       # shrinking products along K (powers of two)
+    A[m // 3: 2 * m // 3] *= decay
+    return A.astype(np.float32), B.astype(np.float32)
+
+
+@pytest.mark.parametrize("kind", [0, 2], ids=["tf32x3", "f16"])
+@pytest.mark.parametrize("m,n,d", [(128, 256, 768), (96, 200, 776)])
+def test_tc_tile_accumulation_on_adversarial_operands(kind, m, n, d):
+    """The guard bands assume the tensor cores' FP32 accumulation errs by at
+    most d 2^-23 of the absolute sum of the products (FP16 kind) and 3e-5 |a|
+    |b| (3xTF32, kTcGuard).  Operands built to stress the accumulation
+    (cancellation, wide magnitude spread, absorption) stay within them."""
+    import torch
+    from paper_2205_00970_b300 import lider
+    rng = np.random.default_rng(kind * 100 + m + d)
+    A, B = _adversarial_rows(rng, m, n, d)
+    At, Bt = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    out = lider.tc_tile(At, Bt, kind=kind).cpu().numpy().astype(np.float64)
+    if kind == 2:
+        A64 = At.half().float().cpu().numpy().astype(np.float64)
+        B64 = Bt.half().float().cpu().numpy().astype(np.float64)
+        assert np.array_equal(A64, A.astype(np.float64)) and np.array_equal(B64, B.astype(np.float64))
+        bound = d * 2.0 ** -23 * (np.abs(A64) @ np.abs(B64).T)
+    else:
+        A64, B64 = A.astype(np.float64), B.astype(np.float64)
+        bound = 3e-5 * np.outer(np.linalg.norm(A64, axis=1), np.linalg.norm(B64, axis=1))
+    err = np.abs(out - A64 @ B64.T)
+    assert np.all(err <= bound), float(np.max(err / bound))
