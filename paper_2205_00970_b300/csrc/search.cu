@@ -1432,22 +1432,19 @@ __global__ void __launch_bounds__(256) mark_kernel(const int32_t* __restrict__ p
     for (int64_t i = lane; i < words; i += 32) bits[i] = 0u;
     __syncwarp();
     // window starts of the L arrays loaded at once (L <= 32), then each
-    // window's positions four loads ahead of their shared-memory atomics
+    // window's positions in rounds of up to kMarkBatch loads per lane, all
+    // issued before their shared-memory atomics
+    constexpr int kMarkBatch = 12;
     const int ws_lane = lane < L ? wstart[pair * L + lane] : 0;
     for (int l = 0; l < L; ++l) {
         const int32_t* P = pos + (int64_t)l * n + base + __shfl_sync(0xffffffffu, ws_lane, l);
-        int t = lane;
-        for (; t + 96 < T; t += 128) {
-            const uint32_t p0 = (uint32_t)__ldg(P + t), p1 = (uint32_t)__ldg(P + t + 32);
-            const uint32_t p2 = (uint32_t)__ldg(P + t + 64), p3 = (uint32_t)__ldg(P + t + 96);
-            atomicOr(&bits[p0 >> 5], 1u << (p0 & 31));
-            atomicOr(&bits[p1 >> 5], 1u << (p1 & 31));
-            atomicOr(&bits[p2 >> 5], 1u << (p2 & 31));
-            atomicOr(&bits[p3 >> 5], 1u << (p3 & 31));
-        }
-        for (; t < T; t += 32) {
-            const uint32_t p = (uint32_t)__ldg(P + t);
-            atomicOr(&bits[p >> 5], 1u << (p & 31));
+        for (int t0 = lane; t0 < T; t0 += 32 * kMarkBatch) {
+            uint32_t pv[kMarkBatch];
+#pragma unroll
+            for (int r = 0; r < kMarkBatch; ++r) pv[r] = t0 + 32 * r < T ? (uint32_t)__ldg(P + t0 + 32 * r) : ~0u;
+#pragma unroll
+            for (int r = 0; r < kMarkBatch; ++r)
+                if (pv[r] != ~0u) atomicOr(&bits[pv[r] >> 5], 1u << (pv[r] & 31));
         }
     }
     __syncwarp();
@@ -2182,6 +2179,7 @@ __global__ void __launch_bounds__(512) select_hist_kernel(
     __shared__ float s_thr;
     __shared__ uint32_t s_rhist[256];              // radix select
     __shared__ int s_pick[2];
+    __shared__ int s_wo[LIDER_MAX_C + 1];          // first chunk-maximum word of each pair
     const int64_t q = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31;
     for (int b = tid; b < kHistBins; b += blockDim.x) hist[b] = 0u;
@@ -2228,15 +2226,47 @@ __global__ void __launch_bounds__(512) select_hist_kernel(
     bool small_lists = true;                        // positions fit the (list, position) packing
     for (int p = 0; p < c; ++p) small_lists = small_lists && s_pr[p].n_c < (1 << 27);
     const bool by_max = need > 0 && need <= kKeep * bd && small_lists;
+    // The chunk maxima of the c pairs as one sequence of words: word g is
+    // word g - s_wo[p] of pair p, for the p with s_wo[p] <= g < s_wo[p + 1].
+    // The scans below take kBatch words per thread per round, their loads
+    // issued before any is used.
+    constexpr int kBatch = 4;
+    if (tid == 0) {
+        int o = 0;
+        for (int p = 0; p < c; ++p) {
+            s_wo[p] = o;
+            o += (s_pr[p].n_c + 31) >> 5;
+        }
+        s_wo[c] = o;
+    }
+    __syncthreads();
+    const int n_words = s_wo[c];
+    // (pair, word) of word g; p is a hint, never past g's pair (the scans
+    // below visit each thread's words in increasing order)
+    auto word_at = [&](int g, int& p, int& w) {
+        while (g >= s_wo[p + 1]) ++p;
+        w = g - s_wo[p];
+    };
     if (by_max) {
         float ts[kKeep];
 #pragma unroll
         for (int j = 0; j < kKeep; ++j) ts[j] = -INFINITY;
-        for (int p = 0; p < c; ++p) {
-            const PairRow pr = s_pr[p];
-            const int nw = (pr.n_c + 31) >> 5;
-            for (int w = tid; w < nw; w += bd) {
-                float vv = __ldg(pr.cm + w);
+        int hp = 0;                                 // this thread's current pair
+        for (int g0 = tid; g0 < n_words; g0 += kBatch * bd) {
+            float vb[kBatch];
+#pragma unroll
+            for (int r = 0; r < kBatch; ++r) {
+                const int g = g0 + r * bd;
+                vb[r] = -INFINITY;
+                if (g < n_words) {
+                    int w;
+                    word_at(g, hp, w);
+                    vb[r] = __ldg(s_pr[hp].cm + w);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < kBatch; ++r) {
+                float vv = vb[r];
 #pragma unroll
                 for (int j = 0; j < kKeep; ++j) {   // insert, best first
                     if (vv > ts[j]) {
@@ -2268,11 +2298,23 @@ __global__ void __launch_bounds__(512) select_hist_kernel(
         const float thr = s_thr;
         // read the chunks whose maximum clears the threshold; a thread reserves
         // its chunk's keys with one atomic
-        for (int p = 0; p < c; ++p) {
-            const PairRow pr = s_pr[p];
-            const int nw = (pr.n_c + 31) >> 5;
-            for (int w = tid; w < nw; w += bd) {
-                if (!(__ldg(pr.cm + w) >= thr)) continue;
+        int hq = 0;                                 // this thread's current pair
+        for (int g0 = tid; g0 < n_words; g0 += kBatch * bd) {
+            uint32_t hit = 0u;                          // bit r: word g0 + r bd clears thr
+            const int hq0 = hq;
+#pragma unroll
+            for (int r = 0; r < kBatch; ++r) {
+                const int g = g0 + r * bd;
+                if (g < n_words) {
+                    int w;
+                    word_at(g, hq, w);
+                    if (__ldg(s_pr[hq].cm + w) >= thr) hit |= 1u << r;
+                }
+            }
+            for (int p = hq0; hit; hit &= hit - 1) {
+                int w;
+                word_at(g0 + (__ffs(hit) - 1) * bd, p, w);
+                const PairRow pr = s_pr[p];
                 const uint32_t bw = __ldg(pr.bm + w);
                 float v[32];
 #pragma unroll
