@@ -1024,12 +1024,16 @@ def run_precision(args, cfg):
     for name, r in out.items():
         top = r["ids"][:, :10]
         agree = np.mean([len(set(top[i].tolist()) & set(plain[i].tolist())) / 10 for i in range(nq)])
-        err = 0.0
+        err, n_scores = 0.0, 0
         for i in range(ns):
             sel = r["ids"][i][r["ids"][i] >= 0]
+            if not len(sel):
+                continue
             ex = X[sel].astype(np.float64) @ q64[i]
             got = r["scores"][i][:len(sel)].astype(np.float64)
-            err = max(err, float(np.max(np.abs(got - ex) / np.maximum(np.abs(ex), 1e-30))) if len(sel) else 0.0)
+            rel = np.abs(got - ex) / np.maximum(np.abs(ex), 1e-30)
+            err = max(err, float(np.max(rel)) if np.all(np.isfinite(rel)) else float("inf"))
+            n_scores += len(sel)
         base, rr = (name.split("@") + ["0"])[:2]
         report[name] = {
             "queries_per_s": nq / (r["ms"] / 1e3), "ms_per_batch": r["ms"], "queries_per_call": r["sub"],
@@ -1039,6 +1043,7 @@ def run_precision(args, cfg):
             "recall_at_10_vs_plain": float(agree),
             "recall_at_10_vs_fp64_knn": recall10(r["ids"][:ns], truth),
             "max_rel_score_error_vs_fp64": err,
+            "scores_checked": n_scores,
         }
     line = {
         "metric": "recall@10 and score error per dtype; queries/s", "n_gpus": 1, "steps": args.steps,
