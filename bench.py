@@ -596,6 +596,7 @@ def run_lider(args, cfg):
         search_host_all()
     e2e_s = max_over_ranks(time.perf_counter() - te, dev)
     e2e_value = job_throughput(nq, args.steps, world, e2e_s * 1e3)
+    link = host_link_rates(Qh, int(nq * k * (8 + 4)), dev)
 
     roofline = score_roofline(args.score, stats, route, idx.cluster_offsets(), cfg["d"], phase_ms["score"] / 1e3,
                               clk)
@@ -621,7 +622,8 @@ def run_lider(args, cfg):
         "search_stats": stats,
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": int(Q.nbytes),
-                "d2h_bytes_per_step": int(nq * k * (8 + 4))},
+                "d2h_bytes_per_step": int(nq * k * (8 + 4)), "ms_per_step": e2e_s * 1e3 / args.steps,
+                "host_link": link},
         "gpu_launches": LAUNCHES_PER_SEARCH[args.score] * passes * args.steps,
         "graph_replay": graph,
         "tuning": tuning,
@@ -798,6 +800,31 @@ def fp64_knn(X, Q, k: int, chunk: int = 262_144, device: str = "cuda:0") -> np.n
         o2 = torch.argsort(-cs, dim=1, stable=True)[:, :k]
         best_s, best_i = cs.gather(1, o2), ci.gather(1, o2)
     return best_i.cpu().numpy()
+
+
+def host_link_rates(Qh, d2h_bytes: int, dev) -> dict:
+    """Plain pinned copies of one step's bytes (the queries in, a buffer of
+    the results' size out), timed with CUDA events: the host link's rate, and
+    the step's transfer time at that rate if nothing overlapped."""
+    import torch
+    src = Qh if Qh.is_pinned() else Qh.pin_memory()
+    dbuf = torch.empty(src.shape, dtype=src.dtype, device=dev)
+    hout = torch.empty(d2h_bytes, dtype=torch.uint8).pin_memory()
+    dout = torch.empty(d2h_bytes, dtype=torch.uint8, device=dev)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for _ in range(2):
+        dbuf.copy_(src, non_blocking=True)
+        hout.copy_(dout, non_blocking=True)
+    torch.cuda.synchronize()
+    e[0].record()
+    dbuf.copy_(src, non_blocking=True)
+    e[1].record()
+    hout.copy_(dout, non_blocking=True)
+    e[2].record()
+    torch.cuda.synchronize()
+    h2d_ms, d2h_ms = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    return {"h2d_gbs": src.numel() * src.element_size() / h2d_ms / 1e6, "d2h_gbs": d2h_bytes / d2h_ms / 1e6,
+            "copy_ms_per_step": h2d_ms + d2h_ms}
 
 
 def recall10(found: np.ndarray, truth: np.ndarray) -> float:

@@ -11,8 +11,6 @@
 #include <cstring>
 #include <memory>
 #include <string>
-#include <thread>
-#include <vector>
 
 #include "lider_internal.cuh"
 #include "server_core.h"
@@ -25,42 +23,6 @@ int search_scratch_entry(const lider_index*, int64_t, int, int, size_t*);
 const char* g_last_error_ptr();
 
 namespace {
-
-// Host copies of a batch (its requests' queries into the pinned staging, or
-// its results back into the requests' buffers): the bytes of all jobs, taken
-// in order, are split evenly over up to kCopyThreads threads; small batches
-// copy on the calling thread.
-struct CopyJob {
-    void* dst;
-    const void* src;
-    size_t bytes;
-};
-constexpr int kCopyThreads = 4;
-constexpr size_t kParallelCopyBytes = (size_t)4 << 20;
-
-void copy_jobs(const std::vector<CopyJob>& jobs) {
-    size_t total = 0;
-    for (const CopyJob& j : jobs) total += j.bytes;
-    auto part = [&](int t, int nt) {
-        const size_t lo = total * t / nt, hi = total * (t + 1) / nt;
-        size_t off = 0;
-        for (const CopyJob& j : jobs) {
-            const size_t a = std::max(lo, off), b = std::min(hi, off + j.bytes);
-            if (a < b)
-                std::memcpy(static_cast<char*>(j.dst) + (a - off), static_cast<const char*>(j.src) + (a - off), b - a);
-            off += j.bytes;
-            if (off >= hi) break;
-        }
-    };
-    if (total < kParallelCopyBytes) {
-        part(0, 1);
-        return;
-    }
-    std::vector<std::thread> helpers;
-    for (int t = 1; t < kCopyThreads; ++t) helpers.emplace_back(part, t, kCopyThreads);
-    part(0, kCopyThreads);
-    for (std::thread& h : helpers) h.join();
-}
 
 struct Slot {
     cudaStream_t stream = nullptr;
@@ -125,14 +87,11 @@ class CudaExecutor final : public serve::Executor {
         if (e != cudaSuccess) return cuda_batch(b, e, "cudaSetDevice");
         Slot& s = slots_[b.slot];
         const int64_t d = ix_->g.d;
-        std::vector<CopyJob> jobs;
-        jobs.reserve(b.reqs.size());
         float* dst = s.q_host;
         for (const serve::Request& r : b.reqs) {
-            jobs.push_back({dst, r.queries, (size_t)r.nq * d * 4});
+            std::memcpy(dst, r.queries, (size_t)r.nq * d * 4);
             dst += r.nq * d;
         }
-        copy_jobs(jobs);
         // a failed batch returns its slot at once: drain what it enqueued first
         auto drained = [&](int rc) {
             cudaStreamSynchronize(s.stream);
@@ -160,15 +119,12 @@ class CudaExecutor final : public serve::Executor {
         const int64_t k = b.k;
         const int64_t* ids = s.ids_host;
         const float* sc = s.scores_host;
-        std::vector<CopyJob> jobs;
-        jobs.reserve(2 * b.reqs.size());
         for (const serve::Request& r : b.reqs) {
-            jobs.push_back({r.ids, ids, (size_t)r.nq * k * 8});
-            jobs.push_back({r.scores, sc, (size_t)r.nq * k * 4});
+            std::memcpy(r.ids, ids, (size_t)r.nq * k * 8);
+            std::memcpy(r.scores, sc, (size_t)r.nq * k * 4);
             ids += r.nq * k;
             sc += r.nq * k;
         }
-        copy_jobs(jobs);
         return LIDER_OK;
     }
 
