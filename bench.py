@@ -511,48 +511,43 @@ def run_lider(args, cfg):
     for _ in range(args.warmup):
         search_all()
     nph = lider.NUM_PHASES + 1
-    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(nph)] for _ in chunks] for _ in range(args.steps)]
-    for step in evs:
-        for row in step:
-            for e in row:
-                e.record()
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # the timed steps run the plain lider_search calls; events mark only the
+    # steps' boundaries (phase events inside a search cost it time)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    for e in evs:
+        e.record()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clocks = ClockSampler(local, args.clocks_dir)
     clocks.start()
     time.sleep(0.3)
-    t0.record()
+    evs[0].record()
     for s in range(args.steps):
-        for ci, (lo, hi) in enumerate(chunks):
-            idx.search_phased(Qd[lo:hi], k, c, evs[s][ci], out=(ids[lo:hi], sc[lo:hi]))
-    t1.record()
+        search_all()
+        evs[s + 1].record()
     torch.cuda.synchronize()
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
-    total_ms = t0.elapsed_time(t1)
-    step_ms = [evs[s][0][0].elapsed_time(evs[s][-1][nph - 1]) for s in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    step_ms = [evs[s].elapsed_time(evs[s + 1]) for s in range(args.steps)]
     passes = stats.get("passes", len(chunks))
-    if passes <= len(chunks):
-        phase_ms = {name: float(np.mean([sum(evs[s][ci][i].elapsed_time(evs[s][ci][i + 1])
-                                             for ci in range(len(chunks))) for s in range(args.steps)]))
-                    for i, name in enumerate(lider.PHASES)}
-        phase_of = "every call of the timed steps"
-    else:
-        # the library searched each call in passes: the phases come from an
-        # untimed run of the same passes, one call per pass
-        pb = -(-nq // (passes // len(chunks)))
-        pev = [[torch.cuda.Event(enable_timing=True) for _ in range(nph)] for _ in range(0, nq, pb)]
-        for row in pev:
-            for e in row:
-                e.record()          # creates the event, so the library gets a handle to record
-        for pi, lo in enumerate(range(0, nq, pb)):
-            idx.search_phased(Qd[lo:lo + pb], k, c, pev[pi], out=(ids[lo:lo + pb], sc[lo:lo + pb]))
-        torch.cuda.synchronize()
-        phase_ms = {name: float(sum(ev[i].elapsed_time(ev[i + 1]) for ev in pev)) for i, name in enumerate(lider.PHASES)}
-        phase_of = f"an untimed run of the {len(pev)} passes of {pb:,} queries, one call each"
+    # the phases: an untimed run of the same search, one call per pass, with
+    # the library recording events at its phase boundaries
+    per_call = max(1, passes // len(chunks))
+    pb = -(-min(hi - lo for lo, hi in chunks) // per_call) if passes > len(chunks) else None
+    calls = [(a, min(hi, a + pb)) for lo, hi in chunks for a in range(lo, hi, pb)] if pb else list(chunks)
+    pev = [[torch.cuda.Event(enable_timing=True) for _ in range(nph)] for _ in calls]
+    for row in pev:
+        for e in row:
+            e.record()              # creates the event, so the library gets a handle to record
+    for pi, (lo, hi) in enumerate(calls):
+        idx.search_phased(Qd[lo:hi], k, c, pev[pi], out=(ids[lo:hi], sc[lo:hi]))
+    torch.cuda.synchronize()
+    phase_ms = {name: float(sum(ev[i].elapsed_time(ev[i + 1]) for ev in pev)) for i, name in enumerate(lider.PHASES)}
+    phase_of = (f"an untimed run of the same search, {len(calls)} call(s) of "
+                f"{max(hi - lo for lo, hi in calls):,} queries with phase events")
     total_ms = max_over_ranks(total_ms, dev)
     value = job_throughput(nq, args.steps, world, total_ms)
 
