@@ -318,15 +318,16 @@ class Index:
 
     def search_phased(self, Q: torch.Tensor, k: int, c: int, events, stream=None, out=None):
         """lider_search that records NUM_PHASES + 1 torch.cuda.Events (already
-        created, e.g. recorded once) at the phase boundaries on the stream."""
+        created, e.g. recorded once) at the phase boundaries on the stream;
+        a None entry skips that boundary."""
         Q = _dev(Q, torch.float32, "queries")
         nq = Q.shape[0]
         ids, sc = out if out is not None else (
             torch.empty((nq, k), dtype=torch.int64, device=Q.device),
             torch.empty((nq, k), dtype=torch.float32, device=Q.device))
-        handles = [e.cuda_event for e in events]
-        if len(handles) != NUM_PHASES + 1 or not all(handles):
-            raise ValueError(f"search_phased needs {NUM_PHASES + 1} created events (record each once first)")
+        handles = [e.cuda_event if e is not None else 0 for e in events]
+        if len(handles) != NUM_PHASES + 1 or not all(h for h, e in zip(handles, events) if e is not None):
+            raise ValueError(f"search_phased needs {NUM_PHASES + 1} created events or None (record each once first)")
         arr = (ctypes.c_void_p * (NUM_PHASES + 1))(*handles)
         tr = Trace(None, None, None, None, None, None, ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)))
         _check(_lib.lider_search_trace(self._h, Q.data_ptr(), nq, k, c, ids.data_ptr(), sc.data_ptr(),
