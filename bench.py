@@ -736,6 +736,9 @@ def run_serve(args, cfg):
                  mem_budget=args.serve_mem_gb << 30, max_wait_us=args.serve_wait_us)
     nq = Q.shape[0]
     warm = poisson_schedule(args.serve, 0.5, ks=ks, max_req=args.serve_max_req, n_queries=nq, seed=1)
+    # the requests' queries live in pinned host memory, so the server copies
+    # them to the device directly
+    Q = torch.from_numpy(Q).pin_memory().numpy()
     for *_, tk in run_load(srv, Q, warm):
         tk.result()
     srv.latencies_ms(clear=True)

@@ -6,8 +6,9 @@
 // same sizes.  A batch gathers its requests' queries into the slot's pinned
 // buffer, copies them to the device, runs lider_search's kernels (scratch from
 // the index's stream-ordered pool) and copies the results back, all on the
-// slot's stream; finishing waits on the slot's event and scatters the rows to
-// the requests' host buffers.
+// slot's stream (queries already in pinned host memory are copied directly);
+// finishing waits on the slot's event and scatters the rows to the requests'
+// host buffers.
 #include <cstring>
 #include <memory>
 #include <string>
@@ -87,19 +88,37 @@ class CudaExecutor final : public serve::Executor {
         if (e != cudaSuccess) return cuda_batch(b, e, "cudaSetDevice");
         Slot& s = slots_[b.slot];
         const int64_t d = ix_->g.d;
-        float* dst = s.q_host;
-        for (const serve::Request& r : b.reqs) {
-            std::memcpy(dst, r.queries, (size_t)r.nq * d * 4);
-            dst += r.nq * d;
-        }
         // a failed batch returns its slot at once: drain what it enqueued first
         auto drained = [&](int rc) {
             cudaStreamSynchronize(s.stream);
             cudaGetLastError();
             return rc;
         };
-        if ((e = cudaMemcpyAsync(s.q_dev, s.q_host, (size_t)b.nq * d * 4, cudaMemcpyHostToDevice, s.stream)))
-            return drained(cuda_batch(b, e, "cudaMemcpyAsync(queries)"));
+        // Queries in pinned host memory are copied to the device directly;
+        // the others are gathered into the slot's pinned staging first, each
+        // run of consecutive such requests in one copy.
+        int64_t off = 0, run = 0;            // the pending staged run: rows [off - run, off)
+        auto flush = [&]() -> cudaError_t {
+            if (run == 0) return cudaSuccess;
+            const size_t r0 = (size_t)(off - run) * d;
+            const cudaError_t ce = cudaMemcpyAsync(s.q_dev + r0, s.q_host + r0, (size_t)run * d * 4,
+                                                   cudaMemcpyHostToDevice, s.stream);
+            run = 0;
+            return ce;
+        };
+        for (const serve::Request& r : b.reqs) {
+            const size_t bytes = (size_t)r.nq * d * 4;
+            if (pinned(r.queries)) {
+                if ((e = flush()) == cudaSuccess)
+                    e = cudaMemcpyAsync(s.q_dev + (size_t)off * d, r.queries, bytes, cudaMemcpyHostToDevice, s.stream);
+                if (e != cudaSuccess) return drained(cuda_batch(b, e, "cudaMemcpyAsync(queries)"));
+            } else {
+                std::memcpy(s.q_host + (size_t)off * d, r.queries, bytes);
+                run += r.nq;
+            }
+            off += r.nq;
+        }
+        if ((e = flush())) return drained(cuda_batch(b, e, "cudaMemcpyAsync(queries)"));
         const int rc = search_entry(ix_, s.q_dev, b.nq, b.k, c_, s.ids_dev, s.scores_dev, nullptr, nullptr,
                                     s.stream);
         if (rc != LIDER_OK) return drained(fail_batch(b, rc, g_last_error_ptr()));
@@ -129,6 +148,15 @@ class CudaExecutor final : public serve::Executor {
     }
 
   private:
+    // Whether p points into page-locked host memory (copies from it are DMA).
+    static bool pinned(const void* p) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return at.type == cudaMemoryTypeHost;
+    }
     static int fail_batch(serve::Batch& b, int code, const std::string& msg) {
         b.error = msg;
         return code;

@@ -73,6 +73,37 @@ def test_served_mix_equals_alone(mode):
 
 
 @pytest.mark.gpu
+def test_pinned_and_pageable_requests_in_one_batch():
+    """Requests alternating between pinned queries (copied to the device
+    directly) and pageable ones (gathered into the slot's staging) share
+    batches; each result equals the same request searched alone."""
+    import torch
+    from paper_2205_00970_b300.serving import Server, poisson_schedule
+    from tests.lider_fixtures import gpu_index, workload
+
+    cfg, X, Q, C, A, b = workload("tiny")
+    cfg = dict(cfg, score_mode=3)
+    ix = gpu_index(cfg, X, C, A, b)
+    Qp = torch.from_numpy(Q).pin_memory().numpy()
+    srv = Server(ix, cfg["c"], slots=2, max_batch=512, max_k=20, mem_budget=256 << 20, max_wait_us=2000)
+    _, size, ks, off = poisson_schedule(300000, 0.2, ks=(10, 20), max_req=64, n_queries=Q.shape[0], seed=3)
+    sent = []
+    for i in range(len(size)):
+        src = Qp if i % 2 else Q
+        o, n, k = int(off[i]), int(size[i]), int(ks[i])
+        sent.append((o, n, k, srv.submit(src[o:o + n], k)))
+    results = [(o, n, k, t.result(timeout=60)) for o, n, k, t in sent]
+    st = srv.stats()
+    srv.close()
+    assert st["failed"] == 0 and st["batches"] < len(sent)
+    for o, n, k, (ids, sc) in results:
+        ai, asc = ix.search(torch.from_numpy(Q[o:o + n]).cuda(), k, cfg["c"])
+        assert np.array_equal(ids, ai.cpu().numpy()), (o, n, k)
+        assert np.array_equal(sc, asc.cpu().numpy()), (o, n, k)
+    ix.free()
+
+
+@pytest.mark.gpu
 def test_server_refusals_and_drain():
     from paper_2205_00970_b300 import lider
     from paper_2205_00970_b300.serving import Server
