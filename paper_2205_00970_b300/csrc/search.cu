@@ -2118,14 +2118,16 @@ constexpr int kHistBins = 2048;
 constexpr int kHistCand = 2048;
 
 // The r-th smallest (1-based, counting repeats) of n 32-bit words word(i),
-// i < n, by a block-wide radix select: four passes over 8-bit digits, most
+// i < n, by a block-wide radix select: passes over 8-bit digits, most
 // significant first, each counting the words that match the digits chosen so
 // far in a 256-bin shared histogram.  All threads call it; r in [1, n].
+// With fewer than four passes the result is the largest word sharing the
+// r-th smallest word's leading digits: an upper bound on it.
 template <class Word>
-__device__ uint32_t block_kth_smallest(Word word, int n, int r, uint32_t* hist256, int* s_pick) {
+__device__ uint32_t block_kth_smallest(Word word, int n, int r, uint32_t* hist256, int* s_pick, int passes = 4) {
     const int tid = threadIdx.x, lane = tid & 31;
     uint32_t prefix = 0u, mask = 0u;
-    for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int shift = 24; shift >= 32 - 8 * passes; shift -= 8) {
         for (int b = tid; b < 256; b += blockDim.x) hist256[b] = 0u;
         __syncthreads();
         for (int i = tid; i < n; i += blockDim.x) {
@@ -2165,7 +2167,7 @@ __device__ uint32_t block_kth_smallest(Word word, int n, int r, uint32_t* hist25
         r = s_pick[1];
         __syncthreads();                           // every thread has read s_pick
     }
-    return prefix;
+    return passes >= 4 ? prefix : prefix | ((1u << (32 - 8 * passes)) - 1u);
 }
 
 __global__ void __launch_bounds__(512) select_hist_kernel(
@@ -2284,7 +2286,9 @@ __global__ void __launch_bounds__(512) select_hist_kernel(
         for (int j = 0; j < kKeep; ++j) hist[tid * kKeep + j] = ts[j] == -INFINITY ? 0xffffffffu : ~float_order(ts[j]);
         __syncthreads();
         // the need-th best kept maximum (need <= kKeep * bd words)
-        const uint32_t wk = block_kth_smallest([&](int i) { return hist[i]; }, kKeep * bd, need, s_rhist, s_pick);
+        // (three digits: an upper bound on the word, i.e. a threshold at most
+        // 2^8 float steps lower, which only reads a few more chunks)
+        const uint32_t wk = block_kth_smallest([&](int i) { return hist[i]; }, kKeep * bd, need, s_rhist, s_pick, 3);
         if (tid == 0) {
             float thr = -INFINITY;                 // fewer chunks with candidates than need: take all
             if (wk != 0xffffffffu) {
@@ -2454,8 +2458,10 @@ __global__ void __launch_bounds__(512) select_hist_kernel(
         // select over the keys' score words; only a band longer than the list
         // (counted as an overflow) needs the sort below to keep the best `so`.
         const int keep0 = min(need, n);
+        // (three digits: the band's bound at most 2^8 float steps lower, so
+        // the band keeps every key it needs and at most a few more)
         const uint32_t wk = block_kth_smallest([&](int i) { return (uint32_t)(cand[i] >> 32); }, n, keep0,
-                                               s_rhist, s_pick);
+                                               s_rhist, s_pick, 3);
         const float t = float_from_order(~wk) - 2.f * qguard[q];
         if (tid == 0) { s_band = 0; s_bt = 0; }
         __syncthreads();
