@@ -424,8 +424,10 @@ typedef struct {
                                  tiles outer (a row tile's query tiles run together)   */
     int32_t probe_batch;      /* queries per pass of lider_search (>= 0; 0: the whole
                                  batch); a batch larger than one pass allows (the caps
-                                 of LIDER_ELIMIT, or 48 GiB of scratch) is searched in
-                                 passes of half as many, halved until one fits      */
+                                 of LIDER_ELIMIT, or a scratch budget of 48 GiB and at
+                                 most 3/4 of the device memory free after the build)
+                                 is searched in passes of half as many, halved until
+                                 one fits                                           */
 } lider_tuning;
 
 /* Current launch shapes of the index (host output). */

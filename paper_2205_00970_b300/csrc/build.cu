@@ -797,6 +797,13 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
         for (int j = 0; j < ncl; ++j) ix->top_words[j + 1] = ix->top_words[j] + wv[j];
     }
 #undef ALLOC
+    {
+        // a pass's scratch stays within 48 GiB and 3/4 of the device memory
+        // left free once the index is built
+        size_t free_b = 0, total_b = 0;
+        LIDER_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+        ix->pass_budget = std::min<size_t>((size_t)48 << 30, free_b / 4 * 3);
+    }
     ix->build_ms = std::chrono::duration<double, std::milli>(clock::now() - t_start).count();
     guard.ix = nullptr;
     *out = ix;

@@ -126,6 +126,7 @@ struct lider_index {
     bool projections_drawn = false;     // A and b were drawn from the seed
     double kmeans_ms = 0.0;             // host wall time of the k-means iterations
     double build_ms = 0.0;              // host wall time of the whole build
+    size_t pass_budget = 0;             // search scratch one pass may take (set at the end of the build)
     lider_tuning tune{128, 128, 64, 1, 0};    // launch shapes (lider_autotune; defaults measured on mid)
     int score_blocks_per_sm = 1;
     int num_sms = 148;

@@ -2797,17 +2797,16 @@ int check_search_args(const lider_index* ix, const float* Q, int64_t nq, int k, 
 
 // Queries per pass of lider_search: the tuning's probe_batch (0: the whole
 // batch), halved until a pass meets the per-pass caps and its scratch stays
-// within kPassScratchBytes.  The scratch of a pass is sized for the worst case
+// within the index's pass budget (48 GiB, and 3/4 of the device memory left
+// free after the build).  The scratch of a pass is sized for the worst case
 // (every query probing the c largest clusters).
-constexpr size_t kPassScratchBytes = (size_t)48 << 30;
-
 int64_t pass_size(const lider_index* ix, int64_t nq, int k, int c) {
     int64_t pb = ix->tune.probe_batch > 0 ? std::min<int64_t>(nq, ix->tune.probe_batch) : nq;
     while (pb > 1) {
         const bool fits = (pb * c <= (int64_t)INT32_MAX) &&
                           (ix->params.score_mode == LIDER_SCORE_SIMT ||
                            (pb * ix->g.H <= (int64_t)INT32_MAX && pb * ix->top_words[c] <= ((int64_t)1 << 30))) &&
-                          carve(nullptr, ix->g, pb, c, search_shape(ix, k, pb, c)).total <= kPassScratchBytes;
+                          carve(nullptr, ix->g, pb, c, search_shape(ix, k, pb, c)).total <= ix->pass_budget;
         if (fits) break;
         pb = (pb + 1) / 2;
     }
