@@ -130,3 +130,27 @@ def test_mid_served_forms(mid, mode, rerank, min10, min100):
     agree10 = np.mean([len(set(ids[i, :10].tolist()) & set(mid["ids"][i, :10].tolist())) / 10 for i in range(len(Q))])
     agree = np.mean([len(set(ids[i].tolist()) & set(mid["ids"][i].tolist())) / cfg["k"] for i in range(len(Q))])
     assert agree10 >= min10 and agree >= min100, (agree10, agree)
+
+
+def test_mid_recall_at_10_against_brute_force(mid):
+    """The whole search at the mid configuration finds at least 90% of each
+    query's true top-10 (FP64 brute force over all 1,000,000 rows, ties to
+    the lower id), on 512 queries spread over the batch."""
+    rows = np.arange(0, 10000, 10000 // 512)[:512]
+    X, Q = mid["X"], mid["Q"]
+    # brute force in slabs of the corpus: FP64 scores, top 10 by (score desc, id asc)
+    best_s = np.full((len(rows), 0), 0.0)
+    best_i = np.zeros((len(rows), 0), dtype=np.int64)
+    q64 = Q[rows].astype(np.float64)
+    for lo in range(0, X.shape[0], 100_000):
+        s = q64 @ X[lo:lo + 100_000].astype(np.float64).T
+        i = np.broadcast_to(np.arange(lo, lo + s.shape[1]), s.shape)
+        cs, ci = np.concatenate([best_s, s], 1), np.concatenate([best_i, i], 1)
+        o = np.lexsort((ci, -cs), axis=1)[:, :10]
+        best_s, best_i = np.take_along_axis(cs, o, 1), np.take_along_axis(ci, o, 1)
+    got = mid["ids"][rows, :10]
+    rec = np.mean([len(set(g.tolist()) & set(t.tolist())) / 10 for g, t in zip(got, best_i)])
+    assert rec >= 0.9, rec
+    # the brute force itself agrees with the oracle's exact kNN on a few queries
+    tid, _ = O.exact_knn(X, Q[rows[:3]], 10)
+    assert np.array_equal(tid, best_i[:3])
