@@ -408,6 +408,7 @@ void release(lider_index* ix) {
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (ix->pool) cudaMemPoolDestroy(ix->pool);
+    if (ix->side) cudaStreamDestroy(ix->side);
     delete ix;
 }
 
@@ -804,6 +805,7 @@ int build_impl(const float* corpus, int64_t n, int32_t d, const float* centroids
         LIDER_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
         ix->pass_budget = std::min<size_t>((size_t)48 << 30, free_b / 4 * 3);
     }
+    LIDER_CUDA_TRY(cudaStreamCreateWithFlags(&ix->side, cudaStreamNonBlocking));
     ix->build_ms = std::chrono::duration<double, std::milli>(clock::now() - t_start).count();
     guard.ix = nullptr;
     *out = ix;

@@ -120,6 +120,7 @@ struct lider_index {
     lider::RmiRoot* croot = nullptr;    // L
     lider::RmiLeaf* cleaf = nullptr;    // L x F
     cudaMemPool_t pool = nullptr;
+    cudaStream_t side = nullptr;        // second stream for the search's independent steps
     // how the index was built (lider_build_info)
     lider_cluster_params cluster{};     // k-means parameters (clustered only)
     bool clustered = false;             // k-means ran inside the build

@@ -2840,6 +2840,31 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
 
     // 1-2. hash and route, chunk by chunk: queries [q0, q1)
     const bool tensor_route = ix->params.score_mode != LIDER_SCORE_SIMT;
+    // Tensor paths: steps that depend only on earlier ones run on the index's
+    // second stream beside the main one (the hash recheck and the key packing
+    // beside the top-c and the grouping; the queries' gather and the tile
+    // descriptors beside the locate and the marking), joined by events.
+    const bool fork = tensor_route && ix->side && ix->params.route_kind != LIDER_ROUTE_CORE;
+    struct Events {
+        cudaEvent_t e[4] = {};
+        ~Events() {
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } fe_ev;
+    if (fork)
+        for (cudaEvent_t& x : fe_ev.e) LIDER_CUDA_TRY(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
+    cudaStream_t side = fork ? ix->side : st;
+    auto fork_to_side = [&](cudaEvent_t ev) -> int {      // the side stream continues after st's work so far
+        LIDER_CUDA_TRY(cudaEventRecord(ev, st));
+        LIDER_CUDA_TRY(cudaStreamWaitEvent(side, ev, 0));
+        return LIDER_OK;
+    };
+    auto join_side = [&](cudaEvent_t ev) -> int {         // st continues after the side stream's work so far
+        LIDER_CUDA_TRY(cudaEventRecord(ev, side));
+        LIDER_CUDA_TRY(cudaStreamWaitEvent(st, ev, 0));
+        return LIDER_OK;
+    };
     // SIMT mode: Dot2 hash values, then exact FP64 routing scores and top-c
     auto simt_chunk = [&](int64_t q0, int64_t q1, bool last) -> int {
         const int64_t n = q1 - q0;
@@ -2914,16 +2939,17 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
     }
     // hash values too close to a bucket edge for the tiles' error, recomputed
     // exactly; then the packed keys of the whole batch
+    if (fork && (rc = fork_to_side(fe_ev.e[0]))) return rc;
     if (tensor_route) {
-        hash_recheck_kernel<<<(unsigned)(16 * ix->num_sms), 32, (size_t)2 * g.d * sizeof(float), st>>>(
+        hash_recheck_kernel<<<(unsigned)(16 * ix->num_sms), 32, (size_t)2 * g.d * sizeof(float), side>>>(
             Q, g.A, g.bproj, g.W, g.d, g.H, w.hrecheck, w.n_hrecheck, w.tq);
         LIDER_LAUNCH_CHECK("hash_recheck_kernel");
     }
     if ((rc = launch_pack(w.tq, nq, g.L, g.m, g.beta, g.hash_kind, 0, g.L, 1, w.qkeys, &w.counters[CNT_QBOUNDARY],
-                          &w.counters[CNT_QCLAMPED], st)))
+                          &w.counters[CNT_QCLAMPED], side)))
         return rc;
     if (tr && tr->qkeys)
-        LIDER_CUDA_TRY(cudaMemcpyAsync(tr->qkeys, w.qkeys, (size_t)nq * g.L * 8, cudaMemcpyDeviceToDevice, st));
+        LIDER_CUDA_TRY(cudaMemcpyAsync(tr->qkeys, w.qkeys, (size_t)nq * g.L * 8, cudaMemcpyDeviceToDevice, side));
     if (ix->params.route_kind == LIDER_ROUTE_CORE) {
         // Layer-1 centroids retriever: replaces the route of the exact scan
         // (whose per-query error bounds the tensor paths still use)
@@ -2947,6 +2973,9 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
     LIDER_LAUNCH_CHECK("group_scan_kernel");
     group_fill_kernel<<<(unsigned)cdiv(np, 256), 256, 0, st>>>(w.route, np, w.cursor, w.pairs);
     LIDER_LAUNCH_CHECK("group_fill_kernel");
+    // the side stream: hash recheck and packing done, now the pairs exist
+    if (fork && (rc = join_side(fe_ev.e[1]))) return rc;
+    if (fork && (rc = fork_to_side(fe_ev.e[2]))) return rc;
     if (w.qorder) {
         primary_order_kernel<<<(unsigned)g.ncl, 256, 0, st>>>(w.pairs, w.off, c, w.qorder, &w.counters[CNT_QORDER]);
         LIDER_LAUNCH_CHECK("primary_order_kernel");
@@ -2966,24 +2995,24 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         CUtensorMap mqh, mql;
         if (sh.mode == LIDER_SCORE_FP8) {
             uint8_t* qp = reinterpret_cast<uint8_t*>(w.qp_hi);
-            qgather_f8_kernel<<<(unsigned)cdiv(np * 32, 256), 256, 0, st>>>(Q, w.pairs, np, c, g.d, w.slot_scale, qp);
+            qgather_f8_kernel<<<(unsigned)cdiv(np * 32, 256), 256, 0, side>>>(Q, w.pairs, np, c, g.d, w.slot_scale, qp);
             LIDER_LAUNCH_CHECK("qgather_f8_kernel");
             if ((rc = make_tensor_map8(&mqh, qp, np, g.d, tc::kBM))) return rc;
             mql = mqh;
         } else if (h16) {
             uint16_t* qp = reinterpret_cast<uint16_t*>(w.qp_hi);
             if (sh.mode == LIDER_SCORE_BF16) {
-                qgather_bf16_kernel<<<(unsigned)cdiv(np * 32, 256), 256, 0, st>>>(Q, w.pairs, np, c, g.d, qp);
+                qgather_bf16_kernel<<<(unsigned)cdiv(np * 32, 256), 256, 0, side>>>(Q, w.pairs, np, c, g.d, qp);
                 LIDER_LAUNCH_CHECK("qgather_bf16_kernel");
             } else {
-                qgather_f16_kernel<<<(unsigned)cdiv(np * 32, 256), 256, 0, st>>>(Q, w.pairs, np, c, g.d, w.qscale,
+                qgather_f16_kernel<<<(unsigned)cdiv(np * 32, 256), 256, 0, side>>>(Q, w.pairs, np, c, g.d, w.qscale,
                                                                                  qp);
                 LIDER_LAUNCH_CHECK("qgather_f16_kernel");
             }
             if ((rc = make_tensor_map(&mqh, qp, np, g.d, tc::kBM, true))) return rc;
             mql = mqh;
         } else {
-            qgather_kernel<<<(unsigned)cdiv(np * 32, 256), 256, 0, st>>>(Q, w.pairs, np, c, g.d, w.qp_hi, w.qp_lo);
+            qgather_kernel<<<(unsigned)cdiv(np * 32, 256), 256, 0, side>>>(Q, w.pairs, np, c, g.d, w.qp_hi, w.qp_lo);
             LIDER_LAUNCH_CHECK("qgather_kernel");
             if ((rc = make_tensor_map(&mqh, w.qp_hi, np, g.d, tc::kBM))) return rc;
             if ((rc = make_tensor_map(&mql, w.qp_lo, np, g.d, tc::kBM))) return rc;
@@ -2998,9 +3027,10 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
             mark_words, np);
         LIDER_LAUNCH_CHECK("mark_kernel");
         if ((rc = mark(LIDER_PHASE_SCORE))) return rc;
-        tc_units_kernel<<<g.ncl, 128, 0, st>>>(w.unit_off, w.off, g.cl_off, w.bm_off, w.pairs, w.qbound, c, g.ncl,
-                                               ix->tune.tile_order, w.units, w.umeta, w.slot_bound);
+        tc_units_kernel<<<g.ncl, 128, 0, side>>>(w.unit_off, w.off, g.cl_off, w.bm_off, w.pairs, w.qbound, c,
+                                                 g.ncl, ix->tune.tile_order, w.units, w.umeta, w.slot_bound);
         LIDER_LAUNCH_CHECK("tc_units_kernel");
+        if (fork && (rc = join_side(fe_ev.e[3]))) return rc;
         TcArgs ta;
         ta.units = w.units;
         ta.umeta = w.umeta;
