@@ -1685,7 +1685,11 @@ __global__ void __launch_bounds__(ScorePlan<Kind>::kThreads, 1)
 // listed id is scored again here on the CUDA cores with exactly the SIMT
 // path's arithmetic, the list re-sorted (score descending, id ascending) and
 // the best k kept.  One block per query; a list holds its entries first, then
-// -1s (S slots).
+// -1s (S slots).  The block first resolves every listed id to its corpus row
+// (key[r] = row << 32 | id, ~0 for none), so a warp's row loads do not wait on
+// the id and row-map loads; with d <= 32 kV float4 per lane (kV > 0) a warp
+// issues all loads of its two rows before the first product.
+template <int kV>
 __global__ void __launch_bounds__(512) rescore_kernel(const float* __restrict__ Q, const float* __restrict__ X,
                                                       const int32_t* __restrict__ row_of, int d, int S,
                                                       const int64_t* in_ids, int k, int64_t* out_ids,
@@ -1703,43 +1707,67 @@ __global__ void __launch_bounds__(512) rescore_kernel(const float* __restrict__ 
         reinterpret_cast<float4*>(qv)[i] = reinterpret_cast<const float4*>(Q + q * d)[i];
     __syncthreads();
     // the list holds its entries first, then -1s
-    for (int r = tid; r < S; r += blockDim.x)
-        if (in_ids[q * S + r] >= 0) atomicMax(&s_nr, r + 1);
+    for (int r = tid; r < S; r += blockDim.x) {
+        int64_t id = in_ids[q * S + r];
+        if (id >= 0) atomicMax(&s_nr, r + 1);
+        if (id >= n) {
+            atomicAdd(bounds, 1ull);
+            id = -1;
+        }
+        key[r] = id >= 0 ? ((uint64_t)(uint32_t)row_of[id] << 32) | (uint64_t)(uint32_t)id : ~0ull;
+    }
     __syncthreads();
     const int nr = s_nr;
     // two rows per warp at a time (each row's sum in the SIMT path's order)
     const float4* y4 = reinterpret_cast<const float4*>(qv);
     for (int r0 = 2 * warp; r0 < nr; r0 += 2 * nwarps) {
-        int64_t id[2];
+        uint64_t kv[2];
         const float4* x4[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            id[h] = r0 + h < nr ? in_ids[q * S + r0 + h] : -1;
-            if (id[h] >= n) {
-                if (lane == 0) atomicAdd(bounds, 1ull);
-                id[h] = -1;
-            }
-            x4[h] = id[h] >= 0 ? reinterpret_cast<const float4*>(X + (int64_t)row_of[id[h]] * d) : nullptr;
+            kv[h] = r0 + h < nr ? key[r0 + h] : ~0ull;
+            x4[h] = kv[h] != ~0ull ? reinterpret_cast<const float4*>(X + (int64_t)(kv[h] >> 32) * d) : nullptr;
         }
         float acc[2] = {0.f, 0.f};
-        for (int i = lane; i < d4; i += 32) {
-            const float4 y = y4[i];
+        if constexpr (kV > 0) {
+            float4 xv[2][kV];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (!x4[h]) continue;
-                const float4 x = __ldg(x4[h] + i);
-                acc[h] = fmaf(x.x, y.x, acc[h]);
-                acc[h] = fmaf(x.y, y.y, acc[h]);
-                acc[h] = fmaf(x.z, y.z, acc[h]);
-                acc[h] = fmaf(x.w, y.w, acc[h]);
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int t = 0; t < kV; ++t)
+                    xv[h][t] = x4[h] && lane + 32 * t < d4 ? __ldg(x4[h] + lane + 32 * t)
+                                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int t = 0; t < kV; ++t) {
+                if (lane + 32 * t >= d4) break;
+                const float4 y = y4[lane + 32 * t];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    acc[h] = fmaf(xv[h][t].x, y.x, acc[h]);
+                    acc[h] = fmaf(xv[h][t].y, y.y, acc[h]);
+                    acc[h] = fmaf(xv[h][t].z, y.z, acc[h]);
+                    acc[h] = fmaf(xv[h][t].w, y.w, acc[h]);
+                }
+            }
+        } else {
+            for (int i = lane; i < d4; i += 32) {
+                const float4 y = y4[i];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (!x4[h]) continue;
+                    const float4 x = __ldg(x4[h] + i);
+                    acc[h] = fmaf(x.x, y.x, acc[h]);
+                    acc[h] = fmaf(x.y, y.y, acc[h]);
+                    acc[h] = fmaf(x.z, y.z, acc[h]);
+                    acc[h] = fmaf(x.w, y.w, acc[h]);
+                }
             }
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             for (int o = 16; o > 0; o >>= 1) acc[h] += __shfl_xor_sync(0xffffffffu, acc[h], o);
             if (lane == 0 && r0 + h < nr)
-                key[r0 + h] = id[h] >= 0 ? ((uint64_t)(~float_order(acc[h])) << 32) | (uint64_t)(uint32_t)id[h]
-                                         : ~0ull;
+                key[r0 + h] = x4[h] ? ((uint64_t)(~float_order(acc[h])) << 32) | (kv[h] & 0xffffffffull) : ~0ull;
         }
     }
     const int SP = nr > 1 ? next_pow2_dev(nr) : 1;
@@ -1756,6 +1784,22 @@ __global__ void __launch_bounds__(512) rescore_kernel(const float* __restrict__ 
             out_ids[q * k + r] = (int64_t)(uint32_t)kv;
             out_scores[q * k + r] = float_from_order(~(uint32_t)(kv >> 32));
         }
+    }
+}
+
+// rescore_kernel's instance for a dimension: all loads of a row pair in
+// flight at once when d <= 1024.
+inline const void* rescore_fn(int d) {
+    switch ((d / 4 + 31) / 32) {
+        case 1: return (const void*)rescore_kernel<1>;
+        case 2: return (const void*)rescore_kernel<2>;
+        case 3: return (const void*)rescore_kernel<3>;
+        case 4: return (const void*)rescore_kernel<4>;
+        case 5: return (const void*)rescore_kernel<5>;
+        case 6: return (const void*)rescore_kernel<6>;
+        case 7: return (const void*)rescore_kernel<7>;
+        case 8: return (const void*)rescore_kernel<8>;
+        default: return (const void*)rescore_kernel<0>;
     }
 }
 
@@ -2865,6 +2909,25 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         LIDER_CUDA_TRY(cudaStreamWaitEvent(st, ev, 0));
         return LIDER_OK;
     };
+    // hash values too close to a bucket edge for the tiles' error, recomputed
+    // exactly; then the packed keys of the whole batch (on the side stream
+    // after the last front launch: with one chunk, beside the top-c)
+    bool keys_launched = false;
+    auto launch_keys = [&]() -> int {
+        keys_launched = true;
+        if (fork && (rc = fork_to_side(fe_ev.e[0]))) return rc;
+        if (tensor_route) {
+            hash_recheck_kernel<<<(unsigned)(16 * ix->num_sms), 32, (size_t)2 * g.d * sizeof(float), side>>>(
+                Q, g.A, g.bproj, g.W, g.d, g.H, w.hrecheck, w.n_hrecheck, w.tq);
+            LIDER_LAUNCH_CHECK("hash_recheck_kernel");
+        }
+        if ((rc = launch_pack(w.tq, nq, g.L, g.m, g.beta, g.hash_kind, 0, g.L, 1, w.qkeys,
+                              &w.counters[CNT_QBOUNDARY], &w.counters[CNT_QCLAMPED], side)))
+            return rc;
+        if (tr && tr->qkeys)
+            LIDER_CUDA_TRY(cudaMemcpyAsync(tr->qkeys, w.qkeys, (size_t)nq * g.L * 8, cudaMemcpyDeviceToDevice, side));
+        return LIDER_OK;
+    };
     // SIMT mode: Dot2 hash values, then exact FP64 routing scores and top-c
     auto simt_chunk = [&](int64_t q0, int64_t q1, bool last) -> int {
         const int64_t n = q1 - q0;
@@ -2917,6 +2980,7 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
             w.tc_err);
         LIDER_LAUNCH_CHECK("front_tc_kernel");
         if (last && (rc = mark(LIDER_PHASE_ROUTE))) return rc;
+        if (fork && last && q0 == 0 && (rc = launch_keys())) return rc;
         // guard: the tensor-core error of one score stays below kTcGuard |q| |mu|
         topc_exact_kernel<<<(unsigned)cdiv(n * 32, 256), 256, g.ncl <= kTopcStageCols ? 8 * g.ncl * 4 : 0, st>>>(
             S, Qc, g.C, g.half_norm, n, g.ncl, g.d, c, kTcGuard * ix->max_cnorm, w.route + q0 * c, trace_route,
@@ -2937,19 +3001,7 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
             return rc;
         }
     }
-    // hash values too close to a bucket edge for the tiles' error, recomputed
-    // exactly; then the packed keys of the whole batch
-    if (fork && (rc = fork_to_side(fe_ev.e[0]))) return rc;
-    if (tensor_route) {
-        hash_recheck_kernel<<<(unsigned)(16 * ix->num_sms), 32, (size_t)2 * g.d * sizeof(float), side>>>(
-            Q, g.A, g.bproj, g.W, g.d, g.H, w.hrecheck, w.n_hrecheck, w.tq);
-        LIDER_LAUNCH_CHECK("hash_recheck_kernel");
-    }
-    if ((rc = launch_pack(w.tq, nq, g.L, g.m, g.beta, g.hash_kind, 0, g.L, 1, w.qkeys, &w.counters[CNT_QBOUNDARY],
-                          &w.counters[CNT_QCLAMPED], side)))
-        return rc;
-    if (tr && tr->qkeys)
-        LIDER_CUDA_TRY(cudaMemcpyAsync(tr->qkeys, w.qkeys, (size_t)nq * g.L * 8, cudaMemcpyDeviceToDevice, side));
+    if (!keys_launched && (rc = launch_keys())) return rc;
     if (ix->params.route_kind == LIDER_ROUTE_CORE) {
         // Layer-1 centroids retriever: replaces the route of the exact scan
         // (whose per-query error bounds the tensor paths still use)
@@ -3142,10 +3194,21 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         LIDER_LAUNCH_CHECK("merge_kernel");
     } else {
         const size_t rs_smem = align_up((size_t)g.d * 4, 16) + (size_t)next_pow2(sh.so) * 8;
-        if ((rc = smem_attr((const void*)rescore_kernel, (int)rs_smem))) return rc;
-        rescore_kernel<<<(unsigned)nq, (unsigned)ix->tune.rescore_threads, rs_smem, st>>>(Q, g.X, g.row_of, g.d, sh.so, w.sl_ids, k, out_ids,
-                                                           out_scores, g.n, &w.counters[CNT_BOUNDS], w.qorder);
-        LIDER_LAUNCH_CHECK("rescore_kernel");
+        const void* rs_kern = rescore_fn(g.d);
+        if ((rc = smem_attr(rs_kern, (int)rs_smem))) return rc;
+        {
+            const float* rq = Q;
+            const float* rx = g.X;
+            const int32_t* rrow = g.row_of;
+            int rd = (int)g.d, rS = (int)sh.so, rk = (int)k;
+            const int64_t* rin = w.sl_ids;
+            int64_t rn = g.n;
+            unsigned long long* rb = &w.counters[CNT_BOUNDS];
+            const int32_t* ro = w.qorder;
+            void* rargs[] = {&rq, &rx, &rrow, &rd, &rS, &rin, &rk, &out_ids, &out_scores, &rn, &rb, &ro};
+            LIDER_CUDA_TRY(cudaLaunchKernel(rs_kern, dim3((unsigned)nq), dim3((unsigned)ix->tune.rescore_threads),
+                                            rargs, rs_smem, st));
+        }
         if (da.ovf) {
             // the listed queries' whole bands, exactly (returns at once when none is listed)
             const size_t bd_smem = align_up((size_t)g.d * 4, 16) + (size_t)2 * kBandChunk * 8 + (size_t)kBandChunk * 4;
