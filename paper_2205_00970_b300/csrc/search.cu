@@ -28,9 +28,10 @@
 //               tcgen05 written as per-pair score rows, with per-32-position
 //               candidate maxima [score_group_kernel: union, exact FP32
 //               scores and per-pair top-k in one persistent kernel]
-//   7. select   select_hist_kernel (per query: the ks best approximate scores
-//               plus the guard band, by radix selects) and select_query_kernel
-//               (fallback for massive ties)
+//   7. select   select_hist_kernel (per query: a threshold from a histogram
+//               of the chunk maxima, the chunks that clear it read, the ks-th
+//               best collected score by a radix select, the guard band below
+//               it kept) and select_query_kernel (fallback for massive ties)
 //   8. merge    rescore_kernel: exact FP32 scores of each query's list, sorted
 //               [merge_kernel: k-way merge of the c per-pair lists]
 
@@ -753,6 +754,116 @@ __global__ void primary_order_kernel(const int32_t* __restrict__ pairs, const in
     for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         const int p = pairs[i];
         if (p % c == 0) qorder[s_base + atomicAdd(&s_pos, 1)] = p / c;
+    }
+}
+
+// The grouping of a small batch in one launch (one block of kGroupThreads):
+// the same outputs as group_count_kernel + group_scan_kernel +
+// group_fill_kernel + primary_order_kernel, with the per-cluster counters in
+// shared memory.  Pairs inside a cluster, and queries inside a first-probe
+// cluster, are in no particular order (as there).
+constexpr int kGroupThreads = 1024;
+constexpr int kGroupMaxCl = 4096;           // clusters (two shared counters each)
+constexpr int64_t kGroupMaxPairs = 131072;  // larger batches take the multi-block kernels (faster there)
+
+// Exclusive scan of one value per thread over the block (all threads call
+// it); *total receives the sum.  s_w holds kGroupThreads / 32 entries.
+template <class T>
+__device__ T block_excl_scan(T v, T* s_w, T* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) s_w[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        T y = lane < nw ? s_w[lane] : T(0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const T t = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += t;
+        }
+        if (lane < nw) s_w[lane] = y;               // inclusive over warps
+    }
+    __syncthreads();
+    const T before = (wid > 0 ? s_w[wid - 1] : T(0)) + x - v;
+    *total = s_w[nw - 1];
+    __syncthreads();                               // s_w is free again
+    return before;
+}
+
+__global__ void __launch_bounds__(kGroupThreads) group_kernel(
+        const int32_t* __restrict__ route, int64_t npairs, int c, int ncl, int G, const int64_t* __restrict__ cl_off,
+        int32_t* __restrict__ cnt_out, int32_t* __restrict__ off, int32_t* __restrict__ item_off,
+        int32_t* __restrict__ unit_off, int64_t* __restrict__ bm_off, int32_t* __restrict__ pairs,
+        int32_t* __restrict__ qorder) {
+    __shared__ int32_t s_cnt[kGroupMaxCl], s_cnt0[kGroupMaxCl];   // counts, then cursors
+    __shared__ int32_t s_w32[kGroupThreads / 32];
+    __shared__ int64_t s_w64[kGroupThreads / 32];
+    const int tid = threadIdx.x;
+    for (int j = tid; j < ncl; j += kGroupThreads) {
+        s_cnt[j] = 0;
+        s_cnt0[j] = 0;
+    }
+    __syncthreads();
+    for (int64_t i = tid; i < npairs; i += kGroupThreads) {
+        const int j = route[i];
+        atomicAdd(&s_cnt[j], 1);
+        if (qorder && i % c == 0) atomicAdd(&s_cnt0[j], 1);   // the query's first probe
+    }
+    __syncthreads();
+    // each thread a run of consecutive clusters; scans of the runs' sums
+    const int per = (ncl + kGroupThreads - 1) / kGroupThreads;
+    const int j0 = min(ncl, tid * per), j1 = min(ncl, j0 + per);
+    int32_t sa = 0, sb = 0, sc = 0, s0 = 0;
+    int64_t sd = 0;
+    for (int j = j0; j < j1; ++j) {
+        const int32_t v = s_cnt[j];
+        const int64_t n_c = cl_off[j + 1] - cl_off[j];
+        sa += v;
+        sb += (v + G - 1) / G;
+        sc += tc_units(v, n_c);
+        sd += (int64_t)v * bitmap_words(n_c);
+        s0 += s_cnt0[j];
+    }
+    int32_t ta, tb, tcn, t0;
+    int64_t td;
+    int32_t ea = block_excl_scan(sa, s_w32, &ta);
+    int32_t eb = block_excl_scan(sb, s_w32, &tb);
+    int32_t ec = block_excl_scan(sc, s_w32, &tcn);
+    int32_t e0 = block_excl_scan(s0, s_w32, &t0);
+    int64_t ed = block_excl_scan(sd, s_w64, &td);
+    for (int j = j0; j < j1; ++j) {
+        const int32_t v = s_cnt[j];
+        const int64_t n_c = cl_off[j + 1] - cl_off[j];
+        cnt_out[j] = v;
+        off[j] = ea;
+        item_off[j] = eb;
+        unit_off[j] = ec;
+        bm_off[j] = ed;
+        const int32_t v0 = s_cnt0[j];
+        s_cnt[j] = ea;                             // cursors
+        s_cnt0[j] = e0;
+        ea += v;
+        eb += (v + G - 1) / G;
+        ec += tc_units(v, n_c);
+        ed += (int64_t)v * bitmap_words(n_c);
+        e0 += v0;
+    }
+    if (tid == 0) {
+        off[ncl] = ta;
+        item_off[ncl] = tb;
+        unit_off[ncl] = tcn;
+        bm_off[ncl] = td;
+    }
+    __syncthreads();
+    for (int64_t i = tid; i < npairs; i += kGroupThreads) {
+        const int j = route[i];
+        pairs[atomicAdd(&s_cnt[j], 1)] = (int32_t)i;
+        if (qorder && i % c == 0) qorder[atomicAdd(&s_cnt0[j], 1)] = (int32_t)(i / c);
     }
 }
 
@@ -2150,33 +2261,71 @@ __global__ void __launch_bounds__(256) select_query_kernel(DenseArgs da, int c, 
     }
 }
 
-// Per-query selection in two streaming passes (tensor paths).  The bins are
-// fixed by a bound B >= |approximate score| of the query (no range pass):
-// bin = floor((B - score) * kHistBins / 2B), bin 0 holding the best scores.
-// Pass 1 counts the candidates per bin; the bin where the count reaches ks
-// fixes a threshold (lowered by the guard band and one bin for rounding);
-// pass 2 collects the candidates of the bins up to it as (score, corpus id),
-// which are sorted in shared memory.  A query whose collection would exceed
-// kHistCand is appended to `redo` and left to select_query_kernel.
+// Per-query selection (tensor paths).  The bins are fixed by a bound B >=
+// |approximate score| of the query (no range pass): bin = floor((B - score) *
+// kHistBins / 2B), bin 0 holding the best scores.  Way 1 (small ks) bins the
+// per-chunk candidate maxima, way 2 every candidate; the bin where the count
+// reaches ks fixes a threshold (lowered by the guard band and one bin, or
+// sub-bin, for rounding), and the candidates above it are collected in
+// shared memory.  A query whose collection would exceed kHistCand is appended
+// to `redo` and left to select_query_kernel.
 constexpr int kHistBins = 2048;
 constexpr int kHistCand = 2048;
 
 // The r-th smallest (1-based, counting repeats) of n 32-bit words word(i),
-// i < n, by a block-wide radix select: passes over 8-bit digits, most
-// significant first, each counting the words that match the digits chosen so
+// i < n, by a block-wide radix select: the bits the smallest and the largest
+// word share are the answer's; passes over the next digits of up to 8 bits,
+// most significant first, each count the words that match the bits chosen so
 // far in a 256-bin shared histogram.  All threads call it; r in [1, n].
-// With fewer than four passes the result is the largest word sharing the
-// r-th smallest word's leading digits: an upper bound on it.
+// `passes` < 4 stops once the bits at or above 32 - 8 passes are chosen: the
+// result is then the largest word sharing the r-th smallest word's bits down
+// to the last digit taken, an upper bound on it.
 template <class Word>
 __device__ uint32_t block_kth_smallest(Word word, int n, int r, uint32_t* hist256, int* s_pick, int passes = 4) {
+    __shared__ uint32_t s_lohi[2];
     const int tid = threadIdx.x, lane = tid & 31;
-    uint32_t prefix = 0u, mask = 0u;
-    for (int shift = 24; shift >= 32 - 8 * passes; shift -= 8) {
+    // the words' common leading bits (those of their minimum and maximum) are
+    // the answer's; the digit passes start below them
+    uint32_t lo = 0xffffffffu, hi = 0u;
+    for (int i = tid; i < n; i += blockDim.x) {
+        const uint32_t v = word(i);
+        lo = min(lo, v);
+        hi = max(hi, v);
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if (tid == 0) {
+        s_lohi[0] = 0xffffffffu;
+        s_lohi[1] = 0u;
+    }
+    __syncthreads();
+    if (lane == 0) {
+        atomicMin(&s_lohi[0], lo);
+        atomicMax(&s_lohi[1], hi);
+    }
+    __syncthreads();
+    lo = s_lohi[0];
+    hi = s_lohi[1];
+    __syncthreads();                               // every thread has read s_lohi
+    if (lo == hi) return lo;
+    const int target = 32 - 8 * passes;            // bits at or above it are resolved
+    int top = 31 - __clz(lo ^ hi), low;
+    uint32_t mask = top == 31 ? 0u : ~((2u << top) - 1u), prefix = lo & mask;
+    do {
+        low = max(top - 7, 0);
+        const uint32_t dm = (2u << (top - low)) - 1u;   // the digit's bits
         for (int b = tid; b < 256; b += blockDim.x) hist256[b] = 0u;
         __syncthreads();
-        for (int i = tid; i < n; i += blockDim.x) {
-            const uint32_t v = word(i);
-            if ((v & mask) == prefix) atomicAdd(&hist256[(v >> shift) & 255u], 1u);
+        // one atomic per distinct digit of a warp's words
+        for (int i0 = tid - lane; i0 < n; i0 += blockDim.x) {
+            const int i = i0 + lane;
+            uint32_t dig = 0xffffffffu;
+            if (i < n) {
+                const uint32_t v = word(i);
+                if ((v & mask) == prefix) dig = (v >> low) & dm;
+            }
+            const uint32_t peers = __match_any_sync(0xffffffffu, dig);
+            if (dig != 0xffffffffu && lane == __ffs(peers) - 1) atomicAdd(&hist256[dig], (uint32_t)__popc(peers));
         }
         __syncthreads();
         if (tid < 32) {
@@ -2206,12 +2355,13 @@ __device__ uint32_t block_kth_smallest(Word word, int n, int r, uint32_t* hist25
             }
         }
         __syncthreads();
-        prefix |= (uint32_t)s_pick[0] << shift;
-        mask |= 255u << shift;
+        prefix |= (uint32_t)s_pick[0] << low;
+        mask |= dm << low;
         r = s_pick[1];
         __syncthreads();                           // every thread has read s_pick
-    }
-    return passes >= 4 ? prefix : prefix | ((1u << (32 - 8 * passes)) - 1u);
+        top = low - 1;
+    } while (low > target);
+    return low > 0 ? prefix | ((1u << low) - 1u) : prefix;
 }
 
 __global__ void __launch_bounds__(512) select_hist_kernel(
@@ -2221,7 +2371,7 @@ __global__ void __launch_bounds__(512) select_hist_kernel(
     __shared__ uint32_t hist[kHistBins];          // also: the threads' maxima (need <= blockDim)
     __shared__ uint64_t cand[kHistCand];
     __shared__ PairRow s_pr[LIDER_MAX_C];
-    __shared__ int s_total, s_cnt, s_bt, s_band;
+    __shared__ int s_total, s_cnt, s_bt, s_band, s_nh, s_ct;
     __shared__ float s_thr;
     __shared__ uint32_t s_rhist[256];              // radix select
     __shared__ int s_pick[2];
@@ -2262,20 +2412,19 @@ __global__ void __launch_bounds__(512) select_hist_kernel(
     };
     auto comp = [](const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; };
     // Way 1 (need <= 4 * blockDim), on the chunk maxima the tensor epilogue
-    // wrote (per pair and 32 positions, the best candidate score there).  Every
-    // thread keeps its 4 best maxima; the need-th best of those 4 * blockDim
-    // values is a score reached by at least `need` distinct candidates (one per
-    // chunk), so the ks-th best is not below it.  Every candidate at or above it
-    // less twice the guard lies in a chunk whose maximum clears that threshold:
-    // only those chunks are read.
+    // wrote (per pair and 32 positions, the best candidate score there): a
+    // histogram of the maxima over the query's bins; the bin where their
+    // count reaches `need` holds a score reached by at least `need` distinct
+    // candidates (one per chunk), so the ks-th best is not below its lower
+    // edge.  Every candidate at or above that edge less twice the guard (and
+    // one bin for rounding) lies in a chunk whose maximum falls in a bin up to
+    // the last one to collect: only those chunks are read.
     constexpr int kKeep = 4;
     bool small_lists = true;                        // positions fit the (list, position) packing
     for (int p = 0; p < c; ++p) small_lists = small_lists && s_pr[p].n_c < (1 << 27);
     const bool by_max = need > 0 && need <= kKeep * bd && small_lists;
     // The chunk maxima of the c pairs as one sequence of words: word g is
     // word g - s_wo[p] of pair p, for the p with s_wo[p] <= g < s_wo[p + 1].
-    // The scans below take kBatch words per thread per round, their loads
-    // issued before any is used.
     constexpr int kBatch = 4;
     if (tid == 0) {
         int o = 0;
@@ -2294,99 +2443,254 @@ __global__ void __launch_bounds__(512) select_hist_kernel(
         w = g - s_wo[p];
     };
     if (by_max) {
-        float ts[kKeep];
-#pragma unroll
-        for (int j = 0; j < kKeep; ++j) ts[j] = -INFINITY;
+        // a thread's words g = tid + r bd: up to kRegW of them stay in
+        // registers (loads all in flight), more are read again below
+        constexpr int kRegW = 16;
+        const bool in_regs = n_words <= kRegW * bd;
+        float vm[kRegW];
         int hp = 0;                                 // this thread's current pair
-        for (int g0 = tid; g0 < n_words; g0 += kBatch * bd) {
-            float vb[kBatch];
+        if (in_regs) {
 #pragma unroll
-            for (int r = 0; r < kBatch; ++r) {
-                const int g = g0 + r * bd;
-                vb[r] = -INFINITY;
+            for (int r = 0; r < kRegW; ++r) {
+                const int g = tid + r * bd;
+                vm[r] = -INFINITY;
                 if (g < n_words) {
                     int w;
                     word_at(g, hp, w);
-                    vb[r] = __ldg(s_pr[hp].cm + w);
+                    vm[r] = __ldg(s_pr[hp].cm + w);
                 }
             }
 #pragma unroll
-            for (int r = 0; r < kBatch; ++r) {
-                float vv = vb[r];
+            for (int r = 0; r < kRegW; ++r)
+                if (vm[r] > -INFINITY) atomicAdd(&hist[bin_of(vm[r])], 1u);
+        } else {
+            for (int g0 = tid; g0 < n_words; g0 += kBatch * bd) {
+                float vb[kBatch];
 #pragma unroll
-                for (int j = 0; j < kKeep; ++j) {   // insert, best first
-                    if (vv > ts[j]) {
-                        const float t0 = ts[j];
-                        ts[j] = vv;
-                        vv = t0;
+                for (int r = 0; r < kBatch; ++r) {
+                    const int g = g0 + r * bd;
+                    vb[r] = -INFINITY;
+                    if (g < n_words) {
+                        int w;
+                        word_at(g, hp, w);
+                        vb[r] = __ldg(s_pr[hp].cm + w);
                     }
                 }
+#pragma unroll
+                for (int r = 0; r < kBatch; ++r)
+                    if (vb[r] > -INFINITY) atomicAdd(&hist[bin_of(vb[r])], 1u);
             }
         }
-        // the kept maxima as sortable words, best first (none: the largest word)
-        for (int u = tid; u < kHistBins; u += bd) hist[u] = 0xffffffffu;
         __syncthreads();
+        // the first bin where the maxima's count reaches need (none: fewer
+        // chunks with candidates than need, take all), 32 bins per step
+        if (tid < 32) {
+            uint32_t cum = 0u;
+            int bsel = -1;
+            for (int b0 = 0; b0 < kHistBins; b0 += 32) {
+                uint32_t v = hist[b0 + lane];
 #pragma unroll
-        for (int j = 0; j < kKeep; ++j) hist[tid * kKeep + j] = ts[j] == -INFINITY ? 0xffffffffu : ~float_order(ts[j]);
-        __syncthreads();
-        // the need-th best kept maximum (need <= kKeep * bd words)
-        // (three digits: an upper bound on the word, i.e. a threshold at most
-        // 2^8 float steps lower, which only reads a few more chunks)
-        const uint32_t wk = block_kth_smallest([&](int i) { return hist[i]; }, kKeep * bd, need, s_rhist, s_pick, 3);
-        if (tid == 0) {
-            float thr = -INFINITY;                 // fewer chunks with candidates than need: take all
-            if (wk != 0xffffffffu) {
-                thr = float_from_order(~wk);
-                if (guarded) thr = thr - 2.f * qguard[q];
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+                    if (lane >= o) v += t;
+                }
+                const unsigned reach = __ballot_sync(0xffffffffu, cum + v >= (uint32_t)need);
+                if (reach) {
+                    const int l = __ffs(reach) - 1;
+                    bsel = b0 + l;
+                    cum += __shfl_sync(0xffffffffu, v, l) - hist[bsel];   // maxima before bin bsel
+                    break;
+                }
+                cum += __shfl_sync(0xffffffffu, v, 31);
             }
-            s_thr = thr;
-            s_bt = 0;
+            for (int u = lane; u < 256; u += 32) s_rhist[u] = 0u;
+            if (lane == 0) {
+                s_bt = bsel;
+                s_band = (int)cum;
+            }
+        }
+        __syncthreads();
+        const int bsel = s_bt;
+        // bin bsel split into 256 sub-bins (the maxima held in registers, or
+        // read again)
+        const bool refine = bsel >= 0 && scale > 0.f;
+        auto sub_count = [&](float m) {
+            if (m > -INFINITY && bin_of(m) == bsel) {
+                const float x = __fmul_rn(__fadd_rn(B, -m), scale);
+                const int sub = (int)fminf(fmaxf((x - (float)bsel) * 256.f, 0.f), 255.f);
+                atomicAdd(&s_rhist[sub], 1u);
+            }
+        };
+        if (refine && in_regs) {
+#pragma unroll
+            for (int r = 0; r < kRegW; ++r) sub_count(vm[r]);
+        } else if (refine) {
+            int hs = 0;
+            for (int g0 = tid; g0 < n_words; g0 += kBatch * bd) {
+                float vb[kBatch];
+#pragma unroll
+                for (int r = 0; r < kBatch; ++r) {
+                    const int g = g0 + r * bd;
+                    vb[r] = -INFINITY;
+                    if (g < n_words) {
+                        int w;
+                        word_at(g, hs, w);
+                        vb[r] = __ldg(s_pr[hs].cm + w);
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < kBatch; ++r) sub_count(vb[r]);
+            }
+        }
+        __syncthreads();
+        if (tid < 32) {
+            // the sub-bin where the count reaches need (lane owns 8 sub-bins)
+            int sub_sel = 255;
+            if (refine) {
+                uint32_t cnt[8], sum = 0u;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) { cnt[u] = s_rhist[8 * lane + u]; sum += cnt[u]; }
+                uint32_t incl = sum;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                const uint32_t r = (uint32_t)(need - s_band);
+                uint32_t run = incl - sum;
+                int mine = -1;
+                if (run < r && incl >= r) {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        if (run + cnt[u] >= r) { mine = 8 * lane + u; break; }
+                        run += cnt[u];
+                    }
+                }
+                const unsigned who = __ballot_sync(0xffffffffu, mine >= 0);
+                if (who) sub_sel = __shfl_sync(0xffffffffu, mine, __ffs(who) - 1);
+            }
+            if (lane == 0) {
+                // the score threshold: the chosen (sub-)bin's lower edge, less
+                // one (sub-)bin for rounding and, in guarded modes, twice the guard
+                float thr = -INFINITY;
+                if (bsel >= 0 && scale > 0.f) {
+                    const float fb = refine ? (float)bsel + (float)(sub_sel + 2) / 256.f : (float)(bsel + 2);
+                    thr = __fadd_rn(B, -fb / scale);
+                    if (guarded) thr = thr - 2.f * qguard[q];
+                }
+                s_thr = thr;
+                s_nh = 0;
+                // the largest code whose score clears thr (-1: none), code_score
+                // being non-increasing in the code
+                int lo = -1, hi = 65536;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (code_score((uint32_t)mid, cB, cstep) >= thr) lo = mid;
+                    else hi = mid;
+                }
+                s_ct = lo;
+            }
         }
         __syncthreads();
         const float thr = s_thr;
-        // read the chunks whose maximum clears the threshold; a thread reserves
-        // its chunk's keys with one atomic
+        const int ct = s_ct;
+        // the chunks whose maximum clears thr, as one list (pair << 24 |
+        // word) in hist, free again once warp 0 has read the counts; a listed
+        // chunk holds a candidate to collect, so more than kHistCand of them
+        // overflow the collection below as well
+        auto list_hit = [&](float m, int p, int w) {
+            if (m > -INFINITY && m >= thr) {                 // (-inf: past the words, or no candidate)
+                const int i = atomicAdd(&s_nh, 1);
+                if (i < kHistBins) hist[i] = ((uint32_t)p << 24) | (uint32_t)w;
+            }
+        };
         int hq = 0;                                 // this thread's current pair
-        for (int g0 = tid; g0 < n_words; g0 += kBatch * bd) {
-            uint32_t hit = 0u;                          // bit r: word g0 + r bd clears thr
-            const int hq0 = hq;
+        if (in_regs) {
 #pragma unroll
-            for (int r = 0; r < kBatch; ++r) {
-                const int g = g0 + r * bd;
-                if (g < n_words) {
+            for (int r = 0; r < kRegW; ++r) {
+                const int g = tid + r * bd;
+                if (g < n_words && vm[r] > -INFINITY) {
                     int w;
                     word_at(g, hq, w);
-                    if (__ldg(s_pr[hq].cm + w) >= thr) hit |= 1u << r;
+                    list_hit(vm[r], hq, w);
                 }
             }
-            for (int p = hq0; hit; hit &= hit - 1) {
-                int w;
-                word_at(g0 + (__ffs(hit) - 1) * bd, p, w);
-                const PairRow pr = s_pr[p];
-                const uint32_t bw = __ldg(pr.bm + w);
-                float v[32];
+        } else {
+            for (int g0 = tid; g0 < n_words; g0 += kBatch * bd) {
+                float vb[kBatch];
+                int pb[kBatch], wb[kBatch];
 #pragma unroll
-                for (int g8 = 0; g8 < 4; ++g8) {
-                    const uint4 cd = __ldg(reinterpret_cast<const uint4*>(pr.row + 32 * w) + g8);
-                    const uint32_t u[4] = {cd.x, cd.y, cd.z, cd.w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        v[8 * g8 + 2 * e] = code_score(u[e] & 0xffffu, cB, cstep);
-                        v[8 * g8 + 2 * e + 1] = code_score(u[e] >> 16, cB, cstep);
+                for (int r = 0; r < kBatch; ++r) {
+                    const int g = g0 + r * bd;
+                    vb[r] = -INFINITY;
+                    pb[r] = 0;
+                    wb[r] = 0;
+                    if (g < n_words) {
+                        word_at(g, hq, wb[r]);
+                        pb[r] = hq;
+                        vb[r] = __ldg(s_pr[hq].cm + wb[r]);
                     }
                 }
+#pragma unroll
+                for (int r = 0; r < kBatch; ++r) list_hit(vb[r], pb[r], wb[r]);
+            }
+        }
+        __syncthreads();
+        const int nh = s_nh;
+        if (nh > kHistCand) {
+            if (tid == 0) redo[atomicAdd(redo_count, 1)] = (int32_t)q;
+            return;
+        }
+        // the listed chunks, one per thread at a time with all its loads in
+        // flight; guarded modes key a candidate by (pair << 27 | position)
+        // (the ids of the band are looked up when it is written), the served
+        // forms by corpus id (their ties order by it)
+        constexpr int kHitBatch = 1;
+        for (int i0 = tid; i0 < nh; i0 += kHitBatch * bd) {
+            uint4 cd[kHitBatch][4];
+            uint32_t bw[kHitBatch], hv[kHitBatch];
+#pragma unroll
+            for (int u = 0; u < kHitBatch; ++u) {
+                const int i = i0 + u * bd;
+                bw[u] = 0u;
+                hv[u] = 0u;
+                if (i < nh) {
+                    hv[u] = hist[i];
+                    const PairRow& pr = s_pr[hv[u] >> 24];
+                    const int w = (int)(hv[u] & 0xffffffu);
+                    bw[u] = __ldg(pr.bm + w);
+#pragma unroll
+                    for (int g8 = 0; g8 < 4; ++g8) cd[u][g8] = __ldg(reinterpret_cast<const uint4*>(pr.row + 32 * w) + g8);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kHitBatch; ++u) {
+                if (!bw[u]) continue;
+                const int p = (int)(hv[u] >> 24), w = (int)(hv[u] & 0xffffffu);
+                const uint32_t cw[8] = {cd[u][0].x, cd[u][0].y, cd[u][0].z, cd[u][0].w,
+                                        cd[u][1].x, cd[u][1].y, cd[u][1].z, cd[u][1].w};
+                const uint32_t cw2[8] = {cd[u][2].x, cd[u][2].y, cd[u][2].z, cd[u][2].w,
+                                         cd[u][3].x, cd[u][3].y, cd[u][3].z, cd[u][3].w};
+                auto code_at = [&](int i) -> uint32_t {
+                    const uint32_t x = i < 16 ? cw[i >> 1] : cw2[(i - 16) >> 1];
+                    return (i & 1) ? x >> 16 : x & 0xffffu;
+                };
+                // score >= thr exactly when code <= ct (code_score decreases)
                 uint32_t take = 0u;
 #pragma unroll
                 for (int i = 0; i < 32; ++i)
-                    if (((bw >> i) & 1u) && v[i] >= thr) take |= 1u << i;
+                    if (((bw[u] >> i) & 1u) && (int)code_at(i) <= ct) take |= 1u << i;
                 const int nt = __popc(take);
                 if (nt == 0) continue;
                 int slot = atomicAdd(&s_cnt, nt);
+                const int64_t idb = s_pr[p].cb + 32 * w;
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
                     if ((take >> i) & 1u) {
                         if (slot < kHistCand)
-                            cand[slot] = sel_key(v[i], (uint32_t)__ldg(da.orig_id + pr.cb + 32 * w + i));
+                            cand[slot] = sel_key(code_score(code_at(i), cB, cstep),
+                                                 guarded ? ((uint32_t)p << 27) | (uint32_t)(32 * w + i)
+                                                         : (uint32_t)__ldg(da.orig_id + idb + i));
                         ++slot;
                     }
                 }
@@ -2495,6 +2799,12 @@ __global__ void __launch_bounds__(512) select_hist_kernel(
         return;
     }
     const int n = min(s_cnt, kHistCand);
+    // a key's corpus id (way 1 of the guarded modes keys by pair and position)
+    const bool packed = by_max && guarded;
+    auto id_of = [&](uint64_t kv) -> int64_t {
+        const uint32_t lo = (uint32_t)kv;
+        return packed ? __ldg(da.orig_id + s_pr[lo >> 27].cb + (lo & 0x7ffffffu)) : (int64_t)lo;
+    };
     if (guarded && need > 0 && n > 0) {
         // Guarded modes: the list is every key within twice the error bound of
         // the need-th best approximate score, in no particular order (the
@@ -2521,7 +2831,7 @@ __global__ void __launch_bounds__(512) select_hist_kernel(
                 const float sc = float_from_order(~(uint32_t)(kv >> 32));
                 if (sc >= t) {
                     const int slot = atomicAdd(&s_bt, 1);
-                    out_ids[q * so + slot] = (int64_t)(uint32_t)kv;
+                    out_ids[q * so + slot] = id_of(kv);
                     out_scores[q * so + slot] = sc;
                 }
             }
@@ -2594,7 +2904,7 @@ __global__ void __launch_bounds__(512) select_hist_kernel(
     for (int r = tid; r < so; r += blockDim.x) {
         if (r < keep) {
             const uint64_t kv = cand[r];
-            out_ids[q * so + r] = (int64_t)(uint32_t)kv;
+            out_ids[q * so + r] = id_of(kv);
             out_scores[q * so + r] = float_from_order(~(uint32_t)(kv >> 32));
         } else {
             out_ids[q * so + r] = -1;
@@ -3018,17 +3328,24 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
     // 3. group
     if ((rc = mark(LIDER_PHASE_GROUP))) return rc;
     const int G = std::max(1, std::min(kMaxGroup, (96 * 1024) / (g.d * 4)));
-    group_count_kernel<<<(unsigned)cdiv(np, 256), 256, 0, st>>>(w.route, np, w.cnt);
-    LIDER_LAUNCH_CHECK("group_count_kernel");
-    group_scan_kernel<<<1, 1024, 0, st>>>(w.cnt, g.ncl, G, g.cl_off, w.off, w.cursor, w.item_off, w.unit_off,
-                                          w.bm_off);
-    LIDER_LAUNCH_CHECK("group_scan_kernel");
-    group_fill_kernel<<<(unsigned)cdiv(np, 256), 256, 0, st>>>(w.route, np, w.cursor, w.pairs);
-    LIDER_LAUNCH_CHECK("group_fill_kernel");
+    const bool one_block = g.ncl <= kGroupMaxCl && np <= kGroupMaxPairs;
+    if (one_block) {
+        group_kernel<<<1, kGroupThreads, 0, st>>>(w.route, np, c, g.ncl, G, g.cl_off, w.cnt, w.off, w.item_off,
+                                                  w.unit_off, w.bm_off, w.pairs, w.qorder);
+        LIDER_LAUNCH_CHECK("group_kernel");
+    } else {
+        group_count_kernel<<<(unsigned)cdiv(np, 256), 256, 0, st>>>(w.route, np, w.cnt);
+        LIDER_LAUNCH_CHECK("group_count_kernel");
+        group_scan_kernel<<<1, 1024, 0, st>>>(w.cnt, g.ncl, G, g.cl_off, w.off, w.cursor, w.item_off, w.unit_off,
+                                              w.bm_off);
+        LIDER_LAUNCH_CHECK("group_scan_kernel");
+        group_fill_kernel<<<(unsigned)cdiv(np, 256), 256, 0, st>>>(w.route, np, w.cursor, w.pairs);
+        LIDER_LAUNCH_CHECK("group_fill_kernel");
+    }
     // the side stream: hash recheck and packing done, now the pairs exist
     if (fork && (rc = join_side(fe_ev.e[1]))) return rc;
     if (fork && (rc = fork_to_side(fe_ev.e[2]))) return rc;
-    if (w.qorder) {
+    if (w.qorder && !one_block) {
         primary_order_kernel<<<(unsigned)g.ncl, 256, 0, st>>>(w.pairs, w.off, c, w.qorder, &w.counters[CNT_QORDER]);
         LIDER_LAUNCH_CHECK("primary_order_kernel");
     }
