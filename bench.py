@@ -39,8 +39,22 @@ sys.path.insert(0, ROOT)
 from paper_2205_00970_b300 import configs, synth  # noqa: E402
 
 METRIC = "queries/s at fixed recall@10 vs FP64 oracle (plain vs served BF16); p50/p99 ms"
-# our kernels per lider_search (phase list in search.cu; confirmed by the ncu launch list)
-LAUNCHES_PER_SEARCH = {"tensor": 19, "simt": 10, "bf16": 18, "f16": 19, "fp8": 18}
+# our kernels per pass of lider_search on device buffers with the
+# multi-kernel grouping (phase list in search.cu; confirmed by the ncu launch
+# list; the tensor modes launch the front kernel twice, routing and hash
+# tiles); a pass of at most GROUP_ONE_BLOCK_PAIRS pairs over at most
+# GROUP_ONE_BLOCK_CLUSTERS clusters groups them in one launch instead of
+# GROUP_SAVED + 1
+LAUNCHES_PER_SEARCH = {"tensor": 20, "simt": 10, "bf16": 19, "f16": 20, "fp8": 19}
+GROUP_SAVED = {"tensor": 3, "simt": 2, "bf16": 3, "f16": 3, "fp8": 3}
+GROUP_ONE_BLOCK_PAIRS, GROUP_ONE_BLOCK_CLUSTERS = 131_072, 4_096
+
+
+def launches_per_pass(score: str, nq_pass: int, c: int, n_clusters: int) -> int:
+    n = LAUNCHES_PER_SEARCH[score]
+    if nq_pass * c <= GROUP_ONE_BLOCK_PAIRS and n_clusters <= GROUP_ONE_BLOCK_CLUSTERS:
+        n -= GROUP_SAVED[score]
+    return n
 MODES = {"tensor": 0, "simt": 1, "bf16": 2, "f16": 3, "fp8": 4}
 DTYPES = {"tensor": "f32", "simt": "f32", "bf16": "bf16", "f16": "f16", "fp8": "fp8-e4m3"}
 FP8_PER_BF16 = 4.5 / 2.25     # nominal dense FP8 / BF16 tensor rate (B300)
@@ -636,7 +650,8 @@ def run_lider(args, cfg):
         "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": int(Q.nbytes),
                 "d2h_bytes_per_step": int(nq * k * (8 + 4)), "ms_per_step": e2e_s * 1e3 / args.steps,
                 "host_link": link},
-        "gpu_launches": LAUNCHES_PER_SEARCH[args.score] * passes * args.steps,
+        "gpu_launches": sum(launches_per_pass(args.score, hi - lo, c, cfg["n_clusters"])
+                            for lo, hi in calls) * args.steps,
         "graph_replay": graph,
         "tuning": tuning,
         "score_mode": args.score,

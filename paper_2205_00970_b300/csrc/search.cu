@@ -765,6 +765,7 @@ __global__ void primary_order_kernel(const int32_t* __restrict__ pairs, const in
 constexpr int kGroupThreads = 1024;
 constexpr int kGroupMaxCl = 4096;           // clusters (two shared counters each)
 constexpr int64_t kGroupMaxPairs = 131072;  // larger batches take the multi-block kernels (faster there)
+constexpr int kGroupLoads = 4;              // int4 loads of route in flight per thread
 
 // Exclusive scan of one value per thread over the block (all threads call
 // it); *total receives the sum.  s_w holds kGroupThreads / 32 entries.
@@ -809,11 +810,35 @@ __global__ void __launch_bounds__(kGroupThreads) group_kernel(
         s_cnt0[j] = 0;
     }
     __syncthreads();
-    for (int64_t i = tid; i < npairs; i += kGroupThreads) {
-        const int j = route[i];
+    // the pairs four at a time (route is 16-byte aligned), kGroupLoads loads
+    // of a thread in flight; then the tail
+    const int64_t n4 = npairs / 4;
+    const int4* r4 = reinterpret_cast<const int4*>(route);
+    auto for_pairs = [&](auto&& f) {
+        for (int64_t v0 = tid; v0 < n4; v0 += (int64_t)kGroupThreads * kGroupLoads) {
+            int4 x[kGroupLoads];
+#pragma unroll
+            for (int u = 0; u < kGroupLoads; ++u) {
+                const int64_t v = v0 + (int64_t)u * kGroupThreads;
+                if (v < n4) x[u] = __ldg(r4 + v);
+            }
+#pragma unroll
+            for (int u = 0; u < kGroupLoads; ++u) {
+                const int64_t v = v0 + (int64_t)u * kGroupThreads;
+                if (v < n4) {
+                    f(4 * v, x[u].x);
+                    f(4 * v + 1, x[u].y);
+                    f(4 * v + 2, x[u].z);
+                    f(4 * v + 3, x[u].w);
+                }
+            }
+        }
+        for (int64_t i = 4 * n4 + tid; i < npairs; i += kGroupThreads) f(i, __ldg(route + i));
+    };
+    for_pairs([&](int64_t i, int j) {
         atomicAdd(&s_cnt[j], 1);
         if (qorder && i % c == 0) atomicAdd(&s_cnt0[j], 1);   // the query's first probe
-    }
+    });
     __syncthreads();
     // each thread a run of consecutive clusters; scans of the runs' sums
     const int per = (ncl + kGroupThreads - 1) / kGroupThreads;
@@ -860,11 +885,10 @@ __global__ void __launch_bounds__(kGroupThreads) group_kernel(
         bm_off[ncl] = td;
     }
     __syncthreads();
-    for (int64_t i = tid; i < npairs; i += kGroupThreads) {
-        const int j = route[i];
+    for_pairs([&](int64_t i, int j) {
         pairs[atomicAdd(&s_cnt[j], 1)] = (int32_t)i;
         if (qorder && i % c == 0) qorder[atomicAdd(&s_cnt0[j], 1)] = (int32_t)(i / c);
-    }
+    });
 }
 
 // ----------------------------------------------------------------- locate --
@@ -3223,9 +3247,9 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
     // exactly; then the packed keys of the whole batch (on the side stream
     // after the last front launch: with one chunk, beside the top-c)
     bool keys_launched = false;
-    auto launch_keys = [&]() -> int {
+    auto launch_keys = [&](bool forked) -> int {
         keys_launched = true;
-        if (fork && (rc = fork_to_side(fe_ev.e[0]))) return rc;
+        if (fork && !forked && (rc = fork_to_side(fe_ev.e[0]))) return rc;
         if (tensor_route) {
             hash_recheck_kernel<<<(unsigned)(16 * ix->num_sms), 32, (size_t)2 * g.d * sizeof(float), side>>>(
                 Q, g.A, g.bproj, g.W, g.d, g.H, w.hrecheck, w.n_hrecheck, w.tq);
@@ -3283,14 +3307,32 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
         fe.nq = (int)n;
         fe.nth = fs.nth;
         fe.ntr = fs.ntr;
-        const int64_t tiles = cdiv(n, tc::kBM) * (fs.nth + fs.ntr);
         if ((rc = smem_attr((const void*)front_tc_kernel, (int)(tc::kSmemBytes)))) return rc;
-        front_tc_kernel<<<(unsigned)std::min<int64_t>(tiles, ix->num_sms), tc::kThreads, tc::kSmemBytes, st>>>(
-            mqs_h, mqs_l, ix->map_fhi, ix->map_flo, (g.d + tc::KindTf32x3::kBK - 1) / tc::KindTf32x3::kBK, fs, fe,
-            w.tc_err);
-        LIDER_LAUNCH_CHECK("front_tc_kernel");
-        if (last && (rc = mark(LIDER_PHASE_ROUTE))) return rc;
-        if (fork && last && q0 == 0 && (rc = launch_keys())) return rc;
+        const int kchunks = (g.d + tc::KindTf32x3::kBK - 1) / tc::KindTf32x3::kBK;
+        auto launch_front = [&](const FrontSched& sch, const FrontEpi& epi, cudaStream_t s2) -> int {
+            const int64_t tiles = cdiv(n, tc::kBM) * (sch.nth + sch.ntr);
+            front_tc_kernel<<<(unsigned)std::min<int64_t>(tiles, ix->num_sms), tc::kThreads, tc::kSmemBytes, s2>>>(
+                mqs_h, mqs_l, ix->map_fhi, ix->map_flo, kchunks, sch, epi, w.tc_err);
+            LIDER_LAUNCH_CHECK("front_tc_kernel");
+            return LIDER_OK;
+        };
+        if (fork && last && q0 == 0) {
+            // one chunk: the routing tiles on this stream, the hash tiles (and
+            // then the recheck and packing) on the side stream, so the top-c
+            // starts after one round of tiles
+            if ((rc = fork_to_side(fe_ev.e[0]))) return rc;
+            FrontSched fr = fs, fh = fs;
+            FrontEpi er = fe, eh = fe;
+            fr.nth = er.nth = 0;
+            fh.ntr = eh.ntr = 0;
+            if ((rc = launch_front(fr, er, st))) return rc;
+            if ((rc = launch_front(fh, eh, side))) return rc;
+            if ((rc = mark(LIDER_PHASE_ROUTE))) return rc;
+            if ((rc = launch_keys(true))) return rc;
+        } else {
+            if ((rc = launch_front(fs, fe, st))) return rc;
+            if (last && (rc = mark(LIDER_PHASE_ROUTE))) return rc;
+        }
         // guard: the tensor-core error of one score stays below kTcGuard |q| |mu|
         topc_exact_kernel<<<(unsigned)cdiv(n * 32, 256), 256, g.ncl <= kTopcStageCols ? 8 * g.ncl * 4 : 0, st>>>(
             S, Qc, g.C, g.half_norm, n, g.ncl, g.d, c, kTcGuard * ix->max_cnorm, w.route + q0 * c, trace_route,
@@ -3311,7 +3353,7 @@ int enqueue_search(const lider_index* ix, const float* Q, int64_t nq, int k, int
             return rc;
         }
     }
-    if (!keys_launched && (rc = launch_keys())) return rc;
+    if (!keys_launched && (rc = launch_keys(false))) return rc;
     if (ix->params.route_kind == LIDER_ROUTE_CORE) {
         // Layer-1 centroids retriever: replaces the route of the exact scan
         // (whose per-query error bounds the tensor paths still use)

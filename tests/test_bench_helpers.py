@@ -58,3 +58,14 @@ def test_score_roofline_counts_the_methods_work():
     assert r["executed"]["flop_per_launch"] == 100 * 128 * 256 * 768 * 2
     # probed clusters 0, 1, 2 (364 rows), 4 gathered queries, bitmap words 4 + 7 + 7 + 2
     assert r["unique_bytes"]["bytes_per_launch"] == (364 * 768 * 2 + 4 * 768 * 2 + (4 + 7 + 7 + 2) * 4)
+
+
+def test_launches_per_pass_follows_the_grouping_path():
+    """A pass small enough for the one-block grouping launches three (SIMT:
+    two) kernels fewer than one that takes the multi-kernel grouping."""
+    import bench
+    assert bench.launches_per_pass("f16", 10_000, 8, 256) == 17          # mid: 80,000 pairs
+    assert bench.launches_per_pass("f16", 12_500, 16, 1_024) == 20       # batched pass: 200,000 pairs
+    assert bench.launches_per_pass("simt", 10_000, 8, 256) == 8
+    assert bench.launches_per_pass("bf16", 16_384, 8, 256) == 16         # exactly 131,072 pairs
+    assert bench.launches_per_pass("tensor", 100, 8, 5_000) == 20        # too many clusters
