@@ -2305,7 +2305,8 @@ constexpr int kHistCand = 2048;
 // result is then the largest word sharing the r-th smallest word's bits down
 // to the last digit taken, an upper bound on it.
 template <class Word>
-__device__ uint32_t block_kth_smallest(Word word, int n, int r, uint32_t* hist256, int* s_pick, int passes = 4) {
+__device__ __forceinline__ uint32_t block_kth_smallest(Word word, int n, int r, uint32_t* hist256, int* s_pick,
+                                                     int passes = 4) {
     __shared__ uint32_t s_lohi[2];
     const int tid = threadIdx.x, lane = tid & 31;
     // the words' common leading bits (those of their minimum and maximum) are
