@@ -127,3 +127,53 @@ def test_server_refusals_and_drain():
         ids, _ = t.result(timeout=0)
         assert ids.shape == (7, 10) and np.all(ids[:, 0] >= 0)
     ix.free()
+
+
+@pytest.mark.gpu
+def test_concurrent_host_searches_equal_device_search():
+    """Two host threads, each calling lider_search_host on a stream of its
+    own (how the bench keeps two batches in flight end to end), get the ids
+    and scores lider_search returns on device buffers, bit for bit; the
+    batches are large enough for the chunked copy-in, and both threads' searches
+    share the index's second stream."""
+    import threading
+
+    import torch
+    from paper_2205_00970_b300 import lider, synth
+
+    d, k, c = 128, 20, 4
+    X = synth.corpus(3, 120_000, d, 64, 0.3, None)
+    Q = synth.queries(3, 12_000, d, 64, 0.3, None)
+    A, b = synth.projections(3, 4, 16, d, 1.0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    ix = lider.Index(t(X), None, t(A), t(b), L=4, m=16, W=1.0, rmi_leaves=64, r0=2, score_mode=lider.SCORE_F16,
+                     n_clusters=32, kmeans_iters=4, kmeans_sample=16_384, seed=3)
+    ref_ids, ref_sc = ix.search(t(Q), k, c)
+    ref_ids, ref_sc = ref_ids.cpu().numpy(), ref_sc.cpu().numpy()
+    Qh = torch.from_numpy(Q).pin_memory()
+    slices = [(0, 12_000), (1_000, 9_000), (5_000, 12_000), (0, 4_096)]
+    out, errors = {}, []
+
+    def work(tid):
+        try:
+            s = torch.cuda.Stream()
+            for j, (lo, hi) in enumerate(slices):
+                ids = torch.empty((hi - lo, k), dtype=torch.int64).pin_memory()
+                sc = torch.empty((hi - lo, k), dtype=torch.float32).pin_memory()
+                ix.search_host(Qh[lo:hi], k, c, ids, sc, stream=s)
+                out[(tid, j)] = (ids.numpy().copy(), sc.numpy().copy())
+        except Exception as e:  # surfaced in the main thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(2)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert not errors, errors
+    assert len(out) == 2 * len(slices)
+    for (tid, j), (ids, sc) in out.items():
+        lo, hi = slices[j]
+        assert np.array_equal(ids, ref_ids[lo:hi]), (tid, j)
+        assert np.array_equal(sc, ref_sc[lo:hi]), (tid, j)
+    ix.free()
