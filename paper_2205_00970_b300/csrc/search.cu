@@ -2393,12 +2393,12 @@ __global__ void __launch_bounds__(512) select_hist_kernel(
         DenseArgs da, int c, int ks, const float* __restrict__ qguard, const float* __restrict__ qbound, int guarded,
         int so, int64_t* __restrict__ out_ids, float* __restrict__ out_scores, int32_t* __restrict__ trace_ucount,
         int32_t* __restrict__ redo, int32_t* __restrict__ redo_count, unsigned long long* counters) {
-    __shared__ uint32_t hist[kHistBins];          // also: the threads' maxima (need <= blockDim)
-    __shared__ uint64_t cand[kHistCand];
+    __shared__ uint32_t hist[kHistBins];          // bin counts; then (way 1) the listed chunks
+    __shared__ uint64_t cand[kHistCand];          // collected keys
     __shared__ PairRow s_pr[LIDER_MAX_C];
     __shared__ int s_total, s_cnt, s_bt, s_band, s_nh, s_ct;
     __shared__ float s_thr;
-    __shared__ uint32_t s_rhist[256];              // radix select
+    __shared__ uint32_t s_rhist[256];              // radix select; sub-bins of the chosen bin
     __shared__ int s_pick[2];
     __shared__ int s_wo[LIDER_MAX_C + 1];          // first chunk-maximum word of each pair
     const int64_t q = blockIdx.x;
