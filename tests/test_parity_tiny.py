@@ -288,6 +288,39 @@ def test_near_tied_kth_scores_at_d768_equal_simt(mode):
 
 
 @pytest.mark.parametrize("mode", [0, 3], ids=["tensor", "f16"])
+def test_wide_rows_beyond_1024_equal_simt(mode):
+    """d = 1,104 (more than 32 float4 per lane): the re-score takes its
+    generic row loop instead of an unrolled instance; ids and scores equal
+    the SIMT path's bit for bit, with no band overflow (so the re-score, not
+    the band kernel, writes every result)."""
+    import torch
+    rng = np.random.default_rng(41)
+    d, n = 1104, 3000
+    centers = rng.standard_normal((12, d))
+    X = centers[rng.integers(0, 12, n)] + 0.5 * rng.standard_normal((n, d))
+    X = (X / np.linalg.norm(X, axis=1, keepdims=True)).astype(np.float32)
+    C = X[rng.choice(n, 6, replace=False)].copy()
+    cfg = dict(L=2, m=8, W=0.7, leaves=8, r0=3, B=1, k=10)
+    A = rng.standard_normal((cfg["L"] * cfg["m"], d)).astype(np.float32)
+    b = (rng.random(cfg["L"] * cfg["m"]) * cfg["W"]).astype(np.float32)
+    Q = (centers[rng.integers(0, 12, 40)] + 0.5 * rng.standard_normal((40, d))).astype(np.float32)
+    Qd = torch.from_numpy(Q).cuda()
+    out, overflow = {}, 0
+    for m in (mode, 1):
+        g = F.gpu_index(dict(cfg, score_mode=m), X, C, A, b)
+        for c in (1, 3):
+            ids, sc, st = g.search(Qd, cfg["k"], c, stats=True)
+            out[m, c] = (ids.cpu().numpy(), sc.cpu().numpy())
+            overflow += st["select_overflow"]
+        g.free()
+    assert overflow == 0
+    for c in (1, 3):
+        assert np.array_equal(out[mode, c][0], out[1, c][0]), c
+        assert np.array_equal(out[mode, c][1].view(np.uint32), out[1, c][1].view(np.uint32)), c
+    assert np.all(out[mode, 3][0] >= 0)
+
+
+@pytest.mark.parametrize("mode", [0, 3], ids=["tensor", "f16"])
 def test_route_with_tied_centroids_equals_simt(mode):
     """Centroids in groups of equal rows (exactly tied routing scores) and of
     rows 1e-7 apart (within the tensor-core error guard): the tensor path
