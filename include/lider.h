@@ -277,9 +277,14 @@ int lider_export_projections(const lider_index* index, float* A_host, float* b_h
  *   out_scores  device, nq x k FP32: exact inner products, -inf where id = -1;
  *   stats       host or NULL; when non-NULL the call synchronises `stream`
  *               and fills the counters;
- *   stream      all work is enqueued on it.
+ *   stream      the call's work is ordered on it: in the tensor score modes
+ *               (default route) independent steps run on a second stream the
+ *               index owns, forked from `stream` and joined back to it by
+ *               events, so the results are complete in `stream` order, and
+ *               under stream capture those steps join the captured graph.
  * Scratch memory comes from a stream-ordered pool owned by the index, so
- * concurrent calls on different streams are safe; the index is read-only.
+ * concurrent calls on different streams are safe (their steps on the
+ * index's second stream run one after another); the index is read-only.
  * nq == 0 is a no-op.  Errors: LIDER_EINVAL (null index/pointers, nq < 0,
  * k < 1, c < 1 or c > n_clusters), LIDER_ELIMIT (caps), LIDER_ENOMEM,
  * LIDER_ECUDA. */
